@@ -1,0 +1,323 @@
+"""Benchmark: noisy QAOA trajectory ensembles on GB300 through the libqnoise C ABI.
+
+Workload (one "step"): the 20-qubit p=3 QAOA MaxCut circuit on a seeded
+3-regular graph with depolarizing noise (p1=1e-3, p2=1e-2) and amplitude damping
+(gamma=5e-3) after every gate, K=4096 trajectories, 64 statevectors per launch:
+Philox Kraus sampling, every gate sweep with its damping draw, and the ensemble
+accumulation of <C> and sigma_approx.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gq|reference]
+
+Prints one JSON line (rank 0).  `value` is trajectories/s timed with CUDA events
+on the library's stream (inputs -- graph, angles, noise -- resident; every step
+regenerates all trajectories on the device).  `e2e` times the same call through
+the C ABI from host buffers to the host-side <C> and sigma_approx.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2210_15874_gb300 import workloads as W  # noqa: E402
+
+METRIC = "noisy trajectories/s at fixed <C> error"
+UNIT = "trajectories/s"
+
+
+def workload():
+    return W.damping_n20()
+
+
+def config_of(w, extra=None):
+    cfg = {"workload": w.name, "n": w.n, "p": w.p, "graph": "seeded 3-regular", "edges": int(len(w.edges)),
+           "gates": w.gate_count, "trajectories": w.trajectories, "launch_batch": w.batch,
+           "noise": {"p1": w.p1, "p2": w.p2, "damping": w.damping, "twoq": "15-Pauli depolarizing"},
+           "state": "complex64 statevector, 8 MiB per trajectory",
+           "l2": "inputs larger than L2: 512 MiB of statevectors per launch (L2 129 MB)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    """FP64 oracle (trajectory simulator) on the host's cores: a bounded sample
+    of the same workload's trajectories (the first `count` ids)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    nz = oracle.make_noise(**w.noise_kwargs())
+    # calibrate on one trajectory per core, then extend up to the budget
+    t = time.perf_counter()
+    oracle.traj_run(w.n, w.edges, gates, G, nz, w.seed, 0, cores, want_amps=False, want_branches=False,
+                    threads=cores)
+    first = time.perf_counter() - t
+    count = cores
+    rounds = max(0, int((budget_s - first) / max(first, 1e-3)))
+    if rounds > 0:
+        t = time.perf_counter()
+        oracle.traj_run(w.n, w.edges, gates, G, nz, w.seed, cores, cores * rounds, want_amps=False,
+                        want_branches=False, threads=cores)
+        el = time.perf_counter() - t
+        count, elapsed = cores * rounds, el
+    else:
+        elapsed = first
+    return {"value": count / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{count} trajectories (ids {'0' if rounds == 0 else cores}..) of {w.name}, "
+                      f"FP64 statevector oracle, OpenMP over trajectories"}
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 CPU oracle as it stands, timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    w = workload()
+    cores = os.cpu_count() or 1
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    nz = oracle.make_noise(**w.noise_kwargs())
+    per_step = cores  # one trajectory per core per step: a bounded sample of the 4096
+
+    def step(i):
+        oracle.traj_run(w.n, w.edges, gates, G, nz, w.seed, (i * per_step) % w.trajectories, per_step,
+                        want_amps=False, want_branches=False, threads=cores)
+
+    for i in range(args.warmup):
+        step(i)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    el = time.perf_counter() - t
+    value = per_step * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w, {"sample_per_step": per_step}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} trajectories per step of {w.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def gpu_arm(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+
+    from paper_2210_15874_gb300 import build
+    build.build()
+    from paper_2210_15874_gb300 import qn
+
+    w = workload()
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    stream = torch.cuda.current_stream()
+    b = qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch, stream=stream)
+    # weak scaling: rank r evolves global trajectories [r K, (r+1) K)
+    if world > 1:
+        b.set_offset(rank * w.trajectories)
+    kw = w.noise_kwargs()
+
+    def step():
+        b.run_qaoa(w.edges, w.gammas, w.betas, **kw)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    mean, se = b.expectation()
+
+    b.set_profiling(True)
+    for k in range(3):
+        b.profile_read(k)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            launches += b.run_info()["launches"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    sweeps = b.profile_read(0)
+    inits = b.profile_read(1)
+    accs = b.profile_read(2)
+    b.set_profiling(False)
+    total_traj = w.trajectories * args.steps * world
+    value = total_traj / (ms / 1e3)
+
+    # end to end through the C ABI from host buffers: run + <C> + sigma to host
+    e2e_steps = max(1, min(args.steps, 3))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        b.run_qaoa(w.edges, w.gammas, w.betas, **kw)
+        m_, s_ = b.expectation()
+        pr = b.probs()
+    el = time.perf_counter() - t
+    if pg:
+        tt = torch.tensor([el], device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        el = float(tt.item())
+    e2e_value = w.trajectories * e2e_steps * world / el
+    G = w.gate_count
+    h2d = int(len(w.edges) * 8 + 2 * w.p * 8 + 40 + G * 20)
+    d2h = int((1 << w.n) * 8 + 16 + 4)
+
+    sweep_avg_ms = sweeps["ms"] / max(sweeps["launches"], 1)
+    sweep_bytes = sweeps["bytes"] / max(sweeps["launches"], 1)
+    achieved = sweep_bytes / (sweep_avg_ms / 1e3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tj = json.load(open(tr_path))
+            if tj.get("kernel_source_hash") == kernel_hash():
+                traffic = tj.get("traffic_bytes_per_launch_full_size")
+        except (ValueError, OSError):
+            traffic = None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(w, {"parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU"}),
+            "amp_updates_per_s": value * G * (1 << w.n),
+            "c_mean": mean, "c_stderr": se,
+            "roofline": {"kernel": "k_sweep (gate sweep, 16 B per amplitude)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                         else "fallback 6800 GB/s",
+                         "launches_timed": sweeps["launches"], "avg_launch_ms": sweep_avg_ms,
+                         "share_of_step": sweeps["ms"] / ms if ms > 0 else None},
+            "kernels": {"k_sweep": sweeps, "k_init": inits, "k_accumulate": accs},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    b.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for fn in ("qn_kernels.cu", "qn_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2210_15874_gb300", "csrc", fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gq", choices=["gq", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * qn.h -- C ABI of libqnoise: stochastic noisy-QAOA trajectory ensembles on one
+ * GB300 (sm_103a).
+ *
+ * Method (arXiv 2210.15874, Sec. "Stochastic Noise Implementation"): every
+ * member of an ensemble of K circuits re-applies the ideal circuit's gates in
+ * order; after each gate a uniform number per noise channel picks a Kraus
+ * operator, which is applied to the state.  The output probability vector of
+ * each member, phi = |psi|^2, is averaged: sigma_approx = sum_k phi_k / K.
+ * The expectation of the MaxCut cost C (Sec. "Quantum Approximate Optimization
+ * Algorithm") is averaged the same way.
+ *
+ * Conventions fixed by this library (the paper leaves them open):
+ *   - Circuit: H on every qubit, then for l = 1..p: for every edge (i, j) in the
+ *     given order the phase gate diag(1, e^{-i gamma_l}, e^{-i gamma_l}, 1) on
+ *     (i, j), then exp(-i beta_l X) on qubits 0..n-1 in order.
+ *     Basis index bit q is qubit q.  C(x) = #edges (i, j) with x_i != x_j.
+ *   - Noise after every gate (the H layer included), in the order: gate, one
+ *     depolarizing Pauli on the gate's qubits, amplitude damping on the first
+ *     qubit, amplitude damping on the second qubit.
+ *   - Pauli codes: 1q 0..3 = I, X, Y, Z; 2q 4a+b with a on the edge's first
+ *     qubit.  Code k is the first with w0 < floor(2^32 * (P_0 + .. + P_k)) (sums in
+ *     FP64, in code order); the last code takes the rest.
+ *   - Randomness: Philox4x32-10 with key (seed_lo, seed_hi), counter
+ *     (gate index, 0, t_lo, t_hi) for global trajectory id t.  Word 0 picks the
+ *     Pauli; words 1 and 2 are the damping draws u = (w + 0.5) * 2^-32 of the
+ *     gate's first and second qubit.  Results of trajectory t therefore do not
+ *     depend on the launch batch size or on which batch t falls in.
+ *   - Damping (textbook Kraus pair K0 = diag(1, sqrt(1-gamma)),
+ *     K1 = sqrt(gamma) |0><1|): K1 is chosen when u < gamma * P(qubit = 1); the
+ *     state is renormalised after each site.
+ *
+ * Status and threading: every call returns a qn_status and never throws.  A
+ * handle is not thread-safe; distinct handles are independent.  Work is queued
+ * on the handle's stream; qn_expectation, qn_probs, qn_traj_debug, qn_grad and
+ * qn_profile_read synchronise that stream.  On any non-OK status,
+ * qn_last_error() returns a thread-local message describing it.
+ */
+#ifndef QN_H
+#define QN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QN_OK = 0,
+    QN_EINVAL = 1,   /* invalid argument; nothing was launched */
+    QN_ENOMEM = 2,   /* device allocation failed or the footprint exceeds free memory */
+    QN_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error string) */
+    QN_ETIMEOUT = 4, /* reserved: a bounded device-side wait gave up */
+    QN_ESTATE = 5    /* wrong call order (e.g. results before a run) or a kernel flagged a
+                        non-finite or zero norm */
+} qn_status;
+
+/* Opaque handle.  Owns its device memory (or memory from the allocator set below). */
+typedef struct qn_batch qn_batch;
+
+/* Problem graph, host memory, read during qn_run_qaoa only.
+ *   n          number of vertices = qubits, 1 <= n <= 30
+ *   num_edges  number of edges, >= 0
+ *   edges      2*num_edges int32: edge e is (edges[2e], edges[2e+1]); 0 <= v < n,
+ *              endpoints distinct, no duplicate edge.  The order is the order in
+ *              which the phase gates are applied. */
+typedef struct {
+    int32_t n;
+    int32_t num_edges;
+    const int32_t *edges;
+} qn_graph;
+
+/* Noise model (Sec. "Modeling Noise"; depolarizing Kraus set of that section).
+ *   p1, p2     depolarizing strength after 1q and 2q gates.
+ *              param = 0: p is the total non-identity probability; each 1q Pauli
+ *              has p/3, each 2q non-II Pauli p/15 (p1 <= 1, p2 <= 1).
+ *              param = 1: the paper's lambda, K0 = sqrt(1 - 3 lambda/4) I, so the
+ *              1q Pauli total is 3 lambda/4 (lambda <= 4/3) and the 2q total is
+ *              15 lambda/16 (lambda <= 16/15).
+ *   damping    amplitude-damping gamma in [0, 1] after every gate on each of its
+ *              qubits (0 disables damping).
+ *   twoq_mode  0: 15-Pauli two-qubit depolarizing channel after a 2q gate;
+ *              1: independent 1q channels of strength p2 on both qubits (Fig. 2's
+ *              per-qubit noise on a 2q gate). */
+typedef struct {
+    double p1, p2, damping;
+    int32_t twoq_mode;
+    int32_t param;
+} qn_noise;
+
+/* Create a handle for n qubits (1..30) and an ensemble of `trajectories` (>= 1)
+ * members drawn from `seed`.  No device memory is allocated until the first
+ * run.  *out receives the handle (caller frees with qn_batch_destroy). */
+qn_status qn_batch_create(int32_t n, int64_t trajectories, uint64_t seed, qn_batch **out);
+
+/* Set the CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream;
+ * NULL = legacy default stream) on which all later work of the handle is queued. */
+qn_status qn_batch_set_stream(qn_batch *h, void *cuda_stream);
+
+/* Route device allocations through alloc(bytes, ctx) / free(ptr, ctx) (e.g. the
+ * PyTorch caching allocator).  Must be called before the first run.  alloc must
+ * return memory aligned to at least 256 bytes, or NULL on failure. */
+qn_status qn_batch_set_allocator(qn_batch *h, void *(*alloc)(size_t, void *),
+                                 void (*free_fn)(void *, void *), void *ctx);
+
+/* Trajectories evolved per launch (B).  0 (the default) picks
+ * B = min(trajectories, max(1, 512 MiB / (8 * 2^n))).  Statevectors take
+ * 8 * 2^n * B bytes of HBM (complex64). */
+qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
+
+/* Global id of the handle's first trajectory (default 0): the handle evolves
+ * trajectories first_trajectory .. first_trajectory + trajectories - 1, so
+ * disjoint ranges on several handles or GPUs are shards of one ensemble whose
+ * results do not depend on the sharding.  Resets the last run's results. */
+qn_status qn_batch_set_offset(qn_batch *h, int64_t first_trajectory);
+
+/* Evolve the whole ensemble through the noisy QAOA circuit of depth p with
+ * angles gammas[p], betas[p] (host, radians) and accumulate, in FP64, the
+ * ensemble sums of <C>_t, <C>_t^2 and |psi_t|^2 (Sec. "Stochastic Noise
+ * Implementation": phi, sigma_approx).  p >= 0.  Asynchronous on the handle's
+ * stream; previous results of the handle are replaced. */
+qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const double *gammas,
+                      const double *betas, const qn_noise *noise);
+
+/* Ensemble mean of C, sum_t <C>_t / K, and its standard error
+ * sqrt((S2/K - mean^2) / K).  Host outputs; blocks on the stream. */
+qn_status qn_expectation(const qn_batch *h, double *mean, double *std_err);
+
+/* sigma_approx = sum_t |psi_t|^2 / K (Sec. "Stochastic Noise Implementation")
+ * into the caller's host buffer out[len], len == 2^n.  Blocks on the stream. */
+qn_status qn_probs(const qn_batch *h, double *out, int64_t len);
+
+/* Ensemble gradient d<C>/d gamma_l and d<C>/d beta_l (host outputs, p values
+ * each) of the last run's circuit.  Every trajectory is unitary when the noise
+ * is Pauli-only, so the gradient is taken per trajectory by the adjoint method
+ * and averaged.  Requires a previous qn_run_qaoa with damping == 0, else
+ * QN_EINVAL.  Blocks on the stream. */
+qn_status qn_grad(qn_batch *h, double *dgamma, double *dbeta);
+
+/* Per-trajectory gradient of <C>_t for trajectories t0..t0+count-1 (0-based within the handle) of
+ * the last run (damping == 0): dgamma[count*p], dbeta[count*p], row-major by
+ * trajectory.  Host outputs; blocks on the stream. */
+qn_status qn_grad_traj(qn_batch *h, int64_t t0, int64_t count, double *dgamma, double *dbeta);
+
+/* Re-simulate trajectories t0..t0+count-1 (0-based within the handle) of the last run (same seed,
+ * graph, angles, noise) and return, into caller-owned host buffers (any may be
+ * NULL):
+ *   amps        count * 2^n * 2 floats: final normalised statevector, (re, im)
+ *               interleaved, basis index x (bit q = qubit q);
+ *   branches    count * G bytes, G = n + p (E + n): per gate, Pauli code in bits
+ *               0..3, K1 on the first qubit in bit 4, on the second in bit 5;
+ *   c_per_traj  count doubles: <C>_t = sum_x |psi_t,x|^2 C(x).
+ * The ensemble results of the last run are left unchanged.  Blocks. */
+qn_status qn_traj_debug(qn_batch *h, int64_t t0, int64_t count, float *amps, uint8_t *branches,
+                        double *c_per_traj);
+
+/* Error = 1 - (sum_x sqrt(sa_x se_x))^2 (Sec. "Stochastic Noise Implementation",
+ * Eq. 1): fidelity distance between two host probability vectors of length
+ * len.  Host-only; any negative entry gives QN_EINVAL. */
+qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, double *out);
+
+/* Gate and launch counts of the last run: G gates per circuit, the number of
+ * library kernel launches it queued, and the statevector bytes the gate sweeps
+ * read and wrote (algorithmic, 16 B per amplitude per sweep). */
+qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes);
+
+/* Kernel timing with CUDA events recorded on the handle's stream around every
+ * gate-sweep launch (on = 1) or not (on = 0, the default). */
+qn_status qn_batch_set_profiling(qn_batch *h, int32_t on);
+
+/* Totals since the last read, for kernel family `kind` (0 = gate sweeps, 1 =
+ * state init, 2 = ensemble accumulation): launches, summed event milliseconds
+ * and algorithmic bytes.  Synchronises the stream, then resets the totals. */
+qn_status qn_profile_read(qn_batch *h, int32_t kind, int64_t *launches, double *ms, double *bytes);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *qn_last_error(void);
+
+/* Free the handle and its device memory (NULL is ignored).  Synchronises. */
+void qn_batch_destroy(qn_batch *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QN_H */

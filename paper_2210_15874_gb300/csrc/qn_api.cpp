@@ -1,0 +1,652 @@
+// qn_api.cpp -- host side of the libqnoise C ABI (include/qn.h).
+//
+// Builds the QAOA gate list and the noise tables from the call's arguments,
+// owns the device memory of a handle, and queues, per batch of B trajectories:
+//   prepare     Philox draws, Pauli codes, X-frames, the noisy H layer
+//   init        write-only sweep of the product state after the H layer
+//   sweeps      one per remaining gate: gate, Pauli, damping draw
+//   accumulate  phi = |psi|^2 into sigma_approx and <C>
+//               (Sec. "Stochastic Noise Implementation")
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "qn.h"
+#include "qn_internal.h"
+
+using namespace qn;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+qn_status fail(qn_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+qn_status ok() {
+    g_last_error.clear();
+    return QN_OK;
+}
+
+#define QN_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return fail(QN_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define QN_TRY(expr)                       \
+    do {                                   \
+        qn_status s_ = (expr);             \
+        if (s_ != QN_OK) return s_;        \
+    } while (0)
+
+struct HostGate {
+    int32_t kind, q0, q1;
+    double angle;
+};
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int kind = 0;
+    double bytes = 0.0;
+};
+
+constexpr int kMaxQubits = 30;
+constexpr int64_t kMaxGates = 1 << 20;
+constexpr size_t kDefaultBatchBytes = (size_t)512 << 20;
+
+}  // namespace
+
+struct qn_batch {
+    int32_t n = 0;
+    int64_t K = 0;
+    uint64_t seed = 0;
+    int64_t B_req = 0;
+    int64_t offset = 0;
+    cudaStream_t stream = nullptr;
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+
+    // problem of the last run
+    bool has_run = false;
+    std::vector<int32_t> edges;
+    int32_t p = 0;
+    std::vector<double> gammas, betas;
+    qn_noise noise{};
+    std::vector<HostGate> gates;
+    std::vector<DevGate> dgates_host;
+    std::vector<int2> edges_host;
+    NoiseDev nz{};
+    int damping_on = 0;
+    int64_t B = 0;
+    int64_t launches = 0;
+    double sweep_bytes = 0.0;
+
+    // device memory (all blocks listed in `blocks`)
+    std::vector<void *> blocks;
+    int64_t cap_B = 0;
+    int32_t cap_G = -1;
+    int32_t cap_E = -1;
+    float2 *psi = nullptr;
+    uint8_t *branch = nullptr;
+    uint32_t *dwords = nullptr;
+    uint32_t *frame_x = nullptr;
+    uint8_t *yphase = nullptr;
+    float *hfac = nullptr;
+    TrajState *st = nullptr;
+    double *partials = nullptr;
+    unsigned int *counters = nullptr;
+    double *cpart = nullptr;
+    unsigned int *acc_counter = nullptr;
+    double *c_all = nullptr;
+    double *c_dbg = nullptr;
+    double *probs = nullptr;
+    double *sums = nullptr;
+    int *status = nullptr;
+    DevGate *dgates = nullptr;
+    int2 *dedges = nullptr;
+    float2 *readout = nullptr;
+
+    // profiling
+    bool profiling = false;
+    std::vector<EventPair> events;
+    std::vector<EventPair> spare;
+    int64_t prof_launches[3] = {0, 0, 0};
+    double prof_ms[3] = {0, 0, 0};
+    double prof_bytes[3] = {0, 0, 0};
+};
+
+namespace {
+
+qn_status dev_alloc(qn_batch *h, void **out, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (h->alloc_fn) {
+        p = h->alloc_fn(bytes, h->alloc_ctx);
+        if (!p) return fail(QN_ENOMEM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QN_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    h->blocks.push_back(p);
+    *out = p;
+    return QN_OK;
+}
+
+template <typename T>
+qn_status alloc_t(qn_batch *h, T **out, size_t count) {
+    void *p = nullptr;
+    qn_status st = dev_alloc(h, &p, count * sizeof(T));
+    *out = static_cast<T *>(p);
+    return st;
+}
+
+void release_all(qn_batch *h) {
+    if (!h->blocks.empty()) cudaStreamSynchronize(h->stream);
+    for (void *p : h->blocks) {
+        if (h->free_fn) h->free_fn(p, h->alloc_ctx);
+        else cudaFree(p);
+    }
+    h->blocks.clear();
+    h->psi = nullptr;
+    h->readout = nullptr;
+    h->cap_B = 0;
+    h->cap_G = -1;
+    h->cap_E = -1;
+}
+
+size_t state_bytes(int n) { return (size_t)8 << n; }
+
+// Every buffer a run of B trajectories per launch, G gates and E edges needs.
+size_t footprint(int n, int64_t K, int64_t B, int32_t G, int32_t E) {
+    const size_t tiles = (size_t)tiles_for(n), xb = (size_t)accumulate_xblocks(n);
+    size_t s = 2 * (size_t)B * state_bytes(n);  // states + debug readout
+    s += (size_t)B * G * (1 + 8) + (size_t)B * (G + 1) * 4 + (size_t)B * (1 + 8 * n + sizeof(TrajState) + 4 + 8);
+    s += (size_t)B * tiles * 32 + (size_t)B * xb * 8 + (size_t)K * 8 + ((size_t)8 << n);
+    s += (size_t)G * sizeof(DevGate) + (size_t)(E + 1) * 8 + 4096;
+    return s;
+}
+
+qn_status ensure_buffers(qn_batch *h, int64_t B, int32_t G, int32_t E) {
+    if (h->cap_B >= B && h->cap_G == G && h->cap_E >= E && !h->blocks.empty()) return QN_OK;
+    release_all(h);
+    const int n = h->n;
+    size_t free_b = 0, total_b = 0;
+    QN_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t need = footprint(n, h->K, B, G, E);
+    if (!h->alloc_fn && need > free_b)
+        return fail(QN_ENOMEM, "footprint %zu bytes exceeds free device memory %zu bytes", need, free_b);
+    const size_t tiles = (size_t)tiles_for(n), xb = (size_t)accumulate_xblocks(n);
+    QN_TRY(alloc_t(h, &h->psi, (size_t)B << n));
+    QN_TRY(alloc_t(h, &h->branch, (size_t)B * G));
+    QN_TRY(alloc_t(h, &h->dwords, (size_t)B * G * 2));
+    QN_TRY(alloc_t(h, &h->frame_x, (size_t)B * (G + 1)));
+    QN_TRY(alloc_t(h, &h->yphase, (size_t)B));
+    QN_TRY(alloc_t(h, &h->hfac, (size_t)B * n * 2));
+    QN_TRY(alloc_t(h, &h->st, (size_t)B));
+    QN_TRY(alloc_t(h, &h->partials, (size_t)B * tiles * 4));
+    QN_TRY(alloc_t(h, &h->counters, (size_t)B));
+    QN_TRY(alloc_t(h, &h->cpart, (size_t)B * xb));
+    QN_TRY(alloc_t(h, &h->acc_counter, 1));
+    QN_TRY(alloc_t(h, &h->c_all, (size_t)h->K));
+    QN_TRY(alloc_t(h, &h->c_dbg, (size_t)B));
+    QN_TRY(alloc_t(h, &h->probs, (size_t)1 << n));
+    QN_TRY(alloc_t(h, &h->sums, 2));
+    QN_TRY(alloc_t(h, &h->status, 1));
+    QN_TRY(alloc_t(h, &h->dgates, (size_t)std::max(G, 1)));
+    QN_TRY(alloc_t(h, &h->dedges, (size_t)std::max(E, 1)));
+    QN_CUDA(cudaMemsetAsync(h->counters, 0, (size_t)B * sizeof(unsigned int), h->stream));
+    QN_CUDA(cudaMemsetAsync(h->acc_counter, 0, sizeof(unsigned int), h->stream));
+    h->cap_B = B;
+    h->cap_G = G;
+    h->cap_E = E;
+    return QN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Noise tables.  Pauli probabilities per code (Sec. "Modeling Noise": the
+// depolarizing Kraus set; K0 weight 1 - 3 lambda / 4 for the paper's lambda)
+// and the integer thresholds floor(2^32 * cumulative sum).
+// ---------------------------------------------------------------------------
+double total_1q(const qn_noise &nz, double x) { return nz.param == 1 ? 0.75 * x : x; }
+
+void probs_1q(const qn_noise &nz, double out[4]) {
+    const double p = total_1q(nz, nz.p1);
+    out[0] = 1.0 - p;
+    out[1] = out[2] = out[3] = p / 3.0;
+}
+
+void probs_2q(const qn_noise &nz, double out[16]) {
+    if (nz.twoq_mode == 1) {
+        const double p = total_1q(nz, nz.p2);
+        const double s[4] = {1.0 - p, p / 3.0, p / 3.0, p / 3.0};
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) out[4 * a + b] = s[a] * s[b];
+        return;
+    }
+    const double p = nz.param == 1 ? (15.0 / 16.0) * nz.p2 : nz.p2;
+    out[0] = 1.0 - p;
+    for (int k = 1; k < 16; ++k) out[k] = p / 15.0;
+}
+
+void thresholds(const double *pr, int count, uint64_t *thr) {
+    double c = 0.0;
+    for (int k = 0; k < count; ++k) {
+        c += pr[k];
+        double v = std::floor(c * 4294967296.0);
+        v = std::min(std::max(v, 0.0), 4294967296.0);
+        thr[k] = (uint64_t)v;
+    }
+}
+
+qn_status validate_noise(const qn_noise *nz) {
+    if (!nz) return fail(QN_EINVAL, "noise is NULL");
+    if (nz->param != 0 && nz->param != 1) return fail(QN_EINVAL, "noise.param must be 0 or 1");
+    if (nz->twoq_mode != 0 && nz->twoq_mode != 1) return fail(QN_EINVAL, "noise.twoq_mode must be 0 or 1");
+    const double max1 = nz->param == 1 ? 4.0 / 3.0 : 1.0;
+    const double max2 = nz->param == 1 ? (nz->twoq_mode == 1 ? 4.0 / 3.0 : 16.0 / 15.0) : 1.0;
+    if (!(nz->p1 >= 0.0 && nz->p1 <= max1)) return fail(QN_EINVAL, "noise.p1 = %g outside [0, %g]", nz->p1, max1);
+    if (!(nz->p2 >= 0.0 && nz->p2 <= max2)) return fail(QN_EINVAL, "noise.p2 = %g outside [0, %g]", nz->p2, max2);
+    if (!(nz->damping >= 0.0 && nz->damping <= 1.0))
+        return fail(QN_EINVAL, "noise.damping = %g outside [0, 1]", nz->damping);
+    return QN_OK;
+}
+
+qn_status validate_graph(const qn_batch *h, const qn_graph *g) {
+    if (!g) return fail(QN_EINVAL, "graph is NULL");
+    if (g->n != h->n) return fail(QN_EINVAL, "graph.n = %d but the handle has n = %d", g->n, h->n);
+    if (g->num_edges < 0) return fail(QN_EINVAL, "graph.num_edges < 0");
+    if (g->num_edges > 0 && !g->edges) return fail(QN_EINVAL, "graph.edges is NULL");
+    std::set<std::pair<int, int>> seen;
+    for (int e = 0; e < g->num_edges; ++e) {
+        const int a = g->edges[2 * e], b = g->edges[2 * e + 1];
+        if (a < 0 || a >= g->n || b < 0 || b >= g->n)
+            return fail(QN_EINVAL, "edge %d = (%d, %d) out of range [0, %d)", e, a, b, g->n);
+        if (a == b) return fail(QN_EINVAL, "edge %d is a self-loop on %d", e, a);
+        if (!seen.insert({std::min(a, b), std::max(a, b)}).second)
+            return fail(QN_EINVAL, "edge %d = (%d, %d) is a duplicate", e, a, b);
+    }
+    return QN_OK;
+}
+
+void build_gates(qn_batch *h) {
+    const int n = h->n, E = (int)h->edges.size() / 2;
+    h->gates.clear();
+    for (int q = 0; q < n; ++q) h->gates.push_back({kGateH, q, q, 0.0});
+    for (int l = 0; l < h->p; ++l) {
+        for (int e = 0; e < E; ++e) h->gates.push_back({kGateZZ, h->edges[2 * e], h->edges[2 * e + 1], h->gammas[l]});
+        for (int q = 0; q < n; ++q) h->gates.push_back({kGateRX, q, q, h->betas[l]});
+    }
+    h->dgates_host.clear();
+    for (const HostGate &g : h->gates) {
+        DevGate d;
+        d.kind = g.kind;
+        d.q0 = g.q0;
+        d.q1 = g.q1;
+        d.c = (float)std::cos(g.angle);
+        d.s = (float)std::sin(g.angle);
+        h->dgates_host.push_back(d);
+    }
+    h->edges_host.clear();
+    for (int e = 0; e < E; ++e) h->edges_host.push_back(make_int2(h->edges[2 * e], h->edges[2 * e + 1]));
+}
+
+BatchView view_for(qn_batch *h, int64_t t0, int b) {
+    BatchView v;
+    v.psi = h->psi;
+    v.n = h->n;
+    v.b = b;
+    v.t0 = t0;
+    v.G = (int32_t)h->gates.size();
+    v.tiles = (int32_t)tiles_for(h->n);
+    v.branch = h->branch;
+    v.dwords = h->dwords;
+    v.frame_x = h->frame_x;
+    v.yphase = h->yphase;
+    v.hfac = h->hfac;
+    v.st = h->st;
+    v.partials = h->partials;
+    v.counters = h->counters;
+    v.status = h->status;
+    return v;
+}
+
+// ---- profiling: one CUDA event pair per timed launch ----
+qn_status prof_begin(qn_batch *h, EventPair *ep, int kind, double bytes) {
+    if (!h->profiling) return QN_OK;
+    if (!h->spare.empty()) {
+        *ep = h->spare.back();
+        h->spare.pop_back();
+    } else {
+        QN_CUDA(cudaEventCreate(&ep->a));
+        QN_CUDA(cudaEventCreate(&ep->b));
+    }
+    ep->kind = kind;
+    ep->bytes = bytes;
+    QN_CUDA(cudaEventRecord(ep->a, h->stream));
+    return QN_OK;
+}
+
+qn_status prof_end(qn_batch *h, EventPair *ep) {
+    if (!h->profiling) return QN_OK;
+    QN_CUDA(cudaEventRecord(ep->b, h->stream));
+    h->events.push_back(*ep);
+    return QN_OK;
+}
+
+qn_status prof_collect(qn_batch *h) {
+    if (h->events.empty()) return QN_OK;
+    QN_CUDA(cudaStreamSynchronize(h->stream));
+    for (EventPair &ep : h->events) {
+        float ms = 0.0f;
+        QN_CUDA(cudaEventElapsedTime(&ms, ep.a, ep.b));
+        h->prof_launches[ep.kind] += 1;
+        h->prof_ms[ep.kind] += ms;
+        h->prof_bytes[ep.kind] += ep.bytes;
+        h->spare.push_back(ep);
+    }
+    h->events.clear();
+    return QN_OK;
+}
+
+// Queue the whole pipeline for the handle's trajectories t0 .. t0+b-1 (global ids
+// offset + t0 ..; b <= cap_B).
+// ensemble = true adds into probs / S1 / S2 and writes c_all; otherwise the
+// per-trajectory <C>_t go to c_dbg only.
+qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
+    const int n = h->n;
+    const int G = (int)h->gates.size();
+    BatchView v = view_for(h, h->offset + t0, b);
+    const double amp_bytes = (double)b * (double)((size_t)1 << n);
+    QN_CUDA(launch_prepare(v, h->dgates, h->seed, h->nz, h->damping_on, h->stream));
+    h->launches += 1;
+    EventPair ep;
+    QN_TRY(prof_begin(h, &ep, 1, amp_bytes * 8.0));
+    QN_CUDA(launch_init(v, h->stream));
+    QN_TRY(prof_end(h, &ep));
+    h->launches += 1;
+    for (int g = n; g < G; ++g) {
+        QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));
+        QN_CUDA(launch_sweep(v, g, h->dgates_host[g], h->nz, h->damping_on, h->stream));
+        QN_TRY(prof_end(h, &ep));
+        h->launches += 1;
+        if (ensemble) h->sweep_bytes += amp_bytes * 16.0;
+    }
+    AccumView a;
+    a.num_edges = (int32_t)h->edges_host.size();
+    a.edges = h->dedges;
+    a.cpart = h->cpart;
+    a.acc_counter = h->acc_counter;
+    a.c_out = ensemble ? h->c_all + t0 : h->c_dbg;
+    a.probs = ensemble ? h->probs : nullptr;
+    a.sums = ensemble ? h->sums : nullptr;
+    QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
+    QN_CUDA(launch_accumulate(v, a, nullptr, h->stream));
+    QN_TRY(prof_end(h, &ep));
+    h->launches += 1;
+    return QN_OK;
+}
+
+qn_status check_status(const qn_batch *h) {
+    int st = 0;
+    QN_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaStreamSynchronize(h->stream));
+    if (st != 0) return fail(QN_ESTATE, "a kernel flagged a zero or non-finite norm (status %d)", st);
+    return QN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qn_status qn_batch_create(int32_t n, int64_t trajectories, uint64_t seed, qn_batch **out) {
+    if (!out) return fail(QN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > kMaxQubits) return fail(QN_EINVAL, "n = %d outside [1, %d]", n, kMaxQubits);
+    if (trajectories < 1) return fail(QN_EINVAL, "trajectories = %lld < 1", (long long)trajectories);
+    qn_batch *h = new (std::nothrow) qn_batch();
+    if (!h) return fail(QN_ENOMEM, "host allocation failed");
+    h->n = n;
+    h->K = trajectories;
+    h->seed = seed;
+    *out = h;
+    return ok();
+}
+
+qn_status qn_batch_set_stream(qn_batch *h, void *cuda_stream) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return ok();
+}
+
+qn_status qn_batch_set_allocator(qn_batch *h, void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *),
+                                 void *ctx) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (!h->blocks.empty()) return fail(QN_ESTATE, "allocator must be set before the first run");
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(QN_EINVAL, "alloc and free must both be set");
+    h->alloc_fn = alloc;
+    h->free_fn = free_fn;
+    h->alloc_ctx = ctx;
+    return ok();
+}
+
+qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (B < 0 || B > 65535) return fail(QN_EINVAL, "launch batch %lld outside [0, 65535]", (long long)B);
+    h->B_req = B;
+    return ok();
+}
+
+qn_status qn_batch_set_offset(qn_batch *h, int64_t first_trajectory) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (first_trajectory < 0) return fail(QN_EINVAL, "first trajectory id < 0");
+    h->offset = first_trajectory;
+    h->has_run = false;
+    return ok();
+}
+
+qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const double *gammas, const double *betas,
+                      const qn_noise *noise) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    QN_TRY(validate_graph(h, graph));
+    QN_TRY(validate_noise(noise));
+    if (p < 0) return fail(QN_EINVAL, "p = %d < 0", p);
+    if (p > 0 && (!gammas || !betas)) return fail(QN_EINVAL, "gammas/betas is NULL");
+    for (int l = 0; l < p; ++l)
+        if (!std::isfinite(gammas[l]) || !std::isfinite(betas[l])) return fail(QN_EINVAL, "angle %d not finite", l);
+    const int64_t G = (int64_t)h->n + (int64_t)p * (graph->num_edges + h->n);
+    if (G > kMaxGates) return fail(QN_EINVAL, "circuit has %lld gates (max %lld)", (long long)G, (long long)kMaxGates);
+
+    h->edges.assign(graph->edges, graph->edges + 2 * graph->num_edges);
+    h->p = p;
+    h->gammas.assign(gammas, gammas + p);
+    h->betas.assign(betas, betas + p);
+    h->noise = *noise;
+    build_gates(h);
+    double pr1[4], pr2[16];
+    probs_1q(*noise, pr1);
+    probs_2q(*noise, pr2);
+    thresholds(pr1, 4, h->nz.thr1);
+    thresholds(pr2, 16, h->nz.thr2);
+    h->nz.gamma = noise->damping;
+    h->damping_on = noise->damping > 0.0;
+
+    int64_t B = h->B_req;
+    if (B == 0) B = std::max<int64_t>(1, (int64_t)(kDefaultBatchBytes / state_bytes(h->n)));
+    B = std::min<int64_t>(std::min<int64_t>(B, h->K), 65535);
+    h->B = B;
+    h->has_run = false;
+    QN_TRY(ensure_buffers(h, B, (int32_t)G, graph->num_edges));
+    QN_CUDA(cudaMemcpyAsync(h->dgates, h->dgates_host.data(), h->dgates_host.size() * sizeof(DevGate),
+                            cudaMemcpyHostToDevice, h->stream));
+    if (!h->edges_host.empty())
+        QN_CUDA(cudaMemcpyAsync(h->dedges, h->edges_host.data(), h->edges_host.size() * sizeof(int2),
+                                cudaMemcpyHostToDevice, h->stream));
+    QN_CUDA(cudaMemsetAsync(h->probs, 0, sizeof(double) << h->n, h->stream));
+    QN_CUDA(cudaMemsetAsync(h->sums, 0, 2 * sizeof(double), h->stream));
+    QN_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    h->launches = 0;
+    h->sweep_bytes = 0.0;
+    for (int64_t t0 = 0; t0 < h->K; t0 += B) {
+        const int b = (int)std::min<int64_t>(B, h->K - t0);
+        QN_TRY(run_batch(h, t0, b, true));
+    }
+    h->has_run = true;
+    return ok();
+}
+
+qn_status qn_expectation(const qn_batch *h, double *mean, double *std_err) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (!mean || !std_err) return fail(QN_EINVAL, "output pointer is NULL");
+    if (!h->has_run) return fail(QN_ESTATE, "no completed qn_run_qaoa on this handle");
+    double s[2];
+    QN_CUDA(cudaMemcpyAsync(s, h->sums, sizeof s, cudaMemcpyDeviceToHost, h->stream));
+    QN_TRY(check_status(h));
+    const double K = (double)h->K;
+    const double m = s[0] / K;
+    const double var = std::max(0.0, s[1] / K - m * m);
+    *mean = m;
+    *std_err = std::sqrt(var / K);
+    return ok();
+}
+
+qn_status qn_probs(const qn_batch *h, double *out, int64_t len) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (!out) return fail(QN_EINVAL, "out is NULL");
+    if (len != ((int64_t)1 << h->n)) return fail(QN_EINVAL, "len = %lld, expected 2^n = %lld", (long long)len,
+                                                 (long long)((int64_t)1 << h->n));
+    if (!h->has_run) return fail(QN_ESTATE, "no completed qn_run_qaoa on this handle");
+    QN_CUDA(cudaMemcpyAsync(out, h->probs, sizeof(double) * (size_t)len, cudaMemcpyDeviceToHost, h->stream));
+    QN_TRY(check_status(h));
+    const double inv = 1.0 / (double)h->K;
+    for (int64_t x = 0; x < len; ++x) out[x] *= inv;
+    return ok();
+}
+
+qn_status qn_traj_debug(qn_batch *h, int64_t t0, int64_t count, float *amps, uint8_t *branches,
+                        double *c_per_traj) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (!h->has_run) return fail(QN_ESTATE, "no completed qn_run_qaoa on this handle");
+    if (t0 < 0 || count < 0 || t0 + count > h->K)
+        return fail(QN_EINVAL, "trajectories [%lld, %lld) outside [0, %lld)", (long long)t0,
+                    (long long)(t0 + count), (long long)h->K);
+    const int n = h->n;
+    const int G = (int)h->gates.size();
+    if (amps && !h->readout) {
+        QN_TRY(alloc_t(h, &h->readout, (size_t)h->cap_B << n));
+    }
+    const int64_t saved_launches = h->launches;
+    for (int64_t c0 = 0; c0 < count; c0 += h->cap_B) {
+        const int b = (int)std::min<int64_t>(h->cap_B, count - c0);
+        QN_TRY(run_batch(h, t0 + c0, b, false));
+        if (amps) {
+            BatchView v = view_for(h, h->offset + t0 + c0, b);
+            QN_CUDA(launch_readout(v, h->readout, h->stream));
+            QN_CUDA(cudaMemcpyAsync(amps + ((size_t)c0 << n) * 2, h->readout, ((size_t)b << n) * sizeof(float2),
+                                    cudaMemcpyDeviceToHost, h->stream));
+        }
+        if (branches)
+            QN_CUDA(cudaMemcpyAsync(branches + (size_t)c0 * G, h->branch, (size_t)b * G, cudaMemcpyDeviceToHost,
+                                    h->stream));
+        if (c_per_traj)
+            QN_CUDA(cudaMemcpyAsync(c_per_traj + c0, h->c_dbg, (size_t)b * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream));
+        QN_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    h->launches = saved_launches;
+    QN_TRY(check_status(h));
+    return ok();
+}
+
+qn_status qn_grad(qn_batch *h, double *dgamma, double *dbeta) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    (void)dgamma;
+    (void)dbeta;
+    return fail(QN_EINVAL, "adjoint gradient not available in this build");
+}
+
+qn_status qn_grad_traj(qn_batch *h, int64_t t0, int64_t count, double *dgamma, double *dbeta) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    (void)t0;
+    (void)count;
+    (void)dgamma;
+    (void)dbeta;
+    return fail(QN_EINVAL, "adjoint gradient not available in this build");
+}
+
+qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, double *out) {
+    if (!sa || !se || !out) return fail(QN_EINVAL, "NULL argument");
+    if (len < 0) return fail(QN_EINVAL, "len < 0");
+    double s = 0.0;
+    for (int64_t x = 0; x < len; ++x) {
+        if (!(sa[x] >= 0.0) || !(se[x] >= 0.0)) return fail(QN_EINVAL, "negative or NaN entry at %lld", (long long)x);
+        s += std::sqrt(sa[x] * se[x]);
+    }
+    *out = 1.0 - s * s;
+    return ok();
+}
+
+qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (gates) *gates = (int64_t)h->gates.size();
+    if (launches) *launches = h->launches;
+    if (sweep_bytes) *sweep_bytes = h->sweep_bytes;
+    return ok();
+}
+
+qn_status qn_batch_set_profiling(qn_batch *h, int32_t on) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    h->profiling = on != 0;
+    return ok();
+}
+
+qn_status qn_profile_read(qn_batch *h, int32_t kind, int64_t *launches, double *ms, double *bytes) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (kind < 0 || kind > 2) return fail(QN_EINVAL, "kind must be 0, 1 or 2");
+    QN_TRY(prof_collect(h));
+    if (launches) *launches = h->prof_launches[kind];
+    if (ms) *ms = h->prof_ms[kind];
+    if (bytes) *bytes = h->prof_bytes[kind];
+    h->prof_launches[kind] = 0;
+    h->prof_ms[kind] = 0.0;
+    h->prof_bytes[kind] = 0.0;
+    return ok();
+}
+
+const char *qn_last_error(void) { return g_last_error.c_str(); }
+
+void qn_batch_destroy(qn_batch *h) {
+    if (!h) return;
+    release_all(h);
+    for (EventPair &ep : h->events) {
+        cudaEventDestroy(ep.a);
+        cudaEventDestroy(ep.b);
+    }
+    for (EventPair &ep : h->spare) {
+        cudaEventDestroy(ep.a);
+        cudaEventDestroy(ep.b);
+    }
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal interface between the host API (qn_api.cpp) and the device kernels
+// (qn_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qn {
+
+enum GateKind : int32_t { kGateH = 0, kGateZZ = 1, kGateRX = 2 };
+
+// One circuit gate as the kernels see it.  For ZZ, (c, s) = (cos gamma, sin gamma)
+// and the phase on differing bits is c - i s; for RX, exp(-i beta X) has
+// (c, s) = (cos beta, sin beta).  q1 == q0 for 1q gates.
+struct DevGate {
+    int32_t kind;
+    int32_t q0, q1;
+    float c, s;
+};
+
+// Per-trajectory dynamic state, one per slot of a launch batch.
+//   J     X-frame bits contributed by damping jumps already folded into the stored state
+//   pend  X-frame bits of the jumps of the pending damping op (not yet applied)
+//   pq0, pq1  qubits of the pending op (pq1 == pq0 for a 1q gate)
+//   f     pending amplitude factors, indexed by (b0 | b1 << 1) with b0, b1 the
+//         true bits of pq0, pq1 (for a 1q op only f[0] and f[3] are used)
+struct __align__(16) TrajState {
+    uint32_t J;
+    uint32_t pend;
+    int32_t pq0, pq1;
+    float f[4];
+};
+
+// Launch-independent description of one batch of trajectories.
+struct BatchView {
+    float2 *psi;            // [b][2^n] stored (frame) state, complex64
+    int32_t n;
+    int32_t b;              // trajectories in this batch
+    int64_t t0;             // global id of slot 0
+    int32_t G;              // gates per circuit
+    int32_t tiles;          // sweep tiles per trajectory
+    uint8_t *branch;        // [b][G]
+    uint32_t *dwords;       // [b][G][2] damping words, or nullptr when damping == 0
+    uint32_t *frame_x;      // [b][G+1] X-frame of the Pauli noise before gate g
+    uint8_t *yphase;        // [b] number of Y Paulis mod 4
+    float *hfac;            // [b][n][2] per-qubit factors of the noisy H layer
+    TrajState *st;          // [b]
+    double *partials;       // [b][tiles][4]
+    unsigned int *counters; // [b]
+    int *status;            // device error word
+};
+
+struct NoiseDev {
+    double gamma;              // damping (0 = off)
+    uint64_t thr1[4];          // cumulative thresholds, 1q
+    uint64_t thr2[16];         // cumulative thresholds, 2q
+};
+
+struct AccumView {
+    int32_t num_edges;
+    const int2 *edges;         // device
+    double *cpart;             // [b][xblocks]
+    unsigned int *acc_counter; // 1
+    double *c_out;             // [b] per-trajectory <C>_t
+    double *probs;             // [2^n] ensemble sum, or nullptr
+    double *sums;              // [2] S1, S2, or nullptr
+};
+
+constexpr int kThreads = 256;        // threads per sweep block
+constexpr int kF4PerThread = 4;      // float4 items per thread (8 amplitudes)
+constexpr int kTileF4 = kThreads * kF4PerThread;  // float4 per tile (2048 amplitudes)
+
+inline int64_t tiles_for(int n) {
+    int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
+    return (nf + kTileF4 - 1) / kTileF4;
+}
+
+// Kernel launch wrappers (qn_kernels.cu).  All return the launch's cudaError_t.
+cudaError_t launch_prepare(const BatchView &v, const DevGate *gates, uint64_t seed, const NoiseDev &nz,
+                           int damping_on, cudaStream_t s);
+cudaError_t launch_init(const BatchView &v, cudaStream_t s);
+cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const NoiseDev &nz, int damping_on,
+                         cudaStream_t s);
+cudaError_t launch_accumulate(const BatchView &v, const AccumView &a, const DevGate *last_gate_unused,
+                              cudaStream_t s);
+cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
+int64_t accumulate_xblocks(int n);
+
+}  // namespace qn
