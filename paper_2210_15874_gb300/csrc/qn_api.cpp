@@ -113,7 +113,7 @@ struct qn_batch {
     TrajState *st = nullptr;
     double *partials = nullptr;
     unsigned int *counters = nullptr;
-    double *cpart = nullptr;
+    double *inv_norm = nullptr;
     unsigned int *acc_counter = nullptr;
     double *c_all = nullptr;
     double *c_dbg = nullptr;
@@ -179,10 +179,10 @@ size_t state_bytes(int n) { return (size_t)8 << n; }
 
 // Every buffer a run of B trajectories per launch, G gates and E edges needs.
 size_t footprint(int n, int64_t K, int64_t B, int32_t G, int32_t E) {
-    const size_t tiles = (size_t)tiles_for(n), xb = (size_t)accumulate_xblocks(n);
+    const size_t tiles = (size_t)tiles_for(n);
     size_t s = 2 * (size_t)B * state_bytes(n);  // states + debug readout
     s += (size_t)B * G * (1 + 8) + (size_t)B * (G + 1) * 4 + (size_t)B * (1 + 8 * n + sizeof(TrajState) + 4 + 8);
-    s += (size_t)B * tiles * 32 + (size_t)B * xb * 8 + (size_t)K * 8 + ((size_t)8 << n);
+    s += (size_t)B * tiles * 32 + (size_t)B * 8 + (size_t)K * 8 + ((size_t)8 << n);
     s += (size_t)G * sizeof(DevGate) + (size_t)(E + 1) * 8 + 4096;
     return s;
 }
@@ -196,7 +196,7 @@ qn_status ensure_buffers(qn_batch *h, int64_t B, int32_t G, int32_t E) {
     const size_t need = footprint(n, h->K, B, G, E);
     if (!h->alloc_fn && need > free_b)
         return fail(QN_ENOMEM, "footprint %zu bytes exceeds free device memory %zu bytes", need, free_b);
-    const size_t tiles = (size_t)tiles_for(n), xb = (size_t)accumulate_xblocks(n);
+    const size_t tiles = (size_t)tiles_for(n);
     QN_TRY(alloc_t(h, &h->psi, (size_t)B << n));
     QN_TRY(alloc_t(h, &h->branch, (size_t)B * G));
     QN_TRY(alloc_t(h, &h->dwords, (size_t)B * G * 2));
@@ -206,7 +206,7 @@ qn_status ensure_buffers(qn_batch *h, int64_t B, int32_t G, int32_t E) {
     QN_TRY(alloc_t(h, &h->st, (size_t)B));
     QN_TRY(alloc_t(h, &h->partials, (size_t)B * tiles * 4));
     QN_TRY(alloc_t(h, &h->counters, (size_t)B));
-    QN_TRY(alloc_t(h, &h->cpart, (size_t)B * xb));
+    QN_TRY(alloc_t(h, &h->inv_norm, (size_t)B));
     QN_TRY(alloc_t(h, &h->acc_counter, 1));
     QN_TRY(alloc_t(h, &h->c_all, (size_t)h->K));
     QN_TRY(alloc_t(h, &h->c_dbg, (size_t)B));
@@ -326,6 +326,7 @@ BatchView view_for(qn_batch *h, int64_t t0, int b) {
     v.hfac = h->hfac;
     v.st = h->st;
     v.partials = h->partials;
+    v.inv_norm = h->inv_norm;
     v.counters = h->counters;
     v.status = h->status;
     return v;
@@ -395,15 +396,20 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     AccumView a;
     a.num_edges = (int32_t)h->edges_host.size();
     a.edges = h->dedges;
-    a.cpart = h->cpart;
     a.acc_counter = h->acc_counter;
     a.c_out = ensemble ? h->c_all + t0 : h->c_dbg;
     a.probs = ensemble ? h->probs : nullptr;
     a.sums = ensemble ? h->sums : nullptr;
     QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
-    QN_CUDA(launch_accumulate(v, a, nullptr, h->stream));
+    QN_CUDA(launch_observe(v, a, h->stream));
     QN_TRY(prof_end(h, &ep));
     h->launches += 1;
+    if (ensemble) {
+        QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
+        QN_CUDA(launch_probs(v, a, h->stream));
+        QN_TRY(prof_end(h, &ep));
+        h->launches += 1;
+    }
     return QN_OK;
 }
 

@@ -46,6 +46,7 @@ struct BatchView {
     float *hfac;            // [b][n][2] per-qubit factors of the noisy H layer
     TrajState *st;          // [b]
     double *partials;       // [b][tiles][4]
+    double *inv_norm;       // [b] 1 / ||psi||^2 of the final state (set by k_observe)
     unsigned int *counters; // [b]
     int *status;            // device error word
 };
@@ -59,7 +60,6 @@ struct NoiseDev {
 struct AccumView {
     int32_t num_edges;
     const int2 *edges;         // device
-    double *cpart;             // [b][xblocks]
     unsigned int *acc_counter; // 1
     double *c_out;             // [b] per-trajectory <C>_t
     double *probs;             // [2^n] ensemble sum, or nullptr
@@ -81,8 +81,8 @@ cudaError_t launch_prepare(const BatchView &v, const DevGate *gates, uint64_t se
 cudaError_t launch_init(const BatchView &v, cudaStream_t s);
 cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const NoiseDev &nz, int damping_on,
                          cudaStream_t s);
-cudaError_t launch_accumulate(const BatchView &v, const AccumView &a, const DevGate *last_gate_unused,
-                              cudaStream_t s);
+cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
+cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
 int64_t accumulate_xblocks(int n);
 

@@ -455,117 +455,180 @@ __global__ void __launch_bounds__(kThreads) k_sweep(BatchView v, int g, DevGate 
 }
 
 // ---------------------------------------------------------------------------
-// Ensemble accumulation (after the last gate): applies the last pending
-// damping op on the fly, then phi -> |psi|^2.  A block owns 2048 basis states x
-// (true index) and loops over the batch, so probs[x] gets one FP64 update per
-// batch (fixed order over batches and trajectories) and C(x) is computed once per
-// x.  <C>_t partials per (t, block) are summed by the last block in fixed order.
+// Observables of the final state.  The last pending damping op is applied on
+// the fly.  k_observe reduces, per trajectory, N_t = ||psi_t||^2 and
+// sum_x |psi_t,x|^2 C(x) in FP64 (per-amplitude FP64 adds: this pass runs once
+// per trajectory, so its FP64 cost is small next to the gate sweeps), then the
+// last block of the trajectory stores 1/N_t and <C>_t = sum |psi|^2 C / N_t:
+// the final state is normalised exactly (the paper takes psi normalised before
+// phi = |psi|^2 is formed).  k_probs then adds |psi_t,x|^2 / N_t over the batch
+// into sigma's FP64 sums, one fixed-order update per basis state x and batch.
 // ---------------------------------------------------------------------------
-constexpr int kAccChunk = 32;
+__device__ __forceinline__ int cut_of(uint32_t x, int num_edges, const int2 *__restrict__ edges) {
+    int cnt = 0;
+    for (int j = 0; j < num_edges; ++j) {
+        const int2 ed = edges[j];
+        cnt += (int)(((x >> ed.x) ^ (x >> ed.y)) & 1u);
+    }
+    return cnt;
+}
 
-__global__ void __launch_bounds__(kThreads) k_accumulate(BatchView v, AccumView a, int64_t xblocks) {
+__global__ void __launch_bounds__(kThreads) k_observe(BatchView v, AccumView a) {
+    const int t = blockIdx.y;
+    const int tile = blockIdx.x;
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
+    __shared__ SweepCtx sc;
+    __shared__ double redd[kThreads / 32][2];
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        const TrajState s = v.st[t];
+        SweepCtx c;
+        c.Fa = v.frame_x[(size_t)t * (v.G + 1) + v.G] ^ s.J;
+        c.Fb = c.Fa ^ s.pend;  // final frame
+        c.Fc = 0;
+        c.pq0 = s.pq0;
+        c.pq1 = s.pq1;
+        for (int k = 0; k < 4; ++k) c.f[k] = s.f[k];
+        c.code = 0;
+        sc = c;
+    }
+    __syncthreads();
+    const SweepCtx c = sc;
+    const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)t << n));
+    double sn = 0.0, scut = 0.0;
+#pragma unroll
+    for (int k = 0; k < kF4PerThread; ++k) {
+        const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
+        if (f < nf) {
+            const float4 val = p4[f];
+            const uint32_t y = (uint32_t)(2 * f);
+            const float f0 = pend_factor(c, y), f1 = pend_factor(c, y | 1u);
+            const float p0 = f0 * f0 * (val.x * val.x + val.y * val.y);
+            const float p1 = f1 * f1 * (val.z * val.z + val.w * val.w);
+            const int c0 = cut_of(y ^ c.Fb, a.num_edges, a.edges);
+            const int c1 = cut_of((y | 1u) ^ c.Fb, a.num_edges, a.edges);
+            sn += (double)p0 + (double)p1;
+            scut += (double)p0 * c0 + (double)p1 * c1;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sn += __shfl_xor_sync(0xffffffffu, sn, off);
+        scut += __shfl_xor_sync(0xffffffffu, scut, off);
+    }
+    if (lane == 0) {
+        redd[warp][0] = sn;
+        redd[warp][1] = scut;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w][threadIdx.x];
+        v.partials[((size_t)t * v.tiles + tile) * 4 + threadIdx.x] = sum;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&v.counters[t], 1u);
+        last = prev == (unsigned)(v.tiles - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < v.tiles; i += kThreads) {
+        const double *pp = v.partials + ((size_t)t * v.tiles + i) * 4;
+        s0 += __ldcg(pp);
+        s1 += __ldcg(pp + 1);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    }
+    __syncthreads();
+    if (lane == 0) {
+        redd[warp][0] = s0;
+        redd[warp][1] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double N = 0.0, C = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            N += redd[w][0];
+            C += redd[w][1];
+        }
+        if (!(N > 0.0) || !isfinite(N)) atomicOr(v.status, 2);
+        v.inv_norm[t] = 1.0 / N;
+        a.c_out[t] = C / N;
+        v.counters[t] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a) {
     const int xb = blockIdx.x;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ float cw[kAccChunk][kThreads / 32];
     __shared__ int last;
-    float cutv[2 * kF4PerThread];
     int64_t fp[kF4PerThread];
+    double acc[2 * kF4PerThread];
 #pragma unroll
     for (int k = 0; k < kF4PerThread; ++k) {
         fp[k] = (int64_t)xb * kTileF4 + threadIdx.x + k * kThreads;
-        for (int e = 0; e < 2; ++e) {
-            const uint32_t x = (uint32_t)(2 * fp[k] + e);
-            int cnt = 0;
-            for (int j = 0; j < a.num_edges; ++j) {
-                const int2 ed = a.edges[j];
-                cnt += (int)(((x >> ed.x) ^ (x >> ed.y)) & 1u);
-            }
-            cutv[2 * k + e] = (float)cnt;
-        }
+        acc[2 * k] = acc[2 * k + 1] = 0.0;
     }
-    float pacc[2 * kF4PerThread];
-    double pacc64[2 * kF4PerThread];
+    for (int tt = 0; tt < v.b; ++tt) {
+        const TrajState s = v.st[tt];
+        const uint32_t Ff = v.frame_x[(size_t)tt * (v.G + 1) + v.G] ^ s.J ^ s.pend;
+        const double inv = v.inv_norm[tt];
+        const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)tt << n));
 #pragma unroll
-    for (int i = 0; i < 2 * kF4PerThread; ++i) { pacc[i] = 0.0f; pacc64[i] = 0.0; }
-    const bool one_amp = (n == 1);  // nf == 1 holds both amplitudes of the only pair
-    for (int t0c = 0; t0c < v.b; t0c += kAccChunk) {
-        const int tend = min(v.b, t0c + kAccChunk);
-        for (int tt = t0c; tt < tend; ++tt) {
-            const TrajState s = v.st[tt];
-            const uint32_t Ff = v.frame_x[(size_t)tt * (v.G + 1) + v.G] ^ s.J ^ s.pend;
-            const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)tt << n));
-            float cp = 0.0f;
+        for (int k = 0; k < kF4PerThread; ++k) {
+            if (fp[k] < nf) {
+                const int64_t f = fp[k] ^ (int64_t)(Ff >> 1);
+                float4 val = p4[f];
+                if (Ff & 1u) val = make_float4(val.z, val.w, val.x, val.y);
 #pragma unroll
-            for (int k = 0; k < kF4PerThread; ++k) {
-                if (fp[k] < nf) {
-                    const int64_t f = fp[k] ^ (int64_t)(Ff >> 1);
-                    float4 val = p4[one_amp ? 0 : f];
-                    if (Ff & 1u) val = make_float4(val.z, val.w, val.x, val.y);
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const uint32_t x = (uint32_t)(2 * fp[k] + e);
-                        const uint32_t tb = x ^ s.pend;
-                        const int idx = (int)(((tb >> s.pq0) & 1u) | (((tb >> s.pq1) & 1u) << 1));
-                        const float fac = s.f[idx];
-                        const float re = e ? val.z : val.x, im = e ? val.w : val.y;
-                        const float pr = fac * fac * (re * re + im * im);
-                        pacc[2 * k + e] += pr;
-                        cp += pr * cutv[2 * k + e];
-                    }
+                for (int e = 0; e < 2; ++e) {
+                    const uint32_t x = (uint32_t)(2 * fp[k] + e);
+                    const uint32_t tb = x ^ s.pend;
+                    const uint32_t b0 = (tb >> s.pq0) & 1u, b1 = (tb >> s.pq1) & 1u;
+                    const float fac = b1 ? (b0 ? s.f[3] : s.f[2]) : (b0 ? s.f[1] : s.f[0]);
+                    const float re = e ? val.z : val.x, im = e ? val.w : val.y;
+                    acc[2 * k + e] = fma((double)(fac * fac * (re * re + im * im)), inv, acc[2 * k + e]);
                 }
             }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
-            if (lane == 0) cw[tt - t0c][warp] = cp;
         }
-#pragma unroll
-        for (int i = 0; i < 2 * kF4PerThread; ++i) { pacc64[i] += (double)pacc[i]; pacc[i] = 0.0f; }
-        __syncthreads();
-        if (threadIdx.x < tend - t0c) {
-            double sum = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) sum += (double)cw[threadIdx.x][w];
-            a.cpart[(size_t)(t0c + threadIdx.x) * xblocks + xb] = sum;
-        }
-        __syncthreads();
     }
     if (a.probs) {
 #pragma unroll
         for (int k = 0; k < kF4PerThread; ++k)
             if (fp[k] < nf) {
-                a.probs[2 * fp[k]] += pacc64[2 * k];
-                a.probs[2 * fp[k] + 1] += pacc64[2 * k + 1];
+                a.probs[2 * fp[k]] += acc[2 * k];
+                a.probs[2 * fp[k] + 1] += acc[2 * k + 1];
             }
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(a.acc_counter, 1u);
-        last = prev == (unsigned)(xblocks - 1);
+        last = prev == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last) return;
+    if (!last || threadIdx.x != 0) return;
     __threadfence();
-    for (int tt = threadIdx.x; tt < v.b; tt += kThreads) {
-        double sum = 0.0;
-        for (int64_t i = 0; i < xblocks; ++i) sum += __ldcg(a.cpart + (size_t)tt * xblocks + i);
-        a.c_out[tt] = sum;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (a.sums) {
-            double s1 = a.sums[0], s2 = a.sums[1];
-            for (int tt = 0; tt < v.b; ++tt) {
-                const double cv = a.c_out[tt];
-                s1 += cv;
-                s2 += cv * cv;
-            }
-            a.sums[0] = s1;
-            a.sums[1] = s2;
+    if (a.sums) {
+        double s1 = a.sums[0], s2 = a.sums[1];
+        for (int tt = 0; tt < v.b; ++tt) {
+            const double cv = __ldcg(a.c_out + tt);
+            s1 += cv;
+            s2 += cv * cv;
         }
-        *a.acc_counter = 0;
+        a.sums[0] = s1;
+        a.sums[1] = s2;
     }
+    *a.acc_counter = 0;
 }
 
 // Readout of psi_x = i^k * D * phi_{x xor F} in the true basis (debug path).
@@ -581,7 +644,8 @@ __global__ void __launch_bounds__(kThreads) k_readout(BatchView v, float2 *out) 
         const float2 a = v.psi[((size_t)t << n) + y];
         const uint32_t tb = (uint32_t)x ^ s.pend;
         const float fac = s.f[((tb >> s.pq0) & 1u) | (((tb >> s.pq1) & 1u) << 1)];
-        float re = a.x * fac, im = a.y * fac;
+        const float sc = fac * (float)sqrt(v.inv_norm[t]);
+        float re = a.x * sc, im = a.y * sc;
         float2 r;
         if (k == 0) r = make_float2(re, im);
         else if (k == 1) r = make_float2(-im, re);
@@ -620,9 +684,13 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
 
 int64_t accumulate_xblocks(int n) { return tiles_for(n); }
 
-cudaError_t launch_accumulate(const BatchView &v, const AccumView &a, const DevGate *, cudaStream_t s) {
-    const int64_t xb = accumulate_xblocks(v.n);
-    k_accumulate<<<(unsigned)xb, kThreads, 0, s>>>(v, a, xb);
+cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s) {
+    k_observe<<<dim3((unsigned)v.tiles, (unsigned)v.b), kThreads, 0, s>>>(v, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s) {
+    k_probs<<<(unsigned)accumulate_xblocks(v.n), kThreads, 0, s>>>(v, a);
     return cudaGetLastError();
 }
 

@@ -70,7 +70,7 @@ def test_plain_n8_matches_oracle(qn):
     orc, gates, G, nz = run_oracle(w)
     compare_trajectories(gpu, orc, w, G)
     K = w.trajectories
-    assert abs(gpu["mean"] - orc["s1"] / K) < 1e-6
+    assert abs(gpu["mean"] - orc["s1"] / K) < 8 * U32 * G * len(w.edges)
     np.testing.assert_allclose(gpu["probs"], orc["probs_sum"] / K, atol=1e-6)
     assert abs(gpu["probs"].sum() - 1) < 1e-6
     assert oracle.error(gpu["probs"], orc["probs_sum"] / K) < 1e-9
