@@ -174,6 +174,33 @@ qn_status qn_batch_set_profiling(qn_batch *h, int32_t on);
  * and algorithmic bytes.  Synchronises the stream, then resets the totals. */
 qn_status qn_profile_read(qn_batch *h, int32_t kind, int64_t *launches, double *ms, double *bytes);
 
+/* Allocation-free variant of qn_run_qaoa for one batch (no counterpart in the
+ * paper).  For callers that must not allocate device memory -- memory owned by
+ * another runtime or pool, a fixed budget carved at start-up, or loops that
+ * cannot take the synchronisation of cudaMalloc/cudaFree.  The library
+ * allocates nothing: the caller passes the statevector workspace and the
+ * outputs, and all other scratch comes from one static 8 MiB device array per
+ * GPU (held until process exit).
+ *   n, graph, p, gammas, betas, noise   as for qn_batch_create and qn_run_qaoa (host)
+ *   seed, first_trajectory, count       trajectories first_trajectory ..
+ *                                       first_trajectory + count - 1 of the
+ *                                       ensemble drawn from seed (count <= 65535)
+ *   psi        device, count * 2^n * 8 bytes, 16-byte aligned: workspace; on
+ *              return it holds the final states in the library's internal form
+ *   c_out      device, count doubles: <C>_t of each trajectory
+ *   probs_out  device, 2^n doubles: overwritten with sum_t |psi_t,x|^2 over the
+ *              batch (divide by count for sigma_approx)
+ *   cuda_stream  cudaStream_t to queue on (NULL = legacy default stream)
+ * Results equal those of a handle with the same seed.  Returns QN_EINVAL when
+ * the batch needs more scratch than the 8 MiB array (lower count or n).  The
+ * first call on each device looks up the array's device address; make it
+ * before any stream capture.  Calls share the array: calls that overlap on the
+ * GPU race.  Blocks until the batch is done. */
+qn_status qn_run_qaoa_noalloc(int32_t n, const qn_graph *graph, int32_t p, const double *gammas,
+                              const double *betas, const qn_noise *noise, uint64_t seed,
+                              int64_t first_trajectory, int32_t count, void *psi, double *c_out,
+                              double *probs_out, void *cuda_stream);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *qn_last_error(void);
 

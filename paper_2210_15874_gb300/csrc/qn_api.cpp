@@ -423,6 +423,42 @@ qn_status check_status(const qn_batch *h) {
 
 }  // namespace
 
+namespace qn {
+
+qn_status set_error(qn_status st, const char *msg) { return fail(st, "%s", msg); }
+
+qn_status plan_qaoa(int32_t n, const qn_graph *graph, int32_t p, const double *gammas, const double *betas,
+                    const qn_noise *noise, QaoaPlan *out) {
+    if (n < 1 || n > kMaxQubits) return fail(QN_EINVAL, "n = %d outside [1, %d]", n, kMaxQubits);
+    qn_batch tmp;  // host-only description; owns no device memory
+    tmp.n = n;
+    QN_TRY(validate_graph(&tmp, graph));
+    QN_TRY(validate_noise(noise));
+    if (p < 0) return fail(QN_EINVAL, "p = %d < 0", p);
+    if (p > 0 && (!gammas || !betas)) return fail(QN_EINVAL, "gammas/betas is NULL");
+    for (int l = 0; l < p; ++l)
+        if (!std::isfinite(gammas[l]) || !std::isfinite(betas[l])) return fail(QN_EINVAL, "angle %d not finite", l);
+    const int64_t G = (int64_t)n + (int64_t)p * (graph->num_edges + n);
+    if (G > kMaxGates) return fail(QN_EINVAL, "circuit has %lld gates (max %lld)", (long long)G, (long long)kMaxGates);
+    tmp.edges.assign(graph->edges, graph->edges + 2 * graph->num_edges);
+    tmp.p = p;
+    tmp.gammas.assign(gammas, gammas + p);
+    tmp.betas.assign(betas, betas + p);
+    build_gates(&tmp);
+    double pr1[4], pr2[16];
+    probs_1q(*noise, pr1);
+    probs_2q(*noise, pr2);
+    thresholds(pr1, 4, out->nz.thr1);
+    thresholds(pr2, 16, out->nz.thr2);
+    out->nz.gamma = noise->damping;
+    out->damping_on = noise->damping > 0.0;
+    out->gates = tmp.dgates_host;
+    out->edges = tmp.edges_host;
+    return QN_OK;
+}
+
+}  // namespace qn
+
 extern "C" {
 
 qn_status qn_batch_create(int32_t n, int64_t trajectories, uint64_t seed, qn_batch **out) {

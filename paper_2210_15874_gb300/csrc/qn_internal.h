@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "qn.h"
+
 namespace qn {
 
 enum GateKind : int32_t { kGateH = 0, kGateZZ = 1, kGateRX = 2 };
@@ -85,5 +89,19 @@ cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t 
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
 int64_t accumulate_xblocks(int n);
+
+// Validated circuit and noise tables of one qn_run_qaoa call, built by the
+// same host code the handle path uses (qn_api.cpp), for entry points that work
+// without a handle.
+struct QaoaPlan {
+    std::vector<DevGate> gates;
+    std::vector<int2> edges;
+    NoiseDev nz;
+    int damping_on;
+};
+qn_status plan_qaoa(int32_t n, const qn_graph *graph, int32_t p, const double *gammas, const double *betas,
+                    const qn_noise *noise, QaoaPlan *out);
+// Record `msg` as this thread's qn_last_error() and return `st`.
+qn_status set_error(qn_status st, const char *msg);
 
 }  // namespace qn

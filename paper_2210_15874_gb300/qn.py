@@ -55,6 +55,8 @@ _SIGS = {
     "qn_run_info": (c_i32, [c_vp, P(c_i64), P(c_i64), P(c_dbl)]),
     "qn_batch_set_profiling": (c_i32, [c_vp, c_i32]),
     "qn_profile_read": (c_i32, [c_vp, c_i32, P(c_i64), P(c_dbl), P(c_dbl)]),
+    "qn_run_qaoa_noalloc": (c_i32, [c_i32, P(qn_graph), c_i32, P(c_dbl), P(c_dbl), P(qn_noise), c_u64, c_i64,
+                                    c_i32, c_vp, c_vp, c_vp, c_vp]),
     "qn_last_error": (ctypes.c_char_p, []),
     "qn_batch_destroy": (None, [c_vp]),
 }
