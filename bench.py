@@ -33,6 +33,7 @@ from paper_2210_15874_gb300 import workloads as W  # noqa: E402
 
 METRIC = "noisy trajectories/s at fixed <C> error"
 UNIT = "trajectories/s"
+PROFILE_PERIOD = 16  # time every 16th gate-sweep launch with a CUDA event pair
 
 
 def workload():
@@ -208,7 +209,7 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     mean, se = b.expectation()
 
-    b.set_profiling(True)
+    b.set_profiling(PROFILE_PERIOD)
     for k in range(3):
         b.profile_read(k)
     if pg:
@@ -232,7 +233,7 @@ def gpu_arm(args):
     sweeps = b.profile_read(0)
     inits = b.profile_read(1)
     accs = b.profile_read(2)
-    b.set_profiling(False)
+    b.set_profiling(0)
     total_traj = w.trajectories * args.steps * world
     value = total_traj / (ms / 1e3)
 
@@ -277,14 +278,15 @@ def gpu_arm(args):
             "config": config_of(w, {"parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU"}),
             "amp_updates_per_s": value * G * (1 << w.n),
             "c_mean": mean, "c_stderr": se,
-            "roofline": {"kernel": "k_sweep (gate sweep, 16 B per amplitude)", "bound": "hbm",
+            "roofline": {"kernel": "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)", "bound": "hbm",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback 6800 GB/s",
                          "launches_timed": sweeps["launches"], "avg_launch_ms": sweep_avg_ms,
-                         "share_of_step": sweeps["ms"] / ms if ms > 0 else None},
-            "kernels": {"k_sweep": sweeps, "k_init": inits, "k_accumulate": accs},
+                         "share_of_step": sweeps["ms"] * PROFILE_PERIOD / ms if ms > 0 else None},
+            "kernels": {"k_sweep_zz+k_sweep_rx (sampled 1/%d)" % PROFILE_PERIOD: sweeps, "k_init": inits,
+                        "k_observe+k_probs": accs},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks.summary(),
@@ -295,6 +297,18 @@ def gpu_arm(args):
     b.close()
     if pg:
         pg.destroy_process_group()
+
+
+def profile_case():
+    """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state)."""
+    from paper_2210_15874_gb300 import build
+    build.build()
+    from paper_2210_15874_gb300 import qn
+
+    w = W.qaoa_workload("ncu_n20_p1_damp", 20, 1, index=1, trajectories=32, batch=32, damping=5e-3)
+    with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        print(json.dumps({"case": w.name, "c": b.expectation()}))
 
 
 def kernel_hash():
@@ -312,7 +326,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gq", choices=["gq", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one small ensemble (n=20, p=1, 32 trajectories in one launch: 256 MiB of "
+                         "statevectors) for ncu captures, then exit")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case()
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -165,9 +165,12 @@ qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, dou
  * read and wrote (algorithmic, 16 B per amplitude per sweep). */
 qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes);
 
-/* Kernel timing with CUDA events recorded on the handle's stream around every
- * gate-sweep launch (on = 1) or not (on = 0, the default). */
-qn_status qn_batch_set_profiling(qn_batch *h, int32_t on);
+/* Kernel timing with CUDA events recorded on the handle's stream: period = 0
+ * (default) records none; period = k >= 1 brackets every k-th gate-sweep
+ * launch and every init / observable launch with an event pair.  An event pair
+ * stops the next sweep from overlapping the previous one's tail, so a period
+ * above 1 keeps the timed stream representative. */
+qn_status qn_batch_set_profiling(qn_batch *h, int32_t period);
 
 /* Totals since the last read, for kernel family `kind` (0 = gate sweeps, 1 =
  * state init, 2 = ensemble accumulation): launches, summed event milliseconds

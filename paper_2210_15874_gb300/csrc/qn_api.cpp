@@ -114,6 +114,7 @@ struct qn_batch {
     double *partials = nullptr;
     unsigned int *counters = nullptr;
     double *inv_norm = nullptr;
+    double *cpart = nullptr;
     unsigned int *acc_counter = nullptr;
     double *c_all = nullptr;
     double *c_dbg = nullptr;
@@ -124,8 +125,10 @@ struct qn_batch {
     int2 *dedges = nullptr;
     float2 *readout = nullptr;
 
-    // profiling
-    bool profiling = false;
+    // profiling: every `prof_period`-th gate-sweep launch (and every init /
+    // observable launch) is bracketed by a CUDA event pair; 0 = off
+    int32_t prof_period = 0;
+    int64_t prof_counter = 0;
     std::vector<EventPair> events;
     std::vector<EventPair> spare;
     int64_t prof_launches[3] = {0, 0, 0};
@@ -182,7 +185,8 @@ size_t footprint(int n, int64_t K, int64_t B, int32_t G, int32_t E) {
     const size_t tiles = (size_t)tiles_for(n);
     size_t s = 2 * (size_t)B * state_bytes(n);  // states + debug readout
     s += (size_t)B * G * (1 + 8) + (size_t)B * (G + 1) * 4 + (size_t)B * (1 + 8 * n + sizeof(TrajState) + 4 + 8);
-    s += (size_t)B * tiles * 32 + (size_t)B * 8 + (size_t)K * 8 + ((size_t)8 << n);
+    s += (size_t)B * tiles * 32 + (size_t)B * 8 + (size_t)B * accumulate_xblocks(n) * 8 + (size_t)K * 8 +
+         ((size_t)8 << n);
     s += (size_t)G * sizeof(DevGate) + (size_t)(E + 1) * 8 + 4096;
     return s;
 }
@@ -207,6 +211,7 @@ qn_status ensure_buffers(qn_batch *h, int64_t B, int32_t G, int32_t E) {
     QN_TRY(alloc_t(h, &h->partials, (size_t)B * tiles * 4));
     QN_TRY(alloc_t(h, &h->counters, (size_t)B));
     QN_TRY(alloc_t(h, &h->inv_norm, (size_t)B));
+    QN_TRY(alloc_t(h, &h->cpart, (size_t)B * accumulate_xblocks(n)));
     QN_TRY(alloc_t(h, &h->acc_counter, 1));
     QN_TRY(alloc_t(h, &h->c_all, (size_t)h->K));
     QN_TRY(alloc_t(h, &h->c_dbg, (size_t)B));
@@ -319,6 +324,7 @@ BatchView view_for(qn_batch *h, int64_t t0, int b) {
     v.t0 = t0;
     v.G = (int32_t)h->gates.size();
     v.tiles = (int32_t)tiles_for(h->n);
+    v.stiles = (int32_t)sweep_tiles_for(h->n);
     v.branch = h->branch;
     v.dwords = h->dwords;
     v.frame_x = h->frame_x;
@@ -333,8 +339,15 @@ BatchView view_for(qn_batch *h, int64_t t0, int b) {
 }
 
 // ---- profiling: one CUDA event pair per timed launch ----
+bool prof_sampled(qn_batch *h, int kind) {
+    if (h->prof_period <= 0) return false;
+    if (kind != 0) return true;
+    return (h->prof_counter++ % h->prof_period) == 0;
+}
+
 qn_status prof_begin(qn_batch *h, EventPair *ep, int kind, double bytes) {
-    if (!h->profiling) return QN_OK;
+    ep->kind = -1;
+    if (!prof_sampled(h, kind)) return QN_OK;
     if (!h->spare.empty()) {
         *ep = h->spare.back();
         h->spare.pop_back();
@@ -349,7 +362,7 @@ qn_status prof_begin(qn_batch *h, EventPair *ep, int kind, double bytes) {
 }
 
 qn_status prof_end(qn_batch *h, EventPair *ep) {
-    if (!h->profiling) return QN_OK;
+    if (ep->kind < 0) return QN_OK;
     QN_CUDA(cudaEventRecord(ep->b, h->stream));
     h->events.push_back(*ep);
     return QN_OK;
@@ -396,6 +409,7 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     AccumView a;
     a.num_edges = (int32_t)h->edges_host.size();
     a.edges = h->dedges;
+    a.cpart = h->cpart;
     a.acc_counter = h->acc_counter;
     a.c_out = ensemble ? h->c_all + t0 : h->c_dbg;
     a.probs = ensemble ? h->probs : nullptr;
@@ -403,13 +417,10 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
     QN_CUDA(launch_observe(v, a, h->stream));
     QN_TRY(prof_end(h, &ep));
-    h->launches += 1;
-    if (ensemble) {
-        QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
-        QN_CUDA(launch_probs(v, a, h->stream));
-        QN_TRY(prof_end(h, &ep));
-        h->launches += 1;
-    }
+    QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
+    QN_CUDA(launch_probs(v, a, h->stream));
+    QN_TRY(prof_end(h, &ep));
+    h->launches += 2;
     return QN_OK;
 }
 
@@ -656,9 +667,11 @@ qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, doub
     return ok();
 }
 
-qn_status qn_batch_set_profiling(qn_batch *h, int32_t on) {
+qn_status qn_batch_set_profiling(qn_batch *h, int32_t period) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
-    h->profiling = on != 0;
+    if (period < 0) return fail(QN_EINVAL, "profiling period < 0");
+    h->prof_period = period;
+    h->prof_counter = 0;
     return ok();
 }
 

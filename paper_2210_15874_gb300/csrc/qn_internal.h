@@ -42,7 +42,8 @@ struct BatchView {
     int32_t b;              // trajectories in this batch
     int64_t t0;             // global id of slot 0
     int32_t G;              // gates per circuit
-    int32_t tiles;          // sweep tiles per trajectory
+    int32_t tiles;          // 2048-amplitude tiles per trajectory (init, observables)
+    int32_t stiles;         // sweep blocks per trajectory (kSub tiles each)
     uint8_t *branch;        // [b][G]
     uint32_t *dwords;       // [b][G][2] damping words, or nullptr when damping == 0
     uint32_t *frame_x;      // [b][G+1] X-frame of the Pauli noise before gate g
@@ -64,6 +65,7 @@ struct NoiseDev {
 struct AccumView {
     int32_t num_edges;
     const int2 *edges;         // device
+    double *cpart;             // [b][xblocks] partial sums of |psi|^2 C(x)
     unsigned int *acc_counter; // 1
     double *c_out;             // [b] per-trajectory <C>_t
     double *probs;             // [2^n] ensemble sum, or nullptr
@@ -74,9 +76,17 @@ constexpr int kThreads = 256;        // threads per sweep block
 constexpr int kF4PerThread = 4;      // float4 items per thread (8 amplitudes)
 constexpr int kTileF4 = kThreads * kF4PerThread;  // float4 per tile (2048 amplitudes)
 
+constexpr int kSub = 4;             // sub-tiles streamed by one sweep block (8192 amplitudes)
+
 inline int64_t tiles_for(int n) {
     int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
     return (nf + kTileF4 - 1) / kTileF4;
+}
+
+// Blocks per trajectory of a gate sweep (each streams kSub tiles).
+inline int64_t sweep_tiles_for(int n) {
+    int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
+    return (nf + (int64_t)kTileF4 * kSub - 1) / ((int64_t)kTileF4 * kSub);
 }
 
 // Kernel launch wrappers (qn_kernels.cu).  All return the launch's cudaError_t.

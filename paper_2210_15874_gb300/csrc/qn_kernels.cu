@@ -256,156 +256,20 @@ __device__ void decide_damping(const BatchView &v, int t, int g, const DevGate &
     v.branch[(size_t)t * v.G + g] |= jb;
 }
 
-template <int KIND, bool DAMP>
-__global__ void __launch_bounds__(kThreads) k_sweep(BatchView v, int g, DevGate gt, double gamma) {
-    const int t = blockIdx.y;
-    const int tile = blockIdx.x;
-    __shared__ SweepCtx sc;
+// Programmatic dependent launch: a sweep may be scheduled while the previous
+// kernel drains; it waits here before touching anything that kernel wrote.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+// Damping marginal of one block -> partials; the last block of the trajectory
+// reduces all partials of the trajectory in fixed order and draws the branch.
+__device__ __forceinline__ void sweep_epilogue(const BatchView &v, int t, int tile, int g, const DevGate &gt,
+                                               double gamma, float acc0, float acc1, float acc2, float acc3) {
     __shared__ float red[kThreads / 32][4];
     __shared__ double redd[kThreads / 32][4];
     __shared__ int last;
-    if (threadIdx.x == 0) {
-        const uint32_t fxg = v.frame_x[(size_t)t * (v.G + 1) + g];
-        const uint32_t fxg1 = v.frame_x[(size_t)t * (v.G + 1) + g + 1];
-        SweepCtx c;
-        c.code = v.branch[(size_t)t * v.G + g] & 15;
-        if (DAMP) {
-            const TrajState s = v.st[t];
-            c.Fa = fxg ^ s.J;
-            c.Fb = c.Fa ^ s.pend;
-            c.Fc = fxg1 ^ s.J ^ s.pend;
-            c.pq0 = s.pq0;
-            c.pq1 = s.pq1;
-            for (int k = 0; k < 4; ++k) c.f[k] = s.f[k];
-        } else {
-            c.Fa = c.Fb = fxg;
-            c.Fc = fxg1;
-            c.pq0 = c.pq1 = 0;
-            c.f[0] = c.f[1] = c.f[2] = c.f[3] = 1.0f;
-        }
-        sc = c;
-    }
-    __syncthreads();
-    const SweepCtx c = sc;
-    const int n = v.n;
-    const int64_t nf = (int64_t)1 << (n - 1);
-    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-
-    if (KIND == kGateZZ) {
-        const int q0 = gt.q0, q1 = gt.q1;
-        const uint32_t za = (uint32_t)(c.code >> 3) & 1u, zb = (uint32_t)(c.code >> 1) & 1u;
-        auto proc = [&](float &re, float &im, uint32_t y) {
-            if (DAMP) {
-                const float fa = pend_factor(c, y);
-                re *= fa;
-                im *= fa;
-            }
-            const uint32_t tb = y ^ c.Fb;
-            const uint32_t b0 = (tb >> q0) & 1u, b1 = (tb >> q1) & 1u;
-            const float sgn = ((za & b0) ^ (zb & b1)) ? -1.0f : 1.0f;
-            const bool diff = (b0 ^ b1) != 0u;
-            const float pc = (diff ? gt.c : 1.0f) * sgn;
-            const float ps = (diff ? gt.s : 0.0f) * sgn;
-            const float nr = re * pc + im * ps;
-            const float ni = im * pc - re * ps;
-            re = nr;
-            im = ni;
-            if (DAMP) {
-                const uint32_t tc = y ^ c.Fc;
-                add_bin(acc, (int)(((tc >> q0) & 1u) | (((tc >> q1) & 1u) << 1)), nr * nr + ni * ni);
-            }
-        };
-        float4 val[kF4PerThread];
-#pragma unroll
-        for (int k = 0; k < kF4PerThread; ++k) {
-            const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
-            if (f < nf) val[k] = p4[f];
-        }
-#pragma unroll
-        for (int k = 0; k < kF4PerThread; ++k) {
-            const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
-            if (f < nf) {
-                const uint32_t y = (uint32_t)(2 * f);
-                proc(val[k].x, val[k].y, y);
-                proc(val[k].z, val[k].w, y | 1u);
-                p4[f] = val[k];
-            }
-        }
-    } else {  // RX
-        const int q = gt.q0;
-        const float cb = gt.c, sb = gt.s;
-        const uint32_t z = (uint32_t)(c.code >> 1) & 1u;
-        const uint32_t fbq = (c.Fb >> q) & 1u;  // true bit of the element with stored bit 0
-        const uint32_t fcq = (c.Fc >> q) & 1u;
-        // (a0 at y0 with stored bit q = 0, a1 at y1 = y0 | 2^q)
-        auto proc = [&](float &r0, float &i0, float &r1, float &i1, uint32_t y0, uint32_t y1) {
-            if (DAMP) {
-                const float f0 = pend_factor(c, y0), f1 = pend_factor(c, y1);
-                r0 *= f0; i0 *= f0; r1 *= f1; i1 *= f1;
-            }
-            float w0r = cb * r0 + sb * i1, w0i = cb * i0 - sb * r1;
-            float w1r = cb * r1 + sb * i0, w1i = cb * i1 - sb * r0;
-            if (z) {  // negate the element whose true bit is 1
-                if (fbq) { w0r = -w0r; w0i = -w0i; } else { w1r = -w1r; w1i = -w1i; }
-            }
-            r0 = w0r; i0 = w0i; r1 = w1r; i1 = w1i;
-            if (DAMP) {
-                const float p0 = w0r * w0r + w0i * w0i, p1 = w1r * w1r + w1i * w1i;
-                acc[0] += fcq ? p1 : p0;
-                acc[3] += fcq ? p0 : p1;
-            }
-        };
-        if (q == 0) {
-            float4 val[kF4PerThread];
-#pragma unroll
-            for (int k = 0; k < kF4PerThread; ++k) {
-                const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
-                if (f < nf) val[k] = p4[f];
-            }
-#pragma unroll
-            for (int k = 0; k < kF4PerThread; ++k) {
-                const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
-                if (f < nf) {
-                    const uint32_t y = (uint32_t)(2 * f);
-                    proc(val[k].x, val[k].y, val[k].z, val[k].w, y, y | 1u);
-                    p4[f] = val[k];
-                }
-            }
-        } else {
-            const int sh = q - 1;
-            const int64_t npairs = nf >> 1;
-            constexpr int kPairs = kF4PerThread / 2;
-            float4 lo[kPairs], hi[kPairs];
-            int64_t flo[kPairs];
-#pragma unroll
-            for (int k = 0; k < kPairs; ++k) {
-                const int64_t r = (int64_t)tile * (kTileF4 / 2) + threadIdx.x + k * kThreads;
-                flo[k] = ((r >> sh) << (sh + 1)) | (r & (((int64_t)1 << sh) - 1));
-                if (r < npairs) {
-                    lo[k] = p4[flo[k]];
-                    hi[k] = p4[flo[k] | ((int64_t)1 << sh)];
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kPairs; ++k) {
-                const int64_t r = (int64_t)tile * (kTileF4 / 2) + threadIdx.x + k * kThreads;
-                if (r < npairs) {
-                    const uint32_t y0 = (uint32_t)(2 * flo[k]);
-                    const uint32_t qb = 1u << q;
-                    proc(lo[k].x, lo[k].y, hi[k].x, hi[k].y, y0, y0 | qb);
-                    proc(lo[k].z, lo[k].w, hi[k].z, hi[k].w, y0 | 1u, y0 | 1u | qb);
-                    p4[flo[k]] = lo[k];
-                    p4[flo[k] | ((int64_t)1 << sh)] = hi[k];
-                }
-            }
-        }
-    }
-
-    if (!DAMP) return;
-
-    // ---- epilogue: marginal of gate g's qubits, then the damping draw ----
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc[4] = {acc0, acc1, acc2, acc3};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         float a = acc[k];
@@ -417,20 +281,20 @@ __global__ void __launch_bounds__(kThreads) k_sweep(BatchView v, int g, DevGate 
     if (threadIdx.x < 4) {
         double s = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) s += (double)red[w][threadIdx.x];
-        v.partials[((size_t)t * v.tiles + tile) * 4 + threadIdx.x] = s;
+        v.partials[((size_t)t * v.stiles + tile) * 4 + threadIdx.x] = s;
         __threadfence();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&v.counters[t], 1u);
-        last = prev == (unsigned)(v.tiles - 1);
+        last = prev == (unsigned)(v.stiles - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < v.tiles; i += kThreads) {
-        const double *pp = v.partials + ((size_t)t * v.tiles + i) * 4;
+    for (int i = threadIdx.x; i < v.stiles; i += kThreads) {
+        const double *pp = v.partials + ((size_t)t * v.stiles + i) * 4;
 #pragma unroll
         for (int k = 0; k < 4; ++k) s[k] += __ldcg(pp + k);
     }
@@ -454,49 +318,275 @@ __global__ void __launch_bounds__(kThreads) k_sweep(BatchView v, int g, DevGate 
     }
 }
 
-// ---------------------------------------------------------------------------
-// Observables of the final state.  The last pending damping op is applied on
-// the fly.  k_observe reduces, per trajectory, N_t = ||psi_t||^2 and
-// sum_x |psi_t,x|^2 C(x) in FP64 (per-amplitude FP64 adds: this pass runs once
-// per trajectory, so its FP64 cost is small next to the gate sweeps), then the
-// last block of the trajectory stores 1/N_t and <C>_t = sum |psi|^2 C / N_t:
-// the final state is normalised exactly (the paper takes psi normalised before
-// phi = |psi|^2 is formed).  k_probs then adds |psi_t,x|^2 / N_t over the batch
-// into sigma's FP64 sums, one fixed-order update per basis state x and batch.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int cut_of(uint32_t x, int num_edges, const int2 *__restrict__ edges) {
-    int cnt = 0;
-    for (int j = 0; j < num_edges; ++j) {
-        const int2 ed = edges[j];
-        cnt += (int)(((x >> ed.x) ^ (x >> ed.y)) & 1u);
+// Context of trajectory t for gate g, read by every thread (uniform addresses,
+// served from L1 after the first warp).
+__device__ __forceinline__ SweepCtx load_ctx(const BatchView &v, int t, int g, bool damp) {
+    SweepCtx c;
+    const uint32_t fxg = v.frame_x[(size_t)t * (v.G + 1) + g];
+    const uint32_t fxg1 = v.frame_x[(size_t)t * (v.G + 1) + g + 1];
+    c.code = v.branch[(size_t)t * v.G + g] & 15;
+    if (damp) {
+        const TrajState s = v.st[t];
+        c.Fa = fxg ^ s.J;
+        c.Fb = c.Fa ^ s.pend;
+        c.Fc = fxg1 ^ s.J ^ s.pend;
+        c.pq0 = s.pq0;
+        c.pq1 = s.pq1;
+        for (int k = 0; k < 4; ++k) c.f[k] = s.f[k];
+    } else {
+        c.Fa = c.Fb = fxg;
+        c.Fc = fxg1;
+        c.pq0 = c.pq1 = 0;
+        c.f[0] = c.f[1] = c.f[2] = c.f[3] = 1.0f;
     }
-    return cnt;
+    return c;
 }
 
-__global__ void __launch_bounds__(kThreads) k_observe(BatchView v, AccumView a) {
+__device__ __forceinline__ void load_tile(float4 (&dst)[kF4PerThread], const float4 *p4, int64_t f0, int64_t nf) {
+#pragma unroll
+    for (int k = 0; k < kF4PerThread; ++k)
+        if (f0 + k * kThreads < nf) dst[k] = p4[f0 + k * kThreads];
+}
+
+// ZZ phase sweep: phi_y *= D_{g-1}(y) * (true bits of q0, q1 differ ? e^{-i gamma} : 1)
+// * (Z part of the Pauli), then bins of |phi|^2 by the true bits after the Pauli.
+// A block streams kSub tiles of one trajectory, prefetching the next tile into
+// registers while it computes the current one.
+template <bool DAMP>
+__global__ void __launch_bounds__(kThreads, 4) k_sweep_zz(BatchView v, int g, DevGate gt, double gamma) {
+    const int t = blockIdx.y;
+    const int tile = blockIdx.x;
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1);
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
+    const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
+    grid_dependency_wait();
+    float4 cur[kF4PerThread], nxt[kF4PerThread];
+    load_tile(cur, p4, fbase, nf);
+    const SweepCtx c = load_ctx(v, t, g, DAMP);
+    const int q0 = gt.q0, q1 = gt.q1;
+    const uint32_t za = (uint32_t)(c.code >> 3) & 1u, zb = (uint32_t)(c.code >> 1) & 1u;
+    // frame bits at the qubits this op reads (per thread constants)
+    const uint32_t fb0 = (c.Fb >> q0) & 1u, fb1 = (c.Fb >> q1) & 1u;
+    const uint32_t fc0 = (c.Fc >> q0) & 1u, fc1 = (c.Fc >> q1) & 1u;
+    const uint32_t fa0 = (c.Fa >> c.pq0) & 1u, fa1 = (c.Fa >> c.pq1) & 1u;
+    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
+    // bit 0 (the two halves of a float4) touches no qubit of this op: one
+    // coefficient per float4
+    const bool pair_uniform = q0 != 0 && q1 != 0 && (!DAMP || (c.pq0 != 0 && c.pq1 != 0));
+#pragma unroll
+    for (int sub = 0; sub < kSub; ++sub) {
+        const int64_t f0 = fbase + (int64_t)sub * kTileF4;
+        if (sub + 1 < kSub) load_tile(nxt, p4, f0 + kTileF4, nf);
+#pragma unroll
+        for (int k = 0; k < kF4PerThread; ++k) {
+            const int64_t f = f0 + k * kThreads;
+            if (f >= nf) continue;
+            const uint32_t y = (uint32_t)(2 * f);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (e == 1 && pair_uniform) break;
+                const uint32_t ye = y | (uint32_t)e;
+                const uint32_t y0 = (ye >> q0) & 1u, y1 = (ye >> q1) & 1u;
+                float fa = 1.0f;
+                if (DAMP) {
+                    const uint32_t a0 = ((ye >> c.pq0) & 1u) ^ fa0, a1 = ((ye >> c.pq1) & 1u) ^ fa1;
+                    fa = a1 ? (a0 ? c.f[3] : c.f[2]) : (a0 ? c.f[1] : c.f[0]);
+                }
+                const uint32_t b0 = y0 ^ fb0, b1 = y1 ^ fb1;
+                const float sgn = ((za & b0) ^ (zb & b1)) ? -fa : fa;
+                const bool diff = (b0 ^ b1) != 0u;
+                const float pc = diff ? gt.c * sgn : sgn;
+                const float ps = diff ? gt.s * sgn : 0.0f;
+                float p;
+                if (pair_uniform) {
+                    const float r0 = cur[k].x, i0 = cur[k].y, r1 = cur[k].z, i1 = cur[k].w;
+                    cur[k].x = r0 * pc + i0 * ps;
+                    cur[k].y = i0 * pc - r0 * ps;
+                    cur[k].z = r1 * pc + i1 * ps;
+                    cur[k].w = i1 * pc - r1 * ps;
+                    p = cur[k].x * cur[k].x + cur[k].y * cur[k].y + cur[k].z * cur[k].z + cur[k].w * cur[k].w;
+                } else {
+                    float &re = e ? cur[k].z : cur[k].x;
+                    float &im = e ? cur[k].w : cur[k].y;
+                    const float nr = re * pc + im * ps, ni = im * pc - re * ps;
+                    re = nr;
+                    im = ni;
+                    p = nr * nr + ni * ni;
+                }
+                if (DAMP) {
+                    const uint32_t idx = (y0 ^ fc0) | ((y1 ^ fc1) << 1);
+                    acc0 += idx == 0u ? p : 0.0f;
+                    acc1 += idx == 1u ? p : 0.0f;
+                    acc2 += idx == 2u ? p : 0.0f;
+                    acc3 += idx == 3u ? p : 0.0f;
+                }
+            }
+            p4[f] = cur[k];
+        }
+        if (sub + 1 < kSub) {
+#pragma unroll
+            for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
+        }
+    }
+    allow_dependent_launch();
+    if (DAMP) sweep_epilogue(v, t, tile, g, gt, gamma, acc0, acc1, acc2, acc3);
+}
+
+// exp(-i beta X) sweep on qubit q: pairs (y0, y0 | 2^q) after D_{g-1}; the Z
+// part of the Pauli negates the element whose true bit is 1; bins by the true
+// bit of q after the Pauli.  The two rows' coefficients carry those signs.
+template <bool DAMP>
+__global__ void __launch_bounds__(kThreads, 4) k_sweep_rx(BatchView v, int g, DevGate gt, double gamma) {
+    const int t = blockIdx.y;
+    const int tile = blockIdx.x;
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1);
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
+    const int q = gt.q0;
+    float acc_lo = 0.0f, acc_hi = 0.0f;  // weight of rows 0 (stored bit 0) and 1
+    grid_dependency_wait();
+    if (q == 0) {
+        const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
+        float4 cur[kF4PerThread], nxt[kF4PerThread];
+        load_tile(cur, p4, fbase, nf);
+        const SweepCtx c = load_ctx(v, t, g, DAMP);
+        const uint32_t fbq = c.Fb & 1u;
+        const float s0 = ((c.code >> 1) & 1) && fbq ? -1.0f : 1.0f;   // row of stored bit 0
+        const float s1 = ((c.code >> 1) & 1) && !fbq ? -1.0f : 1.0f;  // row of stored bit 1
+        const float c0 = gt.c * s0, sn0 = gt.s * s0, c1 = gt.c * s1, sn1 = gt.s * s1;
+#pragma unroll
+        for (int sub = 0; sub < kSub; ++sub) {
+            const int64_t f0 = fbase + (int64_t)sub * kTileF4;
+            if (sub + 1 < kSub) load_tile(nxt, p4, f0 + kTileF4, nf);
+#pragma unroll
+            for (int k = 0; k < kF4PerThread; ++k) {
+                const int64_t f = f0 + k * kThreads;
+                if (f >= nf) continue;
+                const uint32_t y = (uint32_t)(2 * f);
+                const float fa0 = DAMP ? pend_factor(c, y) : 1.0f, fa1 = DAMP ? pend_factor(c, y | 1u) : 1.0f;
+                const float r0 = cur[k].x * fa0, i0 = cur[k].y * fa0, r1 = cur[k].z * fa1, i1 = cur[k].w * fa1;
+                cur[k].x = c0 * r0 + sn0 * i1;
+                cur[k].y = c0 * i0 - sn0 * r1;
+                cur[k].z = c1 * r1 + sn1 * i0;
+                cur[k].w = c1 * i1 - sn1 * r0;
+                acc_lo += cur[k].x * cur[k].x + cur[k].y * cur[k].y;
+                acc_hi += cur[k].z * cur[k].z + cur[k].w * cur[k].w;
+                p4[f] = cur[k];
+            }
+            if (sub + 1 < kSub) {
+#pragma unroll
+                for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
+            }
+        }
+        allow_dependent_launch();
+        if (DAMP) {
+            const uint32_t fcq = c.Fc & 1u;
+            sweep_epilogue(v, t, tile, g, gt, gamma, fcq ? acc_hi : acc_lo, 0.0f, 0.0f, fcq ? acc_lo : acc_hi);
+        }
+        return;
+    }
+    const int sh = q - 1;
+    const int64_t npairs = nf >> 1;
+    constexpr int kPairs = kF4PerThread / 2;
+    const int64_t rbase = (int64_t)tile * (kTileF4 / 2) * kSub + threadIdx.x;
+    const int64_t hib = (int64_t)1 << sh;
+    float4 lo[kPairs], hi[kPairs], nlo[kPairs], nhi[kPairs];
+    auto load_pairs = [&](float4 (&dl)[kPairs], float4 (&dh)[kPairs], int64_t r0) {
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+            const int64_t r = r0 + k * kThreads;
+            const int64_t fl = ((r >> sh) << (sh + 1)) | (r & (hib - 1));
+            if (r < npairs) {
+                dl[k] = p4[fl];
+                dh[k] = p4[fl | hib];
+            }
+        }
+    };
+    load_pairs(lo, hi, rbase);
+    const SweepCtx c = load_ctx(v, t, g, DAMP);
+    const uint32_t fbq = (c.Fb >> q) & 1u;
+    const float s0 = ((c.code >> 1) & 1) && fbq ? -1.0f : 1.0f;
+    const float s1 = ((c.code >> 1) & 1) && !fbq ? -1.0f : 1.0f;
+    const float c0 = gt.c * s0, sn0 = gt.s * s0, c1 = gt.c * s1, sn1 = gt.s * s1;
+    const bool quad_uniform = !DAMP || (c.pq0 != 0 && c.pq0 != q && c.pq1 != 0 && c.pq1 != q);
+#pragma unroll
+    for (int sub = 0; sub < kSub; ++sub) {
+        const int64_t r0 = rbase + (int64_t)sub * (kTileF4 / 2);
+        if (sub + 1 < kSub) load_pairs(nlo, nhi, r0 + kTileF4 / 2);
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+            const int64_t r = r0 + k * kThreads;
+            if (r >= npairs) continue;
+            const int64_t fl = ((r >> sh) << (sh + 1)) | (r & (hib - 1));
+            const uint32_t y0 = (uint32_t)(2 * fl);
+            const uint32_t qb = 1u << q;
+            float fl0, fl1, fh0, fh1;  // pending factors of lo.xy, lo.zw, hi.xy, hi.zw
+            if (!DAMP) {
+                fl0 = fl1 = fh0 = fh1 = 1.0f;
+            } else if (quad_uniform) {
+                fl0 = fl1 = fh0 = fh1 = pend_factor(c, y0);
+            } else {
+                fl0 = pend_factor(c, y0);
+                fl1 = pend_factor(c, y0 | 1u);
+                fh0 = pend_factor(c, y0 | qb);
+                fh1 = pend_factor(c, y0 | 1u | qb);
+            }
+            const float a0r = lo[k].x * fl0, a0i = lo[k].y * fl0, b0r = hi[k].x * fh0, b0i = hi[k].y * fh0;
+            const float a1r = lo[k].z * fl1, a1i = lo[k].w * fl1, b1r = hi[k].z * fh1, b1i = hi[k].w * fh1;
+            lo[k].x = c0 * a0r + sn0 * b0i;
+            lo[k].y = c0 * a0i - sn0 * b0r;
+            hi[k].x = c1 * b0r + sn1 * a0i;
+            hi[k].y = c1 * b0i - sn1 * a0r;
+            lo[k].z = c0 * a1r + sn0 * b1i;
+            lo[k].w = c0 * a1i - sn0 * b1r;
+            hi[k].z = c1 * b1r + sn1 * a1i;
+            hi[k].w = c1 * b1i - sn1 * a1r;
+            acc_lo += lo[k].x * lo[k].x + lo[k].y * lo[k].y + lo[k].z * lo[k].z + lo[k].w * lo[k].w;
+            acc_hi += hi[k].x * hi[k].x + hi[k].y * hi[k].y + hi[k].z * hi[k].z + hi[k].w * hi[k].w;
+            p4[fl] = lo[k];
+            p4[fl | hib] = hi[k];
+        }
+        if (sub + 1 < kSub) {
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k) {
+                lo[k] = nlo[k];
+                hi[k] = nhi[k];
+            }
+        }
+    }
+    allow_dependent_launch();
+    if (DAMP) {
+        const uint32_t fcq = (c.Fc >> q) & 1u;
+        sweep_epilogue(v, t, tile, g, gt, gamma, fcq ? acc_hi : acc_lo, 0.0f, 0.0f, fcq ? acc_lo : acc_hi);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Observables of the final state.  The last pending damping op is applied on
+// the fly.  k_observe reduces N_t = ||psi_t||^2 per trajectory (FP64 above the
+// float4 level) and stores 1/N_t: the final state is normalised exactly before
+// phi = |psi|^2 is formed (the paper takes psi normalised).  k_probs owns a
+// block of 2048 basis states x (true index), computes C(x) once for them and
+// loops over the batch: sigma's FP64 sums get |psi_t,x|^2 / N_t in fixed
+// order, and sum_x |psi_t,x|^2 C(x) is reduced per (t, block); its last block
+// forms <C>_t and adds S1, S2 in trajectory order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
     const int t = blockIdx.y;
     const int tile = blockIdx.x;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
-    __shared__ SweepCtx sc;
-    __shared__ double redd[kThreads / 32][2];
+    __shared__ double redd[kThreads / 32];
     __shared__ int last;
-    if (threadIdx.x == 0) {
-        const TrajState s = v.st[t];
-        SweepCtx c;
-        c.Fa = v.frame_x[(size_t)t * (v.G + 1) + v.G] ^ s.J;
-        c.Fb = c.Fa ^ s.pend;  // final frame
-        c.Fc = 0;
-        c.pq0 = s.pq0;
-        c.pq1 = s.pq1;
-        for (int k = 0; k < 4; ++k) c.f[k] = s.f[k];
-        c.code = 0;
-        sc = c;
-    }
-    __syncthreads();
-    const SweepCtx c = sc;
+    const TrajState st = v.st[t];
+    SweepCtx c;
+    c.Fa = v.frame_x[(size_t)t * (v.G + 1) + v.G] ^ st.J;
+    c.pq0 = st.pq0;
+    c.pq1 = st.pq1;
+    for (int k = 0; k < 4; ++k) c.f[k] = st.f[k];
     const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)t << n));
-    double sn = 0.0, scut = 0.0;
+    double sn = 0.0;
 #pragma unroll
     for (int k = 0; k < kF4PerThread; ++k) {
         const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
@@ -504,103 +594,105 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v, AccumView a) 
             const float4 val = p4[f];
             const uint32_t y = (uint32_t)(2 * f);
             const float f0 = pend_factor(c, y), f1 = pend_factor(c, y | 1u);
-            const float p0 = f0 * f0 * (val.x * val.x + val.y * val.y);
-            const float p1 = f1 * f1 * (val.z * val.z + val.w * val.w);
-            const int c0 = cut_of(y ^ c.Fb, a.num_edges, a.edges);
-            const int c1 = cut_of((y | 1u) ^ c.Fb, a.num_edges, a.edges);
-            sn += (double)p0 + (double)p1;
-            scut += (double)p0 * c0 + (double)p1 * c1;
+            sn += (double)(f0 * f0 * (val.x * val.x + val.y * val.y) + f1 * f1 * (val.z * val.z + val.w * val.w));
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        sn += __shfl_xor_sync(0xffffffffu, sn, off);
-        scut += __shfl_xor_sync(0xffffffffu, scut, off);
-    }
-    if (lane == 0) {
-        redd[warp][0] = sn;
-        redd[warp][1] = scut;
-    }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        double sum = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w][threadIdx.x];
-        v.partials[((size_t)t * v.tiles + tile) * 4 + threadIdx.x] = sum;
-        __threadfence();
-    }
+    for (int off = 16; off > 0; off >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, off);
+    if (lane == 0) redd[warp] = sn;
     __syncthreads();
     if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+        v.partials[((size_t)t * v.tiles + tile) * 4] = sum;
+        __threadfence();
         const unsigned prev = atomicAdd(&v.counters[t], 1u);
         last = prev == (unsigned)(v.tiles - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double s0 = 0.0, s1 = 0.0;
-    for (int i = threadIdx.x; i < v.tiles; i += kThreads) {
-        const double *pp = v.partials + ((size_t)t * v.tiles + i) * 4;
-        s0 += __ldcg(pp);
-        s1 += __ldcg(pp + 1);
-    }
+    double s0 = 0.0;
+    for (int i = threadIdx.x; i < v.tiles; i += kThreads) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-    }
+    for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
     __syncthreads();
-    if (lane == 0) {
-        redd[warp][0] = s0;
-        redd[warp][1] = s1;
-    }
+    if (lane == 0) redd[warp] = s0;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double N = 0.0, C = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            N += redd[w][0];
-            C += redd[w][1];
-        }
+        double N = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) N += redd[w];
         if (!(N > 0.0) || !isfinite(N)) atomicOr(v.status, 2);
         v.inv_norm[t] = 1.0 / N;
-        a.c_out[t] = C / N;
         v.counters[t] = 0;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a) {
+constexpr int kAccChunk = 32;
+
+__global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, int64_t xblocks) {
     const int xb = blockIdx.x;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ float cw[kAccChunk][kThreads / 32];
     __shared__ int last;
     int64_t fp[kF4PerThread];
+    float cut[2 * kF4PerThread];
     double acc[2 * kF4PerThread];
 #pragma unroll
     for (int k = 0; k < kF4PerThread; ++k) {
         fp[k] = (int64_t)xb * kTileF4 + threadIdx.x + k * kThreads;
         acc[2 * k] = acc[2 * k + 1] = 0.0;
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t x = (uint32_t)(2 * fp[k] + e);
+            int cnt = 0;
+            for (int j = 0; j < a.num_edges; ++j) {
+                const int2 ed = a.edges[j];
+                cnt += (int)(((x >> ed.x) ^ (x >> ed.y)) & 1u);
+            }
+            cut[2 * k + e] = (float)cnt;
+        }
     }
-    for (int tt = 0; tt < v.b; ++tt) {
-        const TrajState s = v.st[tt];
-        const uint32_t Ff = v.frame_x[(size_t)tt * (v.G + 1) + v.G] ^ s.J ^ s.pend;
-        const double inv = v.inv_norm[tt];
-        const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)tt << n));
+    for (int t0c = 0; t0c < v.b; t0c += kAccChunk) {
+        const int tend = min(v.b, t0c + kAccChunk);
+        for (int tt = t0c; tt < tend; ++tt) {
+            const TrajState s = v.st[tt];
+            const uint32_t Ff = v.frame_x[(size_t)tt * (v.G + 1) + v.G] ^ s.J ^ s.pend;
+            const double inv = v.inv_norm[tt];
+            const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)tt << n));
+            float cp = 0.0f;
 #pragma unroll
-        for (int k = 0; k < kF4PerThread; ++k) {
-            if (fp[k] < nf) {
-                const int64_t f = fp[k] ^ (int64_t)(Ff >> 1);
-                float4 val = p4[f];
-                if (Ff & 1u) val = make_float4(val.z, val.w, val.x, val.y);
+            for (int k = 0; k < kF4PerThread; ++k) {
+                if (fp[k] < nf) {
+                    const int64_t f = fp[k] ^ (int64_t)(Ff >> 1);
+                    float4 val = p4[f];
+                    if (Ff & 1u) val = make_float4(val.z, val.w, val.x, val.y);
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const uint32_t x = (uint32_t)(2 * fp[k] + e);
-                    const uint32_t tb = x ^ s.pend;
-                    const uint32_t b0 = (tb >> s.pq0) & 1u, b1 = (tb >> s.pq1) & 1u;
-                    const float fac = b1 ? (b0 ? s.f[3] : s.f[2]) : (b0 ? s.f[1] : s.f[0]);
-                    const float re = e ? val.z : val.x, im = e ? val.w : val.y;
-                    acc[2 * k + e] = fma((double)(fac * fac * (re * re + im * im)), inv, acc[2 * k + e]);
+                    for (int e = 0; e < 2; ++e) {
+                        const uint32_t x = (uint32_t)(2 * fp[k] + e);
+                        const uint32_t tb = x ^ s.pend;
+                        const uint32_t b0 = (tb >> s.pq0) & 1u, b1 = (tb >> s.pq1) & 1u;
+                        const float fac = b1 ? (b0 ? s.f[3] : s.f[2]) : (b0 ? s.f[1] : s.f[0]);
+                        const float re = e ? val.z : val.x, im = e ? val.w : val.y;
+                        const float pr = fac * fac * (re * re + im * im);
+                        if (a.probs) acc[2 * k + e] = fma((double)pr, inv, acc[2 * k + e]);
+                        cp += pr * cut[2 * k + e];
+                    }
                 }
             }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
+            if (lane == 0) cw[tt - t0c][warp] = cp;
         }
+        __syncthreads();
+        if (threadIdx.x < tend - t0c) {
+            double sum = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) sum += (double)cw[threadIdx.x][w];
+            a.cpart[(size_t)(t0c + threadIdx.x) * xblocks + xb] = sum;
+        }
+        __syncthreads();
     }
     if (a.probs) {
 #pragma unroll
@@ -610,25 +702,34 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a) {
                 a.probs[2 * fp[k] + 1] += acc[2 * k + 1];
             }
     }
+    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(a.acc_counter, 1u);
-        last = prev == gridDim.x - 1;
+        last = prev == (unsigned)(xblocks - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
-    if (a.sums) {
-        double s1 = a.sums[0], s2 = a.sums[1];
-        for (int tt = 0; tt < v.b; ++tt) {
-            const double cv = __ldcg(a.c_out + tt);
-            s1 += cv;
-            s2 += cv * cv;
-        }
-        a.sums[0] = s1;
-        a.sums[1] = s2;
+    for (int tt = threadIdx.x; tt < v.b; tt += kThreads) {
+        double sum = 0.0;
+        for (int64_t i = 0; i < xblocks; ++i) sum += __ldcg(a.cpart + (size_t)tt * xblocks + i);
+        a.c_out[tt] = sum * v.inv_norm[tt];
     }
-    *a.acc_counter = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (a.sums) {
+            double s1 = a.sums[0], s2 = a.sums[1];
+            for (int tt = 0; tt < v.b; ++tt) {
+                const double cv = a.c_out[tt];
+                s1 += cv;
+                s2 += cv * cv;
+            }
+            a.sums[0] = s1;
+            a.sums[1] = s2;
+        }
+        *a.acc_counter = 0;
+    }
 }
 
 // Readout of psi_x = i^k * D * phi_{x xor F} in the true basis (debug path).
@@ -671,26 +772,34 @@ cudaError_t launch_init(const BatchView &v, cudaStream_t s) {
 
 cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const NoiseDev &nz, int damping_on,
                          cudaStream_t s) {
-    const dim3 grid((unsigned)v.tiles, (unsigned)v.b);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)v.stiles, (unsigned)v.b);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (gate.kind == kGateZZ) {
-        if (damping_on) k_sweep<kGateZZ, true><<<grid, kThreads, 0, s>>>(v, g, gate, nz.gamma);
-        else k_sweep<kGateZZ, false><<<grid, kThreads, 0, s>>>(v, g, gate, nz.gamma);
-    } else {
-        if (damping_on) k_sweep<kGateRX, true><<<grid, kThreads, 0, s>>>(v, g, gate, nz.gamma);
-        else k_sweep<kGateRX, false><<<grid, kThreads, 0, s>>>(v, g, gate, nz.gamma);
+        if (damping_on) return cudaLaunchKernelEx(&cfg, k_sweep_zz<true>, v, g, gate, nz.gamma);
+        return cudaLaunchKernelEx(&cfg, k_sweep_zz<false>, v, g, gate, nz.gamma);
     }
-    return cudaGetLastError();
+    if (damping_on) return cudaLaunchKernelEx(&cfg, k_sweep_rx<true>, v, g, gate, nz.gamma);
+    return cudaLaunchKernelEx(&cfg, k_sweep_rx<false>, v, g, gate, nz.gamma);
 }
 
 int64_t accumulate_xblocks(int n) { return tiles_for(n); }
 
-cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s) {
-    k_observe<<<dim3((unsigned)v.tiles, (unsigned)v.b), kThreads, 0, s>>>(v, a);
+cudaError_t launch_observe(const BatchView &v, const AccumView &, cudaStream_t s) {
+    k_observe<<<dim3((unsigned)v.tiles, (unsigned)v.b), kThreads, 0, s>>>(v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s) {
-    k_probs<<<(unsigned)accumulate_xblocks(v.n), kThreads, 0, s>>>(v, a);
+    const int64_t xb = accumulate_xblocks(v.n);
+    k_probs<<<(unsigned)xb, kThreads, 0, s>>>(v, a, xb);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,7 @@ size_t scratch_needed(int n, int count, int G, int E) {
     c.take<qn::TrajState>((size_t)count);
     c.take<double>((size_t)count * tiles * 4);
     c.take<double>((size_t)count);
+    c.take<double>((size_t)count * qn::accumulate_xblocks(n));
     c.take<unsigned int>((size_t)count);
     c.take<unsigned int>(1);
     c.take<int>(1);
@@ -143,6 +144,7 @@ extern "C" qn_status qn_run_qaoa_noalloc(int32_t n, const qn_graph *graph, int32
     v.t0 = first_trajectory;
     v.G = G;
     v.tiles = (int32_t)tiles_for(n);
+    v.stiles = (int32_t)sweep_tiles_for(n);
     v.branch = c.take<uint8_t>((size_t)count * G);
     v.dwords = c.take<uint32_t>((size_t)count * G * 2);
     v.frame_x = c.take<uint32_t>((size_t)count * (G + 1));
@@ -151,6 +153,7 @@ extern "C" qn_status qn_run_qaoa_noalloc(int32_t n, const qn_graph *graph, int32
     v.st = c.take<TrajState>((size_t)count);
     v.partials = c.take<double>((size_t)count * v.tiles * 4);
     v.inv_norm = c.take<double>((size_t)count);
+    double *cpart = c.take<double>((size_t)count * accumulate_xblocks(n));
     v.counters = c.take<unsigned int>((size_t)count);
     unsigned int *acc_counter = c.take<unsigned int>(1);
     v.status = c.take<int>(1);
@@ -172,6 +175,7 @@ extern "C" qn_status qn_run_qaoa_noalloc(int32_t n, const qn_graph *graph, int32
     AccumView a;
     a.num_edges = E;
     a.edges = dedges;
+    a.cpart = cpart;
     a.acc_counter = acc_counter;
     a.c_out = c_out;
     a.probs = probs_out;

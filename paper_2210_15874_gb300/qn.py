@@ -133,8 +133,9 @@ class Batch:
         """Global id of this handle's first trajectory (shards of one ensemble)."""
         check(qn_batch_set_offset(self._h, int(first_trajectory)), "qn_batch_set_offset")
 
-    def set_profiling(self, on: bool) -> None:
-        check(qn_batch_set_profiling(self._h, int(bool(on))), "qn_batch_set_profiling")
+    def set_profiling(self, period: int) -> None:
+        """Time every `period`-th sweep launch with CUDA events (0 = off)."""
+        check(qn_batch_set_profiling(self._h, int(period)), "qn_batch_set_profiling")
 
     # -- the method ---------------------------------------------------------
     def run_qaoa(self, edges, gammas, betas, *, p1=0.0, p2=0.0, damping=0.0, twoq_mode=0, param=0) -> None:
