@@ -261,7 +261,7 @@ def gpu_arm(args):
     sweep_bytes = sweeps["bytes"] / max(sweeps["launches"], 1)
     achieved = sweep_bytes / (sweep_avg_ms / 1e3) / 1e9
     traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    tr_path = os.path.join(ROOT, "profiles", "k_sweep_n20_damping_traffic.json")
     if os.path.exists(tr_path):
         try:
             tj = json.load(open(tr_path))
