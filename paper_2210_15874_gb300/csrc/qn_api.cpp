@@ -124,6 +124,9 @@ struct qn_batch {
     DevGate *dgates = nullptr;
     int2 *dedges = nullptr;
     float2 *readout = nullptr;
+    float2 *lambda = nullptr;  // adjoint vectors (qn_grad), allocated on first use
+    double *grad = nullptr;    // [K][2p] per-trajectory gradients
+    int32_t grad_cap = 0;      // 2p the grad buffer was sized for
 
     // profiling: every `prof_period`-th gate-sweep launch (and every init /
     // observable launch) is bracketed by a CUDA event pair; 0 = off
@@ -173,6 +176,9 @@ void release_all(qn_batch *h) {
     h->blocks.clear();
     h->psi = nullptr;
     h->readout = nullptr;
+    h->lambda = nullptr;
+    h->grad = nullptr;
+    h->grad_cap = 0;
     h->cap_B = 0;
     h->cap_G = -1;
     h->cap_E = -1;
@@ -631,20 +637,98 @@ qn_status qn_traj_debug(qn_batch *h, int64_t t0, int64_t count, float *amps, uin
     return ok();
 }
 
+}  // extern "C"
+
+namespace {
+
+// Parameter index of gate g (>= n): 2l for the phase gates of layer l, 2l+1 for
+// its mixer gates.
+int param_of(const qn_batch *h, int g) {
+    const int E = (int)h->edges.size() / 2;
+    const int r = g - h->n;
+    const int l = r / (E + h->n);
+    return (r % (E + h->n)) < E ? 2 * l : 2 * l + 1;
+}
+
+// Per-trajectory adjoint gradients of trajectories [t0, t0 + count) (handle-local
+// ids) into h->grad[(t0 + i) * 2p + param].
+qn_status run_grad(qn_batch *h, int64_t t0, int64_t count) {
+    if (!h->has_run) return fail(QN_ESTATE, "no completed qn_run_qaoa on this handle");
+    if (h->noise.damping > 0.0)
+        return fail(QN_EINVAL, "the adjoint gradient needs Pauli-only noise (damping = 0): damping makes "
+                               "trajectories non-unitary");
+    const int n = h->n;
+    const int G = (int)h->gates.size();
+    const int np = 2 * h->p;
+    if (np == 0) return QN_OK;
+    if (!h->lambda) QN_TRY(alloc_t(h, &h->lambda, (size_t)h->cap_B << n));
+    if (!h->grad || h->grad_cap != np) {
+        QN_TRY(alloc_t(h, &h->grad, (size_t)h->K * np));
+        h->grad_cap = np;
+    }
+    QN_CUDA(cudaMemsetAsync(h->grad + (size_t)t0 * np, 0, (size_t)count * np * sizeof(double), h->stream));
+    const int64_t saved_launches = h->launches;
+    for (int64_t c0 = 0; c0 < count; c0 += h->cap_B) {
+        const int b = (int)std::min<int64_t>(h->cap_B, count - c0);
+        QN_TRY(run_batch(h, t0 + c0, b, false));
+        BatchView v = view_for(h, h->offset + t0 + c0, b);
+        AccumView a;
+        a.num_edges = (int32_t)h->edges_host.size();
+        a.edges = h->dedges;
+        QN_CUDA(launch_adj_init(v, h->lambda, a, h->stream));
+        double *gr = h->grad + (size_t)(t0 + c0) * np;
+        for (int g = G - 1; g >= n; --g)
+            QN_CUDA(launch_adj_sweep(v, h->lambda, g, h->dgates_host[g], gr, param_of(h, g), np, h->stream));
+    }
+    h->launches = saved_launches;
+    QN_TRY(check_status(h));
+    return QN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 qn_status qn_grad(qn_batch *h, double *dgamma, double *dbeta) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
-    (void)dgamma;
-    (void)dbeta;
-    return fail(QN_EINVAL, "adjoint gradient not available in this build");
+    if (h->p > 0 && (!dgamma || !dbeta)) return fail(QN_EINVAL, "output pointer is NULL");
+    QN_TRY(run_grad(h, 0, h->K));
+    const int np = 2 * h->p;
+    if (np == 0) return ok();
+    std::vector<double> all((size_t)h->K * np);
+    QN_CUDA(cudaMemcpyAsync(all.data(), h->grad, all.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaStreamSynchronize(h->stream));
+    for (int l = 0; l < h->p; ++l) {
+        double sg = 0.0, sb = 0.0;
+        for (int64_t t = 0; t < h->K; ++t) {
+            sg += all[(size_t)t * np + 2 * l];
+            sb += all[(size_t)t * np + 2 * l + 1];
+        }
+        dgamma[l] = sg / (double)h->K;
+        dbeta[l] = sb / (double)h->K;
+    }
+    return ok();
 }
 
 qn_status qn_grad_traj(qn_batch *h, int64_t t0, int64_t count, double *dgamma, double *dbeta) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
-    (void)t0;
-    (void)count;
-    (void)dgamma;
-    (void)dbeta;
-    return fail(QN_EINVAL, "adjoint gradient not available in this build");
+    if (t0 < 0 || count < 0 || t0 + count > h->K)
+        return fail(QN_EINVAL, "trajectories [%lld, %lld) outside [0, %lld)", (long long)t0, (long long)(t0 + count),
+                    (long long)h->K);
+    if (h->p > 0 && count > 0 && (!dgamma || !dbeta)) return fail(QN_EINVAL, "output pointer is NULL");
+    QN_TRY(run_grad(h, t0, count));
+    const int np = 2 * h->p;
+    if (np == 0 || count == 0) return ok();
+    std::vector<double> all((size_t)count * np);
+    QN_CUDA(cudaMemcpyAsync(all.data(), h->grad + (size_t)t0 * np, all.size() * sizeof(double),
+                            cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaStreamSynchronize(h->stream));
+    for (int64_t i = 0; i < count; ++i)
+        for (int l = 0; l < h->p; ++l) {
+            dgamma[i * h->p + l] = all[(size_t)i * np + 2 * l];
+            dbeta[i * h->p + l] = all[(size_t)i * np + 2 * l + 1];
+        }
+    return ok();
 }
 
 qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, double *out) {

@@ -98,6 +98,11 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
 cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
+// Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n
+// adding d<C>_t / d theta_param into grad[t * nparam + param] (FP64).
+cudaError_t launch_adj_init(const BatchView &v, float2 *lam, const AccumView &a, cudaStream_t s);
+cudaError_t launch_adj_sweep(const BatchView &v, float2 *lam, int g, const DevGate &gate, double *grad, int param,
+                             int nparam, cudaStream_t s);
 int64_t accumulate_xblocks(int n);
 
 // Validated circuit and noise tables of one qn_run_qaoa call, built by the

@@ -732,6 +732,168 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint gradient (Pauli-only noise: every trajectory is a unitary circuit).
+// With U_g = P_g G_g(theta), <C>_t = <psi_T|C|psi_T> and
+//   d<C>_t/d theta = sum over gates g with parameter theta of
+//                    2 Im <lambda_g'| H_g |chi_g>,
+// where chi_g = G_g psi_{g-1} (after the gate, before its Pauli), H_g the
+// gate's generator (G = exp(-i theta H)): the differing-bit indicator for the
+// ZZ phase gate, X_q for exp(-i beta X_q), and lambda_g' = P_g^dagger U_{g+1}^dagger
+// ... U_G^dagger C psi_T.  Both vectors stay in the trajectory's X-frame (the
+// frame is a unitary shared by psi and lambda, so inner products and the
+// diagonal C are evaluated on true bits).  The reverse sweep for gate g undoes
+// the Pauli's Z part on phi and lambda, accumulates the term, then applies
+// G_g^dagger to both.  One 2048-amplitude tile per block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_adj_init(BatchView v, float2 *lam, AccumView a) {
+    const int t = blockIdx.y;
+    const int tile = blockIdx.x;
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
+    const uint32_t F = v.frame_x[(size_t)t * (v.G + 1) + v.G];
+    const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)t << n));
+    float4 *l4 = reinterpret_cast<float4 *>(lam + ((size_t)t << n));
+#pragma unroll
+    for (int k = 0; k < kF4PerThread; ++k) {
+        const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
+        if (f >= nf) continue;
+        const float4 val = p4[f];
+        float cw[2];
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t x = (uint32_t)(2 * f + e) ^ F;
+            int cnt = 0;
+            for (int j = 0; j < a.num_edges; ++j) {
+                const int2 ed = a.edges[j];
+                cnt += (int)(((x >> ed.x) ^ (x >> ed.y)) & 1u);
+            }
+            cw[e] = (float)cnt;
+        }
+        l4[f] = make_float4(cw[0] * val.x, cw[0] * val.y, cw[1] * val.z, cw[1] * val.w);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) k_adj_sweep(BatchView v, float2 *lam, int g, DevGate gt, double *grad,
+                                                         int param, int nparam) {
+    const int t = blockIdx.y;
+    const int tile = blockIdx.x;
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
+    const uint32_t Fb = v.frame_x[(size_t)t * (v.G + 1) + g];
+    const int code = v.branch[(size_t)t * v.G + g] & 15;
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
+    float4 *l4 = reinterpret_cast<float4 *>(lam + ((size_t)t << n));
+    float acc = 0.0f;
+    if (KIND == kGateZZ) {
+        const int q0 = gt.q0, q1 = gt.q1;
+        const uint32_t za = (uint32_t)(code >> 3) & 1u, zb = (uint32_t)(code >> 1) & 1u;
+#pragma unroll
+        for (int k = 0; k < kF4PerThread; ++k) {
+            const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
+            if (f >= nf) continue;
+            float4 ph = p4[f], la = l4[f];
+            float pv[4] = {ph.x, ph.y, ph.z, ph.w}, lv[4] = {la.x, la.y, la.z, la.w};
+            for (int e = 0; e < 2; ++e) {
+                const uint32_t tb = (uint32_t)(2 * f + e) ^ Fb;
+                const uint32_t b0 = (tb >> q0) & 1u, b1 = (tb >> q1) & 1u;
+                const float sgn = ((za & b0) ^ (zb & b1)) ? -1.0f : 1.0f;
+                float pr = pv[2 * e] * sgn, pi = pv[2 * e + 1] * sgn;
+                float lr = lv[2 * e] * sgn, li = lv[2 * e + 1] * sgn;
+                if (b0 ^ b1) {
+                    // H = indicator: Im(conj(l) * p)
+                    acc += lr * pi - li * pr;
+                    // undo e^{-i gamma}: multiply by e^{+i gamma} = c + i s
+                    const float npr = pr * gt.c - pi * gt.s, npi = pi * gt.c + pr * gt.s;
+                    const float nlr = lr * gt.c - li * gt.s, nli = li * gt.c + lr * gt.s;
+                    pr = npr; pi = npi; lr = nlr; li = nli;
+                }
+                pv[2 * e] = pr; pv[2 * e + 1] = pi; lv[2 * e] = lr; lv[2 * e + 1] = li;
+            }
+            p4[f] = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            l4[f] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        }
+    } else {
+        const int q = gt.q0;
+        const uint32_t z = (uint32_t)(code >> 1) & 1u;
+        const uint32_t fbq = (Fb >> q) & 1u;
+        // element with stored bit 0 has true bit fbq
+        const float s0 = (z && fbq) ? -1.0f : 1.0f, s1 = (z && !fbq) ? -1.0f : 1.0f;
+        const float cb = gt.c, sb = gt.s;
+        auto pair = [&](float &a0r, float &a0i, float &a1r, float &a1i, float &m0r, float &m0i, float &m1r,
+                        float &m1i) {
+            a0r *= s0; a0i *= s0; a1r *= s1; a1i *= s1;
+            m0r *= s0; m0i *= s0; m1r *= s1; m1i *= s1;
+            // H = X: Im(conj(l0) p1 + conj(l1) p0)
+            acc += (m0r * a1i - m0i * a1r) + (m1r * a0i - m1i * a0r);
+            // exp(-i beta X)^dagger = [[c, i s], [i s, c]]
+            float n0r = cb * a0r - sb * a1i, n0i = cb * a0i + sb * a1r;
+            float n1r = cb * a1r - sb * a0i, n1i = cb * a1i + sb * a0r;
+            a0r = n0r; a0i = n0i; a1r = n1r; a1i = n1i;
+            n0r = cb * m0r - sb * m1i; n0i = cb * m0i + sb * m1r;
+            n1r = cb * m1r - sb * m0i; n1i = cb * m1i + sb * m0r;
+            m0r = n0r; m0i = n0i; m1r = n1r; m1i = n1i;
+        };
+        if (q == 0) {
+#pragma unroll
+            for (int k = 0; k < kF4PerThread; ++k) {
+                const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
+                if (f >= nf) continue;
+                float4 ph = p4[f], la = l4[f];
+                pair(ph.x, ph.y, ph.z, ph.w, la.x, la.y, la.z, la.w);
+                p4[f] = ph;
+                l4[f] = la;
+            }
+        } else {
+            const int sh = q - 1;
+            const int64_t npairs = nf >> 1, hib = (int64_t)1 << sh;
+#pragma unroll
+            for (int k = 0; k < kF4PerThread / 2; ++k) {
+                const int64_t r = (int64_t)tile * (kTileF4 / 2) + threadIdx.x + k * kThreads;
+                if (r >= npairs) continue;
+                const int64_t fl = ((r >> sh) << (sh + 1)) | (r & (hib - 1));
+                float4 plo = p4[fl], phi = p4[fl | hib], llo = l4[fl], lhi = l4[fl | hib];
+                pair(plo.x, plo.y, phi.x, phi.y, llo.x, llo.y, lhi.x, lhi.y);
+                pair(plo.z, plo.w, phi.z, phi.w, llo.z, llo.w, lhi.z, lhi.w);
+                p4[fl] = plo; p4[fl | hib] = phi; l4[fl] = llo; l4[fl | hib] = lhi;
+            }
+        }
+    }
+    // block reduction -> per-tile partial; last block adds 2 * sum to grad[t][param]
+    __shared__ double redd[kThreads / 32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double d = (double)acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (lane == 0) redd[warp] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+        v.partials[((size_t)t * v.tiles + tile) * 4] = sum;
+        __threadfence();
+        const unsigned prev = atomicAdd(&v.counters[t], 1u);
+        last = prev == (unsigned)(v.tiles - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0;
+    for (int i = threadIdx.x; i < v.tiles; i += kThreads) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    __syncthreads();
+    if (lane == 0) redd[warp] = s0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+        grad[(size_t)t * nparam + param] += 2.0 * sum * v.inv_norm[t];
+        v.counters[t] = 0;
+    }
+}
+
 // Readout of psi_x = i^k * D * phi_{x xor F} in the true basis (debug path).
 __global__ void __launch_bounds__(kThreads) k_readout(BatchView v, float2 *out) {
     const int t = blockIdx.y;
@@ -808,6 +970,19 @@ cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s) {
     int64_t blocks = (dim + kThreads - 1) / kThreads;
     if (blocks > 4096) blocks = 4096;
     k_readout<<<dim3((unsigned)blocks, (unsigned)v.b), kThreads, 0, s>>>(v, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(const BatchView &v, float2 *lam, const AccumView &a, cudaStream_t s) {
+    k_adj_init<<<dim3((unsigned)v.tiles, (unsigned)v.b), kThreads, 0, s>>>(v, lam, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_sweep(const BatchView &v, float2 *lam, int g, const DevGate &gate, double *grad, int param,
+                             int nparam, cudaStream_t s) {
+    const dim3 grid((unsigned)v.tiles, (unsigned)v.b);
+    if (gate.kind == kGateZZ) k_adj_sweep<kGateZZ><<<grid, kThreads, 0, s>>>(v, lam, g, gate, grad, param, nparam);
+    else k_adj_sweep<kGateRX><<<grid, kThreads, 0, s>>>(v, lam, g, gate, grad, param, nparam);
     return cudaGetLastError();
 }
 
