@@ -195,7 +195,8 @@ def gpu_arm(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     stream = torch.cuda.current_stream()
-    b = qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch, stream=stream)
+    b = qn.Batch(w.n, w.trajectories, w.seed, launch_batch=0 if args.sharing else w.batch, stream=stream)
+    b.set_sharing(bool(args.sharing))
     # weak scaling: rank r evolves global trajectories [r K, (r+1) K)
     if world > 1:
         b.set_offset(rank * w.trajectories)
@@ -326,6 +327,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gq", choices=["gq", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sharing", type=int, default=1, choices=[0, 1],
+                    help="1: shared-prefix mode (trajectories share common Kraus prefixes); "
+                         "0: every trajectory evolved separately, 64 per launch")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small ensemble (n=20, p=1, 32 trajectories in one launch: 256 MiB of "
                          "statevectors) for ncu captures, then exit")

@@ -109,6 +109,18 @@ qn_status qn_batch_set_allocator(qn_batch *h, void *(*alloc)(size_t, void *),
  * 8 * 2^n * B bytes of HBM (complex64). */
 qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
 
+/* Shared-prefix mode (on = 1; default 0).  Trajectories whose Kraus strings
+ * agree so far share one statevector; when a trajectory's own Pauli or damping
+ * draw differs from the shared branch it forks into a copy.  Every trajectory
+ * sees exactly the state and the draws it would see alone, so results equal
+ * the default mode's up to FP summation order; only the work on common
+ * prefixes is done once.  A launch batch then holds up to B distinct states
+ * (default B: a quarter of the free device memory, capped by trajectories).
+ * qn_run_info's sweep_bytes returns the number of distinct final states in this
+ * mode.  qn_traj_debug and qn_grad are unaffected (they re-simulate trajectories
+ * one by one). */
+qn_status qn_batch_set_sharing(qn_batch *h, int32_t on);
+
 /* Global id of the handle's first trajectory (default 0): the handle evolves
  * trajectories first_trajectory .. first_trajectory + trajectories - 1, so
  * disjoint ranges on several handles or GPUs are shards of one ensemble whose

@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <set>
 #include <string>
 #include <utility>
@@ -124,6 +125,14 @@ struct qn_batch {
     DevGate *dgates = nullptr;
     int2 *dedges = nullptr;
     float2 *readout = nullptr;
+    // shared-prefix mode
+    int32_t sharing = 0;
+    int32_t *sh_members = nullptr, *sh_tmp = nullptr, *sh_ctr = nullptr, *sh_order = nullptr;
+    uint8_t *sh_cls = nullptr;
+    int2 *sh_range = nullptr, *sh_forks = nullptr;
+    double *sh_weights = nullptr;
+    int64_t sh_cap = 0;
+    int64_t sh_slots = 0;  // slots of the last shared-prefix run (all chunks)
     float2 *lambda = nullptr;  // adjoint vectors (qn_grad), allocated on first use
     double *grad = nullptr;    // [K][2p] per-trajectory gradients
     int32_t grad_cap = 0;      // 2p the grad buffer was sized for
@@ -178,6 +187,11 @@ void release_all(qn_batch *h) {
     h->readout = nullptr;
     h->lambda = nullptr;
     h->grad = nullptr;
+    h->sh_members = h->sh_tmp = h->sh_ctr = h->sh_order = nullptr;
+    h->sh_cls = nullptr;
+    h->sh_range = h->sh_forks = nullptr;
+    h->sh_weights = nullptr;
+    h->sh_cap = 0;
     h->grad_cap = 0;
     h->cap_B = 0;
     h->cap_G = -1;
@@ -344,6 +358,8 @@ BatchView view_for(qn_batch *h, int64_t t0, int b) {
     return v;
 }
 
+qn_status check_status(const qn_batch *h);
+
 // ---- profiling: one CUDA event pair per timed launch ----
 bool prof_sampled(qn_batch *h, int kind) {
     if (h->prof_period <= 0) return false;
@@ -415,6 +431,8 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     AccumView a;
     a.num_edges = (int32_t)h->edges_host.size();
     a.edges = h->dedges;
+    a.order = nullptr;
+    a.weights = nullptr;
     a.cpart = h->cpart;
     a.acc_counter = h->acc_counter;
     a.c_out = ensemble ? h->c_all + t0 : h->c_dbg;
@@ -427,6 +445,158 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     QN_CUDA(launch_probs(v, a, h->stream));
     QN_TRY(prof_end(h, &ep));
     h->launches += 2;
+    return QN_OK;
+}
+
+// Shared-prefix run of trajectories t0 .. t0 + kc - 1 (kc <= cap_B): one slot
+// per distinct Kraus prefix, forked on the device as branches diverge.
+qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
+    const int n = h->n;
+    const int G = (int)h->gates.size();
+    if (h->sh_cap < kc) {
+        QN_TRY(alloc_t(h, &h->sh_members, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->sh_tmp, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->sh_cls, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->sh_range, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->sh_forks, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->sh_ctr, 4));
+        QN_TRY(alloc_t(h, &h->sh_order, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->sh_weights, (size_t)kc));
+        h->sh_cap = kc;
+    }
+    BatchView v = view_for(h, h->offset + t0, kc);
+    QN_CUDA(launch_prepare(v, h->dgates, h->seed, h->nz, h->damping_on, h->stream));
+    h->launches += 1;
+    // group the trajectories by their noisy H-layer outcome (the first n branch bytes)
+    std::vector<uint8_t> hbr((size_t)kc * n);
+    std::vector<TrajState> tst((size_t)kc);
+    std::vector<uint32_t> fx((size_t)kc);
+    std::vector<float> hf((size_t)kc * n * 2);
+    QN_CUDA(cudaMemcpy2DAsync(hbr.data(), n, h->branch, G, n, kc, cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaMemcpyAsync(tst.data(), h->st, (size_t)kc * sizeof(TrajState), cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaMemcpy2DAsync(fx.data(), sizeof(uint32_t), h->frame_x + n, (size_t)(G + 1) * sizeof(uint32_t),
+                              sizeof(uint32_t), kc, cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaMemcpyAsync(hf.data(), h->hfac, hf.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaStreamSynchronize(h->stream));
+    std::map<std::string, int> key_slot;
+    std::vector<std::vector<int32_t>> groups;
+    for (int t = 0; t < kc; ++t) {
+        std::string key(reinterpret_cast<const char *>(&hbr[(size_t)t * n]), (size_t)n);
+        auto it = key_slot.find(key);
+        if (it == key_slot.end()) {
+            key_slot.emplace(key, (int)groups.size());
+            groups.push_back({t});
+        } else {
+            groups[it->second].push_back(t);
+        }
+    }
+    const int ns = (int)groups.size();
+    std::vector<int32_t> members;
+    std::vector<int2> range((size_t)ns);
+    std::vector<TrajState> sst((size_t)ns);
+    std::vector<float> shf((size_t)ns * n * 2);
+    for (int sl = 0; sl < ns; ++sl) {
+        range[sl] = make_int2((int)members.size(), (int)groups[sl].size());
+        members.insert(members.end(), groups[sl].begin(), groups[sl].end());
+        const int rep = groups[sl][0];
+        TrajState st;
+        st.J = fx[rep] ^ tst[rep].J;
+        st.pend = 0;
+        st.pq0 = st.pq1 = 0;
+        st.f[0] = st.f[1] = st.f[2] = st.f[3] = 1.0f;
+        sst[sl] = st;
+        std::copy(hf.begin() + (size_t)rep * n * 2, hf.begin() + (size_t)(rep + 1) * n * 2,
+                  shf.begin() + (size_t)sl * n * 2);
+    }
+    const int32_t ctr[4] = {ns, ns, 0, 0};  // slot_count, active, fork_count
+    QN_CUDA(cudaMemcpyAsync(h->sh_members, members.data(), members.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            h->stream));
+    QN_CUDA(cudaMemcpyAsync(h->sh_range, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                            h->stream));
+    QN_CUDA(cudaMemcpyAsync(h->st, sst.data(), sst.size() * sizeof(TrajState), cudaMemcpyHostToDevice, h->stream));
+    QN_CUDA(cudaMemcpyAsync(h->hfac, shf.data(), shf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    QN_CUDA(cudaMemcpyAsync(h->sh_ctr, ctr, sizeof ctr, cudaMemcpyHostToDevice, h->stream));
+    QN_CUDA(cudaMemsetAsync(h->frame_x, 0, (size_t)kc * (G + 1) * sizeof(uint32_t), h->stream));
+    QN_CUDA(cudaMemsetAsync(h->counters, 0, (size_t)kc * sizeof(unsigned int), h->stream));
+    QN_CUDA(cudaStreamSynchronize(h->stream));  // host vectors above go out of scope
+
+    SlotView sv;
+    sv.members = h->sh_members;
+    sv.tmp = h->sh_tmp;
+    sv.cls = h->sh_cls;
+    sv.range = h->sh_range;
+    sv.slot_count = h->sh_ctr;
+    sv.active = h->sh_ctr + 1;
+    sv.forks = h->sh_forks;
+    sv.fork_count = h->sh_ctr + 2;
+    sv.max_slots = kc;
+
+    BatchView vs = v;
+    vs.b = ns;
+    EventPair ep;
+    QN_TRY(prof_begin(h, &ep, 1, (double)ns * 8.0 * (double)((size_t)1 << n)));
+    QN_CUDA(launch_init(vs, h->stream));
+    QN_TRY(prof_end(h, &ep));
+    h->launches += 1;
+    int32_t *active_host = nullptr;
+    QN_CUDA(cudaMallocHost(&active_host, sizeof(int32_t)));
+    int active = ns;
+    for (int g = n; g < G; ++g) {
+        QN_TRY(prof_begin(h, &ep, 0, (double)active * 16.0 * (double)((size_t)1 << n)));
+        cudaError_t e = launch_slot_gate(v, sv, active, g, h->dgates_host[g], h->nz, h->damping_on, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(active_host, sv.active, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                                  h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            cudaFreeHost(active_host);
+            return fail(QN_ECUDA, "shared-prefix gate %d: %s", g, cudaGetErrorString(e));
+        }
+        QN_TRY(prof_end(h, &ep));
+        h->sweep_bytes += (double)active * 16.0 * (double)((size_t)1 << n);
+        active = *active_host;
+        h->launches += 3;
+    }
+    cudaFreeHost(active_host);
+    // deterministic accumulation order: slots by their first member
+    int32_t nslots = 0;
+    QN_CUDA(cudaMemcpyAsync(&nslots, h->sh_ctr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    QN_TRY(check_status(h));  // synchronises
+    if (nslots > kc) return fail(QN_ESTATE, "shared-prefix run created %d slots for %d trajectories", nslots, kc);
+    std::vector<int2> fr((size_t)nslots);
+    std::vector<int32_t> fm((size_t)kc);
+    QN_CUDA(cudaMemcpyAsync(fr.data(), h->sh_range, fr.size() * sizeof(int2), cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaMemcpyAsync(fm.data(), h->sh_members, fm.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    QN_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<int32_t> order((size_t)nslots);
+    std::vector<double> weights((size_t)nslots);
+    for (int sl = 0; sl < nslots; ++sl) {
+        order[sl] = sl;
+        weights[sl] = (double)fr[sl].y;
+    }
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return fm[fr[a].x] < fm[fr[b].x]; });
+    QN_CUDA(cudaMemcpyAsync(h->sh_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            h->stream));
+    QN_CUDA(cudaMemcpyAsync(h->sh_weights, weights.data(), weights.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream));
+    BatchView vo = v;
+    vo.b = nslots;
+    AccumView a;
+    a.num_edges = (int32_t)h->edges_host.size();
+    a.edges = h->dedges;
+    a.order = h->sh_order;
+    a.weights = h->sh_weights;
+    a.cpart = h->cpart;
+    a.acc_counter = h->acc_counter;
+    a.c_out = h->c_dbg;
+    a.probs = h->probs;
+    a.sums = h->sums;
+    QN_TRY(prof_begin(h, &ep, 2, (double)nslots * 8.0 * (double)((size_t)1 << n)));
+    QN_CUDA(launch_observe(vo, a, h->stream));
+    QN_CUDA(launch_probs(vo, a, h->stream));
+    QN_TRY(prof_end(h, &ep));
+    h->launches += 2;
+    h->sh_slots += nslots;
+    QN_CUDA(cudaStreamSynchronize(h->stream));  // order / weights host vectors
     return QN_OK;
 }
 
@@ -516,6 +686,14 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B) {
     return ok();
 }
 
+qn_status qn_batch_set_sharing(qn_batch *h, int32_t on) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (on != 0 && on != 1) return fail(QN_EINVAL, "sharing must be 0 or 1");
+    h->sharing = on;
+    h->has_run = false;
+    return ok();
+}
+
 qn_status qn_batch_set_offset(qn_batch *h, int64_t first_trajectory) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
     if (first_trajectory < 0) return fail(QN_EINVAL, "first trajectory id < 0");
@@ -551,7 +729,17 @@ qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const doubl
     h->damping_on = noise->damping > 0.0;
 
     int64_t B = h->B_req;
-    if (B == 0) B = std::max<int64_t>(1, (int64_t)(kDefaultBatchBytes / state_bytes(h->n)));
+    if (B == 0) {
+        // shared-prefix mode keeps one slot per distinct prefix alive: give it
+        // up to a quarter of the free memory for statevectors
+        size_t budget = kDefaultBatchBytes;
+        if (h->sharing) {
+            size_t fb = 0, tb = 0;
+            QN_CUDA(cudaMemGetInfo(&fb, &tb));
+            budget = std::max(budget, fb / 4);
+        }
+        B = std::max<int64_t>(1, (int64_t)(budget / state_bytes(h->n)));
+    }
     B = std::min<int64_t>(std::min<int64_t>(B, h->K), 65535);
     h->B = B;
     h->has_run = false;
@@ -566,9 +754,11 @@ qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const doubl
     QN_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
     h->launches = 0;
     h->sweep_bytes = 0.0;
+    h->sh_slots = 0;
     for (int64_t t0 = 0; t0 < h->K; t0 += B) {
         const int b = (int)std::min<int64_t>(B, h->K - t0);
-        QN_TRY(run_batch(h, t0, b, true));
+        if (h->sharing) QN_TRY(run_shared(h, t0, b));
+        else QN_TRY(run_batch(h, t0, b, true));
     }
     h->has_run = true;
     return ok();
@@ -672,7 +862,7 @@ qn_status run_grad(qn_batch *h, int64_t t0, int64_t count) {
         const int b = (int)std::min<int64_t>(h->cap_B, count - c0);
         QN_TRY(run_batch(h, t0 + c0, b, false));
         BatchView v = view_for(h, h->offset + t0 + c0, b);
-        AccumView a;
+        AccumView a = {};
         a.num_edges = (int32_t)h->edges_host.size();
         a.edges = h->dedges;
         QN_CUDA(launch_adj_init(v, h->lambda, a, h->stream));
@@ -745,6 +935,12 @@ qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, dou
 
 qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (h->sharing && sweep_bytes) {
+        *sweep_bytes = (double)h->sh_slots;  // shared-prefix mode: distinct final states
+        if (gates) *gates = (int64_t)h->gates.size();
+        if (launches) *launches = h->launches;
+        return ok();
+    }
     if (gates) *gates = (int64_t)h->gates.size();
     if (launches) *launches = h->launches;
     if (sweep_bytes) *sweep_bytes = h->sweep_bytes;

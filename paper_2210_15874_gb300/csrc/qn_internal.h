@@ -56,6 +56,19 @@ struct BatchView {
     int *status;            // device error word
 };
 
+// Shared-prefix mode: slots (distinct states) and their member trajectories.
+struct SlotView {
+    int32_t *members;    // [K] batch-local trajectory indices, grouped by slot
+    int32_t *tmp;        // [K] partition scratch
+    uint8_t *cls;        // [K] branch class of each member at the current gate
+    int2 *range;         // [max_slots] (offset, count) of each slot in members
+    int32_t *slot_count; // slots created so far
+    int32_t *active;     // slots swept by the current gate
+    int2 *forks;         // [max_slots] (parent, child) created at the current gate
+    int32_t *fork_count;
+    int32_t max_slots;
+};
+
 struct NoiseDev {
     double gamma;              // damping (0 = off)
     uint64_t thr1[4];          // cumulative thresholds, 1q
@@ -65,6 +78,8 @@ struct NoiseDev {
 struct AccumView {
     int32_t num_edges;
     const int2 *edges;         // device
+    const int32_t *order;      // shared-prefix mode: slot of position tt, or nullptr
+    const double *weights;     // shared-prefix mode: trajectories per slot, or nullptr
     double *cpart;             // [b][xblocks] partial sums of |psi|^2 C(x)
     unsigned int *acc_counter; // 1
     double *c_out;             // [b] per-trajectory <C>_t
@@ -98,6 +113,11 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
 cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
+// Shared-prefix mode: sweep gate g over the `active` live slots, fork the slots
+// whose members drew other branches, copy the forked states (three launches;
+// the new live-slot count is left in *sv.active).
+cudaError_t launch_slot_gate(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
+                             const NoiseDev &nz, int damping_on, cudaStream_t s);
 // Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n
 // adding d<C>_t / d theta_param into grad[t * nparam + param] (FP64).
 cudaError_t launch_adj_init(const BatchView &v, float2 *lam, const AccumView &a, cudaStream_t s);

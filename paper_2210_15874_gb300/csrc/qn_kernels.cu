@@ -201,59 +201,110 @@ __device__ __forceinline__ void add_bin(float acc[4], int idx, float p) {
     acc[3] += idx == 3 ? p : 0.0f;
 }
 
-// Damping branch of gate g from its marginal m[4] (FP64).  m[b0 | b1 << 1] is
-// the weight of true bits (b0, b1) of the gate's qubits after its Pauli (for a
-// 1q gate only m[0] and m[3]).  Draws in the order first qubit, second qubit,
-// the second conditioned on the first.  Writes the pending op for the next sweep.
+// One branch class of gate g: Pauli `code` (its X part flips frame bits, its Z
+// part signs true bits), then amplitude damping on the gate's qubits with
+// outcomes ji, jj.  m[b0 | b1 << 1] is the weight of the state after the gate
+// by true bits (b0, b1) of its qubits *before* the class's Pauli (a 1q gate uses
+// m[0], m[3]).  Fills the pending op the next sweep applies: f indexed the same
+// way (Z sign x damping Kraus factor x renormalisation), the frame flips of the
+// Pauli X part (xmask) and of the jumps (jmask).
+struct ClassOp {
+    double f[4];
+    uint32_t xmask, jmask;
+    bool bad;
+};
+
+__device__ __forceinline__ void class_marginal(const DevGate &gt, const double m[4], int code, double mc[4]) {
+    if (gt.kind == kGateZZ) {
+        const int x = (int)(xpart_1q(code >> 2) | (xpart_1q(code & 3) << 1));
+        for (int k = 0; k < 4; ++k) mc[k] = m[k ^ x];
+    } else {
+        const bool x = xpart_1q(code) != 0;
+        mc[0] = x ? m[3] : m[0];
+        mc[3] = x ? m[0] : m[3];
+        mc[1] = mc[2] = 0.0;
+    }
+}
+
+// Damping draws of one trajectory in class `code` (the second conditioned on the
+// first), from the post-Pauli marginal mc.
+__device__ __forceinline__ void damping_draws(const DevGate &gt, const double mc[4], double u0, double u1,
+                                              double gamma, bool &ji, bool &jj) {
+    const double sg = sqrt(gamma), sg1 = sqrt(1.0 - gamma);
+    if (gt.kind == kGateZZ) {
+        const double N = mc[0] + mc[1] + mc[2] + mc[3];
+        ji = u0 < gamma * (mc[1] + mc[3]) / N;
+        const double ki0 = ji ? 0.0 : 1.0, ki1 = ji ? sg : sg1;
+        const double Ni = (mc[0] + mc[2]) * ki0 * ki0 + (mc[1] + mc[3]) * ki1 * ki1;
+        jj = u1 < gamma * (mc[2] * ki0 * ki0 + mc[3] * ki1 * ki1) / Ni;
+    } else {
+        ji = u0 < gamma * mc[3] / (mc[0] + mc[3]);
+        jj = false;
+    }
+}
+
+__device__ __noinline__ ClassOp class_op(const DevGate &gt, const double m[4], int code, bool ji, bool jj, double gamma,
+                                     bool damp) {
+    ClassOp op;
+    double mc[4];
+    class_marginal(gt, m, code, mc);
+    const double sg = sqrt(gamma), sg1 = sqrt(1.0 - gamma);
+    const double ki0 = !damp ? 1.0 : (ji ? 0.0 : 1.0), ki1 = !damp ? 1.0 : (ji ? sg : sg1);
+    const double kj0 = !damp ? 1.0 : (jj ? 0.0 : 1.0), kj1 = !damp ? 1.0 : (jj ? sg : sg1);
+    if (gt.kind == kGateZZ) {
+        const int a = code >> 2, b = code & 3;
+        const uint32_t xa = xpart_1q(a), xb = xpart_1q(b), za = zpart_1q(a), zb = zpart_1q(b);
+        // norm after the ops, from post-Pauli bins
+        const double Nf = mc[0] * ki0 * ki0 * kj0 * kj0 + mc[1] * ki1 * ki1 * kj0 * kj0 +
+                          mc[2] * ki0 * ki0 * kj1 * kj1 + mc[3] * ki1 * ki1 * kj1 * kj1;
+        const double sc = damp ? 1.0 / sqrt(Nf) : 1.0;
+        for (int idx = 0; idx < 4; ++idx) {
+            const uint32_t b0 = idx & 1, b1 = (idx >> 1) & 1;
+            const double zs = ((za & b0) ^ (zb & b1)) ? -1.0 : 1.0;
+            const double k0 = (b0 ^ xa) ? ki1 : ki0, k1 = (b1 ^ xb) ? kj1 : kj0;
+            op.f[idx] = zs * k0 * k1 * sc;
+        }
+        op.xmask = (xa << gt.q0) | (xb << gt.q1);
+        op.jmask = ((uint32_t)(damp && ji) << gt.q0) | ((uint32_t)(damp && jj) << gt.q1);
+        op.bad = damp && (!(Nf > 0.0) || !isfinite(sc));
+    } else {
+        const uint32_t x = xpart_1q(code), z = zpart_1q(code);
+        const double Nf = mc[0] * ki0 * ki0 + mc[3] * ki1 * ki1;
+        const double sc = damp ? 1.0 / sqrt(Nf) : 1.0;
+        op.f[0] = (x ? ki1 : ki0) * sc;
+        op.f[3] = (z ? -1.0 : 1.0) * (x ? ki0 : ki1) * sc;
+        op.f[1] = op.f[2] = 0.0;
+        op.xmask = x << gt.q0;
+        op.jmask = (uint32_t)(damp && ji) << gt.q0;
+        op.bad = damp && (!(Nf > 0.0) || !isfinite(sc));
+    }
+    return op;
+}
+
+__device__ __forceinline__ void set_pending(TrajState &s, const DevGate &gt, const ClassOp &op) {
+    s.J ^= s.pend;
+    s.pend = op.xmask ^ op.jmask;
+    s.pq0 = gt.q0;
+    s.pq1 = gt.kind == kGateZZ ? gt.q1 : gt.q0;
+    for (int k = 0; k < 4; ++k) s.f[k] = (float)op.f[k];
+}
+
+// Damping branch of gate g for one trajectory of a launch batch.  m[4] is the
+// marginal after the gate's Pauli (already applied by the sweep: Z part on the
+// data, X part in the frame), so the branch class here is the identity Pauli.
 __device__ void decide_damping(const BatchView &v, int t, int g, const DevGate &gt, const double m[4],
                                double gamma) {
     TrajState s = v.st[t];
     const uint32_t *dw = v.dwords + ((size_t)t * v.G + g) * 2;
     const double u0 = ((double)dw[0] + 0.5) * kTwoM32;
     const double u1 = ((double)dw[1] + 0.5) * kTwoM32;
-    const double sg = sqrt(gamma), sg1 = sqrt(1.0 - gamma);
-    uint32_t newpend = 0;
-    uint8_t jb = 0;
-    double f[4];
-    bool bad = false;
-    if (gt.kind == kGateZZ) {
-        const double N = m[0] + m[1] + m[2] + m[3];
-        const bool ji = u0 < gamma * (m[1] + m[3]) / N;
-        const double ki0 = ji ? 0.0 : 1.0, ki1 = ji ? sg : sg1;
-        const double Ni = (m[0] + m[2]) * ki0 * ki0 + (m[1] + m[3]) * ki1 * ki1;
-        const bool jj = u1 < gamma * (m[2] * ki0 * ki0 + m[3] * ki1 * ki1) / Ni;
-        const double kj0 = jj ? 0.0 : 1.0, kj1 = jj ? sg : sg1;
-        const double Nf = m[0] * ki0 * ki0 * kj0 * kj0 + m[1] * ki1 * ki1 * kj0 * kj0 +
-                          m[2] * ki0 * ki0 * kj1 * kj1 + m[3] * ki1 * ki1 * kj1 * kj1;
-        const double sc = 1.0 / sqrt(Nf);
-        f[0] = ki0 * kj0 * sc;
-        f[1] = ki1 * kj0 * sc;
-        f[2] = ki0 * kj1 * sc;
-        f[3] = ki1 * kj1 * sc;
-        newpend = ((uint32_t)ji << gt.q0) | ((uint32_t)jj << gt.q1);
-        jb = (uint8_t)(((uint32_t)ji << 4) | ((uint32_t)jj << 5));
-        bad = !(N > 0.0) || !(Ni > 0.0) || !(Nf > 0.0) || !isfinite(sc);
-    } else {
-        const double N = m[0] + m[3];
-        const bool j = u0 < gamma * m[3] / N;
-        const double k0 = j ? 0.0 : 1.0, k1 = j ? sg : sg1;
-        const double Nf = m[0] * k0 * k0 + m[3] * k1 * k1;
-        const double sc = 1.0 / sqrt(Nf);
-        f[0] = k0 * sc;
-        f[3] = k1 * sc;
-        f[1] = f[2] = 0.0;
-        newpend = (uint32_t)j << gt.q0;
-        jb = (uint8_t)((uint32_t)j << 4);
-        bad = !(N > 0.0) || !(Nf > 0.0) || !isfinite(sc);
-    }
-    if (bad) atomicOr(v.status, 1);
-    s.J ^= s.pend;
-    s.pend = newpend;
-    s.pq0 = gt.q0;
-    s.pq1 = gt.kind == kGateZZ ? gt.q1 : gt.q0;
-    for (int k = 0; k < 4; ++k) s.f[k] = (float)f[k];
+    bool ji, jj;
+    damping_draws(gt, m, u0, u1, gamma, ji, jj);
+    const ClassOp op = class_op(gt, m, 0, ji, jj, gamma, true);
+    if (op.bad || !((m[0] + m[1] + m[2] + m[3]) > 0.0)) atomicOr(v.status, 1);
+    set_pending(s, gt, op);
     v.st[t] = s;
-    v.branch[(size_t)t * v.G + g] |= jb;
+    v.branch[(size_t)t * v.G + g] |= (uint8_t)(((uint32_t)ji << 4) | ((uint32_t)(jj && gt.kind == kGateZZ) << 5));
 }
 
 // Programmatic dependent launch: a sweep may be scheduled while the previous
@@ -261,10 +312,11 @@ __device__ void decide_damping(const BatchView &v, int t, int g, const DevGate &
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
 
-// Damping marginal of one block -> partials; the last block of the trajectory
-// reduces all partials of the trajectory in fixed order and draws the branch.
-__device__ __forceinline__ void sweep_epilogue(const BatchView &v, int t, int tile, int g, const DevGate &gt,
-                                               double gamma, float acc0, float acc1, float acc2, float acc3) {
+// Block reduction of the damping marginal of one unit -> partials[t][tile];
+// returns true in the last block to finish trajectory (or slot) t, with the
+// trajectory's marginal (FP64, fixed summation order) in m_out (shared).
+__device__ __forceinline__ bool reduce_marginal(const BatchView &v, int t, int tile, float acc0, float acc1, float acc2,
+                                                float acc3, double *m_out) {
     __shared__ float red[kThreads / 32][4];
     __shared__ double redd[kThreads / 32][4];
     __shared__ int last;
@@ -290,7 +342,7 @@ __device__ __forceinline__ void sweep_epilogue(const BatchView &v, int t, int ti
         last = prev == (unsigned)(v.stiles - 1);
     }
     __syncthreads();
-    if (!last) return;
+    if (!last) return false;
     __threadfence();
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (int i = threadIdx.x; i < v.stiles; i += kThreads) {
@@ -306,16 +358,14 @@ __device__ __forceinline__ void sweep_epilogue(const BatchView &v, int t, int ti
         if (lane == 0) redd[warp][k] = a;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double m[4];
-        for (int k = 0; k < 4; ++k) {
-            double a = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) a += redd[w][k];
-            m[k] = a;
-        }
-        decide_damping(v, t, g, gt, m, gamma);
-        v.counters[t] = 0;
+    if (threadIdx.x < 4) {
+        double a = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) a += redd[w][threadIdx.x];
+        m_out[threadIdx.x] = a;
     }
+    if (threadIdx.x == 0) v.counters[t] = 0;
+    __syncthreads();
+    return true;
 }
 
 // Context of trajectory t for gate g, read by every thread (uniform addresses,
@@ -342,38 +392,49 @@ __device__ __forceinline__ SweepCtx load_ctx(const BatchView &v, int t, int g, b
     return c;
 }
 
+// Context of a shared-prefix slot: its whole frame lives in J ^ pend and the
+// slot itself always takes the identity Pauli (other classes fork off).
+__device__ __forceinline__ SweepCtx load_slot_ctx(const BatchView &v, int slot) {
+    SweepCtx c;
+    const TrajState s = v.st[slot];
+    c.code = 0;
+    c.Fa = s.J;
+    c.Fb = c.Fc = s.J ^ s.pend;
+    c.pq0 = s.pq0;
+    c.pq1 = s.pq1;
+    for (int k = 0; k < 4; ++k) c.f[k] = s.f[k];
+    return c;
+}
+
 __device__ __forceinline__ void load_tile(float4 (&dst)[kF4PerThread], const float4 *p4, int64_t f0, int64_t nf) {
 #pragma unroll
     for (int k = 0; k < kF4PerThread; ++k)
         if (f0 + k * kThreads < nf) dst[k] = p4[f0 + k * kThreads];
 }
 
-// ZZ phase sweep: phi_y *= D_{g-1}(y) * (true bits of q0, q1 differ ? e^{-i gamma} : 1)
-// * (Z part of the Pauli), then bins of |phi|^2 by the true bits after the Pauli.
-// A block streams kSub tiles of one trajectory, prefetching the next tile into
-// registers while it computes the current one.
-template <bool DAMP>
-__global__ void __launch_bounds__(kThreads, 4) k_sweep_zz(BatchView v, int g, DevGate gt, double gamma) {
-    const int t = blockIdx.y;
-    const int tile = blockIdx.x;
+// ZZ phase on one unit (kSub tiles) of trajectory or slot t: phi_y *=
+// D_{g-1}(y) * (true bits of q0, q1 differ ? e^{-i gamma} : 1) * (Z part of the
+// Pauli), then bins of |phi|^2 by the true bits after the Pauli.  The next
+// tile is prefetched into registers while the current one is computed.
+template <bool DAMP, bool SLOT>
+__device__ __forceinline__ void zz_unit(const BatchView &v, int t, int tile, int g, const DevGate &gt, float &acc0,
+                                        float &acc1, float &acc2, float &acc3) {
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
     const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
-    grid_dependency_wait();
     float4 cur[kF4PerThread], nxt[kF4PerThread];
     load_tile(cur, p4, fbase, nf);
-    const SweepCtx c = load_ctx(v, t, g, DAMP);
+    const SweepCtx c = SLOT ? load_slot_ctx(v, t) : load_ctx(v, t, g, DAMP);
+    constexpr bool PEND = DAMP || SLOT;  // pending factors to apply
     const int q0 = gt.q0, q1 = gt.q1;
     const uint32_t za = (uint32_t)(c.code >> 3) & 1u, zb = (uint32_t)(c.code >> 1) & 1u;
-    // frame bits at the qubits this op reads (per thread constants)
     const uint32_t fb0 = (c.Fb >> q0) & 1u, fb1 = (c.Fb >> q1) & 1u;
     const uint32_t fc0 = (c.Fc >> q0) & 1u, fc1 = (c.Fc >> q1) & 1u;
     const uint32_t fa0 = (c.Fa >> c.pq0) & 1u, fa1 = (c.Fa >> c.pq1) & 1u;
-    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
     // bit 0 (the two halves of a float4) touches no qubit of this op: one
     // coefficient per float4
-    const bool pair_uniform = q0 != 0 && q1 != 0 && (!DAMP || (c.pq0 != 0 && c.pq1 != 0));
+    const bool pair_uniform = q0 != 0 && q1 != 0 && (!PEND || (c.pq0 != 0 && c.pq1 != 0));
 #pragma unroll
     for (int sub = 0; sub < kSub; ++sub) {
         const int64_t f0 = fbase + (int64_t)sub * kTileF4;
@@ -389,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep_zz(BatchView v, int g, De
                 const uint32_t ye = y | (uint32_t)e;
                 const uint32_t y0 = (ye >> q0) & 1u, y1 = (ye >> q1) & 1u;
                 float fa = 1.0f;
-                if (DAMP) {
+                if (PEND) {
                     const uint32_t a0 = ((ye >> c.pq0) & 1u) ^ fa0, a1 = ((ye >> c.pq1) & 1u) ^ fa1;
                     fa = a1 ? (a0 ? c.f[3] : c.f[2]) : (a0 ? c.f[1] : c.f[0]);
                 }
@@ -429,29 +490,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep_zz(BatchView v, int g, De
             for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
         }
     }
-    allow_dependent_launch();
-    if (DAMP) sweep_epilogue(v, t, tile, g, gt, gamma, acc0, acc1, acc2, acc3);
 }
 
-// exp(-i beta X) sweep on qubit q: pairs (y0, y0 | 2^q) after D_{g-1}; the Z
-// part of the Pauli negates the element whose true bit is 1; bins by the true
-// bit of q after the Pauli.  The two rows' coefficients carry those signs.
-template <bool DAMP>
-__global__ void __launch_bounds__(kThreads, 4) k_sweep_rx(BatchView v, int g, DevGate gt, double gamma) {
-    const int t = blockIdx.y;
-    const int tile = blockIdx.x;
+// exp(-i beta X) on qubit q for one unit: pairs (y0, y0 | 2^q) after D_{g-1};
+// the Z part of the Pauli negates the element whose true bit is 1; bins by the
+// true bit of q after the Pauli (acc0: true bit 0, acc3: true bit 1).
+template <bool DAMP, bool SLOT>
+__device__ __forceinline__ void rx_unit(const BatchView &v, int t, int tile, int g, const DevGate &gt, float &acc0,
+                                        float &acc3) {
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
     const int q = gt.q0;
+    constexpr bool PEND = DAMP || SLOT;
     float acc_lo = 0.0f, acc_hi = 0.0f;  // weight of rows 0 (stored bit 0) and 1
-    grid_dependency_wait();
+    uint32_t fcq = 0;
     if (q == 0) {
         const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
         float4 cur[kF4PerThread], nxt[kF4PerThread];
         load_tile(cur, p4, fbase, nf);
-        const SweepCtx c = load_ctx(v, t, g, DAMP);
+        const SweepCtx c = SLOT ? load_slot_ctx(v, t) : load_ctx(v, t, g, DAMP);
         const uint32_t fbq = c.Fb & 1u;
+        fcq = c.Fc & 1u;
         const float s0 = ((c.code >> 1) & 1) && fbq ? -1.0f : 1.0f;   // row of stored bit 0
         const float s1 = ((c.code >> 1) & 1) && !fbq ? -1.0f : 1.0f;  // row of stored bit 1
         const float c0 = gt.c * s0, sn0 = gt.s * s0, c1 = gt.c * s1, sn1 = gt.s * s1;
@@ -464,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep_rx(BatchView v, int g, De
                 const int64_t f = f0 + k * kThreads;
                 if (f >= nf) continue;
                 const uint32_t y = (uint32_t)(2 * f);
-                const float fa0 = DAMP ? pend_factor(c, y) : 1.0f, fa1 = DAMP ? pend_factor(c, y | 1u) : 1.0f;
+                const float fa0 = PEND ? pend_factor(c, y) : 1.0f, fa1 = PEND ? pend_factor(c, y | 1u) : 1.0f;
                 const float r0 = cur[k].x * fa0, i0 = cur[k].y * fa0, r1 = cur[k].z * fa1, i1 = cur[k].w * fa1;
                 cur[k].x = c0 * r0 + sn0 * i1;
                 cur[k].y = c0 * i0 - sn0 * r1;
@@ -479,87 +539,264 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep_rx(BatchView v, int g, De
                 for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
             }
         }
-        allow_dependent_launch();
-        if (DAMP) {
-            const uint32_t fcq = c.Fc & 1u;
-            sweep_epilogue(v, t, tile, g, gt, gamma, fcq ? acc_hi : acc_lo, 0.0f, 0.0f, fcq ? acc_lo : acc_hi);
-        }
-        return;
-    }
-    const int sh = q - 1;
-    const int64_t npairs = nf >> 1;
-    constexpr int kPairs = kF4PerThread / 2;
-    const int64_t rbase = (int64_t)tile * (kTileF4 / 2) * kSub + threadIdx.x;
-    const int64_t hib = (int64_t)1 << sh;
-    float4 lo[kPairs], hi[kPairs], nlo[kPairs], nhi[kPairs];
-    auto load_pairs = [&](float4 (&dl)[kPairs], float4 (&dh)[kPairs], int64_t r0) {
-#pragma unroll
-        for (int k = 0; k < kPairs; ++k) {
-            const int64_t r = r0 + k * kThreads;
-            const int64_t fl = ((r >> sh) << (sh + 1)) | (r & (hib - 1));
-            if (r < npairs) {
-                dl[k] = p4[fl];
-                dh[k] = p4[fl | hib];
-            }
-        }
-    };
-    load_pairs(lo, hi, rbase);
-    const SweepCtx c = load_ctx(v, t, g, DAMP);
-    const uint32_t fbq = (c.Fb >> q) & 1u;
-    const float s0 = ((c.code >> 1) & 1) && fbq ? -1.0f : 1.0f;
-    const float s1 = ((c.code >> 1) & 1) && !fbq ? -1.0f : 1.0f;
-    const float c0 = gt.c * s0, sn0 = gt.s * s0, c1 = gt.c * s1, sn1 = gt.s * s1;
-    const bool quad_uniform = !DAMP || (c.pq0 != 0 && c.pq0 != q && c.pq1 != 0 && c.pq1 != q);
-#pragma unroll
-    for (int sub = 0; sub < kSub; ++sub) {
-        const int64_t r0 = rbase + (int64_t)sub * (kTileF4 / 2);
-        if (sub + 1 < kSub) load_pairs(nlo, nhi, r0 + kTileF4 / 2);
-#pragma unroll
-        for (int k = 0; k < kPairs; ++k) {
-            const int64_t r = r0 + k * kThreads;
-            if (r >= npairs) continue;
-            const int64_t fl = ((r >> sh) << (sh + 1)) | (r & (hib - 1));
-            const uint32_t y0 = (uint32_t)(2 * fl);
-            const uint32_t qb = 1u << q;
-            float fl0, fl1, fh0, fh1;  // pending factors of lo.xy, lo.zw, hi.xy, hi.zw
-            if (!DAMP) {
-                fl0 = fl1 = fh0 = fh1 = 1.0f;
-            } else if (quad_uniform) {
-                fl0 = fl1 = fh0 = fh1 = pend_factor(c, y0);
-            } else {
-                fl0 = pend_factor(c, y0);
-                fl1 = pend_factor(c, y0 | 1u);
-                fh0 = pend_factor(c, y0 | qb);
-                fh1 = pend_factor(c, y0 | 1u | qb);
-            }
-            const float a0r = lo[k].x * fl0, a0i = lo[k].y * fl0, b0r = hi[k].x * fh0, b0i = hi[k].y * fh0;
-            const float a1r = lo[k].z * fl1, a1i = lo[k].w * fl1, b1r = hi[k].z * fh1, b1i = hi[k].w * fh1;
-            lo[k].x = c0 * a0r + sn0 * b0i;
-            lo[k].y = c0 * a0i - sn0 * b0r;
-            hi[k].x = c1 * b0r + sn1 * a0i;
-            hi[k].y = c1 * b0i - sn1 * a0r;
-            lo[k].z = c0 * a1r + sn0 * b1i;
-            lo[k].w = c0 * a1i - sn0 * b1r;
-            hi[k].z = c1 * b1r + sn1 * a1i;
-            hi[k].w = c1 * b1i - sn1 * a1r;
-            acc_lo += lo[k].x * lo[k].x + lo[k].y * lo[k].y + lo[k].z * lo[k].z + lo[k].w * lo[k].w;
-            acc_hi += hi[k].x * hi[k].x + hi[k].y * hi[k].y + hi[k].z * hi[k].z + hi[k].w * hi[k].w;
-            p4[fl] = lo[k];
-            p4[fl | hib] = hi[k];
-        }
-        if (sub + 1 < kSub) {
+    } else {
+        const int sh = q - 1;
+        const int64_t npairs = nf >> 1;
+        constexpr int kPairs = kF4PerThread / 2;
+        const int64_t rbase = (int64_t)tile * (kTileF4 / 2) * kSub + threadIdx.x;
+        const int64_t hib = (int64_t)1 << sh;
+        float4 lo[kPairs], hi[kPairs], nlo[kPairs], nhi[kPairs];
+        auto load_pairs = [&](float4 (&dl)[kPairs], float4 (&dh)[kPairs], int64_t r0) {
 #pragma unroll
             for (int k = 0; k < kPairs; ++k) {
-                lo[k] = nlo[k];
-                hi[k] = nhi[k];
+                const int64_t r = r0 + k * kThreads;
+                const int64_t fl = ((r >> sh) << (sh + 1)) | (r & (hib - 1));
+                if (r < npairs) {
+                    dl[k] = p4[fl];
+                    dh[k] = p4[fl | hib];
+                }
+            }
+        };
+        load_pairs(lo, hi, rbase);
+        const SweepCtx c = SLOT ? load_slot_ctx(v, t) : load_ctx(v, t, g, DAMP);
+        const uint32_t fbq = (c.Fb >> q) & 1u;
+        fcq = (c.Fc >> q) & 1u;
+        const float s0 = ((c.code >> 1) & 1) && fbq ? -1.0f : 1.0f;
+        const float s1 = ((c.code >> 1) & 1) && !fbq ? -1.0f : 1.0f;
+        const float c0 = gt.c * s0, sn0 = gt.s * s0, c1 = gt.c * s1, sn1 = gt.s * s1;
+        const bool quad_uniform = !PEND || (c.pq0 != 0 && c.pq0 != q && c.pq1 != 0 && c.pq1 != q);
+#pragma unroll
+        for (int sub = 0; sub < kSub; ++sub) {
+            const int64_t r0 = rbase + (int64_t)sub * (kTileF4 / 2);
+            if (sub + 1 < kSub) load_pairs(nlo, nhi, r0 + kTileF4 / 2);
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k) {
+                const int64_t r = r0 + k * kThreads;
+                if (r >= npairs) continue;
+                const int64_t fl = ((r >> sh) << (sh + 1)) | (r & (hib - 1));
+                const uint32_t y0 = (uint32_t)(2 * fl);
+                const uint32_t qb = 1u << q;
+                float fl0, fl1, fh0, fh1;  // pending factors of lo.xy, lo.zw, hi.xy, hi.zw
+                if (!PEND) {
+                    fl0 = fl1 = fh0 = fh1 = 1.0f;
+                } else if (quad_uniform) {
+                    fl0 = fl1 = fh0 = fh1 = pend_factor(c, y0);
+                } else {
+                    fl0 = pend_factor(c, y0);
+                    fl1 = pend_factor(c, y0 | 1u);
+                    fh0 = pend_factor(c, y0 | qb);
+                    fh1 = pend_factor(c, y0 | 1u | qb);
+                }
+                const float a0r = lo[k].x * fl0, a0i = lo[k].y * fl0, b0r = hi[k].x * fh0, b0i = hi[k].y * fh0;
+                const float a1r = lo[k].z * fl1, a1i = lo[k].w * fl1, b1r = hi[k].z * fh1, b1i = hi[k].w * fh1;
+                lo[k].x = c0 * a0r + sn0 * b0i;
+                lo[k].y = c0 * a0i - sn0 * b0r;
+                hi[k].x = c1 * b0r + sn1 * a0i;
+                hi[k].y = c1 * b0i - sn1 * a0r;
+                lo[k].z = c0 * a1r + sn0 * b1i;
+                lo[k].w = c0 * a1i - sn0 * b1r;
+                hi[k].z = c1 * b1r + sn1 * a1i;
+                hi[k].w = c1 * b1i - sn1 * a1r;
+                acc_lo += lo[k].x * lo[k].x + lo[k].y * lo[k].y + lo[k].z * lo[k].z + lo[k].w * lo[k].w;
+                acc_hi += hi[k].x * hi[k].x + hi[k].y * hi[k].y + hi[k].z * hi[k].z + hi[k].w * hi[k].w;
+                p4[fl] = lo[k];
+                p4[fl | hib] = hi[k];
+            }
+            if (sub + 1 < kSub) {
+#pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    lo[k] = nlo[k];
+                    hi[k] = nhi[k];
+                }
             }
         }
     }
+    acc0 = fcq ? acc_hi : acc_lo;
+    acc3 = fcq ? acc_lo : acc_hi;
+}
+
+// Gate sweeps of a launch batch: grid (sweep tiles, trajectories).
+template <bool DAMP>
+__global__ void __launch_bounds__(kThreads, 4) k_sweep_zz(BatchView v, int g, DevGate gt, double gamma) {
+    grid_dependency_wait();
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    zz_unit<DAMP, false>(v, blockIdx.y, blockIdx.x, g, gt, a0, a1, a2, a3);
     allow_dependent_launch();
     if (DAMP) {
-        const uint32_t fcq = (c.Fc >> q) & 1u;
-        sweep_epilogue(v, t, tile, g, gt, gamma, fcq ? acc_hi : acc_lo, 0.0f, 0.0f, fcq ? acc_lo : acc_hi);
+        __shared__ double m[4];
+        if (reduce_marginal(v, blockIdx.y, blockIdx.x, a0, a1, a2, a3, m) && threadIdx.x == 0)
+            decide_damping(v, blockIdx.y, g, gt, m, gamma);
     }
+}
+
+template <bool DAMP>
+__global__ void __launch_bounds__(kThreads, 4) k_sweep_rx(BatchView v, int g, DevGate gt, double gamma) {
+    grid_dependency_wait();
+    float a0 = 0.0f, a3 = 0.0f;
+    rx_unit<DAMP, false>(v, blockIdx.y, blockIdx.x, g, gt, a0, a3);
+    allow_dependent_launch();
+    if (DAMP) {
+        __shared__ double m[4];
+        if (reduce_marginal(v, blockIdx.y, blockIdx.x, a0, 0.0f, 0.0f, a3, m) && threadIdx.x == 0)
+            decide_damping(v, blockIdx.y, g, gt, m, gamma);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-prefix mode.  Trajectories whose Kraus strings agree so far share one
+// statevector ("slot").  A slot always takes the identity Pauli and, with
+// damping, the no-jump branch; after every gate the last block of each slot
+// draws, for every member trajectory, its own Pauli (from the member's Philox
+// word) and damping outcomes (from the slot's marginal, permuted by that
+// Pauli's X part), groups the members by outcome, keeps the identity / no-jump
+// group and forks every other group into a new slot that copies the state and
+// carries its class's Z sign, damping factors and renormalisation as the
+// pending op.  Every trajectory therefore sees exactly the state and branch
+// draws it would see alone; only the work on common prefixes is shared.
+// ---------------------------------------------------------------------------
+__device__ __noinline__ void decide_slot(const BatchView &v, const SlotView &sv, int s, int g, const DevGate &gt,
+                            const double *m_sh, double gamma, bool damp) {
+    __shared__ int ccount[64], cstart[64], order[64];
+    __shared__ int norder, child_base, run;
+    __shared__ int wcnt[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int2 rg = sv.range[s];
+    const int off = rg.x, cnt = rg.y;
+    if (threadIdx.x < 64) ccount[threadIdx.x] = 0;
+    __syncthreads();
+    double m[4];
+    for (int k = 0; k < 4; ++k) m[k] = damp ? m_sh[k] : 0.0;
+    for (int i = threadIdx.x; i < cnt; i += kThreads) {
+        const int t = sv.members[off + i];
+        const int code = v.branch[(size_t)t * v.G + g] & 15;
+        int cls = code;
+        if (damp) {
+            const uint32_t *dw = v.dwords + ((size_t)t * v.G + g) * 2;
+            double mc[4];
+            class_marginal(gt, m, code, mc);
+            bool ji, jj;
+            damping_draws(gt, mc, ((double)dw[0] + 0.5) * kTwoM32, ((double)dw[1] + 0.5) * kTwoM32, gamma, ji, jj);
+            cls |= ((int)ji << 4) | ((int)jj << 5);
+            v.branch[(size_t)t * v.G + g] = (uint8_t)cls;
+        }
+        sv.cls[off + i] = (uint8_t)cls;
+        atomicAdd(&ccount[cls], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int first = ccount[0] > 0 ? 0 : -1;
+        for (int c = 1; c < 64 && first < 0; ++c)
+            if (ccount[c] > 0) first = c;
+        int no = 0;
+        order[no++] = first;
+        for (int c = 0; c < 64; ++c)
+            if (c != first && ccount[c] > 0) order[no++] = c;
+        int pos = 0;
+        for (int k = 0; k < no; ++k) {
+            cstart[order[k]] = pos;
+            pos += ccount[order[k]];
+        }
+        norder = no;
+        child_base = no > 1 ? atomicAdd(sv.slot_count, no - 1) : 0;
+    }
+    __syncthreads();
+    const int no = norder;
+    if (no > 1) {
+        // stable partition of the members by class, into tmp[off ..]
+        for (int k = 0; k < no; ++k) {
+            const int c = order[k];
+            if (threadIdx.x == 0) run = 0;
+            __syncthreads();
+            for (int i0 = 0; i0 < cnt; i0 += kThreads) {
+                const int i = i0 + threadIdx.x;
+                const bool flag = i < cnt && sv.cls[off + i] == c;
+                const unsigned bal = __ballot_sync(0xffffffffu, flag);
+                if (lane == 0) wcnt[warp] = __popc(bal);
+                __syncthreads();
+                int before = run;
+                for (int w = 0; w < warp; ++w) before += wcnt[w];
+                if (flag) sv.tmp[off + cstart[c] + before + __popc(bal & ((1u << lane) - 1u))] = sv.members[off + i];
+                __syncthreads();
+                if (threadIdx.x == 0)
+                    for (int w = 0; w < kThreads / 32; ++w) run += wcnt[w];
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < cnt; i += kThreads) sv.members[off + i] = sv.tmp[off + i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const TrajState parent = v.st[s];
+        for (int k = 0; k < no; ++k) {
+            const int c = order[k];
+            const ClassOp op = class_op(gt, m, c & 15, (c >> 4) & 1, (c >> 5) & 1, gamma, damp);
+            if (op.bad) atomicOr(v.status, 1);
+            TrajState ns = parent;
+            set_pending(ns, gt, op);
+            const int2 r = make_int2(off + cstart[c], ccount[c]);
+            if (k == 0) {
+                v.st[s] = ns;
+                sv.range[s] = r;
+            } else {
+                const int child = child_base + k - 1;
+                if (child >= sv.max_slots) {
+                    atomicOr(v.status, 4);
+                    continue;
+                }
+                v.st[child] = ns;
+                sv.range[child] = r;
+                const int f = atomicAdd(sv.fork_count, 1);
+                sv.forks[f] = make_int2(s, child);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Slot sweeps: grid (sweep tiles, slots alive before this gate), one unit per
+// block, the same body as the batch sweeps.
+template <bool DAMP, int KIND>
+__global__ void __launch_bounds__(kThreads, 4) k_slot_sweep(BatchView v, SlotView sv, int g, DevGate gt,
+                                                            double gamma) {
+    grid_dependency_wait();
+    const int slot = blockIdx.y, tile = blockIdx.x;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    if (KIND == kGateZZ) zz_unit<DAMP, true>(v, slot, tile, g, gt, a0, a1, a2, a3);
+    else rx_unit<DAMP, true>(v, slot, tile, g, gt, a0, a3);
+    allow_dependent_launch();
+    __shared__ double m[4];
+    if (reduce_marginal(v, slot, tile, a0, a1, a2, a3, m)) decide_slot(v, sv, slot, g, gt, m, gamma, DAMP);
+}
+
+// Copy the parent's statevector into every slot forked at this gate.
+__global__ void __launch_bounds__(kThreads) k_fork_copy(BatchView v, SlotView sv) {
+    grid_dependency_wait();
+    const int nforks = *sv.fork_count;
+    const int64_t nf = (int64_t)1 << (v.n - 1 > 0 ? v.n - 1 : 0);
+    const int64_t chunks = (nf + kTileF4 - 1) / kTileF4;
+    const int64_t units = (int64_t)nforks * chunks;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+        const int2 fk = sv.forks[u / chunks];
+        const int64_t f0 = (u % chunks) * kTileF4 + threadIdx.x;
+        const float4 *src = reinterpret_cast<const float4 *>(v.psi + ((size_t)fk.x << v.n));
+        float4 *dst = reinterpret_cast<float4 *>(v.psi + ((size_t)fk.y << v.n));
+        float4 tmp[kF4PerThread];
+#pragma unroll
+        for (int k = 0; k < kF4PerThread; ++k)
+            if (f0 + k * kThreads < nf) tmp[k] = src[f0 + k * kThreads];
+#pragma unroll
+        for (int k = 0; k < kF4PerThread; ++k)
+            if (f0 + k * kThreads < nf) dst[f0 + k * kThreads] = tmp[k];
+    }
+    allow_dependent_launch();
+}
+
+// After the copies: the new slots join the next sweep.
+__global__ void k_fork_finish(SlotView sv) {
+    grid_dependency_wait();
+    const int sc = *sv.slot_count;
+    *sv.active = sc < sv.max_slots ? sc : sv.max_slots;
+    *sv.fork_count = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -572,6 +809,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep_rx(BatchView v, int g, De
 // order, and sum_x |psi_t,x|^2 C(x) is reduced per (t, block); its last block
 // forms <C>_t and adds S1, S2 in trajectory order.
 // ---------------------------------------------------------------------------
+// |fac * a|^2 with fixed rounding (no contraction), so that the norm pass and
+// the probability pass see bit-identical FP32 values and sum(sigma) = 1 to FP64
+// rounding.
+__device__ __forceinline__ float prob_of(float fac, float re, float im) {
+    return __fmul_rn(__fmul_rn(fac, fac), __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im)));
+}
+
 __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
     const int t = blockIdx.y;
     const int tile = blockIdx.x;
@@ -594,7 +838,8 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
             const float4 val = p4[f];
             const uint32_t y = (uint32_t)(2 * f);
             const float f0 = pend_factor(c, y), f1 = pend_factor(c, y | 1u);
-            sn += (double)(f0 * f0 * (val.x * val.x + val.y * val.y) + f1 * f1 * (val.z * val.z + val.w * val.w));
+            sn += (double)prob_of(f0, val.x, val.y);
+            sn += (double)prob_of(f1, val.z, val.w);
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -658,10 +903,11 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
     for (int t0c = 0; t0c < v.b; t0c += kAccChunk) {
         const int tend = min(v.b, t0c + kAccChunk);
         for (int tt = t0c; tt < tend; ++tt) {
-            const TrajState s = v.st[tt];
-            const uint32_t Ff = v.frame_x[(size_t)tt * (v.G + 1) + v.G] ^ s.J ^ s.pend;
-            const double inv = v.inv_norm[tt];
-            const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)tt << n));
+            const int sl = a.order ? a.order[tt] : tt;
+            const TrajState s = v.st[sl];
+            const uint32_t Ff = v.frame_x[(size_t)sl * (v.G + 1) + v.G] ^ s.J ^ s.pend;
+            const double inv = v.inv_norm[sl] * (a.weights ? a.weights[sl] : 1.0);
+            const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)sl << n));
             float cp = 0.0f;
 #pragma unroll
             for (int k = 0; k < kF4PerThread; ++k) {
@@ -676,7 +922,7 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
                         const uint32_t b0 = (tb >> s.pq0) & 1u, b1 = (tb >> s.pq1) & 1u;
                         const float fac = b1 ? (b0 ? s.f[3] : s.f[2]) : (b0 ? s.f[1] : s.f[0]);
                         const float re = e ? val.z : val.x, im = e ? val.w : val.y;
-                        const float pr = fac * fac * (re * re + im * im);
+                        const float pr = prob_of(fac, re, im);
                         if (a.probs) acc[2 * k + e] = fma((double)pr, inv, acc[2 * k + e]);
                         cp += pr * cut[2 * k + e];
                     }
@@ -714,7 +960,7 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
     for (int tt = threadIdx.x; tt < v.b; tt += kThreads) {
         double sum = 0.0;
         for (int64_t i = 0; i < xblocks; ++i) sum += __ldcg(a.cpart + (size_t)tt * xblocks + i);
-        a.c_out[tt] = sum * v.inv_norm[tt];
+        a.c_out[tt] = sum * v.inv_norm[a.order ? a.order[tt] : tt];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -722,8 +968,9 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
             double s1 = a.sums[0], s2 = a.sums[1];
             for (int tt = 0; tt < v.b; ++tt) {
                 const double cv = a.c_out[tt];
-                s1 += cv;
-                s2 += cv * cv;
+                const double w = a.weights ? a.weights[a.order ? a.order[tt] : tt] : 1.0;
+                s1 += w * cv;
+                s2 += w * cv * cv;
             }
             a.sums[0] = s1;
             a.sums[1] = s2;
@@ -953,6 +1200,50 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
 }
 
 int64_t accumulate_xblocks(int n) { return tiles_for(n); }
+
+static int persistent_blocks() {
+    static int blocks = 0;
+    if (!blocks) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_slot_sweep<true, kGateZZ>, kThreads, 0);
+        blocks = (sms > 0 ? sms : 152) * (per > 0 ? per : 4);
+    }
+    return blocks;
+}
+
+template <typename K, typename... Args>
+static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+cudaError_t launch_slot_gate(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
+                             const NoiseDev &nz, int damping_on, cudaStream_t s) {
+    const int blocks = persistent_blocks();
+    const dim3 grid((unsigned)v.stiles, (unsigned)active), block(kThreads);
+    cudaError_t e;
+    if (gate.kind == kGateZZ)
+        e = damping_on ? launch_pdl(k_slot_sweep<true, kGateZZ>, grid, block, s, v, sv, g, gate, nz.gamma)
+                       : launch_pdl(k_slot_sweep<false, kGateZZ>, grid, block, s, v, sv, g, gate, nz.gamma);
+    else
+        e = damping_on ? launch_pdl(k_slot_sweep<true, kGateRX>, grid, block, s, v, sv, g, gate, nz.gamma)
+                       : launch_pdl(k_slot_sweep<false, kGateRX>, grid, block, s, v, sv, g, gate, nz.gamma);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_fork_copy, dim3(blocks), block, s, v, sv);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
+}
 
 cudaError_t launch_observe(const BatchView &v, const AccumView &, cudaStream_t s) {
     k_observe<<<dim3((unsigned)v.tiles, (unsigned)v.b), kThreads, 0, s>>>(v);

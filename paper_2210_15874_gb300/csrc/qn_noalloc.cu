@@ -175,6 +175,8 @@ extern "C" qn_status qn_run_qaoa_noalloc(int32_t n, const qn_graph *graph, int32
     AccumView a;
     a.num_edges = E;
     a.edges = dedges;
+    a.order = nullptr;
+    a.weights = nullptr;
     a.cpart = cpart;
     a.acc_counter = acc_counter;
     a.c_out = c_out;

@@ -45,6 +45,7 @@ _SIGS = {
     "qn_batch_set_allocator": (c_i32, [c_vp, ALLOC_FN, FREE_FN, c_vp]),
     "qn_batch_set_launch_batch": (c_i32, [c_vp, c_i64]),
     "qn_batch_set_offset": (c_i32, [c_vp, c_i64]),
+    "qn_batch_set_sharing": (c_i32, [c_vp, c_i32]),
     "qn_run_qaoa": (c_i32, [c_vp, P(qn_graph), c_i32, P(c_dbl), P(c_dbl), P(qn_noise)]),
     "qn_expectation": (c_i32, [c_vp, P(c_dbl), P(c_dbl)]),
     "qn_probs": (c_i32, [c_vp, P(c_dbl), c_i64]),
@@ -128,6 +129,10 @@ class Batch:
         a, f = ALLOC_FN(_alloc), FREE_FN(_free)
         self._keep += [a, f]
         check(qn_batch_set_allocator(self._h, a, f, None), "qn_batch_set_allocator")
+
+    def set_sharing(self, on: bool) -> None:
+        """Shared-prefix mode: trajectories share their common Kraus prefix."""
+        check(qn_batch_set_sharing(self._h, int(bool(on))), "qn_batch_set_sharing")
 
     def set_offset(self, first_trajectory: int) -> None:
         """Global id of this handle's first trajectory (shards of one ensemble)."""

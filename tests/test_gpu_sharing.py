@@ -1,0 +1,103 @@
+"""Shared-prefix mode (qn_batch_set_sharing): trajectories share the state of
+their common Kraus prefix and fork when their own draws diverge.
+
+Exactness checks: the number of distinct states equals the number of distinct
+full Kraus strings among the trajectories (from the one-by-one re-simulation),
+and the ensemble results equal the default mode's up to FP summation order and
+the oracle's within the FP32 bound."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_15874_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def qn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_15874_gb300 import build
+    build.build()
+    from paper_2210_15874_gb300 import qn as mod
+    return mod
+
+
+def run(qn, w, sharing, launch_batch=0):
+    with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=launch_batch) as b:
+        b.set_sharing(sharing)
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        mean, se = b.expectation()
+        probs = b.probs()
+        info = b.run_info()
+        br = b.traj_debug(0, w.trajectories, amps=False, c=False)["branches"] if sharing else None
+    return mean, se, probs, info, br
+
+
+CASES = {
+    "n8_pauli": dict(n=8, p=1, index=0, trajectories=1024, p1=1e-3, p2=1e-2, damping=0.0),
+    "n12_damping": dict(n=12, p=2, index=31, trajectories=300, p1=5e-3, p2=2e-2, damping=0.02),
+    "n14_damping_multitile": dict(n=14, p=2, index=32, trajectories=96, p1=1e-2, p2=3e-2, damping=0.05),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_sharing_equals_default_mode_and_oracle(qn, case):
+    kw = dict(CASES[case])
+    n, p, idx, K = kw.pop("n"), kw.pop("p"), kw.pop("index"), kw.pop("trajectories")
+    w = W.qaoa_workload(case, n, p, index=idx, trajectories=K, batch=K, **kw)
+    m1, s1, p1, _, _ = run(qn, w, False)
+    m2, s2, p2, info, br = run(qn, w, True)
+    distinct = len({bytes(r) for r in br})
+    assert info["sweep_bytes"] == distinct  # one shared state per distinct Kraus string
+    if case != "n14_damping_multitile":  # heavy noise: every string differs there
+        assert distinct < K
+    assert abs(m1 - m2) < 1e-9 and abs(s1 - s2) < 1e-9
+    assert abs(p1.sum() - 1) < 1e-12 and abs(p2.sum() - 1) < 1e-12
+    np.testing.assert_allclose(p2, p1, rtol=1e-12, atol=0)
+    assert abs(oracle.error(p2, p1)) < 1e-12
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    ref = oracle.traj_run(w.n, w.edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, 0, K,
+                          want_amps=False, want_branches=False)
+    assert abs(m2 - ref["s1"] / K) < 8 * U32 * G * len(w.edges)
+    assert oracle.error(p2, ref["probs_sum"] / K) < 1e-9
+
+
+def test_sharing_in_chunks_and_with_offset(qn):
+    """K larger than the launch batch: chunks of 37 trajectories form their own
+    prefix trees; a nonzero global offset selects other Philox streams."""
+    w = W.qaoa_workload("chunks", 10, 2, index=33, trajectories=100, batch=37, p1=5e-3, p2=2e-2, damping=0.03)
+    res = []
+    for sharing in (False, True):
+        with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=37) as b:
+            b.set_sharing(sharing)
+            b.set_offset(1000)
+            b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+            res.append((b.expectation(), b.probs()))
+    (ma, _), pa = res[0]
+    (mb, _), pb = res[1]
+    assert abs(ma - mb) < 1e-9
+    np.testing.assert_allclose(pa, pb, atol=1e-12)
+
+
+def test_sharing_full_size_damping_n20(qn):
+    """The 20-qubit p=3 damping workload (K=4096) in shared-prefix mode against
+    the default mode."""
+    w = W.damping_n20()
+    with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        m1, s1 = b.expectation()
+        p1 = b.probs()
+    with qn.Batch(w.n, w.trajectories, w.seed) as b:
+        b.set_sharing(True)
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        m2, s2 = b.expectation()
+        p2 = b.probs()
+        slots = b.run_info()["sweep_bytes"]
+    assert slots < w.trajectories
+    assert abs(m1 - m2) < 1e-8 and abs(s1 - s2) < 1e-8
+    np.testing.assert_allclose(p2, p1, rtol=1e-12, atol=0)
