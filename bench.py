@@ -6,11 +6,13 @@ Workload (one "step"): the 20-qubit p=3 QAOA MaxCut circuit on a seeded
 Philox Kraus sampling, every gate sweep with its damping draw, and the ensemble
 accumulation of <C> and sigma_approx.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gq|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gq|reference] [--sharing 0|1]
 
 Prints one JSON line (rank 0).  `value` is trajectories/s timed with CUDA events
 on the library's stream (inputs -- graph, angles, noise -- resident; every step
-regenerates all trajectories on the device).  `e2e` times the same call through
+regenerates all trajectories on the device).  The default mode shares the state
+of common Kraus prefixes between trajectories (exact); the same line reports
+the one-statevector-per-trajectory mode under `per_trajectory_mode`.  `e2e` times the same call through
 the C ABI from host buffers to the host-side <C> and sigma_approx.
 `--impl reference` times the FP64 CPU oracle on a bounded sample instead.
 """
@@ -171,6 +173,73 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def measure(qn, w, args, sharing, stream, rank, world, local, pg, with_e2e):
+    """Time `args.steps` whole-ensemble steps (after `args.warmup`) in one mode."""
+    import torch
+
+    b = qn.Batch(w.n, w.trajectories, w.seed, launch_batch=0 if sharing else w.batch, stream=stream)
+    b.set_sharing(sharing)
+    # weak scaling: rank r evolves global trajectories [r K, (r+1) K)
+    if world > 1:
+        b.set_offset(rank * w.trajectories)
+    kw = w.noise_kwargs()
+
+    def step():
+        b.run_qaoa(w.edges, w.gammas, w.betas, **kw)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    mean, se = b.expectation()
+    b.set_profiling(PROFILE_PERIOD)
+    for k in range(3):
+        b.profile_read(k)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches, sweep_bytes, states = 0, 0.0, 0
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            info = b.run_info()
+            launches += info["launches"]
+            sweep_bytes += info["sweep_bytes"]
+            states += info["states"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    res = dict(ms=ms, value=w.trajectories * args.steps * world / (ms / 1e3), mean=mean, se=se,
+               launches=launches, sweep_bytes_per_step=sweep_bytes / args.steps, states_per_step=states / args.steps,
+               sweeps=b.profile_read(0), inits=b.profile_read(1), accs=b.profile_read(2), clocks=clocks.summary())
+    b.set_profiling(0)
+    if with_e2e:
+        # end to end through the C ABI from host buffers: run + <C> + sigma to host
+        e2e_steps = max(1, min(args.steps, 3))
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(e2e_steps):
+            b.run_qaoa(w.edges, w.gammas, w.betas, **kw)
+            b.expectation()
+            b.probs()
+        el = time.perf_counter() - t
+        if pg:
+            tt = torch.tensor([el], device="cuda")
+            pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+            el = float(tt.item())
+        res["e2e_value"] = w.trajectories * e2e_steps * world / el
+    b.close()
+    return res
+
+
 def gpu_arm(args):
     import torch
 
@@ -193,114 +262,77 @@ def gpu_arm(args):
         peaks = json.load(open(pk_path))
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-
     stream = torch.cuda.current_stream()
-    b = qn.Batch(w.n, w.trajectories, w.seed, launch_batch=0 if args.sharing else w.batch, stream=stream)
-    b.set_sharing(bool(args.sharing))
-    # weak scaling: rank r evolves global trajectories [r K, (r+1) K)
-    if world > 1:
-        b.set_offset(rank * w.trajectories)
-    kw = w.noise_kwargs()
 
-    def step():
-        b.run_qaoa(w.edges, w.gammas, w.betas, **kw)
+    sharing = bool(args.sharing)
+    main = measure(qn, w, args, sharing, stream, rank, world, local, pg, with_e2e=True)
+    other = None
+    if sharing and not args.single_mode:
+        other = measure(qn, w, args, False, stream, rank, world, local, pg, with_e2e=False)
 
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-    mean, se = b.expectation()
-
-    b.set_profiling(PROFILE_PERIOD)
-    for k in range(3):
-        b.profile_read(k)
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = 0
-    with ClockSampler(local) as clocks:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-            launches += b.run_info()["launches"]
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-        pg.barrier()
-    sweeps = b.profile_read(0)
-    inits = b.profile_read(1)
-    accs = b.profile_read(2)
-    b.set_profiling(0)
-    total_traj = w.trajectories * args.steps * world
-    value = total_traj / (ms / 1e3)
-
-    # end to end through the C ABI from host buffers: run + <C> + sigma to host
-    e2e_steps = max(1, min(args.steps, 3))
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(e2e_steps):
-        b.run_qaoa(w.edges, w.gammas, w.betas, **kw)
-        m_, s_ = b.expectation()
-        pr = b.probs()
-    el = time.perf_counter() - t
-    if pg:
-        tt = torch.tensor([el], device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        el = float(tt.item())
-    e2e_value = w.trajectories * e2e_steps * world / el
-    G = w.gate_count
+    G, n, K = w.gate_count, w.n, w.trajectories
     h2d = int(len(w.edges) * 8 + 2 * w.p * 8 + 40 + G * 20)
-    d2h = int((1 << w.n) * 8 + 16 + 4)
+    d2h = int((1 << n) * 8 + 16 + 4)
+    if sharing:
+        # grouping of the noisy H layer into the first slots, per-gate live-slot
+        # counts, and the slot order for the final accumulation
+        d2h += K * (n + 32 + 4 + 8 * n) + 4 * (G - n) + 4 + K * 12
+        h2d += K * (4 + 8 + 32 + 8 * n + 12) + 16
 
-    sweep_avg_ms = sweeps["ms"] / max(sweeps["launches"], 1)
-    sweep_bytes = sweeps["bytes"] / max(sweeps["launches"], 1)
-    achieved = sweep_bytes / (sweep_avg_ms / 1e3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "k_sweep_n20_damping_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            tj = json.load(open(tr_path))
-            if tj.get("kernel_source_hash") == kernel_hash():
-                traffic = tj.get("traffic_bytes_per_launch_full_size")
-        except (ValueError, OSError):
-            traffic = None
+    def roof(res, kernel):
+        sw = res["sweeps"]
+        avg_ms = sw["ms"] / max(sw["launches"], 1)
+        achieved = (sw["bytes"] / max(sw["launches"], 1)) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
+        traffic = None
+        tr_path = os.path.join(ROOT, "profiles", "k_sweep_n20_damping_traffic.json")
+        if os.path.exists(tr_path):
+            try:
+                tj = json.load(open(tr_path))
+                if tj.get("kernel_source_hash") == kernel_hash() and tj.get("kernel") == kernel:
+                    traffic = tj.get("traffic_bytes_per_launch_full_size")
+            except (ValueError, OSError):
+                traffic = None
+        return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "launches_timed": sw["launches"], "avg_launch_ms": avg_ms,
+                "share_of_step": sw["ms"] * PROFILE_PERIOD / res["ms"] if res["ms"] > 0 else None}
 
     if rank == 0:
+        kname = "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
+            "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)"
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_of(w, {"parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU"}),
-            "amp_updates_per_s": value * G * (1 << w.n),
-            "c_mean": mean, "c_stderr": se,
-            "roofline": {"kernel": "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)", "bound": "hbm",
-                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": traffic,
-                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
-                         else "fallback 6800 GB/s",
-                         "launches_timed": sweeps["launches"], "avg_launch_ms": sweep_avg_ms,
-                         "share_of_step": sweeps["ms"] * PROFILE_PERIOD / ms if ms > 0 else None},
-            "kernels": {"k_sweep_zz+k_sweep_rx (sampled 1/%d)" % PROFILE_PERIOD: sweeps, "k_init": inits,
-                        "k_observe+k_probs": accs},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clocks.summary(),
+            "config": config_of(w, {
+                "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
+                "mode": "shared-prefix: one statevector per distinct Kraus prefix, all 4096 trajectories in one "
+                        "prefix tree" if sharing else "one statevector per trajectory, 64 per launch"}),
+            "amp_updates_per_s": main["value"] * G * (1 << n),
+            "distinct_states_per_step": main["states_per_step"],
+            "sweep_bytes_per_step": main["sweep_bytes_per_step"],
+            "c_mean": main["mean"], "c_stderr": main["se"],
+            "roofline": roof(main, kname),
+            "kernels": {"gate sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["sweeps"], "k_init": main["inits"],
+                        "k_observe+k_probs": main["accs"]},
+            "e2e": {"value": main["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": main["launches"],
+            "clocks": main["clocks"],
         }
+        if other is not None:
+            line["per_trajectory_mode"] = {
+                "value": other["value"], "unit": UNIT, "ms_per_step": other["ms"] / args.steps,
+                "c_mean": other["mean"], "gpu_launches": other["launches"], "clocks": other["clocks"],
+                "roofline": roof(other, "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
-    b.close()
     if pg:
         pg.destroy_process_group()
 
 
-def profile_case():
+def profile_case(sharing=False):
     """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state)."""
     from paper_2210_15874_gb300 import build
     build.build()
@@ -308,6 +340,7 @@ def profile_case():
 
     w = W.qaoa_workload("ncu_n20_p1_damp", 20, 1, index=1, trajectories=32, batch=32, damping=5e-3)
     with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+        b.set_sharing(sharing)
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
         print(json.dumps({"case": w.name, "c": b.expectation()}))
 
@@ -330,12 +363,14 @@ def main():
     ap.add_argument("--sharing", type=int, default=1, choices=[0, 1],
                     help="1: shared-prefix mode (trajectories share common Kraus prefixes); "
                          "0: every trajectory evolved separately, 64 per launch")
+    ap.add_argument("--single-mode", action="store_true",
+                    help="time only the selected mode (skip the per-trajectory comparison run)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small ensemble (n=20, p=1, 32 trajectories in one launch: 256 MiB of "
                          "statevectors) for ncu captures, then exit")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case()
+        profile_case(bool(args.sharing))
         return
     if args.impl == "reference":
         reference_arm(args)

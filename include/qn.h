@@ -116,9 +116,8 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
  * the default mode's up to FP summation order; only the work on common
  * prefixes is done once.  A launch batch then holds up to B distinct states
  * (default B: a quarter of the free device memory, capped by trajectories).
- * qn_run_info's sweep_bytes returns the number of distinct final states in this
- * mode.  qn_traj_debug and qn_grad are unaffected (they re-simulate trajectories
- * one by one). */
+ * qn_traj_debug and qn_grad are unaffected (they re-simulate trajectories one by
+ * one). */
 qn_status qn_batch_set_sharing(qn_batch *h, int32_t on);
 
 /* Global id of the handle's first trajectory (default 0): the handle evolves
@@ -172,10 +171,12 @@ qn_status qn_traj_debug(qn_batch *h, int64_t t0, int64_t count, float *amps, uin
  * len.  Host-only; any negative entry gives QN_EINVAL. */
 qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, double *out);
 
-/* Gate and launch counts of the last run: G gates per circuit, the number of
- * library kernel launches it queued, and the statevector bytes the gate sweeps
- * read and wrote (algorithmic, 16 B per amplitude per sweep). */
-qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes);
+/* Counts of the last run: G gates per circuit, the library kernel launches it
+ * queued, the statevector bytes its gate sweeps read and wrote (algorithmic:
+ * 16 B per amplitude per sweep), and the number of distinct statevectors it
+ * evolved (= trajectories, or the distinct Kraus strings in shared-prefix
+ * mode).  Any output may be NULL. */
+qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes, int64_t *states);
 
 /* Kernel timing with CUDA events recorded on the handle's stream: period = 0
  * (default) records none; period = k >= 1 brackets every k-th gate-sweep

@@ -131,6 +131,7 @@ struct qn_batch {
     uint8_t *sh_cls = nullptr;
     int2 *sh_range = nullptr, *sh_forks = nullptr;
     double *sh_weights = nullptr;
+    double *sh_marg = nullptr;
     int64_t sh_cap = 0;
     int64_t sh_slots = 0;  // slots of the last shared-prefix run (all chunks)
     float2 *lambda = nullptr;  // adjoint vectors (qn_grad), allocated on first use
@@ -191,6 +192,7 @@ void release_all(qn_batch *h) {
     h->sh_cls = nullptr;
     h->sh_range = h->sh_forks = nullptr;
     h->sh_weights = nullptr;
+    h->sh_marg = nullptr;
     h->sh_cap = 0;
     h->grad_cap = 0;
     h->cap_B = 0;
@@ -462,6 +464,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
         QN_TRY(alloc_t(h, &h->sh_ctr, 4));
         QN_TRY(alloc_t(h, &h->sh_order, (size_t)kc));
         QN_TRY(alloc_t(h, &h->sh_weights, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->sh_marg, (size_t)kc * 4));
         h->sh_cap = kc;
     }
     BatchView v = view_for(h, h->offset + t0, kc);
@@ -529,6 +532,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     sv.active = h->sh_ctr + 1;
     sv.forks = h->sh_forks;
     sv.fork_count = h->sh_ctr + 2;
+    sv.marg = h->sh_marg;
     sv.max_slots = kc;
 
     BatchView vs = v;
@@ -543,7 +547,11 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     int active = ns;
     for (int g = n; g < G; ++g) {
         QN_TRY(prof_begin(h, &ep, 0, (double)active * 16.0 * (double)((size_t)1 << n)));
-        cudaError_t e = launch_slot_gate(v, sv, active, g, h->dgates_host[g], h->nz, h->damping_on, h->stream);
+        cudaError_t e = launch_slot_sweep(v, sv, active, g, h->dgates_host[g], h->damping_on, h->stream);
+        if (e == cudaSuccess) {
+            QN_TRY(prof_end(h, &ep));
+            e = launch_slot_fork(v, sv, active, g, h->dgates_host[g], h->nz, h->damping_on, h->stream);
+        }
         if (e == cudaSuccess) e = cudaMemcpyAsync(active_host, sv.active, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                                   h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -551,10 +559,9 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             cudaFreeHost(active_host);
             return fail(QN_ECUDA, "shared-prefix gate %d: %s", g, cudaGetErrorString(e));
         }
-        QN_TRY(prof_end(h, &ep));
         h->sweep_bytes += (double)active * 16.0 * (double)((size_t)1 << n);
         active = *active_host;
-        h->launches += 3;
+        h->launches += 4;
     }
     cudaFreeHost(active_host);
     // deterministic accumulation order: slots by their first member
@@ -933,14 +940,9 @@ qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, dou
     return ok();
 }
 
-qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes) {
+qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes, int64_t *states) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
-    if (h->sharing && sweep_bytes) {
-        *sweep_bytes = (double)h->sh_slots;  // shared-prefix mode: distinct final states
-        if (gates) *gates = (int64_t)h->gates.size();
-        if (launches) *launches = h->launches;
-        return ok();
-    }
+    if (states) *states = h->sharing ? h->sh_slots : h->K;
     if (gates) *gates = (int64_t)h->gates.size();
     if (launches) *launches = h->launches;
     if (sweep_bytes) *sweep_bytes = h->sweep_bytes;

@@ -66,6 +66,7 @@ struct SlotView {
     int32_t *active;     // slots swept by the current gate
     int2 *forks;         // [max_slots] (parent, child) created at the current gate
     int32_t *fork_count;
+    double *marg;        // [max_slots][4] damping marginal of each slot at the current gate
     int32_t max_slots;
 };
 
@@ -113,10 +114,13 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
 cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
-// Shared-prefix mode: sweep gate g over the `active` live slots, fork the slots
-// whose members drew other branches, copy the forked states (three launches;
-// the new live-slot count is left in *sv.active).
-cudaError_t launch_slot_gate(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
+// Shared-prefix mode, gate g: sweep the `active` live slots; then draw each
+// member's branch, fork the slots whose members drew other branches and copy
+// the forked states (three launches; the new live-slot count is left in
+// *sv.active).
+cudaError_t launch_slot_sweep(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
+                              int damping_on, cudaStream_t s);
+cudaError_t launch_slot_fork(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
                              const NoiseDev &nz, int damping_on, cudaStream_t s);
 // Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n
 // adding d<C>_t / d theta_param into grad[t * nparam + param] (FP64).

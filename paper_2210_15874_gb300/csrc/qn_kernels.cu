@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep_rx(BatchView v, int g, De
 // pending op.  Every trajectory therefore sees exactly the state and branch
 // draws it would see alone; only the work on common prefixes is shared.
 // ---------------------------------------------------------------------------
-__device__ __noinline__ void decide_slot(const BatchView &v, const SlotView &sv, int s, int g, const DevGate &gt,
+__device__ __forceinline__ void decide_slot(const BatchView &v, const SlotView &sv, int s, int g, const DevGate &gt,
                             const double *m_sh, double gamma, bool damp) {
     __shared__ int ccount[64], cstart[64], order[64];
     __shared__ int norder, child_base, run;
@@ -754,18 +754,29 @@ __device__ __noinline__ void decide_slot(const BatchView &v, const SlotView &sv,
 }
 
 // Slot sweeps: grid (sweep tiles, slots alive before this gate), one unit per
-// block, the same body as the batch sweeps.
+// block, the same body as the batch sweeps; the last block of a slot stores the
+// slot's marginal for k_slot_decide.
 template <bool DAMP, int KIND>
-__global__ void __launch_bounds__(kThreads, 4) k_slot_sweep(BatchView v, SlotView sv, int g, DevGate gt,
-                                                            double gamma) {
+__global__ void __launch_bounds__(kThreads, 4) k_slot_sweep(BatchView v, SlotView sv, int g, DevGate gt) {
     grid_dependency_wait();
     const int slot = blockIdx.y, tile = blockIdx.x;
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
     if (KIND == kGateZZ) zz_unit<DAMP, true>(v, slot, tile, g, gt, a0, a1, a2, a3);
     else rx_unit<DAMP, true>(v, slot, tile, g, gt, a0, a3);
     allow_dependent_launch();
-    __shared__ double m[4];
-    if (reduce_marginal(v, slot, tile, a0, a1, a2, a3, m)) decide_slot(v, sv, slot, g, gt, m, gamma, DAMP);
+    if (DAMP) {
+        __shared__ double m[4];
+        if (reduce_marginal(v, slot, tile, a0, a1, a2, a3, m) && threadIdx.x < 4)
+            sv.marg[(size_t)slot * 4 + threadIdx.x] = m[threadIdx.x];
+    }
+}
+
+// Branch classes of every live slot at gate g: one block per slot.
+template <bool DAMP>
+__global__ void __launch_bounds__(kThreads) k_slot_decide(BatchView v, SlotView sv, int g, DevGate gt, double gamma) {
+    grid_dependency_wait();
+    decide_slot(v, sv, blockIdx.x, g, gt, sv.marg + (size_t)blockIdx.x * 4, gamma, DAMP);
+    allow_dependent_launch();
 }
 
 // Copy the parent's statevector into every slot forked at this gate.
@@ -1207,7 +1218,7 @@ static int persistent_blocks() {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_slot_sweep<true, kGateZZ>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fork_copy, kThreads, 0);
         blocks = (sms > 0 ? sms : 152) * (per > 0 ? per : 4);
     }
     return blocks;
@@ -1228,17 +1239,22 @@ static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, cudaStream_t s, A
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-cudaError_t launch_slot_gate(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
+cudaError_t launch_slot_sweep(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
+                              int damping_on, cudaStream_t s) {
+    const dim3 grid((unsigned)v.stiles, (unsigned)active), block(kThreads);
+    if (gate.kind == kGateZZ)
+        return damping_on ? launch_pdl(k_slot_sweep<true, kGateZZ>, grid, block, s, v, sv, g, gate)
+                          : launch_pdl(k_slot_sweep<false, kGateZZ>, grid, block, s, v, sv, g, gate);
+    return damping_on ? launch_pdl(k_slot_sweep<true, kGateRX>, grid, block, s, v, sv, g, gate)
+                      : launch_pdl(k_slot_sweep<false, kGateRX>, grid, block, s, v, sv, g, gate);
+}
+
+cudaError_t launch_slot_fork(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
                              const NoiseDev &nz, int damping_on, cudaStream_t s) {
     const int blocks = persistent_blocks();
-    const dim3 grid((unsigned)v.stiles, (unsigned)active), block(kThreads);
-    cudaError_t e;
-    if (gate.kind == kGateZZ)
-        e = damping_on ? launch_pdl(k_slot_sweep<true, kGateZZ>, grid, block, s, v, sv, g, gate, nz.gamma)
-                       : launch_pdl(k_slot_sweep<false, kGateZZ>, grid, block, s, v, sv, g, gate, nz.gamma);
-    else
-        e = damping_on ? launch_pdl(k_slot_sweep<true, kGateRX>, grid, block, s, v, sv, g, gate, nz.gamma)
-                       : launch_pdl(k_slot_sweep<false, kGateRX>, grid, block, s, v, sv, g, gate, nz.gamma);
+    const dim3 block(kThreads);
+    cudaError_t e = damping_on ? launch_pdl(k_slot_decide<true>, dim3((unsigned)active), block, s, v, sv, g, gate, nz.gamma)
+                               : launch_pdl(k_slot_decide<false>, dim3((unsigned)active), block, s, v, sv, g, gate, nz.gamma);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_fork_copy, dim3(blocks), block, s, v, sv);
     if (e != cudaSuccess) return e;

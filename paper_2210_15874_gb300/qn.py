@@ -53,7 +53,7 @@ _SIGS = {
     "qn_grad_traj": (c_i32, [c_vp, c_i64, c_i64, P(c_dbl), P(c_dbl)]),
     "qn_traj_debug": (c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
     "qn_fidelity_error": (c_i32, [P(c_dbl), P(c_dbl), c_i64, P(c_dbl)]),
-    "qn_run_info": (c_i32, [c_vp, P(c_i64), P(c_i64), P(c_dbl)]),
+    "qn_run_info": (c_i32, [c_vp, P(c_i64), P(c_i64), P(c_dbl), P(c_i64)]),
     "qn_batch_set_profiling": (c_i32, [c_vp, c_i32]),
     "qn_profile_read": (c_i32, [c_vp, c_i32, P(c_i64), P(c_dbl), P(c_dbl)]),
     "qn_run_qaoa_noalloc": (c_i32, [c_i32, P(qn_graph), c_i32, P(c_dbl), P(c_dbl), P(qn_noise), c_u64, c_i64,
@@ -190,9 +190,10 @@ class Batch:
                     c_traj=None if cc is None else cc[:count])
 
     def run_info(self) -> dict:
-        g, l, b = c_i64(), c_i64(), c_dbl()
-        check(qn_run_info(self._h, ctypes.byref(g), ctypes.byref(l), ctypes.byref(b)), "qn_run_info")
-        return dict(gates=g.value, launches=l.value, sweep_bytes=b.value)
+        g, l, b, st = c_i64(), c_i64(), c_dbl(), c_i64()
+        check(qn_run_info(self._h, ctypes.byref(g), ctypes.byref(l), ctypes.byref(b), ctypes.byref(st)),
+              "qn_run_info")
+        return dict(gates=g.value, launches=l.value, sweep_bytes=b.value, states=st.value)
 
     def profile_read(self, kind: int) -> dict:
         l, ms, b = c_i64(), c_dbl(), c_dbl()

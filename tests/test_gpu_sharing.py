@@ -53,7 +53,7 @@ def test_sharing_equals_default_mode_and_oracle(qn, case):
     m1, s1, p1, _, _ = run(qn, w, False)
     m2, s2, p2, info, br = run(qn, w, True)
     distinct = len({bytes(r) for r in br})
-    assert info["sweep_bytes"] == distinct  # one shared state per distinct Kraus string
+    assert info["states"] == distinct  # one shared state per distinct Kraus string
     if case != "n14_damping_multitile":  # heavy noise: every string differs there
         assert distinct < K
     assert abs(m1 - m2) < 1e-9 and abs(s1 - s2) < 1e-9
@@ -97,7 +97,7 @@ def test_sharing_full_size_damping_n20(qn):
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
         m2, s2 = b.expectation()
         p2 = b.probs()
-        slots = b.run_info()["sweep_bytes"]
+        slots = b.run_info()["states"]
     assert slots < w.trajectories
     assert abs(m1 - m2) < 1e-8 and abs(s1 - s2) < 1e-8
     np.testing.assert_allclose(p2, p1, rtol=1e-12, atol=0)
