@@ -288,9 +288,11 @@ def gpu_arm(args):
         if os.path.exists(tr_path):
             try:
                 tj = json.load(open(tr_path))
-                if tj.get("kernel_source_hash") == kernel_hash() and tj.get("kernel") == kernel:
-                    traffic = tj.get("traffic_bytes_per_launch_full_size")
-            except (ValueError, OSError):
+                entry = tj.get("kernels", {}).get(kernel.split(" ")[0])
+                if entry and tj.get("kernel_source_hash") == kernel_hash():
+                    states_per_launch = (sw["bytes"] / max(sw["launches"], 1)) / (16.0 * (1 << w.n))
+                    traffic = entry["traffic_bytes_per_state"] * states_per_launch
+            except (ValueError, OSError, KeyError):
                 traffic = None
         return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
@@ -338,11 +340,17 @@ def profile_case(sharing=False):
     build.build()
     from paper_2210_15874_gb300 import qn
 
-    w = W.qaoa_workload("ncu_n20_p1_damp", 20, 1, index=1, trajectories=32, batch=32, damping=5e-3)
+    if sharing:
+        # heavy Pauli noise so that most of the 64 trajectories fork early: the
+        # late gates sweep ~64 live states (512 MiB, above L2)
+        w = W.qaoa_workload("ncu_n20_p1_damp_shared", 20, 1, index=1, trajectories=64, batch=64, p1=0.1, p2=0.3,
+                            damping=5e-3)
+    else:
+        w = W.qaoa_workload("ncu_n20_p1_damp", 20, 1, index=1, trajectories=32, batch=32, damping=5e-3)
     with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
         b.set_sharing(sharing)
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
-        print(json.dumps({"case": w.name, "c": b.expectation()}))
+        print(json.dumps({"case": w.name, "c": b.expectation(), "states": b.run_info()["states"]}))
 
 
 def kernel_hash():
@@ -366,8 +374,8 @@ def main():
     ap.add_argument("--single-mode", action="store_true",
                     help="time only the selected mode (skip the per-trajectory comparison run)")
     ap.add_argument("--profile-case", action="store_true",
-                    help="run one small ensemble (n=20, p=1, 32 trajectories in one launch: 256 MiB of "
-                         "statevectors) for ncu captures, then exit")
+                    help="run one small ensemble for ncu captures, then exit (n=20, p=1: 32 trajectories in "
+                         "one launch, or with --sharing 1 64 heavily noisy trajectories)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(bool(args.sharing))
