@@ -38,16 +38,28 @@ UNIT = "trajectories/s"
 PROFILE_PERIOD = 16  # time every 16th gate-sweep launch with a CUDA event pair
 
 
-def workload():
-    return W.damping_n20()
+WORKLOADS = {
+    # name: (factory, headline mode, comparison mode); a mode is (sharing, fusion)
+    "damping20": (W.damping_n20, (True, True), (False, True)),
+    "precision26": (W.precision_n26, (False, True), (False, False)),
+    "precision30": (W.precision_n30, (False, True), (False, False)),
+    "gradient16": (W.gradient_n16, (False, True), (False, False)),
+    "plain8": (W.plain_n8, (False, True), (False, False)),
+}
+
+
+def workload(name="damping20"):
+    return WORKLOADS[name][0]()
 
 
 def config_of(w, extra=None):
+    state_mib = 8 * (1 << w.n) / 2 ** 20
     cfg = {"workload": w.name, "n": w.n, "p": w.p, "graph": "seeded 3-regular", "edges": int(len(w.edges)),
            "gates": w.gate_count, "trajectories": w.trajectories, "launch_batch": w.batch,
            "noise": {"p1": w.p1, "p2": w.p2, "damping": w.damping, "twoq": "15-Pauli depolarizing"},
-           "state": "complex64 statevector, 8 MiB per trajectory",
-           "l2": "inputs larger than L2: 512 MiB of statevectors per launch (L2 129 MB)"}
+           "state": f"complex64 statevector, {state_mib:g} MiB per trajectory",
+           "l2": f"inputs larger than L2: {state_mib * w.batch / 1024:g} GiB of statevectors per launch "
+                 "(L2 129 MB)" if state_mib * w.batch > 129 else "launch fits in L2"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -173,12 +185,14 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def measure(qn, w, args, sharing, stream, rank, world, local, pg, with_e2e):
+def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
     """Time `args.steps` whole-ensemble steps (after `args.warmup`) in one mode."""
     import torch
 
+    sharing, fusion = mode
     b = qn.Batch(w.n, w.trajectories, w.seed, launch_batch=0 if sharing else w.batch, stream=stream)
     b.set_sharing(sharing)
+    b.set_fusion(fusion)
     # weak scaling: rank r evolves global trajectories [r K, (r+1) K)
     if world > 1:
         b.set_offset(rank * w.trajectories)
@@ -255,7 +269,7 @@ def gpu_arm(args):
     build.build()
     from paper_2210_15874_gb300 import qn
 
-    w = workload()
+    w = workload(args.workload)
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
@@ -264,11 +278,14 @@ def gpu_arm(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     stream = torch.cuda.current_stream()
 
-    sharing = bool(args.sharing)
-    main = measure(qn, w, args, sharing, stream, rank, world, local, pg, with_e2e=True)
+    _, main_mode, other_mode = WORKLOADS[args.workload]
+    if not args.sharing:
+        main_mode = (False, main_mode[1])
+    sharing = main_mode[0] and w.damping > 0
+    main = measure(qn, w, args, main_mode, stream, rank, world, local, pg, with_e2e=True)
     other = None
-    if sharing and not args.single_mode:
-        other = measure(qn, w, args, False, stream, rank, world, local, pg, with_e2e=False)
+    if not args.single_mode and other_mode != main_mode:
+        other = measure(qn, w, args, other_mode, stream, rank, world, local, pg, with_e2e=False)
 
     G, n, K = w.gate_count, w.n, w.trajectories
     h2d = int(len(w.edges) * 8 + 2 * w.p * 8 + 40 + G * 20)
@@ -301,16 +318,20 @@ def gpu_arm(args):
                 "share_of_step": sw["ms"] * PROFILE_PERIOD / res["ms"] if res["ms"] > 0 else None}
 
     if rank == 0:
+        fused = main_mode[1] and w.damping == 0
         kname = "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
-            "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)"
+            ("k_fused_sweep (fused layer sweeps, 16 B per amplitude)" if fused else
+             "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")
         line = {
             "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_of(w, {
                 "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
-                "mode": "shared-prefix: one statevector per distinct Kraus prefix, all 4096 trajectories in one "
-                        "prefix tree" if sharing else "one statevector per trajectory, 64 per launch"}),
+                "mode": ("shared-prefix: one statevector per distinct Kraus prefix, all trajectories in one "
+                         "prefix tree") if sharing else
+                        (f"fused layers: ceil(n/3) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused
+                         else f"one statevector per trajectory, one sweep per gate, {w.batch} per launch")}),
             "amp_updates_per_s": main["value"] * G * (1 << n),
             "distinct_states_per_step": main["states_per_step"],
             "sweep_bytes_per_step": main["sweep_bytes_per_step"],
@@ -323,11 +344,13 @@ def gpu_arm(args):
             "clocks": main["clocks"],
         }
         if other is not None:
-            line["per_trajectory_mode"] = {
+            key = "per_trajectory_mode" if sharing else "per_gate_mode"
+            line[key] = {
                 "value": other["value"], "unit": UNIT, "ms_per_step": other["ms"] / args.steps,
                 "c_mean": other["mean"], "gpu_launches": other["launches"], "clocks": other["clocks"],
+                "sweep_bytes_per_step": other["sweep_bytes_per_step"],
                 "roofline": roof(other, "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")}
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and w.n <= 20:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
     if pg:
@@ -368,6 +391,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gq", choices=["gq", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="damping20", choices=sorted(WORKLOADS),
+                    help="damping20 (default, the headline), precision26 / precision30 (Pauli-only, fused layers "
+                         "vs one sweep per gate), gradient16, plain8")
     ap.add_argument("--sharing", type=int, default=1, choices=[0, 1],
                     help="1: shared-prefix mode (trajectories share common Kraus prefixes); "
                          "0: every trajectory evolved separately, 64 per launch")

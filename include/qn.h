@@ -109,6 +109,15 @@ qn_status qn_batch_set_allocator(qn_batch *h, void *(*alloc)(size_t, void *),
  * 8 * 2^n * B bytes of HBM (complex64). */
 qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
 
+/* Fused layers (on = 1, the default; 0 = one sweep per gate).  With Pauli-only
+ * noise (damping == 0) no branch depends on the state, so each QAOA layer is
+ * applied as ceil(n / 3) sweeps instead of E + n: the cost layer (every phase
+ * gate and every Pauli's Z part) is one diagonal factor folded into a mixer
+ * sweep, and the mixer rotations are applied three qubits per sweep.  Needs
+ * at most 64 edges; otherwise, or with damping, gates are swept one by one.
+ * With damping == 0 fusion takes precedence over shared-prefix mode. */
+qn_status qn_batch_set_fusion(qn_batch *h, int32_t on);
+
 /* Shared-prefix mode (on = 1; default 0).  Trajectories whose Kraus strings
  * agree so far share one statevector; when a trajectory's own Pauli or damping
  * draw differs from the shared branch it forks into a copy.  Every trajectory

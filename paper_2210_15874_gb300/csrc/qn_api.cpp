@@ -125,6 +125,17 @@ struct qn_batch {
     DevGate *dgates = nullptr;
     int2 *dedges = nullptr;
     float2 *readout = nullptr;
+    // fused layers (Pauli-only noise)
+    int32_t fusion = 1;
+    uint64_t *fl_ev = nullptr;    // [4][256]
+    float2 *fl_phase = nullptr;   // [p][E+1]
+    int2 *fl_edges = nullptr;     // [E]
+    uint64_t *fl_s = nullptr;     // [p][B]
+    uint32_t *fl_u = nullptr;     // [p][4][B]: zm, zc, mz, mf
+    int32_t fl_cap_p = 0, fl_cap_E = -1;
+    int64_t fl_cap_B = 0;
+    std::vector<uint64_t> ev_host;
+    std::vector<float2> phase_host;
     // shared-prefix mode
     int32_t sharing = 0;
     int32_t *sh_members = nullptr, *sh_tmp = nullptr, *sh_ctr = nullptr, *sh_order = nullptr;
@@ -194,6 +205,14 @@ void release_all(qn_batch *h) {
     h->sh_weights = nullptr;
     h->sh_marg = nullptr;
     h->sh_cap = 0;
+    h->fl_ev = nullptr;
+    h->fl_phase = nullptr;
+    h->fl_edges = nullptr;
+    h->fl_s = nullptr;
+    h->fl_u = nullptr;
+    h->fl_cap_p = 0;
+    h->fl_cap_E = -1;
+    h->fl_cap_B = 0;
     h->grad_cap = 0;
     h->cap_B = 0;
     h->cap_G = -1;
@@ -205,7 +224,7 @@ size_t state_bytes(int n) { return (size_t)8 << n; }
 // Every buffer a run of B trajectories per launch, G gates and E edges needs.
 size_t footprint(int n, int64_t K, int64_t B, int32_t G, int32_t E) {
     const size_t tiles = (size_t)tiles_for(n);
-    size_t s = 2 * (size_t)B * state_bytes(n);  // states + debug readout
+    size_t s = (size_t)B * state_bytes(n);  // states (debug readout and adjoint vectors come on demand)
     s += (size_t)B * G * (1 + 8) + (size_t)B * (G + 1) * 4 + (size_t)B * (1 + 8 * n + sizeof(TrajState) + 4 + 8);
     s += (size_t)B * tiles * 32 + (size_t)B * 8 + (size_t)B * accumulate_xblocks(n) * 8 + (size_t)K * 8 +
          ((size_t)8 << n);
@@ -407,6 +426,100 @@ qn_status prof_collect(qn_batch *h) {
     return QN_OK;
 }
 
+bool use_fusion(const qn_batch *h) {
+    return h->fusion && !h->damping_on && h->edges.size() / 2 <= 64 && h->n >= 2;
+}
+
+// Graph tables of the fused cost layer: EV byte tables (bit e of EV(y) set when
+// the endpoints of edge e differ in y) and e^{-i gamma_l k}, k = 0..E.
+qn_status prepare_fusion(qn_batch *h) {
+    const int E = (int)h->edges.size() / 2;
+    const int p = h->p;
+    const int64_t B = h->cap_B;
+    if (h->fl_cap_p < p || h->fl_cap_E != E || h->fl_cap_B < B || !h->fl_ev) {
+        QN_TRY(alloc_t(h, &h->fl_ev, 1024));
+        QN_TRY(alloc_t(h, &h->fl_phase, (size_t)std::max(p, 1) * (E + 1)));
+        QN_TRY(alloc_t(h, &h->fl_edges, (size_t)std::max(E, 1)));
+        QN_TRY(alloc_t(h, &h->fl_s, (size_t)std::max(p, 1) * B));
+        QN_TRY(alloc_t(h, &h->fl_u, (size_t)std::max(p, 1) * 4 * B));
+        h->fl_cap_p = p;
+        h->fl_cap_E = E;
+        h->fl_cap_B = B;
+    }
+    std::vector<uint64_t> col((size_t)h->n, 0);
+    for (int e = 0; e < E; ++e) {
+        col[h->edges[2 * e]] ^= (uint64_t)1 << e;
+        col[h->edges[2 * e + 1]] ^= (uint64_t)1 << e;
+    }
+    h->ev_host.assign(1024, 0);
+    for (int b = 0; b < 4; ++b)
+        for (int v = 0; v < 256; ++v) {
+            uint64_t acc = 0;
+            for (int k = 0; k < 8; ++k)
+                if ((v >> k) & 1) {
+                    const int q = 8 * b + k;
+                    if (q < h->n) acc ^= col[q];
+                }
+            h->ev_host[(size_t)b * 256 + v] = acc;
+        }
+    h->phase_host.assign((size_t)std::max(p, 1) * (E + 1), make_float2(1.0f, 0.0f));
+    for (int l = 0; l < p; ++l)
+        for (int k = 0; k <= E; ++k)
+            h->phase_host[(size_t)l * (E + 1) + k] =
+                make_float2((float)std::cos(h->gammas[l] * k), (float)-std::sin(h->gammas[l] * k));
+    QN_CUDA(cudaMemcpyAsync(h->fl_ev, h->ev_host.data(), 1024 * sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+    QN_CUDA(cudaMemcpyAsync(h->fl_phase, h->phase_host.data(), h->phase_host.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice, h->stream));
+    if (E > 0)
+        QN_CUDA(cudaMemcpyAsync(h->fl_edges, h->edges_host.data(), (size_t)E * sizeof(int2), cudaMemcpyHostToDevice,
+                                h->stream));
+    return QN_OK;
+}
+
+LayerView layer_view(const qn_batch *h, int l) {
+    const int E = (int)h->edges.size() / 2;
+    const int64_t B = h->cap_B;
+    LayerView L;
+    L.ev = h->fl_ev;
+    L.phase = h->fl_phase + (size_t)l * (E + 1);
+    L.edges = h->fl_edges;
+    L.s = h->fl_s + (size_t)l * B;
+    L.zm = h->fl_u + ((size_t)l * 4 + 0) * B;
+    L.zc = h->fl_u + ((size_t)l * 4 + 1) * B;
+    L.mz = h->fl_u + ((size_t)l * 4 + 2) * B;
+    L.mf = h->fl_u + ((size_t)l * 4 + 3) * B;
+    L.cb = (float)std::cos(h->betas[l]);
+    L.sb = (float)std::sin(h->betas[l]);
+    return L;
+}
+
+// All gates after the H layer as fused sweeps: per layer ceil(n / kFuse)
+// mixer sweeps; the cost phase of layer 0 rides on the first sweep and that of
+// layer l+1 on the last mixer sweep of layer l.
+qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, bool ensemble) {
+    const int n = h->n, p = h->p;
+    const int E = (int)h->edges.size() / 2;
+    for (int l = 0; l < p; ++l) {
+        QN_CUDA(launch_layer_params(v, layer_view(h, l), n + l * (E + n), E, h->stream));
+        h->launches += 1;
+    }
+    EventPair ep;
+    for (int l = 0; l < p; ++l) {
+        for (int q_lo = 0; q_lo < n; q_lo += kFuse) {
+            const int m = std::min(kFuse, n - q_lo);
+            const bool pre = l == 0 && q_lo == 0;
+            const bool post = q_lo + m >= n && l + 1 < p;
+            QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));
+            QN_CUDA(launch_fused_sweep(v, layer_view(h, l), layer_view(h, l), layer_view(h, post ? l + 1 : l), q_lo, m,
+                                       pre, post, h->stream));
+            QN_TRY(prof_end(h, &ep));
+            h->launches += 1;
+            if (ensemble) h->sweep_bytes += amp_bytes * 16.0;
+        }
+    }
+    return QN_OK;
+}
+
 // Queue the whole pipeline for the handle's trajectories t0 .. t0+b-1 (global ids
 // offset + t0 ..; b <= cap_B).
 // ensemble = true adds into probs / S1 / S2 and writes c_all; otherwise the
@@ -423,12 +536,16 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     QN_CUDA(launch_init(v, h->stream));
     QN_TRY(prof_end(h, &ep));
     h->launches += 1;
-    for (int g = n; g < G; ++g) {
-        QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));
-        QN_CUDA(launch_sweep(v, g, h->dgates_host[g], h->nz, h->damping_on, h->stream));
-        QN_TRY(prof_end(h, &ep));
-        h->launches += 1;
-        if (ensemble) h->sweep_bytes += amp_bytes * 16.0;
+    if (use_fusion(h)) {
+        QN_TRY(run_fused_gates(h, v, amp_bytes, ensemble));
+    } else {
+        for (int g = n; g < G; ++g) {
+            QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));
+            QN_CUDA(launch_sweep(v, g, h->dgates_host[g], h->nz, h->damping_on, h->stream));
+            QN_TRY(prof_end(h, &ep));
+            h->launches += 1;
+            if (ensemble) h->sweep_bytes += amp_bytes * 16.0;
+        }
     }
     AccumView a;
     a.num_edges = (int32_t)h->edges_host.size();
@@ -693,6 +810,14 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B) {
     return ok();
 }
 
+qn_status qn_batch_set_fusion(qn_batch *h, int32_t on) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (on != 0 && on != 1) return fail(QN_EINVAL, "fusion must be 0 or 1");
+    h->fusion = on;
+    h->has_run = false;
+    return ok();
+}
+
 qn_status qn_batch_set_sharing(qn_batch *h, int32_t on) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
     if (on != 0 && on != 1) return fail(QN_EINVAL, "sharing must be 0 or 1");
@@ -759,12 +884,13 @@ qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const doubl
     QN_CUDA(cudaMemsetAsync(h->probs, 0, sizeof(double) << h->n, h->stream));
     QN_CUDA(cudaMemsetAsync(h->sums, 0, 2 * sizeof(double), h->stream));
     QN_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    if (use_fusion(h)) QN_TRY(prepare_fusion(h));
     h->launches = 0;
     h->sweep_bytes = 0.0;
     h->sh_slots = 0;
     for (int64_t t0 = 0; t0 < h->K; t0 += B) {
         const int b = (int)std::min<int64_t>(B, h->K - t0);
-        if (h->sharing) QN_TRY(run_shared(h, t0, b));
+        if (h->sharing && !use_fusion(h)) QN_TRY(run_shared(h, t0, b));
         else QN_TRY(run_batch(h, t0, b, true));
     }
     h->has_run = true;
@@ -942,7 +1068,7 @@ qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, dou
 
 qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes, int64_t *states) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
-    if (states) *states = h->sharing ? h->sh_slots : h->K;
+    if (states) *states = (h->sharing && !use_fusion(h)) ? h->sh_slots : h->K;
     if (gates) *gates = (int64_t)h->gates.size();
     if (launches) *launches = h->launches;
     if (sweep_bytes) *sweep_bytes = h->sweep_bytes;

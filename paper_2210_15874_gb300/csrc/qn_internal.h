@@ -70,6 +70,19 @@ struct SlotView {
     int32_t max_slots;
 };
 
+// One QAOA layer for the fused (Pauli-only) sweeps.
+struct LayerView {
+    const uint64_t *ev;      // [4][256] edge-difference vectors by byte of y (bit e: endpoints of edge e differ)
+    const float2 *phase;     // [E+1] e^{-i gamma k}
+    const int2 *edges;       // [E]
+    uint64_t *s;             // [b] edges whose endpoints' frame bits differ at their gate
+    uint32_t *zm, *zc;       // [b] Z parts of the cost layer's Paulis: mask and frame parity
+    uint32_t *mz, *mf;       // [b] mixer: Z part of each qubit's Pauli, frame bit at its gate
+    float cb, sb;            // cos beta, sin beta of the layer
+};
+
+constexpr int kFuse = 3;     // qubits per fused mixer sweep
+
 struct NoiseDev {
     double gamma;              // damping (0 = off)
     uint64_t thr1[4];          // cumulative thresholds, 1q
@@ -114,6 +127,13 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
 cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
+// Fused layers (Pauli-only): per-trajectory layer parameters from the branch
+// tables, then sweeps applying the rotations of qubits [q_lo, q_lo + m) of
+// layer Lr, with layer Lp's phase before them (pre) and layer Lq's after (post).
+cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, int E, cudaStream_t s);
+cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
+                               int q_lo, int m, bool pre, bool post, cudaStream_t s);
+cudaError_t launch_phase_sweep(const BatchView &v, const LayerView &L, cudaStream_t s);
 // Shared-prefix mode, gate g: sweep the `active` live slots; then draw each
 // member's branch, fork the slots whose members drew other branches and copy
 // the forked states (three launches; the new live-slot count is left in

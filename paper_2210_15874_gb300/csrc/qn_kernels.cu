@@ -1152,6 +1152,158 @@ __global__ void __launch_bounds__(kThreads) k_adj_sweep(BatchView v, float2 *lam
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused layers (Pauli-only noise).  Without damping no branch depends on the
+// state, so a whole QAOA layer can be applied in few sweeps:
+//  * the cost layer -- every edge's phase gate and every Pauli's Z part -- is
+//    diagonal in the stored basis: phi_y *= (-1)^{popc(y & zm) + zc} *
+//    e^{-i gamma k(y)}, k(y) = popc(EV(y) xor s), where EV(y) has bit e set when
+//    the stored bits of edge e's endpoints differ (XOR of four byte tables) and
+//    s_e flips edge e when the frame differs on its endpoints at that gate;
+//  * the mixer layer is a tensor product of one 2x2 matrix per qubit (the
+//    rotation with the row signs of its Pauli's Z part), applied in register
+//    fibers over kFuse consecutive qubits per sweep.
+// A sweep applies [phase of layer l] (first sweep) and the rotations of one
+// qubit group; the last group of a layer also applies the next layer's phase.
+// ---------------------------------------------------------------------------
+__global__ void k_layer_params(BatchView v, LayerView L, int g0, int E) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= v.b) return;
+    uint64_t sv = 0;
+    uint32_t zm = 0, zc = 0, mz = 0, mf = 0;
+    for (int e = 0; e < E; ++e) {
+        const int g = g0 + e;
+        const uint32_t F = v.frame_x[(size_t)t * (v.G + 1) + g];
+        const int2 ed = L.edges[e];
+        sv |= (uint64_t)(((F >> ed.x) ^ (F >> ed.y)) & 1u) << e;
+        const int code = v.branch[(size_t)t * v.G + g] & 15;
+        const uint32_t za = zpart_1q(code >> 2), zb = zpart_1q(code & 3);
+        zm ^= (za << ed.x) ^ (zb << ed.y);
+        zc ^= (za & (F >> ed.x)) ^ (zb & (F >> ed.y));
+    }
+    for (int q = 0; q < v.n; ++q) {
+        const int g = g0 + E + q;
+        const uint32_t F = v.frame_x[(size_t)t * (v.G + 1) + g];
+        mz |= zpart_1q(v.branch[(size_t)t * v.G + g] & 15) << q;
+        mf |= ((F >> q) & 1u) << q;
+    }
+    L.s[t] = sv;
+    L.zm[t] = zm;
+    L.zc[t] = zc & 1u;
+    L.mz[t] = mz;
+    L.mf[t] = mf;
+}
+
+__device__ __forceinline__ float2 layer_phase(const LayerView &L, uint32_t y, uint64_t sv, uint32_t zm, uint32_t zc) {
+    const uint64_t ev = __ldg(L.ev + (y & 255u)) ^ __ldg(L.ev + 256 + ((y >> 8) & 255u)) ^
+                        __ldg(L.ev + 512 + ((y >> 16) & 255u)) ^ __ldg(L.ev + 768 + (y >> 24));
+    const int k = __popcll(ev ^ sv);
+    const float2 ph = __ldg(L.phase + k);
+    const float sg = ((__popc(y & zm) ^ zc) & 1u) ? -1.0f : 1.0f;
+    return make_float2(ph.x * sg, ph.y * sg);
+}
+
+__device__ __forceinline__ void cmul_inplace(float &re, float &im, float2 w) {
+    const float r = re * w.x - im * w.y, i = re * w.y + im * w.x;
+    re = r;
+    im = i;
+}
+
+// One fused sweep.  The group is qubits [q_lo, q_lo + M); with HAS0 (q_lo == 0)
+// bit 0 lies inside each float4 and a thread holds 2^(M-1) float4, otherwise
+// 2^M float4 along f bits q_lo-1 .. q_lo+M-2.  PRE: phase of layer `lp` before
+// the rotations; POST: phase of layer `lq` after them.
+template <int M, bool HAS0, bool PRE, bool POST>
+__global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerView Lp, LayerView Lr, LayerView Lq,
+                                                             int q_lo) {
+    constexpr int D = HAS0 ? M - 1 : M;  // fiber bits in float4 index space
+    constexpr int NE = 1 << D;
+    const int t = blockIdx.y;
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1);
+    const int fl = HAS0 ? 0 : q_lo - 1;
+    const int64_t nfib = nf >> D;
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= nfib) return;
+    const int64_t fbase = ((r >> fl) << (fl + D)) | (r & (((int64_t)1 << fl) - 1));
+    float4 val[NE];
+#pragma unroll
+    for (int k = 0; k < NE; ++k) val[k] = p4[fbase + ((int64_t)k << fl)];
+    if (PRE) {
+        const uint64_t sv = Lp.s[t];
+        const uint32_t zm = Lp.zm[t], zc = Lp.zc[t];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            const uint32_t y = (uint32_t)(2 * (fbase + ((int64_t)k << fl)));
+            cmul_inplace(val[k].x, val[k].y, layer_phase(Lp, y, sv, zm, zc));
+            cmul_inplace(val[k].z, val[k].w, layer_phase(Lp, y | 1u, sv, zm, zc));
+        }
+    }
+    const uint32_t mz = Lr.mz[t], mf = Lr.mf[t];
+    const float cb = Lr.cb, sb = Lr.sb;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const int q = q_lo + j;
+        const uint32_t z = (mz >> q) & 1u, fb = (mf >> q) & 1u;
+        const float s0 = (z && fb) ? -1.0f : 1.0f, s1 = (z && !fb) ? -1.0f : 1.0f;
+        const float c0 = cb * s0, sn0 = sb * s0, c1 = cb * s1, sn1 = sb * s1;
+        if (HAS0 && j == 0) {
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                const float r0 = val[k].x, i0 = val[k].y, r1 = val[k].z, i1 = val[k].w;
+                val[k].x = c0 * r0 + sn0 * i1;
+                val[k].y = c0 * i0 - sn0 * r1;
+                val[k].z = c1 * r1 + sn1 * i0;
+                val[k].w = c1 * i1 - sn1 * r0;
+            }
+        } else {
+            const int bit = HAS0 ? j - 1 : j;  // element-index bit of qubit q
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                if (k & (1 << bit)) continue;
+                float4 &a = val[k];
+                float4 &b = val[k | (1 << bit)];
+                float nx = c0 * a.x + sn0 * b.y, ny = c0 * a.y - sn0 * b.x;
+                float mx = c1 * b.x + sn1 * a.y, my = c1 * b.y - sn1 * a.x;
+                float nz = c0 * a.z + sn0 * b.w, nw = c0 * a.w - sn0 * b.z;
+                float mzv = c1 * b.z + sn1 * a.w, mw = c1 * b.w - sn1 * a.z;
+                a = make_float4(nx, ny, nz, nw);
+                b = make_float4(mx, my, mzv, mw);
+            }
+        }
+    }
+    if (POST) {
+        const uint64_t sv = Lq.s[t];
+        const uint32_t zm = Lq.zm[t], zc = Lq.zc[t];
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            const uint32_t y = (uint32_t)(2 * (fbase + ((int64_t)k << fl)));
+            cmul_inplace(val[k].x, val[k].y, layer_phase(Lq, y, sv, zm, zc));
+            cmul_inplace(val[k].z, val[k].w, layer_phase(Lq, y | 1u, sv, zm, zc));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NE; ++k) p4[fbase + ((int64_t)k << fl)] = val[k];
+}
+
+// Phase only (a circuit whose layers have no mixer qubits left to fuse with).
+__global__ void __launch_bounds__(kThreads) k_phase_sweep(BatchView v, LayerView L) {
+    const int t = blockIdx.y;
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
+    const uint64_t sv = L.s[t];
+    const uint32_t zm = L.zm[t], zc = L.zc[t];
+    for (int64_t f = (int64_t)blockIdx.x * kThreads + threadIdx.x; f < nf; f += (int64_t)gridDim.x * kThreads) {
+        float4 val = p4[f];
+        const uint32_t y = (uint32_t)(2 * f);
+        cmul_inplace(val.x, val.y, layer_phase(L, y, sv, zm, zc));
+        cmul_inplace(val.z, val.w, layer_phase(L, y | 1u, sv, zm, zc));
+        p4[f] = val;
+    }
+}
+
 // Readout of psi_x = i^k * D * phi_{x xor F} in the true basis (debug path).
 __global__ void __launch_bounds__(kThreads) k_readout(BatchView v, float2 *out) {
     const int t = blockIdx.y;
@@ -1293,4 +1445,45 @@ cudaError_t launch_adj_sweep(const BatchView &v, float2 *lam, int g, const DevGa
     return cudaGetLastError();
 }
 
+cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, int E, cudaStream_t s) {
+    k_layer_params<<<(v.b + 127) / 128, 128, 0, s>>>(v, L, g0, E);
+    return cudaGetLastError();
+}
+
+template <int M, bool HAS0>
+static cudaError_t fused_dispatch(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
+                                  int q_lo, bool pre, bool post, cudaStream_t s) {
+    constexpr int D = HAS0 ? M - 1 : M;
+    const int64_t nfib = ((int64_t)1 << (v.n - 1)) >> D;
+    const dim3 grid((unsigned)((nfib + kThreads - 1) / kThreads), (unsigned)v.b);
+    if (pre && post) k_fused_sweep<M, HAS0, true, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    else if (pre) k_fused_sweep<M, HAS0, true, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    else if (post) k_fused_sweep<M, HAS0, false, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    else k_fused_sweep<M, HAS0, false, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
+                               int q_lo, int m, bool pre, bool post, cudaStream_t s) {
+    const bool has0 = q_lo == 0;
+    // fiber dimension D must stay below the n-1 float4 index bits
+    switch (m) {
+    case 1: return has0 ? fused_dispatch<1, true>(v, Lp, Lr, Lq, q_lo, pre, post, s)
+                        : fused_dispatch<1, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 2: return has0 ? fused_dispatch<2, true>(v, Lp, Lr, Lq, q_lo, pre, post, s)
+                        : fused_dispatch<2, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    default: return has0 ? fused_dispatch<3, true>(v, Lp, Lr, Lq, q_lo, pre, post, s)
+                         : fused_dispatch<3, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    }
+}
+
+cudaError_t launch_phase_sweep(const BatchView &v, const LayerView &L, cudaStream_t s) {
+    const int64_t nf = (int64_t)1 << (v.n - 1 > 0 ? v.n - 1 : 0);
+    int64_t blocks = (nf + kThreads - 1) / kThreads;
+    if (blocks > 65535) blocks = 65535;
+    k_phase_sweep<<<dim3((unsigned)blocks, (unsigned)v.b), kThreads, 0, s>>>(v, L);
+    return cudaGetLastError();
+}
+
 }  // namespace qn
+

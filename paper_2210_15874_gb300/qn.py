@@ -46,6 +46,7 @@ _SIGS = {
     "qn_batch_set_launch_batch": (c_i32, [c_vp, c_i64]),
     "qn_batch_set_offset": (c_i32, [c_vp, c_i64]),
     "qn_batch_set_sharing": (c_i32, [c_vp, c_i32]),
+    "qn_batch_set_fusion": (c_i32, [c_vp, c_i32]),
     "qn_run_qaoa": (c_i32, [c_vp, P(qn_graph), c_i32, P(c_dbl), P(c_dbl), P(qn_noise)]),
     "qn_expectation": (c_i32, [c_vp, P(c_dbl), P(c_dbl)]),
     "qn_probs": (c_i32, [c_vp, P(c_dbl), c_i64]),
@@ -129,6 +130,10 @@ class Batch:
         a, f = ALLOC_FN(_alloc), FREE_FN(_free)
         self._keep += [a, f]
         check(qn_batch_set_allocator(self._h, a, f, None), "qn_batch_set_allocator")
+
+    def set_fusion(self, on: bool) -> None:
+        """Fused layers for Pauli-only noise (default on)."""
+        check(qn_batch_set_fusion(self._h, int(bool(on))), "qn_batch_set_fusion")
 
     def set_sharing(self, on: bool) -> None:
         """Shared-prefix mode: trajectories share their common Kraus prefix."""

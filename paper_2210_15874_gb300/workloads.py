@@ -115,6 +115,12 @@ def precision_n26() -> Workload:
     return qaoa_workload("qaoa_n26_p4_depol", 26, 4, index=2, trajectories=64, batch=64)
 
 
+def precision_n30() -> Workload:
+    """QAOA p=4 on a seeded 3-regular n=30 graph, depolarizing only, 16 trajectories
+    of 8 GiB each in one launch."""
+    return qaoa_workload("qaoa_n30_p4_depol", 30, 4, index=2, trajectories=16, batch=16)
+
+
 def gradient_n16() -> Workload:
     """QAOA p=6 on a seeded 3-regular n=16 graph, depolarizing only, K=2048."""
     return qaoa_workload("qaoa_n16_p6_depol_K2048", 16, 6, index=4, trajectories=2048, batch=256)

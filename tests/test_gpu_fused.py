@@ -1,0 +1,85 @@
+"""Fused layers (Pauli-only noise): ceil(n/3) sweeps per QAOA layer instead of
+one per gate.  Checked against the per-gate sweeps and the FP64 oracle on the
+same trajectories: Pauli codes bit-exact, amplitudes within 1e-5, <C>_t within
+the FP32 bound; the precision figures at n=14 are printed (pytest -s)."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_15874_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def qn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_15874_gb300 import build
+    build.build()
+    from paper_2210_15874_gb300 import qn as mod
+    return mod
+
+
+def run(qn, w, fusion, launch_batch=0):
+    with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=launch_batch) as b:
+        b.set_fusion(fusion)
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        mean, se = b.expectation()
+        probs = b.probs()
+        dbg = b.traj_debug(0, w.trajectories)
+        info = b.run_info()
+    return dict(mean=mean, se=se, probs=probs, info=info, **dbg)
+
+
+@pytest.mark.parametrize("n,p,edges_kind", [(2, 1, "one"), (3, 2, "ring"), (4, 2, "ring"), (7, 2, "reg"),
+                                            (8, 1, "reg"), (12, 3, "reg"), (14, 2, "reg")])
+def test_fused_matches_per_gate_and_oracle(qn, n, p, edges_kind):
+    if edges_kind == "one":
+        edges = np.array([[0, 1]], dtype=np.int32)
+    elif edges_kind == "ring":
+        edges = W.ring_graph(n)
+    else:
+        edges = W.regular_graph(n, 3 if n % 2 == 0 else 4, 70 + n)
+    g, b = W.angles(p, 80 + n)
+    K = 24
+    w = W.Workload(f"fused_n{n}", n, edges, p, g, b, 0.02, 0.05, 0.0, K, K, 555 + n)
+    fused = run(qn, w, True, launch_batch=10)
+    plain = run(qn, w, False, launch_batch=10)
+    gates, G = oracle.qaoa_gates(n, edges, g, b)
+    ref = oracle.traj_run(n, edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, 0, K)
+    np.testing.assert_array_equal(fused["branches"], ref["branches"])
+    tol_c = 8 * U32 * G * len(edges)
+    for res in (fused, plain):
+        assert np.abs(res["amps"] - ref["amps"]).max() < 1e-5
+        assert np.abs(res["c_traj"] - ref["c_traj"]).max() < tol_c
+        assert abs(res["mean"] - ref["s1"] / K) < tol_c
+    assert np.abs(fused["amps"] - plain["amps"]).max() < 1e-5
+    # fewer sweeps: launches per batch = prepare + init + p layer-parameter kernels
+    # + p ceil(n/3) fused sweeps + observe + probs
+    nb = -(-K // 10)
+    assert fused["info"]["launches"] == nb * (2 + p + p * (-(-n // 3)) + 2)
+
+
+def test_fused_precision_n14(qn):
+    """The 26/30-qubit precision workload's circuit family (3-regular, p=4,
+    p1=1e-3, p2=1e-2) at n=14 against the FP64 oracle, both schedules."""
+    w = W.qaoa_workload("precision_n14", 14, 4, index=2, trajectories=32, batch=32)
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    ref = oracle.traj_run(w.n, w.edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, 0, w.trajectories)
+    out = {}
+    for name, fusion in (("fused", True), ("per_gate", False)):
+        r = run(qn, w, fusion)
+        d = r["amps"] - ref["amps"]
+        out[name] = {"max_abs_amp_err": float(np.abs(d).max()),
+                     "rms_amp_err": float(np.sqrt(np.mean(np.abs(d) ** 2))),
+                     "max_abs_c_err": float(np.abs(r["c_traj"] - ref["c_traj"]).max()),
+                     "mean_c_err": float(abs(r["mean"] - ref["s1"] / w.trajectories)),
+                     "sweeps_per_trajectory": int(r["info"]["sweep_bytes"] / (16 * 2 ** w.n * w.trajectories))}
+        assert out[name]["max_abs_amp_err"] < 1e-5
+    print(json.dumps({"precision_n14_fp32": out, "gates": G}))

@@ -30,6 +30,7 @@ def qn():
 def run(qn, w, sharing, launch_batch=0):
     with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=launch_batch) as b:
         b.set_sharing(sharing)
+        b.set_fusion(False)  # with Pauli-only noise fusion would take precedence over sharing
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
         mean, se = b.expectation()
         probs = b.probs()
