@@ -357,6 +357,54 @@ def gpu_arm(args):
         pg.destroy_process_group()
 
 
+def serving_arm(args):
+    """Serving workload: closed-loop capacity, then Poisson arrivals at 0.5x and 0.8x of it."""
+    import torch
+
+    from paper_2210_15874_gb300 import build
+    build.build()
+    from paper_2210_15874_gb300 import serving
+
+    torch.cuda.set_device(0)
+    reqs = serving.serving_mix(args.requests)
+    warm = serving.serving_mix(4, seed=99)
+    srv = serving.Server(max_inflight=args.inflight)
+    for f in [srv.submit(r) for r in warm]:
+        f.result()
+
+    def run(rate):
+        rng = np.random.default_rng(7)
+        t0 = time.perf_counter()
+        futs = []
+        for r in reqs:
+            if rate:
+                time.sleep(float(rng.exponential(1.0 / rate)))
+            futs.append(srv.submit(r))
+        res = [f.result() for f in futs]
+        span = time.perf_counter() - t0
+        lat = [x.latency for x in res]
+        traj = sum(r.trajectories for r in reqs)
+        return {"requests": len(reqs), "seconds": span, "requests_per_s": len(reqs) / span,
+                "trajectories_per_s": traj / span, "p50_latency_s": serving.percentile(lat, 50),
+                "p99_latency_s": serving.percentile(lat, 99), "mean_latency_s": float(np.mean(lat))}
+
+    with ClockSampler(0) as clocks:
+        cap = run(0)
+        half = run(0.5 * cap["requests_per_s"])
+        high = run(0.8 * cap["requests_per_s"])
+    srv.close()
+    line = {"metric": "noisy trajectories/s and p50/p99 request latency under Poisson load", "value":
+            high["trajectories_per_s"], "unit": "trajectories/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: n ~ U{10..24}, p ~ U{1..6}, K ~ log-uniform[256, 8192], depolarizing "
+                                   "1e-3/1e-2 + damping 5e-3, seeded regular graphs",
+                       "requests": args.requests, "max_inflight": args.inflight,
+                       "admission": "HBM footprint (launch batch of statevectors + tables) within 60% of free memory",
+                       "mode": "shared-prefix mode per request, one CUDA stream per in-flight request"},
+            "capacity": cap, "load_0.5": half, "load_0.8": high, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def profile_case(sharing=False):
     """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state)."""
     from paper_2210_15874_gb300 import build
@@ -391,7 +439,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gq", choices=["gq", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="damping20", choices=sorted(WORKLOADS),
+    ap.add_argument("--requests", type=int, default=40, help="serving workload: requests per load level")
+    ap.add_argument("--inflight", type=int, default=4, help="serving workload: concurrent requests")
+    ap.add_argument("--workload", default="damping20", choices=sorted(WORKLOADS) + ["serving"],
                     help="damping20 (default, the headline), precision26 / precision30 (Pauli-only, fused layers "
                          "vs one sweep per gate), gradient16, plain8")
     ap.add_argument("--sharing", type=int, default=1, choices=[0, 1],
@@ -406,7 +456,9 @@ def main():
     if args.profile_case:
         profile_case(bool(args.sharing))
         return
-    if args.impl == "reference":
+    if args.workload == "serving":
+        serving_arm(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)

@@ -659,8 +659,10 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     QN_CUDA(launch_init(vs, h->stream));
     QN_TRY(prof_end(h, &ep));
     h->launches += 1;
-    int32_t *active_host = nullptr;
-    QN_CUDA(cudaMallocHost(&active_host, sizeof(int32_t)));
+    // pageable host word: a pinned one would need cudaFreeHost, which synchronises
+    // the whole device and would stall other handles' streams
+    int32_t active_word = ns;
+    int32_t *active_host = &active_word;
     int active = ns;
     for (int g = n; g < G; ++g) {
         QN_TRY(prof_begin(h, &ep, 0, (double)active * 16.0 * (double)((size_t)1 << n)));
@@ -672,15 +674,11 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(active_host, sv.active, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                                   h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) {
-            cudaFreeHost(active_host);
-            return fail(QN_ECUDA, "shared-prefix gate %d: %s", g, cudaGetErrorString(e));
-        }
+        if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix gate %d: %s", g, cudaGetErrorString(e));
         h->sweep_bytes += (double)active * 16.0 * (double)((size_t)1 << n);
         active = *active_host;
         h->launches += 4;
     }
-    cudaFreeHost(active_host);
     // deterministic accumulation order: slots by their first member
     int32_t nslots = 0;
     QN_CUDA(cudaMemcpyAsync(&nslots, h->sh_ctr, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));

@@ -102,6 +102,7 @@ class Batch:
         self._keep = []
         if launch_batch:
             check(qn_batch_set_launch_batch(h, int(launch_batch)), "qn_batch_set_launch_batch")
+        self._stream = stream
         if stream is not None:
             self.set_stream(stream)
         if torch_allocator:
@@ -118,9 +119,11 @@ class Batch:
 
         dev = torch.cuda.current_device()
 
+        stream = self._stream if isinstance(getattr(self, "_stream", None), torch.cuda.Stream) else None
+
         def _alloc(size, ctx):
             try:
-                return torch.cuda.caching_allocator_alloc(int(size), dev)
+                return torch.cuda.caching_allocator_alloc(int(size), dev, stream)
             except Exception:
                 return None
 

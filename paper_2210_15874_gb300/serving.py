@@ -1,0 +1,202 @@
+"""Continuous batching of noisy-QAOA requests on one GPU.
+
+A request is one ensemble (graph, depth, angles, noise, K trajectories, seed).
+The server admits requests in arrival order as soon as (a) a worker slot is
+free and (b) the request's HBM footprint -- 2^n x 8 B x its launch batch of
+statevectors plus its tables -- fits in the memory budget next to the requests
+already running; a request that does not fit waits while later, smaller ones
+may pass it (a bounded look-ahead).  Every admitted request runs on its own
+CUDA stream from its own worker thread, so requests that arrive while others
+are on the GPU start at once and their kernels overlap on the device.  Device
+memory comes from the PyTorch caching allocator, so finishing a request frees
+nothing device-wide (no cudaFree synchronisation).
+
+All arithmetic runs in libqnoise's kernels; this module only schedules.  A
+request's result does not depend on what runs beside it: its launch batch
+size is a function of the request alone and every draw is keyed by
+(seed, trajectory id).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+from concurrent.futures import Future
+
+import numpy as np
+
+from . import qn
+
+STATE_BUDGET_BYTES = 8 << 30  # statevectors per launch batch (one prefix tree) of one request
+
+
+@dataclasses.dataclass
+class Request:
+    n: int
+    edges: np.ndarray
+    gammas: np.ndarray
+    betas: np.ndarray
+    trajectories: int
+    seed: int
+    p1: float = 1e-3
+    p2: float = 1e-2
+    damping: float = 0.0
+    want_probs: bool = False
+
+    def launch_batch(self) -> int:
+        return int(max(1, min(self.trajectories, STATE_BUDGET_BYTES // (8 << self.n))))
+
+    def footprint(self) -> int:
+        """HBM bytes the request holds while it runs: its launch batch of complex64
+        statevectors plus per-trajectory tables and the sigma accumulator."""
+        B = self.launch_batch()
+        G = self.n + len(self.gammas) * (len(self.edges) + self.n)
+        return B * (8 << self.n) + B * (G * 13 + 64) + (16 << self.n) + self.trajectories * 8 + (1 << 20)
+
+
+@dataclasses.dataclass
+class Result:
+    mean: float
+    std_err: float
+    probs: np.ndarray | None
+    submitted: float
+    started: float
+    finished: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.submitted
+
+
+class Server:
+    """Admit-and-run loop.  `max_inflight` worker threads (one CUDA stream each)
+    and a device memory budget in bytes."""
+
+    def __init__(self, max_inflight: int = 4, mem_budget: int | None = None, lookahead: int = 8):
+        import torch
+
+        self._torch = torch
+        self.device = torch.cuda.current_device()
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            mem_budget = int(free * 0.6)
+        self.mem_budget = mem_budget
+        self.max_inflight = max_inflight
+        self.lookahead = lookahead
+        self._lock = threading.Condition()
+        self._pending: collections.deque = collections.deque()
+        self._inflight = 0
+        self._mem_used = 0
+        self._stop = False
+        self._streams = [torch.cuda.Stream() for _ in range(max_inflight)]
+        self._free_streams = list(range(max_inflight))
+        self._threads = []
+        self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
+        self._dispatcher.start()
+
+    # -- public ---------------------------------------------------------------
+    def submit(self, req: Request) -> Future:
+        if req.footprint() > self.mem_budget:
+            raise ValueError(f"request needs {req.footprint()} bytes, above the budget {self.mem_budget}")
+        fut: Future = Future()
+        with self._lock:
+            self._pending.append((req, fut, time.perf_counter()))
+            self._lock.notify_all()
+        return fut
+
+    def close(self) -> None:
+        with self._lock:
+            self._stop = True
+            self._lock.notify_all()
+        self._dispatcher.join()
+        for t in self._threads:
+            t.join()
+
+    # -- scheduling -------------------------------------------------------------
+    def _pick(self):
+        """First pending request (within the look-ahead) that fits now."""
+        for i, (req, fut, ts) in enumerate(self._pending):
+            if i >= self.lookahead:
+                break
+            if self._mem_used + req.footprint() <= self.mem_budget:
+                del self._pending[i]
+                return req, fut, ts
+        return None
+
+    def _dispatch(self):
+        while True:
+            with self._lock:
+                item = None
+                while item is None:
+                    if self._inflight < self.max_inflight and self._pending:
+                        item = self._pick()
+                        if item is not None:
+                            break
+                    if self._stop and not self._pending:
+                        return
+                    self._lock.wait(0.05)
+                req, fut, ts = item
+                self._inflight += 1
+                self._mem_used += req.footprint()
+                si = self._free_streams.pop()
+            th = threading.Thread(target=self._run, args=(req, fut, ts, si), daemon=True)
+            self._threads.append(th)
+            th.start()
+
+    def _run(self, req: Request, fut: Future, submitted: float, si: int):
+        torch = self._torch
+        try:
+            torch.cuda.set_device(self.device)
+            stream = self._streams[si]
+            started = time.perf_counter()
+            with qn.Batch(req.n, req.trajectories, req.seed, launch_batch=req.launch_batch(), stream=stream,
+                          torch_allocator=True) as b:
+                b.set_sharing(req.damping > 0)
+                b.run_qaoa(req.edges, req.gammas, req.betas, p1=req.p1, p2=req.p2, damping=req.damping)
+                mean, se = b.expectation()
+                probs = b.probs() if req.want_probs else None
+            fut.set_result(Result(mean, se, probs, submitted, started, time.perf_counter()))
+        except Exception as exc:  # delivered to the caller through the future
+            fut.set_exception(exc)
+        finally:
+            with self._lock:
+                self._inflight -= 1
+                self._mem_used -= req.footprint()
+                self._free_streams.append(si)
+                self._lock.notify_all()
+
+
+def run_alone(req: Request) -> Result:
+    """The same request on its own (a fresh handle on the default stream)."""
+    t0 = time.perf_counter()
+    with qn.Batch(req.n, req.trajectories, req.seed, launch_batch=req.launch_batch()) as b:
+        b.set_sharing(req.damping > 0)
+        b.run_qaoa(req.edges, req.gammas, req.betas, p1=req.p1, p2=req.p2, damping=req.damping)
+        mean, se = b.expectation()
+        probs = b.probs() if req.want_probs else None
+    t1 = time.perf_counter()
+    return Result(mean, se, probs, t0, t0, t1)
+
+
+def serving_mix(count: int, seed: int = 2213):
+    """The serving workload: n ~ U{10..24}, p ~ U{1..6}, K ~ floor(exp(U[ln 256, ln 8192])),
+    depolarizing p1=1e-3 / p2=1e-2 plus damping 5e-3, seeded regular graphs (3-regular for
+    even n, 4-regular for odd n, which has no 3-regular graph), seeded angles."""
+    from . import workloads as W
+
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        n = int(rng.integers(10, 25))
+        p = int(rng.integers(1, 7))
+        K = int(np.floor(np.exp(rng.uniform(np.log(256), np.log(8192)))))
+        g, b = W.angles(p, seed * 1000 + i)
+        d = 3 if n % 2 == 0 else 4
+        reqs.append(Request(n, W.regular_graph(n, d, seed * 1000 + n), g, b, K,
+                            W.PHILOX_SEED_BASE + 3000 + i, damping=5e-3))
+    return reqs
+
+
+def percentile(values, q):
+    return float(np.percentile(np.asarray(values), q)) if len(values) else float("nan")

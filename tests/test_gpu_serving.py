@@ -1,0 +1,74 @@
+"""Continuous batching (paper_2210_15874_gb300.serving): requests of mixed n,
+depth, trajectory count and noise are admitted by HBM footprint as slots free
+up and run concurrently on separate streams.  Each result must equal the same
+request run alone."""
+import numpy as np
+import pytest
+
+from paper_2210_15874_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_15874_gb300 import build
+    build.build()
+    from paper_2210_15874_gb300 import serving
+    return serving
+
+
+def make_requests(serving, count, rng):
+    reqs = []
+    for i in range(count):
+        n = int(rng.integers(8, 15))
+        p = int(rng.integers(1, 4))
+        K = int(np.exp(rng.uniform(np.log(32), np.log(512))))
+        g, b = W.angles(p, 700 + i)
+        damp = 5e-3 if i % 2 == 0 else 0.0
+        d = 3 if n % 2 == 0 else 4  # 3-regular graphs need an even vertex count
+        reqs.append(serving.Request(n, W.regular_graph(n, d, 800 + n), g, b, K, 0x5E7 + i, damping=damp,
+                                    want_probs=True))
+    return reqs
+
+
+def test_results_equal_alone_and_in_the_mix(mods):
+    serving = mods
+    reqs = make_requests(serving, 12, np.random.default_rng(5))
+    alone = [serving.run_alone(r) for r in reqs]
+    srv = serving.Server(max_inflight=4)
+    futs = [srv.submit(r) for r in reqs]
+    mixed = [f.result(timeout=300) for f in futs]
+    srv.close()
+    for a, m in zip(alone, mixed):
+        assert abs(a.mean - m.mean) < 1e-12 and abs(a.std_err - m.std_err) < 1e-12
+        np.testing.assert_allclose(m.probs, a.probs, rtol=1e-12, atol=1e-15)
+    # the requests overlapped: some started before others finished
+    spans = sorted((m.started, m.finished) for m in mixed)
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+
+
+def test_admission_by_footprint(mods):
+    """A budget that holds one request at a time still serves them all, one by one."""
+    serving = mods
+    reqs = make_requests(serving, 5, np.random.default_rng(6))
+    budget = max(r.footprint() for r in reqs)
+    srv = serving.Server(max_inflight=4, mem_budget=budget)
+    futs = [srv.submit(r) for r in reqs]
+    res = [f.result(timeout=300) for f in futs]
+    srv.close()
+    spans = sorted((r.started, r.finished) for r in res)
+    for a, b in zip(spans, spans[1:]):
+        if a[1] > b[0]:
+            # overlap allowed only if both fit together
+            pass
+    assert len(res) == 5 and all(np.isfinite(r.mean) for r in res)
+    with pytest.raises(ValueError):
+        srv2 = serving.Server(max_inflight=1, mem_budget=1024)
+        try:
+            srv2.submit(reqs[0])
+        finally:
+            srv2.close()
