@@ -206,7 +206,7 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
     torch.cuda.synchronize()
     mean, se = b.expectation()
     b.set_profiling(PROFILE_PERIOD)
-    for k in range(3):
+    for k in range(4):
         b.profile_read(k)
     if pg:
         pg.barrier()
@@ -231,7 +231,8 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
         pg.barrier()
     res = dict(ms=ms, value=w.trajectories * args.steps * world / (ms / 1e3), mean=mean, se=se,
                launches=launches, sweep_bytes_per_step=sweep_bytes / args.steps, states_per_step=states / args.steps,
-               sweeps=b.profile_read(0), inits=b.profile_read(1), accs=b.profile_read(2), clocks=clocks.summary())
+               sweeps=b.profile_read(0), inits=b.profile_read(1), accs=b.profile_read(2),
+               groups=b.profile_read(3), clocks=clocks.summary())
     b.set_profiling(0)
     if with_e2e:
         # end to end through the C ABI from host buffers: run + <C> + sigma to host
@@ -296,8 +297,8 @@ def gpu_arm(args):
         d2h += K * (n + 32 + 4 + 8 * n) + 4 * (G - n) + 4 + K * 12
         h2d += K * (4 + 8 + 32 + 8 * n + 12) + 16
 
-    def roof(res, kernel):
-        sw = res["sweeps"]
+    def roof(res, kernel, family="sweeps"):
+        sw = res[family]
         avg_ms = sw["ms"] / max(sw["launches"], 1)
         achieved = (sw["bytes"] / max(sw["launches"], 1)) / (avg_ms / 1e3) / 1e9 if avg_ms > 0 else 0.0
         traffic = None
@@ -319,7 +320,9 @@ def gpu_arm(args):
 
     if rank == 0:
         fused = main_mode[1] and w.damping == 0
-        kname = "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
+        grouped = sharing and main_mode[1] and main["groups"]["launches"] > 0
+        kname = "k_slot_sweep (mixer gate sweeps over live prefix states)" if grouped else \
+            "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
             ("k_fused_sweep (fused layer sweeps, 16 B per amplitude)" if fused else
              "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")
         line = {
@@ -329,7 +332,9 @@ def gpu_arm(args):
             "config": config_of(w, {
                 "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
                 "mode": ("shared-prefix: one statevector per distinct Kraus prefix, all trajectories in one "
-                         "prefix tree") if sharing else
+                         "prefix tree" + ("; phase gates applied in groups on <= 8 qubits (one joint pass per "
+                                          "layer, one sweep per group), mixer gates one sweep each" if grouped
+                                          else "; one sweep per gate")) if sharing else
                         (f"fused layers: ceil(n/3) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused
                          else f"one statevector per trajectory, one sweep per gate, {w.batch} per launch")}),
             "amp_updates_per_s": main["value"] * G * (1 << n),
@@ -337,12 +342,16 @@ def gpu_arm(args):
             "sweep_bytes_per_step": main["sweep_bytes_per_step"],
             "c_mean": main["mean"], "c_stderr": main["se"],
             "roofline": roof(main, kname),
-            "kernels": {"gate sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["sweeps"], "k_init": main["inits"],
-                        "k_observe+k_probs": main["accs"]},
+            "kernels": {"gate sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["sweeps"],
+                        "phase-group sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["groups"],
+                        "k_init": main["inits"], "k_observe+k_probs": main["accs"]},
             "e2e": {"value": main["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": main["launches"],
             "clocks": main["clocks"],
         }
+        if grouped:
+            line["roofline_phase_groups"] = roof(main, "k_group_apply + k_group_hist (phase-group sweeps, 16 B and "
+                                                       "8 B per amplitude)", "groups")
         if other is not None:
             key = "per_trajectory_mode" if sharing else "per_gate_mode"
             line[key] = {

@@ -114,16 +114,22 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
  * applied as ceil(n / 3) sweeps instead of E + n: the cost layer (every phase
  * gate and every Pauli's Z part) is one diagonal factor folded into a mixer
  * sweep, and the mixer rotations are applied three qubits per sweep.  Needs
- * at most 64 edges; otherwise, or with damping, gates are swept one by one.
- * With damping == 0 fusion takes precedence over shared-prefix mode. */
+ * at most 64 edges; otherwise gates are swept one by one.  With damping == 0
+ * fusion takes precedence over shared-prefix mode.  With damping, fusion acts
+ * in shared-prefix mode only: consecutive phase gates of a layer on at most 8
+ * qubits form a group whose damping branches are all drawn from one joint
+ * distribution of those qubits, and the group is applied in one sweep (the
+ * same Kraus draws as gate by gate; the state differs by FP32 rounding).
+ * Without shared-prefix mode damping runs are swept gate by gate. */
 qn_status qn_batch_set_fusion(qn_batch *h, int32_t on);
 
 /* Shared-prefix mode (on = 1; default 0).  Trajectories whose Kraus strings
  * agree so far share one statevector; when a trajectory's own Pauli or damping
  * draw differs from the shared branch it forks into a copy.  Every trajectory
- * sees exactly the state and the draws it would see alone, so results equal
- * the default mode's up to FP summation order; only the work on common
- * prefixes is done once.  A launch batch then holds up to B distinct states
+ * sees exactly the draws it would see alone; with fusion off results equal the
+ * default mode's up to FP summation order, with fusion on (phase-gate groups,
+ * see qn_batch_set_fusion) up to FP32 rounding of the states.  Only the work on
+ * common prefixes is done once.  A launch batch then holds up to B distinct states
  * (default B: a quarter of the free device memory, capped by trajectories).
  * qn_traj_debug and qn_grad are unaffected (they re-simulate trajectories one by
  * one). */
@@ -195,8 +201,10 @@ qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, doub
 qn_status qn_batch_set_profiling(qn_batch *h, int32_t period);
 
 /* Totals since the last read, for kernel family `kind` (0 = gate sweeps, 1 =
- * state init, 2 = ensemble accumulation): launches, summed event milliseconds
- * and algorithmic bytes.  Synchronises the stream, then resets the totals. */
+ * state init, 2 = ensemble accumulation, 3 = phase-group sweeps of
+ * shared-prefix mode: joint passes and apply sweeps): launches, summed event
+ * milliseconds and algorithmic bytes.  Kinds 0 and 3 share one sampling
+ * counter.  Synchronises the stream, then resets the totals. */
 qn_status qn_profile_read(qn_batch *h, int32_t kind, int64_t *launches, double *ms, double *bytes);
 
 /* Allocation-free variant of qn_run_qaoa for one batch (no counterpart in the

@@ -145,6 +145,17 @@ struct qn_batch {
     double *sh_marg = nullptr;
     int64_t sh_cap = 0;
     int64_t sh_slots = 0;  // slots of the last shared-prefix run (all chunks)
+    // phase-gate groups of shared-prefix mode with damping
+    std::vector<ZZGroup> groups;
+    std::vector<int32_t> group_at;  // [G] index of the group that starts at gate g, or -1
+    ZZGroup *gr_dev = nullptr;
+    int64_t gr_cap = 0;
+    unsigned long long *gv_H = nullptr;  // [2][gv_cap][256]
+    float2 *gv_T = nullptr;
+    TrajState *gv_stprev = nullptr;
+    uint64_t *gv_ekey = nullptr;
+    int32_t *gv_i32 = nullptr;  // [5][gv_cap]: evt, rep, lead, lstart, lcount
+    int64_t gv_cap = 0;
     float2 *lambda = nullptr;  // adjoint vectors (qn_grad), allocated on first use
     double *grad = nullptr;    // [K][2p] per-trajectory gradients
     int32_t grad_cap = 0;      // 2p the grad buffer was sized for
@@ -155,9 +166,9 @@ struct qn_batch {
     int64_t prof_counter = 0;
     std::vector<EventPair> events;
     std::vector<EventPair> spare;
-    int64_t prof_launches[3] = {0, 0, 0};
-    double prof_ms[3] = {0, 0, 0};
-    double prof_bytes[3] = {0, 0, 0};
+    int64_t prof_launches[4] = {0, 0, 0, 0};
+    double prof_ms[4] = {0, 0, 0, 0};
+    double prof_bytes[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -205,6 +216,14 @@ void release_all(qn_batch *h) {
     h->sh_weights = nullptr;
     h->sh_marg = nullptr;
     h->sh_cap = 0;
+    h->gr_dev = nullptr;
+    h->gr_cap = 0;
+    h->gv_H = nullptr;
+    h->gv_T = nullptr;
+    h->gv_stprev = nullptr;
+    h->gv_ekey = nullptr;
+    h->gv_i32 = nullptr;
+    h->gv_cap = 0;
     h->fl_ev = nullptr;
     h->fl_phase = nullptr;
     h->fl_edges = nullptr;
@@ -357,6 +376,58 @@ void build_gates(qn_batch *h) {
     for (int e = 0; e < E; ++e) h->edges_host.push_back(make_int2(h->edges[2 * e], h->edges[2 * e + 1]));
 }
 
+// Phase-gate groups of every layer: greedy runs of consecutive ZZ gates whose
+// qubits number at most 8 (at most kMaxGroupEdges gates, so that a member's
+// outcome string fits 6 bits per gate in 64 bits).
+void build_groups(qn_batch *h) {
+    const int n = h->n, E = (int)h->edges.size() / 2;
+    h->groups.clear();
+    h->group_at.assign(h->gates.size(), -1);
+    for (int l = 0; l < h->p; ++l) {
+        const int base = n + l * (E + n);
+        int g = base;
+        while (g < base + E) {
+            ZZGroup z;
+            std::memset(&z, 0, sizeof z);
+            z.g0 = g;
+            uint32_t S = 0;
+            while (g < base + E && z.m < kMaxGroupEdges) {
+                const uint32_t S2 = S | (1u << h->gates[g].q0) | (1u << h->gates[g].q1);
+                if (__builtin_popcount(S2) > 8) break;
+                S = S2;
+                ++z.m;
+                ++g;
+            }
+            int local[32];
+            z.s = 0;
+            for (int q = 0; q < n; ++q)
+                if ((S >> q) & 1u) {
+                    local[q] = z.s;
+                    z.sp[z.s++] = q;
+                }
+            for (int e = 0; e < z.m; ++e) {
+                z.ei[e] = local[h->gates[z.g0 + e].q0];
+                z.ej[e] = local[h->gates[z.g0 + e].q1];
+            }
+            z.c = h->dgates_host[z.g0].c;
+            z.sn = h->dgates_host[z.g0].s;
+            for (int byte = 0; byte < 4; ++byte)
+                for (int v = 0; v < 256; ++v) {
+                    int bins = 0;
+                    for (int bit = 0; bit < 8; ++bit) {
+                        const int q = 8 * byte + bit;
+                        if (((v >> bit) & 1) && q < n && ((S >> q) & 1u)) bins |= 1 << local[q];
+                    }
+                    z.tab[byte][v] = (uint8_t)bins;
+                }
+            h->group_at[z.g0] = (int32_t)h->groups.size();
+            h->groups.push_back(z);
+        }
+    }
+}
+
+bool use_groups(const qn_batch *h) { return h->fusion && h->damping_on && !h->groups.empty(); }
+
 BatchView view_for(qn_batch *h, int64_t t0, int b) {
     BatchView v;
     v.psi = h->psi;
@@ -384,7 +455,7 @@ qn_status check_status(const qn_batch *h);
 // ---- profiling: one CUDA event pair per timed launch ----
 bool prof_sampled(qn_batch *h, int kind) {
     if (h->prof_period <= 0) return false;
-    if (kind != 0) return true;
+    if (kind != 0 && kind != 3) return true;
     return (h->prof_counter++ % h->prof_period) == 0;
 }
 
@@ -584,6 +655,25 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
         QN_TRY(alloc_t(h, &h->sh_marg, (size_t)kc * 4));
         h->sh_cap = kc;
     }
+    const bool grouped = use_groups(h);
+    if (grouped && h->gv_cap < kc) {
+        QN_TRY(alloc_t(h, &h->gv_H, (size_t)2 * kc * kGroupBins));
+        QN_TRY(alloc_t(h, &h->gv_T, (size_t)kc * kGroupBins));
+        QN_TRY(alloc_t(h, &h->gv_stprev, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->gv_ekey, (size_t)kc));
+        QN_TRY(alloc_t(h, &h->gv_i32, (size_t)5 * kc));
+        h->gv_cap = kc;
+    }
+    if (grouped && h->gr_cap < (int64_t)h->groups.size()) {
+        QN_TRY(alloc_t(h, &h->gr_dev, h->groups.size()));
+        h->gr_cap = (int64_t)h->groups.size();
+    }
+    if (grouped) {
+        QN_CUDA(cudaMemcpyAsync(h->gr_dev, h->groups.data(), h->groups.size() * sizeof(ZZGroup),
+                                cudaMemcpyHostToDevice, h->stream));
+        QN_CUDA(cudaMemsetAsync(h->gv_H, 0, sizeof(unsigned long long) * 2 * (size_t)h->gv_cap * kGroupBins,
+                                h->stream));
+    }
     BatchView v = view_for(h, h->offset + t0, kc);
     QN_CUDA(launch_prepare(v, h->dgates, h->seed, h->nz, h->damping_on, h->stream));
     h->launches += 1;
@@ -664,7 +754,51 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     int32_t active_word = ns;
     int32_t *active_host = &active_word;
     int active = ns;
+    const double amp_count = (double)((size_t)1 << n);
     for (int g = n; g < G; ++g) {
+        const int gi = grouped ? h->group_at[g] : -1;
+        if (gi >= 0) {
+            // a group of phase gates: (joint pass,) decide + forks, one apply sweep
+            const ZZGroup &z = h->groups[gi];
+            const int ng = (int)h->groups.size();
+            const bool first = gi == 0 || h->groups[gi - 1].g0 + h->groups[gi - 1].m != z.g0;
+            const bool has_next = gi + 1 < ng && h->groups[gi + 1].g0 == z.g0 + z.m;
+            GroupView gv;
+            gv.grp = h->gr_dev + gi;
+            gv.next = has_next ? h->gr_dev + gi + 1 : nullptr;
+            gv.Hcur = h->gv_H + (size_t)(gi & 1) * h->gv_cap * kGroupBins;
+            gv.Hnext = h->gv_H + (size_t)((gi + 1) & 1) * h->gv_cap * kGroupBins;
+            gv.T = h->gv_T;
+            gv.st_prev = h->gv_stprev;
+            gv.ekey = h->gv_ekey;
+            gv.evt = h->gv_i32;
+            gv.rep = h->gv_i32 + h->gv_cap;
+            gv.lead = h->gv_i32 + 2 * h->gv_cap;
+            gv.lstart = h->gv_i32 + 3 * h->gv_cap;
+            gv.lcount = h->gv_i32 + 4 * h->gv_cap;
+            cudaError_t e = cudaSuccess;
+            if (first) {
+                QN_TRY(prof_begin(h, &ep, 3, (double)active * 8.0 * amp_count));
+                e = launch_group_hist(v, sv, gv, active, h->stream);
+                if (e == cudaSuccess) QN_TRY(prof_end(h, &ep));
+                h->sweep_bytes += (double)active * 8.0 * amp_count;
+                h->launches += 1;
+            }
+            if (e == cudaSuccess) e = launch_group_decide(v, sv, gv, active, h->nz.gamma, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(active_host, sv.active, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                                      h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
+            active = *active_host;
+            QN_TRY(prof_begin(h, &ep, 3, (double)active * 16.0 * amp_count));
+            e = launch_group_apply(v, sv, gv, active, h->stream);
+            if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
+            QN_TRY(prof_end(h, &ep));
+            h->sweep_bytes += (double)active * 16.0 * amp_count;
+            h->launches += 4;
+            g += z.m - 1;
+            continue;
+        }
         QN_TRY(prof_begin(h, &ep, 0, (double)active * 16.0 * (double)((size_t)1 << n)));
         cudaError_t e = launch_slot_sweep(v, sv, active, g, h->dgates_host[g], h->damping_on, h->stream);
         if (e == cudaSuccess) {
@@ -850,6 +984,7 @@ qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const doubl
     h->betas.assign(betas, betas + p);
     h->noise = *noise;
     build_gates(h);
+    build_groups(h);
     double pr1[4], pr2[16];
     probs_1q(*noise, pr1);
     probs_2q(*noise, pr2);
@@ -1083,7 +1218,7 @@ qn_status qn_batch_set_profiling(qn_batch *h, int32_t period) {
 
 qn_status qn_profile_read(qn_batch *h, int32_t kind, int64_t *launches, double *ms, double *bytes) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
-    if (kind < 0 || kind > 2) return fail(QN_EINVAL, "kind must be 0, 1 or 2");
+    if (kind < 0 || kind > 3) return fail(QN_EINVAL, "kind must be 0, 1, 2 or 3");
     QN_TRY(prof_collect(h));
     if (launches) *launches = h->prof_launches[kind];
     if (ms) *ms = h->prof_ms[kind];

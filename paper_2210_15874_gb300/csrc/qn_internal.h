@@ -70,6 +70,40 @@ struct SlotView {
     int32_t max_slots;
 };
 
+// Consecutive phase gates of one layer whose qubits S number at most 8 (shared-
+// prefix mode with damping): their damping branches follow from the joint
+// distribution of the true bits of S, because every op of the group is
+// diagonal (phases, Z parts, K0) or a relabelling (X parts, K1) in the stored
+// basis.
+constexpr int kMaxGroupEdges = 10;
+constexpr int kGroupBins = 256;
+
+struct ZZGroup {
+    int32_t g0, m, s;               // first gate, gates, qubits in S
+    int32_t sp[8];                  // qubits of S, ascending
+    int32_t ei[kMaxGroupEdges];     // S index of each gate's first qubit
+    int32_t ej[kMaxGroupEdges];     // S index of each gate's second qubit
+    float c, sn;                    // cos gamma, sin gamma of the layer
+    uint8_t tab[4][256];            // index over S of the stored bits in each byte of y
+};
+
+// Device view of one group step.  Per-slot arrays are indexed by slot; the
+// per-member scratch arrays by the position of the member in SlotView::members.
+struct GroupView {
+    const ZZGroup *grp;    // group applied by this step
+    const ZZGroup *next;   // group whose joint the apply sweep accumulates, or nullptr
+    unsigned long long *Hcur;   // [max_slots][256] joint of this group, fixed point 2^-60
+    unsigned long long *Hnext;  // [max_slots][256] joint of the next group (zero on entry)
+    float2 *T;             // [max_slots][256] amplitude factor by stored bits of S
+    TrajState *st_prev;    // [max_slots] pending op of the gate before the group
+    uint64_t *ekey;        // [K] outcome string of the k-th event member of a slot
+    int32_t *evt;          // [K] member index (within the slot) of the k-th event member
+    int32_t *rep;          // [K] first event of a slot with the same outcome string
+    int32_t *lead;         // [K] events that open a class, in event order
+    int32_t *lstart;       // [K] first position of each opened class
+    int32_t *lcount;       // [K] members of each opened class
+};
+
 // One QAOA layer for the fused (Pauli-only) sweeps.
 struct LayerView {
     const uint64_t *ev;      // [4][256] edge-difference vectors by byte of y (bit e: endpoints of edge e differ)
@@ -142,6 +176,13 @@ cudaError_t launch_slot_sweep(const BatchView &v, const SlotView &sv, int active
                               int damping_on, cudaStream_t s);
 cudaError_t launch_slot_fork(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
                              const NoiseDev &nz, int damping_on, cudaStream_t s);
+// Shared-prefix mode, phase-gate groups: joint of the first group (read pass),
+// per-slot decisions and forks of a group, and the apply sweep (which also
+// accumulates the next group's joint).
+cudaError_t launch_group_hist(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
+cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, double gamma,
+                                cudaStream_t s);
+cudaError_t launch_group_apply(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
 // Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n
 // adding d<C>_t / d theta_param into grad[t * nparam + param] (FP64).
 cudaError_t launch_adj_init(const BatchView &v, float2 *lam, const AccumView &a, cudaStream_t s);

@@ -779,6 +779,511 @@ __global__ void __launch_bounds__(kThreads) k_slot_decide(BatchView v, SlotView 
     allow_dependent_launch();
 }
 
+// ---------------------------------------------------------------------------
+// Phase-gate groups in shared-prefix mode.  A group is a run of consecutive
+// phase gates of one layer on a qubit set S of at most 8 qubits.  Every op of
+// the group -- phase, Z part of a Pauli, K0 -- is diagonal in the stored basis,
+// and every X part or K1 jump only relabels true bits, so the branch of every
+// damping site in the group follows from the joint distribution of the true
+// bits of S when the group starts.  k_group_decide draws all members' branches
+// from that joint in FP64 (the same draws, conditioned the same way, as one
+// gate at a time), forks every outcome string other than the shared one and
+// writes per slot a table T of 2^|S| amplitude factors; k_group_apply multiplies
+// the state by T in one sweep and accumulates the next group's joint on the
+// way.  Joints are summed in warp-private shared histograms in a fixed order
+// and added across blocks as 2^-60 fixed-point integers, so they do not depend
+// on the order in which blocks run.
+// ---------------------------------------------------------------------------
+constexpr double kHistScale = 1152921504606846976.0;  // 2^60
+constexpr double kHistUnit = 1.0 / kHistScale;
+static_assert(kThreads == 256 && kTileF4 == 1024 && kF4PerThread == 4 && kSub == 4,
+              "group bins assume y = e | tid << 1 | k << 9 | sub << 11 | tile << 13");
+
+__device__ __forceinline__ int group_bin(const ZZGroup *gp, uint32_t y) {
+    return gp->tab[0][y & 255u] | gp->tab[1][(y >> 8) & 255u] | gp->tab[2][(y >> 16) & 255u] | gp->tab[3][y >> 24];
+}
+
+// Bins of one sweep block split into a per-thread part (tid and tile bits) and
+// a part that depends only on the unrolled loop indices (e, k, sub), kept in
+// the shared table vtab[e | k << 1 | sub << 3].
+struct GroupBins {
+    int base;        // bins of this thread's tid and tile bits
+    unsigned lmask;  // lane bits that are no qubit of S
+};
+
+__device__ __forceinline__ GroupBins group_bins(const ZZGroup *gp, int tile, unsigned char *vtab) {
+    GroupBins gb;
+    gb.base = group_bin(gp, ((uint32_t)threadIdx.x << 1) | ((uint32_t)tile << 13));
+    unsigned lm = 0;
+    for (int i = 0; i < 5; ++i)
+        if (group_bin(gp, 2u << i) == 0) lm |= 1u << i;
+    gb.lmask = lm;
+    if (threadIdx.x < 32) {
+        const uint32_t j = threadIdx.x;
+        vtab[j] = (unsigned char)group_bin(gp, (j & 1u) | (((j >> 1) & 3u) << 9) | (((j >> 3) & 3u) << 11));
+    }
+    return gb;
+}
+
+// Add x, summed over the lanes that differ only outside S, to the warp's
+// histogram (lanes left after the butterfly hold distinct bins).
+__device__ __forceinline__ void hist_flush(float *hw, float x, int bin, unsigned lmask) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        if ((lmask >> i) & 1u) x += __shfl_xor_sync(0xffffffffu, x, 1 << i);
+    if (((threadIdx.x & 31u) & lmask) == 0u) hw[bin] += x;
+    __syncwarp();
+}
+
+// Run of consecutive (e = 0, e = 1) probabilities with the same loop-index bin
+// `ks`; flushed when ks changes (ks is warp-uniform).  e1 = bin bits of y bit 0.
+struct HistRun {
+    float r0 = 0.0f, r1 = 0.0f;
+    int ks = -1;
+};
+
+__device__ __forceinline__ void hist_close(float *hw, const GroupBins &gb, int e1, const HistRun &run) {
+    if (run.ks < 0) return;
+    if (e1) {
+        hist_flush(hw, run.r0, gb.base | run.ks, gb.lmask);
+        hist_flush(hw, run.r1, gb.base | run.ks | e1, gb.lmask);
+    } else {
+        hist_flush(hw, run.r0 + run.r1, gb.base | run.ks, gb.lmask);
+    }
+}
+
+__device__ __forceinline__ void hist_push(float *hw, const GroupBins &gb, int e1, int ks, float p0, float p1,
+                                          HistRun &run) {
+    if (ks != run.ks) {
+        hist_close(hw, gb, e1, run);
+        run.ks = ks;
+        run.r0 = p0;
+        run.r1 = p1;
+    } else {
+        run.r0 += p0;
+        run.r1 += p1;
+    }
+}
+
+// Block histogram -> the slot's global joint (fixed-point integer adds).
+__device__ __forceinline__ void hist_commit(const float *hw, int nb, unsigned long long *H) {
+    for (int b = threadIdx.x; b < nb; b += kThreads) {
+        double acc = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) acc += (double)hw[w * kGroupBins + b];
+        if (acc > 0.0) atomicAdd(H + b, __double2ull_rn(acc * kHistScale));
+    }
+}
+
+__device__ __forceinline__ SweepCtx pending_ctx(const TrajState &s) {
+    SweepCtx c;
+    c.code = 0;
+    c.Fa = s.J;
+    c.Fb = c.Fc = s.J ^ s.pend;
+    c.pq0 = s.pq0;
+    c.pq1 = s.pq1;
+    for (int k = 0; k < 4; ++k) c.f[k] = s.f[k];
+    return c;
+}
+
+// Joint of the first group of a layer: a read-only pass that applies the
+// pending op of the gate before on the fly.  Grid (sweep tiles, live slots).
+__global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupView gv) {
+    grid_dependency_wait();
+    const int slot = blockIdx.y, tile = blockIdx.x;
+    const ZZGroup *gp = gv.grp;
+    __shared__ float hw[kThreads / 32][kGroupBins];
+    __shared__ unsigned char vtab[32];
+    for (int i = threadIdx.x; i < (kThreads / 32) * kGroupBins; i += kThreads) (&hw[0][0])[i] = 0.0f;
+    const GroupBins gb = group_bins(gp, tile, vtab);
+    __syncthreads();
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1);
+    const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)slot << n));
+    const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
+    const SweepCtx c = pending_ctx(v.st[slot]);
+    float *my = hw[threadIdx.x >> 5];
+    const int e1 = vtab[1];
+    HistRun run;
+    float4 cur[kF4PerThread], nxt[kF4PerThread];
+    load_tile(cur, p4, fbase, nf);
+#pragma unroll
+    for (int sub = 0; sub < kSub; ++sub) {
+        const int64_t f0 = fbase + (int64_t)sub * kTileF4;
+        if (sub + 1 < kSub) load_tile(nxt, p4, f0 + kTileF4, nf);
+#pragma unroll
+        for (int k = 0; k < kF4PerThread; ++k) {
+            const int64_t f = f0 + k * kThreads;
+            float p0 = 0.0f, p1 = 0.0f;
+            if (f < nf) {
+                const uint32_t y = (uint32_t)(2 * f);
+                const float fa0 = pend_factor(c, y), fa1 = pend_factor(c, y | 1u);
+                p0 = fa0 * fa0 * (cur[k].x * cur[k].x + cur[k].y * cur[k].y);
+                p1 = fa1 * fa1 * (cur[k].z * cur[k].z + cur[k].w * cur[k].w);
+            }
+            hist_push(my, gb, e1, vtab[(k << 1) | (sub << 3)], p0, p1, run);
+        }
+        if (sub + 1 < kSub) {
+#pragma unroll
+            for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
+        }
+    }
+    hist_close(my, gb, e1, run);
+    __syncthreads();
+    allow_dependent_launch();
+    hist_commit(&hw[0][0], 1 << gp->s, gv.Hcur + (size_t)slot * kGroupBins);
+}
+
+// Apply a group: phi_y *= D(y) * T[slot][stored bits of S], D the pending op of
+// the gate before the group; accumulate the next group's joint if there is one.
+__global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupView gv) {
+    grid_dependency_wait();
+    const int slot = blockIdx.y, tile = blockIdx.x;
+    const ZZGroup *gp = gv.grp;
+    const ZZGroup *nx = gv.next;
+    __shared__ float2 Ts[kGroupBins];
+    __shared__ float hw[kThreads / 32][kGroupBins];
+    __shared__ unsigned char vT[32], vN[32];
+    for (int i = threadIdx.x; i < (1 << gp->s); i += kThreads) Ts[i] = gv.T[(size_t)slot * kGroupBins + i];
+    const GroupBins gt = group_bins(gp, tile, vT);
+    GroupBins gn{0, 0u};
+    if (nx) {
+        for (int i = threadIdx.x; i < (kThreads / 32) * kGroupBins; i += kThreads) (&hw[0][0])[i] = 0.0f;
+        gn = group_bins(nx, tile, vN);
+    }
+    __syncthreads();
+    const int n = v.n;
+    const int64_t nf = (int64_t)1 << (n - 1);
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << n));
+    const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
+    const SweepCtx c = pending_ctx(gv.st_prev[slot]);
+    float *my = hw[threadIdx.x >> 5];
+    const int tE1 = vT[1];
+    const int nE1 = nx ? vN[1] : 0;
+    HistRun run;
+    float4 cur[kF4PerThread], nxt[kF4PerThread];
+    load_tile(cur, p4, fbase, nf);
+#pragma unroll
+    for (int sub = 0; sub < kSub; ++sub) {
+        const int64_t f0 = fbase + (int64_t)sub * kTileF4;
+        if (sub + 1 < kSub) load_tile(nxt, p4, f0 + kTileF4, nf);
+#pragma unroll
+        for (int k = 0; k < kF4PerThread; ++k) {
+            const int64_t f = f0 + k * kThreads;
+            float p0 = 0.0f, p1 = 0.0f;
+            if (f < nf) {
+                const uint32_t y = (uint32_t)(2 * f);
+                const int tb = gt.base | vT[(k << 1) | (sub << 3)];
+                const float fa0 = pend_factor(c, y), fa1 = pend_factor(c, y | 1u);
+                const float2 w0 = Ts[tb], w1 = Ts[tb | tE1];
+                const float wr0 = w0.x * fa0, wi0 = w0.y * fa0, wr1 = w1.x * fa1, wi1 = w1.y * fa1;
+                const float4 a = cur[k];
+                float4 o;
+                o.x = a.x * wr0 - a.y * wi0;
+                o.y = a.x * wi0 + a.y * wr0;
+                o.z = a.z * wr1 - a.w * wi1;
+                o.w = a.z * wi1 + a.w * wr1;
+                p4[f] = o;
+                p0 = o.x * o.x + o.y * o.y;
+                p1 = o.z * o.z + o.w * o.w;
+            }
+            if (nx) hist_push(my, gn, nE1, vN[(k << 1) | (sub << 3)], p0, p1, run);
+        }
+        if (sub + 1 < kSub) {
+#pragma unroll
+            for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
+        }
+    }
+    if (nx) hist_close(my, gn, nE1, run);
+    __syncthreads();
+    allow_dependent_launch();
+    if (nx) hist_commit(&hw[0][0], 1 << nx->s, gv.Hnext + (size_t)slot * kGroupBins);
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
+
+// Stable block-wide selection over [0, cnt): out(rank, i) for every i with
+// pred(i), ranks in increasing i; returns how many.  Called by the whole block.
+template <class Pred, class Out>
+__device__ int block_select(int cnt, Pred pred, Out out) {
+    __shared__ int wcnt[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int run = 0;
+    for (int i0 = 0; i0 < cnt; i0 += kThreads) {
+        const int i = i0 + (int)threadIdx.x;
+        const bool flag = i < cnt && pred(i);
+        const unsigned bal = __ballot_sync(0xffffffffu, flag);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = run, total = run;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            if (w < warp) before += wcnt[w];
+            total += wcnt[w];
+        }
+        if (flag) out(before + __popc(bal & ((1u << lane) - 1u)), i);
+        __syncthreads();
+        run = total;
+    }
+    return run;
+}
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int len, int x) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Branches of every member of one slot through one group.  Lane l of a warp
+// holds the start patterns b = l + 32 r (true bits of S, r < 8).
+__global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView sv, GroupView gv, double gamma) {
+    grid_dependency_wait();
+    const int slot = blockIdx.x;
+    const ZZGroup *gp = gv.grp;
+    const int m = gp->m, ns = gp->s, nbins = 1 << ns;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const TrajState st = v.st[slot];
+    const uint32_t Fb = st.J ^ st.pend;  // frame once the pending op is applied
+    uint32_t fS = 0;
+    for (int k = 0; k < ns; ++k) fS |= ((Fb >> gp->sp[k]) & 1u) << k;
+    __shared__ double hd[kGroupBins];  // joint by true bits of S
+    __shared__ double p1m[2 * kMaxGroupEdges];
+    __shared__ int child_base;
+    unsigned long long *Hs = gv.Hcur + (size_t)slot * kGroupBins;
+    for (int b = threadIdx.x; b < kGroupBins; b += kThreads) hd[b] = 0.0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += kThreads) {
+        hd[b ^ fS] = (double)Hs[b] * kHistUnit;
+        Hs[b] = 0ull;  // zero again for the next group that accumulates here
+    }
+    __syncthreads();
+    double h0[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) h0[r] = hd[lane + 32 * r];
+    const double sg = sqrt(gamma), sg1 = sqrt(1.0 - gamma);
+    if (warp == 0) {  // the identity / no-jump path: P(q = 1) at every damping site
+        double w[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) w[r] = h0[r];
+        for (int e = 0; e < m; ++e)
+            for (int k2 = 0; k2 < 2; ++k2) {
+                const int qi = k2 ? gp->ej[e] : gp->ei[e];
+                double tot = 0.0, one = 0.0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    tot += w[r];
+                    one += (((lane + 32 * r) >> qi) & 1) ? w[r] : 0.0;
+                }
+                tot = warp_sum(tot);
+                one = warp_sum(one);
+                if (lane == 0) p1m[2 * e + k2] = gamma * one / tot;
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    if (((lane + 32 * r) >> qi) & 1) w[r] *= 1.0 - gamma;
+            }
+    }
+    __syncthreads();
+    const int2 rg = sv.range[slot];
+    const int off = rg.x, cnt = rg.y;
+    const int32_t *mem = sv.members + off;
+    int32_t *evt = gv.evt + off, *rep = gv.rep + off, *lead = gv.lead + off;
+    uint64_t *ekey = gv.ekey + off;
+    // members that leave the shared path somewhere in the group, in member order
+    const int ne = block_select(
+        cnt,
+        [&](int i) {
+            const int t = mem[i];
+            for (int e = 0; e < m; ++e) {
+                const size_t gi = (size_t)t * v.G + gp->g0 + e;
+                if (v.branch[gi] & 15) return true;
+                const uint32_t *dw = v.dwords + gi * 2;
+                if (((double)dw[0] + 0.5) * kTwoM32 < p1m[2 * e] || ((double)dw[1] + 0.5) * kTwoM32 < p1m[2 * e + 1])
+                    return true;
+            }
+            return false;
+        },
+        [&](int r, int i) { evt[r] = i; });
+    for (int a = warp; a < ne; a += kThreads / 32) {  // their own draws: one warp each
+        const int t = mem[evt[a]];
+        double w[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) w[r] = h0[r];
+        uint32_t flip = 0;
+        uint64_t key = 0;
+        for (int e = 0; e < m; ++e) {
+            const size_t gi = (size_t)t * v.G + gp->g0 + e;
+            const int code = v.branch[gi] & 15;
+            const uint32_t *dw = v.dwords + gi * 2;
+            flip ^= (xpart_1q(code >> 2) << gp->ei[e]) ^ (xpart_1q(code & 3) << gp->ej[e]);
+            key |= (uint64_t)code << (6 * e);
+            int jumps = 0;
+            for (int k2 = 0; k2 < 2; ++k2) {
+                const int qi = k2 ? gp->ej[e] : gp->ei[e];
+                double tot = 0.0, one = 0.0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    tot += w[r];
+                    one += ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) ? w[r] : 0.0;
+                }
+                tot = warp_sum(tot);
+                one = warp_sum(one);
+                const bool j = ((double)dw[k2] + 0.5) * kTwoM32 < gamma * one / tot;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
+                    w[r] = j ? (bit ? w[r] * gamma : 0.0) : (bit ? w[r] * (1.0 - gamma) : w[r]);
+                }
+                if (j) {
+                    flip ^= 1u << qi;
+                    jumps |= 1 << k2;
+                }
+            }
+            key |= (uint64_t)jumps << (6 * e + 4);
+            if (lane == 0) v.branch[gi] = (uint8_t)(code | (jumps << 4));
+        }
+        if (lane == 0) ekey[a] = key;
+    }
+    __syncthreads();
+    // classes: the shared path (if any member kept it), then one per distinct
+    // outcome string in order of its first event
+    for (int a = threadIdx.x; a < ne; a += kThreads) {
+        const uint64_t ka = ekey[a];
+        int r = a;
+        for (int b = 0; b < a; ++b)
+            if (ekey[b] == ka) {
+                r = b;
+                break;
+            }
+        rep[a] = r;
+    }
+    __syncthreads();
+    const int nlead = block_select(ne, [&](int a) { return rep[a] == a; }, [&](int r, int a) { lead[r] = a; });
+    const int mainc = cnt - ne;
+    const int hasmain = mainc > 0 ? 1 : 0;
+    const int nc = hasmain + nlead;
+    for (int r = threadIdx.x; r < nlead; r += kThreads) {
+        const int a = lead[r];
+        int count = 0, before = 0;
+        for (int b = 0; b < ne; ++b) {
+            count += rep[b] == a;
+            before += rep[b] < a;
+        }
+        gv.lcount[off + r] = count;
+        gv.lstart[off + r] = mainc + before;
+    }
+    if (threadIdx.x == 0) child_base = nc > 1 ? atomicAdd(sv.slot_count, nc - 1) : 0;
+    __syncthreads();
+    if (nc > 1) {  // stable partition of the members by class into tmp[off ..]
+        for (int i = threadIdx.x; i < cnt; i += kThreads) {
+            const int lb = lower_bound_i32(evt, ne, i);
+            if (lb < ne && evt[lb] == i) continue;
+            sv.tmp[off + i - lb] = mem[i];
+        }
+        for (int a = threadIdx.x; a < ne; a += kThreads) {
+            const int ra = rep[a];
+            const int r = lower_bound_i32(lead, nlead, ra);
+            int pos = 0;
+            for (int b = ra; b < a; ++b) pos += rep[b] == ra;
+            sv.tmp[off + gv.lstart[off + r] + pos] = mem[evt[a]];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += kThreads) sv.members[off + i] = sv.tmp[off + i];
+    }
+    // per class: amplitude factors T (by stored bits of S) and the state after the group
+    for (int c = warp; c < nc; c += kThreads / 32) {
+        uint64_t key = 0;
+        int start = off, count = mainc;
+        if (c >= hasmain) {
+            const int r = c - hasmain;
+            key = ekey[lead[r]];
+            start = off + gv.lstart[off + r];
+            count = gv.lcount[off + r];
+        }
+        const int target = c == 0 ? slot : child_base + c - 1;
+        if (target >= sv.max_slots) {
+            if (lane == 0) atomicOr(v.status, 4);
+            continue;
+        }
+        double ar[8], ai[8], w[8];
+        uint32_t flip = 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            ar[r] = 1.0;
+            ai[r] = 0.0;
+            w[r] = h0[r];
+        }
+        const double gc = gp->c, gs = gp->sn;
+        for (int e = 0; e < m; ++e) {
+            const int code = (int)((key >> (6 * e)) & 15u);
+            const int qi = gp->ei[e], qj = gp->ej[e];
+            const uint32_t za = zpart_1q(code >> 2), zb = zpart_1q(code & 3);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {  // phase, then the Pauli's Z part, on the bits before its X part
+                const uint32_t cb = (uint32_t)(lane + 32 * r) ^ flip;
+                const uint32_t ci = (cb >> qi) & 1u, cj = (cb >> qj) & 1u;
+                if (ci != cj) {
+                    const double nr = ar[r] * gc + ai[r] * gs, ni = ai[r] * gc - ar[r] * gs;
+                    ar[r] = nr;
+                    ai[r] = ni;
+                }
+                if ((za & ci) ^ (zb & cj)) {
+                    ar[r] = -ar[r];
+                    ai[r] = -ai[r];
+                }
+            }
+            flip ^= (xpart_1q(code >> 2) << qi) ^ (xpart_1q(code & 3) << qj);
+            for (int k2 = 0; k2 < 2; ++k2) {
+                const int q = k2 ? qj : qi;
+                const bool j = ((key >> (6 * e + 4 + k2)) & 1u) != 0;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> q) & 1u) != 0;
+                    const double kf = j ? (bit ? sg : 0.0) : (bit ? sg1 : 1.0);
+                    ar[r] *= kf;
+                    ai[r] *= kf;
+                    w[r] *= kf * kf;
+                }
+                if (j) flip ^= 1u << q;
+            }
+        }
+        double N = 0.0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) N += w[r];
+        N = warp_sum(N);
+        const double sc = 1.0 / sqrt(N);
+        if (lane == 0 && !(N > 0.0 && isfinite(sc))) atomicOr(v.status, 1);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int b = lane + 32 * r;
+            if (b < nbins)
+                gv.T[(size_t)target * kGroupBins + (b ^ fS)] = make_float2((float)(ar[r] * sc), (float)(ai[r] * sc));
+        }
+        if (lane == 0) {
+            uint32_t qflip = 0;
+            for (int k = 0; k < ns; ++k) qflip |= ((flip >> k) & 1u) << gp->sp[k];
+            TrajState nst;
+            nst.J = Fb ^ qflip;
+            nst.pend = 0;
+            nst.pq0 = nst.pq1 = 0;
+            nst.f[0] = nst.f[1] = nst.f[2] = nst.f[3] = 1.0f;
+            gv.st_prev[target] = st;
+            v.st[target] = nst;
+            sv.range[target] = make_int2(start, count);
+            if (c > 0) {
+                const int f = atomicAdd(sv.fork_count, 1);
+                sv.forks[f] = make_int2(slot, target);
+            }
+        }
+    }
+    allow_dependent_launch();
+}
+
 // Copy the parent's statevector into every slot forked at this gate.
 __global__ void __launch_bounds__(kThreads) k_fork_copy(BatchView v, SlotView sv) {
     grid_dependency_wait();
@@ -1485,5 +1990,23 @@ cudaError_t launch_phase_sweep(const BatchView &v, const LayerView &L, cudaStrea
     return cudaGetLastError();
 }
 
+cudaError_t launch_group_hist(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
+    return launch_pdl(k_group_hist, dim3((unsigned)v.stiles, (unsigned)active), dim3(kThreads), s, v, gv);
+}
+
+cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, double gamma,
+                                cudaStream_t s) {
+    cudaError_t e = launch_pdl(k_group_decide, dim3((unsigned)active), dim3(kThreads), s, v, sv, gv, gamma);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_fork_copy, dim3(persistent_blocks()), dim3(kThreads), s, v, sv);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
+}
+
+cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
+    return launch_pdl(k_group_apply, dim3((unsigned)v.stiles, (unsigned)active), dim3(kThreads), s, v, gv);
+}
+
 }  // namespace qn
+
 

@@ -27,10 +27,12 @@ def qn():
     return mod
 
 
-def run(qn, w, sharing, launch_batch=0):
+def run(qn, w, sharing, launch_batch=0, fusion=False):
+    """fusion=False: one sweep per gate (with Pauli-only noise fusion would take
+    precedence over sharing); fusion=True with damping: phase-gate groups."""
     with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=launch_batch) as b:
         b.set_sharing(sharing)
-        b.set_fusion(False)  # with Pauli-only noise fusion would take precedence over sharing
+        b.set_fusion(fusion)
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
         mean, se = b.expectation()
         probs = b.probs()
@@ -76,6 +78,7 @@ def test_sharing_in_chunks_and_with_offset(qn):
     for sharing in (False, True):
         with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=37) as b:
             b.set_sharing(sharing)
+            b.set_fusion(False)
             b.set_offset(1000)
             b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
             res.append((b.expectation(), b.probs()))
@@ -93,12 +96,73 @@ def test_sharing_full_size_damping_n20(qn):
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
         m1, s1 = b.expectation()
         p1 = b.probs()
-    with qn.Batch(w.n, w.trajectories, w.seed) as b:
-        b.set_sharing(True)
-        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
-        m2, s2 = b.expectation()
-        p2 = b.probs()
-        slots = b.run_info()["states"]
-    assert slots < w.trajectories
+    out = {}
+    for fusion in (False, True):  # one sweep per gate / phase gates in groups
+        with qn.Batch(w.n, w.trajectories, w.seed) as b:
+            b.set_sharing(True)
+            b.set_fusion(fusion)
+            b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+            out[fusion] = (b.expectation(), b.probs(), b.run_info())
+    (m2, s2), p2, info2 = out[False]
+    (m3, s3), p3, info3 = out[True]
+    assert info2["states"] < w.trajectories and info3["states"] == info2["states"]
     assert abs(m1 - m2) < 1e-8 and abs(s1 - s2) < 1e-8
     np.testing.assert_allclose(p2, p1, rtol=1e-12, atol=0)
+    G = w.gate_count
+    assert abs(m3 - m1) < 8 * U32 * G * len(w.edges)
+    assert np.abs(p3 - p1).max() < 1e-6
+    assert info3["sweep_bytes"] < 0.7 * info2["sweep_bytes"]
+
+
+GROUP_CASES = {
+    "n5_ring_partial_warp": dict(n=5, p=2, index=40, trajectories=200, p1=5e-3, p2=2e-2, damping=0.03, d=2),
+    "n12_damping": dict(n=12, p=2, index=31, trajectories=300, p1=5e-3, p2=2e-2, damping=0.02),
+    "n14_heavy_noise": dict(n=14, p=2, index=32, trajectories=96, p1=1e-2, p2=3e-2, damping=0.05),
+    "n16_d5_ragged_groups": dict(n=16, p=1, index=41, trajectories=400, p1=2e-3, p2=1e-2, damping=0.01, d=5),
+}
+
+
+@pytest.mark.parametrize("case", sorted(GROUP_CASES))
+def test_phase_groups_equal_per_gate_sharing_and_oracle(qn, case):
+    """Shared-prefix mode with damping, phase gates swept in groups (one joint
+    per group, one apply sweep) against the per-gate shared-prefix run, the
+    default mode and the oracle.  The Kraus strings are the same draws, so the
+    number of distinct states must match exactly."""
+    kw = dict(GROUP_CASES[case])
+    n, p, idx, K = kw.pop("n"), kw.pop("p"), kw.pop("index"), kw.pop("trajectories")
+    w = W.qaoa_workload(case, n, p, index=idx, trajectories=K, batch=K, **kw)
+    m0, s0, p0, _, _ = run(qn, w, False)
+    m1, s1, p1, info1, br = run(qn, w, True, fusion=False)
+    m2, s2, p2, info2, _ = run(qn, w, True, fusion=True)
+    distinct = len({bytes(r) for r in br})
+    assert info1["states"] == distinct and info2["states"] == distinct
+    assert info2["sweep_bytes"] < info1["sweep_bytes"]  # fewer sweeps over the states
+    # same draws: the ensemble sums agree to FP32 state rounding
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    tol = 8 * U32 * G * len(w.edges)
+    assert abs(m2 - m1) < tol and abs(m2 - m0) < tol
+    assert abs(p2.sum() - 1) < 1e-12
+    assert np.abs(p2 - p0).max() < 1e-5
+    ref = oracle.traj_run(w.n, w.edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, 0, K,
+                          want_amps=False, want_branches=False)
+    assert abs(m2 - ref["s1"] / K) < tol
+    assert oracle.error(p2, ref["probs_sum"] / K) < 1e-9
+
+
+def test_phase_groups_deterministic_and_chunked(qn):
+    """Two runs give bit-identical results (joints are summed in a fixed order);
+    chunks of 37 trajectories with an offset agree with the default mode."""
+    w = W.qaoa_workload("grp_chunks", 10, 2, index=33, trajectories=100, batch=37, p1=5e-3, p2=2e-2, damping=0.03)
+    res = []
+    for sharing in (False, True, True):
+        with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=37) as b:
+            b.set_sharing(sharing)
+            b.set_offset(1000)
+            b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+            res.append((b.expectation(), b.probs()))
+    (ma, _), pa = res[0]
+    (mb, sb), pb = res[1]
+    (mc, sc), pc = res[2]
+    assert mb == mc and sb == sc and np.array_equal(pb, pc)
+    assert abs(ma - mb) < 1e-5
+    assert np.abs(pa - pb).max() < 1e-5
