@@ -146,9 +146,9 @@ struct qn_batch {
     int64_t sh_cap = 0;
     int64_t sh_slots = 0;  // slots of the last shared-prefix run (all chunks)
     // phase-gate groups of shared-prefix mode with damping
-    std::vector<ZZGroup> groups;
+    std::vector<GateGroup> groups;
     std::vector<int32_t> group_at;  // [G] index of the group that starts at gate g, or -1
-    ZZGroup *gr_dev = nullptr;
+    GateGroup *gr_dev = nullptr;
     int64_t gr_cap = 0;
     unsigned long long *gv_H = nullptr;  // [2][gv_cap][256]
     float2 *gv_T = nullptr;
@@ -376,6 +376,10 @@ void build_gates(qn_batch *h) {
     for (int e = 0; e < E; ++e) h->edges_host.push_back(make_int2(h->edges[2 * e], h->edges[2 * e + 1]));
 }
 
+// Mixer blocks need at least one full block of 256 fibers of three qubits and a
+// phase group before them (whose apply sweep forms the first block's joint).
+bool mixer_blocks_fit(int n, int E) { return n >= 12 && E > 0; }
+
 // Phase-gate groups of every layer: greedy runs of consecutive ZZ gates whose
 // qubits number at most 8 (at most kMaxGroupEdges gates, so that a member's
 // outcome string fits 6 bits per gate in 64 bits).
@@ -387,7 +391,7 @@ void build_groups(qn_batch *h) {
         const int base = n + l * (E + n);
         int g = base;
         while (g < base + E) {
-            ZZGroup z;
+            GateGroup z;
             std::memset(&z, 0, sizeof z);
             z.g0 = g;
             uint32_t S = 0;
@@ -423,7 +427,66 @@ void build_groups(qn_batch *h) {
             h->group_at[z.g0] = (int32_t)h->groups.size();
             h->groups.push_back(z);
         }
+        if (!mixer_blocks_fit(n, E)) continue;
+        // mixer rotations in blocks of three consecutive qubits
+        for (int q = 0; q < n; q += 3) {
+            GateGroup z;
+            std::memset(&z, 0, sizeof z);
+            z.kind = 1;
+            z.g0 = base + E + q;
+            z.m = z.s = std::min(3, n - q);
+            for (int k = 0; k < z.m; ++k) {
+                z.sp[k] = q + k;
+                z.ei[k] = z.ej[k] = k;
+            }
+            z.c = h->dgates_host[z.g0].c;
+            z.sn = h->dgates_host[z.g0].s;
+            h->group_at[z.g0] = (int32_t)h->groups.size();
+            h->groups.push_back(z);
+        }
     }
+}
+
+// Thread -> float4-index map of the sweep of the mixer block on qubits
+// q_lo .. q_lo + M - 1, with the qubits `next` of the following block on lane
+// bits (so that the sweep can form that block's joint with warp shuffles).
+MixMap mix_map(int n, int q_lo, int M, const std::vector<int> &next) {
+    MixMap mm;
+    std::memset(&mm, 0, sizeof mm);
+    mm.has0 = q_lo == 0;
+    const int D = mm.has0 ? M - 1 : M;
+    mm.fl = mm.has0 ? 0 : q_lo - 1;
+    std::vector<int> nf;  // f bits of the next block's qubits
+    for (int q : next) nf.push_back(q - 1);
+    std::vector<int> free_bits;
+    for (int b = 0; b < n - 1; ++b)
+        if (b < mm.fl || b >= mm.fl + D) free_bits.push_back(b);
+    const int nN = (int)nf.size();
+    std::vector<int> order;
+    bool low = true;  // the next block's bits are among the five lowest free bits
+    for (int b : nf)
+        if (std::find(free_bits.begin(), free_bits.begin() + std::min<size_t>(5, free_bits.size()), b) ==
+            free_bits.begin() + std::min<size_t>(5, free_bits.size()))
+            low = false;
+    if (low) {
+        order = free_bits;
+    } else {
+        for (int b : free_bits)
+            if ((int)order.size() < 5 - nN && std::find(nf.begin(), nf.end(), b) == nf.end()) order.push_back(b);
+        for (int b : nf) order.push_back(b);
+        for (int b : free_bits)
+            if (std::find(order.begin(), order.end(), b) == order.end()) order.push_back(b);
+    }
+    mm.nfree = (int)order.size();
+    for (int i = 0; i < mm.nfree; ++i) mm.fb[i] = (int8_t)order[i];
+    mm.nN = nN;
+    uint32_t used = 0;
+    for (int i = 0; i < nN; ++i) {
+        mm.npos[i] = (int)(std::find(order.begin(), order.end(), nf[i]) - order.begin());
+        used |= 1u << mm.npos[i];
+    }
+    mm.lmask = 31u & ~used;
+    return mm;
 }
 
 bool use_groups(const qn_batch *h) { return h->fusion && h->damping_on && !h->groups.empty(); }
@@ -669,7 +732,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
         h->gr_cap = (int64_t)h->groups.size();
     }
     if (grouped) {
-        QN_CUDA(cudaMemcpyAsync(h->gr_dev, h->groups.data(), h->groups.size() * sizeof(ZZGroup),
+        QN_CUDA(cudaMemcpyAsync(h->gr_dev, h->groups.data(), h->groups.size() * sizeof(GateGroup),
                                 cudaMemcpyHostToDevice, h->stream));
         QN_CUDA(cudaMemsetAsync(h->gv_H, 0, sizeof(unsigned long long) * 2 * (size_t)h->gv_cap * kGroupBins,
                                 h->stream));
@@ -758,14 +821,19 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     for (int g = n; g < G; ++g) {
         const int gi = grouped ? h->group_at[g] : -1;
         if (gi >= 0) {
-            // a group of phase gates: (joint pass,) decide + forks, one apply sweep
-            const ZZGroup &z = h->groups[gi];
+            // a group: (joint pass,) decide + forks, one sweep that applies the
+            // group and forms the next group's joint
+            const GateGroup &z = h->groups[gi];
             const int ng = (int)h->groups.size();
-            const bool first = gi == 0 || h->groups[gi - 1].g0 + h->groups[gi - 1].m != z.g0;
-            const bool has_next = gi + 1 < ng && h->groups[gi + 1].g0 == z.g0 + z.m;
+            const GateGroup *nz = gi + 1 < ng && h->groups[gi + 1].g0 == z.g0 + z.m ? &h->groups[gi + 1] : nullptr;
+            const bool first = z.kind == 0 && (gi == 0 || h->groups[gi - 1].kind != 0 ||
+                                               h->groups[gi - 1].g0 + h->groups[gi - 1].m != z.g0);
             GroupView gv;
             gv.grp = h->gr_dev + gi;
-            gv.next = has_next ? h->gr_dev + gi + 1 : nullptr;
+            gv.next = nz && nz->kind == 0 && z.kind == 0 ? h->gr_dev + gi + 1 : nullptr;
+            gv.vq = nz && nz->kind == 1 && z.kind == 0 ? nz->s : 0;
+            gv.vc = nz ? nz->c : 1.0f;
+            gv.vs = nz ? nz->sn : 0.0f;
             gv.Hcur = h->gv_H + (size_t)(gi & 1) * h->gv_cap * kGroupBins;
             gv.Hnext = h->gv_H + (size_t)((gi + 1) & 1) * h->gv_cap * kGroupBins;
             gv.T = h->gv_T;
@@ -791,7 +859,14 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
             active = *active_host;
             QN_TRY(prof_begin(h, &ep, 3, (double)active * 16.0 * amp_count));
-            e = launch_group_apply(v, sv, gv, active, h->stream);
+            if (z.kind == 0) {
+                e = launch_group_apply(v, sv, gv, active, h->stream);
+            } else {
+                std::vector<int> next;
+                if (nz && nz->kind == 1)
+                    for (int k = 0; k < nz->s; ++k) next.push_back(nz->sp[k]);
+                e = launch_mix_sweep(v, gv, mix_map(n, z.sp[0], z.s, next), z.s, active, h->stream);
+            }
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
             QN_TRY(prof_end(h, &ep));
             h->sweep_bytes += (double)active * 16.0 * amp_count;

@@ -78,20 +78,41 @@ struct SlotView {
 constexpr int kMaxGroupEdges = 10;
 constexpr int kGroupBins = 256;
 
-struct ZZGroup {
+// A group of consecutive gates of one layer whose noise sites are all decided
+// from one joint distribution of the true bits of the group's qubits S:
+//   kind 0  phase gates (two damping sites each); the joint is taken before them
+//   kind 1  mixer rotations on consecutive qubits (one site each); the joint is
+//           that of the state after the rotations
+struct GateGroup {
     int32_t g0, m, s;               // first gate, gates, qubits in S
+    int32_t kind;
     int32_t sp[8];                  // qubits of S, ascending
     int32_t ei[kMaxGroupEdges];     // S index of each gate's first qubit
-    int32_t ej[kMaxGroupEdges];     // S index of each gate's second qubit
-    float c, sn;                    // cos gamma, sin gamma of the layer
-    uint8_t tab[4][256];            // index over S of the stored bits in each byte of y
+    int32_t ej[kMaxGroupEdges];     // S index of each gate's second qubit (== ei for a rotation)
+    float c, sn;                    // cos, sin of the layer's gamma (kind 0) or beta (kind 1)
+    uint8_t tab[4][256];            // index over S of the stored bits in each byte of y (kind 0)
+};
+
+// Thread -> float4-index map of a mixer-block sweep: bit i of the fiber id goes
+// to f bit fb[i]; the next block's qubits sit on lane bits npos[].
+struct MixMap {
+    int8_t fb[32];
+    int32_t nfree;    // fiber-id bits
+    int32_t fl;       // lowest f bit of the fiber
+    int32_t has0;     // the block holds qubit 0 (the two halves of a float4)
+    int32_t nN;       // qubits of the next block (0: no joint to accumulate)
+    int32_t npos[3];  // lane bit of each of them
+    uint32_t lmask;   // lane bits that are none of them
 };
 
 // Device view of one group step.  Per-slot arrays are indexed by slot; the
 // per-member scratch arrays by the position of the member in SlotView::members.
 struct GroupView {
-    const ZZGroup *grp;    // group applied by this step
-    const ZZGroup *next;   // group whose joint the apply sweep accumulates, or nullptr
+    const GateGroup *grp;    // group applied by this step
+    const GateGroup *next;   // phase group whose joint the apply sweep accumulates, or nullptr
+    int32_t vq;              // > 0: the apply sweep accumulates instead the joint of the
+                             // mixer block on qubits 0 .. vq-1 after rotations (vc, vs)
+    float vc, vs;
     unsigned long long *Hcur;   // [max_slots][256] joint of this group, fixed point 2^-60
     unsigned long long *Hnext;  // [max_slots][256] joint of the next group (zero on entry)
     float2 *T;             // [max_slots][256] amplitude factor by stored bits of S
@@ -182,6 +203,8 @@ cudaError_t launch_slot_fork(const BatchView &v, const SlotView &sv, int active,
 cudaError_t launch_group_hist(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, double gamma,
                                 cudaStream_t s);
+cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int M, int active,
+                            cudaStream_t s);
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
 // Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n
 // adding d<C>_t / d theta_param into grad[t * nparam + param] (FP64).

@@ -799,7 +799,7 @@ constexpr double kHistUnit = 1.0 / kHistScale;
 static_assert(kThreads == 256 && kTileF4 == 1024 && kF4PerThread == 4 && kSub == 4,
               "group bins assume y = e | tid << 1 | k << 9 | sub << 11 | tile << 13");
 
-__device__ __forceinline__ int group_bin(const ZZGroup *gp, uint32_t y) {
+__device__ __forceinline__ int group_bin(const GateGroup *gp, uint32_t y) {
     return gp->tab[0][y & 255u] | gp->tab[1][(y >> 8) & 255u] | gp->tab[2][(y >> 16) & 255u] | gp->tab[3][y >> 24];
 }
 
@@ -811,7 +811,7 @@ struct GroupBins {
     unsigned lmask;  // lane bits that are no qubit of S
 };
 
-__device__ __forceinline__ GroupBins group_bins(const ZZGroup *gp, int tile, unsigned char *vtab) {
+__device__ __forceinline__ GroupBins group_bins(const GateGroup *gp, int tile, unsigned char *vtab) {
     GroupBins gb;
     gb.base = group_bin(gp, ((uint32_t)threadIdx.x << 1) | ((uint32_t)tile << 13));
     unsigned lm = 0;
@@ -890,7 +890,7 @@ __device__ __forceinline__ SweepCtx pending_ctx(const TrajState &s) {
 __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupView gv) {
     grid_dependency_wait();
     const int slot = blockIdx.y, tile = blockIdx.x;
-    const ZZGroup *gp = gv.grp;
+    const GateGroup *gp = gv.grp;
     __shared__ float hw[kThreads / 32][kGroupBins];
     __shared__ unsigned char vtab[32];
     for (int i = threadIdx.x; i < (kThreads / 32) * kGroupBins; i += kThreads) (&hw[0][0])[i] = 0.0f;
@@ -933,13 +933,58 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
     hist_commit(&hw[0][0], 1 << gp->s, gv.Hcur + (size_t)slot * kGroupBins);
 }
 
-// Apply a group: phi_y *= D(y) * T[slot][stored bits of S], D the pending op of
-// the gate before the group; accumulate the next group's joint if there is one.
+// exp(-i beta X) on the amplitude pair (a, b) of one qubit: a' = c a - i s b,
+// b' = c b - i s a.
+__device__ __forceinline__ void rx_pair(float &ar, float &ai, float &br, float &bi, float c, float s) {
+    const float nar = c * ar + s * bi, nai = c * ai - s * br;
+    const float nbr = c * br + s * ai, nbi = c * bi - s * ar;
+    ar = nar;
+    ai = nai;
+    br = nbr;
+    bi = nbi;
+}
+
+// The same rotation on a qubit whose two values sit in lanes that differ in
+// `lanebit` (every lane of the warp takes part).
+__device__ __forceinline__ void rx_lanes(float4 &o, int lanebit, float c, float s) {
+    const float px = __shfl_xor_sync(0xffffffffu, o.x, lanebit), py = __shfl_xor_sync(0xffffffffu, o.y, lanebit);
+    const float pz = __shfl_xor_sync(0xffffffffu, o.z, lanebit), pw = __shfl_xor_sync(0xffffffffu, o.w, lanebit);
+    o.x = c * o.x + s * py;
+    o.y = c * o.y - s * px;
+    o.z = c * o.z + s * pw;
+    o.w = c * o.w - s * pz;
+}
+
+// Per-block joint of a mixer block whose qubits sit on lane bits.  put: this
+// lane's sum `acc` for bin `bin`, summed first over the lanes that differ only
+// in `lmask`, goes to the warp's row of hw[8][8].  commit (after a block
+// barrier): warps summed in fixed order, the block's 2^nb bins added to H.
+__device__ __forceinline__ void lane_joint_put(float acc, int bin, unsigned lmask, float *hw) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        if ((lmask >> i) & 1u) acc += __shfl_xor_sync(0xffffffffu, acc, 1 << i);
+    if (((threadIdx.x & 31u) & lmask) == 0u) hw[(threadIdx.x >> 5) * 8 + bin] = acc;
+}
+
+__device__ __forceinline__ void lane_joint_commit(int nb, const float *hw, unsigned long long *H) {
+    if ((int)threadIdx.x < nb) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += (double)hw[w * 8 + threadIdx.x];
+        if (sum > 0.0) atomicAdd(H + threadIdx.x, __double2ull_rn(sum * kHistScale));
+    }
+}
+
+// Apply a phase group: phi_y *= D(y) * T[slot][stored bits of S], D the pending
+// op of the gate before the group.  Then accumulate either the next phase
+// group's joint (gv.next) or the joint of the mixer block on qubits 0 .. vq-1
+// as it will be after that block's rotations (gv.vq > 0): qubit 0 is the pair
+// inside a float4, qubits 1 and 2 are lane bits 0 and 1 of the sweep layout.
 __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupView gv) {
     grid_dependency_wait();
     const int slot = blockIdx.y, tile = blockIdx.x;
-    const ZZGroup *gp = gv.grp;
-    const ZZGroup *nx = gv.next;
+    const GateGroup *gp = gv.grp;
+    const GateGroup *nx = gv.next;
+    const int vq = gv.vq;
     __shared__ float2 Ts[kGroupBins];
     __shared__ float hw[kThreads / 32][kGroupBins];
     __shared__ unsigned char vT[32], vN[32];
@@ -959,7 +1004,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     float *my = hw[threadIdx.x >> 5];
     const int tE1 = vT[1];
     const int nE1 = nx ? vN[1] : 0;
+    const float vc = gv.vc, vs = gv.vs;
     HistRun run;
+    float va0 = 0.0f, va1 = 0.0f;
     float4 cur[kF4PerThread], nxt[kF4PerThread];
     load_tile(cur, p4, fbase, nf);
 #pragma unroll
@@ -969,7 +1016,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
 #pragma unroll
         for (int k = 0; k < kF4PerThread; ++k) {
             const int64_t f = f0 + k * kThreads;
-            float p0 = 0.0f, p1 = 0.0f;
+            float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (f < nf) {
                 const uint32_t y = (uint32_t)(2 * f);
                 const int tb = gt.base | vT[(k << 1) | (sub << 3)];
@@ -977,16 +1024,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
                 const float2 w0 = Ts[tb], w1 = Ts[tb | tE1];
                 const float wr0 = w0.x * fa0, wi0 = w0.y * fa0, wr1 = w1.x * fa1, wi1 = w1.y * fa1;
                 const float4 a = cur[k];
-                float4 o;
                 o.x = a.x * wr0 - a.y * wi0;
                 o.y = a.x * wi0 + a.y * wr0;
                 o.z = a.z * wr1 - a.w * wi1;
                 o.w = a.z * wi1 + a.w * wr1;
                 p4[f] = o;
-                p0 = o.x * o.x + o.y * o.y;
-                p1 = o.z * o.z + o.w * o.w;
             }
-            if (nx) hist_push(my, gn, nE1, vN[(k << 1) | (sub << 3)], p0, p1, run);
+            if (nx) hist_push(my, gn, nE1, vN[(k << 1) | (sub << 3)], o.x * o.x + o.y * o.y, o.z * o.z + o.w * o.w,
+                              run);
+            if (vq > 0) {
+                rx_pair(o.x, o.y, o.z, o.w, vc, vs);
+                if (vq > 1) rx_lanes(o, 1, vc, vs);
+                if (vq > 2) rx_lanes(o, 2, vc, vs);
+                va0 += o.x * o.x + o.y * o.y;
+                va1 += o.z * o.z + o.w * o.w;
+            }
         }
         if (sub + 1 < kSub) {
 #pragma unroll
@@ -997,6 +1049,90 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     __syncthreads();
     allow_dependent_launch();
     if (nx) hist_commit(&hw[0][0], 1 << nx->s, gv.Hnext + (size_t)slot * kGroupBins);
+    if (vq > 0) {
+        // bins: qubit 0 = e, qubits 1 .. vq-1 = lane bits 0 .. vq-2
+        const unsigned lq = (1u << (vq - 1)) - 1u;
+        const unsigned lmask = 31u & ~lq;
+        const int lb = (int)((threadIdx.x & 31u) & lq) << 1;
+        lane_joint_put(va0, lb, lmask, &hw[0][0]);
+        lane_joint_put(va1, lb | 1, lmask, &hw[0][0]);
+        __syncthreads();
+        lane_joint_commit(1 << vq, &hw[0][0], gv.Hnext + (size_t)slot * kGroupBins);
+    }
+}
+
+// Mixer block sweep (shared-prefix mode): exp(-i beta X) on the M consecutive
+// qubits of the block, held as a register fiber per thread, then the block's
+// drawn Pauli and damping ops as the real factor T[slot][stored bits of the
+// block] (drawn beforehand from the joint after the rotations, so the state is
+// final when written); then the joint of the next block, whose qubits sit on
+// lane bits, as it will be after that block's rotations.
+template <int M, bool HAS0>
+__global__ void __launch_bounds__(kThreads, 2) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
+    constexpr int D = HAS0 ? M - 1 : M;  // fiber bits in float4-index space
+    constexpr int NE = 1 << D;
+    grid_dependency_wait();
+    const int slot = blockIdx.y;
+    __shared__ float Df[8];
+    __shared__ float hw[(kThreads / 32) * 8];
+    if (threadIdx.x < (1u << M)) Df[threadIdx.x] = gv.T[(size_t)slot * kGroupBins + threadIdx.x].x;
+    const uint32_t u = blockIdx.x * kThreads + threadIdx.x;  // fiber id
+    int64_t fbase = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
+        if (i < mm.nfree) fbase |= (int64_t)((u >> i) & 1u) << mm.fb[i];
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << v.n));
+    float4 val[NE];
+#pragma unroll
+    for (int k = 0; k < NE; ++k) val[k] = p4[fbase + ((int64_t)k << mm.fl)];
+    const float c = gv.grp->c, sn = gv.grp->sn;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        if (HAS0 && j == 0) {
+#pragma unroll
+            for (int k = 0; k < NE; ++k) rx_pair(val[k].x, val[k].y, val[k].z, val[k].w, c, sn);
+        } else {
+            const int bit = HAS0 ? j - 1 : j;
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                if (k & (1 << bit)) continue;
+                float4 &a = val[k];
+                float4 &b = val[k | (1 << bit)];
+                rx_pair(a.x, a.y, b.x, b.y, c, sn);
+                rx_pair(a.z, a.w, b.z, b.w, c, sn);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+        const float f0 = HAS0 ? Df[k << 1] : Df[k], f1 = HAS0 ? Df[(k << 1) | 1] : Df[k];
+        val[k].x *= f0;
+        val[k].y *= f0;
+        val[k].z *= f1;
+        val[k].w *= f1;
+        p4[fbase + ((int64_t)k << mm.fl)] = val[k];
+    }
+    allow_dependent_launch();
+    if (mm.nN > 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (i >= mm.nN) break;
+#pragma unroll
+            for (int k = 0; k < NE; ++k) rx_lanes(val[k], 1 << mm.npos[i], c, sn);
+        }
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) acc += val[k].x * val[k].x + val[k].y * val[k].y + val[k].z * val[k].z + val[k].w * val[k].w;
+        const int lane = threadIdx.x & 31;
+        int bin = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i < mm.nN) bin |= ((lane >> mm.npos[i]) & 1) << i;
+        lane_joint_put(acc, bin, mm.lmask, hw);
+        __syncthreads();
+        lane_joint_commit(1 << mm.nN, hw, gv.Hnext + (size_t)slot * kGroupBins);
+    }
 }
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -1040,13 +1176,38 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int len, int x)
     return lo;
 }
 
+// X and Z parts of a gate's Pauli on its (one or two) qubits.
+struct GateCode {
+    uint32_t xa, za, xb, zb;
+    int sites;  // damping sites of the gate
+};
+
+__device__ __forceinline__ GateCode gate_code(int kind, int code) {
+    GateCode g;
+    if (kind == 0) {
+        g.xa = xpart_1q(code >> 2);
+        g.za = zpart_1q(code >> 2);
+        g.xb = xpart_1q(code & 3);
+        g.zb = zpart_1q(code & 3);
+        g.sites = 2;
+    } else {
+        g.xa = xpart_1q(code);
+        g.za = zpart_1q(code);
+        g.xb = g.zb = 0;
+        g.sites = 1;
+    }
+    return g;
+}
+
 // Branches of every member of one slot through one group.  Lane l of a warp
-// holds the start patterns b = l + 32 r (true bits of S, r < 8).
+// holds the patterns b = l + 32 r (true bits of S, r < 8) of the joint: at the
+// start of a phase group, after the rotations of a mixer block.
 __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView sv, GroupView gv, double gamma) {
     grid_dependency_wait();
     const int slot = blockIdx.x;
-    const ZZGroup *gp = gv.grp;
-    const int m = gp->m, ns = gp->s, nbins = 1 << ns;
+    const GateGroup *gp = gv.grp;
+    const int m = gp->m, ns = gp->s, nbins = 1 << ns, kind = gp->kind;
+    const int nsite = kind == 0 ? 2 : 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TrajState st = v.st[slot];
     const uint32_t Fb = st.J ^ st.pend;  // frame once the pending op is applied
@@ -1072,7 +1233,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
 #pragma unroll
         for (int r = 0; r < 8; ++r) w[r] = h0[r];
         for (int e = 0; e < m; ++e)
-            for (int k2 = 0; k2 < 2; ++k2) {
+            for (int k2 = 0; k2 < nsite; ++k2) {
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
                 double tot = 0.0, one = 0.0;
 #pragma unroll
@@ -1103,8 +1264,8 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 const size_t gi = (size_t)t * v.G + gp->g0 + e;
                 if (v.branch[gi] & 15) return true;
                 const uint32_t *dw = v.dwords + gi * 2;
-                if (((double)dw[0] + 0.5) * kTwoM32 < p1m[2 * e] || ((double)dw[1] + 0.5) * kTwoM32 < p1m[2 * e + 1])
-                    return true;
+                if (((double)dw[0] + 0.5) * kTwoM32 < p1m[2 * e]) return true;
+                if (nsite == 2 && ((double)dw[1] + 0.5) * kTwoM32 < p1m[2 * e + 1]) return true;
             }
             return false;
         },
@@ -1120,10 +1281,11 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
             const size_t gi = (size_t)t * v.G + gp->g0 + e;
             const int code = v.branch[gi] & 15;
             const uint32_t *dw = v.dwords + gi * 2;
-            flip ^= (xpart_1q(code >> 2) << gp->ei[e]) ^ (xpart_1q(code & 3) << gp->ej[e]);
+            const GateCode gc = gate_code(kind, code);
+            flip ^= (gc.xa << gp->ei[e]) ^ (gc.xb << gp->ej[e]);
             key |= (uint64_t)code << (6 * e);
             int jumps = 0;
-            for (int k2 = 0; k2 < 2; ++k2) {
+            for (int k2 = 0; k2 < nsite; ++k2) {
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
                 double tot = 0.0, one = 0.0;
 #pragma unroll
@@ -1222,23 +1384,23 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
         for (int e = 0; e < m; ++e) {
             const int code = (int)((key >> (6 * e)) & 15u);
             const int qi = gp->ei[e], qj = gp->ej[e];
-            const uint32_t za = zpart_1q(code >> 2), zb = zpart_1q(code & 3);
+            const GateCode pc = gate_code(kind, code);
 #pragma unroll
             for (int r = 0; r < 8; ++r) {  // phase, then the Pauli's Z part, on the bits before its X part
                 const uint32_t cb = (uint32_t)(lane + 32 * r) ^ flip;
                 const uint32_t ci = (cb >> qi) & 1u, cj = (cb >> qj) & 1u;
-                if (ci != cj) {
+                if (kind == 0 && ci != cj) {
                     const double nr = ar[r] * gc + ai[r] * gs, ni = ai[r] * gc - ar[r] * gs;
                     ar[r] = nr;
                     ai[r] = ni;
                 }
-                if ((za & ci) ^ (zb & cj)) {
+                if ((pc.za & ci) ^ (pc.zb & cj)) {
                     ar[r] = -ar[r];
                     ai[r] = -ai[r];
                 }
             }
-            flip ^= (xpart_1q(code >> 2) << qi) ^ (xpart_1q(code & 3) << qj);
-            for (int k2 = 0; k2 < 2; ++k2) {
+            flip ^= (pc.xa << qi) ^ (pc.xb << qj);
+            for (int k2 = 0; k2 < nsite; ++k2) {
                 const int q = k2 ? qj : qi;
                 const bool j = ((key >> (6 * e + 4 + k2)) & 1u) != 0;
 #pragma unroll
@@ -2001,6 +2163,20 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
     e = launch_pdl(k_fork_copy, dim3(persistent_blocks()), dim3(kThreads), s, v, sv);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
+}
+
+cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int M, int active,
+                            cudaStream_t s) {
+    const bool has0 = mm.has0 != 0;
+    const unsigned blocks = (unsigned)(((int64_t)1 << mm.nfree) / kThreads);
+    const dim3 grid(blocks, (unsigned)active);
+    if (M == 3) return has0 ? launch_pdl(k_mix_sweep<3, true>, grid, dim3(kThreads), s, v, gv, mm)
+                            : launch_pdl(k_mix_sweep<3, false>, grid, dim3(kThreads), s, v, gv, mm);
+    if (M == 2) return has0 ? launch_pdl(k_mix_sweep<2, true>, grid, dim3(kThreads), s, v, gv, mm)
+                            : launch_pdl(k_mix_sweep<2, false>, grid, dim3(kThreads), s, v, gv, mm);
+    if (M == 1) return has0 ? launch_pdl(k_mix_sweep<1, true>, grid, dim3(kThreads), s, v, gv, mm)
+                            : launch_pdl(k_mix_sweep<1, false>, grid, dim3(kThreads), s, v, gv, mm);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
