@@ -206,7 +206,7 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
     torch.cuda.synchronize()
     mean, se = b.expectation()
     b.set_profiling(PROFILE_PERIOD)
-    for k in range(4):
+    for k in range(5):
         b.profile_read(k)
     if pg:
         pg.barrier()
@@ -232,7 +232,7 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
     res = dict(ms=ms, value=w.trajectories * args.steps * world / (ms / 1e3), mean=mean, se=se,
                launches=launches, sweep_bytes_per_step=sweep_bytes / args.steps, states_per_step=states / args.steps,
                sweeps=b.profile_read(0), inits=b.profile_read(1), accs=b.profile_read(2),
-               groups=b.profile_read(3), clocks=clocks.summary())
+               groups=b.profile_read(3), mixers=b.profile_read(4), clocks=clocks.summary())
     b.set_profiling(0)
     if with_e2e:
         # end to end through the C ABI from host buffers: run + <C> + sigma to host
@@ -321,7 +321,9 @@ def gpu_arm(args):
     if rank == 0:
         fused = main_mode[1] and w.damping == 0
         grouped = sharing and main_mode[1] and main["groups"]["launches"] > 0
-        kname = "k_slot_sweep (mixer gate sweeps over live prefix states)" if grouped else \
+        blocks = grouped and main["mixers"]["launches"] > 0
+        kname = "k_mix_sweep (mixer blocks of 3 qubits over live prefix states, 16 B per amplitude)" if blocks else \
+            "k_slot_sweep (mixer gate sweeps over live prefix states)" if grouped else \
             "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
             ("k_fused_sweep (fused layer sweeps, 16 B per amplitude)" if fused else
              "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")
@@ -341,9 +343,10 @@ def gpu_arm(args):
             "distinct_states_per_step": main["states_per_step"],
             "sweep_bytes_per_step": main["sweep_bytes_per_step"],
             "c_mean": main["mean"], "c_stderr": main["se"],
-            "roofline": roof(main, kname),
+            "roofline": roof(main, kname, "mixers" if blocks else "sweeps"),
             "kernels": {"gate sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["sweeps"],
                         "phase-group sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["groups"],
+                        "mixer-block sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["mixers"],
                         "k_init": main["inits"], "k_observe+k_probs": main["accs"]},
             "e2e": {"value": main["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": main["launches"],

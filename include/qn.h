@@ -202,9 +202,10 @@ qn_status qn_batch_set_profiling(qn_batch *h, int32_t period);
 
 /* Totals since the last read, for kernel family `kind` (0 = gate sweeps, 1 =
  * state init, 2 = ensemble accumulation, 3 = phase-group sweeps of
- * shared-prefix mode: joint passes and apply sweeps): launches, summed event
- * milliseconds and algorithmic bytes.  Kinds 0 and 3 share one sampling
- * counter.  Synchronises the stream, then resets the totals. */
+ * shared-prefix mode: joint passes and apply sweeps, 4 = mixer-block sweeps of
+ * shared-prefix mode): launches, summed event milliseconds and algorithmic
+ * bytes.  Kinds 0, 3 and 4 share one sampling counter.  Synchronises the
+ * stream, then resets the totals. */
 qn_status qn_profile_read(qn_batch *h, int32_t kind, int64_t *launches, double *ms, double *bytes);
 
 /* Allocation-free variant of qn_run_qaoa for one batch (no counterpart in the

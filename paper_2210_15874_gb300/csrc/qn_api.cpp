@@ -166,9 +166,9 @@ struct qn_batch {
     int64_t prof_counter = 0;
     std::vector<EventPair> events;
     std::vector<EventPair> spare;
-    int64_t prof_launches[4] = {0, 0, 0, 0};
-    double prof_ms[4] = {0, 0, 0, 0};
-    double prof_bytes[4] = {0, 0, 0, 0};
+    int64_t prof_launches[5] = {0, 0, 0, 0, 0};
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+    double prof_bytes[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -447,45 +447,49 @@ void build_groups(qn_batch *h) {
     }
 }
 
-// Thread -> float4-index map of the sweep of the mixer block on qubits
+// Unit -> float4-index map of the sweep of the mixer block on qubits
 // q_lo .. q_lo + M - 1, with the qubits `next` of the following block on lane
-// bits (so that the sweep can form that block's joint with warp shuffles).
+// bits 2.. (so that the sweep can form that block's joint with warp shuffles).
+// Qubit 0 is the pair inside a float4; the block's other qubits go to lane bits
+// 0, 1 when the block holds qubit 0 (the plain tile layout), else to the two
+// register bits and lane bit 1; every other unit bit takes the lowest f bit
+// left, so that lane bit 0 pairs neighbouring float4 whenever it can.
 MixMap mix_map(int n, int q_lo, int M, const std::vector<int> &next) {
     MixMap mm;
     std::memset(&mm, 0, sizeof mm);
-    mm.has0 = q_lo == 0;
-    const int D = mm.has0 ? M - 1 : M;
-    mm.fl = mm.has0 ? 0 : q_lo - 1;
-    std::vector<int> nf;  // f bits of the next block's qubits
-    for (int q : next) nf.push_back(q - 1);
-    std::vector<int> free_bits;
-    for (int b = 0; b < n - 1; ++b)
-        if (b < mm.fl || b >= mm.fl + D) free_bits.push_back(b);
-    const int nN = (int)nf.size();
-    std::vector<int> order;
-    bool low = true;  // the next block's bits are among the five lowest free bits
-    for (int b : nf)
-        if (std::find(free_bits.begin(), free_bits.begin() + std::min<size_t>(5, free_bits.size()), b) ==
-            free_bits.begin() + std::min<size_t>(5, free_bits.size()))
-            low = false;
-    if (low) {
-        order = free_bits;
-    } else {
-        for (int b : free_bits)
-            if ((int)order.size() < 5 - nN && std::find(nf.begin(), nf.end(), b) == nf.end()) order.push_back(b);
-        for (int b : nf) order.push_back(b);
-        for (int b : free_bits)
-            if (std::find(order.begin(), order.end(), b) == order.end()) order.push_back(b);
+    const int nb = n - 1;  // f bits
+    std::vector<int> unit(32, -2);
+    std::vector<bool> taken((size_t)std::max(nb, 1), false);
+    auto put = [&](int u, int f) {
+        unit[u] = f;
+        taken[f] = true;
+    };
+    mm.M = M;
+    for (int j = 0; j < M; ++j) {
+        const int q = q_lo + j;
+        if (q == 0) {
+            mm.qpos[j] = -1;
+            continue;
+        }
+        const int u = q_lo == 0 ? q - 1 : (j == 0 ? 8 : (j == 1 ? 9 : 1));
+        mm.qpos[j] = u;
+        put(u, q - 1);
     }
-    mm.nfree = (int)order.size();
-    for (int i = 0; i < mm.nfree; ++i) mm.fb[i] = (int8_t)order[i];
-    mm.nN = nN;
+    mm.nN = (int)next.size();
     uint32_t used = 0;
-    for (int i = 0; i < nN; ++i) {
-        mm.npos[i] = (int)(std::find(order.begin(), order.end(), nf[i]) - order.begin());
-        used |= 1u << mm.npos[i];
+    for (int i = 0; i < mm.nN; ++i) {
+        put(2 + i, next[i] - 1);
+        used |= 1u << (2 + i);
     }
     mm.lmask = 31u & ~used;
+    int f = 0;
+    for (int u = 0; u < nb; ++u) {
+        if (unit[u] != -2) continue;
+        while (f < nb && taken[f]) ++f;
+        put(u, f);
+    }
+    mm.nbits = nb;
+    for (int u = 0; u < 32; ++u) mm.fb[u] = (int8_t)(u < nb ? unit[u] : 0);
     return mm;
 }
 
@@ -518,7 +522,7 @@ qn_status check_status(const qn_batch *h);
 // ---- profiling: one CUDA event pair per timed launch ----
 bool prof_sampled(qn_batch *h, int kind) {
     if (h->prof_period <= 0) return false;
-    if (kind != 0 && kind != 3) return true;
+    if (kind == 1 || kind == 2) return true;
     return (h->prof_counter++ % h->prof_period) == 0;
 }
 
@@ -817,6 +821,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     int32_t active_word = ns;
     int32_t *active_host = &active_word;
     int active = ns;
+    bool final_norms = false;  // the last sweep formed 1 / ||psi||^2 of every state
     const double amp_count = (double)((size_t)1 << n);
     for (int g = n; g < G; ++g) {
         const int gi = grouped ? h->group_at[g] : -1;
@@ -858,14 +863,17 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
             active = *active_host;
-            QN_TRY(prof_begin(h, &ep, 3, (double)active * 16.0 * amp_count));
+            QN_TRY(prof_begin(h, &ep, z.kind == 0 ? 3 : 4, (double)active * 16.0 * amp_count));
             if (z.kind == 0) {
                 e = launch_group_apply(v, sv, gv, active, h->stream);
             } else {
                 std::vector<int> next;
                 if (nz && nz->kind == 1)
                     for (int k = 0; k < nz->s; ++k) next.push_back(nz->sp[k]);
-                e = launch_mix_sweep(v, gv, mix_map(n, z.sp[0], z.s, next), z.s, active, h->stream);
+                MixMap mm = mix_map(n, z.sp[0], z.s, next);
+                mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
+                final_norms = final_norms || mm.final_norm;
+                e = launch_mix_sweep(v, gv, mm, active, h->stream);
             }
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
             QN_TRY(prof_end(h, &ep));
@@ -921,11 +929,11 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     a.c_out = h->c_dbg;
     a.probs = h->probs;
     a.sums = h->sums;
-    QN_TRY(prof_begin(h, &ep, 2, (double)nslots * 8.0 * (double)((size_t)1 << n)));
-    QN_CUDA(launch_observe(vo, a, h->stream));
+    QN_TRY(prof_begin(h, &ep, 2, (double)nslots * (final_norms ? 8.0 : 16.0) * (double)((size_t)1 << n)));
+    if (!final_norms) QN_CUDA(launch_observe(vo, a, h->stream));
     QN_CUDA(launch_probs(vo, a, h->stream));
     QN_TRY(prof_end(h, &ep));
-    h->launches += 2;
+    h->launches += final_norms ? 1 : 2;
     h->sh_slots += nslots;
     QN_CUDA(cudaStreamSynchronize(h->stream));  // order / weights host vectors
     return QN_OK;
@@ -1293,7 +1301,7 @@ qn_status qn_batch_set_profiling(qn_batch *h, int32_t period) {
 
 qn_status qn_profile_read(qn_batch *h, int32_t kind, int64_t *launches, double *ms, double *bytes) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
-    if (kind < 0 || kind > 3) return fail(QN_EINVAL, "kind must be 0, 1, 2 or 3");
+    if (kind < 0 || kind > 4) return fail(QN_EINVAL, "kind must be 0 .. 4");
     QN_TRY(prof_collect(h));
     if (launches) *launches = h->prof_launches[kind];
     if (ms) *ms = h->prof_ms[kind];

@@ -93,16 +93,19 @@ struct GateGroup {
     uint8_t tab[4][256];            // index over S of the stored bits in each byte of y (kind 0)
 };
 
-// Thread -> float4-index map of a mixer-block sweep: bit i of the fiber id goes
-// to f bit fb[i]; the next block's qubits sit on lane bits npos[].
+// Map of a mixer-block sweep from unit bits to float4-index (f) bits.  Unit
+// bits: 0-7 the thread, 8-9 the register index k, 10-11 the sub-tile, 12.. the
+// block; unit bit i covers f bit fb[i] (nbits bits in all).  The block's qubit j
+// sits at qpos[j]: -1 the two halves of a float4 (qubit 0), 0-4 a lane bit,
+// 8-9 a register bit.  The next block's qubits sit on lane bits 2 .. 2 + nN - 1.
 struct MixMap {
     int8_t fb[32];
-    int32_t nfree;    // fiber-id bits
-    int32_t fl;       // lowest f bit of the fiber
-    int32_t has0;     // the block holds qubit 0 (the two halves of a float4)
+    int32_t nbits;
+    int32_t M;        // qubits of this block
+    int32_t qpos[3];
     int32_t nN;       // qubits of the next block (0: no joint to accumulate)
-    int32_t npos[3];  // lane bit of each of them
-    uint32_t lmask;   // lane bits that are none of them
+    uint32_t lmask;   // lane bits that hold none of the next block's qubits
+    int32_t final_norm;  // last sweep of the circuit: also form 1 / ||psi||^2 per state
 };
 
 // Device view of one group step.  Per-slot arrays are indexed by slot; the
@@ -203,8 +206,7 @@ cudaError_t launch_slot_fork(const BatchView &v, const SlotView &sv, int active,
 cudaError_t launch_group_hist(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, double gamma,
                                 cudaStream_t s);
-cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int M, int active,
-                            cudaStream_t s);
+cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s);
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
 // Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n
 // adding d<C>_t / d theta_param into grad[t * nparam + param] (FP64).

@@ -194,13 +194,6 @@ __device__ __forceinline__ float pend_factor(const SweepCtx &c, uint32_t y) {
     return b1 ? hi : lo;
 }
 
-__device__ __forceinline__ void add_bin(float acc[4], int idx, float p) {
-    acc[0] += idx == 0 ? p : 0.0f;
-    acc[1] += idx == 1 ? p : 0.0f;
-    acc[2] += idx == 2 ? p : 0.0f;
-    acc[3] += idx == 3 ? p : 0.0f;
-}
-
 // One branch class of gate g: Pauli `code` (its X part flips frame bits, its Z
 // part signs true bits), then amplitude damping on the gate's qubits with
 // outcomes ji, jj.  m[b0 | b1 << 1] is the weight of the state after the gate
@@ -779,6 +772,54 @@ __global__ void __launch_bounds__(kThreads) k_slot_decide(BatchView v, SlotView 
     allow_dependent_launch();
 }
 
+// |fac * a|^2 with fixed rounding (no contraction), so that the norm pass and
+// the probability pass see bit-identical FP32 values and sum(sigma) = 1 to FP64
+// rounding.
+__device__ __forceinline__ float prob_of(float fac, float re, float im) {
+    return __fmul_rn(__fmul_rn(fac, fac), __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im)));
+}
+
+// Compensated FP32 sums (double-float): FP64 is slow on this part, so the
+// per-amplitude accumulations run as FP32 pairs (hi, lo) with the exact error
+// of every step kept in lo (Knuth's TwoSum; the product error from one FMA),
+// and only short sums are carried this way before they are added in FP64.
+// The _rn intrinsics keep the compiler from contracting or reordering them.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// (hi, lo) += x * (mh + ml), with x * mh split exactly into product and error.
+__device__ __forceinline__ void df_add_prod(float &hi, float &lo, float x, float mh, float ml) {
+    const float p = __fmul_rn(x, mh);
+    const float pe = __fmaf_rn(x, ml, __fmaf_rn(x, mh, -p));
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+// Warp sum of double-float pairs (fixed butterfly order), returned as FP64.
+__device__ __forceinline__ double df_warp_sum(float hi, float lo) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, off), ol = __shfl_xor_sync(0xffffffffu, lo, off);
+        float s, e;
+        two_sum(hi, oh, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(ol, e));
+    }
+    return (double)hi + (double)lo;
+}
+
 // ---------------------------------------------------------------------------
 // Phase-gate groups in shared-prefix mode.  A group is a run of consecutive
 // phase gates of one layer on a qubit set S of at most 8 qubits.  Every op of
@@ -944,6 +985,12 @@ __device__ __forceinline__ void rx_pair(float &ar, float &ai, float &br, float &
     bi = nbi;
 }
 
+// The rotation on both halves of two float4 whose elements differ in the qubit.
+__device__ __forceinline__ void rx_pair4(float4 &a, float4 &b, float c, float s) {
+    rx_pair(a.x, a.y, b.x, b.y, c, s);
+    rx_pair(a.z, a.w, b.z, b.w, c, s);
+}
+
 // The same rotation on a qubit whose two values sit in lanes that differ in
 // `lanebit` (every lane of the warp takes part).
 __device__ __forceinline__ void rx_lanes(float4 &o, int lanebit, float c, float s) {
@@ -1061,83 +1108,142 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     }
 }
 
-// Mixer block sweep (shared-prefix mode): exp(-i beta X) on the M consecutive
-// qubits of the block, held as a register fiber per thread, then the block's
-// drawn Pauli and damping ops as the real factor T[slot][stored bits of the
-// block] (drawn beforehand from the joint after the rotations, so the state is
-// final when written); then the joint of the next block, whose qubits sit on
-// lane bits, as it will be after that block's rotations.
-template <int M, bool HAS0>
-__global__ void __launch_bounds__(kThreads, 2) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
-    constexpr int D = HAS0 ? M - 1 : M;  // fiber bits in float4-index space
-    constexpr int NE = 1 << D;
+// Mixer block sweep (shared-prefix mode): exp(-i beta X) on the block's (up
+// to three consecutive) qubits, then the block's drawn Pauli and damping ops
+// as the real factor T[slot][stored bits of the block] (drawn beforehand from
+// the joint after the rotations, so the state is final when written), then the
+// joint of the next block, whose qubits sit on lane bits, as it will be after
+// that block's rotations.  Same streaming shape as the gate sweeps: kSub
+// sub-tiles of 4 float4 per thread, the next one prefetched into registers.
+__global__ void __launch_bounds__(kThreads, 4) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
     grid_dependency_wait();
     const int slot = blockIdx.y;
+    const int lane = threadIdx.x & 31;
     __shared__ float Df[8];
     __shared__ float hw[(kThreads / 32) * 8];
-    if (threadIdx.x < (1u << M)) Df[threadIdx.x] = gv.T[(size_t)slot * kGroupBins + threadIdx.x].x;
-    const uint32_t u = blockIdx.x * kThreads + threadIdx.x;  // fiber id
-    int64_t fbase = 0;
+    if (threadIdx.x < 8u) Df[threadIdx.x] = threadIdx.x < (1u << mm.M) ? gv.T[(size_t)slot * kGroupBins + threadIdx.x].x : 0.0f;
+    int64_t base = 0;
 #pragma unroll
-    for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
-        if (i < mm.nfree) fbase |= (int64_t)((u >> i) & 1u) << mm.fb[i];
+    for (int i = 0; i < 8; ++i) base |= (int64_t)((threadIdx.x >> i) & 1u) << mm.fb[i];
+#pragma unroll
+    for (int i = 12; i < 32; ++i)
+        if (i < mm.nbits) base |= (int64_t)((blockIdx.x >> (i - 12)) & 1u) << mm.fb[i];
+    const int64_t ko1 = (int64_t)1 << mm.fb[8], ko2 = (int64_t)1 << mm.fb[9];
+    const int64_t so1 = mm.nbits > 10 ? (int64_t)1 << mm.fb[10] : 0, so2 = mm.nbits > 11 ? (int64_t)1 << mm.fb[11] : 0;
+    const int nsub = mm.nbits >= 12 ? 4 : (mm.nbits == 11 ? 2 : 1);
+    // stored bits of the block for element (e, k) of this lane: lanebin | kbin(k) | e * ebin
+    int lanebin = 0, kb1 = 0, kb2 = 0, ebin = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j >= mm.M) break;
+        const int q = mm.qpos[j];
+        if (q < 0) ebin = 1 << j;
+        else if (q == 8) kb1 = 1 << j;
+        else if (q == 9) kb2 = 1 << j;
+        else lanebin |= ((lane >> q) & 1) << j;
+    }
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << v.n));
-    float4 val[NE];
-#pragma unroll
-    for (int k = 0; k < NE; ++k) val[k] = p4[fbase + ((int64_t)k << mm.fl)];
     const float c = gv.grp->c, sn = gv.grp->sn;
+    auto addr = [&](int sub, int k) {
+        return base + ((k & 1) ? ko1 : 0) + ((k & 2) ? ko2 : 0) + ((sub & 1) ? so1 : 0) + ((sub & 2) ? so2 : 0);
+    };
+    float acc = 0.0f;
+    float nh = 0.0f, nl = 0.0f;  // final norm (double-float), same FP32 terms as k_probs forms
+    float4 cur[4], nxt[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cur[k] = p4[addr(0, k)];
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < M; ++j) {
-        if (HAS0 && j == 0) {
+    for (int sub = 0; sub < kSub; ++sub) {
+        if (sub >= nsub) break;
+        if (sub + 1 < nsub) {
 #pragma unroll
-            for (int k = 0; k < NE; ++k) rx_pair(val[k].x, val[k].y, val[k].z, val[k].w, c, sn);
-        } else {
-            const int bit = HAS0 ? j - 1 : j;
+            for (int k = 0; k < 4; ++k) nxt[k] = p4[addr(sub + 1, k)];
+        }
 #pragma unroll
-            for (int k = 0; k < NE; ++k) {
-                if (k & (1 << bit)) continue;
-                float4 &a = val[k];
-                float4 &b = val[k | (1 << bit)];
-                rx_pair(a.x, a.y, b.x, b.y, c, sn);
-                rx_pair(a.z, a.w, b.z, b.w, c, sn);
+        for (int j = 0; j < 3; ++j) {
+            if (j >= mm.M) break;
+            const int q = mm.qpos[j];
+            if (q < 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) rx_pair(cur[k].x, cur[k].y, cur[k].z, cur[k].w, c, sn);
+            } else if (q == 8) {  // register bit 0: elements (0, 1), (2, 3)
+                rx_pair4(cur[0], cur[1], c, sn);
+                rx_pair4(cur[2], cur[3], c, sn);
+            } else if (q == 9) {  // register bit 1: elements (0, 2), (1, 3)
+                rx_pair4(cur[0], cur[2], c, sn);
+                rx_pair4(cur[1], cur[3], c, sn);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) rx_lanes(cur[k], 1 << q, c, sn);
             }
         }
-    }
 #pragma unroll
-    for (int k = 0; k < NE; ++k) {
-        const float f0 = HAS0 ? Df[k << 1] : Df[k], f1 = HAS0 ? Df[(k << 1) | 1] : Df[k];
-        val[k].x *= f0;
-        val[k].y *= f0;
-        val[k].z *= f1;
-        val[k].w *= f1;
-        p4[fbase + ((int64_t)k << mm.fl)] = val[k];
+        for (int k = 0; k < 4; ++k) {
+            const int kb = lanebin | ((k & 1) ? kb1 : 0) | ((k & 2) ? kb2 : 0);
+            const float f0 = Df[kb], f1 = Df[kb | ebin];
+            cur[k].x *= f0;
+            cur[k].y *= f0;
+            cur[k].z *= f1;
+            cur[k].w *= f1;
+            p4[addr(sub, k)] = cur[k];
+            if (mm.final_norm) {
+                df_add(nh, nl, prob_of(1.0f, cur[k].x, cur[k].y));
+                df_add(nh, nl, prob_of(1.0f, cur[k].z, cur[k].w));
+            }
+        }
+        if (mm.nN > 0) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (i >= mm.nN) break;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) rx_lanes(cur[k], 4 << i, c, sn);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                acc += cur[k].x * cur[k].x + cur[k].y * cur[k].y + cur[k].z * cur[k].z + cur[k].w * cur[k].w;
+        }
+        if (sub + 1 < nsub) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+        }
     }
     allow_dependent_launch();
     if (mm.nN > 0) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            if (i >= mm.nN) break;
-#pragma unroll
-            for (int k = 0; k < NE; ++k) rx_lanes(val[k], 1 << mm.npos[i], c, sn);
-        }
-        float acc = 0.0f;
-#pragma unroll
-        for (int k = 0; k < NE; ++k) acc += val[k].x * val[k].x + val[k].y * val[k].y + val[k].z * val[k].z + val[k].w * val[k].w;
-        const int lane = threadIdx.x & 31;
-        int bin = 0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            if (i < mm.nN) bin |= ((lane >> mm.npos[i]) & 1) << i;
-        lane_joint_put(acc, bin, mm.lmask, hw);
+        lane_joint_put(acc, (lane >> 2) & ((1 << mm.nN) - 1), mm.lmask, hw);
         __syncthreads();
         lane_joint_commit(1 << mm.nN, hw, gv.Hnext + (size_t)slot * kGroupBins);
     }
+    if (mm.final_norm) {
+        // block partial -> partials[slot][block]; the slot's last block forms 1/N
+        __shared__ double redd[kThreads / 32];
+        __shared__ int last;
+        const double ws = df_warp_sum(nh, nl);
+        if (lane == 0) redd[threadIdx.x >> 5] = ws;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+            v.partials[((size_t)slot * v.tiles + blockIdx.x) * 4] = sum;
+            __threadfence();
+            const unsigned prev = atomicAdd(&v.counters[slot], 1u);
+            last = prev == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            double N = 0.0;
+            for (unsigned i = 0; i < gridDim.x; ++i) N += __ldcg(v.partials + ((size_t)slot * v.tiles + i) * 4);
+            if (!(N > 0.0) || !isfinite(N)) atomicOr(v.status, 2);
+            v.inv_norm[slot] = 1.0 / N;
+            v.counters[slot] = 0;
+        }
+    }
 }
 
-__device__ __forceinline__ double warp_sum(double x) {
+__device__ __forceinline__ float warp_sumf(float x) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    for (int off = 16; off > 0; off >>= 1) x = __fadd_rn(x, __shfl_xor_sync(0xffffffffu, x, off));
     return x;
 }
 
@@ -1213,40 +1319,48 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
     const uint32_t Fb = st.J ^ st.pend;  // frame once the pending op is applied
     uint32_t fS = 0;
     for (int k = 0; k < ns; ++k) fS |= ((Fb >> gp->sp[k]) & 1u) << k;
-    __shared__ double hd[kGroupBins];  // joint by true bits of S
-    __shared__ double p1m[2 * kMaxGroupEdges];
+    // FP32 throughout (FP64 is slow on this part and the joint comes from FP32
+    // amplitudes); the shared path and every member's own path run the same
+    // operations in the same order, so a member that never leaves the shared
+    // path draws exactly what the shared path drew.
+    __shared__ float hd[kGroupBins];  // joint by true bits of S
+    __shared__ float p1m[2 * kMaxGroupEdges];
     __shared__ int child_base;
     unsigned long long *Hs = gv.Hcur + (size_t)slot * kGroupBins;
-    for (int b = threadIdx.x; b < kGroupBins; b += kThreads) hd[b] = 0.0;
+    for (int b = threadIdx.x; b < kGroupBins; b += kThreads) hd[b] = 0.0f;
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += kThreads) {
-        hd[b ^ fS] = (double)Hs[b] * kHistUnit;
+        hd[b ^ fS] = (float)((double)Hs[b] * kHistUnit);
         Hs[b] = 0ull;  // zero again for the next group that accumulates here
     }
     __syncthreads();
-    double h0[8];
+    float h0[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) h0[r] = hd[lane + 32 * r];
-    const double sg = sqrt(gamma), sg1 = sqrt(1.0 - gamma);
+    const float gf = (float)gamma, omg = (float)(1.0 - gamma);
+    const float sg = (float)sqrt(gamma), sg1 = (float)sqrt(1.0 - gamma);
     if (warp == 0) {  // the identity / no-jump path: P(q = 1) at every damping site
-        double w[8];
+        float w[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) w[r] = h0[r];
         for (int e = 0; e < m; ++e)
             for (int k2 = 0; k2 < nsite; ++k2) {
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
-                double tot = 0.0, one = 0.0;
+                float tot = 0.0f, one = 0.0f;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    tot += w[r];
-                    one += (((lane + 32 * r) >> qi) & 1) ? w[r] : 0.0;
+                    const bool bit = (((uint32_t)(lane + 32 * r) >> qi) & 1u) != 0;
+                    tot = __fadd_rn(tot, w[r]);
+                    one = __fadd_rn(one, bit ? w[r] : 0.0f);
                 }
-                tot = warp_sum(tot);
-                one = warp_sum(one);
-                if (lane == 0) p1m[2 * e + k2] = gamma * one / tot;
+                tot = warp_sumf(tot);
+                one = warp_sumf(one);
+                if (lane == 0) p1m[2 * e + k2] = __fdiv_rn(__fmul_rn(gf, one), tot);
 #pragma unroll
-                for (int r = 0; r < 8; ++r)
-                    if (((lane + 32 * r) >> qi) & 1) w[r] *= 1.0 - gamma;
+                for (int r = 0; r < 8; ++r) {
+                    const bool bit = (((uint32_t)(lane + 32 * r) >> qi) & 1u) != 0;
+                    w[r] = bit ? __fmul_rn(w[r], omg) : w[r];
+                }
             }
     }
     __syncthreads();
@@ -1264,15 +1378,15 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 const size_t gi = (size_t)t * v.G + gp->g0 + e;
                 if (v.branch[gi] & 15) return true;
                 const uint32_t *dw = v.dwords + gi * 2;
-                if (((double)dw[0] + 0.5) * kTwoM32 < p1m[2 * e]) return true;
-                if (nsite == 2 && ((double)dw[1] + 0.5) * kTwoM32 < p1m[2 * e + 1]) return true;
+                if (((double)dw[0] + 0.5) * kTwoM32 < (double)p1m[2 * e]) return true;
+                if (nsite == 2 && ((double)dw[1] + 0.5) * kTwoM32 < (double)p1m[2 * e + 1]) return true;
             }
             return false;
         },
         [&](int r, int i) { evt[r] = i; });
     for (int a = warp; a < ne; a += kThreads / 32) {  // their own draws: one warp each
         const int t = mem[evt[a]];
-        double w[8];
+        float w[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) w[r] = h0[r];
         uint32_t flip = 0;
@@ -1287,19 +1401,20 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
             int jumps = 0;
             for (int k2 = 0; k2 < nsite; ++k2) {
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
-                double tot = 0.0, one = 0.0;
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    tot += w[r];
-                    one += ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) ? w[r] : 0.0;
-                }
-                tot = warp_sum(tot);
-                one = warp_sum(one);
-                const bool j = ((double)dw[k2] + 0.5) * kTwoM32 < gamma * one / tot;
+                float tot = 0.0f, one = 0.0f;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
-                    w[r] = j ? (bit ? w[r] * gamma : 0.0) : (bit ? w[r] * (1.0 - gamma) : w[r]);
+                    tot = __fadd_rn(tot, w[r]);
+                    one = __fadd_rn(one, bit ? w[r] : 0.0f);
+                }
+                tot = warp_sumf(tot);
+                one = warp_sumf(one);
+                const bool j = ((double)dw[k2] + 0.5) * kTwoM32 < (double)__fdiv_rn(__fmul_rn(gf, one), tot);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
+                    w[r] = j ? (bit ? __fmul_rn(w[r], gf) : 0.0f) : (bit ? __fmul_rn(w[r], omg) : w[r]);
                 }
                 if (j) {
                     flip ^= 1u << qi;
@@ -1372,15 +1487,15 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
             if (lane == 0) atomicOr(v.status, 4);
             continue;
         }
-        double ar[8], ai[8], w[8];
+        float ar[8], ai[8], w[8];
         uint32_t flip = 0;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-            ar[r] = 1.0;
-            ai[r] = 0.0;
+            ar[r] = 1.0f;
+            ai[r] = 0.0f;
             w[r] = h0[r];
         }
-        const double gc = gp->c, gs = gp->sn;
+        const float gc = gp->c, gs = gp->sn;
         for (int e = 0; e < m; ++e) {
             const int code = (int)((key >> (6 * e)) & 15u);
             const int qi = gp->ei[e], qj = gp->ej[e];
@@ -1390,7 +1505,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 const uint32_t cb = (uint32_t)(lane + 32 * r) ^ flip;
                 const uint32_t ci = (cb >> qi) & 1u, cj = (cb >> qj) & 1u;
                 if (kind == 0 && ci != cj) {
-                    const double nr = ar[r] * gc + ai[r] * gs, ni = ai[r] * gc - ar[r] * gs;
+                    const float nr = ar[r] * gc + ai[r] * gs, ni = ai[r] * gc - ar[r] * gs;
                     ar[r] = nr;
                     ai[r] = ni;
                 }
@@ -1406,7 +1521,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> q) & 1u) != 0;
-                    const double kf = j ? (bit ? sg : 0.0) : (bit ? sg1 : 1.0);
+                    const float kf = j ? (bit ? sg : 0.0f) : (bit ? sg1 : 1.0f);
                     ar[r] *= kf;
                     ai[r] *= kf;
                     w[r] *= kf * kf;
@@ -1414,17 +1529,17 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 if (j) flip ^= 1u << q;
             }
         }
-        double N = 0.0;
+        float N = 0.0f;
 #pragma unroll
         for (int r = 0; r < 8; ++r) N += w[r];
-        N = warp_sum(N);
-        const double sc = 1.0 / sqrt(N);
-        if (lane == 0 && !(N > 0.0 && isfinite(sc))) atomicOr(v.status, 1);
+        N = warp_sumf(N);
+        const float sc = 1.0f / sqrtf(N);
+        if (lane == 0 && !(N > 0.0f && isfinite(sc))) atomicOr(v.status, 1);
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int b = lane + 32 * r;
             if (b < nbins)
-                gv.T[(size_t)target * kGroupBins + (b ^ fS)] = make_float2((float)(ar[r] * sc), (float)(ai[r] * sc));
+                gv.T[(size_t)target * kGroupBins + (b ^ fS)] = make_float2(ar[r] * sc, ai[r] * sc);
         }
         if (lane == 0) {
             uint32_t qflip = 0;
@@ -1487,12 +1602,6 @@ __global__ void k_fork_finish(SlotView sv) {
 // order, and sum_x |psi_t,x|^2 C(x) is reduced per (t, block); its last block
 // forms <C>_t and adds S1, S2 in trajectory order.
 // ---------------------------------------------------------------------------
-// |fac * a|^2 with fixed rounding (no contraction), so that the norm pass and
-// the probability pass see bit-identical FP32 values and sum(sigma) = 1 to FP64
-// rounding.
-__device__ __forceinline__ float prob_of(float fac, float re, float im) {
-    return __fmul_rn(__fmul_rn(fac, fac), __fadd_rn(__fmul_rn(re, re), __fmul_rn(im, im)));
-}
 
 __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
     const int t = blockIdx.y;
@@ -1508,7 +1617,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
     c.pq1 = st.pq1;
     for (int k = 0; k < 4; ++k) c.f[k] = st.f[k];
     const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)t << n));
-    double sn = 0.0;
+    float sh = 0.0f, sl = 0.0f;
 #pragma unroll
     for (int k = 0; k < kF4PerThread; ++k) {
         const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
@@ -1516,13 +1625,12 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
             const float4 val = p4[f];
             const uint32_t y = (uint32_t)(2 * f);
             const float f0 = pend_factor(c, y), f1 = pend_factor(c, y | 1u);
-            sn += (double)prob_of(f0, val.x, val.y);
-            sn += (double)prob_of(f1, val.z, val.w);
+            df_add(sh, sl, prob_of(f0, val.x, val.y));
+            df_add(sh, sl, prob_of(f1, val.z, val.w));
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) sn += __shfl_xor_sync(0xffffffffu, sn, off);
+    const double sn = df_warp_sum(sh, sl);
     if (lane == 0) redd[warp] = sn;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1559,59 +1667,97 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kX = 2 * kF4PerThread;  // basis states per thread
     __shared__ float cw[kAccChunk][kThreads / 32];
+    __shared__ int c_sl[kAccChunk], c_pq0[kAccChunk], c_pq1[kAccChunk];
+    __shared__ uint32_t c_Ff[kAccChunk], c_pend[kAccChunk];
+    __shared__ float4 c_f[kAccChunk];
+    __shared__ float c_ih[kAccChunk], c_il[kAccChunk];
+    __shared__ float s_cut[kX][kThreads];
+    __shared__ double s_acc[kX][kThreads];
     __shared__ int last;
-    int64_t fp[kF4PerThread];
-    float cut[2 * kF4PerThread];
-    double acc[2 * kF4PerThread];
+    const int64_t f0 = (int64_t)xb * kTileF4 + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < kF4PerThread; ++k) {
-        fp[k] = (int64_t)xb * kTileF4 + threadIdx.x + k * kThreads;
-        acc[2 * k] = acc[2 * k + 1] = 0.0;
+    for (int k = 0; k < kF4PerThread; ++k)
         for (int e = 0; e < 2; ++e) {
-            const uint32_t x = (uint32_t)(2 * fp[k] + e);
+            const uint32_t x = (uint32_t)(2 * (f0 + k * kThreads) + e);
             int cnt = 0;
             for (int j = 0; j < a.num_edges; ++j) {
                 const int2 ed = a.edges[j];
                 cnt += (int)(((x >> ed.x) ^ (x >> ed.y)) & 1u);
             }
-            cut[2 * k + e] = (float)cnt;
+            s_cut[2 * k + e][threadIdx.x] = (float)cnt;
+            s_acc[2 * k + e][threadIdx.x] = 0.0;
         }
-    }
+    auto load_state = [&](int ci, float4 (&val)[kF4PerThread]) {
+        const uint32_t Ff = c_Ff[ci];
+        const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)c_sl[ci] << n));
+#pragma unroll
+        for (int k = 0; k < kF4PerThread; ++k)
+            if (f0 + k * kThreads < nf) val[k] = p4[(f0 + k * kThreads) ^ (int64_t)(Ff >> 1)];
+    };
+    // sigma terms of state ci into (ah, al); returns this thread's sum of p * C(x)
+    auto take_state = [&](int ci, float4 (&val)[kF4PerThread], float (&ah)[kX], float (&al)[kX]) {
+        const uint32_t Ff = c_Ff[ci], pend = c_pend[ci];
+        const int pq0 = c_pq0[ci], pq1 = c_pq1[ci];
+        const float4 fs = c_f[ci];
+        const float ih = c_ih[ci], il = c_il[ci];
+        float cp = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kF4PerThread; ++k) {
+            if (f0 + k * kThreads >= nf) continue;
+            float4 vv = val[k];
+            if (Ff & 1u) vv = make_float4(vv.z, vv.w, vv.x, vv.y);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const uint32_t x = (uint32_t)(2 * (f0 + k * kThreads) + e);
+                const uint32_t tb = x ^ pend;
+                const uint32_t b0 = (tb >> pq0) & 1u, b1 = (tb >> pq1) & 1u;
+                const float fac = b1 ? (b0 ? fs.w : fs.z) : (b0 ? fs.y : fs.x);
+                const float re = e ? vv.z : vv.x, im = e ? vv.w : vv.y;
+                const float pr = prob_of(fac, re, im);
+                if (a.probs) df_add_prod(ah[2 * k + e], al[2 * k + e], pr, ih, il);
+                cp += pr * s_cut[2 * k + e][threadIdx.x];
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
+        if (lane == 0) cw[ci][warp] = cp;
+    };
     for (int t0c = 0; t0c < v.b; t0c += kAccChunk) {
         const int tend = min(v.b, t0c + kAccChunk);
-        for (int tt = t0c; tt < tend; ++tt) {
+        // the chunk's per-state parameters, once per block
+        if ((int)threadIdx.x < tend - t0c) {
+            const int tt = t0c + threadIdx.x;
             const int sl = a.order ? a.order[tt] : tt;
-            const TrajState s = v.st[sl];
-            const uint32_t Ff = v.frame_x[(size_t)sl * (v.G + 1) + v.G] ^ s.J ^ s.pend;
+            const TrajState st = v.st[sl];
+            c_sl[threadIdx.x] = sl;
+            c_Ff[threadIdx.x] = v.frame_x[(size_t)sl * (v.G + 1) + v.G] ^ st.J ^ st.pend;
+            c_pend[threadIdx.x] = st.pend;
+            c_pq0[threadIdx.x] = st.pq0;
+            c_pq1[threadIdx.x] = st.pq1;
+            c_f[threadIdx.x] = make_float4(st.f[0], st.f[1], st.f[2], st.f[3]);
             const double inv = v.inv_norm[sl] * (a.weights ? a.weights[sl] : 1.0);
-            const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)sl << n));
-            float cp = 0.0f;
-#pragma unroll
-            for (int k = 0; k < kF4PerThread; ++k) {
-                if (fp[k] < nf) {
-                    const int64_t f = fp[k] ^ (int64_t)(Ff >> 1);
-                    float4 val = p4[f];
-                    if (Ff & 1u) val = make_float4(val.z, val.w, val.x, val.y);
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const uint32_t x = (uint32_t)(2 * fp[k] + e);
-                        const uint32_t tb = x ^ s.pend;
-                        const uint32_t b0 = (tb >> s.pq0) & 1u, b1 = (tb >> s.pq1) & 1u;
-                        const float fac = b1 ? (b0 ? s.f[3] : s.f[2]) : (b0 ? s.f[1] : s.f[0]);
-                        const float re = e ? val.z : val.x, im = e ? val.w : val.y;
-                        const float pr = prob_of(fac, re, im);
-                        if (a.probs) acc[2 * k + e] = fma((double)pr, inv, acc[2 * k + e]);
-                        cp += pr * cut[2 * k + e];
-                    }
-                }
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
-            if (lane == 0) cw[tt - t0c][warp] = cp;
+            const float ih = (float)inv;
+            c_ih[threadIdx.x] = ih;
+            c_il[threadIdx.x] = (float)(inv - (double)ih);
         }
         __syncthreads();
-        if (threadIdx.x < tend - t0c) {
+        float ah[kX], al[kX];  // sigma terms of this chunk (double-float)
+#pragma unroll
+        for (int i = 0; i < kX; ++i) ah[i] = al[i] = 0.0f;
+        const int cn = tend - t0c;
+        for (int ci = 0; ci < cn; ci += 2) {  // two states per step: eight loads in flight
+            float4 va[kF4PerThread], vb[kF4PerThread];
+            load_state(ci, va);
+            if (ci + 1 < cn) load_state(ci + 1, vb);
+            take_state(ci, va, ah, al);
+            if (ci + 1 < cn) take_state(ci + 1, vb, ah, al);
+        }
+#pragma unroll
+        for (int i = 0; i < kX; ++i) s_acc[i][threadIdx.x] += (double)ah[i] + (double)al[i];
+        __syncthreads();
+        if ((int)threadIdx.x < cn) {
             double sum = 0.0;
             for (int w = 0; w < kThreads / 32; ++w) sum += (double)cw[threadIdx.x][w];
             a.cpart[(size_t)(t0c + threadIdx.x) * xblocks + xb] = sum;
@@ -1621,9 +1767,9 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
     if (a.probs) {
 #pragma unroll
         for (int k = 0; k < kF4PerThread; ++k)
-            if (fp[k] < nf) {
-                a.probs[2 * fp[k]] += acc[2 * k];
-                a.probs[2 * fp[k] + 1] += acc[2 * k + 1];
+            if (f0 + k * kThreads < nf) {
+                a.probs[2 * (f0 + k * kThreads)] += s_acc[2 * k][threadIdx.x];
+                a.probs[2 * (f0 + k * kThreads) + 1] += s_acc[2 * k + 1][threadIdx.x];
             }
     }
     __threadfence();
@@ -2165,18 +2311,9 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
     return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
 }
 
-cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int M, int active,
-                            cudaStream_t s) {
-    const bool has0 = mm.has0 != 0;
-    const unsigned blocks = (unsigned)(((int64_t)1 << mm.nfree) / kThreads);
-    const dim3 grid(blocks, (unsigned)active);
-    if (M == 3) return has0 ? launch_pdl(k_mix_sweep<3, true>, grid, dim3(kThreads), s, v, gv, mm)
-                            : launch_pdl(k_mix_sweep<3, false>, grid, dim3(kThreads), s, v, gv, mm);
-    if (M == 2) return has0 ? launch_pdl(k_mix_sweep<2, true>, grid, dim3(kThreads), s, v, gv, mm)
-                            : launch_pdl(k_mix_sweep<2, false>, grid, dim3(kThreads), s, v, gv, mm);
-    if (M == 1) return has0 ? launch_pdl(k_mix_sweep<1, true>, grid, dim3(kThreads), s, v, gv, mm)
-                            : launch_pdl(k_mix_sweep<1, false>, grid, dim3(kThreads), s, v, gv, mm);
-    return cudaErrorInvalidValue;
+cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
+    const unsigned blocks = mm.nbits > 12 ? 1u << (mm.nbits - 12) : 1u;
+    return launch_pdl(k_mix_sweep, dim3(blocks, (unsigned)active), dim3(kThreads), s, v, gv, mm);
 }
 
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
