@@ -154,7 +154,7 @@ struct qn_batch {
     float2 *gv_T = nullptr;
     TrajState *gv_stprev = nullptr;
     uint64_t *gv_ekey = nullptr;
-    int32_t *gv_i32 = nullptr;  // [5][gv_cap]: evt, rep, lead, lstart, lcount
+    int32_t *gv_i32 = nullptr;  // [6][gv_cap]: evt, rep, lead, lstart, lcount, parent
     int64_t gv_cap = 0;
     float2 *lambda = nullptr;  // adjoint vectors (qn_grad), allocated on first use
     double *grad = nullptr;    // [K][2p] per-trajectory gradients
@@ -728,7 +728,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
         QN_TRY(alloc_t(h, &h->gv_T, (size_t)kc * kGroupBins));
         QN_TRY(alloc_t(h, &h->gv_stprev, (size_t)kc));
         QN_TRY(alloc_t(h, &h->gv_ekey, (size_t)kc));
-        QN_TRY(alloc_t(h, &h->gv_i32, (size_t)5 * kc));
+        QN_TRY(alloc_t(h, &h->gv_i32, (size_t)6 * kc));
         h->gv_cap = kc;
     }
     if (grouped && h->gr_cap < (int64_t)h->groups.size()) {
@@ -831,11 +831,12 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             const GateGroup &z = h->groups[gi];
             const int ng = (int)h->groups.size();
             const GateGroup *nz = gi + 1 < ng && h->groups[gi + 1].g0 == z.g0 + z.m ? &h->groups[gi + 1] : nullptr;
-            const bool first = z.kind == 0 && (gi == 0 || h->groups[gi - 1].kind != 0 ||
-                                               h->groups[gi - 1].g0 + h->groups[gi - 1].m != z.g0);
+            // a phase group needs its own joint pass unless the sweep before it
+            // (a phase group or the previous layer's last mixer block) formed it
+            const bool first = z.kind == 0 && (gi == 0 || h->groups[gi - 1].g0 + h->groups[gi - 1].m != z.g0);
             GroupView gv;
             gv.grp = h->gr_dev + gi;
-            gv.next = nz && nz->kind == 0 && z.kind == 0 ? h->gr_dev + gi + 1 : nullptr;
+            gv.next = nz && nz->kind == 0 ? h->gr_dev + gi + 1 : nullptr;
             gv.vq = nz && nz->kind == 1 && z.kind == 0 ? nz->s : 0;
             gv.vc = nz ? nz->c : 1.0f;
             gv.vs = nz ? nz->sn : 0.0f;
@@ -849,6 +850,9 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             gv.lead = h->gv_i32 + 2 * h->gv_cap;
             gv.lstart = h->gv_i32 + 3 * h->gv_cap;
             gv.lcount = h->gv_i32 + 4 * h->gv_cap;
+            gv.parent = h->gv_i32 + 5 * h->gv_cap;
+            gv.src = nullptr;
+            gv.slot_base = 0;
             cudaError_t e = cudaSuccess;
             if (first) {
                 QN_TRY(prof_begin(h, &ep, 3, (double)active * 8.0 * amp_count));
@@ -862,23 +866,34 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                                                       h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
+            const int old_active = active;
             active = *active_host;
-            QN_TRY(prof_begin(h, &ep, z.kind == 0 ? 3 : 4, (double)active * 16.0 * amp_count));
-            if (z.kind == 0) {
-                e = launch_group_apply(v, sv, gv, active, h->stream);
-            } else {
+            MixMap mm;
+            if (z.kind == 1) {
                 std::vector<int> next;
                 if (nz && nz->kind == 1)
                     for (int k = 0; k < nz->s; ++k) next.push_back(nz->sp[k]);
-                MixMap mm = mix_map(n, z.sp[0], z.s, next);
+                mm = mix_map(n, z.sp[0], z.s, next);
                 mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
                 final_norms = final_norms || mm.final_norm;
-                e = launch_mix_sweep(v, gv, mm, active, h->stream);
+            }
+            // the slots forked here first, reading their parents' states; then
+            // the older slots in place (the launch order keeps parents unread-over)
+            QN_TRY(prof_begin(h, &ep, z.kind == 0 ? 3 : 4, (double)active * 16.0 * amp_count));
+            for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+                const int first = part == 0 ? old_active : 0;
+                const int count = part == 0 ? active - old_active : old_active;
+                if (count <= 0) continue;
+                gv.src = part == 0 ? gv.parent : nullptr;
+                gv.slot_base = first;
+                e = z.kind == 0 ? launch_group_apply(v, sv, gv, count, h->stream)
+                                : launch_mix_sweep(v, gv, mm, count, h->stream);
+                h->launches += 1;
             }
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
             QN_TRY(prof_end(h, &ep));
             h->sweep_bytes += (double)active * 16.0 * amp_count;
-            h->launches += 4;
+            h->launches += 2;  // decide, finish
             g += z.m - 1;
             continue;
         }

@@ -113,6 +113,10 @@ struct MixMap {
 struct GroupView {
     const GateGroup *grp;    // group applied by this step
     const GateGroup *next;   // phase group whose joint the apply sweep accumulates, or nullptr
+    const int32_t *src;      // per slot: the state a sweep reads (a forked slot's parent), or
+                             // nullptr: every slot reads its own state
+    int32_t slot_base;       // first slot of the launch (blockIdx.y + slot_base)
+    int32_t *parent;         // [max_slots] decide writes each new slot's parent here
     int32_t vq;              // > 0: the apply sweep accumulates instead the joint of the
                              // mixer block on qubits 0 .. vq-1 after rotations (vc, vs)
     float vc, vs;

@@ -1028,7 +1028,8 @@ __device__ __forceinline__ void lane_joint_commit(int nb, const float *hw, unsig
 // inside a float4, qubits 1 and 2 are lane bits 0 and 1 of the sweep layout.
 __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupView gv) {
     grid_dependency_wait();
-    const int slot = blockIdx.y, tile = blockIdx.x;
+    const int slot = blockIdx.y + gv.slot_base, tile = blockIdx.x;
+    const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
     const GateGroup *gp = gv.grp;
     const GateGroup *nx = gv.next;
     const int vq = gv.vq;
@@ -1045,6 +1046,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     __syncthreads();
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
+    const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)from << n));
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << n));
     const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
     const SweepCtx c = pending_ctx(gv.st_prev[slot]);
@@ -1055,11 +1057,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     HistRun run;
     float va0 = 0.0f, va1 = 0.0f;
     float4 cur[kF4PerThread], nxt[kF4PerThread];
-    load_tile(cur, p4, fbase, nf);
+    load_tile(cur, q4, fbase, nf);
 #pragma unroll
     for (int sub = 0; sub < kSub; ++sub) {
         const int64_t f0 = fbase + (int64_t)sub * kTileF4;
-        if (sub + 1 < kSub) load_tile(nxt, p4, f0 + kTileF4, nf);
+        if (sub + 1 < kSub) load_tile(nxt, q4, f0 + kTileF4, nf);
 #pragma unroll
         for (int k = 0; k < kF4PerThread; ++k) {
             const int64_t f = f0 + k * kThreads;
@@ -1117,11 +1119,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
 // sub-tiles of 4 float4 per thread, the next one prefetched into registers.
 __global__ void __launch_bounds__(kThreads, 4) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
     grid_dependency_wait();
-    const int slot = blockIdx.y;
+    const int slot = blockIdx.y + gv.slot_base;
+    const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
     const int lane = threadIdx.x & 31;
+    const GateGroup *nx = gv.next;  // next layer's first phase group: its joint is formed here
     __shared__ float Df[8];
-    __shared__ float hw[(kThreads / 32) * 8];
+    __shared__ float hw[kThreads / 32][kGroupBins];
     if (threadIdx.x < 8u) Df[threadIdx.x] = threadIdx.x < (1u << mm.M) ? gv.T[(size_t)slot * kGroupBins + threadIdx.x].x : 0.0f;
+    if (nx)
+        for (int i = threadIdx.x; i < (kThreads / 32) * kGroupBins; i += kThreads) (&hw[0][0])[i] = 0.0f;
     int64_t base = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) base |= (int64_t)((threadIdx.x >> i) & 1u) << mm.fb[i];
@@ -1142,23 +1148,40 @@ __global__ void __launch_bounds__(kThreads, 4) k_mix_sweep(BatchView v, GroupVie
         else if (q == 9) kb2 = 1 << j;
         else lanebin |= ((lane >> q) & 1) << j;
     }
+    const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)from << v.n));
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << v.n));
     const float c = gv.grp->c, sn = gv.grp->sn;
     auto addr = [&](int sub, int k) {
         return base + ((k & 1) ? ko1 : 0) + ((k & 2) ? ko2 : 0) + ((sub & 1) ? so1 : 0) + ((sub & 2) ? so2 : 0);
     };
+    // bins of the next phase group: this thread's part, the (k, sub) parts and
+    // the float4 half; lanes that differ only outside its qubits are summed first
+    GroupBins gn{0, 0u};
+    int nk1 = 0, nk2 = 0, ns1 = 0, ns2 = 0, ne1 = 0;
+    if (nx) {
+        gn.base = group_bin(nx, (uint32_t)(2 * base));
+        nk1 = group_bin(nx, (uint32_t)(2 * ko1));
+        nk2 = group_bin(nx, (uint32_t)(2 * ko2));
+        ns1 = group_bin(nx, (uint32_t)(2 * so1));
+        ns2 = group_bin(nx, (uint32_t)(2 * so2));
+        ne1 = group_bin(nx, 1u);
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            if (group_bin(nx, 2u << mm.fb[i]) == 0) gn.lmask |= 1u << i;
+    }
+    HistRun run;
     float acc = 0.0f;
     float nh = 0.0f, nl = 0.0f;  // final norm (double-float), same FP32 terms as k_probs forms
     float4 cur[4], nxt[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cur[k] = p4[addr(0, k)];
+    for (int k = 0; k < 4; ++k) cur[k] = q4[addr(0, k)];
     __syncthreads();
 #pragma unroll
     for (int sub = 0; sub < kSub; ++sub) {
         if (sub >= nsub) break;
         if (sub + 1 < nsub) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) nxt[k] = p4[addr(sub + 1, k)];
+            for (int k = 0; k < 4; ++k) nxt[k] = q4[addr(sub + 1, k)];
         }
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -1187,6 +1210,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_mix_sweep(BatchView v, GroupVie
             cur[k].z *= f1;
             cur[k].w *= f1;
             p4[addr(sub, k)] = cur[k];
+            if (nx)
+                hist_push(hw[threadIdx.x >> 5], gn, ne1, ((k & 1) ? nk1 : 0) | ((k & 2) ? nk2 : 0) |
+                                                             ((sub & 1) ? ns1 : 0) | ((sub & 2) ? ns2 : 0),
+                          cur[k].x * cur[k].x + cur[k].y * cur[k].y, cur[k].z * cur[k].z + cur[k].w * cur[k].w, run);
             if (mm.final_norm) {
                 df_add(nh, nl, prob_of(1.0f, cur[k].x, cur[k].y));
                 df_add(nh, nl, prob_of(1.0f, cur[k].z, cur[k].w));
@@ -1210,9 +1237,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_mix_sweep(BatchView v, GroupVie
     }
     allow_dependent_launch();
     if (mm.nN > 0) {
-        lane_joint_put(acc, (lane >> 2) & ((1 << mm.nN) - 1), mm.lmask, hw);
+        lane_joint_put(acc, (lane >> 2) & ((1 << mm.nN) - 1), mm.lmask, &hw[0][0]);
         __syncthreads();
-        lane_joint_commit(1 << mm.nN, hw, gv.Hnext + (size_t)slot * kGroupBins);
+        lane_joint_commit(1 << mm.nN, &hw[0][0], gv.Hnext + (size_t)slot * kGroupBins);
+    }
+    if (nx) {
+        hist_close(hw[threadIdx.x >> 5], gn, ne1, run);
+        __syncthreads();
+        hist_commit(&hw[0][0], 1 << nx->s, gv.Hnext + (size_t)slot * kGroupBins);
     }
     if (mm.final_norm) {
         // block partial -> partials[slot][block]; the slot's last block forms 1/N
@@ -1552,10 +1584,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
             gv.st_prev[target] = st;
             v.st[target] = nst;
             sv.range[target] = make_int2(start, count);
-            if (c > 0) {
-                const int f = atomicAdd(sv.fork_count, 1);
-                sv.forks[f] = make_int2(slot, target);
-            }
+            if (c > 0) gv.parent[target] = slot;  // its first sweep reads the parent's state
         }
     }
     allow_dependent_launch();
@@ -2305,8 +2334,6 @@ cudaError_t launch_group_hist(const BatchView &v, const SlotView &, const GroupV
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, double gamma,
                                 cudaStream_t s) {
     cudaError_t e = launch_pdl(k_group_decide, dim3((unsigned)active), dim3(kThreads), s, v, sv, gv, gamma);
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(k_fork_copy, dim3(persistent_blocks()), dim3(kThreads), s, v, sv);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
 }
