@@ -322,7 +322,7 @@ def gpu_arm(args):
         fused = main_mode[1] and w.damping == 0
         grouped = sharing and main_mode[1] and main["groups"]["launches"] > 0
         blocks = grouped and main["mixers"]["launches"] > 0
-        kname = "k_mix_sweep (mixer blocks of 3 qubits over live prefix states, 16 B per amplitude)" if blocks else \
+        kname = "k_mix_sweep (mixer blocks of 4 qubits over live prefix states, 16 B per amplitude)" if blocks else \
             "k_slot_sweep (mixer gate sweeps over live prefix states)" if grouped else \
             "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
             ("k_fused_sweep (fused layer sweeps, 16 B per amplitude)" if fused else
@@ -334,8 +334,8 @@ def gpu_arm(args):
             "config": config_of(w, {
                 "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
                 "mode": ("shared-prefix: one statevector per distinct Kraus prefix, all trajectories in one "
-                         "prefix tree" + ("; phase gates applied in groups on <= 8 qubits (one joint pass per "
-                                          "layer, one sweep per group), mixer gates one sweep each" if grouped
+                         "prefix tree" + ("; phase gates applied in groups on <= 9 qubits and mixer rotations "
+                                          "in blocks of 4 qubits, one sweep per group or block" if grouped
                                           else "; one sweep per gate")) if sharing else
                         (f"fused layers: ceil(n/3) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused
                          else f"one statevector per trajectory, one sweep per gate, {w.batch} per launch")}),

@@ -116,11 +116,13 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
  * sweep, and the mixer rotations are applied three qubits per sweep.  Needs
  * at most 64 edges; otherwise gates are swept one by one.  With damping == 0
  * fusion takes precedence over shared-prefix mode.  With damping, fusion acts
- * in shared-prefix mode only: consecutive phase gates of a layer on at most 8
+ * in shared-prefix mode only: consecutive phase gates of a layer on at most 9
  * qubits form a group whose damping branches are all drawn from one joint
- * distribution of those qubits, and the group is applied in one sweep (the
- * same Kraus draws as gate by gate; the state differs by FP32 rounding).
- * Without shared-prefix mode damping runs are swept gate by gate. */
+ * distribution of those qubits, and the group is applied in one sweep; for
+ * n >= 12 the mixer rotations go four qubits per sweep, their damping drawn
+ * from the joint of those qubits after the rotations (the same Kraus draws as
+ * gate by gate; the state differs by FP32 rounding).  Without shared-prefix
+ * mode damping runs are swept gate by gate. */
 qn_status qn_batch_set_fusion(qn_batch *h, int32_t on);
 
 /* Shared-prefix mode (on = 1; default 0).  Trajectories whose Kraus strings

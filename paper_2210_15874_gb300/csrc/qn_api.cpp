@@ -381,7 +381,7 @@ void build_gates(qn_batch *h) {
 bool mixer_blocks_fit(int n, int E) { return n >= 12 && E > 0; }
 
 // Phase-gate groups of every layer: greedy runs of consecutive ZZ gates whose
-// qubits number at most 8 (at most kMaxGroupEdges gates, so that a member's
+// qubits number at most kMaxGroupQubits (at most kMaxGroupEdges gates, so that a member's
 // outcome string fits 6 bits per gate in 64 bits).
 void build_groups(qn_batch *h) {
     const int n = h->n, E = (int)h->edges.size() / 2;
@@ -397,7 +397,7 @@ void build_groups(qn_batch *h) {
             uint32_t S = 0;
             while (g < base + E && z.m < kMaxGroupEdges) {
                 const uint32_t S2 = S | (1u << h->gates[g].q0) | (1u << h->gates[g].q1);
-                if (__builtin_popcount(S2) > 8) break;
+                if (__builtin_popcount(S2) > kMaxGroupQubits) break;
                 S = S2;
                 ++z.m;
                 ++g;
@@ -422,19 +422,19 @@ void build_groups(qn_batch *h) {
                         const int q = 8 * byte + bit;
                         if (((v >> bit) & 1) && q < n && ((S >> q) & 1u)) bins |= 1 << local[q];
                     }
-                    z.tab[byte][v] = (uint8_t)bins;
+                    z.tab[byte][v] = (uint16_t)bins;
                 }
             h->group_at[z.g0] = (int32_t)h->groups.size();
             h->groups.push_back(z);
         }
         if (!mixer_blocks_fit(n, E)) continue;
-        // mixer rotations in blocks of three consecutive qubits
-        for (int q = 0; q < n; q += 3) {
+        // mixer rotations in blocks of kMixQ consecutive qubits
+        for (int q = 0; q < n; q += kMixQ) {
             GateGroup z;
             std::memset(&z, 0, sizeof z);
             z.kind = 1;
             z.g0 = base + E + q;
-            z.m = z.s = std::min(3, n - q);
+            z.m = z.s = std::min(kMixQ, n - q);
             for (int k = 0; k < z.m; ++k) {
                 z.sp[k] = q + k;
                 z.ei[k] = z.ej[k] = k;
@@ -447,49 +447,47 @@ void build_groups(qn_batch *h) {
     }
 }
 
-// Unit -> float4-index map of the sweep of the mixer block on qubits
-// q_lo .. q_lo + M - 1, with the qubits `next` of the following block on lane
-// bits 2.. (so that the sweep can form that block's joint with warp shuffles).
-// Qubit 0 is the pair inside a float4; the block's other qubits go to lane bits
-// 0, 1 when the block holds qubit 0 (the plain tile layout), else to the two
-// register bits and lane bit 1; every other unit bit takes the lowest f bit
-// left, so that lane bit 0 pairs neighbouring float4 whenever it can.
+// Tile map of the sweep of the mixer block on qubits q_lo .. q_lo + M - 1
+// whose next block holds the qubits `next`: A bits = the block's f bits (qubit
+// q sits on f bit q - 1; qubit 0 is the pair inside a float4), B bits = the
+// next block's; L = the kMixL lowest f bits left (consecutive lanes read
+// neighbouring float4 whenever the low f bits are free); then A and B are
+// filled up to kMixQ with the lowest f bits left; every other f bit numbers
+// tiles.
 MixMap mix_map(int n, int q_lo, int M, const std::vector<int> &next) {
     MixMap mm;
     std::memset(&mm, 0, sizeof mm);
     const int nb = n - 1;  // f bits
-    std::vector<int> unit(32, -2);
     std::vector<bool> taken((size_t)std::max(nb, 1), false);
-    auto put = [&](int u, int f) {
-        unit[u] = f;
+    auto lowest_free = [&]() {
+        int f = 0;
+        while (f < nb && taken[f]) ++f;
         taken[f] = true;
+        return f;
     };
     mm.M = M;
-    for (int j = 0; j < M; ++j) {
-        const int q = q_lo + j;
-        if (q == 0) {
-            mm.qpos[j] = -1;
-            continue;
-        }
-        const int u = q_lo == 0 ? q - 1 : (j == 0 ? 8 : (j == 1 ? 9 : 1));
-        mm.qpos[j] = u;
-        put(u, q - 1);
-    }
+    mm.has0 = q_lo == 0;
     mm.nN = (int)next.size();
-    uint32_t used = 0;
-    for (int i = 0; i < mm.nN; ++i) {
-        put(2 + i, next[i] - 1);
-        used |= 1u << (2 + i);
+    std::vector<int> A, B;
+    for (int j = 0; j < M; ++j)
+        if (q_lo + j > 0) {
+            A.push_back(q_lo + j - 1);
+            taken[q_lo + j - 1] = true;
+        }
+    for (int q : next) {
+        B.push_back(q - 1);
+        taken[q - 1] = true;
     }
-    mm.lmask = 31u & ~used;
-    int f = 0;
-    for (int u = 0; u < nb; ++u) {
-        if (unit[u] != -2) continue;
-        while (f < nb && taken[f]) ++f;
-        put(u, f);
+    for (int i = 0; i < kMixL; ++i) mm.fL[i] = (int8_t)lowest_free();
+    while ((int)A.size() < kMixQ) A.push_back(lowest_free());
+    while ((int)B.size() < kMixQ) B.push_back(lowest_free());
+    for (int i = 0; i < kMixQ; ++i) {
+        mm.fA[i] = (int8_t)A[i];
+        mm.fB[i] = (int8_t)B[i];
     }
-    mm.nbits = nb;
-    for (int u = 0; u < 32; ++u) mm.fb[u] = (int8_t)(u < nb ? unit[u] : 0);
+    mm.ntile = 0;
+    for (int f = 0; f < nb; ++f)
+        if (!taken[f]) mm.ftile[mm.ntile++] = (int8_t)f;
     return mm;
 }
 
@@ -874,6 +872,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                 if (nz && nz->kind == 1)
                     for (int k = 0; k < nz->s; ++k) next.push_back(nz->sp[k]);
                 mm = mix_map(n, z.sp[0], z.s, next);
+                mm.tanf = std::fabs(z.c) >= std::fabs(z.sn);
                 mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
                 final_norms = final_norms || mm.final_norm;
             }

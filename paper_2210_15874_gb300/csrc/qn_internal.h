@@ -70,13 +70,14 @@ struct SlotView {
     int32_t max_slots;
 };
 
-// Consecutive phase gates of one layer whose qubits S number at most 8 (shared-
+// Consecutive phase gates of one layer whose qubits S number at most 9 (shared-
 // prefix mode with damping): their damping branches follow from the joint
 // distribution of the true bits of S, because every op of the group is
 // diagonal (phases, Z parts, K0) or a relabelling (X parts, K1) in the stored
 // basis.
 constexpr int kMaxGroupEdges = 10;
-constexpr int kGroupBins = 256;
+constexpr int kMaxGroupQubits = 9;
+constexpr int kGroupBins = 1 << kMaxGroupQubits;
 
 // A group of consecutive gates of one layer whose noise sites are all decided
 // from one joint distribution of the true bits of the group's qubits S:
@@ -86,27 +87,36 @@ constexpr int kGroupBins = 256;
 struct GateGroup {
     int32_t g0, m, s;               // first gate, gates, qubits in S
     int32_t kind;
-    int32_t sp[8];                  // qubits of S, ascending
+    int32_t sp[kMaxGroupQubits];    // qubits of S, ascending
     int32_t ei[kMaxGroupEdges];     // S index of each gate's first qubit
     int32_t ej[kMaxGroupEdges];     // S index of each gate's second qubit (== ei for a rotation)
     float c, sn;                    // cos, sin of the layer's gamma (kind 0) or beta (kind 1)
-    uint8_t tab[4][256];            // index over S of the stored bits in each byte of y (kind 0)
+    uint16_t tab[4][256];           // index over S of the stored bits in each byte of y (kind 0)
 };
 
-// Map of a mixer-block sweep from unit bits to float4-index (f) bits.  Unit
-// bits: 0-7 the thread, 8-9 the register index k, 10-11 the sub-tile, 12.. the
-// block; unit bit i covers f bit fb[i] (nbits bits in all).  The block's qubit j
-// sits at qpos[j]: -1 the two halves of a float4 (qubit 0), 0-4 a lane bit,
-// 8-9 a register bit.  The next block's qubits sit on lane bits 2 .. 2 + nN - 1.
+// Mixer blocks: kMixQ consecutive qubits per sweep.  A block of the sweep
+// takes tiles of 2048 float4 (11 f bits): kMixL bits L go to the lanes, kMixQ
+// bits A hold the block's qubits, kMixQ bits B the next block's; A and B are
+// filled up with low f bits left over.  In the first phase a thread holds the
+// 2^kMixQ float4 along A (lane and warp from L and B), in the second those
+// along B (lane and warp from L and A).  The other f bits number the tiles
+// (ftile).  Qubit 0 is the pair inside a float4: a block holding it (has0) has
+// its other qubits on A bits 0 ..; otherwise qubit q_lo + i sits on A bit i.
+// The next block's qubit i sits on B bit i.
+constexpr int kMixQ = 4;
+constexpr int kMixL = 11 - 2 * kMixQ;
+constexpr int kMixThreads = 2048 >> kMixQ;
 struct MixMap {
-    int8_t fb[32];
-    int32_t nbits;
+    int8_t fL[5], fA[4], fB[4];
+    int8_t ftile[32];
+    int32_t ntile;    // tile bits
     int32_t M;        // qubits of this block
-    int32_t qpos[3];
+    int32_t has0;
     int32_t nN;       // qubits of the next block (0: no joint to accumulate)
-    uint32_t lmask;   // lane bits that hold none of the next block's qubits
     int32_t final_norm;  // last sweep of the circuit: also form 1 / ||psi||^2 per state
+    int32_t tanf;     // |cos beta| >= |sin beta|: rotations in the tan form, else the cot form
 };
+constexpr int kMixSubs = 4;  // tiles per thread block (streamed through two shared buffers)
 
 // Device view of one group step.  Per-slot arrays are indexed by slot; the
 // per-member scratch arrays by the position of the member in SlotView::members.

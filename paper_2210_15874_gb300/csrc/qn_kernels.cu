@@ -822,7 +822,7 @@ __device__ __forceinline__ double df_warp_sum(float hi, float lo) {
 
 // ---------------------------------------------------------------------------
 // Phase-gate groups in shared-prefix mode.  A group is a run of consecutive
-// phase gates of one layer on a qubit set S of at most 8 qubits.  Every op of
+// phase gates of one layer on a qubit set S of at most 9 qubits.  Every op of
 // the group -- phase, Z part of a Pauli, K0 -- is diagonal in the stored basis,
 // and every X part or K1 jump only relabels true bits, so the branch of every
 // damping site in the group follows from the joint distribution of the true
@@ -852,7 +852,7 @@ struct GroupBins {
     unsigned lmask;  // lane bits that are no qubit of S
 };
 
-__device__ __forceinline__ GroupBins group_bins(const GateGroup *gp, int tile, unsigned char *vtab) {
+__device__ __forceinline__ GroupBins group_bins(const GateGroup *gp, int tile, uint16_t *vtab) {
     GroupBins gb;
     gb.base = group_bin(gp, ((uint32_t)threadIdx.x << 1) | ((uint32_t)tile << 13));
     unsigned lm = 0;
@@ -861,7 +861,7 @@ __device__ __forceinline__ GroupBins group_bins(const GateGroup *gp, int tile, u
     gb.lmask = lm;
     if (threadIdx.x < 32) {
         const uint32_t j = threadIdx.x;
-        vtab[j] = (unsigned char)group_bin(gp, (j & 1u) | (((j >> 1) & 3u) << 9) | (((j >> 3) & 3u) << 11));
+        vtab[j] = (uint16_t)group_bin(gp, (j & 1u) | (((j >> 1) & 3u) << 9) | (((j >> 3) & 3u) << 11));
     }
     return gb;
 }
@@ -933,7 +933,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
     const int slot = blockIdx.y, tile = blockIdx.x;
     const GateGroup *gp = gv.grp;
     __shared__ float hw[kThreads / 32][kGroupBins];
-    __shared__ unsigned char vtab[32];
+    __shared__ uint16_t vtab[32];
     for (int i = threadIdx.x; i < (kThreads / 32) * kGroupBins; i += kThreads) (&hw[0][0])[i] = 0.0f;
     const GroupBins gb = group_bins(gp, tile, vtab);
     __syncthreads();
@@ -985,12 +985,6 @@ __device__ __forceinline__ void rx_pair(float &ar, float &ai, float &br, float &
     bi = nbi;
 }
 
-// The rotation on both halves of two float4 whose elements differ in the qubit.
-__device__ __forceinline__ void rx_pair4(float4 &a, float4 &b, float c, float s) {
-    rx_pair(a.x, a.y, b.x, b.y, c, s);
-    rx_pair(a.z, a.w, b.z, b.w, c, s);
-}
-
 // The same rotation on a qubit whose two values sit in lanes that differ in
 // `lanebit` (every lane of the warp takes part).
 __device__ __forceinline__ void rx_lanes(float4 &o, int lanebit, float c, float s) {
@@ -1004,19 +998,21 @@ __device__ __forceinline__ void rx_lanes(float4 &o, int lanebit, float c, float 
 
 // Per-block joint of a mixer block whose qubits sit on lane bits.  put: this
 // lane's sum `acc` for bin `bin`, summed first over the lanes that differ only
-// in `lmask`, goes to the warp's row of hw[8][8].  commit (after a block
+// in `lmask`, goes to the warp's row of hw[warps][kJointBins].  commit (after a block
 // barrier): warps summed in fixed order, the block's 2^nb bins added to H.
+constexpr int kJointBins = 16;  // bins of a mixer block's joint (at most 4 qubits)
+
 __device__ __forceinline__ void lane_joint_put(float acc, int bin, unsigned lmask, float *hw) {
 #pragma unroll
     for (int i = 0; i < 5; ++i)
         if ((lmask >> i) & 1u) acc += __shfl_xor_sync(0xffffffffu, acc, 1 << i);
-    if (((threadIdx.x & 31u) & lmask) == 0u) hw[(threadIdx.x >> 5) * 8 + bin] = acc;
+    if (((threadIdx.x & 31u) & lmask) == 0u) hw[(threadIdx.x >> 5) * kJointBins + bin] = acc;
 }
 
-__device__ __forceinline__ void lane_joint_commit(int nb, const float *hw, unsigned long long *H) {
+__device__ __forceinline__ void lane_joint_commit(int nb, int warps, const float *hw, unsigned long long *H) {
     if ((int)threadIdx.x < nb) {
         double sum = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) sum += (double)hw[w * 8 + threadIdx.x];
+        for (int w = 0; w < warps; ++w) sum += (double)hw[w * kJointBins + threadIdx.x];
         if (sum > 0.0) atomicAdd(H + threadIdx.x, __double2ull_rn(sum * kHistScale));
     }
 }
@@ -1025,7 +1021,7 @@ __device__ __forceinline__ void lane_joint_commit(int nb, const float *hw, unsig
 // op of the gate before the group.  Then accumulate either the next phase
 // group's joint (gv.next) or the joint of the mixer block on qubits 0 .. vq-1
 // as it will be after that block's rotations (gv.vq > 0): qubit 0 is the pair
-// inside a float4, qubits 1 and 2 are lane bits 0 and 1 of the sweep layout.
+// inside a float4, qubits 1 .. 3 are lane bits 0 .. 2 of the sweep layout.
 __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupView gv) {
     grid_dependency_wait();
     const int slot = blockIdx.y + gv.slot_base, tile = blockIdx.x;
@@ -1035,7 +1031,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     const int vq = gv.vq;
     __shared__ float2 Ts[kGroupBins];
     __shared__ float hw[kThreads / 32][kGroupBins];
-    __shared__ unsigned char vT[32], vN[32];
+    __shared__ uint16_t vT[32], vN[32];
     for (int i = threadIdx.x; i < (1 << gp->s); i += kThreads) Ts[i] = gv.T[(size_t)slot * kGroupBins + i];
     const GroupBins gt = group_bins(gp, tile, vT);
     GroupBins gn{0, 0u};
@@ -1085,6 +1081,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
                 rx_pair(o.x, o.y, o.z, o.w, vc, vs);
                 if (vq > 1) rx_lanes(o, 1, vc, vs);
                 if (vq > 2) rx_lanes(o, 2, vc, vs);
+                if (vq > 3) rx_lanes(o, 4, vc, vs);
                 va0 += o.x * o.x + o.y * o.y;
                 va1 += o.z * o.z + o.w * o.w;
             }
@@ -1106,156 +1103,317 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
         lane_joint_put(va0, lb, lmask, &hw[0][0]);
         lane_joint_put(va1, lb | 1, lmask, &hw[0][0]);
         __syncthreads();
-        lane_joint_commit(1 << vq, &hw[0][0], gv.Hnext + (size_t)slot * kGroupBins);
+        lane_joint_commit(1 << vq, kThreads / 32, &hw[0][0], gv.Hnext + (size_t)slot * kGroupBins);
     }
 }
 
+// 16-byte asynchronous global -> shared copies (the copy engine of the SM
+// streams the next tile while the current one is computed).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kMixTile = 2048;  // float4 per tile
+constexpr size_t kMixSmem = 2 * kMixTile * sizeof(float4);
+constexpr int kMixE = 1 << kMixQ;  // float4 per thread and phase
+
+// exp(-i beta X) on a pair up to the common factor sc (cos beta when TANF,
+// sin beta otherwise): (I - i t X) with t = tan beta, or (t I - i X) with
+// t = cot beta -- four FMAs per pair, and |t| <= 1 either way.
+template <bool TANF>
+__device__ __forceinline__ void rx_pair_t(float &ar, float &ai, float &br, float &bi, float t) {
+    float nar, nai, nbr, nbi;
+    if (TANF) {
+        nar = __fmaf_rn(t, bi, ar);
+        nai = __fmaf_rn(-t, br, ai);
+        nbr = __fmaf_rn(t, ai, br);
+        nbi = __fmaf_rn(-t, ar, bi);
+    } else {
+        nar = __fmaf_rn(t, ar, bi);
+        nai = __fmaf_rn(t, ai, -br);
+        nbr = __fmaf_rn(t, br, ai);
+        nbi = __fmaf_rn(t, bi, -ar);
+    }
+    ar = nar;
+    ai = nai;
+    br = nbr;
+    bi = nbi;
+}
+
+template <bool TANF>
+__device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
+    rx_pair_t<TANF>(a.x, a.y, b.x, b.y, t);
+    rx_pair_t<TANF>(a.z, a.w, b.z, b.w, t);
+}
+
 // Mixer block sweep (shared-prefix mode): exp(-i beta X) on the block's (up
-// to three consecutive) qubits, then the block's drawn Pauli and damping ops
+// to kMixQ consecutive) qubits, then the block's drawn Pauli and damping ops
 // as the real factor T[slot][stored bits of the block] (drawn beforehand from
-// the joint after the rotations, so the state is final when written), then the
-// joint of the next block, whose qubits sit on lane bits, as it will be after
-// that block's rotations.  Same streaming shape as the gate sweeps: kSub
-// sub-tiles of 4 float4 per thread, the next one prefetched into registers.
-__global__ void __launch_bounds__(kThreads, 4) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
+// the joint after the rotations, so the state is final when written).  Tiles
+// of 2048 float4 stream through two shared buffers (cp.async, one tile
+// ahead), each copied by the threads that take it in phase 1: (1) per thread
+// the float4 along the block's qubits (A bits) are rotated, scaled and stored
+// to HBM (and back to the tile); (2) per thread the float4 along the next
+// block's qubits (B bits) are read from the tile and rotated without being
+// kept, and their squared magnitudes give that block's joint after its
+// rotations.  Register pairs only, no shuffles; the tile is read in lane order
+// (tile index = L | A << kMixL | B << (kMixL + kMixQ)).
+// Variants with every bound a constant (all for full blocks of kMixQ qubits):
+//   kMixMid   not qubit 0, a full next block
+//   kMixFirst qubit 0, a full next block
+//   kMixHist  not qubit 0, no next block, the next layer's first phase-group joint
+//   kMixNorm  not qubit 0, no next block, the final norms
+// and kMixAny, which reads everything from the map.
+enum { kMixAny = 0, kMixMid = 1, kMixFirst = 2, kMixHist = 3, kMixNorm = 4 };
+
+template <bool TANF, int VAR>
+__global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
+    extern __shared__ float4 mix_buf[];  // [2][kMixTile]
+    constexpr int kWarps = kMixThreads / 32;
     grid_dependency_wait();
     const int slot = blockIdx.y + gv.slot_base;
     const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
-    const int lane = threadIdx.x & 31;
-    const GateGroup *nx = gv.next;  // next layer's first phase group: its joint is formed here
-    __shared__ float Df[8];
-    __shared__ float hw[kThreads / 32][kGroupBins];
-    if (threadIdx.x < 8u) Df[threadIdx.x] = threadIdx.x < (1u << mm.M) ? gv.T[(size_t)slot * kGroupBins + threadIdx.x].x : 0.0f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tL = threadIdx.x & ((1 << kMixL) - 1), tH = threadIdx.x >> kMixL;  // L part, A or B part
+    constexpr bool kFix = VAR != kMixAny;
+    // next layer's first phase group: its joint is formed here
+    const GateGroup *nx = kFix ? (VAR == kMixHist ? gv.next : nullptr) : gv.next;
+    const bool has0 = kFix ? VAR == kMixFirst : mm.has0 != 0;
+    const int M = kFix ? kMixQ : mm.M;
+    const int nN = kFix ? ((VAR == kMixMid || VAR == kMixFirst) ? kMixQ : 0) : mm.nN;
+    const bool final_norm = kFix ? VAR == kMixNorm : mm.final_norm != 0;
+    const float c = gv.grp->c, sn = gv.grp->sn;
+    const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;  // rotation = rsc * (tangent form)
+    float scM = 1.0f;  // rsc^M: the block's rotations, folded into its factors
+    for (int i = 0; i < M; ++i) scM *= rsc;
+    __shared__ float Df[16];
+    __shared__ float hw[kWarps][kGroupBins];
+    if (threadIdx.x < 16u)
+        Df[threadIdx.x] = threadIdx.x < (1u << M) ? gv.T[(size_t)slot * kGroupBins + threadIdx.x].x * scM : 0.0f;
     if (nx)
-        for (int i = threadIdx.x; i < (kThreads / 32) * kGroupBins; i += kThreads) (&hw[0][0])[i] = 0.0f;
-    int64_t base = 0;
+        for (int i = threadIdx.x; i < kWarps * kGroupBins; i += kMixThreads) (&hw[0][0])[i] = 0.0f;
+    // float4 indices fit 32 bits (n <= 30)
+    uint32_t offL = 0, offW = 0, ao[kMixQ];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) base |= (int64_t)((threadIdx.x >> i) & 1u) << mm.fb[i];
+    for (int i = 0; i < kMixL; ++i) offL |= (uint32_t)((tL >> i) & 1) << mm.fL[i];
 #pragma unroll
-    for (int i = 12; i < 32; ++i)
-        if (i < mm.nbits) base |= (int64_t)((blockIdx.x >> (i - 12)) & 1u) << mm.fb[i];
-    const int64_t ko1 = (int64_t)1 << mm.fb[8], ko2 = (int64_t)1 << mm.fb[9];
-    const int64_t so1 = mm.nbits > 10 ? (int64_t)1 << mm.fb[10] : 0, so2 = mm.nbits > 11 ? (int64_t)1 << mm.fb[11] : 0;
-    const int nsub = mm.nbits >= 12 ? 4 : (mm.nbits == 11 ? 2 : 1);
-    // stored bits of the block for element (e, k) of this lane: lanebin | kbin(k) | e * ebin
-    int lanebin = 0, kb1 = 0, kb2 = 0, ebin = 0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        if (j >= mm.M) break;
-        const int q = mm.qpos[j];
-        if (q < 0) ebin = 1 << j;
-        else if (q == 8) kb1 = 1 << j;
-        else if (q == 9) kb2 = 1 << j;
-        else lanebin |= ((lane >> q) & 1) << j;
+    for (int i = 0; i < kMixQ; ++i) {
+        offW |= (uint32_t)((tH >> i) & 1) << mm.fB[i];
+        ao[i] = 1u << mm.fA[i];
     }
+    auto aoff = [&](int j) {
+        uint32_t o = 0;
+#pragma unroll
+        for (int i = 0; i < kMixQ; ++i) o |= (j & (1 << i)) ? ao[i] : 0u;
+        return o;
+    };
     const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)from << v.n));
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << v.n));
-    const float c = gv.grp->c, sn = gv.grp->sn;
-    auto addr = [&](int sub, int k) {
-        return base + ((k & 1) ? ko1 : 0) + ((k & 2) ? ko2 : 0) + ((sub & 1) ? so1 : 0) + ((sub & 2) ? so2 : 0);
-    };
-    // bins of the next phase group: this thread's part, the (k, sub) parts and
-    // the float4 half; lanes that differ only outside its qubits are summed first
-    GroupBins gn{0, 0u};
-    int nk1 = 0, nk2 = 0, ns1 = 0, ns2 = 0, ne1 = 0;
-    if (nx) {
-        gn.base = group_bin(nx, (uint32_t)(2 * base));
-        nk1 = group_bin(nx, (uint32_t)(2 * ko1));
-        nk2 = group_bin(nx, (uint32_t)(2 * ko2));
-        ns1 = group_bin(nx, (uint32_t)(2 * so1));
-        ns2 = group_bin(nx, (uint32_t)(2 * so2));
-        ne1 = group_bin(nx, 1u);
+    const int nqa = has0 ? M - 1 : M;  // block qubits on A bits
+    const int dmask = (1 << nqa) - 1;
+    const int nsubs = mm.ntile >= 2 ? kMixSubs : (1 << mm.ntile);
+    // tile offsets: the block's first tile, plus sub-tile steps (tile bits 0, 1)
+    uint32_t tbits = 0;  // tile bits of the block's first tile
+    {
+        const uint32_t t0 = blockIdx.x * nsubs;
 #pragma unroll
-        for (int i = 0; i < 5; ++i)
-            if (group_bin(nx, 2u << mm.fb[i]) == 0) gn.lmask |= 1u << i;
+        for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
+            if (i < mm.ntile) tbits |= ((t0 >> i) & 1u) << mm.ftile[i];
+    }
+    const uint32_t tbase = tbits | offL | offW;
+    const uint32_t ts1 = mm.ntile > 0 ? 1u << mm.ftile[0] : 0u;
+    const uint32_t ts2 = mm.ntile > 1 ? 1u << mm.ftile[1] : 0u;
+    auto tile_base = [&](int sub) { return tbase | ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u); };
+    // shared tile slot of tile index i: the low A bits are XOR-ed into the L bits, so
+    // that eight lanes apart by A (the copy order of the qubit-0 block) hit distinct banks
+    auto sw = [](int i) { return i ^ ((i >> kMixL) & ((1 << kMixL) - 1)); };
+    auto idx1 = [&](int j) { return sw(tL | (j << kMixL) | (tH << (kMixL + kMixQ))); };  // phase 1: j along A
+    auto idx2 = [&](int j) { return sw(tL | (tH << kMixL) | (j << (kMixL + kMixQ))); };  // phase 2: j along B
+    // The block holding qubit 0 has its own qubits on the lowest f bits, where
+    // the phase-1 order would give every lane its own 128-byte line: it copies
+    // in an order with A bits 0-2 on lane bits 0-2 instead, and takes a block
+    // barrier before phase 1 (threads then read what others copied).
+    uint32_t cbase = 0;
+    int cidx = 0;
+    uint32_t bo[kMixQ];
+#pragma unroll
+    for (int i = 0; i < kMixQ; ++i) bo[i] = 1u << mm.fB[i];
+    if (has0) {
+        const int la = lane & 7, ll = ((lane >> 3) & 3) | ((warp & 1) << 2), ah = warp >> 1;
+        cidx = ll | (la << kMixL) | (ah << (kMixL + 3));
+#pragma unroll
+        for (int i = 0; i < kMixL; ++i) cbase |= (uint32_t)((ll >> i) & 1) << mm.fL[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) cbase |= (uint32_t)((la >> i) & 1) << mm.fA[i];
+        cbase |= (uint32_t)ah << mm.fA[3];
+    }
+    auto fetch = [&](int sub) {  // tile `sub` into its buffer
+        const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
+        float4 *buf = mix_buf + (sub & 1) * kMixTile;
+        if (has0) {
+#pragma unroll
+            for (int j = 0; j < kMixE; ++j) {
+                uint32_t bofs = 0;
+#pragma unroll
+                for (int i = 0; i < kMixQ; ++i) bofs |= (j & (1 << i)) ? bo[i] : 0u;
+                cp_async16(buf + sw(cidx | (j << (kMixL + kMixQ))), q4 + (tbits | ts | cbase | bofs));
+            }
+        } else {
+            const uint32_t fb = tbase | ts;
+#pragma unroll
+            for (int j = 0; j < kMixE; ++j) cp_async16(buf + idx1(j), q4 + (fb | aoff(j)));
+        }
+        cp_async_commit();
+    };
+    // next phase group's bins: this thread's part, the A part of element j, the float4 half
+    GroupBins gn{0, 0u};
+    int nab[kMixQ], ne1 = 0;
+#pragma unroll
+    for (int i = 0; i < kMixQ; ++i) nab[i] = 0;
+    if (nx) {
+#pragma unroll
+        for (int i = 0; i < kMixQ; ++i) nab[i] = group_bin(nx, (uint32_t)(2 * ao[i]));
+        ne1 = group_bin(nx, 1u);
+        // lane bits: kMixL bits of L, then the low B bits
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const int fbit = i < kMixL ? mm.fL[i] : mm.fB[i - kMixL];
+            if (group_bin(nx, 2u << fbit) == 0) gn.lmask |= 1u << i;
+        }
     }
     HistRun run;
-    float acc = 0.0f;
+    float acc[kMixE];  // phase 2: sum of |.|^2 by B index j (folded into the next block's bins at the end)
+#pragma unroll
+    for (int j = 0; j < kMixE; ++j) acc[j] = 0.0f;
     float nh = 0.0f, nl = 0.0f;  // final norm (double-float), same FP32 terms as k_probs forms
-    float4 cur[4], nxt[4];
+    fetch(0);
+    __syncthreads();  // Df, hw
+    for (int sub = 0; sub < nsubs; ++sub) {
+        if (sub + 1 < nsubs) {
+            fetch(sub + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        if (has0) __syncthreads();  // copies by other threads
+        float4 *buf = mix_buf + (sub & 1) * kMixTile;
+        const uint32_t fb = tile_base(sub);
+        float4 x[kMixE];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cur[k] = q4[addr(0, k)];
-    __syncthreads();
+        for (int j = 0; j < kMixE; ++j) x[j] = buf[idx1(j)];  // this thread's own copies unless has0
+        // phase 1: the block's rotations, then its factors
+        if (has0) {
 #pragma unroll
-    for (int sub = 0; sub < kSub; ++sub) {
-        if (sub >= nsub) break;
-        if (sub + 1 < nsub) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) nxt[k] = q4[addr(sub + 1, k)];
+            for (int j = 0; j < kMixE; ++j) rx_pair_t<TANF>(x[j].x, x[j].y, x[j].z, x[j].w, rt);
         }
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            if (j >= mm.M) break;
-            const int q = mm.qpos[j];
-            if (q < 0) {
+        for (int i = 0; i < kMixQ; ++i) {
+            if (i >= nqa) break;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) rx_pair(cur[k].x, cur[k].y, cur[k].z, cur[k].w, c, sn);
-            } else if (q == 8) {  // register bit 0: elements (0, 1), (2, 3)
-                rx_pair4(cur[0], cur[1], c, sn);
-                rx_pair4(cur[2], cur[3], c, sn);
-            } else if (q == 9) {  // register bit 1: elements (0, 2), (1, 3)
-                rx_pair4(cur[0], cur[2], c, sn);
-                rx_pair4(cur[1], cur[3], c, sn);
-            } else {
+            for (int j = 0; j < kMixE; ++j)
+                if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
+        }
 #pragma unroll
-                for (int k = 0; k < 4; ++k) rx_lanes(cur[k], 1 << q, c, sn);
+        for (int j = 0; j < kMixE; ++j) {
+            const int d = j & dmask;
+            const float f0 = has0 ? Df[d << 1] : Df[d], f1 = has0 ? Df[(d << 1) | 1] : Df[d];
+            x[j].x *= f0;
+            x[j].y *= f0;
+            x[j].z *= f1;
+            x[j].w *= f1;
+            if (has0) buf[idx1(j)] = x[j];  // stored from the tile in copy order below
+            else p4[fb | aoff(j)] = x[j];
+            if (nN > 0 && !has0) buf[idx1(j)] = x[j];
+            if (nx) {
+                if (j == 0) gn.base = group_bin(nx, (uint32_t)(2 * fb));
+                int ks = 0;
+#pragma unroll
+                for (int i = 0; i < kMixQ; ++i) ks |= (j & (1 << i)) ? nab[i] : 0;
+                hist_push(hw[warp], gn, ne1, ks, x[j].x * x[j].x + x[j].y * x[j].y, x[j].z * x[j].z + x[j].w * x[j].w,
+                          run);
+            }
+            if (final_norm) {
+                df_add(nh, nl, prob_of(1.0f, x[j].x, x[j].y));
+                df_add(nh, nl, prob_of(1.0f, x[j].z, x[j].w));
             }
         }
+        if (nx) {  // the per-thread bin part changes with the tile
+            hist_close(hw[warp], gn, ne1, run);
+            run = HistRun();
+        }
+        if (nN > 0 || has0) __syncthreads();
+        if (has0) {
+            const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int kb = lanebin | ((k & 1) ? kb1 : 0) | ((k & 2) ? kb2 : 0);
-            const float f0 = Df[kb], f1 = Df[kb | ebin];
-            cur[k].x *= f0;
-            cur[k].y *= f0;
-            cur[k].z *= f1;
-            cur[k].w *= f1;
-            p4[addr(sub, k)] = cur[k];
-            if (nx)
-                hist_push(hw[threadIdx.x >> 5], gn, ne1, ((k & 1) ? nk1 : 0) | ((k & 2) ? nk2 : 0) |
-                                                             ((sub & 1) ? ns1 : 0) | ((sub & 2) ? ns2 : 0),
-                          cur[k].x * cur[k].x + cur[k].y * cur[k].y, cur[k].z * cur[k].z + cur[k].w * cur[k].w, run);
-            if (mm.final_norm) {
-                df_add(nh, nl, prob_of(1.0f, cur[k].x, cur[k].y));
-                df_add(nh, nl, prob_of(1.0f, cur[k].z, cur[k].w));
+            for (int j = 0; j < kMixE; ++j) {
+                uint32_t bofs = 0;
+#pragma unroll
+                for (int i = 0; i < kMixQ; ++i) bofs |= (j & (1 << i)) ? bo[i] : 0u;
+                p4[tbits | ts | cbase | bofs] = buf[sw(cidx | (j << (kMixL + kMixQ)))];
             }
         }
-        if (mm.nN > 0) {
+        if (nN > 0) {
+            // phase 2: the next block's rotations on the tile, kept only as squared magnitudes
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if (i >= mm.nN) break;
+            for (int j = 0; j < kMixE; ++j) x[j] = buf[idx2(j)];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) rx_lanes(cur[k], 4 << i, c, sn);
+            for (int i = 0; i < kMixQ; ++i) {
+                if (i >= nN) break;
+#pragma unroll
+                for (int j = 0; j < kMixE; ++j)
+                    if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                acc += cur[k].x * cur[k].x + cur[k].y * cur[k].y + cur[k].z * cur[k].z + cur[k].w * cur[k].w;
+            for (int j = 0; j < kMixE; ++j) acc[j] += x[j].x * x[j].x + x[j].y * x[j].y + x[j].z * x[j].z + x[j].w * x[j].w;
         }
-        if (sub + 1 < nsub) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
-        }
+        if (nN > 0 || has0) __syncthreads();  // the buffer is refilled two tiles on
     }
     allow_dependent_launch();
-    if (mm.nN > 0) {
-        lane_joint_put(acc, (lane >> 2) & ((1 << mm.nN) - 1), mm.lmask, &hw[0][0]);
+    if (nN > 0) {
+        // bins of the next block are the low nN bits of j: fold, then lanes and warps
+        const int nb = 1 << nN;
+#pragma unroll
+        for (int half = kMixE / 2; half >= 1; half >>= 1) {
+            if (nb <= half) {
+#pragma unroll
+                for (int j = 0; j < half; ++j) acc[j] += acc[j + half];
+            }
+        }
+        float sc2 = 1.0f;  // the next block's rotations were taken up to rsc each: restore |.|^2
+        for (int i = 0; i < nN; ++i) sc2 *= rsc * rsc;
+        float *red = &hw[0][0];
+#pragma unroll
+        for (int b = 0; b < kMixE; ++b) {
+            float x = acc[b] * sc2;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) red[warp * kJointBins + b] = x;
+        }
         __syncthreads();
-        lane_joint_commit(1 << mm.nN, &hw[0][0], gv.Hnext + (size_t)slot * kGroupBins);
+        lane_joint_commit(nb, kWarps, red, gv.Hnext + (size_t)slot * kGroupBins);
     }
     if (nx) {
-        hist_close(hw[threadIdx.x >> 5], gn, ne1, run);
         __syncthreads();
-        hist_commit(&hw[0][0], 1 << nx->s, gv.Hnext + (size_t)slot * kGroupBins);
+        for (int b = threadIdx.x; b < (1 << nx->s); b += kMixThreads) {
+            double a2 = 0.0;
+            for (int w = 0; w < kWarps; ++w) a2 += (double)hw[w][b];
+            if (a2 > 0.0) atomicAdd(gv.Hnext + (size_t)slot * kGroupBins + b, __double2ull_rn(a2 * kHistScale));
+        }
     }
-    if (mm.final_norm) {
+    if (final_norm) {
         // block partial -> partials[slot][block]; the slot's last block forms 1/N
-        __shared__ double redd[kThreads / 32];
+        __shared__ double redd[kWarps];
         __shared__ int last;
         const double ws = df_warp_sum(nh, nl);
-        if (lane == 0) redd[threadIdx.x >> 5] = ws;
+        if (lane == 0) redd[warp] = ws;
         __syncthreads();
         if (threadIdx.x == 0) {
             double sum = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+            for (int w = 0; w < kWarps; ++w) sum += redd[w];
             v.partials[((size_t)slot * v.tiles + blockIdx.x) * 4] = sum;
             __threadfence();
             const unsigned prev = atomicAdd(&v.counters[slot], 1u);
@@ -1338,8 +1496,10 @@ __device__ __forceinline__ GateCode gate_code(int kind, int code) {
 }
 
 // Branches of every member of one slot through one group.  Lane l of a warp
-// holds the patterns b = l + 32 r (true bits of S, r < 8) of the joint: at the
+// holds the patterns b = l + 32 r (true bits of S, r < kPatR) of the joint: at the
 // start of a phase group, after the rotations of a mixer block.
+constexpr int kPatR = kGroupBins / 32;  // patterns per lane
+
 __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView sv, GroupView gv, double gamma) {
     grid_dependency_wait();
     const int slot = blockIdx.x;
@@ -1366,21 +1526,21 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
         Hs[b] = 0ull;  // zero again for the next group that accumulates here
     }
     __syncthreads();
-    float h0[8];
+    float h0[kPatR];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) h0[r] = hd[lane + 32 * r];
+    for (int r = 0; r < kPatR; ++r) h0[r] = hd[lane + 32 * r];
     const float gf = (float)gamma, omg = (float)(1.0 - gamma);
     const float sg = (float)sqrt(gamma), sg1 = (float)sqrt(1.0 - gamma);
     if (warp == 0) {  // the identity / no-jump path: P(q = 1) at every damping site
-        float w[8];
+        float w[kPatR];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) w[r] = h0[r];
+        for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
         for (int e = 0; e < m; ++e)
             for (int k2 = 0; k2 < nsite; ++k2) {
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
                 float tot = 0.0f, one = 0.0f;
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < kPatR; ++r) {
                     const bool bit = (((uint32_t)(lane + 32 * r) >> qi) & 1u) != 0;
                     tot = __fadd_rn(tot, w[r]);
                     one = __fadd_rn(one, bit ? w[r] : 0.0f);
@@ -1389,7 +1549,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 one = warp_sumf(one);
                 if (lane == 0) p1m[2 * e + k2] = __fdiv_rn(__fmul_rn(gf, one), tot);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < kPatR; ++r) {
                     const bool bit = (((uint32_t)(lane + 32 * r) >> qi) & 1u) != 0;
                     w[r] = bit ? __fmul_rn(w[r], omg) : w[r];
                 }
@@ -1418,9 +1578,9 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
         [&](int r, int i) { evt[r] = i; });
     for (int a = warp; a < ne; a += kThreads / 32) {  // their own draws: one warp each
         const int t = mem[evt[a]];
-        float w[8];
+        float w[kPatR];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) w[r] = h0[r];
+        for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
         uint32_t flip = 0;
         uint64_t key = 0;
         for (int e = 0; e < m; ++e) {
@@ -1435,7 +1595,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
                 float tot = 0.0f, one = 0.0f;
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < kPatR; ++r) {
                     const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
                     tot = __fadd_rn(tot, w[r]);
                     one = __fadd_rn(one, bit ? w[r] : 0.0f);
@@ -1444,7 +1604,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 one = warp_sumf(one);
                 const bool j = ((double)dw[k2] + 0.5) * kTwoM32 < (double)__fdiv_rn(__fmul_rn(gf, one), tot);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < kPatR; ++r) {
                     const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
                     w[r] = j ? (bit ? __fmul_rn(w[r], gf) : 0.0f) : (bit ? __fmul_rn(w[r], omg) : w[r]);
                 }
@@ -1519,10 +1679,10 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
             if (lane == 0) atomicOr(v.status, 4);
             continue;
         }
-        float ar[8], ai[8], w[8];
+        float ar[kPatR], ai[kPatR], w[kPatR];
         uint32_t flip = 0;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < kPatR; ++r) {
             ar[r] = 1.0f;
             ai[r] = 0.0f;
             w[r] = h0[r];
@@ -1533,7 +1693,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
             const int qi = gp->ei[e], qj = gp->ej[e];
             const GateCode pc = gate_code(kind, code);
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {  // phase, then the Pauli's Z part, on the bits before its X part
+            for (int r = 0; r < kPatR; ++r) {  // phase, then the Pauli's Z part, on the bits before its X part
                 const uint32_t cb = (uint32_t)(lane + 32 * r) ^ flip;
                 const uint32_t ci = (cb >> qi) & 1u, cj = (cb >> qj) & 1u;
                 if (kind == 0 && ci != cj) {
@@ -1551,7 +1711,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 const int q = k2 ? qj : qi;
                 const bool j = ((key >> (6 * e + 4 + k2)) & 1u) != 0;
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < kPatR; ++r) {
                     const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> q) & 1u) != 0;
                     const float kf = j ? (bit ? sg : 0.0f) : (bit ? sg1 : 1.0f);
                     ar[r] *= kf;
@@ -1563,12 +1723,12 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
         }
         float N = 0.0f;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) N += w[r];
+        for (int r = 0; r < kPatR; ++r) N += w[r];
         N = warp_sumf(N);
         const float sc = 1.0f / sqrtf(N);
         if (lane == 0 && !(N > 0.0f && isfinite(sc))) atomicOr(v.status, 1);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < kPatR; ++r) {
             const int b = lane + 32 * r;
             if (b < nbins)
                 gv.T[(size_t)target * kGroupBins + (b ^ fS)] = make_float2(ar[r] * sc, ai[r] * sc);
@@ -2219,11 +2379,11 @@ static int persistent_blocks() {
 }
 
 template <typename K, typename... Args>
-static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+static cudaError_t launch_pdl_smem(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -2231,6 +2391,11 @@ static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, cudaStream_t s, A
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+template <typename K, typename... Args>
+static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    return launch_pdl_smem(kernel, grid, block, 0, s, args...);
 }
 
 cudaError_t launch_slot_sweep(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
@@ -2339,8 +2504,37 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
 }
 
 cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
-    const unsigned blocks = mm.nbits > 12 ? 1u << (mm.nbits - 12) : 1u;
-    return launch_pdl(k_mix_sweep, dim3(blocks, (unsigned)active), dim3(kThreads), s, v, gv, mm);
+    static const cudaError_t attr = [] {
+        const void *ks[] = {(const void *)k_mix_sweep<true, kMixAny>,  (const void *)k_mix_sweep<true, kMixMid>,
+                            (const void *)k_mix_sweep<true, kMixFirst>, (const void *)k_mix_sweep<true, kMixHist>,
+                            (const void *)k_mix_sweep<true, kMixNorm>, (const void *)k_mix_sweep<false, kMixAny>,
+                            (const void *)k_mix_sweep<false, kMixMid>, (const void *)k_mix_sweep<false, kMixFirst>,
+                            (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixNorm>};
+        for (const void *k : ks) {
+            const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }();
+    if (attr != cudaSuccess) return attr;
+    const unsigned blocks = mm.ntile >= 2 ? (1u << mm.ntile) / kMixSubs : 1u;
+    const dim3 grid(blocks, (unsigned)active), block(kMixThreads);
+    int var = kMixAny;
+    if (mm.M == kMixQ) {
+        const bool next_full = mm.nN == kMixQ && !gv.next && !mm.final_norm;
+        if (next_full) var = mm.has0 ? kMixFirst : kMixMid;
+        else if (!mm.has0 && mm.nN == 0 && gv.next && !mm.final_norm) var = kMixHist;
+        else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm) var = kMixNorm;
+    }
+#define QN_MIX(T, V) launch_pdl_smem(k_mix_sweep<T, V>, grid, block, kMixSmem, s, v, gv, mm)
+    switch (var) {
+    case kMixMid: return mm.tanf ? QN_MIX(true, kMixMid) : QN_MIX(false, kMixMid);
+    case kMixFirst: return mm.tanf ? QN_MIX(true, kMixFirst) : QN_MIX(false, kMixFirst);
+    case kMixHist: return mm.tanf ? QN_MIX(true, kMixHist) : QN_MIX(false, kMixHist);
+    case kMixNorm: return mm.tanf ? QN_MIX(true, kMixNorm) : QN_MIX(false, kMixNorm);
+    default: return mm.tanf ? QN_MIX(true, kMixAny) : QN_MIX(false, kMixAny);
+    }
+#undef QN_MIX
 }
 
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
