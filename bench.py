@@ -35,7 +35,7 @@ from paper_2210_15874_gb300 import workloads as W  # noqa: E402
 
 METRIC = "noisy trajectories/s at fixed <C> error"
 UNIT = "trajectories/s"
-PROFILE_PERIOD = 16  # time every 16th gate-sweep launch with a CUDA event pair
+PROFILE_PERIOD = 4  # time every 4th sweep launch with a CUDA event pair
 
 
 WORKLOADS = {
