@@ -122,6 +122,27 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(w, budget_s: float = 15.0):
     """FP64 oracle (trajectory simulator) on the host's cores: a bounded sample
     of the same workload's trajectories (the first `count` ids)."""
@@ -145,9 +166,15 @@ def cpu_baseline(w, budget_s: float = 15.0):
         count, elapsed = cores * rounds, el
     else:
         elapsed = first
+    # one core alone, on one trajectory of the same workload
+    t = time.perf_counter()
+    oracle.traj_run(w.n, w.edges, gates, G, nz, w.seed, 0, 1, want_amps=False, want_branches=False, threads=1)
+    single = 1.0 / (time.perf_counter() - t)
     return {"value": count / elapsed, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{count} trajectories (ids {'0' if rounds == 0 else cores}..) of {w.name}, "
-                      f"FP64 statevector oracle, OpenMP over trajectories"}
+                      f"FP64 statevector oracle, OpenMP over trajectories",
+            "single_thread": {"value": single, "unit": UNIT, "sample": f"trajectory 0 of {w.name}, 1 thread"},
+            "cpu_model": cpu_model()}
 
 
 def reference_arm(args):
