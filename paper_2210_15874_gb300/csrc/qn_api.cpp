@@ -859,7 +859,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                 h->sweep_bytes += (double)active * 8.0 * amp_count;
                 h->launches += 1;
             }
-            if (e == cudaSuccess) e = launch_group_decide(v, sv, gv, active, h->nz.gamma, h->stream);
+            if (e == cudaSuccess) e = launch_group_decide(v, sv, gv, z.s, active, h->nz.gamma, h->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(active_host, sv.active, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                                       h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

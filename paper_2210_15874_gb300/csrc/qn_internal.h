@@ -218,7 +218,8 @@ cudaError_t launch_slot_fork(const BatchView &v, const SlotView &sv, int active,
 // per-slot decisions and forks of a group, and the apply sweep (which also
 // accumulates the next group's joint).
 cudaError_t launch_group_hist(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
-cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, double gamma,
+cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int ns, int active,
+                                double gamma,
                                 cudaStream_t s);
 cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s);
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);

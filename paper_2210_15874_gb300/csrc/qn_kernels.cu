@@ -1498,8 +1498,8 @@ __device__ __forceinline__ GateCode gate_code(int kind, int code) {
 // Branches of every member of one slot through one group.  Lane l of a warp
 // holds the patterns b = l + 32 r (true bits of S, r < kPatR) of the joint: at the
 // start of a phase group, after the rotations of a mixer block.
-constexpr int kPatR = kGroupBins / 32;  // patterns per lane
-
+// kPatR patterns per lane: 1 for groups on <= 5 qubits, 4 for <= 7, 16 for <= 9.
+template <int kPatR>
 __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView sv, GroupView gv, double gamma) {
     grid_dependency_wait();
     const int slot = blockIdx.x;
@@ -1519,7 +1519,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
     __shared__ float p1m[2 * kMaxGroupEdges];
     __shared__ int child_base;
     unsigned long long *Hs = gv.Hcur + (size_t)slot * kGroupBins;
-    for (int b = threadIdx.x; b < kGroupBins; b += kThreads) hd[b] = 0.0f;
+    for (int b = threadIdx.x; b < 32 * kPatR; b += kThreads) hd[b] = 0.0f;
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += kThreads) {
         hd[b ^ fS] = (float)((double)Hs[b] * kHistUnit);
@@ -2496,9 +2496,12 @@ cudaError_t launch_group_hist(const BatchView &v, const SlotView &, const GroupV
     return launch_pdl(k_group_hist, dim3((unsigned)v.stiles, (unsigned)active), dim3(kThreads), s, v, gv);
 }
 
-cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, double gamma,
-                                cudaStream_t s) {
-    cudaError_t e = launch_pdl(k_group_decide, dim3((unsigned)active), dim3(kThreads), s, v, sv, gv, gamma);
+cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int ns, int active,
+                                double gamma, cudaStream_t s) {
+    cudaError_t e = ns <= 5   ? launch_pdl(k_group_decide<1>, dim3((unsigned)active), dim3(kThreads), s, v, sv, gv, gamma)
+                    : ns <= 7 ? launch_pdl(k_group_decide<4>, dim3((unsigned)active), dim3(kThreads), s, v, sv, gv, gamma)
+                              : launch_pdl(k_group_decide<kGroupBins / 32>, dim3((unsigned)active), dim3(kThreads), s, v,
+                                           sv, gv, gamma);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
 }
