@@ -156,6 +156,8 @@ struct qn_batch {
     uint64_t *gv_ekey = nullptr;
     int32_t *gv_i32 = nullptr;  // [6][gv_cap]: evt, rep, lead, lstart, lcount, parent
     int64_t gv_cap = 0;
+    double *spart = nullptr;   // sigma terms of k_probs row blocks 1 .. parts-1
+    int64_t spart_cap = 0;     // doubles
     float2 *lambda = nullptr;  // adjoint vectors (qn_grad), allocated on first use
     double *grad = nullptr;    // [K][2p] per-trajectory gradients
     int32_t grad_cap = 0;      // 2p the grad buffer was sized for
@@ -224,6 +226,8 @@ void release_all(qn_batch *h) {
     h->gv_ekey = nullptr;
     h->gv_i32 = nullptr;
     h->gv_cap = 0;
+    h->spart = nullptr;
+    h->spart_cap = 0;
     h->fl_ev = nullptr;
     h->fl_phase = nullptr;
     h->fl_edges = nullptr;
@@ -517,6 +521,20 @@ BatchView view_for(qn_batch *h, int64_t t0, int b) {
 
 qn_status check_status(const qn_batch *h);
 
+// Row blocks for k_probs over b states, with their sigma scratch.
+qn_status probs_rows(qn_batch *h, int b, AccumView *a) {
+    a->parts = a->probs ? probs_parts(h->n, b) : 1;
+    if (a->parts > 1) {
+        const int64_t need = (int64_t)(a->parts - 1) << h->n;
+        if (h->spart_cap < need) {
+            QN_TRY(alloc_t(h, &h->spart, (size_t)need));
+            h->spart_cap = need;
+        }
+        a->spart = h->spart;
+    }
+    return QN_OK;
+}
+
 // ---- profiling: one CUDA event pair per timed launch ----
 bool prof_sampled(qn_batch *h, int kind) {
     if (h->prof_period <= 0) return false;
@@ -693,13 +711,14 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     a.c_out = ensemble ? h->c_all + t0 : h->c_dbg;
     a.probs = ensemble ? h->probs : nullptr;
     a.sums = ensemble ? h->sums : nullptr;
+    QN_TRY(probs_rows(h, b, &a));
     QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
     QN_CUDA(launch_observe(v, a, h->stream));
     QN_TRY(prof_end(h, &ep));
     QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
     QN_CUDA(launch_probs(v, a, h->stream));
     QN_TRY(prof_end(h, &ep));
-    h->launches += 2;
+    h->launches += 2 + (a.parts > 1 ? 1 : 0);
     return QN_OK;
 }
 
@@ -943,11 +962,13 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     a.c_out = h->c_dbg;
     a.probs = h->probs;
     a.sums = h->sums;
+    a.trivial_pending = final_norms;  // the last sweep left no pending op
+    QN_TRY(probs_rows(h, nslots, &a));
     QN_TRY(prof_begin(h, &ep, 2, (double)nslots * (final_norms ? 8.0 : 16.0) * (double)((size_t)1 << n)));
     if (!final_norms) QN_CUDA(launch_observe(vo, a, h->stream));
     QN_CUDA(launch_probs(vo, a, h->stream));
     QN_TRY(prof_end(h, &ep));
-    h->launches += final_norms ? 1 : 2;
+    h->launches += (final_norms ? 1 : 2) + (a.parts > 1 ? 1 : 0);
     h->sh_slots += nslots;
     QN_CUDA(cudaStreamSynchronize(h->stream));  // order / weights host vectors
     return QN_OK;

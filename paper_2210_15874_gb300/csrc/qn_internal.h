@@ -171,6 +171,9 @@ struct AccumView {
     double *c_out;             // [b] per-trajectory <C>_t
     double *probs;             // [2^n] ensemble sum, or nullptr
     double *sums;              // [2] S1, S2, or nullptr
+    int32_t trivial_pending = 0;  // every state's pending op is the identity
+    int32_t parts = 1;            // row blocks that split the states (k_probs grid y)
+    double *spart = nullptr;      // [parts - 1][2^n] sigma terms of rows 1 .. parts-1
 };
 
 constexpr int kThreads = 256;        // threads per sweep block
@@ -198,6 +201,9 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
                          cudaStream_t s);
 cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
+// Row blocks worth giving k_probs for b states (1 .. kMaxProbParts).
+int probs_parts(int n, int b);
+constexpr int kMaxProbParts = 4;
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
 // Fused layers (Pauli-only): per-trajectory layer parameters from the branch
 // tables, then sweeps applying the rotations of qubits [q_lo, q_lo + m) of

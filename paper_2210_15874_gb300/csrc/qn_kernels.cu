@@ -1851,6 +1851,9 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
 
 constexpr int kAccChunk = 32;
 
+// Row block blockIdx.y takes chunks [y C / P, (y + 1) C / P) of the C chunks of states; row 0 adds
+// its sigma terms to probs, the others store theirs in spart (summed on in row order afterwards).
+template <bool TRIVIAL>
 __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, int64_t xblocks) {
     const int xb = blockIdx.x;
     const int n = v.n;
@@ -1900,9 +1903,12 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const uint32_t x = (uint32_t)(2 * (f0 + k * kThreads) + e);
-                const uint32_t tb = x ^ pend;
-                const uint32_t b0 = (tb >> pq0) & 1u, b1 = (tb >> pq1) & 1u;
-                const float fac = b1 ? (b0 ? fs.w : fs.z) : (b0 ? fs.y : fs.x);
+                float fac = 1.0f;
+                if (!TRIVIAL) {
+                    const uint32_t tb = x ^ pend;
+                    const uint32_t b0 = (tb >> pq0) & 1u, b1 = (tb >> pq1) & 1u;
+                    fac = b1 ? (b0 ? fs.w : fs.z) : (b0 ? fs.y : fs.x);
+                }
                 const float re = e ? vv.z : vv.x, im = e ? vv.w : vv.y;
                 const float pr = prob_of(fac, re, im);
                 if (a.probs) df_add_prod(ah[2 * k + e], al[2 * k + e], pr, ih, il);
@@ -1913,7 +1919,10 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
         for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
         if (lane == 0) cw[ci][warp] = cp;
     };
-    for (int t0c = 0; t0c < v.b; t0c += kAccChunk) {
+    const int nchunks = (v.b + kAccChunk - 1) / kAccChunk;
+    const int cbeg = (int)((int64_t)blockIdx.y * nchunks / gridDim.y);
+    const int cend = (int)((int64_t)(blockIdx.y + 1) * nchunks / gridDim.y);
+    for (int t0c = cbeg * kAccChunk; t0c < min(v.b, cend * kAccChunk); t0c += kAccChunk) {
         const int tend = min(v.b, t0c + kAccChunk);
         // the chunk's per-state parameters, once per block
         if ((int)threadIdx.x < tend - t0c) {
@@ -1954,18 +1963,25 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
         __syncthreads();
     }
     if (a.probs) {
+        double *dst = blockIdx.y == 0 ? nullptr : a.spart + (size_t)(blockIdx.y - 1) * (2 * (size_t)nf);
 #pragma unroll
         for (int k = 0; k < kF4PerThread; ++k)
             if (f0 + k * kThreads < nf) {
-                a.probs[2 * (f0 + k * kThreads)] += s_acc[2 * k][threadIdx.x];
-                a.probs[2 * (f0 + k * kThreads) + 1] += s_acc[2 * k + 1][threadIdx.x];
+                const int64_t x = 2 * (f0 + k * kThreads);
+                if (dst) {
+                    dst[x] = s_acc[2 * k][threadIdx.x];
+                    dst[x + 1] = s_acc[2 * k + 1][threadIdx.x];
+                } else {
+                    a.probs[x] += s_acc[2 * k][threadIdx.x];
+                    a.probs[x + 1] += s_acc[2 * k + 1][threadIdx.x];
+                }
             }
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(a.acc_counter, 1u);
-        last = prev == (unsigned)(xblocks - 1);
+        last = prev == (unsigned)(xblocks * gridDim.y - 1);
     }
     __syncthreads();
     if (!last) return;
@@ -1989,6 +2005,15 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
             a.sums[1] = s2;
         }
         *a.acc_counter = 0;
+    }
+}
+
+// sigma += the other row blocks' terms, in row order.
+__global__ void k_probs_combine(double *probs, const double *spart, int parts, int64_t dim) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < dim; x += (int64_t)gridDim.x * blockDim.x) {
+        double acc = probs[x];
+        for (int p = 0; p + 1 < parts; ++p) acc += spart[(size_t)p * dim + x];
+        probs[x] = acc;
     }
 }
 
@@ -2425,9 +2450,31 @@ cudaError_t launch_observe(const BatchView &v, const AccumView &, cudaStream_t s
     return cudaGetLastError();
 }
 
+int probs_parts(int n, int b) {
+    const int64_t xb = accumulate_xblocks(n);
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    // about four waves of two blocks per SM, at least one chunk of states per row
+    int p = (int)((4 * 2 * (int64_t)sms + xb - 1) / xb);
+    p = std::min(p, (b + kAccChunk - 1) / kAccChunk);
+    return std::max(1, std::min(p, kMaxProbParts));
+}
+
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s) {
     const int64_t xb = accumulate_xblocks(v.n);
-    k_probs<<<(unsigned)xb, kThreads, 0, s>>>(v, a, xb);
+    const int parts = a.probs && a.spart ? a.parts : 1;
+    const dim3 grid((unsigned)xb, (unsigned)parts);
+    if (a.trivial_pending) k_probs<true><<<grid, kThreads, 0, s>>>(v, a, xb);
+    else k_probs<false><<<grid, kThreads, 0, s>>>(v, a, xb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || parts == 1) return e;
+    const int64_t dim = (int64_t)1 << v.n;
+    k_probs_combine<<<(unsigned)std::min<int64_t>((dim + 255) / 256, 4096), 256, 0, s>>>(a.probs, a.spart, parts, dim);
     return cudaGetLastError();
 }
 
