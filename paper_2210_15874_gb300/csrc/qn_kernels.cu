@@ -1495,6 +1495,25 @@ __device__ __forceinline__ GateCode gate_code(int kind, int code) {
     return g;
 }
 
+// Warp sum of the weights w[r] of patterns b = lane + 32 r whose current bit qi
+// (b ^ flip) is set, or of all of them for qi < 0: a pairwise tree per lane, then
+// the butterfly -- a fixed order, so equal inputs give equal sums everywhere.
+template <int R>
+__device__ __forceinline__ float site_weight(const float (&w)[R], int lane, uint32_t flip, int qi) {
+    float t[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool bit = qi < 0 || ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
+        t[r] = bit ? w[r] : 0.0f;
+    }
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int r = 0; r < h; ++r) t[r] = __fadd_rn(t[r], t[r + h]);
+    }
+    return warp_sumf(t[0]);
+}
+
 // Branches of every member of one slot through one group.  Lane l of a warp
 // holds the patterns b = l + 32 r (true bits of S, r < kPatR) of the joint: at the
 // start of a phase group, after the rotations of a mixer block.
@@ -1529,25 +1548,22 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
     float h0[kPatR];
 #pragma unroll
     for (int r = 0; r < kPatR; ++r) h0[r] = hd[lane + 32 * r];
+    // total weight, carried through the sites in closed form (the same arithmetic on
+    // the shared path and on every member's own path)
+    const float tot0 = site_weight<kPatR>(h0, lane, 0u, -1);
     const float gf = (float)gamma, omg = (float)(1.0 - gamma);
     const float sg = (float)sqrt(gamma), sg1 = (float)sqrt(1.0 - gamma);
     if (warp == 0) {  // the identity / no-jump path: P(q = 1) at every damping site
         float w[kPatR];
 #pragma unroll
         for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
+        float tot = tot0;
         for (int e = 0; e < m; ++e)
             for (int k2 = 0; k2 < nsite; ++k2) {
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
-                float tot = 0.0f, one = 0.0f;
-#pragma unroll
-                for (int r = 0; r < kPatR; ++r) {
-                    const bool bit = (((uint32_t)(lane + 32 * r) >> qi) & 1u) != 0;
-                    tot = __fadd_rn(tot, w[r]);
-                    one = __fadd_rn(one, bit ? w[r] : 0.0f);
-                }
-                tot = warp_sumf(tot);
-                one = warp_sumf(one);
+                const float one = site_weight<kPatR>(w, lane, 0u, qi);
                 if (lane == 0) p1m[2 * e + k2] = __fdiv_rn(__fmul_rn(gf, one), tot);
+                tot = __fsub_rn(tot, __fmul_rn(gf, one));  // no jump: the weight on bit 1 shrinks by 1 - gamma
 #pragma unroll
                 for (int r = 0; r < kPatR; ++r) {
                     const bool bit = (((uint32_t)(lane + 32 * r) >> qi) & 1u) != 0;
@@ -1581,6 +1597,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
         float w[kPatR];
 #pragma unroll
         for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
+        float tot = tot0;
         uint32_t flip = 0;
         uint64_t key = 0;
         for (int e = 0; e < m; ++e) {
@@ -1593,16 +1610,9 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
             int jumps = 0;
             for (int k2 = 0; k2 < nsite; ++k2) {
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
-                float tot = 0.0f, one = 0.0f;
-#pragma unroll
-                for (int r = 0; r < kPatR; ++r) {
-                    const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
-                    tot = __fadd_rn(tot, w[r]);
-                    one = __fadd_rn(one, bit ? w[r] : 0.0f);
-                }
-                tot = warp_sumf(tot);
-                one = warp_sumf(one);
+                const float one = site_weight<kPatR>(w, lane, flip, qi);
                 const bool j = ((double)dw[k2] + 0.5) * kTwoM32 < (double)__fdiv_rn(__fmul_rn(gf, one), tot);
+                tot = j ? __fmul_rn(gf, one) : __fsub_rn(tot, __fmul_rn(gf, one));
 #pragma unroll
                 for (int r = 0; r < kPatR; ++r) {
                     const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
