@@ -1581,19 +1581,34 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
     const int ne = block_select(
         cnt,
         [&](int i) {
-            const int t = mem[i];
-            for (int e = 0; e < m; ++e) {
-                const size_t gi = (size_t)t * v.G + gp->g0 + e;
-                if (v.branch[gi] & 15) return true;
-                const uint32_t *dw = v.dwords + gi * 2;
-                if (((double)dw[0] + 0.5) * kTwoM32 < (double)p1m[2 * e]) return true;
-                if (nsite == 2 && ((double)dw[1] + 0.5) * kTwoM32 < (double)p1m[2 * e + 1]) return true;
-            }
-            return false;
+            // all of the member's codes and words first (independent loads), then the tests
+            const size_t g0 = (size_t)mem[i] * v.G + gp->g0;
+            uint32_t codes = 0, dwv[2 * kMaxGroupEdges];
+#pragma unroll
+            for (int e = 0; e < kMaxGroupEdges; ++e)
+                if (e < m) {
+                    codes |= (uint32_t)(v.branch[g0 + e] & 15);
+                    dwv[2 * e] = v.dwords[(g0 + e) * 2];
+                    dwv[2 * e + 1] = nsite == 2 ? v.dwords[(g0 + e) * 2 + 1] : 0xffffffffu;
+                }
+            bool ev = codes != 0;
+#pragma unroll
+            for (int e = 0; e < kMaxGroupEdges; ++e)
+                if (e < m) {
+                    ev = ev || ((double)dwv[2 * e] + 0.5) * kTwoM32 < (double)p1m[2 * e];
+                    if (nsite == 2) ev = ev || ((double)dwv[2 * e + 1] + 0.5) * kTwoM32 < (double)p1m[2 * e + 1];
+                }
+            return ev;
         },
         [&](int r, int i) { evt[r] = i; });
+    __shared__ uint8_t s_code[kThreads / 32][kMaxGroupEdges];
+    __shared__ uint32_t s_dw[kThreads / 32][2 * kMaxGroupEdges];
     for (int a = warp; a < ne; a += kThreads / 32) {  // their own draws: one warp each
         const int t = mem[evt[a]];
+        // the member's codes and damping words, one load per lane
+        if (lane < m) s_code[warp][lane] = v.branch[(size_t)t * v.G + gp->g0 + lane] & 15;
+        if (lane < 2 * m) s_dw[warp][lane] = v.dwords[((size_t)t * v.G + gp->g0) * 2 + lane];
+        __syncwarp();
         float w[kPatR];
 #pragma unroll
         for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
@@ -1602,8 +1617,8 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
         uint64_t key = 0;
         for (int e = 0; e < m; ++e) {
             const size_t gi = (size_t)t * v.G + gp->g0 + e;
-            const int code = v.branch[gi] & 15;
-            const uint32_t *dw = v.dwords + gi * 2;
+            const int code = s_code[warp][e];
+            const uint32_t *dw = &s_dw[warp][2 * e];
             const GateCode gc = gate_code(kind, code);
             flip ^= (gc.xa << gp->ei[e]) ^ (gc.xb << gp->ej[e]);
             key |= (uint64_t)code << (6 * e);
@@ -1627,6 +1642,7 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
             if (lane == 0) v.branch[gi] = (uint8_t)(code | (jumps << 4));
         }
         if (lane == 0) ekey[a] = key;
+        __syncwarp();  // the staged codes are refilled for the warp's next member
     }
     __syncthreads();
     // classes: the shared path (if any member kept it), then one per distinct
