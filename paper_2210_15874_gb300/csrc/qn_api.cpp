@@ -482,8 +482,15 @@ MixMap mix_map(int n, int q_lo, int M, const std::vector<int> &next) {
         B.push_back(q - 1);
         taken[q - 1] = true;
     }
-    for (int i = 0; i < kMixL; ++i) mm.fL[i] = (int8_t)lowest_free();
-    while ((int)A.size() < kMixQ) A.push_back(lowest_free());
+    if (mm.has0) {
+        // the block holding qubit 0 and a full next block cover f bits 0 .. 6; padding A
+        // before L makes the tile the contiguous f bits 0 .. 10 (copied in address order)
+        while ((int)A.size() < kMixQ) A.push_back(lowest_free());
+        for (int i = 0; i < kMixL; ++i) mm.fL[i] = (int8_t)lowest_free();
+    } else {
+        for (int i = 0; i < kMixL; ++i) mm.fL[i] = (int8_t)lowest_free();
+        while ((int)A.size() < kMixQ) A.push_back(lowest_free());
+    }
     while ((int)B.size() < kMixQ) B.push_back(lowest_free());
     for (int i = 0; i < kMixQ; ++i) {
         mm.fA[i] = (int8_t)A[i];

@@ -1251,10 +1251,22 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         for (int i = 0; i < 3; ++i) cbase |= (uint32_t)((la >> i) & 1) << mm.fA[i];
         cbase |= (uint32_t)ah << mm.fA[3];
     }
+    // kMixFirst: the tile is the contiguous f bits 0 .. 10 (A = f0-f2 and f7, B = f3-f6,
+    // L = f8-f10); copies and stores go in address order, each float4 to its tile slot
+    static_assert(kMixQ == 4 && kMixL == 3, "the first block's tile layout assumes 4 + 4 + 3 bits");
+    auto nat_slot = [](uint32_t f) {
+        return (int)(((f >> 8) & 7u) | ((f & 7u) << 3) | (((f >> 7) & 1u) << 6) | (((f >> 3) & 15u) << 7));
+    };
     auto fetch = [&](int sub) {  // tile `sub` into its buffer
         const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
         float4 *buf = mix_buf + (sub & 1) * kMixTile;
-        if (has0) {
+        if (VAR == kMixFirst) {
+#pragma unroll
+            for (int c = 0; c < kMixE; ++c) {
+                const uint32_t f = threadIdx.x + (uint32_t)c * kMixThreads;
+                cp_async16(buf + sw(nat_slot(f)), q4 + (tbits | ts | f));
+            }
+        } else if (has0) {
 #pragma unroll
             for (int j = 0; j < kMixE; ++j) {
                 uint32_t bofs = 0;
@@ -1346,7 +1358,14 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
             run = HistRun();
         }
         if (nN > 0 || has0) __syncthreads();
-        if (has0) {
+        if (VAR == kMixFirst) {
+            const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
+#pragma unroll
+            for (int c = 0; c < kMixE; ++c) {
+                const uint32_t f = threadIdx.x + (uint32_t)c * kMixThreads;
+                p4[tbits | ts | f] = buf[sw(nat_slot(f))];
+            }
+        } else if (has0) {
             const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
 #pragma unroll
             for (int j = 0; j < kMixE; ++j) {
@@ -2598,7 +2617,10 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
     int var = kMixAny;
     if (mm.M == kMixQ) {
         const bool next_full = mm.nN == kMixQ && !gv.next && !mm.final_norm;
-        if (next_full) var = mm.has0 ? kMixFirst : kMixMid;
+        const bool natural = mm.fA[0] == 0 && mm.fA[1] == 1 && mm.fA[2] == 2 && mm.fA[3] == 7 && mm.fB[0] == 3 &&
+                             mm.fB[1] == 4 && mm.fB[2] == 5 && mm.fB[3] == 6 && mm.fL[0] == 8 && mm.fL[1] == 9 &&
+                             mm.fL[2] == 10;
+        if (next_full && (!mm.has0 || natural)) var = mm.has0 ? kMixFirst : kMixMid;
         else if (!mm.has0 && mm.nN == 0 && gv.next && !mm.final_norm) var = kMixHist;
         else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm) var = kMixNorm;
     }
