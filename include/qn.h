@@ -195,6 +195,32 @@ qn_status qn_fidelity_error(const double *sa, const double *se, int64_t len, dou
  * mode).  Any output may be NULL. */
 qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, double *sweep_bytes, int64_t *states);
 
+/* The gate groups of shared-prefix mode with damping and fusion on -- a view
+ * of the schedule qn_run_qaoa uses (no counterpart in the paper; host only,
+ * no device memory).  For an n-qubit graph and depth p, writes up to
+ * `capacity` groups in circuit order: kind (0 = consecutive phase gates of a
+ * layer on at most 9 qubits, at most 10 gates; 1 = a block of consecutive
+ * mixer rotations, present when n >= 12), first gate (the noisy H layer is
+ * gates 0 .. n-1), number of gates, and the group's qubits as a bit mask.
+ * *count is the number of groups, also when it exceeds capacity.  Output
+ * arrays may be NULL when capacity is 0.  QN_EINVAL on an invalid graph or
+ * p < 0. */
+qn_status qn_group_plan(int32_t n, const qn_graph *graph, int32_t p, int32_t capacity, int32_t *kind,
+                        int32_t *first_gate, int32_t *gates, uint32_t *qubit_mask, int32_t *count);
+
+/* Tile map of the sweep of the mixer block on qubits q_lo .. q_lo + m - 1
+ * whose next block has m_next qubits (q_lo + m .. q_lo + m + m_next - 1; 0:
+ * no next block) -- exposed for tests (no counterpart in the paper; host
+ * only).  A float4 index f holds amplitudes 2f and 2f + 1, so f bit b is
+ * amplitude bit b + 1 and qubit 0 is inside the float4.  Writes the f bits
+ * that go to lanes (lane_bits[3]), that hold the block's qubits (a_bits[4],
+ * padded with free bits), the next block's (b_bits[4], padded), and the
+ * remaining ones that number tiles (tile_bits[32], *ntile of them).
+ * QN_EINVAL unless 12 <= n <= 30, 1 <= m <= 4, 0 <= m_next <= 4 and the qubits
+ * fit below n. */
+qn_status qn_mix_tile_map(int32_t n, int32_t q_lo, int32_t m, int32_t m_next, int8_t *lane_bits, int8_t *a_bits,
+                          int8_t *b_bits, int8_t *tile_bits, int32_t *ntile);
+
 /* Kernel timing with CUDA events recorded on the handle's stream: period = 0
  * (default) records none; period = k >= 1 brackets every k-th gate-sweep
  * launch and every init / observable launch with an event pair.  An event pair

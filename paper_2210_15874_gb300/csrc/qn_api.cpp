@@ -1333,6 +1333,54 @@ qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, doub
     return ok();
 }
 
+qn_status qn_group_plan(int32_t n, const qn_graph *graph, int32_t p, int32_t capacity, int32_t *kind,
+                        int32_t *first_gate, int32_t *gates, uint32_t *qubit_mask, int32_t *count) {
+    if (!count) return fail(QN_EINVAL, "count is NULL");
+    if (n < 1 || n > kMaxQubits) return fail(QN_EINVAL, "n = %d outside [1, %d]", n, kMaxQubits);
+    if (p < 0) return fail(QN_EINVAL, "p = %d < 0", p);
+    if (capacity < 0 || (capacity > 0 && (!kind || !first_gate || !gates || !qubit_mask)))
+        return fail(QN_EINVAL, "capacity < 0 or an output array is NULL");
+    qn_batch tmp;  // host-only description; owns no device memory
+    tmp.n = n;
+    QN_TRY(validate_graph(&tmp, graph));
+    tmp.edges.assign(graph->edges, graph->edges + 2 * graph->num_edges);
+    tmp.p = p;
+    tmp.gammas.assign((size_t)p, 0.0);
+    tmp.betas.assign((size_t)p, 0.0);
+    build_gates(&tmp);
+    build_groups(&tmp);
+    *count = (int32_t)tmp.groups.size();
+    for (int i = 0; i < (int)tmp.groups.size() && i < capacity; ++i) {
+        const GateGroup &z = tmp.groups[i];
+        kind[i] = z.kind;
+        first_gate[i] = z.g0;
+        gates[i] = z.m;
+        uint32_t mask = 0;
+        for (int k = 0; k < z.s; ++k) mask |= 1u << z.sp[k];
+        qubit_mask[i] = mask;
+    }
+    return ok();
+}
+
+qn_status qn_mix_tile_map(int32_t n, int32_t q_lo, int32_t m, int32_t m_next, int8_t *lane_bits, int8_t *a_bits,
+                          int8_t *b_bits, int8_t *tile_bits, int32_t *ntile) {
+    if (!lane_bits || !a_bits || !b_bits || !tile_bits || !ntile) return fail(QN_EINVAL, "an output is NULL");
+    if (n < 12 || n > kMaxQubits || m < 1 || m > kMixQ || m_next < 0 || m_next > kMixQ || q_lo < 0 ||
+        q_lo + m + m_next > n)
+        return fail(QN_EINVAL, "no mixer block of %d qubits at %d (next %d) for n = %d", m, q_lo, m_next, n);
+    std::vector<int> next;
+    for (int k = 0; k < m_next; ++k) next.push_back(q_lo + m + k);
+    const MixMap mm = mix_map(n, q_lo, m, next);
+    for (int i = 0; i < kMixL; ++i) lane_bits[i] = mm.fL[i];
+    for (int i = 0; i < kMixQ; ++i) {
+        a_bits[i] = mm.fA[i];
+        b_bits[i] = mm.fB[i];
+    }
+    for (int i = 0; i < 32; ++i) tile_bits[i] = i < mm.ntile ? mm.ftile[i] : (int8_t)-1;
+    *ntile = mm.ntile;
+    return ok();
+}
+
 qn_status qn_batch_set_profiling(qn_batch *h, int32_t period) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
     if (period < 0) return fail(QN_EINVAL, "profiling period < 0");

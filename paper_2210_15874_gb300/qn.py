@@ -59,6 +59,8 @@ _SIGS = {
     "qn_profile_read": (c_i32, [c_vp, c_i32, P(c_i64), P(c_dbl), P(c_dbl)]),
     "qn_run_qaoa_noalloc": (c_i32, [c_i32, P(qn_graph), c_i32, P(c_dbl), P(c_dbl), P(qn_noise), c_u64, c_i64,
                                     c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "qn_group_plan": (c_i32, [c_i32, P(qn_graph), c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, P(c_i32)]),
+    "qn_mix_tile_map": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, P(c_i32)]),
     "qn_last_error": (ctypes.c_char_p, []),
     "qn_batch_destroy": (None, [c_vp]),
 }
@@ -86,6 +88,10 @@ def check(status: int, where: str) -> None:
 
 def _dptr(a):
     return a.ctypes.data_as(P(c_dbl))
+
+
+def _vp(a):
+    return ctypes.c_void_p(a.ctypes.data)
 
 
 class Batch:
@@ -232,3 +238,33 @@ def fidelity_error(sa, se) -> float:
     out = c_dbl()
     check(qn_fidelity_error(_dptr(a), _dptr(b), len(a), ctypes.byref(out)), "qn_fidelity_error")
     return out.value
+
+
+def group_plan(n: int, edges, p: int) -> list:
+    """The gate groups of shared-prefix mode with damping and fusion (host only):
+    a list of dicts kind (0 phase gates, 1 mixer rotations), first_gate, gates, qubits."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    g = qn_graph(n, len(e) // 2, e.ctypes.data_as(P(c_i32)))
+    cnt = c_i32()
+    check(qn_group_plan(n, ctypes.byref(g), p, 0, None, None, None, None, ctypes.byref(cnt)), "qn_group_plan")
+    k = np.zeros(cnt.value, dtype=np.int32)
+    f = np.zeros(cnt.value, dtype=np.int32)
+    m = np.zeros(cnt.value, dtype=np.int32)
+    q = np.zeros(cnt.value, dtype=np.uint32)
+    if cnt.value:
+        check(qn_group_plan(n, ctypes.byref(g), p, cnt.value, _vp(k), _vp(f), _vp(m), _vp(q),
+                            ctypes.byref(cnt)), "qn_group_plan")
+    return [dict(kind=int(k[i]), first_gate=int(f[i]), gates=int(m[i]),
+                 qubits=[b for b in range(n) if (int(q[i]) >> b) & 1]) for i in range(cnt.value)]
+
+
+def mix_tile_map(n: int, q_lo: int, m: int, m_next: int) -> dict:
+    """Float4-index bits of a mixer-block sweep's tile (host only): lane, a, b, tile."""
+    lane = np.zeros(3, dtype=np.int8)
+    a = np.zeros(4, dtype=np.int8)
+    b = np.zeros(4, dtype=np.int8)
+    t = np.zeros(32, dtype=np.int8)
+    nt = c_i32()
+    check(qn_mix_tile_map(n, q_lo, m, m_next, _vp(lane), _vp(a), _vp(b), _vp(t), ctypes.byref(nt)),
+          "qn_mix_tile_map")
+    return dict(lane=lane.tolist(), a=a.tolist(), b=b.tolist(), tile=t[:nt.value].tolist())
