@@ -154,7 +154,10 @@ struct qn_batch {
     float2 *gv_T = nullptr;
     TrajState *gv_stprev = nullptr;
     uint64_t *gv_ekey = nullptr;
-    int32_t *gv_i32 = nullptr;  // [6][gv_cap]: evt, rep, lead, lstart, lcount, parent
+    int32_t *gv_i32 = nullptr;  // [7][gv_cap]: evt, rep, lead, lstart, lcount, parent, pos_slot
+    float *gv_htrue = nullptr;  // [gv_cap][kGroupBins]
+    float *gv_p1m = nullptr;    // [gv_cap][2 kMaxGroupEdges]
+    GroupClass *gv_cls = nullptr;
     int64_t gv_cap = 0;
     double *spart = nullptr;   // sigma terms of k_probs row blocks 1 .. parts-1
     int64_t spart_cap = 0;     // doubles
@@ -225,6 +228,9 @@ void release_all(qn_batch *h) {
     h->gv_stprev = nullptr;
     h->gv_ekey = nullptr;
     h->gv_i32 = nullptr;
+    h->gv_htrue = nullptr;
+    h->gv_p1m = nullptr;
+    h->gv_cls = nullptr;
     h->gv_cap = 0;
     h->spart = nullptr;
     h->spart_cap = 0;
@@ -752,7 +758,10 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
         QN_TRY(alloc_t(h, &h->gv_T, (size_t)kc * kGroupBins));
         QN_TRY(alloc_t(h, &h->gv_stprev, (size_t)kc));
         QN_TRY(alloc_t(h, &h->gv_ekey, (size_t)kc));
-        QN_TRY(alloc_t(h, &h->gv_i32, (size_t)6 * kc));
+        QN_TRY(alloc_t(h, &h->gv_i32, (size_t)7 * kc));
+        QN_TRY(alloc_t(h, &h->gv_htrue, (size_t)kc * kGroupBins));
+        QN_TRY(alloc_t(h, &h->gv_p1m, (size_t)kc * 2 * kMaxGroupEdges));
+        QN_TRY(alloc_t(h, &h->gv_cls, (size_t)kc));
         h->gv_cap = kc;
     }
     if (grouped && h->gr_cap < (int64_t)h->groups.size()) {
@@ -875,6 +884,12 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             gv.lstart = h->gv_i32 + 3 * h->gv_cap;
             gv.lcount = h->gv_i32 + 4 * h->gv_cap;
             gv.parent = h->gv_i32 + 5 * h->gv_cap;
+            gv.pos_slot = h->gv_i32 + 6 * h->gv_cap;
+            gv.members = kc;
+            gv.Htrue = h->gv_htrue;
+            gv.p1m = h->gv_p1m;
+            gv.cls = h->gv_cls;
+            gv.ncls = sv.fork_count;  // reset by the fork-finish kernel
             gv.src = nullptr;
             gv.slot_base = 0;
             cudaError_t e = cudaSuccess;

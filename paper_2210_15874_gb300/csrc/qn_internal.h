@@ -120,6 +120,15 @@ constexpr int kMixSubs = 4;  // tiles per thread block (streamed through two sha
 
 // Device view of one group step.  Per-slot arrays are indexed by slot; the
 // per-member scratch arrays by the position of the member in SlotView::members.
+// One outcome class of a slot in a group (written by the class step, read by the table step).
+struct GroupClass {
+    uint64_t key;    // outcome string: per gate, Pauli code (4 bits) and jumps (2 bits)
+    int32_t slot;    // the slot the members were in
+    int32_t target;  // the slot that holds them after the group (slot itself for class 0)
+    int32_t start;   // first member position
+    int32_t count;   // members
+};
+
 struct GroupView {
     const GateGroup *grp;    // group applied by this step
     const GateGroup *next;   // phase group whose joint the apply sweep accumulates, or nullptr
@@ -130,16 +139,22 @@ struct GroupView {
     int32_t vq;              // > 0: the apply sweep accumulates instead the joint of the
                              // mixer block on qubits 0 .. vq-1 after rotations (vc, vs)
     float vc, vs;
-    unsigned long long *Hcur;   // [max_slots][256] joint of this group, fixed point 2^-60
-    unsigned long long *Hnext;  // [max_slots][256] joint of the next group (zero on entry)
-    float2 *T;             // [max_slots][256] amplitude factor by stored bits of S
+    unsigned long long *Hcur;   // [max_slots][kGroupBins] joint of this group, fixed point 2^-60
+    unsigned long long *Hnext;  // [max_slots][kGroupBins] joint of the next group (zero on entry)
+    float2 *T;             // [max_slots][kGroupBins] amplitude factor by stored bits of S
     TrajState *st_prev;    // [max_slots] pending op of the gate before the group
-    uint64_t *ekey;        // [K] outcome string of the k-th event member of a slot
-    int32_t *evt;          // [K] member index (within the slot) of the k-th event member
-    int32_t *rep;          // [K] first event of a slot with the same outcome string
-    int32_t *lead;         // [K] events that open a class, in event order
-    int32_t *lstart;       // [K] first position of each opened class
-    int32_t *lcount;       // [K] members of each opened class
+    float *Htrue;          // [max_slots][kGroupBins] this group's joint by true bits (FP32)
+    float *p1m;            // [max_slots][2 kMaxGroupEdges] shared path's gamma P(q=1) per site
+    int32_t *pos_slot;     // [K] slot of each member position
+    int32_t members;       // member positions in the prefix tree (K of this run)
+    uint64_t *ekey;        // [K] outcome string of the member at each position (0: shared path)
+    int32_t *evt;          // [K] per slot: member index of the k-th member with an event
+    int32_t *rep;          // [K] per slot: first event with the same outcome string
+    int32_t *lead;         // [K] per slot: events that open a class, in event order
+    int32_t *lstart;       // [K] per slot: first position of each opened class
+    int32_t *lcount;       // [K] per slot: members of each opened class
+    GroupClass *cls;       // [max_slots] the classes of all slots
+    int32_t *ncls;         // device counter of cls (reset by the fork-finish kernel)
 };
 
 // One QAOA layer for the fused (Pauli-only) sweeps.
@@ -225,8 +240,7 @@ cudaError_t launch_slot_fork(const BatchView &v, const SlotView &sv, int active,
 // accumulates the next group's joint).
 cudaError_t launch_group_hist(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int ns, int active,
-                                double gamma,
-                                cudaStream_t s);
+                                double gamma, cudaStream_t s);
 cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s);
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
 // Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n

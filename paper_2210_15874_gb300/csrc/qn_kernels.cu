@@ -1533,50 +1533,90 @@ __device__ __forceinline__ float site_weight(const float (&w)[R], int lane, uint
     return warp_sumf(t[0]);
 }
 
-// Branches of every member of one slot through one group.  Lane l of a warp
-// holds the patterns b = l + 32 r (true bits of S, r < kPatR) of the joint: at the
-// start of a phase group, after the rotations of a mixer block.
-// kPatR patterns per lane: 1 for groups on <= 5 qubits, 4 for <= 7, 16 for <= 9.
+// The draws of a group, in four steps.  FP32 throughout (FP64 is slow on this
+// part and the joint comes from FP32 amplitudes); the shared path and every
+// member's own path run the same operations in the same order (site_weight,
+// the closed-form total), so a member that never leaves the shared path draws
+// exactly what the shared path drew.  A warp holds the patterns b = lane + 32 r
+// (true bits of S, r < kPatR) of the joint: at the start of a phase group,
+// after the rotations of a mixer block.
+//   1 k_gd_joint    block per slot: joint by true bits, the shared path's
+//                   gamma P(q=1) per site, the slot of each member position
+//   2 k_gd_members  thread per member: leaves the shared path? a warp per
+//                   such member draws its outcome string (key)
+//   3 k_gd_classes  block per slot: classes by first occurrence, the stable
+//                   member partition, forks
+//   4 k_gd_tables   warp per class: factor table and the state after the group
+
+// The outcome string of one member from the slot's joint h0: its Pauli codes
+// and damping words, staged in shared memory (codes[e], dws[2e + site]).
+// Writes the jump bits into the member's branch bytes (lane 0).
 template <int kPatR>
-__global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView sv, GroupView gv, double gamma) {
+__device__ uint64_t member_key(const BatchView &v, const GateGroup *gp, const float (&h0)[kPatR], float tot0,
+                               const uint8_t *codes, const uint32_t *dws, size_t gbase, float gf, float omg, int lane) {
+    const int m = gp->m, kind = gp->kind, nsite = kind == 0 ? 2 : 1;
+    float w[kPatR];
+#pragma unroll
+    for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
+    float tot = tot0;
+    uint32_t flip = 0;
+    uint64_t key = 0;
+    for (int e = 0; e < m; ++e) {
+        const int code = codes[e];
+        const GateCode gc = gate_code(kind, code);
+        flip ^= (gc.xa << gp->ei[e]) ^ (gc.xb << gp->ej[e]);
+        key |= (uint64_t)code << (6 * e);
+        int jumps = 0;
+        for (int k2 = 0; k2 < nsite; ++k2) {
+            const int qi = k2 ? gp->ej[e] : gp->ei[e];
+            const float one = site_weight<kPatR>(w, lane, flip, qi);
+            const bool j = ((double)dws[2 * e + k2] + 0.5) * kTwoM32 < (double)__fdiv_rn(__fmul_rn(gf, one), tot);
+            tot = j ? __fmul_rn(gf, one) : __fsub_rn(tot, __fmul_rn(gf, one));
+#pragma unroll
+            for (int r = 0; r < kPatR; ++r) {
+                const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
+                w[r] = j ? (bit ? __fmul_rn(w[r], gf) : 0.0f) : (bit ? __fmul_rn(w[r], omg) : w[r]);
+            }
+            if (j) {
+                flip ^= 1u << qi;
+                jumps |= 1 << k2;
+            }
+        }
+        key |= (uint64_t)jumps << (6 * e + 4);
+        if (lane == 0) v.branch[gbase + e] = (uint8_t)(code | (jumps << 4));
+    }
+    return key;
+}
+
+template <int kPatR>
+__global__ void __launch_bounds__(kThreads) k_gd_joint(BatchView v, SlotView sv, GroupView gv, double gamma) {
     grid_dependency_wait();
     const int slot = blockIdx.x;
     const GateGroup *gp = gv.grp;
-    const int m = gp->m, ns = gp->s, nbins = 1 << ns, kind = gp->kind;
-    const int nsite = kind == 0 ? 2 : 1;
+    const int m = gp->m, ns = gp->s, nbins = 1 << ns, nsite = gp->kind == 0 ? 2 : 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TrajState st = v.st[slot];
     const uint32_t Fb = st.J ^ st.pend;  // frame once the pending op is applied
     uint32_t fS = 0;
     for (int k = 0; k < ns; ++k) fS |= ((Fb >> gp->sp[k]) & 1u) << k;
-    // FP32 throughout (FP64 is slow on this part and the joint comes from FP32
-    // amplitudes); the shared path and every member's own path run the same
-    // operations in the same order, so a member that never leaves the shared
-    // path draws exactly what the shared path drew.
-    __shared__ float hd[kGroupBins];  // joint by true bits of S
-    __shared__ float p1m[2 * kMaxGroupEdges];
-    __shared__ int child_base;
-    unsigned long long *Hs = gv.Hcur + (size_t)slot * kGroupBins;
+    __shared__ float hd[kGroupBins];
     for (int b = threadIdx.x; b < 32 * kPatR; b += kThreads) hd[b] = 0.0f;
     __syncthreads();
+    unsigned long long *Hs = gv.Hcur + (size_t)slot * kGroupBins;
     for (int b = threadIdx.x; b < nbins; b += kThreads) {
         hd[b ^ fS] = (float)((double)Hs[b] * kHistUnit);
         Hs[b] = 0ull;  // zero again for the next group that accumulates here
     }
     __syncthreads();
-    float h0[kPatR];
-#pragma unroll
-    for (int r = 0; r < kPatR; ++r) h0[r] = hd[lane + 32 * r];
-    // total weight, carried through the sites in closed form (the same arithmetic on
-    // the shared path and on every member's own path)
-    const float tot0 = site_weight<kPatR>(h0, lane, 0u, -1);
-    const float gf = (float)gamma, omg = (float)(1.0 - gamma);
-    const float sg = (float)sqrt(gamma), sg1 = (float)sqrt(1.0 - gamma);
-    if (warp == 0) {  // the identity / no-jump path: P(q = 1) at every damping site
+    float *ht = gv.Htrue + (size_t)slot * kGroupBins;
+    for (int b = threadIdx.x; b < 32 * kPatR; b += kThreads) ht[b] = hd[b];
+    if (warp == 0) {  // the identity / no-jump path: gamma P(q = 1) at every damping site
+        const float gf = (float)gamma, omg = (float)(1.0 - gamma);
         float w[kPatR];
 #pragma unroll
-        for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
-        float tot = tot0;
+        for (int r = 0; r < kPatR; ++r) w[r] = hd[lane + 32 * r];
+        float tot = site_weight<kPatR>(w, lane, 0u, -1);
+        float *p1m = gv.p1m + (size_t)slot * 2 * kMaxGroupEdges;
         for (int e = 0; e < m; ++e)
             for (int k2 = 0; k2 < nsite; ++k2) {
                 const int qi = k2 ? gp->ej[e] : gp->ei[e];
@@ -1590,87 +1630,84 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
                 }
             }
     }
-    __syncthreads();
+    if (threadIdx.x == 0) gv.st_prev[slot] = st;
+    const int2 rg = sv.range[slot];
+    for (int i = threadIdx.x; i < rg.y; i += kThreads) gv.pos_slot[rg.x + i] = slot;
+    allow_dependent_launch();
+}
+
+template <int kPatR>
+__global__ void __launch_bounds__(kThreads) k_gd_members(BatchView v, SlotView sv, GroupView gv, double gamma) {
+    grid_dependency_wait();
+    const GateGroup *gp = gv.grp;
+    const int m = gp->m, nsite = gp->kind == 0 ? 2 : 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pos = blockIdx.x * kThreads + threadIdx.x;
+    bool ev = false;
+    if (pos < gv.members) {
+        // all of the member's codes and words first (independent loads), then the tests
+        const int slot = gv.pos_slot[pos];
+        const size_t g0 = (size_t)sv.members[pos] * v.G + gp->g0;
+        const float *p1m = gv.p1m + (size_t)slot * 2 * kMaxGroupEdges;
+        uint32_t codes = 0, dwv[2 * kMaxGroupEdges];
+#pragma unroll
+        for (int e = 0; e < kMaxGroupEdges; ++e)
+            if (e < m) {
+                codes |= (uint32_t)(v.branch[g0 + e] & 15);
+                dwv[2 * e] = v.dwords[(g0 + e) * 2];
+                dwv[2 * e + 1] = nsite == 2 ? v.dwords[(g0 + e) * 2 + 1] : 0xffffffffu;
+            }
+        ev = codes != 0;
+#pragma unroll
+        for (int e = 0; e < kMaxGroupEdges; ++e)
+            if (e < m) {
+                ev = ev || ((double)dwv[2 * e] + 0.5) * kTwoM32 < (double)p1m[2 * e];
+                if (nsite == 2) ev = ev || ((double)dwv[2 * e + 1] + 0.5) * kTwoM32 < (double)p1m[2 * e + 1];
+            }
+        if (!ev) gv.ekey[pos] = 0;
+    }
+    __shared__ int evl[kThreads];
+    const int ne = block_select(kThreads, [&](int) { return ev; }, [&](int r, int i) { evl[r] = i; });
+    __shared__ uint8_t s_code[kThreads / 32][kMaxGroupEdges];
+    __shared__ uint32_t s_dw[kThreads / 32][2 * kMaxGroupEdges];
+    const float gf = (float)gamma, omg = (float)(1.0 - gamma);
+    for (int a = warp; a < ne; a += kThreads / 32) {  // their own draws: one warp each
+        const int p = blockIdx.x * kThreads + evl[a];
+        const int slot = gv.pos_slot[p];
+        const size_t gbase = (size_t)sv.members[p] * v.G + gp->g0;
+        if (lane < m) s_code[warp][lane] = v.branch[gbase + lane] & 15;
+        if (lane < 2 * m) s_dw[warp][lane] = v.dwords[gbase * 2 + lane];
+        float h0[kPatR];
+        const float *ht = gv.Htrue + (size_t)slot * kGroupBins;
+#pragma unroll
+        for (int r = 0; r < kPatR; ++r) h0[r] = ht[lane + 32 * r];
+        const float tot0 = site_weight<kPatR>(h0, lane, 0u, -1);
+        __syncwarp();
+        const uint64_t key = member_key<kPatR>(v, gp, h0, tot0, s_code[warp], s_dw[warp], gbase, gf, omg, lane);
+        if (lane == 0) gv.ekey[p] = key;
+        __syncwarp();  // the staged codes are refilled for the warp's next member
+    }
+    allow_dependent_launch();
+}
+
+__global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView sv, GroupView gv) {
+    grid_dependency_wait();
+    const int slot = blockIdx.x;
+    __shared__ int child_base;
     const int2 rg = sv.range[slot];
     const int off = rg.x, cnt = rg.y;
     const int32_t *mem = sv.members + off;
+    const uint64_t *key = gv.ekey + off;
     int32_t *evt = gv.evt + off, *rep = gv.rep + off, *lead = gv.lead + off;
-    uint64_t *ekey = gv.ekey + off;
-    // members that leave the shared path somewhere in the group, in member order
-    const int ne = block_select(
-        cnt,
-        [&](int i) {
-            // all of the member's codes and words first (independent loads), then the tests
-            const size_t g0 = (size_t)mem[i] * v.G + gp->g0;
-            uint32_t codes = 0, dwv[2 * kMaxGroupEdges];
-#pragma unroll
-            for (int e = 0; e < kMaxGroupEdges; ++e)
-                if (e < m) {
-                    codes |= (uint32_t)(v.branch[g0 + e] & 15);
-                    dwv[2 * e] = v.dwords[(g0 + e) * 2];
-                    dwv[2 * e + 1] = nsite == 2 ? v.dwords[(g0 + e) * 2 + 1] : 0xffffffffu;
-                }
-            bool ev = codes != 0;
-#pragma unroll
-            for (int e = 0; e < kMaxGroupEdges; ++e)
-                if (e < m) {
-                    ev = ev || ((double)dwv[2 * e] + 0.5) * kTwoM32 < (double)p1m[2 * e];
-                    if (nsite == 2) ev = ev || ((double)dwv[2 * e + 1] + 0.5) * kTwoM32 < (double)p1m[2 * e + 1];
-                }
-            return ev;
-        },
-        [&](int r, int i) { evt[r] = i; });
-    __shared__ uint8_t s_code[kThreads / 32][kMaxGroupEdges];
-    __shared__ uint32_t s_dw[kThreads / 32][2 * kMaxGroupEdges];
-    for (int a = warp; a < ne; a += kThreads / 32) {  // their own draws: one warp each
-        const int t = mem[evt[a]];
-        // the member's codes and damping words, one load per lane
-        if (lane < m) s_code[warp][lane] = v.branch[(size_t)t * v.G + gp->g0 + lane] & 15;
-        if (lane < 2 * m) s_dw[warp][lane] = v.dwords[((size_t)t * v.G + gp->g0) * 2 + lane];
-        __syncwarp();
-        float w[kPatR];
-#pragma unroll
-        for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
-        float tot = tot0;
-        uint32_t flip = 0;
-        uint64_t key = 0;
-        for (int e = 0; e < m; ++e) {
-            const size_t gi = (size_t)t * v.G + gp->g0 + e;
-            const int code = s_code[warp][e];
-            const uint32_t *dw = &s_dw[warp][2 * e];
-            const GateCode gc = gate_code(kind, code);
-            flip ^= (gc.xa << gp->ei[e]) ^ (gc.xb << gp->ej[e]);
-            key |= (uint64_t)code << (6 * e);
-            int jumps = 0;
-            for (int k2 = 0; k2 < nsite; ++k2) {
-                const int qi = k2 ? gp->ej[e] : gp->ei[e];
-                const float one = site_weight<kPatR>(w, lane, flip, qi);
-                const bool j = ((double)dw[k2] + 0.5) * kTwoM32 < (double)__fdiv_rn(__fmul_rn(gf, one), tot);
-                tot = j ? __fmul_rn(gf, one) : __fsub_rn(tot, __fmul_rn(gf, one));
-#pragma unroll
-                for (int r = 0; r < kPatR; ++r) {
-                    const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> qi) & 1u) != 0;
-                    w[r] = j ? (bit ? __fmul_rn(w[r], gf) : 0.0f) : (bit ? __fmul_rn(w[r], omg) : w[r]);
-                }
-                if (j) {
-                    flip ^= 1u << qi;
-                    jumps |= 1 << k2;
-                }
-            }
-            key |= (uint64_t)jumps << (6 * e + 4);
-            if (lane == 0) v.branch[gi] = (uint8_t)(code | (jumps << 4));
-        }
-        if (lane == 0) ekey[a] = key;
-        __syncwarp();  // the staged codes are refilled for the warp's next member
-    }
-    __syncthreads();
+    // members that left the shared path, in member order
+    const int ne = block_select(cnt, [&](int i) { return key[i] != 0; }, [&](int r, int i) { evt[r] = i; });
     // classes: the shared path (if any member kept it), then one per distinct
     // outcome string in order of its first event
     for (int a = threadIdx.x; a < ne; a += kThreads) {
-        const uint64_t ka = ekey[a];
+        const uint64_t ka = key[evt[a]];
         int r = a;
         for (int b = 0; b < a; ++b)
-            if (ekey[b] == ka) {
+            if (key[evt[b]] == ka) {
                 r = b;
                 break;
             }
@@ -1709,90 +1746,111 @@ __global__ void __launch_bounds__(kThreads) k_group_decide(BatchView v, SlotView
         __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += kThreads) sv.members[off + i] = sv.tmp[off + i];
     }
-    // per class: amplitude factors T (by stored bits of S) and the state after the group
-    for (int c = warp; c < nc; c += kThreads / 32) {
-        uint64_t key = 0;
-        int start = off, count = mainc;
+    for (int c = threadIdx.x; c < nc; c += kThreads) {
+        GroupClass gc;
+        gc.key = 0;
+        gc.slot = slot;
+        gc.start = off;
+        gc.count = mainc;
         if (c >= hasmain) {
             const int r = c - hasmain;
-            key = ekey[lead[r]];
-            start = off + gv.lstart[off + r];
-            count = gv.lcount[off + r];
+            gc.key = key[evt[lead[r]]];
+            gc.start = off + gv.lstart[off + r];
+            gc.count = gv.lcount[off + r];
         }
-        const int target = c == 0 ? slot : child_base + c - 1;
-        if (target >= sv.max_slots) {
-            if (lane == 0) atomicOr(v.status, 4);
+        gc.target = c == 0 ? slot : child_base + c - 1;
+        if (gc.target >= sv.max_slots) {
+            atomicOr(v.status, 4);
             continue;
         }
-        float ar[kPatR], ai[kPatR], w[kPatR];
-        uint32_t flip = 0;
-#pragma unroll
-        for (int r = 0; r < kPatR; ++r) {
-            ar[r] = 1.0f;
-            ai[r] = 0.0f;
-            w[r] = h0[r];
-        }
-        const float gc = gp->c, gs = gp->sn;
-        for (int e = 0; e < m; ++e) {
-            const int code = (int)((key >> (6 * e)) & 15u);
-            const int qi = gp->ei[e], qj = gp->ej[e];
-            const GateCode pc = gate_code(kind, code);
-#pragma unroll
-            for (int r = 0; r < kPatR; ++r) {  // phase, then the Pauli's Z part, on the bits before its X part
-                const uint32_t cb = (uint32_t)(lane + 32 * r) ^ flip;
-                const uint32_t ci = (cb >> qi) & 1u, cj = (cb >> qj) & 1u;
-                if (kind == 0 && ci != cj) {
-                    const float nr = ar[r] * gc + ai[r] * gs, ni = ai[r] * gc - ar[r] * gs;
-                    ar[r] = nr;
-                    ai[r] = ni;
-                }
-                if ((pc.za & ci) ^ (pc.zb & cj)) {
-                    ar[r] = -ar[r];
-                    ai[r] = -ai[r];
-                }
-            }
-            flip ^= (pc.xa << qi) ^ (pc.xb << qj);
-            for (int k2 = 0; k2 < nsite; ++k2) {
-                const int q = k2 ? qj : qi;
-                const bool j = ((key >> (6 * e + 4 + k2)) & 1u) != 0;
-#pragma unroll
-                for (int r = 0; r < kPatR; ++r) {
-                    const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> q) & 1u) != 0;
-                    const float kf = j ? (bit ? sg : 0.0f) : (bit ? sg1 : 1.0f);
-                    ar[r] *= kf;
-                    ai[r] *= kf;
-                    w[r] *= kf * kf;
-                }
-                if (j) flip ^= 1u << q;
-            }
-        }
-        float N = 0.0f;
-#pragma unroll
-        for (int r = 0; r < kPatR; ++r) N += w[r];
-        N = warp_sumf(N);
-        const float sc = 1.0f / sqrtf(N);
-        if (lane == 0 && !(N > 0.0f && isfinite(sc))) atomicOr(v.status, 1);
-#pragma unroll
-        for (int r = 0; r < kPatR; ++r) {
-            const int b = lane + 32 * r;
-            if (b < nbins)
-                gv.T[(size_t)target * kGroupBins + (b ^ fS)] = make_float2(ar[r] * sc, ai[r] * sc);
-        }
-        if (lane == 0) {
-            uint32_t qflip = 0;
-            for (int k = 0; k < ns; ++k) qflip |= ((flip >> k) & 1u) << gp->sp[k];
-            TrajState nst;
-            nst.J = Fb ^ qflip;
-            nst.pend = 0;
-            nst.pq0 = nst.pq1 = 0;
-            nst.f[0] = nst.f[1] = nst.f[2] = nst.f[3] = 1.0f;
-            gv.st_prev[target] = st;
-            v.st[target] = nst;
-            sv.range[target] = make_int2(start, count);
-            if (c > 0) gv.parent[target] = slot;  // its first sweep reads the parent's state
-        }
+        gv.cls[atomicAdd(gv.ncls, 1)] = gc;
     }
     allow_dependent_launch();
+}
+
+template <int kPatR>
+__global__ void __launch_bounds__(kThreads) k_gd_tables(BatchView v, SlotView sv, GroupView gv, double gamma) {
+    grid_dependency_wait();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * (kThreads / 32) + warp;
+    if (c >= *gv.ncls) return;
+    const GroupClass gc = gv.cls[c];
+    const GateGroup *gp = gv.grp;
+    const int m = gp->m, ns = gp->s, nbins = 1 << ns, kind = gp->kind, nsite = kind == 0 ? 2 : 1;
+    const TrajState st = gv.st_prev[gc.slot];
+    const uint32_t Fb = st.J ^ st.pend;
+    uint32_t fS = 0;
+    for (int k = 0; k < ns; ++k) fS |= ((Fb >> gp->sp[k]) & 1u) << k;
+    const float sg = (float)sqrt(gamma), sg1 = (float)sqrt(1.0 - gamma);
+    const float *ht = gv.Htrue + (size_t)gc.slot * kGroupBins;
+    float ar[kPatR], ai[kPatR], w[kPatR];
+    uint32_t flip = 0;
+#pragma unroll
+    for (int r = 0; r < kPatR; ++r) {
+        ar[r] = 1.0f;
+        ai[r] = 0.0f;
+        w[r] = ht[lane + 32 * r];
+    }
+    const float gcos = gp->c, gsin = gp->sn;
+    for (int e = 0; e < m; ++e) {
+        const int code = (int)((gc.key >> (6 * e)) & 15u);
+        const int qi = gp->ei[e], qj = gp->ej[e];
+        const GateCode pc = gate_code(kind, code);
+#pragma unroll
+        for (int r = 0; r < kPatR; ++r) {  // phase, then the Pauli's Z part, on the bits before its X part
+            const uint32_t cb = (uint32_t)(lane + 32 * r) ^ flip;
+            const uint32_t ci = (cb >> qi) & 1u, cj = (cb >> qj) & 1u;
+            if (kind == 0 && ci != cj) {
+                const float nr = ar[r] * gcos + ai[r] * gsin, ni = ai[r] * gcos - ar[r] * gsin;
+                ar[r] = nr;
+                ai[r] = ni;
+            }
+            if ((pc.za & ci) ^ (pc.zb & cj)) {
+                ar[r] = -ar[r];
+                ai[r] = -ai[r];
+            }
+        }
+        flip ^= (pc.xa << qi) ^ (pc.xb << qj);
+        for (int k2 = 0; k2 < nsite; ++k2) {
+            const int q = k2 ? qj : qi;
+            const bool j = ((gc.key >> (6 * e + 4 + k2)) & 1u) != 0;
+#pragma unroll
+            for (int r = 0; r < kPatR; ++r) {
+                const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> q) & 1u) != 0;
+                const float kf = j ? (bit ? sg : 0.0f) : (bit ? sg1 : 1.0f);
+                ar[r] *= kf;
+                ai[r] *= kf;
+                w[r] *= kf * kf;
+            }
+            if (j) flip ^= 1u << q;
+        }
+    }
+    float N = 0.0f;
+#pragma unroll
+    for (int r = 0; r < kPatR; ++r) N += w[r];
+    N = warp_sumf(N);
+    const float sc = 1.0f / sqrtf(N);
+    if (lane == 0 && !(N > 0.0f && isfinite(sc))) atomicOr(v.status, 1);
+#pragma unroll
+    for (int r = 0; r < kPatR; ++r) {
+        const int b = lane + 32 * r;
+        if (b < nbins) gv.T[(size_t)gc.target * kGroupBins + (b ^ fS)] = make_float2(ar[r] * sc, ai[r] * sc);
+    }
+    if (lane == 0) {
+        uint32_t qflip = 0;
+        for (int k = 0; k < ns; ++k) qflip |= ((flip >> k) & 1u) << gp->sp[k];
+        TrajState nst;
+        nst.J = Fb ^ qflip;
+        nst.pend = 0;
+        nst.pq0 = nst.pq1 = 0;
+        nst.f[0] = nst.f[1] = nst.f[2] = nst.f[3] = 1.0f;
+        v.st[gc.target] = nst;
+        sv.range[gc.target] = make_int2(gc.start, gc.count);
+        if (gc.target != gc.slot) {
+            gv.st_prev[gc.target] = st;      // the pending op of the gate before, applied with T
+            gv.parent[gc.target] = gc.slot;  // its first sweep reads the parent's state
+        }
+    }
 }
 
 // Copy the parent's statevector into every slot forked at this gate.
@@ -2590,10 +2648,24 @@ cudaError_t launch_group_hist(const BatchView &v, const SlotView &, const GroupV
 
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int ns, int active,
                                 double gamma, cudaStream_t s) {
-    cudaError_t e = ns <= 5   ? launch_pdl(k_group_decide<1>, dim3((unsigned)active), dim3(kThreads), s, v, sv, gv, gamma)
-                    : ns <= 7 ? launch_pdl(k_group_decide<4>, dim3((unsigned)active), dim3(kThreads), s, v, sv, gv, gamma)
-                              : launch_pdl(k_group_decide<kGroupBins / 32>, dim3((unsigned)active), dim3(kThreads), s, v,
-                                           sv, gv, gamma);
+    const dim3 blk(kThreads);
+    const dim3 slots((unsigned)active);
+    const dim3 members((unsigned)((gv.members + kThreads - 1) / kThreads));
+    const dim3 classes((unsigned)((sv.max_slots + kThreads / 32 - 1) / (kThreads / 32)));
+    cudaError_t e;
+#define QN_GD(R)                                                                                \
+    e = launch_pdl(k_gd_joint<R>, slots, blk, s, v, sv, gv, gamma);                             \
+    if (e == cudaSuccess) e = launch_pdl(k_gd_members<R>, members, blk, s, v, sv, gv, gamma);   \
+    if (e == cudaSuccess) e = launch_pdl(k_gd_classes, slots, blk, s, v, sv, gv);               \
+    if (e == cudaSuccess) e = launch_pdl(k_gd_tables<R>, classes, blk, s, v, sv, gv, gamma);
+    if (ns <= 5) {
+        QN_GD(1)
+    } else if (ns <= 7) {
+        QN_GD(4)
+    } else {
+        QN_GD(kGroupBins / 32)
+    }
+#undef QN_GD
     if (e != cudaSuccess) return e;
     return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
 }
