@@ -361,7 +361,7 @@ def gpu_arm(args):
             "config": config_of(w, {
                 "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
                 "mode": ("shared-prefix: one statevector per distinct Kraus prefix, all trajectories in one "
-                         "prefix tree" + ("; phase gates applied in groups on <= 9 qubits and mixer rotations "
+                         "prefix tree" + ("; phase gates applied in groups on <= 10 qubits and mixer rotations "
                                           "in blocks of 4 qubits, one sweep per group or block" if grouped
                                           else "; one sweep per gate")) if sharing else
                         (f"fused layers: ceil(n/3) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused

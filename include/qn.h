@@ -116,7 +116,7 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
  * sweep, and the mixer rotations are applied three qubits per sweep.  Needs
  * at most 64 edges; otherwise gates are swept one by one.  With damping == 0
  * fusion takes precedence over shared-prefix mode.  With damping, fusion acts
- * in shared-prefix mode only: consecutive phase gates of a layer on at most 9
+ * in shared-prefix mode only: consecutive phase gates of a layer on at most 10
  * qubits form a group whose damping branches are all drawn from one joint
  * distribution of those qubits, and the group is applied in one sweep; for
  * n >= 12 the mixer rotations go four qubits per sweep, their damping drawn
@@ -199,7 +199,7 @@ qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, doub
  * of the schedule qn_run_qaoa uses (no counterpart in the paper; host only,
  * no device memory).  For an n-qubit graph and depth p, writes up to
  * `capacity` groups in circuit order: kind (0 = consecutive phase gates of a
- * layer on at most 9 qubits, at most 10 gates; 1 = a block of consecutive
+ * layer on at most 10 qubits, at most 12 gates; 1 = a block of consecutive
  * mixer rotations, present when n >= 12), first gate (the noisy H layer is
  * gates 0 .. n-1), number of gates, and the group's qubits as a bit mask.
  * *count is the number of groups, also when it exceeds capacity.  Output

@@ -153,7 +153,7 @@ struct qn_batch {
     unsigned long long *gv_H = nullptr;  // [2][gv_cap][256]
     float2 *gv_T = nullptr;
     TrajState *gv_stprev = nullptr;
-    uint64_t *gv_ekey = nullptr;
+    GroupKey *gv_ekey = nullptr;
     int32_t *gv_i32 = nullptr;  // [7][gv_cap]: evt, rep, lead, lstart, lcount, parent, pos_slot
     float *gv_htrue = nullptr;  // [gv_cap][kGroupBins]
     float *gv_p1m = nullptr;    // [gv_cap][2 kMaxGroupEdges]
@@ -391,8 +391,9 @@ void build_gates(qn_batch *h) {
 bool mixer_blocks_fit(int n, int E) { return n >= 12 && E > 0; }
 
 // Phase-gate groups of every layer: greedy runs of consecutive ZZ gates whose
-// qubits number at most kMaxGroupQubits (at most kMaxGroupEdges gates, so that a member's
-// outcome string fits 6 bits per gate in 64 bits).
+// qubits number at most kMaxGroupQubits (joints of 2^10 bins), at most
+// kMaxGroupEdges gates (a member's outcome string takes 6 bits per gate in a
+// two-word key).
 void build_groups(qn_batch *h) {
     const int n = h->n, E = (int)h->edges.size() / 2;
     h->groups.clear();

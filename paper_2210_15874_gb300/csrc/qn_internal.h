@@ -70,13 +70,13 @@ struct SlotView {
     int32_t max_slots;
 };
 
-// Consecutive phase gates of one layer whose qubits S number at most 9 (shared-
+// Consecutive phase gates of one layer whose qubits S number at most 10 (shared-
 // prefix mode with damping): their damping branches follow from the joint
 // distribution of the true bits of S, because every op of the group is
 // diagonal (phases, Z parts, K0) or a relabelling (X parts, K1) in the stored
 // basis.
-constexpr int kMaxGroupEdges = 10;
-constexpr int kMaxGroupQubits = 9;
+constexpr int kMaxGroupEdges = 12;
+constexpr int kMaxGroupQubits = 10;
 constexpr int kGroupBins = 1 << kMaxGroupQubits;
 
 // A group of consecutive gates of one layer whose noise sites are all decided
@@ -121,8 +121,12 @@ constexpr int kMixSubs = 4;  // tiles per thread block (streamed through two sha
 // Device view of one group step.  Per-slot arrays are indexed by slot; the
 // per-member scratch arrays by the position of the member in SlotView::members.
 // One outcome class of a slot in a group (written by the class step, read by the table step).
+// A member's outcome string over a group: per gate 6 bits (Pauli code, then the
+// two jump bits); gates 0-9 in x, gates 10-11 in y.  All zero: the shared path.
+using GroupKey = ulonglong2;
+
 struct GroupClass {
-    uint64_t key;    // outcome string: per gate, Pauli code (4 bits) and jumps (2 bits)
+    GroupKey key;    // the class's outcome string
     int32_t slot;    // the slot the members were in
     int32_t target;  // the slot that holds them after the group (slot itself for class 0)
     int32_t start;   // first member position
@@ -147,7 +151,7 @@ struct GroupView {
     float *p1m;            // [max_slots][2 kMaxGroupEdges] shared path's gamma P(q=1) per site
     int32_t *pos_slot;     // [K] slot of each member position
     int32_t members;       // member positions in the prefix tree (K of this run)
-    uint64_t *ekey;        // [K] outcome string of the member at each position (0: shared path)
+    GroupKey *ekey;        // [K] outcome string of the member at each position (0: shared path)
     int32_t *evt;          // [K] per slot: member index of the k-th member with an event
     int32_t *rep;          // [K] per slot: first event with the same outcome string
     int32_t *lead;         // [K] per slot: events that open a class, in event order

@@ -822,7 +822,7 @@ __device__ __forceinline__ double df_warp_sum(float hi, float lo) {
 
 // ---------------------------------------------------------------------------
 // Phase-gate groups in shared-prefix mode.  A group is a run of consecutive
-// phase gates of one layer on a qubit set S of at most 9 qubits.  Every op of
+// phase gates of one layer on a qubit set S of at most 10 qubits.  Every op of
 // the group -- phase, Z part of a Pauli, K0 -- is diagonal in the stored basis,
 // and every X part or K1 jump only relabels true bits, so the branch of every
 // damping site in the group follows from the joint distribution of the true
@@ -1191,11 +1191,14 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     float scM = 1.0f;  // rsc^M: the block's rotations, folded into its factors
     for (int i = 0; i < M; ++i) scM *= rsc;
     __shared__ float Df[16];
-    __shared__ float hw[kWarps][kGroupBins];
+    // per-warp histograms of the next phase group's joint (variants that form one), else
+    // the per-warp rows of the next mixer block's joint
+    constexpr bool kHist = VAR == kMixAny || VAR == kMixHist;
+    __shared__ float hw_flat[kHist ? kWarps * kGroupBins : kWarps * kJointBins];
     if (threadIdx.x < 16u)
         Df[threadIdx.x] = threadIdx.x < (1u << M) ? gv.T[(size_t)slot * kGroupBins + threadIdx.x].x * scM : 0.0f;
     if (nx)
-        for (int i = threadIdx.x; i < kWarps * kGroupBins; i += kMixThreads) (&hw[0][0])[i] = 0.0f;
+        for (int i = threadIdx.x; i < kWarps * kGroupBins; i += kMixThreads) hw_flat[i] = 0.0f;
     // float4 indices fit 32 bits (n <= 30)
     uint32_t offL = 0, offW = 0, ao[kMixQ];
 #pragma unroll
@@ -1345,7 +1348,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
                 int ks = 0;
 #pragma unroll
                 for (int i = 0; i < kMixQ; ++i) ks |= (j & (1 << i)) ? nab[i] : 0;
-                hist_push(hw[warp], gn, ne1, ks, x[j].x * x[j].x + x[j].y * x[j].y, x[j].z * x[j].z + x[j].w * x[j].w,
+                hist_push(hw_flat + warp * kGroupBins, gn, ne1, ks, x[j].x * x[j].x + x[j].y * x[j].y, x[j].z * x[j].z + x[j].w * x[j].w,
                           run);
             }
             if (final_norm) {
@@ -1354,7 +1357,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
             }
         }
         if (nx) {  // the per-thread bin part changes with the tile
-            hist_close(hw[warp], gn, ne1, run);
+            hist_close(hw_flat + warp * kGroupBins, gn, ne1, run);
             run = HistRun();
         }
         if (nN > 0 || has0) __syncthreads();
@@ -1404,7 +1407,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         }
         float sc2 = 1.0f;  // the next block's rotations were taken up to rsc each: restore |.|^2
         for (int i = 0; i < nN; ++i) sc2 *= rsc * rsc;
-        float *red = &hw[0][0];
+        float *red = hw_flat;
 #pragma unroll
         for (int b = 0; b < kMixE; ++b) {
             float x = acc[b] * sc2;
@@ -1419,7 +1422,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         __syncthreads();
         for (int b = threadIdx.x; b < (1 << nx->s); b += kMixThreads) {
             double a2 = 0.0;
-            for (int w = 0; w < kWarps; ++w) a2 += (double)hw[w][b];
+            for (int w = 0; w < kWarps; ++w) a2 += (double)hw_flat[w * kGroupBins + b];
             if (a2 > 0.0) atomicAdd(gv.Hnext + (size_t)slot * kGroupBins + b, __double2ull_rn(a2 * kHistScale));
         }
     }
@@ -1548,11 +1551,21 @@ __device__ __forceinline__ float site_weight(const float (&w)[R], int lane, uint
 //                   member partition, forks
 //   4 k_gd_tables   warp per class: factor table and the state after the group
 
+__device__ __forceinline__ void key_put(GroupKey &k, int e, uint64_t bits) {
+    if (e < 10) k.x |= bits << (6 * e);
+    else k.y |= bits << (6 * (e - 10));
+}
+__device__ __forceinline__ int key_gate(const GroupKey &k, int e) {  // the gate's 6 bits
+    return (int)((e < 10 ? k.x >> (6 * e) : k.y >> (6 * (e - 10))) & 63u);
+}
+__device__ __forceinline__ bool key_eq(const GroupKey &a, const GroupKey &b) { return a.x == b.x && a.y == b.y; }
+__device__ __forceinline__ bool key_zero(const GroupKey &a) { return (a.x | a.y) == 0; }
+
 // The outcome string of one member from the slot's joint h0: its Pauli codes
 // and damping words, staged in shared memory (codes[e], dws[2e + site]).
 // Writes the jump bits into the member's branch bytes (lane 0).
 template <int kPatR>
-__device__ uint64_t member_key(const BatchView &v, const GateGroup *gp, const float (&h0)[kPatR], float tot0,
+__device__ GroupKey member_key(const BatchView &v, const GateGroup *gp, const float (&h0)[kPatR], float tot0,
                                const uint8_t *codes, const uint32_t *dws, size_t gbase, float gf, float omg, int lane) {
     const int m = gp->m, kind = gp->kind, nsite = kind == 0 ? 2 : 1;
     float w[kPatR];
@@ -1560,12 +1573,11 @@ __device__ uint64_t member_key(const BatchView &v, const GateGroup *gp, const fl
     for (int r = 0; r < kPatR; ++r) w[r] = h0[r];
     float tot = tot0;
     uint32_t flip = 0;
-    uint64_t key = 0;
+    GroupKey key = make_ulonglong2(0ull, 0ull);
     for (int e = 0; e < m; ++e) {
         const int code = codes[e];
         const GateCode gc = gate_code(kind, code);
         flip ^= (gc.xa << gp->ei[e]) ^ (gc.xb << gp->ej[e]);
-        key |= (uint64_t)code << (6 * e);
         int jumps = 0;
         for (int k2 = 0; k2 < nsite; ++k2) {
             const int qi = k2 ? gp->ej[e] : gp->ei[e];
@@ -1582,7 +1594,7 @@ __device__ uint64_t member_key(const BatchView &v, const GateGroup *gp, const fl
                 jumps |= 1 << k2;
             }
         }
-        key |= (uint64_t)jumps << (6 * e + 4);
+        key_put(key, e, (uint64_t)(code | (jumps << 4)));
         if (lane == 0) v.branch[gbase + e] = (uint8_t)(code | (jumps << 4));
     }
     return key;
@@ -1664,7 +1676,7 @@ __global__ void __launch_bounds__(kThreads) k_gd_members(BatchView v, SlotView s
                 ev = ev || ((double)dwv[2 * e] + 0.5) * kTwoM32 < (double)p1m[2 * e];
                 if (nsite == 2) ev = ev || ((double)dwv[2 * e + 1] + 0.5) * kTwoM32 < (double)p1m[2 * e + 1];
             }
-        if (!ev) gv.ekey[pos] = 0;
+        if (!ev) gv.ekey[pos] = make_ulonglong2(0ull, 0ull);
     }
     __shared__ int evl[kThreads];
     const int ne = block_select(kThreads, [&](int) { return ev; }, [&](int r, int i) { evl[r] = i; });
@@ -1683,7 +1695,7 @@ __global__ void __launch_bounds__(kThreads) k_gd_members(BatchView v, SlotView s
         for (int r = 0; r < kPatR; ++r) h0[r] = ht[lane + 32 * r];
         const float tot0 = site_weight<kPatR>(h0, lane, 0u, -1);
         __syncwarp();
-        const uint64_t key = member_key<kPatR>(v, gp, h0, tot0, s_code[warp], s_dw[warp], gbase, gf, omg, lane);
+        const GroupKey key = member_key<kPatR>(v, gp, h0, tot0, s_code[warp], s_dw[warp], gbase, gf, omg, lane);
         if (lane == 0) gv.ekey[p] = key;
         __syncwarp();  // the staged codes are refilled for the warp's next member
     }
@@ -1697,17 +1709,17 @@ __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView s
     const int2 rg = sv.range[slot];
     const int off = rg.x, cnt = rg.y;
     const int32_t *mem = sv.members + off;
-    const uint64_t *key = gv.ekey + off;
+    const GroupKey *key = gv.ekey + off;
     int32_t *evt = gv.evt + off, *rep = gv.rep + off, *lead = gv.lead + off;
     // members that left the shared path, in member order
-    const int ne = block_select(cnt, [&](int i) { return key[i] != 0; }, [&](int r, int i) { evt[r] = i; });
+    const int ne = block_select(cnt, [&](int i) { return !key_zero(key[i]); }, [&](int r, int i) { evt[r] = i; });
     // classes: the shared path (if any member kept it), then one per distinct
     // outcome string in order of its first event
     for (int a = threadIdx.x; a < ne; a += kThreads) {
-        const uint64_t ka = key[evt[a]];
+        const GroupKey ka = key[evt[a]];
         int r = a;
         for (int b = 0; b < a; ++b)
-            if (key[evt[b]] == ka) {
+            if (key_eq(key[evt[b]], ka)) {
                 r = b;
                 break;
             }
@@ -1748,7 +1760,7 @@ __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView s
     }
     for (int c = threadIdx.x; c < nc; c += kThreads) {
         GroupClass gc;
-        gc.key = 0;
+        gc.key = make_ulonglong2(0ull, 0ull);
         gc.slot = slot;
         gc.start = off;
         gc.count = mainc;
@@ -1793,7 +1805,7 @@ __global__ void __launch_bounds__(kThreads) k_gd_tables(BatchView v, SlotView sv
     }
     const float gcos = gp->c, gsin = gp->sn;
     for (int e = 0; e < m; ++e) {
-        const int code = (int)((gc.key >> (6 * e)) & 15u);
+        const int code = key_gate(gc.key, e) & 15;
         const int qi = gp->ei[e], qj = gp->ej[e];
         const GateCode pc = gate_code(kind, code);
 #pragma unroll
@@ -1813,7 +1825,7 @@ __global__ void __launch_bounds__(kThreads) k_gd_tables(BatchView v, SlotView sv
         flip ^= (pc.xa << qi) ^ (pc.xb << qj);
         for (int k2 = 0; k2 < nsite; ++k2) {
             const int q = k2 ? qj : qi;
-            const bool j = ((gc.key >> (6 * e + 4 + k2)) & 1u) != 0;
+            const bool j = ((key_gate(gc.key, e) >> (4 + k2)) & 1) != 0;
 #pragma unroll
             for (int r = 0; r < kPatR; ++r) {
                 const bool bit = ((((uint32_t)(lane + 32 * r) ^ flip) >> q) & 1u) != 0;

@@ -119,7 +119,7 @@ GROUP_CASES = {
     "n12_damping": dict(n=12, p=2, index=31, trajectories=300, p1=5e-3, p2=2e-2, damping=0.02),
     "n14_heavy_noise": dict(n=14, p=2, index=32, trajectories=96, p1=1e-2, p2=3e-2, damping=0.05),
     "n16_d5_ragged_groups": dict(n=16, p=1, index=41, trajectories=400, p1=2e-3, p2=1e-2, damping=0.01, d=5),
-    # 18 edges on 9 qubits: phase groups end at the 10-gate limit
+    # 18 edges on 9 qubits: phase groups end at the 12-gate limit
     "n9_d4_gate_limit": dict(n=9, p=2, index=42, trajectories=300, p1=5e-3, p2=2e-2, damping=0.02, d=4),
     # mixer blocks of 4, 4, 4 and 1 qubits: the last one takes the generic sweep
     "n13_d4_one_qubit_block": dict(n=13, p=2, index=43, trajectories=200, p1=5e-3, p2=2e-2, damping=0.02, d=4),

@@ -3,7 +3,7 @@ shared-prefix mode (qn_group_plan) and the tile maps of the mixer-block
 sweeps (qn_mix_tile_map).
 
 The groups must cover the circuit's gates exactly once and in circuit order:
-consecutive phase gates of one layer on at most 9 qubits and at most 10 gates,
+consecutive phase gates of one layer on at most 10 qubits and at most 12 gates,
 each group ending only where the next gate would break a limit or the layer
 ends; for n >= 12, consecutive mixer rotations in blocks of four qubits.  A
 tile map must be a bijection of the float4-index bits that puts the block's
@@ -14,7 +14,7 @@ import pytest
 
 from paper_2210_15874_gb300 import workloads as W
 
-MAX_QUBITS, MAX_GATES, BLOCK = 9, 10, 4
+MAX_QUBITS, MAX_GATES, BLOCK = 10, 12, 4
 
 
 @pytest.fixture(scope="module")
