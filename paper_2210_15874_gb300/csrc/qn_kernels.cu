@@ -847,14 +847,24 @@ __device__ __forceinline__ int group_bin(const GateGroup *gp, uint32_t y) {
 // Bins of one sweep block split into a per-thread part (tid and tile bits) and
 // a part that depends only on the unrolled loop indices (e, k, sub), kept in
 // the shared table vtab[e | k << 1 | sub << 3].
+// A sweep block covers amplitude bits 0-12 and fixes the higher ones, so it
+// touches only the bins of S's qubits below 13 -- the low `nlow` bin bits (S is
+// numbered in ascending qubit order) -- above a block-constant part `hi`.  The
+// block's histogram is indexed by the low bits alone.
 struct GroupBins {
-    int base;        // bins of this thread's tid and tile bits
+    int base;        // low bins of this thread's tid bits
     unsigned lmask;  // lane bits that are no qubit of S
+    int hi;          // the block's high bins (its tile bits)
+    int nlow;        // S's qubits below 13
 };
 
 __device__ __forceinline__ GroupBins group_bins(const GateGroup *gp, int tile, uint16_t *vtab) {
     GroupBins gb;
-    gb.base = group_bin(gp, ((uint32_t)threadIdx.x << 1) | ((uint32_t)tile << 13));
+    int nlow = 0;
+    while (nlow < gp->s && gp->sp[nlow] < 13) ++nlow;
+    gb.nlow = nlow;
+    gb.base = group_bin(gp, (uint32_t)threadIdx.x << 1);
+    gb.hi = group_bin(gp, (uint32_t)tile << 13);
     unsigned lm = 0;
     for (int i = 0; i < 5; ++i)
         if (group_bin(gp, 2u << i) == 0) lm |= 1u << i;
@@ -907,12 +917,18 @@ __device__ __forceinline__ void hist_push(float *hw, const GroupBins &gb, int e1
 }
 
 // Block histogram -> the slot's global joint (fixed-point integer adds).
-__device__ __forceinline__ void hist_commit(const float *hw, int nb, unsigned long long *H) {
-    for (int b = threadIdx.x; b < nb; b += kThreads) {
+__device__ __forceinline__ void hist_commit(const float *hw, const GroupBins &gb, unsigned long long *H) {
+    for (int b = threadIdx.x; b < (1 << gb.nlow); b += kThreads) {
         double acc = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) acc += (double)hw[w * kGroupBins + b];
-        if (acc > 0.0) atomicAdd(H + b, __double2ull_rn(acc * kHistScale));
+        if (acc > 0.0) atomicAdd(H + (gb.hi | b), __double2ull_rn(acc * kHistScale));
     }
+}
+
+// Zero the block's histogram rows (the low bins only).
+__device__ __forceinline__ void hist_zero(float *hw, int nlow) {
+    const int nb = 1 << nlow;
+    for (int i = threadIdx.x; i < (kThreads / 32) * nb; i += kThreads) hw[(i / nb) * kGroupBins + (i % nb)] = 0.0f;
 }
 
 __device__ __forceinline__ SweepCtx pending_ctx(const TrajState &s) {
@@ -934,8 +950,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
     const GateGroup *gp = gv.grp;
     __shared__ float hw[kThreads / 32][kGroupBins];
     __shared__ uint16_t vtab[32];
-    for (int i = threadIdx.x; i < (kThreads / 32) * kGroupBins; i += kThreads) (&hw[0][0])[i] = 0.0f;
     const GroupBins gb = group_bins(gp, tile, vtab);
+    hist_zero(&hw[0][0], gb.nlow);
     __syncthreads();
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
@@ -971,7 +987,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
     hist_close(my, gb, e1, run);
     __syncthreads();
     allow_dependent_launch();
-    hist_commit(&hw[0][0], 1 << gp->s, gv.Hcur + (size_t)slot * kGroupBins);
+    hist_commit(&hw[0][0], gb, gv.Hcur + (size_t)slot * kGroupBins);
 }
 
 // exp(-i beta X) on the amplitude pair (a, b) of one qubit: a' = c a - i s b,
@@ -1034,10 +1050,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     __shared__ uint16_t vT[32], vN[32];
     for (int i = threadIdx.x; i < (1 << gp->s); i += kThreads) Ts[i] = gv.T[(size_t)slot * kGroupBins + i];
     const GroupBins gt = group_bins(gp, tile, vT);
-    GroupBins gn{0, 0u};
+    GroupBins gn{0, 0u, 0, 0};
     if (nx) {
-        for (int i = threadIdx.x; i < (kThreads / 32) * kGroupBins; i += kThreads) (&hw[0][0])[i] = 0.0f;
         gn = group_bins(nx, tile, vN);
+        hist_zero(&hw[0][0], gn.nlow);
     }
     __syncthreads();
     const int n = v.n;
@@ -1064,7 +1080,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
             float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             if (f < nf) {
                 const uint32_t y = (uint32_t)(2 * f);
-                const int tb = gt.base | vT[(k << 1) | (sub << 3)];
+                const int tb = gt.hi | gt.base | vT[(k << 1) | (sub << 3)];
                 const float fa0 = pend_factor(c, y), fa1 = pend_factor(c, y | 1u);
                 const float2 w0 = Ts[tb], w1 = Ts[tb | tE1];
                 const float wr0 = w0.x * fa0, wi0 = w0.y * fa0, wr1 = w1.x * fa1, wi1 = w1.y * fa1;
@@ -1094,7 +1110,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     if (nx) hist_close(my, gn, nE1, run);
     __syncthreads();
     allow_dependent_launch();
-    if (nx) hist_commit(&hw[0][0], 1 << nx->s, gv.Hnext + (size_t)slot * kGroupBins);
+    if (nx) hist_commit(&hw[0][0], gn, gv.Hnext + (size_t)slot * kGroupBins);
     if (vq > 0) {
         // bins: qubit 0 = e, qubits 1 .. vq-1 = lane bits 0 .. vq-2
         const unsigned lq = (1u << (vq - 1)) - 1u;
