@@ -826,12 +826,12 @@ __device__ __forceinline__ double df_warp_sum(float hi, float lo) {
 // the group -- phase, Z part of a Pauli, K0 -- is diagonal in the stored basis,
 // and every X part or K1 jump only relabels true bits, so the branch of every
 // damping site in the group follows from the joint distribution of the true
-// bits of S when the group starts.  k_group_decide draws all members' branches
-// from that joint in FP64 (the same draws, conditioned the same way, as one
-// gate at a time), forks every outcome string other than the shared one and
-// writes per slot a table T of 2^|S| amplitude factors; k_group_apply multiplies
-// the state by T in one sweep and accumulates the next group's joint on the
-// way.  Joints are summed in warp-private shared histograms in a fixed order
+// bits of S when the group starts.  The group decide (k_gd_*) draws all
+// members' branches from that joint in FP32 (the same draws, conditioned the
+// same way, as one gate at a time), forks every outcome string other than the
+// shared one and writes per slot a table T of 2^|S| amplitude factors;
+// k_group_apply multiplies the state by T in one sweep and accumulates the
+// next group's joint on the way.  Joints are summed in warp-private shared histograms in a fixed order
 // and added across blocks as 2^-60 fixed-point integers, so they do not depend
 // on the order in which blocks run.
 // ---------------------------------------------------------------------------
