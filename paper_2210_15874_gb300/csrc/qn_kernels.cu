@@ -837,41 +837,45 @@ __device__ __forceinline__ double df_warp_sum(float hi, float lo) {
 // ---------------------------------------------------------------------------
 constexpr double kHistScale = 1152921504606846976.0;  // 2^60
 constexpr double kHistUnit = 1.0 / kHistScale;
-static_assert(kThreads == 256 && kTileF4 == 1024 && kF4PerThread == 4 && kSub == 4,
-              "group bins assume y = e | tid << 1 | k << 9 | sub << 11 | tile << 13");
+// Phase-group sweeps stream kGSub sub-tiles per block (twice the gate sweeps'
+// kSub), so the per-block histogram work is spread over more amplitudes.
+constexpr int kGSub = 8;
+constexpr int kGLow = 14;  // amplitude bits a group-sweep block covers
+static_assert(kThreads == 256 && kTileF4 == 1024 && kF4PerThread == 4 && kGSub == 8,
+              "group bins assume y = e | tid << 1 | k << 9 | sub << 11 | tile << 14");
 
 __device__ __forceinline__ int group_bin(const GateGroup *gp, uint32_t y) {
     return gp->tab[0][y & 255u] | gp->tab[1][(y >> 8) & 255u] | gp->tab[2][(y >> 16) & 255u] | gp->tab[3][y >> 24];
 }
 
-// Bins of one sweep block split into a per-thread part (tid and tile bits) and
-// a part that depends only on the unrolled loop indices (e, k, sub), kept in
-// the shared table vtab[e | k << 1 | sub << 3].
-// A sweep block covers amplitude bits 0-12 and fixes the higher ones, so it
-// touches only the bins of S's qubits below 13 -- the low `nlow` bin bits (S is
-// numbered in ascending qubit order) -- above a block-constant part `hi`.  The
-// block's histogram is indexed by the low bits alone.
+// Bins of one group-sweep block split into a per-thread part (tid bits), a
+// block part (tile bits) and a part that depends only on the unrolled loop
+// indices (e, k, sub), kept in the shared table vtab[e | k << 1 | sub << 3].
+// A group-sweep block covers amplitude bits 0 .. kGLow-1 and fixes the higher
+// ones, so it touches only the bins of S's qubits below kGLow -- the low `nlow`
+// bin bits (S is numbered in ascending qubit order) -- above a block-constant
+// part `hi`.  The block's histogram is indexed by the low bits alone.
 struct GroupBins {
     int base;        // low bins of this thread's tid bits
     unsigned lmask;  // lane bits that are no qubit of S
     int hi;          // the block's high bins (its tile bits)
-    int nlow;        // S's qubits below 13
+    int nlow;        // S's qubits below kGLow
 };
 
 __device__ __forceinline__ GroupBins group_bins(const GateGroup *gp, int tile, uint16_t *vtab) {
     GroupBins gb;
     int nlow = 0;
-    while (nlow < gp->s && gp->sp[nlow] < 13) ++nlow;
+    while (nlow < gp->s && gp->sp[nlow] < kGLow) ++nlow;
     gb.nlow = nlow;
     gb.base = group_bin(gp, (uint32_t)threadIdx.x << 1);
-    gb.hi = group_bin(gp, (uint32_t)tile << 13);
+    gb.hi = group_bin(gp, (uint32_t)tile << kGLow);
     unsigned lm = 0;
     for (int i = 0; i < 5; ++i)
         if (group_bin(gp, 2u << i) == 0) lm |= 1u << i;
     gb.lmask = lm;
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < 2 * 4 * kGSub) {  // j = e | k << 1 | sub << 3
         const uint32_t j = threadIdx.x;
-        vtab[j] = (uint16_t)group_bin(gp, (j & 1u) | (((j >> 1) & 3u) << 9) | (((j >> 3) & 3u) << 11));
+        vtab[j] = (uint16_t)group_bin(gp, (j & 1u) | (((j >> 1) & 3u) << 9) | ((j >> 3) << 11));
     }
     return gb;
 }
@@ -949,14 +953,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
     const int slot = blockIdx.y, tile = blockIdx.x;
     const GateGroup *gp = gv.grp;
     __shared__ float hw[kThreads / 32][kGroupBins];
-    __shared__ uint16_t vtab[32];
+    __shared__ uint16_t vtab[2 * 4 * kGSub];
     const GroupBins gb = group_bins(gp, tile, vtab);
     hist_zero(&hw[0][0], gb.nlow);
     __syncthreads();
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
     const float4 *p4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)slot << n));
-    const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
+    const int64_t fbase = (int64_t)tile * kTileF4 * kGSub + threadIdx.x;
     const SweepCtx c = pending_ctx(v.st[slot]);
     float *my = hw[threadIdx.x >> 5];
     const int e1 = vtab[1];
@@ -964,9 +968,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
     float4 cur[kF4PerThread], nxt[kF4PerThread];
     load_tile(cur, p4, fbase, nf);
 #pragma unroll
-    for (int sub = 0; sub < kSub; ++sub) {
+    for (int sub = 0; sub < kGSub; ++sub) {
         const int64_t f0 = fbase + (int64_t)sub * kTileF4;
-        if (sub + 1 < kSub) load_tile(nxt, p4, f0 + kTileF4, nf);
+        if (sub + 1 < kGSub) load_tile(nxt, p4, f0 + kTileF4, nf);
 #pragma unroll
         for (int k = 0; k < kF4PerThread; ++k) {
             const int64_t f = f0 + k * kThreads;
@@ -979,7 +983,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
             }
             hist_push(my, gb, e1, vtab[(k << 1) | (sub << 3)], p0, p1, run);
         }
-        if (sub + 1 < kSub) {
+        if (sub + 1 < kGSub) {
 #pragma unroll
             for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
         }
@@ -1047,7 +1051,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     const int vq = gv.vq;
     __shared__ float2 Ts[kGroupBins];
     __shared__ float hw[kThreads / 32][kGroupBins];
-    __shared__ uint16_t vT[32], vN[32];
+    __shared__ uint16_t vT[2 * 4 * kGSub], vN[2 * 4 * kGSub];
     for (int i = threadIdx.x; i < (1 << gp->s); i += kThreads) Ts[i] = gv.T[(size_t)slot * kGroupBins + i];
     const GroupBins gt = group_bins(gp, tile, vT);
     GroupBins gn{0, 0u, 0, 0};
@@ -1060,7 +1064,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     const int64_t nf = (int64_t)1 << (n - 1);
     const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)from << n));
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << n));
-    const int64_t fbase = (int64_t)tile * kTileF4 * kSub + threadIdx.x;
+    const int64_t fbase = (int64_t)tile * kTileF4 * kGSub + threadIdx.x;
     const SweepCtx c = pending_ctx(gv.st_prev[slot]);
     float *my = hw[threadIdx.x >> 5];
     const int tE1 = vT[1];
@@ -1071,9 +1075,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     float4 cur[kF4PerThread], nxt[kF4PerThread];
     load_tile(cur, q4, fbase, nf);
 #pragma unroll
-    for (int sub = 0; sub < kSub; ++sub) {
+    for (int sub = 0; sub < kGSub; ++sub) {
         const int64_t f0 = fbase + (int64_t)sub * kTileF4;
-        if (sub + 1 < kSub) load_tile(nxt, q4, f0 + kTileF4, nf);
+        if (sub + 1 < kGSub) load_tile(nxt, q4, f0 + kTileF4, nf);
 #pragma unroll
         for (int k = 0; k < kF4PerThread; ++k) {
             const int64_t f = f0 + k * kThreads;
@@ -1102,7 +1106,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
                 va1 += o.z * o.z + o.w * o.w;
             }
         }
-        if (sub + 1 < kSub) {
+        if (sub + 1 < kGSub) {
 #pragma unroll
             for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
         }
@@ -2670,8 +2674,14 @@ cudaError_t launch_phase_sweep(const BatchView &v, const LayerView &L, cudaStrea
     return cudaGetLastError();
 }
 
+// Blocks of a group sweep per state (kGSub sub-tiles each).
+static unsigned group_tiles(int n) {
+    const int64_t nf = (int64_t)1 << (n - 1);
+    return (unsigned)((nf + (int64_t)kTileF4 * kGSub - 1) / ((int64_t)kTileF4 * kGSub));
+}
+
 cudaError_t launch_group_hist(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
-    return launch_pdl(k_group_hist, dim3((unsigned)v.stiles, (unsigned)active), dim3(kThreads), s, v, gv);
+    return launch_pdl(k_group_hist, dim3(group_tiles(v.n), (unsigned)active), dim3(kThreads), s, v, gv);
 }
 
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int ns, int active,
@@ -2736,7 +2746,7 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
 }
 
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
-    return launch_pdl(k_group_apply, dim3((unsigned)v.stiles, (unsigned)active), dim3(kThreads), s, v, gv);
+    return launch_pdl(k_group_apply, dim3(group_tiles(v.n), (unsigned)active), dim3(kThreads), s, v, gv);
 }
 
 }  // namespace qn
