@@ -893,6 +893,9 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             gv.ncls = sv.fork_count;  // reset by the fork-finish kernel
             gv.src = nullptr;
             gv.slot_base = 0;
+            // a group right after the H layer or after another group finds no pending op
+            // (decides leave none); one after a per-gate sweep may
+            gv.pend = !(z.g0 == n || (gi > 0 && h->groups[gi - 1].g0 + h->groups[gi - 1].m == z.g0));
             cudaError_t e = cudaSuccess;
             if (first) {
                 QN_TRY(prof_begin(h, &ep, 3, (double)active * 8.0 * amp_count));

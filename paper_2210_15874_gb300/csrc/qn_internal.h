@@ -139,6 +139,7 @@ struct GroupView {
     const int32_t *src;      // per slot: the state a sweep reads (a forked slot's parent), or
                              // nullptr: every slot reads its own state
     int32_t slot_base;       // first slot of the launch (blockIdx.y + slot_base)
+    int32_t pend;            // the gate before the group may have left a pending op
     int32_t *parent;         // [max_slots] decide writes each new slot's parent here
     int32_t vq;              // > 0: the apply sweep accumulates instead the joint of the
                              // mixer block on qubits 0 .. vq-1 after rotations (vc, vs)

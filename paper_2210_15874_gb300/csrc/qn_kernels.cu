@@ -948,6 +948,7 @@ __device__ __forceinline__ SweepCtx pending_ctx(const TrajState &s) {
 
 // Joint of the first group of a layer: a read-only pass that applies the
 // pending op of the gate before on the fly.  Grid (sweep tiles, live slots).
+template <bool PEND>
 __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupView gv) {
     grid_dependency_wait();
     const int slot = blockIdx.y, tile = blockIdx.x;
@@ -977,7 +978,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
             float p0 = 0.0f, p1 = 0.0f;
             if (f < nf) {
                 const uint32_t y = (uint32_t)(2 * f);
-                const float fa0 = pend_factor(c, y), fa1 = pend_factor(c, y | 1u);
+                const float fa0 = PEND ? pend_factor(c, y) : 1.0f, fa1 = PEND ? pend_factor(c, y | 1u) : 1.0f;
                 p0 = fa0 * fa0 * (cur[k].x * cur[k].x + cur[k].y * cur[k].y);
                 p1 = fa1 * fa1 * (cur[k].z * cur[k].z + cur[k].w * cur[k].w);
             }
@@ -1042,20 +1043,24 @@ __device__ __forceinline__ void lane_joint_commit(int nb, int warps, const float
 // group's joint (gv.next) or the joint of the mixer block on qubits 0 .. vq-1
 // as it will be after that block's rotations (gv.vq > 0): qubit 0 is the pair
 // inside a float4, qubits 1 .. 3 are lane bits 0 .. 2 of the sweep layout.
+// PEND: the gate before left a pending op (else it is the identity and skipped).
+// NEXT: the joint this sweep forms -- 0 none, 1 the next phase group's, 2 the
+// first mixer block's after its rotations.
+template <bool PEND, int NEXT>
 __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupView gv) {
     grid_dependency_wait();
     const int slot = blockIdx.y + gv.slot_base, tile = blockIdx.x;
     const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
     const GateGroup *gp = gv.grp;
-    const GateGroup *nx = gv.next;
-    const int vq = gv.vq;
+    const GateGroup *nx = NEXT == 1 ? gv.next : nullptr;
+    const int vq = NEXT == 2 ? gv.vq : 0;
     __shared__ float2 Ts[kGroupBins];
     __shared__ float hw[kThreads / 32][kGroupBins];
     __shared__ uint16_t vT[2 * 4 * kGSub], vN[2 * 4 * kGSub];
     for (int i = threadIdx.x; i < (1 << gp->s); i += kThreads) Ts[i] = gv.T[(size_t)slot * kGroupBins + i];
     const GroupBins gt = group_bins(gp, tile, vT);
     GroupBins gn{0, 0u, 0, 0};
-    if (nx) {
+    if (NEXT == 1) {
         gn = group_bins(nx, tile, vN);
         hist_zero(&hw[0][0], gn.nlow);
     }
@@ -1068,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     const SweepCtx c = pending_ctx(gv.st_prev[slot]);
     float *my = hw[threadIdx.x >> 5];
     const int tE1 = vT[1];
-    const int nE1 = nx ? vN[1] : 0;
+    const int nE1 = NEXT == 1 ? vN[1] : 0;
     const float vc = gv.vc, vs = gv.vs;
     HistRun run;
     float va0 = 0.0f, va1 = 0.0f;
@@ -1085,7 +1090,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
             if (f < nf) {
                 const uint32_t y = (uint32_t)(2 * f);
                 const int tb = gt.hi | gt.base | vT[(k << 1) | (sub << 3)];
-                const float fa0 = pend_factor(c, y), fa1 = pend_factor(c, y | 1u);
+                const float fa0 = PEND ? pend_factor(c, y) : 1.0f, fa1 = PEND ? pend_factor(c, y | 1u) : 1.0f;
                 const float2 w0 = Ts[tb], w1 = Ts[tb | tE1];
                 const float wr0 = w0.x * fa0, wi0 = w0.y * fa0, wr1 = w1.x * fa1, wi1 = w1.y * fa1;
                 const float4 a = cur[k];
@@ -1095,9 +1100,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
                 o.w = a.z * wi1 + a.w * wr1;
                 p4[f] = o;
             }
-            if (nx) hist_push(my, gn, nE1, vN[(k << 1) | (sub << 3)], o.x * o.x + o.y * o.y, o.z * o.z + o.w * o.w,
+            if (NEXT == 1) hist_push(my, gn, nE1, vN[(k << 1) | (sub << 3)], o.x * o.x + o.y * o.y, o.z * o.z + o.w * o.w,
                               run);
-            if (vq > 0) {
+            if (NEXT == 2) {
                 rx_pair(o.x, o.y, o.z, o.w, vc, vs);
                 if (vq > 1) rx_lanes(o, 1, vc, vs);
                 if (vq > 2) rx_lanes(o, 2, vc, vs);
@@ -1111,13 +1116,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
             for (int k = 0; k < kF4PerThread; ++k) cur[k] = nxt[k];
         }
     }
-    if (nx) hist_close(my, gn, nE1, run);
+    if (NEXT == 1) hist_close(my, gn, nE1, run);
     __syncthreads();
     allow_dependent_launch();
-    if (nx) hist_commit(&hw[0][0], gn, gv.Hnext + (size_t)slot * kGroupBins);
-    if (vq > 0) {
+    if (NEXT == 1) hist_commit(&hw[0][0], gn, gv.Hnext + (size_t)slot * kGroupBins);
+    if (NEXT == 2) {
         // bins: qubit 0 = e, qubits 1 .. vq-1 = lane bits 0 .. vq-2
-        const unsigned lq = (1u << (vq - 1)) - 1u;
+        const unsigned lq = (1u << (vq > 0 ? vq - 1 : 0)) - 1u;
         const unsigned lmask = 31u & ~lq;
         const int lb = (int)((threadIdx.x & 31u) & lq) << 1;
         lane_joint_put(va0, lb, lmask, &hw[0][0]);
@@ -2681,7 +2686,9 @@ static unsigned group_tiles(int n) {
 }
 
 cudaError_t launch_group_hist(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
-    return launch_pdl(k_group_hist, dim3(group_tiles(v.n), (unsigned)active), dim3(kThreads), s, v, gv);
+    const dim3 grid(group_tiles(v.n), (unsigned)active);
+    return gv.pend ? launch_pdl(k_group_hist<true>, grid, dim3(kThreads), s, v, gv)
+                   : launch_pdl(k_group_hist<false>, grid, dim3(kThreads), s, v, gv);
 }
 
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int ns, int active,
@@ -2746,7 +2753,12 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
 }
 
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
-    return launch_pdl(k_group_apply, dim3(group_tiles(v.n), (unsigned)active), dim3(kThreads), s, v, gv);
+    const dim3 grid(group_tiles(v.n), (unsigned)active), blk(kThreads);
+    const int next = gv.next ? 1 : (gv.vq > 0 ? 2 : 0);
+#define QN_APPLY(P, N) launch_pdl(k_group_apply<P, N>, grid, blk, s, v, gv)
+    if (gv.pend) return next == 1 ? QN_APPLY(true, 1) : next == 2 ? QN_APPLY(true, 2) : QN_APPLY(true, 0);
+    return next == 1 ? QN_APPLY(false, 1) : next == 2 ? QN_APPLY(false, 2) : QN_APPLY(false, 0);
+#undef QN_APPLY
 }
 
 }  // namespace qn
