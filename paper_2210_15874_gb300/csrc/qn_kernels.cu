@@ -1387,7 +1387,12 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         }
         if (nN > 0 || has0) __syncthreads();
         if (VAR == kMixFirst) {
-            // stored from phase 2's registers below (64-byte runs per request)
+            const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
+#pragma unroll
+            for (int c = 0; c < kMixE; ++c) {
+                const uint32_t f = threadIdx.x + (uint32_t)c * kMixThreads;
+                p4[tbits | ts | f] = buf[sw(nat_slot(f))];
+            }
         } else if (has0) {
             const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
 #pragma unroll
@@ -1402,13 +1407,6 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
             // phase 2: the next block's rotations on the tile, kept only as squared magnitudes
 #pragma unroll
             for (int j = 0; j < kMixE; ++j) x[j] = buf[idx2(j)];
-            if (VAR == kMixFirst) {
-                // the final values, in phase 2's order: f = L (f8-f10) | A (f0-f2, f7) | B (f3-f6) = j << 3
-                const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
-                const uint32_t f2 = tbits | ts | ((uint32_t)tL << 8) | ((uint32_t)(tH & 7) | ((uint32_t)(tH >> 3) << 7));
-#pragma unroll
-                for (int j = 0; j < kMixE; ++j) p4[f2 | ((uint32_t)j << 3)] = x[j];
-            }
 #pragma unroll
             for (int i = 0; i < kMixQ; ++i) {
                 if (i >= nN) break;
