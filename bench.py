@@ -262,8 +262,9 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
                groups=b.profile_read(3), mixers=b.profile_read(4), clocks=clocks.summary())
     b.set_profiling(0)
     if with_e2e:
-        # end to end through the C ABI from host buffers: run + <C> + sigma to host
+        # end to end through the C ABI from host buffers: run + <C> + sigma to a page-locked host buffer
         e2e_steps = max(1, min(args.steps, 3))
+        sigma = torch.empty(1 << w.n, dtype=torch.float64, pin_memory=True).numpy()
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -271,7 +272,7 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
         for _ in range(e2e_steps):
             b.run_qaoa(w.edges, w.gammas, w.betas, **kw)
             b.expectation()
-            b.probs()
+            b.probs(out=sigma)
         el = time.perf_counter() - t
         if pg:
             tt = torch.tensor([el], device="cuda")
@@ -349,7 +350,7 @@ def gpu_arm(args):
         fused = main_mode[1] and w.damping == 0
         grouped = sharing and main_mode[1] and main["groups"]["launches"] > 0
         blocks = grouped and main["mixers"]["launches"] > 0
-        kname = "k_mix_sweep (mixer blocks of 4 qubits over live prefix states, 16 B per amplitude)" if blocks else \
+        kname = "k_mix_sweep + k_mix_first (mixer blocks of 4 qubits over live prefix states, 16 B per amplitude)" if blocks else \
             "k_slot_sweep (mixer gate sweeps over live prefix states)" if grouped else \
             "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
             ("k_fused_sweep (fused layer sweeps, 16 B per amplitude)" if fused else
@@ -444,8 +445,9 @@ def serving_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(sharing=False):
-    """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state)."""
+def profile_case(sharing=False, depth=1):
+    """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state);
+    depth 2 adds a layer, so the last mixer block of the first one forms the next layer's joint."""
     from paper_2210_15874_gb300 import build
     build.build()
     from paper_2210_15874_gb300 import qn
@@ -453,10 +455,10 @@ def profile_case(sharing=False):
     if sharing:
         # heavy Pauli noise so that most of the 64 trajectories fork early: the
         # late gates sweep ~64 live states (512 MiB, above L2)
-        w = W.qaoa_workload("ncu_n20_p1_damp_shared", 20, 1, index=1, trajectories=64, batch=64, p1=0.1, p2=0.3,
-                            damping=5e-3)
+        w = W.qaoa_workload(f"ncu_n20_p{depth}_damp_shared", 20, depth, index=1, trajectories=64, batch=64, p1=0.1,
+                            p2=0.3, damping=5e-3)
     else:
-        w = W.qaoa_workload("ncu_n20_p1_damp", 20, 1, index=1, trajectories=32, batch=32, damping=5e-3)
+        w = W.qaoa_workload(f"ncu_n20_p{depth}_damp", 20, depth, index=1, trajectories=32, batch=32, damping=5e-3)
     with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
         b.set_sharing(sharing)
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
@@ -491,9 +493,10 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="run one small ensemble for ncu captures, then exit (n=20, p=1: 32 trajectories in "
                          "one launch, or with --sharing 1 64 heavily noisy trajectories)")
+    ap.add_argument("--profile-depth", type=int, default=1, choices=[1, 2], help="QAOA depth of --profile-case")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(bool(args.sharing))
+        profile_case(bool(args.sharing), args.profile_depth)
         return
     if args.workload == "serving":
         serving_arm(args)

@@ -22,7 +22,7 @@
  *       state (Sec. "Stochastic Noise Implementation").  phi = |psi|^2 and
  *       sigma_approx = sum_k phi_k / K (same section).
  *
- * Readings of the paper where it is silent (each is listed in the design doc):
+ * Readings of the paper where it is silent:
  *   - depolarizing parameter: param=0 gives p = total non-identity probability,
  *     each 1q Pauli p/3 (lambda = 4p/3); param=1 takes the paper's lambda,
  *     K0 = sqrt(1-3 lambda/4) I  ->  p = 3 lambda / 4 (1q), 15 lambda / 16 (2q).

@@ -537,7 +537,7 @@ qn_status check_status(const qn_batch *h);
 
 // Row blocks for k_probs over b states, with their sigma scratch.
 qn_status probs_rows(qn_batch *h, int b, AccumView *a) {
-    a->parts = a->probs ? probs_parts(h->n, b) : 1;
+    a->parts = a->probs ? probs_parts(h->n, b, a->trivial_pending != 0) : 1;
     if (a->parts > 1) {
         const int64_t need = (int64_t)(a->parts - 1) << h->n;
         if (h->spart_cap < need) {

@@ -150,7 +150,7 @@ struct GroupView {
     TrajState *st_prev;    // [max_slots] pending op of the gate before the group
     float *Htrue;          // [max_slots][kGroupBins] this group's joint by true bits (FP32)
     float *p1m;            // [max_slots][2 kMaxGroupEdges] shared path's gamma P(q=1) per site
-    int32_t *pos_slot;     // [K] slot of each member position
+    int32_t *pos_slot;     // [K] slot of each member position (then scratch of k_gd_classes)
     int32_t members;       // member positions in the prefix tree (K of this run)
     GroupKey *ekey;        // [K] outcome string of the member at each position (0: shared path)
     int32_t *evt;          // [K] per slot: member index of the k-th member with an event
@@ -221,9 +221,10 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
                          cudaStream_t s);
 cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
-// Row blocks worth giving k_probs for b states (1 .. kMaxProbParts).
-int probs_parts(int n, int b);
-constexpr int kMaxProbParts = 4;
+// Row blocks worth giving k_probs for b states (1 .. kMaxProbParts), for the
+// variant without (trivial_pending) or with a pending op.
+int probs_parts(int n, int b, bool trivial_pending);
+constexpr int kMaxProbParts = 16;
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
 // Fused layers (Pauli-only): per-trajectory layer parameters from the branch
 // tables, then sweeps applying the rotations of qubits [q_lo, q_lo + m) of

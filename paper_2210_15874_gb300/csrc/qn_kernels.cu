@@ -890,6 +890,17 @@ __device__ __forceinline__ void hist_flush(float *hw, float x, int bin, unsigned
     __syncwarp();
 }
 
+// The same into a block-wide histogram of 2^-60 fixed-point integers: each
+// flushed value is quantised once and integer adds commute, so the block's
+// sums do not depend on the order in which its warps arrive.
+constexpr float kHistScaleF = 1152921504606846976.0f;  // 2^60
+__device__ __forceinline__ void hist_flush(unsigned long long *h, float x, int bin, unsigned lmask) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        if ((lmask >> i) & 1u) x += __shfl_xor_sync(0xffffffffu, x, 1 << i);
+    if (((threadIdx.x & 31u) & lmask) == 0u && x > 0.0f) atomicAdd(h + bin, (unsigned long long)__float2ull_rn(x * kHistScaleF));
+}
+
 // Run of consecutive (e = 0, e = 1) probabilities with the same loop-index bin
 // `ks`; flushed when ks changes (ks is warp-uniform).  e1 = bin bits of y bit 0.
 struct HistRun {
@@ -897,7 +908,8 @@ struct HistRun {
     int ks = -1;
 };
 
-__device__ __forceinline__ void hist_close(float *hw, const GroupBins &gb, int e1, const HistRun &run) {
+template <class Sink>
+__device__ __forceinline__ void hist_close(Sink *hw, const GroupBins &gb, int e1, const HistRun &run) {
     if (run.ks < 0) return;
     if (e1) {
         hist_flush(hw, run.r0, gb.base | run.ks, gb.lmask);
@@ -907,7 +919,8 @@ __device__ __forceinline__ void hist_close(float *hw, const GroupBins &gb, int e
     }
 }
 
-__device__ __forceinline__ void hist_push(float *hw, const GroupBins &gb, int e1, int ks, float p0, float p1,
+template <class Sink>
+__device__ __forceinline__ void hist_push(Sink *hw, const GroupBins &gb, int e1, int ks, float p0, float p1,
                                           HistRun &run) {
     if (ks != run.ks) {
         hist_close(hw, gb, e1, run);
@@ -1189,11 +1202,11 @@ __device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
 // (tile index = L | A << kMixL | B << (kMixL + kMixQ)).
 // Variants with every bound a constant (all for full blocks of kMixQ qubits):
 //   kMixMid   not qubit 0, a full next block
-//   kMixFirst qubit 0, a full next block
 //   kMixHist  not qubit 0, no next block, the next layer's first phase-group joint
 //   kMixNorm  not qubit 0, no next block, the final norms
-// and kMixAny, which reads everything from the map.
-enum { kMixAny = 0, kMixMid = 1, kMixFirst = 2, kMixHist = 3, kMixNorm = 4 };
+// and kMixAny, which reads everything from the map.  The block holding qubit 0
+// with a full next block has a kernel of its own (k_mix_first).
+enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixNorm = 3 };
 
 template <bool TANF, int VAR>
 __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
@@ -1207,23 +1220,24 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     constexpr bool kFix = VAR != kMixAny;
     // next layer's first phase group: its joint is formed here
     const GateGroup *nx = kFix ? (VAR == kMixHist ? gv.next : nullptr) : gv.next;
-    const bool has0 = kFix ? VAR == kMixFirst : mm.has0 != 0;
+    const bool has0 = kFix ? false : mm.has0 != 0;
     const int M = kFix ? kMixQ : mm.M;
-    const int nN = kFix ? ((VAR == kMixMid || VAR == kMixFirst) ? kMixQ : 0) : mm.nN;
+    const int nN = kFix ? (VAR == kMixMid ? kMixQ : 0) : mm.nN;
     const bool final_norm = kFix ? VAR == kMixNorm : mm.final_norm != 0;
     const float c = gv.grp->c, sn = gv.grp->sn;
     const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;  // rotation = rsc * (tangent form)
     float scM = 1.0f;  // rsc^M: the block's rotations, folded into its factors
     for (int i = 0; i < M; ++i) scM *= rsc;
     __shared__ float Df[16];
-    // per-warp histograms of the next phase group's joint (variants that form one), else
-    // the per-warp rows of the next mixer block's joint
+    // the block's histogram of the next phase group's joint (variants that form one; 2^-60
+    // fixed point, one row for all warps), and the per-warp rows of the next mixer block's joint
     constexpr bool kHist = VAR == kMixAny || VAR == kMixHist;
-    __shared__ float hw_flat[kHist ? kWarps * kGroupBins : kWarps * kJointBins];
+    __shared__ unsigned long long hist[kHist ? kGroupBins : 1];
+    __shared__ float red[kWarps * kJointBins];
     if (threadIdx.x < 16u)
         Df[threadIdx.x] = threadIdx.x < (1u << M) ? gv.T[(size_t)slot * kGroupBins + threadIdx.x].x * scM : 0.0f;
     if (nx)
-        for (int i = threadIdx.x; i < kWarps * kGroupBins; i += kMixThreads) hw_flat[i] = 0.0f;
+        for (int i = threadIdx.x; i < kGroupBins; i += kMixThreads) hist[i] = 0ull;
     // float4 indices fit 32 bits (n <= 30)
     uint32_t offL = 0, offW = 0, ao[kMixQ];
 #pragma unroll
@@ -1279,22 +1293,10 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         for (int i = 0; i < 3; ++i) cbase |= (uint32_t)((la >> i) & 1) << mm.fA[i];
         cbase |= (uint32_t)ah << mm.fA[3];
     }
-    // kMixFirst: the tile is the contiguous f bits 0 .. 10 (A = f0-f2 and f7, B = f3-f6,
-    // L = f8-f10); copies and stores go in address order, each float4 to its tile slot
-    static_assert(kMixQ == 4 && kMixL == 3, "the first block's tile layout assumes 4 + 4 + 3 bits");
-    auto nat_slot = [](uint32_t f) {
-        return (int)(((f >> 8) & 7u) | ((f & 7u) << 3) | (((f >> 7) & 1u) << 6) | (((f >> 3) & 15u) << 7));
-    };
     auto fetch = [&](int sub) {  // tile `sub` into its buffer
         const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
         float4 *buf = mix_buf + (sub & 1) * kMixTile;
-        if (VAR == kMixFirst) {
-#pragma unroll
-            for (int c = 0; c < kMixE; ++c) {
-                const uint32_t f = threadIdx.x + (uint32_t)c * kMixThreads;
-                cp_async16(buf + sw(nat_slot(f)), q4 + (tbits | ts | f));
-            }
-        } else if (has0) {
+        if (has0) {
 #pragma unroll
             for (int j = 0; j < kMixE; ++j) {
                 uint32_t bofs = 0;
@@ -1312,12 +1314,17 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     // next phase group's bins: this thread's part, the A part of element j, the float4 half
     GroupBins gn{0, 0u};
     int nab[kMixQ], ne1 = 0;
+    int nb0 = 0, nb1 = 0, nb2 = 0;  // bins of the first tile's thread offset and of the sub-tile steps
 #pragma unroll
     for (int i = 0; i < kMixQ; ++i) nab[i] = 0;
     if (nx) {
 #pragma unroll
         for (int i = 0; i < kMixQ; ++i) nab[i] = group_bin(nx, (uint32_t)(2 * ao[i]));
         ne1 = group_bin(nx, 1u);
+        // a bin is the OR of its bits' bins, so a tile's is the first's with the steps' ORed in
+        nb0 = group_bin(nx, 2u * tbase);
+        nb1 = group_bin(nx, 2u * ts1);
+        nb2 = group_bin(nx, 2u * ts2);
         // lane bits: kMixL bits of L, then the low B bits
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
@@ -1369,12 +1376,11 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
             else p4[fb | aoff(j)] = x[j];
             if (nN > 0 && !has0) buf[idx1(j)] = x[j];
             if (nx) {
-                if (j == 0) gn.base = group_bin(nx, (uint32_t)(2 * fb));
+                if (j == 0) gn.base = nb0 | ((sub & 1) ? nb1 : 0) | ((sub & 2) ? nb2 : 0);
                 int ks = 0;
 #pragma unroll
                 for (int i = 0; i < kMixQ; ++i) ks |= (j & (1 << i)) ? nab[i] : 0;
-                hist_push(hw_flat + warp * kGroupBins, gn, ne1, ks, x[j].x * x[j].x + x[j].y * x[j].y, x[j].z * x[j].z + x[j].w * x[j].w,
-                          run);
+                hist_push(hist, gn, ne1, ks, x[j].x * x[j].x + x[j].y * x[j].y, x[j].z * x[j].z + x[j].w * x[j].w, run);
             }
             if (final_norm) {
                 df_add(nh, nl, prob_of(1.0f, x[j].x, x[j].y));
@@ -1382,18 +1388,11 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
             }
         }
         if (nx) {  // the per-thread bin part changes with the tile
-            hist_close(hw_flat + warp * kGroupBins, gn, ne1, run);
+            hist_close(hist, gn, ne1, run);
             run = HistRun();
         }
         if (nN > 0 || has0) __syncthreads();
-        if (VAR == kMixFirst) {
-            const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
-#pragma unroll
-            for (int c = 0; c < kMixE; ++c) {
-                const uint32_t f = threadIdx.x + (uint32_t)c * kMixThreads;
-                p4[tbits | ts | f] = buf[sw(nat_slot(f))];
-            }
-        } else if (has0) {
+        if (has0) {
             const uint32_t ts = ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u);
 #pragma unroll
             for (int j = 0; j < kMixE; ++j) {
@@ -1432,7 +1431,6 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         }
         float sc2 = 1.0f;  // the next block's rotations were taken up to rsc each: restore |.|^2
         for (int i = 0; i < nN; ++i) sc2 *= rsc * rsc;
-        float *red = hw_flat;
 #pragma unroll
         for (int b = 0; b < kMixE; ++b) {
             float x = acc[b] * sc2;
@@ -1445,11 +1443,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     }
     if (nx) {
         __syncthreads();
-        for (int b = threadIdx.x; b < (1 << nx->s); b += kMixThreads) {
-            double a2 = 0.0;
-            for (int w = 0; w < kWarps; ++w) a2 += (double)hw_flat[w * kGroupBins + b];
-            if (a2 > 0.0) atomicAdd(gv.Hnext + (size_t)slot * kGroupBins + b, __double2ull_rn(a2 * kHistScale));
-        }
+        for (int b = threadIdx.x; b < (1 << nx->s); b += kMixThreads)
+            if (hist[b]) atomicAdd(gv.Hnext + (size_t)slot * kGroupBins + b, hist[b]);
     }
     if (final_norm) {
         // block partial -> partials[slot][block]; the slot's last block forms 1/N
@@ -1476,6 +1471,133 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
             v.counters[slot] = 0;
         }
     }
+}
+
+// exp(-i beta X) up to the common factor (see rx_pair_t) on a qubit whose two
+// values sit in lanes that differ in `lanebit`.  The rotation treats both
+// values alike, so each lane forms its own from its value and its partner's,
+// with the same operations rx_pair_t takes for that value.
+template <bool TANF>
+__device__ __forceinline__ void rx_lanes_t(float4 &o, int lanebit, float t) {
+    const float px = __shfl_xor_sync(0xffffffffu, o.x, lanebit), py = __shfl_xor_sync(0xffffffffu, o.y, lanebit);
+    const float pz = __shfl_xor_sync(0xffffffffu, o.z, lanebit), pw = __shfl_xor_sync(0xffffffffu, o.w, lanebit);
+    if (TANF) {
+        o.x = __fmaf_rn(t, py, o.x);
+        o.y = __fmaf_rn(-t, px, o.y);
+        o.z = __fmaf_rn(t, pw, o.z);
+        o.w = __fmaf_rn(-t, pz, o.w);
+    } else {
+        o.x = __fmaf_rn(t, o.x, py);
+        o.y = __fmaf_rn(t, o.y, -px);
+        o.z = __fmaf_rn(t, o.z, pw);
+        o.w = __fmaf_rn(t, o.w, -pz);
+    }
+}
+
+// Mixer block on qubits 0-3 followed by a full block on qubits 4-7 (shared-prefix
+// mode, n >= 12).  The tile is the contiguous float4 bits f0-f10: qubit 0 is the
+// pair inside a float4, qubits 1-3 (f0-f2) are lane bits 0-2, the next block's
+// qubits 4-7 (f3-f6) are the register index j, and f7-f10 are lane bits 3-4
+// and the warp.  So every copy and store is a run of 128 bytes, qubits 1-3
+// rotate across lanes by shuffles, and the next block's rotations and joint
+// stay in registers.  A thread stages only its own float4 (cp.async, one tile
+// ahead) and reads back only those, so the tile loop takes no block barrier.
+// Same operations per amplitude as k_mix_sweep: qubit 0, then 1, 2, 3, then the
+// block's factors; the next block's qubits in order 4 .. 7.
+template <bool TANF>
+__global__ void __launch_bounds__(kMixThreads, 3) k_mix_first(BatchView v, GroupView gv, MixMap mm) {
+    extern __shared__ float4 mix_buf[];  // [2][kMixE][kMixThreads]
+    constexpr int kWarps = kMixThreads / 32;
+    static_assert(kMixThreads == 128 && kMixE == 16 && kMixQ == 4, "the tile is f0-f10: 16 float4 x 128 threads");
+    grid_dependency_wait();
+    const int slot = blockIdx.y + gv.slot_base;
+    const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float c = gv.grp->c, sn = gv.grp->sn;
+    const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;
+    float scM = 1.0f;  // rsc^4: the block's rotations, folded into its factors
+    for (int i = 0; i < kMixQ; ++i) scM *= rsc;
+    __shared__ float Df[16];
+    __shared__ float red[kWarps * kJointBins];
+    if (threadIdx.x < 16u) Df[threadIdx.x] = gv.T[(size_t)slot * kGroupBins + threadIdx.x].x * scM;
+    const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)from << v.n));
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << v.n));
+    const int nsubs = mm.ntile >= 2 ? kMixSubs : (1 << mm.ntile);
+    uint32_t tbits = 0;  // tile bits of the block's first tile
+    {
+        const uint32_t t0 = blockIdx.x * nsubs;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
+            if (i < mm.ntile) tbits |= ((t0 >> i) & 1u) << mm.ftile[i];
+    }
+    const uint32_t ts1 = mm.ntile > 0 ? 1u << mm.ftile[0] : 0u;
+    const uint32_t ts2 = mm.ntile > 1 ? 1u << mm.ftile[1] : 0u;
+    // this thread's float4 of a tile, j = 0: f0-f2 lane bits 0-2, f7-f8 lane bits 3-4, f9-f10 the warp
+    const uint32_t fth = (uint32_t)(lane & 7) | ((uint32_t)(lane >> 3) << 7) | ((uint32_t)warp << 9);
+    auto tile_f = [&](int sub) { return tbits | ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u) | fth; };
+    auto fetch = [&](int sub) {
+        const uint32_t fb = tile_f(sub);
+        float4 *buf = mix_buf + (sub & 1) * kMixTile + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) cp_async16(buf + j * kMixThreads, q4 + (fb | ((uint32_t)j << 3)));
+        cp_async_commit();
+    };
+    float acc[kMixE];  // sum of |.|^2 after the next block's rotations, by its qubits (j)
+#pragma unroll
+    for (int j = 0; j < kMixE; ++j) acc[j] = 0.0f;
+    fetch(0);
+    __syncthreads();  // Df
+    const int d = lane & 7;  // qubits 1-3
+    const float g0 = Df[d << 1], g1 = Df[(d << 1) | 1];
+    for (int sub = 0; sub < nsubs; ++sub) {
+        if (sub + 1 < nsubs) {
+            fetch(sub + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const float4 *buf = mix_buf + (sub & 1) * kMixTile + threadIdx.x;
+        float4 x[kMixE];
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) x[j] = buf[j * kMixThreads];
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) rx_pair_t<TANF>(x[j].x, x[j].y, x[j].z, x[j].w, rt);  // qubit 0
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {  // qubits 1-3
+#pragma unroll
+            for (int j = 0; j < kMixE; ++j) rx_lanes_t<TANF>(x[j], 1 << i, rt);
+        }
+        const uint32_t fb = tile_f(sub);
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) {
+            x[j].x *= g0;
+            x[j].y *= g0;
+            x[j].z *= g1;
+            x[j].w *= g1;
+            p4[fb | ((uint32_t)j << 3)] = x[j];
+        }
+        // the next block's rotations, kept only as squared magnitudes
+#pragma unroll
+        for (int i = 0; i < kMixQ; ++i) {
+#pragma unroll
+            for (int j = 0; j < kMixE; ++j)
+                if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
+        }
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) acc[j] += x[j].x * x[j].x + x[j].y * x[j].y + x[j].z * x[j].z + x[j].w * x[j].w;
+    }
+    allow_dependent_launch();
+    float sc2 = 1.0f;  // the next block's rotations were taken up to rsc each: restore |.|^2
+    for (int i = 0; i < kMixQ; ++i) sc2 *= rsc * rsc;
+#pragma unroll
+    for (int b = 0; b < kMixE; ++b) {
+        float x = acc[b] * sc2;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if (lane == 0) red[warp * kJointBins + b] = x;
+    }
+    __syncthreads();
+    lane_joint_commit(kMixE, kWarps, red, gv.Hnext + (size_t)slot * kGroupBins);
 }
 
 __device__ __forceinline__ float warp_sumf(float x) {
@@ -1568,7 +1690,7 @@ __device__ __forceinline__ float site_weight(const float (&w)[R], int lane, uint
 // exactly what the shared path drew.  A warp holds the patterns b = lane + 32 r
 // (true bits of S, r < kPatR) of the joint: at the start of a phase group,
 // after the rotations of a mixer block.
-//   1 k_gd_joint    block per slot: joint by true bits, the shared path's
+//   1 k_gd_joint    warp per slot: joint by true bits, the shared path's
 //                   gamma P(q=1) per site, the slot of each member position
 //   2 k_gd_members  thread per member: leaves the shared path? a warp per
 //                   such member draws its outcome string (key)
@@ -1626,62 +1748,70 @@ __device__ GroupKey member_key(const BatchView &v, const GateGroup *gp, const fl
 }
 
 template <int kPatR>
-__global__ void __launch_bounds__(kThreads) k_gd_joint(BatchView v, SlotView sv, GroupView gv, double gamma) {
+__global__ void __launch_bounds__(kThreads) k_gd_joint(BatchView v, SlotView sv, GroupView gv, double gamma, int active) {
     grid_dependency_wait();
-    const int slot = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5);  // warp per slot
+    if (slot >= active) return;
     const GateGroup *gp = gv.grp;
     const int m = gp->m, ns = gp->s, nbins = 1 << ns, nsite = gp->kind == 0 ? 2 : 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TrajState st = v.st[slot];
     const uint32_t Fb = st.J ^ st.pend;  // frame once the pending op is applied
     uint32_t fS = 0;
     for (int k = 0; k < ns; ++k) fS |= ((Fb >> gp->sp[k]) & 1u) << k;
-    __shared__ float hd[kGroupBins];
-    for (int b = threadIdx.x; b < 32 * kPatR; b += kThreads) hd[b] = 0.0f;
-    __syncthreads();
+    // the joint by true bits b = stored bits ^ fS, pattern b = lane + 32 r
     unsigned long long *Hs = gv.Hcur + (size_t)slot * kGroupBins;
-    for (int b = threadIdx.x; b < nbins; b += kThreads) {
-        hd[b ^ fS] = (float)((double)Hs[b] * kHistUnit);
-        Hs[b] = 0ull;  // zero again for the next group that accumulates here
+    float w[kPatR];
+#pragma unroll
+    for (int r = 0; r < kPatR; ++r) {
+        const int b = lane + 32 * r;
+        w[r] = b < nbins ? (float)((double)Hs[b ^ fS] * kHistUnit) : 0.0f;
     }
-    __syncthreads();
+    __syncwarp();  // every lane has read before any zeroes
     float *ht = gv.Htrue + (size_t)slot * kGroupBins;
-    for (int b = threadIdx.x; b < 32 * kPatR; b += kThreads) ht[b] = hd[b];
-    if (warp == 0) {  // the identity / no-jump path: gamma P(q = 1) at every damping site
-        const float gf = (float)gamma, omg = (float)(1.0 - gamma);
-        float w[kPatR];
 #pragma unroll
-        for (int r = 0; r < kPatR; ++r) w[r] = hd[lane + 32 * r];
-        float tot = site_weight<kPatR>(w, lane, 0u, -1);
-        float *p1m = gv.p1m + (size_t)slot * 2 * kMaxGroupEdges;
-        for (int e = 0; e < m; ++e)
-            for (int k2 = 0; k2 < nsite; ++k2) {
-                const int qi = k2 ? gp->ej[e] : gp->ei[e];
-                const float one = site_weight<kPatR>(w, lane, 0u, qi);
-                if (lane == 0) p1m[2 * e + k2] = __fdiv_rn(__fmul_rn(gf, one), tot);
-                tot = __fsub_rn(tot, __fmul_rn(gf, one));  // no jump: the weight on bit 1 shrinks by 1 - gamma
-#pragma unroll
-                for (int r = 0; r < kPatR; ++r) {
-                    const bool bit = (((uint32_t)(lane + 32 * r) >> qi) & 1u) != 0;
-                    w[r] = bit ? __fmul_rn(w[r], omg) : w[r];
-                }
-            }
+    for (int r = 0; r < kPatR; ++r) {
+        const int b = lane + 32 * r;
+        if (b < nbins) Hs[b] = 0ull;  // zero again for the next group that accumulates here
+        ht[b] = w[r];
     }
-    if (threadIdx.x == 0) gv.st_prev[slot] = st;
+    // the identity / no-jump path: gamma P(q = 1) at every damping site
+    const float gf = (float)gamma, omg = (float)(1.0 - gamma);
+    float tot = site_weight<kPatR>(w, lane, 0u, -1);
+    float *p1m = gv.p1m + (size_t)slot * 2 * kMaxGroupEdges;
+    for (int e = 0; e < m; ++e)
+        for (int k2 = 0; k2 < nsite; ++k2) {
+            const int qi = k2 ? gp->ej[e] : gp->ei[e];
+            const float one = site_weight<kPatR>(w, lane, 0u, qi);
+            if (lane == 0) p1m[2 * e + k2] = __fdiv_rn(__fmul_rn(gf, one), tot);
+            tot = __fsub_rn(tot, __fmul_rn(gf, one));  // no jump: the weight on bit 1 shrinks by 1 - gamma
+#pragma unroll
+            for (int r = 0; r < kPatR; ++r) {
+                const bool bit = (((uint32_t)(lane + 32 * r) >> qi) & 1u) != 0;
+                w[r] = bit ? __fmul_rn(w[r], omg) : w[r];
+            }
+        }
+    if (lane == 0) gv.st_prev[slot] = st;
     const int2 rg = sv.range[slot];
-    for (int i = threadIdx.x; i < rg.y; i += kThreads) gv.pos_slot[rg.x + i] = slot;
+    for (int i = lane; i < rg.y; i += 32) gv.pos_slot[rg.x + i] = slot;
     allow_dependent_launch();
 }
+
+// Members per k_gd_members block: a member that leaves the shared path costs its
+// warp a serial walk over the group's sites (longer for more patterns per lane),
+// so large groups spread their members thinly and give each event a warp of its own.
+__host__ __device__ constexpr int gd_members_per_block(int pat_r) { return pat_r >= 32 ? 32 : pat_r >= 4 ? 64 : kThreads; }
 
 template <int kPatR>
 __global__ void __launch_bounds__(kThreads) k_gd_members(BatchView v, SlotView sv, GroupView gv, double gamma) {
     grid_dependency_wait();
+    constexpr int kPer = gd_members_per_block(kPatR);
     const GateGroup *gp = gv.grp;
     const int m = gp->m, nsite = gp->kind == 0 ? 2 : 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int pos = blockIdx.x * kThreads + threadIdx.x;
+    const int pos = blockIdx.x * kPer + threadIdx.x;
     bool ev = false;
-    if (pos < gv.members) {
+    if ((int)threadIdx.x < kPer && pos < gv.members) {
         // all of the member's codes and words first (independent loads), then the tests
         const int slot = gv.pos_slot[pos];
         const size_t g0 = (size_t)sv.members[pos] * v.G + gp->g0;
@@ -1709,7 +1839,7 @@ __global__ void __launch_bounds__(kThreads) k_gd_members(BatchView v, SlotView s
     __shared__ uint32_t s_dw[kThreads / 32][2 * kMaxGroupEdges];
     const float gf = (float)gamma, omg = (float)(1.0 - gamma);
     for (int a = warp; a < ne; a += kThreads / 32) {  // their own draws: one warp each
-        const int p = blockIdx.x * kThreads + evl[a];
+        const int p = blockIdx.x * kPer + evl[a];
         const int slot = gv.pos_slot[p];
         const size_t gbase = (size_t)sv.members[p] * v.G + gp->g0;
         if (lane < m) s_code[warp][lane] = v.branch[gbase + lane] & 15;
@@ -1727,6 +1857,34 @@ __global__ void __launch_bounds__(kThreads) k_gd_members(BatchView v, SlotView s
     allow_dependent_launch();
 }
 
+// Exclusive prefix sums of in[0 .. cnt) plus base into out[0 .. cnt), in place
+// allowed; called by the whole block.
+__device__ void block_scan_excl(int cnt, const int *in, int *out, int base) {
+    __shared__ int wsum[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int run = base;
+    for (int i0 = 0; i0 < cnt; i0 += kThreads) {
+        const int i = i0 + (int)threadIdx.x;
+        const int x = i < cnt ? in[i] : 0;
+        int inc = x;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        int before = run, total = run;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            if (w < warp) before += wsum[w];
+            total += wsum[w];
+        }
+        if (i < cnt) out[i] = before + inc - x;
+        __syncthreads();
+        run = total;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView sv, GroupView gv) {
     grid_dependency_wait();
     const int slot = blockIdx.x;
@@ -1736,35 +1894,46 @@ __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView s
     const int32_t *mem = sv.members + off;
     const GroupKey *key = gv.ekey + off;
     int32_t *evt = gv.evt + off, *rep = gv.rep + off, *lead = gv.lead + off;
+    int32_t *lcount = gv.lcount + off, *lstart = gv.lstart + off, *run = gv.pos_slot + off;  // run: scratch
     // members that left the shared path, in member order
     const int ne = block_select(cnt, [&](int i) { return !key_zero(key[i]); }, [&](int r, int i) { evt[r] = i; });
-    // classes: the shared path (if any member kept it), then one per distinct
-    // outcome string in order of its first event
-    for (int a = threadIdx.x; a < ne; a += kThreads) {
-        const GroupKey ka = key[evt[a]];
-        int r = a;
-        for (int b = 0; b < a; ++b)
-            if (key_eq(key[evt[b]], ka)) {
-                r = b;
-                break;
-            }
-        rep[a] = r;
+    // rep[a] = the first event b <= a with a's outcome string, over keys staged in
+    // shared memory a chunk at a time (a thread keeps the same events a throughout)
+    constexpr int kKeyChunk = 2 * kThreads;
+    __shared__ GroupKey skey[kKeyChunk];
+    for (int a = threadIdx.x; a < ne; a += kThreads) rep[a] = -1;
+    for (int c0 = 0; c0 < ne; c0 += kKeyChunk) {
+        const int cn = min(kKeyChunk, ne - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cn; i += kThreads) skey[i] = key[evt[c0 + i]];
+        __syncthreads();
+        for (int a = c0 + (int)threadIdx.x; a < ne; a += kThreads) {
+            if (rep[a] >= 0) continue;
+            const GroupKey ka = key[evt[a]];
+            const int bend = min(a + 1 - c0, cn);  // b <= a
+            for (int b = 0; b < bend; ++b)
+                if (key_eq(skey[b], ka)) {
+                    rep[a] = c0 + b;
+                    break;
+                }
+        }
     }
     __syncthreads();
+    // classes: the shared path (if any member kept it), then one per distinct
+    // outcome string in order of its first event
     const int nlead = block_select(ne, [&](int a) { return rep[a] == a; }, [&](int r, int a) { lead[r] = a; });
     const int mainc = cnt - ne;
     const int hasmain = mainc > 0 ? 1 : 0;
     const int nc = hasmain + nlead;
+    // members per class (integer counts, in any order), then the classes' starts
     for (int r = threadIdx.x; r < nlead; r += kThreads) {
-        const int a = lead[r];
-        int count = 0, before = 0;
-        for (int b = 0; b < ne; ++b) {
-            count += rep[b] == a;
-            before += rep[b] < a;
-        }
-        gv.lcount[off + r] = count;
-        gv.lstart[off + r] = mainc + before;
+        lcount[r] = 0;
+        run[r] = 0;
     }
+    __syncthreads();
+    for (int a = threadIdx.x; a < ne; a += kThreads) atomicAdd(&lcount[lower_bound_i32(lead, nlead, rep[a])], 1);
+    __syncthreads();
+    block_scan_excl(nlead, lcount, lstart, mainc);
     if (threadIdx.x == 0) child_base = nc > 1 ? atomicAdd(sv.slot_count, nc - 1) : 0;
     __syncthreads();
     if (nc > 1) {  // stable partition of the members by class into tmp[off ..]
@@ -1773,14 +1942,24 @@ __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView s
             if (lb < ne && evt[lb] == i) continue;
             sv.tmp[off + i - lb] = mem[i];
         }
-        for (int a = threadIdx.x; a < ne; a += kThreads) {
-            const int ra = rep[a];
-            const int r = lower_bound_i32(lead, nlead, ra);
-            int pos = 0;
-            for (int b = ra; b < a; ++b) pos += rep[b] == ra;
-            sv.tmp[off + gv.lstart[off + r] + pos] = mem[evt[a]];
+        // events in order, a chunk of kThreads at a time: an event's place in its class is
+        // the class's events in earlier chunks (run) plus those before it in its chunk
+        __shared__ int srep[kThreads];
+        for (int a0 = 0; a0 < ne; a0 += kThreads) {
+            const int a = a0 + (int)threadIdx.x;
+            const int ra = a < ne ? rep[a] : -1;
+            srep[threadIdx.x] = ra;
+            __syncthreads();
+            if (a < ne) {
+                int pos = 0;
+                for (int b = 0; b < (int)threadIdx.x; ++b) pos += srep[b] == ra;
+                const int r = lower_bound_i32(lead, nlead, ra);
+                sv.tmp[off + lstart[r] + run[r] + pos] = mem[evt[a]];
+            }
+            __syncthreads();
+            if (a < ne) atomicAdd(&run[lower_bound_i32(lead, nlead, ra)], 1);
+            __syncthreads();
         }
-        __syncthreads();
         for (int i = threadIdx.x; i < cnt; i += kThreads) sv.members[off + i] = sv.tmp[off + i];
     }
     for (int c = threadIdx.x; c < nc; c += kThreads) {
@@ -1792,8 +1971,8 @@ __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView s
         if (c >= hasmain) {
             const int r = c - hasmain;
             gc.key = key[evt[lead[r]]];
-            gc.start = off + gv.lstart[off + r];
-            gc.count = gv.lcount[off + r];
+            gc.start = off + lstart[r];
+            gc.count = lcount[r];
         }
         gc.target = c == 0 ? slot : child_base + c - 1;
         if (gc.target >= sv.max_slots) {
@@ -1806,11 +1985,8 @@ __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView s
 }
 
 template <int kPatR>
-__global__ void __launch_bounds__(kThreads) k_gd_tables(BatchView v, SlotView sv, GroupView gv, double gamma) {
-    grid_dependency_wait();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * (kThreads / 32) + warp;
-    if (c >= *gv.ncls) return;
+__device__ __forceinline__ void gd_table(const BatchView &v, const SlotView &sv, const GroupView &gv, double gamma,
+                                         int c, int lane) {
     const GroupClass gc = gv.cls[c];
     const GateGroup *gp = gv.grp;
     const int m = gp->m, ns = gp->s, nbins = 1 << ns, kind = gp->kind, nsite = kind == 0 ? 2 : 1;
@@ -1888,6 +2064,17 @@ __global__ void __launch_bounds__(kThreads) k_gd_tables(BatchView v, SlotView sv
             gv.parent[gc.target] = gc.slot;  // its first sweep reads the parent's state
         }
     }
+}
+
+// Warp per class, over a grid sized to what is resident at once (the class
+// count is known on the device only).
+template <int kPatR>
+__global__ void __launch_bounds__(kThreads) k_gd_tables(BatchView v, SlotView sv, GroupView gv, double gamma) {
+    grid_dependency_wait();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ncls = *gv.ncls;
+    for (int c = blockIdx.x * (kThreads / 32) + warp; c < ncls; c += gridDim.x * (kThreads / 32))
+        gd_table<kPatR>(v, sv, gv, gamma, c, lane);
 }
 
 // Copy the parent's statevector into every slot forked at this gate.
@@ -1991,8 +2178,9 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
 
 constexpr int kAccChunk = 32;
 
-// Row block blockIdx.y takes chunks [y C / P, (y + 1) C / P) of the C chunks of states; row 0 adds
-// its sigma terms to probs, the others store theirs in spart (summed on in row order afterwards).
+// Row block blockIdx.y takes states [y b / P, (y + 1) b / P) of the b states, in chunks of
+// kAccChunk; row 0 adds its sigma terms to probs, the others store theirs in spart (summed on in
+// row order afterwards).
 template <bool TRIVIAL>
 __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, int64_t xblocks) {
     const int xb = blockIdx.x;
@@ -2059,11 +2247,10 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
         for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
         if (lane == 0) cw[ci][warp] = cp;
     };
-    const int nchunks = (v.b + kAccChunk - 1) / kAccChunk;
-    const int cbeg = (int)((int64_t)blockIdx.y * nchunks / gridDim.y);
-    const int cend = (int)((int64_t)(blockIdx.y + 1) * nchunks / gridDim.y);
-    for (int t0c = cbeg * kAccChunk; t0c < min(v.b, cend * kAccChunk); t0c += kAccChunk) {
-        const int tend = min(v.b, t0c + kAccChunk);
+    const int tbeg = (int)((int64_t)blockIdx.y * v.b / gridDim.y);
+    const int tlim = (int)((int64_t)(blockIdx.y + 1) * v.b / gridDim.y);
+    for (int t0c = tbeg; t0c < tlim; t0c += kAccChunk) {
+        const int tend = min(tlim, t0c + kAccChunk);
         // the chunk's per-state parameters, once per block
         if ((int)threadIdx.x < tend - t0c) {
             const int tt = t0c + threadIdx.x;
@@ -2543,6 +2730,16 @@ static int persistent_blocks() {
     return blocks;
 }
 
+// Blocks of kThreads that fit on the device at once (kernel without dynamic shared memory).
+template <typename K>
+static int resident_blocks(K kernel) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0);
+    return (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+}
+
 template <typename K, typename... Args>
 static cudaError_t launch_pdl_smem(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -2590,19 +2787,36 @@ cudaError_t launch_observe(const BatchView &v, const AccumView &, cudaStream_t s
     return cudaGetLastError();
 }
 
-int probs_parts(int n, int b) {
+int probs_parts(int n, int b, bool trivial_pending) {
     const int64_t xb = accumulate_xblocks(n);
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    static int resident[2] = {0, 0};
+    int &res = resident[trivial_pending ? 1 : 0];
+    if (res == 0) {
+        int dev = 0, sms = 0, occ = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
+        if (trivial_pending) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs<true>, kThreads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs<false>, kThreads, 0);
+        res = std::max(sms, 1) * std::max(occ, 1);
     }
-    // about four waves of two blocks per SM, at least one chunk of states per row
-    int p = (int)((4 * 2 * (int64_t)sms + xb - 1) / xb);
-    p = std::min(p, (b + kAccChunk - 1) / kAccChunk);
-    return std::max(1, std::min(p, kMaxProbParts));
+    // Every block of a row streams all of the row's states, so the launch takes about
+    // ceil(xb P / resident) rounds of b / P states each: take the P with the fewest
+    // state-rounds (the smaller on a tie).  A row keeps at least one chunk of states,
+    // and rows past the first hold a sigma copy (8 B per basis state), 64 MiB at most.
+    const int64_t copies = std::max<int64_t>(0, ((int64_t)64 << 20) / ((int64_t)8 << n));
+    const int64_t row_cap = std::min<int64_t>((int64_t)kMaxProbParts, ((int64_t)b + kAccChunk - 1) / kAccChunk);
+    const int pmax = (int)std::max<int64_t>(1, std::min<int64_t>(row_cap, 1 + copies));
+    int best = 1;
+    double best_cost = 0.0;
+    for (int p = 1; p <= pmax; ++p) {
+        const double rounds = (double)((xb * p + res - 1) / res);
+        const double cost = rounds * std::ceil((double)b / p);
+        if (p == 1 || cost < best_cost * 0.995) {
+            best = p;
+            best_cost = cost;
+        }
+    }
+    return best;
 }
 
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s) {
@@ -2695,11 +2909,14 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
                                 double gamma, cudaStream_t s) {
     const dim3 blk(kThreads);
     const dim3 slots((unsigned)active);
-    const dim3 members((unsigned)((gv.members + kThreads - 1) / kThreads));
-    const dim3 classes((unsigned)((sv.max_slots + kThreads / 32 - 1) / (kThreads / 32)));
+    const dim3 slot_warps((unsigned)((active + kThreads / 32 - 1) / (kThreads / 32)));
+    const int class_blocks = (sv.max_slots + kThreads / 32 - 1) / (kThreads / 32);
     cudaError_t e;
 #define QN_GD(R)                                                                                \
-    e = launch_pdl(k_gd_joint<R>, slots, blk, s, v, sv, gv, gamma);                             \
+    static const int resident = resident_blocks(k_gd_tables<R>);                                \
+    const dim3 classes((unsigned)std::min(class_blocks, resident));                             \
+    const dim3 members((unsigned)((gv.members + gd_members_per_block(R) - 1) / gd_members_per_block(R))); \
+    e = launch_pdl(k_gd_joint<R>, slot_warps, blk, s, v, sv, gv, gamma, active);                \
     if (e == cudaSuccess) e = launch_pdl(k_gd_members<R>, members, blk, s, v, sv, gv, gamma);   \
     if (e == cudaSuccess) e = launch_pdl(k_gd_classes, slots, blk, s, v, sv, gv);               \
     if (e == cudaSuccess) e = launch_pdl(k_gd_tables<R>, classes, blk, s, v, sv, gv, gamma);
@@ -2718,10 +2935,10 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
 cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
     static const cudaError_t attr = [] {
         const void *ks[] = {(const void *)k_mix_sweep<true, kMixAny>,  (const void *)k_mix_sweep<true, kMixMid>,
-                            (const void *)k_mix_sweep<true, kMixFirst>, (const void *)k_mix_sweep<true, kMixHist>,
-                            (const void *)k_mix_sweep<true, kMixNorm>, (const void *)k_mix_sweep<false, kMixAny>,
-                            (const void *)k_mix_sweep<false, kMixMid>, (const void *)k_mix_sweep<false, kMixFirst>,
-                            (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixNorm>};
+                            (const void *)k_mix_sweep<true, kMixHist>, (const void *)k_mix_sweep<true, kMixNorm>,
+                            (const void *)k_mix_sweep<false, kMixAny>, (const void *)k_mix_sweep<false, kMixMid>,
+                            (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixNorm>,
+                            (const void *)k_mix_first<true>,           (const void *)k_mix_first<false>};
         for (const void *k : ks) {
             const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem);
             if (e != cudaSuccess) return e;
@@ -2737,14 +2954,17 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
         const bool natural = mm.fA[0] == 0 && mm.fA[1] == 1 && mm.fA[2] == 2 && mm.fA[3] == 7 && mm.fB[0] == 3 &&
                              mm.fB[1] == 4 && mm.fB[2] == 5 && mm.fB[3] == 6 && mm.fL[0] == 8 && mm.fL[1] == 9 &&
                              mm.fL[2] == 10;
-        if (next_full && (!mm.has0 || natural)) var = mm.has0 ? kMixFirst : kMixMid;
+        if (next_full && mm.has0 && natural) {
+            return mm.tanf ? launch_pdl_smem(k_mix_first<true>, grid, block, kMixSmem, s, v, gv, mm)
+                           : launch_pdl_smem(k_mix_first<false>, grid, block, kMixSmem, s, v, gv, mm);
+        }
+        if (next_full && !mm.has0) var = kMixMid;
         else if (!mm.has0 && mm.nN == 0 && gv.next && !mm.final_norm) var = kMixHist;
         else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm) var = kMixNorm;
     }
 #define QN_MIX(T, V) launch_pdl_smem(k_mix_sweep<T, V>, grid, block, kMixSmem, s, v, gv, mm)
     switch (var) {
     case kMixMid: return mm.tanf ? QN_MIX(true, kMixMid) : QN_MIX(false, kMixMid);
-    case kMixFirst: return mm.tanf ? QN_MIX(true, kMixFirst) : QN_MIX(false, kMixFirst);
     case kMixHist: return mm.tanf ? QN_MIX(true, kMixHist) : QN_MIX(false, kMixHist);
     case kMixNorm: return mm.tanf ? QN_MIX(true, kMixNorm) : QN_MIX(false, kMixNorm);
     default: return mm.tanf ? QN_MIX(true, kMixAny) : QN_MIX(false, kMixAny);

@@ -174,8 +174,13 @@ class Batch:
         check(qn_expectation(self._h, ctypes.byref(m), ctypes.byref(s)), "qn_expectation")
         return m.value, s.value
 
-    def probs(self) -> np.ndarray:
-        out = np.zeros(1 << self.n, dtype=np.float64)
+    def probs(self, out: np.ndarray | None = None) -> np.ndarray:
+        """sigma, the ensemble's output distribution (2^n float64), into `out` if given: a
+        caller that reads it every step can pass the same (e.g. page-locked) buffer each time."""
+        if out is None:
+            out = np.empty(1 << self.n, dtype=np.float64)
+        elif out.dtype != np.float64 or out.size != (1 << self.n) or not out.flags.c_contiguous or not out.flags.writeable:
+            raise ValueError(f"out must be a writable contiguous float64 array of 2^n = {1 << self.n} elements")
         check(qn_probs(self._h, _dptr(out), out.size), "qn_probs")
         return out
 

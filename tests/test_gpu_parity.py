@@ -1,6 +1,6 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI.
 
-Bars (derived in DESIGN.md, "Tolerances"):
+Bars (each follows from the FP32 arithmetic of the path):
   * Pauli codes bit-exact (integer thresholds on the same Philox words);
   * damping branches equal except where u lies within FP32 reach of p1 (counted);
   * amplitudes within 1e-5 absolute;
@@ -185,6 +185,12 @@ def test_invalid_inputs(qn):
     b.run_qaoa([[0, 1]], [0.1], [0.2], p1=0.01)
     out = np.zeros(8)
     assert qn.qn_probs(b._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 8) == qn.QN_EINVAL
+    # sigma into a caller's buffer, reused across reads
+    buf = np.full(16, np.nan)
+    assert b.probs(out=buf) is buf and np.array_equal(buf, b.probs())
+    for bad in (np.zeros(16, dtype=np.float32), np.zeros(8), np.zeros(32)[::2]):
+        with pytest.raises(ValueError):
+            b.probs(out=bad)
     with pytest.raises(qn.QnError, match="QN_EINVAL"):
         b.traj_debug(5, 4)
     b.close()
