@@ -535,9 +535,9 @@ BatchView view_for(qn_batch *h, int64_t t0, int b) {
 
 qn_status check_status(const qn_batch *h);
 
-// Row blocks for k_probs over b states, with their sigma scratch.
-qn_status probs_rows(qn_batch *h, int b, AccumView *a) {
-    a->parts = a->probs ? probs_parts(h->n, b, a->trivial_pending != 0) : 1;
+// Row blocks for the sigma pass (probs_parts kind) over b states, with their sigma scratch.
+qn_status probs_rows(qn_batch *h, int b, AccumView *a, int kind) {
+    a->parts = a->probs ? probs_parts(h->n, b, kind) : 1;
     if (a->parts > 1) {
         const int64_t need = (int64_t)(a->parts - 1) << h->n;
         if (h->spart_cap < need) {
@@ -725,7 +725,7 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     a.c_out = ensemble ? h->c_all + t0 : h->c_dbg;
     a.probs = ensemble ? h->probs : nullptr;
     a.sums = ensemble ? h->sums : nullptr;
-    QN_TRY(probs_rows(h, b, &a));
+    QN_TRY(probs_rows(h, b, &a, 0));
     QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
     QN_CUDA(launch_observe(v, a, h->stream));
     QN_TRY(prof_end(h, &ep));
@@ -856,6 +856,10 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     int32_t *active_host = &active_word;
     int active = ns;
     bool final_norms = false;  // the last sweep formed 1 / ||psi||^2 of every state
+    // the last sweep kept the states (a full mixer block off qubit 0): the sigma pass applies it
+    bool keep = false;
+    MixMap keep_mm;
+    MixTail keep_tail{};
     const double amp_count = (double)((size_t)1 << n);
     for (int g = n; g < G; ++g) {
         const int gi = grouped ? h->group_at[g] : -1;
@@ -920,10 +924,22 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                 mm.tanf = std::fabs(z.c) >= std::fabs(z.sn);
                 mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
                 final_norms = final_norms || mm.final_norm;
+                if (mm.final_norm && mm.M == kMixQ && !mm.has0 && mm.nN == 0 && !gv.next) {
+                    // its states are read once more by the sigma pass anyway: form only the
+                    // norms here and let that pass apply the block, so no state is written
+                    mm.keep = 1;
+                    keep = true;
+                    keep_mm = mm;
+                    keep_tail.grp = gv.grp;
+                    keep_tail.T = gv.T;
+                    keep_tail.parent = gv.parent;
+                    keep_tail.first_new = old_active;
+                }
             }
             // the slots forked here first, reading their parents' states; then
             // the older slots in place (the launch order keeps parents unread-over)
-            QN_TRY(prof_begin(h, &ep, z.kind == 0 ? 3 : 4, (double)active * 16.0 * amp_count));
+            const double sweep_b = (double)active * (mm.keep && z.kind == 1 ? 8.0 : 16.0) * amp_count;
+            QN_TRY(prof_begin(h, &ep, z.kind == 0 ? 3 : 4, sweep_b));
             for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
                 const int first = part == 0 ? old_active : 0;
                 const int count = part == 0 ? active - old_active : old_active;
@@ -936,7 +952,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             }
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
             QN_TRY(prof_end(h, &ep));
-            h->sweep_bytes += (double)active * 16.0 * amp_count;
+            h->sweep_bytes += sweep_b;
             h->launches += 2;  // decide, finish
             g += z.m - 1;
             continue;
@@ -989,10 +1005,11 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     a.probs = h->probs;
     a.sums = h->sums;
     a.trivial_pending = final_norms;  // the last sweep left no pending op
-    QN_TRY(probs_rows(h, nslots, &a));
+    QN_TRY(probs_rows(h, nslots, &a, keep ? 2 : (final_norms ? 1 : 0)));
     QN_TRY(prof_begin(h, &ep, 2, (double)nslots * (final_norms ? 8.0 : 16.0) * (double)((size_t)1 << n)));
     if (!final_norms) QN_CUDA(launch_observe(vo, a, h->stream));
-    QN_CUDA(launch_probs(vo, a, h->stream));
+    if (keep) QN_CUDA(launch_probs_mix(vo, a, keep_mm, keep_tail, h->stream));
+    else QN_CUDA(launch_probs(vo, a, h->stream));
     QN_TRY(prof_end(h, &ep));
     h->launches += (final_norms ? 1 : 2) + (a.parts > 1 ? 1 : 0);
     h->sh_slots += nslots;

@@ -115,6 +115,17 @@ struct MixMap {
     int32_t nN;       // qubits of the next block (0: no joint to accumulate)
     int32_t final_norm;  // last sweep of the circuit: also form 1 / ||psi||^2 per state
     int32_t tanf;     // |cos beta| >= |sin beta|: rotations in the tan form, else the cot form
+    int32_t keep = 0;  // with final_norm: form only the norms and leave the states as they were
+                       // (the sigma pass applies the block; full blocks off qubit 0 only)
+};
+
+// The circuit's last mixer block when its sweep kept the states (MixMap::keep):
+// what the sigma pass needs to apply it to each state.
+struct MixTail {
+    const GateGroup *grp;   // device: the block (its angle)
+    const float2 *T;        // [slots][kGroupBins] the block's drawn factors by stored bits
+    const int32_t *parent;  // [slots] the parent of each slot forked at the block
+    int32_t first_new;      // slots from this one on were forked at the block
 };
 constexpr int kMixSubs = 4;  // tiles per thread block (streamed through two shared buffers)
 
@@ -221,9 +232,13 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
                          cudaStream_t s);
 cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
-// Row blocks worth giving k_probs for b states (1 .. kMaxProbParts), for the
-// variant without (trivial_pending) or with a pending op.
-int probs_parts(int n, int b, bool trivial_pending);
+// The sigma pass that applies the circuit's last mixer block on the fly (states
+// kept by a MixMap::keep sweep); same outputs as launch_probs.
+cudaError_t launch_probs_mix(const BatchView &v, const AccumView &a, const MixMap &mm, const MixTail &tl,
+                             cudaStream_t s);
+// Row blocks worth giving the sigma pass for b states (1 .. kMaxProbParts): k_probs
+// with a pending op (kind 0) or without (1), or the pass of launch_probs_mix (2).
+int probs_parts(int n, int b, int kind);
 constexpr int kMaxProbParts = 16;
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
 // Fused layers (Pauli-only): per-trajectory layer parameters from the branch

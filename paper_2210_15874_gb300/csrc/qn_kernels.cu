@@ -1204,9 +1204,11 @@ __device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
 //   kMixMid   not qubit 0, a full next block
 //   kMixHist  not qubit 0, no next block, the next layer's first phase-group joint
 //   kMixNorm  not qubit 0, no next block, the final norms
+//   kMixKeep  as kMixNorm, but stores nothing: the states stay as they were and
+//             the sigma pass (k_probs_mix) applies the block again on the fly
 // and kMixAny, which reads everything from the map.  The block holding qubit 0
 // with a full next block has a kernel of its own (k_mix_first).
-enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixNorm = 3 };
+enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixNorm = 3, kMixKeep = 4 };
 
 template <bool TANF, int VAR>
 __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
@@ -1223,7 +1225,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     const bool has0 = kFix ? false : mm.has0 != 0;
     const int M = kFix ? kMixQ : mm.M;
     const int nN = kFix ? (VAR == kMixMid ? kMixQ : 0) : mm.nN;
-    const bool final_norm = kFix ? VAR == kMixNorm : mm.final_norm != 0;
+    const bool final_norm = kFix ? (VAR == kMixNorm || VAR == kMixKeep) : mm.final_norm != 0;
     const float c = gv.grp->c, sn = gv.grp->sn;
     const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;  // rotation = rsc * (tangent form)
     float scM = 1.0f;  // rsc^M: the block's rotations, folded into its factors
@@ -1373,7 +1375,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
             x[j].z *= f1;
             x[j].w *= f1;
             if (has0) buf[idx1(j)] = x[j];  // stored from the tile in copy order below
-            else p4[fb | aoff(j)] = x[j];
+            else if (VAR != kMixKeep) p4[fb | aoff(j)] = x[j];
             if (nN > 0 && !has0) buf[idx1(j)] = x[j];
             if (nx) {
                 if (j == 0) gn.base = nb0 | ((sub & 1) ? nb1 : 0) | ((sub & 2) ? nb2 : 0);
@@ -2178,6 +2180,43 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
 
 constexpr int kAccChunk = 32;
 
+// The end of a sigma pass, after a block's sigma terms are out: the last block
+// to finish forms <C>_t of every state from the per-block partial sums and adds
+// S1, S2 in state order.
+__device__ void probs_finish(const BatchView &v, const AccumView &a, int64_t xblocks) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(a.acc_counter, 1u);
+        last = prev == (unsigned)(xblocks * gridDim.y - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int tt = threadIdx.x; tt < v.b; tt += blockDim.x) {
+        double sum = 0.0;
+        for (int64_t i = 0; i < xblocks; ++i) sum += __ldcg(a.cpart + (size_t)tt * xblocks + i);
+        a.c_out[tt] = sum * v.inv_norm[a.order ? a.order[tt] : tt];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (a.sums) {
+            double s1 = a.sums[0], s2 = a.sums[1];
+            for (int tt = 0; tt < v.b; ++tt) {
+                const double cv = a.c_out[tt];
+                const double w = a.weights ? a.weights[a.order ? a.order[tt] : tt] : 1.0;
+                s1 += w * cv;
+                s2 += w * cv * cv;
+            }
+            a.sums[0] = s1;
+            a.sums[1] = s2;
+        }
+        *a.acc_counter = 0;
+    }
+}
+
+
 // Row block blockIdx.y takes states [y b / P, (y + 1) b / P) of the b states, in chunks of
 // kAccChunk; row 0 adds its sigma terms to probs, the others store theirs in spart (summed on in
 // row order afterwards).
@@ -2195,7 +2234,6 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
     __shared__ float c_ih[kAccChunk], c_il[kAccChunk];
     __shared__ float s_cut[kX][kThreads];
     __shared__ double s_acc[kX][kThreads];
-    __shared__ int last;
     const int64_t f0 = (int64_t)xb * kTileF4 + threadIdx.x;
 #pragma unroll
     for (int k = 0; k < kF4PerThread; ++k)
@@ -2304,35 +2342,7 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
                 }
             }
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(a.acc_counter, 1u);
-        last = prev == (unsigned)(xblocks * gridDim.y - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (int tt = threadIdx.x; tt < v.b; tt += kThreads) {
-        double sum = 0.0;
-        for (int64_t i = 0; i < xblocks; ++i) sum += __ldcg(a.cpart + (size_t)tt * xblocks + i);
-        a.c_out[tt] = sum * v.inv_norm[a.order ? a.order[tt] : tt];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (a.sums) {
-            double s1 = a.sums[0], s2 = a.sums[1];
-            for (int tt = 0; tt < v.b; ++tt) {
-                const double cv = a.c_out[tt];
-                const double w = a.weights ? a.weights[a.order ? a.order[tt] : tt] : 1.0;
-                s1 += w * cv;
-                s2 += w * cv * cv;
-            }
-            a.sums[0] = s1;
-            a.sums[1] = s2;
-        }
-        *a.acc_counter = 0;
-    }
+    probs_finish(v, a, xblocks);
 }
 
 // sigma += the other row blocks' terms, in row order.
@@ -2342,6 +2352,166 @@ __global__ void k_probs_combine(double *probs, const double *spart, int parts, i
         for (int p = 0; p + 1 < parts; ++p) acc += spart[(size_t)p * dim + x];
         probs[x] = acc;
     }
+}
+
+// The sigma pass when the circuit ends on a full mixer block off qubit 0 whose
+// sweep (kMixKeep) formed only the final norms and left every state as it was
+// before the block.  The pass applies the block to each state on the fly --
+// the same rotations, then the same drawn factors, in the same order as
+// k_mix_sweep -- so each probability is bit-identical to the ones the norms
+// summed, and the final states are never written.  A slot forked at the block
+// reads its parent's state.  Grid (half tiles of the block's map, row blocks) x
+// kMixThreads: two lanes (lane bit 4 = the block's fourth qubit) share a fiber
+// of 16 float4 along the block's qubits, 8 each (the first three qubits on the
+// register index), at true bits fixed over the states.  Each float4 is read from
+// its true position XOR the state's frame; since a rotation treats a pair's two
+// values alike, rotating in true order gives the stored-order values moved.
+template <bool TANF>
+__global__ void __launch_bounds__(kMixThreads) k_probs_mix(BatchView v, AccumView a, MixMap mm, MixTail tl,
+                                                           int64_t xblocks) {
+    constexpr int kR = kMixE / 2;  // float4 per thread
+    constexpr int kE = 2 * kR;     // basis states per thread
+    constexpr int kWarps = kMixThreads / 32;
+    static_assert(kMixQ == 4 && kMixL == 3 && kMixThreads == 128, "lanes: 3 L bits, 1 B bit, the fourth qubit");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ float cw[kAccChunk][kWarps];
+    __shared__ int c_src[kAccChunk];
+    __shared__ uint32_t c_Ff[kAccChunk];
+    __shared__ float c_ih[kAccChunk], c_il[kAccChunk];
+    __shared__ float c_df[kAccChunk][kMixE];
+    __shared__ float s_cut[kE][kMixThreads];
+    __shared__ double s_acc[kE][kMixThreads];
+    const float c = tl.grp->c, sn = tl.grp->sn;
+    const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;
+    float scM = 1.0f;  // rsc^4, folded into the factors as k_mix_sweep does
+    for (int i = 0; i < kMixQ; ++i) scM *= rsc;
+    // this thread's float4: true index base | aoff(j), j along the block's first three qubits;
+    // lane bits 0-2 the L bits, lane bit 3 and the warp the B bits 0-2, lane bit 4 the fourth
+    // qubit, blockIdx.x B bit 3 then the tile bits
+    const int hi = lane >> 4;  // this lane's fourth-qubit bit
+    uint32_t base = 0, ao[kMixQ - 1];
+#pragma unroll
+    for (int i = 0; i < kMixL; ++i) base |= (uint32_t)((lane >> i) & 1) << mm.fL[i];
+    base |= (uint32_t)((lane >> 3) & 1) << mm.fB[0];
+    base |= (uint32_t)(warp & 1) << mm.fB[1];
+    base |= (uint32_t)((warp >> 1) & 1) << mm.fB[2];
+    base |= (uint32_t)hi << mm.fA[3];
+    base |= (uint32_t)(blockIdx.x & 1u) << mm.fB[3];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
+        if (i < mm.ntile) base |= ((blockIdx.x >> (i + 1)) & 1u) << mm.ftile[i];
+#pragma unroll
+    for (int i = 0; i < kMixQ - 1; ++i) ao[i] = 1u << mm.fA[i];
+    const uint32_t ao3 = 1u << mm.fA[3];
+    auto aoff = [&](int j) {
+        uint32_t o = 0;
+#pragma unroll
+        for (int i = 0; i < kMixQ - 1; ++i) o |= (j & (1 << i)) ? ao[i] : 0u;
+        return o;
+    };
+#pragma unroll
+    for (int j = 0; j < kR; ++j)
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t x = 2u * (base | aoff(j)) + (uint32_t)e;
+            int cnt = 0;
+            for (int k = 0; k < a.num_edges; ++k) {
+                const int2 ed = a.edges[k];
+                cnt += (int)(((x >> ed.x) ^ (x >> ed.y)) & 1u);
+            }
+            s_cut[2 * j + e][threadIdx.x] = (float)cnt;
+            s_acc[2 * j + e][threadIdx.x] = 0.0;
+        }
+    const int tbeg = (int)((int64_t)blockIdx.y * v.b / gridDim.y);
+    const int tlim = (int)((int64_t)(blockIdx.y + 1) * v.b / gridDim.y);
+    for (int t0c = tbeg; t0c < tlim; t0c += kAccChunk) {
+        const int cn = min(tlim, t0c + kAccChunk) - t0c;
+        // the chunk's per-state parameters, once per block
+        if ((int)threadIdx.x < cn) {
+            const int tt = t0c + threadIdx.x;
+            const int sl = a.order ? a.order[tt] : tt;
+            const TrajState st = v.st[sl];
+            c_src[threadIdx.x] = sl >= tl.first_new ? tl.parent[sl] : sl;
+            c_Ff[threadIdx.x] = v.frame_x[(size_t)sl * (v.G + 1) + v.G] ^ st.J ^ st.pend;
+            const double inv = v.inv_norm[sl] * (a.weights ? a.weights[sl] : 1.0);
+            const float ih = (float)inv;
+            c_ih[threadIdx.x] = ih;
+            c_il[threadIdx.x] = (float)(inv - (double)ih);
+        }
+        for (int i = threadIdx.x; i < cn * kMixE; i += kMixThreads) {
+            const int tt = t0c + i / kMixE;
+            const int sl = a.order ? a.order[tt] : tt;
+            c_df[i / kMixE][i % kMixE] = tl.T[(size_t)sl * kGroupBins + i % kMixE].x * scM;
+        }
+        __syncthreads();
+        float ah[kE], al[kE];  // sigma terms of this chunk (double-float)
+#pragma unroll
+        for (int i = 0; i < kE; ++i) ah[i] = al[i] = 0.0f;
+        for (int ci = 0; ci < cn; ++ci) {
+            const uint32_t Ff = c_Ff[ci], Fq = Ff >> 1;  // Fq: the frame on float4 indices
+            // this lane's pattern on the block's qubits is (j | hi << 3); stored: that ^ fa
+            int fa = (Fq & ao3) ? 8 : 0;
+#pragma unroll
+            for (int i = 0; i < kMixQ - 1; ++i) fa |= (Fq & ao[i]) ? 1 << i : 0;
+            // element j's stored index: (base | aoff(j)) ^ Fq = (base ^ Fq) ^ aoff(j)
+            const uint32_t sb = base ^ Fq;
+            const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)c_src[ci] << v.n));
+            float4 x[kR];
+#pragma unroll
+            for (int j = 0; j < kR; ++j) x[j] = q4[sb ^ aoff(j)];
+#pragma unroll
+            for (int i = 0; i < kMixQ - 1; ++i) {
+#pragma unroll
+                for (int j = 0; j < kR; ++j)
+                    if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
+            }
+#pragma unroll
+            for (int j = 0; j < kR; ++j) rx_lanes_t<TANF>(x[j], 16, rt);  // the fourth qubit
+            const float ih = c_ih[ci], il = c_il[ci];
+            const int fd = fa ^ (hi << 3);
+            float cp = 0.0f;
+#pragma unroll
+            for (int j = 0; j < kR; ++j) {
+                const float f = c_df[ci][j ^ fd];
+                x[j].x *= f;
+                x[j].y *= f;
+                x[j].z *= f;
+                x[j].w *= f;
+                const float pa = prob_of(1.0f, x[j].x, x[j].y), pb = prob_of(1.0f, x[j].z, x[j].w);
+                const float p0 = (Ff & 1u) ? pb : pa, p1 = (Ff & 1u) ? pa : pb;  // true qubit 0
+                df_add_prod(ah[2 * j], al[2 * j], p0, ih, il);
+                df_add_prod(ah[2 * j + 1], al[2 * j + 1], p1, ih, il);
+                cp += p0 * s_cut[2 * j][threadIdx.x];
+                cp += p1 * s_cut[2 * j + 1][threadIdx.x];
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
+            if (lane == 0) cw[ci][warp] = cp;
+        }
+#pragma unroll
+        for (int i = 0; i < kE; ++i) s_acc[i][threadIdx.x] += (double)ah[i] + (double)al[i];
+        __syncthreads();
+        if ((int)threadIdx.x < cn) {
+            double sum = 0.0;
+            for (int w = 0; w < kWarps; ++w) sum += (double)cw[threadIdx.x][w];
+            a.cpart[(size_t)(t0c + threadIdx.x) * xblocks + blockIdx.x] = sum;
+        }
+        __syncthreads();
+    }
+    if (a.probs) {
+        double *dst = blockIdx.y == 0 ? a.probs : a.spart + (size_t)(blockIdx.y - 1) * ((size_t)1 << v.n);
+#pragma unroll
+        for (int j = 0; j < kR; ++j) {
+            const size_t x = 2 * (size_t)(base | aoff(j));
+            if (blockIdx.y == 0) {
+                dst[x] += s_acc[2 * j][threadIdx.x];
+                dst[x + 1] += s_acc[2 * j + 1][threadIdx.x];
+            } else {
+                dst[x] = s_acc[2 * j][threadIdx.x];
+                dst[x + 1] = s_acc[2 * j + 1][threadIdx.x];
+            }
+        }
+    }
+    probs_finish(v, a, xblocks);
 }
 
 // ---------------------------------------------------------------------------
@@ -2787,16 +2957,18 @@ cudaError_t launch_observe(const BatchView &v, const AccumView &, cudaStream_t s
     return cudaGetLastError();
 }
 
-int probs_parts(int n, int b, bool trivial_pending) {
-    const int64_t xb = accumulate_xblocks(n);
-    static int resident[2] = {0, 0};
-    int &res = resident[trivial_pending ? 1 : 0];
+int probs_parts(int n, int b, int kind) {
+    // blocks per state: k_probs covers 2048 amplitudes per block, k_probs_mix 2048 (half a mixer tile)
+    const int64_t xb = kind == 2 ? std::max<int64_t>(2, (int64_t)1 << std::max(0, n - 11)) : accumulate_xblocks(n);
+    static int resident[3] = {0, 0, 0};
+    int &res = resident[kind];
     if (res == 0) {
         int dev = 0, sms = 0, occ = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (trivial_pending) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs<true>, kThreads, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs<false>, kThreads, 0);
+        if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs<false>, kThreads, 0);
+        else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs<true>, kThreads, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs_mix<true>, kMixThreads, 0);
         res = std::max(sms, 1) * std::max(occ, 1);
     }
     // Every block of a row streams all of the row's states, so the launch takes about
@@ -2825,6 +2997,20 @@ cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s)
     const dim3 grid((unsigned)xb, (unsigned)parts);
     if (a.trivial_pending) k_probs<true><<<grid, kThreads, 0, s>>>(v, a, xb);
     else k_probs<false><<<grid, kThreads, 0, s>>>(v, a, xb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || parts == 1) return e;
+    const int64_t dim = (int64_t)1 << v.n;
+    k_probs_combine<<<(unsigned)std::min<int64_t>((dim + 255) / 256, 4096), 256, 0, s>>>(a.probs, a.spart, parts, dim);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probs_mix(const BatchView &v, const AccumView &a, const MixMap &mm, const MixTail &tl,
+                             cudaStream_t s) {
+    const int64_t xb = (int64_t)2 << mm.ntile;  // half tiles
+    const int parts = a.probs && a.spart ? a.parts : 1;
+    const dim3 grid((unsigned)xb, (unsigned)parts);
+    if (mm.tanf) k_probs_mix<true><<<grid, kMixThreads, 0, s>>>(v, a, mm, tl, xb);
+    else k_probs_mix<false><<<grid, kMixThreads, 0, s>>>(v, a, mm, tl, xb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || parts == 1) return e;
     const int64_t dim = (int64_t)1 << v.n;
@@ -2938,6 +3124,7 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
                             (const void *)k_mix_sweep<true, kMixHist>, (const void *)k_mix_sweep<true, kMixNorm>,
                             (const void *)k_mix_sweep<false, kMixAny>, (const void *)k_mix_sweep<false, kMixMid>,
                             (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixNorm>,
+                            (const void *)k_mix_sweep<true, kMixKeep>, (const void *)k_mix_sweep<false, kMixKeep>,
                             (const void *)k_mix_first<true>,           (const void *)k_mix_first<false>};
         for (const void *k : ks) {
             const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem);
@@ -2960,13 +3147,14 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
         }
         if (next_full && !mm.has0) var = kMixMid;
         else if (!mm.has0 && mm.nN == 0 && gv.next && !mm.final_norm) var = kMixHist;
-        else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm) var = kMixNorm;
+        else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm) var = mm.keep ? kMixKeep : kMixNorm;
     }
 #define QN_MIX(T, V) launch_pdl_smem(k_mix_sweep<T, V>, grid, block, kMixSmem, s, v, gv, mm)
     switch (var) {
     case kMixMid: return mm.tanf ? QN_MIX(true, kMixMid) : QN_MIX(false, kMixMid);
     case kMixHist: return mm.tanf ? QN_MIX(true, kMixHist) : QN_MIX(false, kMixHist);
     case kMixNorm: return mm.tanf ? QN_MIX(true, kMixNorm) : QN_MIX(false, kMixNorm);
+    case kMixKeep: return mm.tanf ? QN_MIX(true, kMixKeep) : QN_MIX(false, kMixKeep);
     default: return mm.tanf ? QN_MIX(true, kMixAny) : QN_MIX(false, kMixAny);
     }
 #undef QN_MIX
