@@ -2,9 +2,10 @@
 
 Workload (one "step"): the 20-qubit p=3 QAOA MaxCut circuit on a seeded
 3-regular graph with depolarizing noise (p1=1e-3, p2=1e-2) and amplitude damping
-(gamma=5e-3) after every gate, K=4096 trajectories, 64 statevectors per launch:
-Philox Kraus sampling, every gate sweep with its damping draw, and the ensemble
-accumulation of <C> and sigma_approx.
+(gamma=5e-3) after every gate, K=4096 trajectories: Philox Kraus sampling, every
+gate sweep with its damping draws, and the ensemble accumulation of <C> and
+sigma_approx (the one-statevector-per-trajectory mode runs 64 statevectors per
+launch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gq|reference] [--sharing 0|1]
 
@@ -375,7 +376,7 @@ def gpu_arm(args):
             "kernels": {"gate sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["sweeps"],
                         "phase-group sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["groups"],
                         "mixer-block sweeps (sampled 1/%d)" % PROFILE_PERIOD: main["mixers"],
-                        "k_init": main["inits"], "k_observe+k_probs": main["accs"]},
+                        "k_init": main["inits"], "observables (k_observe, k_probs or k_probs_mix)": main["accs"]},
             "e2e": {"value": main["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": main["launches"],
             "clocks": main["clocks"],

@@ -831,9 +831,10 @@ __device__ __forceinline__ double df_warp_sum(float hi, float lo) {
 // same way, as one gate at a time), forks every outcome string other than the
 // shared one and writes per slot a table T of 2^|S| amplitude factors;
 // k_group_apply multiplies the state by T in one sweep and accumulates the
-// next group's joint on the way.  Joints are summed in warp-private shared histograms in a fixed order
-// and added across blocks as 2^-60 fixed-point integers, so they do not depend
-// on the order in which blocks run.
+// next group's joint on the way.  Joints are summed in warp-private shared
+// histograms in a fixed order (or, in the last mixer block of a layer, in one
+// block histogram of integers) and added across blocks as 2^-60 fixed-point
+// integers, so they do not depend on the order in which blocks or warps run.
 // ---------------------------------------------------------------------------
 constexpr double kHistScale = 1152921504606846976.0;  // 2^60
 constexpr double kHistUnit = 1.0 / kHistScale;
@@ -1203,12 +1204,13 @@ __device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
 // Variants with every bound a constant (all for full blocks of kMixQ qubits):
 //   kMixMid   not qubit 0, a full next block
 //   kMixHist  not qubit 0, no next block, the next layer's first phase-group joint
-//   kMixNorm  not qubit 0, no next block, the final norms
-//   kMixKeep  as kMixNorm, but stores nothing: the states stay as they were and
-//             the sigma pass (k_probs_mix) applies the block again on the fly
-// and kMixAny, which reads everything from the map.  The block holding qubit 0
-// with a full next block has a kernel of its own (k_mix_first).
-enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixNorm = 3, kMixKeep = 4 };
+//   kMixKeep  not qubit 0, the circuit's last block: forms the final norms and
+//             stores nothing (the states stay as they were; the sigma pass,
+//             k_probs_mix, applies the block again on the fly)
+// and kMixAny, which reads everything from the map (and stores the final states
+// of a last block it sweeps).  The block holding qubit 0 with a full next block
+// has a kernel of its own (k_mix_first).
+enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixKeep = 4 };
 
 template <bool TANF, int VAR>
 __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
@@ -1225,7 +1227,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     const bool has0 = kFix ? false : mm.has0 != 0;
     const int M = kFix ? kMixQ : mm.M;
     const int nN = kFix ? (VAR == kMixMid ? kMixQ : 0) : mm.nN;
-    const bool final_norm = kFix ? (VAR == kMixNorm || VAR == kMixKeep) : mm.final_norm != 0;
+    const bool final_norm = kFix ? VAR == kMixKeep : mm.final_norm != 0;
     const float c = gv.grp->c, sn = gv.grp->sn;
     const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;  // rotation = rsc * (tangent form)
     float scM = 1.0f;  // rsc^M: the block's rotations, folded into its factors
@@ -3120,12 +3122,11 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
 
 cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
     static const cudaError_t attr = [] {
-        const void *ks[] = {(const void *)k_mix_sweep<true, kMixAny>,  (const void *)k_mix_sweep<true, kMixMid>,
-                            (const void *)k_mix_sweep<true, kMixHist>, (const void *)k_mix_sweep<true, kMixNorm>,
-                            (const void *)k_mix_sweep<false, kMixAny>, (const void *)k_mix_sweep<false, kMixMid>,
-                            (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixNorm>,
-                            (const void *)k_mix_sweep<true, kMixKeep>, (const void *)k_mix_sweep<false, kMixKeep>,
-                            (const void *)k_mix_first<true>,           (const void *)k_mix_first<false>};
+        const void *ks[] = {(const void *)k_mix_sweep<true, kMixAny>,   (const void *)k_mix_sweep<true, kMixMid>,
+                            (const void *)k_mix_sweep<true, kMixHist>,  (const void *)k_mix_sweep<true, kMixKeep>,
+                            (const void *)k_mix_sweep<false, kMixAny>,  (const void *)k_mix_sweep<false, kMixMid>,
+                            (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixKeep>,
+                            (const void *)k_mix_first<true>,            (const void *)k_mix_first<false>};
         for (const void *k : ks) {
             const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem);
             if (e != cudaSuccess) return e;
@@ -3147,13 +3148,12 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
         }
         if (next_full && !mm.has0) var = kMixMid;
         else if (!mm.has0 && mm.nN == 0 && gv.next && !mm.final_norm) var = kMixHist;
-        else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm) var = mm.keep ? kMixKeep : kMixNorm;
+        else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm && mm.keep) var = kMixKeep;
     }
 #define QN_MIX(T, V) launch_pdl_smem(k_mix_sweep<T, V>, grid, block, kMixSmem, s, v, gv, mm)
     switch (var) {
     case kMixMid: return mm.tanf ? QN_MIX(true, kMixMid) : QN_MIX(false, kMixMid);
     case kMixHist: return mm.tanf ? QN_MIX(true, kMixHist) : QN_MIX(false, kMixHist);
-    case kMixNorm: return mm.tanf ? QN_MIX(true, kMixNorm) : QN_MIX(false, kMixNorm);
     case kMixKeep: return mm.tanf ? QN_MIX(true, kMixKeep) : QN_MIX(false, kMixKeep);
     default: return mm.tanf ? QN_MIX(true, kMixAny) : QN_MIX(false, kMixAny);
     }
