@@ -23,6 +23,8 @@
 // coalesced 16-byte access; each amplitude is read once and written once.
 #include "qn_internal.h"
 
+#include <array>
+
 namespace qn {
 namespace {
 
@@ -2891,14 +2893,13 @@ cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const N
 int64_t accumulate_xblocks(int n) { return tiles_for(n); }
 
 static int persistent_blocks() {
-    static int blocks = 0;
-    if (!blocks) {
+    static const int blocks = [] {  // initialised once, safely under concurrent first calls
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fork_copy, kThreads, 0);
-        blocks = (sms > 0 ? sms : 152) * (per > 0 ? per : 4);
-    }
+        return (sms > 0 ? sms : 152) * (per > 0 ? per : 4);
+    }();
     return blocks;
 }
 
@@ -2962,17 +2963,20 @@ cudaError_t launch_observe(const BatchView &v, const AccumView &, cudaStream_t s
 int probs_parts(int n, int b, int kind) {
     // blocks per state: k_probs covers 2048 amplitudes per block, k_probs_mix 2048 (half a mixer tile)
     const int64_t xb = kind == 2 ? std::max<int64_t>(2, (int64_t)1 << std::max(0, n - 11)) : accumulate_xblocks(n);
-    static int resident[3] = {0, 0, 0};
-    int &res = resident[kind];
-    if (res == 0) {
-        int dev = 0, sms = 0, occ = 0;
+    // resident blocks of each pass, initialised once (safely under concurrent first calls)
+    static const std::array<int, 3> resident = [] {
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs<false>, kThreads, 0);
-        else if (kind == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs<true>, kThreads, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probs_mix<true>, kMixThreads, 0);
-        res = std::max(sms, 1) * std::max(occ, 1);
-    }
+        int occ[3] = {0, 0, 0};
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_probs<false>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_probs<true>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_probs_mix<true>, kMixThreads, 0);
+        std::array<int, 3> r{};
+        for (int k = 0; k < 3; ++k) r[k] = std::max(sms, 1) * std::max(occ[k], 1);
+        return r;
+    }();
+    const int res = resident[kind < 0 ? 0 : kind > 2 ? 2 : kind];
     // Every block of a row streams all of the row's states, so the launch takes about
     // ceil(xb P / resident) rounds of b / P states each: take the P with the fewest
     // state-rounds (the smaller on a tie).  A row keeps at least one chunk of states,
