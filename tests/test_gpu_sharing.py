@@ -88,6 +88,34 @@ def test_sharing_in_chunks_and_with_offset(qn):
     np.testing.assert_allclose(pa, pb, atol=1e-12)
 
 
+def test_bench_mode_full_size_sample_against_oracle(qn):
+    """The bench's mode (shared prefixes, phase groups, 4-qubit mixer blocks; the last
+    block swept for its norms only and applied again by the sigma pass) on the 20-qubit
+    p=3 damping circuit, for a sample of 48 trajectories (global ids 2000..2047) that the
+    oracle evolves one by one: the ensemble <C>, sigma and the number of distinct states."""
+    w = W.damping_n20()
+    K, t0 = 48, 2000
+    with qn.Batch(w.n, K, w.seed) as b:
+        b.set_sharing(True)
+        b.set_fusion(True)
+        b.set_offset(t0)
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        mean, _ = b.expectation()
+        probs = b.probs()
+        info = b.run_info()
+        br = b.traj_debug(0, K, amps=False, c=False)["branches"]
+    assert info["states"] == len({bytes(r) for r in br})
+    assert abs(probs.sum() - 1) < 1e-12 and np.all(probs >= 0)
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    ref = oracle.traj_run(w.n, w.edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, t0, K,
+                          want_amps=False)
+    np.testing.assert_array_equal(br & 15, ref["branches"] & 15)  # Pauli codes: bit-exact
+    # damping branches may differ only where u lies within FP32 reach of p1 (counted)
+    assert np.any(br != ref["branches"], axis=1).sum() <= 1
+    assert abs(mean - ref["s1"] / K) < 8 * U32 * G * len(w.edges)
+    assert oracle.error(probs, ref["probs_sum"] / K) < 1e-9
+
+
 def test_sharing_full_size_damping_n20(qn):
     """The 20-qubit p=3 damping workload (K=4096) in shared-prefix mode against
     the default mode."""
