@@ -1374,6 +1374,11 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         for (int j = 0; j < kMixE; ++j) {
             const int d = j & dmask;
             const float f0 = has0 ? Df[d << 1] : Df[d], f1 = has0 ? Df[(d << 1) | 1] : Df[d];
+            if (VAR == kMixKeep) {  // nothing stored: |f x|^2 as the sigma pass forms it
+                df_add(nh, nl, prob_of(f0, x[j].x, x[j].y));
+                df_add(nh, nl, prob_of(f1, x[j].z, x[j].w));
+                continue;
+            }
             x[j].x *= f0;
             x[j].y *= f0;
             x[j].z *= f1;
@@ -1635,16 +1640,6 @@ __device__ int block_select(int cnt, Pred pred, Out out) {
         run = total;
     }
     return run;
-}
-
-__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int len, int x) {
-    int lo = 0, hi = len;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
 }
 
 // X and Z parts of a gate's Pauli on its (one or two) qubits.
@@ -1926,44 +1921,46 @@ __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView s
     }
     __syncthreads();
     // classes: the shared path (if any member kept it), then one per distinct
-    // outcome string in order of its first event
-    const int nlead = block_select(ne, [&](int a) { return rep[a] == a; }, [&](int r, int a) { lead[r] = a; });
+    // outcome string in order of its first event; the rank of each leader goes to
+    // lstart[leader] for the moment, and rep[a] becomes the class rank of event a
+    const int nlead = block_select(ne, [&](int a) { return rep[a] == a; }, [&](int r, int a) {
+        lead[r] = a;
+        lstart[a] = r;
+    });
+    for (int a = threadIdx.x; a < ne; a += kThreads) rep[a] = lstart[rep[a]];
     const int mainc = cnt - ne;
     const int hasmain = mainc > 0 ? 1 : 0;
     const int nc = hasmain + nlead;
+    __syncthreads();
     // members per class (integer counts, in any order), then the classes' starts
     for (int r = threadIdx.x; r < nlead; r += kThreads) {
         lcount[r] = 0;
         run[r] = 0;
     }
     __syncthreads();
-    for (int a = threadIdx.x; a < ne; a += kThreads) atomicAdd(&lcount[lower_bound_i32(lead, nlead, rep[a])], 1);
+    for (int a = threadIdx.x; a < ne; a += kThreads) atomicAdd(&lcount[rep[a]], 1);
     __syncthreads();
     block_scan_excl(nlead, lcount, lstart, mainc);
     if (threadIdx.x == 0) child_base = nc > 1 ? atomicAdd(sv.slot_count, nc - 1) : 0;
     __syncthreads();
     if (nc > 1) {  // stable partition of the members by class into tmp[off ..]
-        for (int i = threadIdx.x; i < cnt; i += kThreads) {
-            const int lb = lower_bound_i32(evt, ne, i);
-            if (lb < ne && evt[lb] == i) continue;
-            sv.tmp[off + i - lb] = mem[i];
-        }
+        // the shared path's members, in member order, at the front
+        block_select(cnt, [&](int i) { return key_zero(key[i]); }, [&](int r, int i) { sv.tmp[off + r] = mem[i]; });
         // events in order, a chunk of kThreads at a time: an event's place in its class is
         // the class's events in earlier chunks (run) plus those before it in its chunk
         __shared__ int srep[kThreads];
         for (int a0 = 0; a0 < ne; a0 += kThreads) {
             const int a = a0 + (int)threadIdx.x;
-            const int ra = a < ne ? rep[a] : -1;
-            srep[threadIdx.x] = ra;
+            const int r = a < ne ? rep[a] : -1;
+            srep[threadIdx.x] = r;
             __syncthreads();
             if (a < ne) {
                 int pos = 0;
-                for (int b = 0; b < (int)threadIdx.x; ++b) pos += srep[b] == ra;
-                const int r = lower_bound_i32(lead, nlead, ra);
+                for (int b = 0; b < (int)threadIdx.x; ++b) pos += srep[b] == r;
                 sv.tmp[off + lstart[r] + run[r] + pos] = mem[evt[a]];
             }
             __syncthreads();
-            if (a < ne) atomicAdd(&run[lower_bound_i32(lead, nlead, ra)], 1);
+            if (a < ne) atomicAdd(&run[r], 1);
             __syncthreads();
         }
         for (int i = threadIdx.x; i < cnt; i += kThreads) sv.members[off + i] = sv.tmp[off + i];
@@ -2361,9 +2358,10 @@ __global__ void k_probs_combine(double *probs, const double *spart, int parts, i
 // The sigma pass when the circuit ends on a full mixer block off qubit 0 whose
 // sweep (kMixKeep) formed only the final norms and left every state as it was
 // before the block.  The pass applies the block to each state on the fly --
-// the same rotations, then the same drawn factors, in the same order as
-// k_mix_sweep -- so each probability is bit-identical to the ones the norms
-// summed, and the final states are never written.  A slot forked at the block
+// the same rotations in the same order as k_mix_sweep, then |f x|^2 with the
+// drawn factor f formed as that sweep forms it -- so each probability is
+// bit-identical to the ones the norms summed, and the final states are never
+// written.  A slot forked at the block
 // reads its parent's state.  Grid (half tiles of the block's map, row blocks) x
 // kMixThreads: two lanes (lane bit 4 = the block's fourth qubit) share a fiber
 // of 16 float4 along the block's qubits, 8 each (the first three qubits on the
@@ -2475,12 +2473,8 @@ __global__ void __launch_bounds__(kMixThreads) k_probs_mix(BatchView v, AccumVie
             float cp = 0.0f;
 #pragma unroll
             for (int j = 0; j < kR; ++j) {
-                const float f = c_df[ci][j ^ fd];
-                x[j].x *= f;
-                x[j].y *= f;
-                x[j].z *= f;
-                x[j].w *= f;
-                const float pa = prob_of(1.0f, x[j].x, x[j].y), pb = prob_of(1.0f, x[j].z, x[j].w);
+                const float f = c_df[ci][j ^ fd];  // |f x|^2 as the kMixKeep sweep forms it
+                const float pa = prob_of(f, x[j].x, x[j].y), pb = prob_of(f, x[j].z, x[j].w);
                 const float p0 = (Ff & 1u) ? pb : pa, p1 = (Ff & 1u) ? pa : pb;  // true qubit 0
                 df_add_prod(ah[2 * j], al[2 * j], p0, ih, il);
                 df_add_prod(ah[2 * j + 1], al[2 * j + 1], p1, ih, il);
