@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <set>
 #include <string>
 #include <utility>
@@ -72,9 +73,54 @@ constexpr int kMaxQubits = 30;
 constexpr int64_t kMaxGates = 1 << 20;
 constexpr size_t kDefaultBatchBytes = (size_t)512 << 20;
 
+// Page-locked host words into which shared-prefix runs read the live-slot count
+// after each group (a copy into pageable memory returns only after a staged copy
+// and wakes the host later).  One pool per process, allocated on first use and
+// never freed -- cudaFreeHost would synchronise the device and stall other
+// handles' streams; a handle takes one word and gives it back when destroyed.
+// nullptr when the pool is spent or cannot be allocated (callers then use a
+// pageable word).
+constexpr int kPinnedWords = 4096;
+struct PinnedWords {
+    std::mutex mu;
+    int32_t *base = nullptr;
+    std::vector<int> free_list;
+    bool tried = false;
+};
+PinnedWords &pinned_words() {
+    static PinnedWords pool;
+    return pool;
+}
+int32_t *pinned_word_take() {
+    PinnedWords &p = pinned_words();
+    std::lock_guard<std::mutex> lock(p.mu);
+    if (!p.tried) {
+        p.tried = true;
+        void *ptr = nullptr;
+        if (cudaHostAlloc(&ptr, kPinnedWords * sizeof(int32_t), cudaHostAllocPortable) == cudaSuccess) {
+            p.base = static_cast<int32_t *>(ptr);
+            for (int i = kPinnedWords - 1; i >= 0; --i) p.free_list.push_back(i);
+        } else {
+            cudaGetLastError();  // clear the error it left; callers fall back to pageable words
+        }
+    }
+    if (!p.base || p.free_list.empty()) return nullptr;
+    const int i = p.free_list.back();
+    p.free_list.pop_back();
+    return p.base + i;
+}
+void pinned_word_give(int32_t *w) {
+    if (!w) return;
+    PinnedWords &p = pinned_words();
+    std::lock_guard<std::mutex> lock(p.mu);
+    p.free_list.push_back((int)(w - p.base));
+}
+
 }  // namespace
 
 struct qn_batch {
+    int32_t *pinned_word = nullptr;  // page-locked word for the live-slot count (or nullptr)
+    bool pinned_tried = false;
     int32_t n = 0;
     int64_t K = 0;
     uint64_t seed = 0;
@@ -850,10 +896,15 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     QN_CUDA(launch_init(vs, h->stream));
     QN_TRY(prof_end(h, &ep));
     h->launches += 1;
-    // pageable host word: a pinned one would need cudaFreeHost, which synchronises
-    // the whole device and would stall other handles' streams
+    // the live-slot count is read into the handle's page-locked word (from a pool that
+    // is never freed: cudaFreeHost would synchronise the device), else a pageable one
+    if (!h->pinned_tried) {
+        h->pinned_tried = true;
+        h->pinned_word = pinned_word_take();
+    }
     int32_t active_word = ns;
-    int32_t *active_host = &active_word;
+    int32_t *active_host = h->pinned_word ? h->pinned_word : &active_word;
+    *active_host = ns;
     int active = ns;
     bool final_norms = false;  // the last sweep formed 1 / ||psi||^2 of every state
     // the last sweep kept the states (a full mixer block off qubit 0): the sigma pass applies it
@@ -1443,6 +1494,7 @@ const char *qn_last_error(void) { return g_last_error.c_str(); }
 void qn_batch_destroy(qn_batch *h) {
     if (!h) return;
     release_all(h);
+    pinned_word_give(h->pinned_word);
     for (EventPair &ep : h->events) {
         cudaEventDestroy(ep.a);
         cudaEventDestroy(ep.b);
