@@ -14,7 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <map>
+#include <unordered_map>
 #include <mutex>
 #include <set>
 #include <string>
@@ -835,10 +835,27 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                               sizeof(uint32_t), kc, cudaMemcpyDeviceToHost, h->stream));
     QN_CUDA(cudaMemcpyAsync(hf.data(), h->hfac, hf.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     QN_CUDA(cudaStreamSynchronize(h->stream));
-    std::map<std::string, int> key_slot;
+    // key: the n outcome bytes (n <= 30) packed into four words; groups in order of first occurrence
+    struct HKey {
+        uint64_t w[4];
+        bool operator==(const HKey &o) const {
+            return w[0] == o.w[0] && w[1] == o.w[1] && w[2] == o.w[2] && w[3] == o.w[3];
+        }
+    };
+    struct HKeyHash {
+        size_t operator()(const HKey &k) const {
+            uint64_t x = 0;
+            for (int i = 0; i < 4; ++i) x = (x ^ k.w[i]) * 0x9E3779B97F4A7C15ull;
+            return (size_t)(x ^ (x >> 29));
+        }
+    };
+    static_assert(kMaxQubits <= 32, "the H-layer key holds 32 bytes");
+    std::unordered_map<HKey, int, HKeyHash> key_slot;
+    key_slot.reserve((size_t)std::min(kc, 1 << 16));
     std::vector<std::vector<int32_t>> groups;
     for (int t = 0; t < kc; ++t) {
-        std::string key(reinterpret_cast<const char *>(&hbr[(size_t)t * n]), (size_t)n);
+        HKey key{{0, 0, 0, 0}};
+        std::memcpy(key.w, &hbr[(size_t)t * n], (size_t)n);
         auto it = key_slot.find(key);
         if (it == key_slot.end()) {
             key_slot.emplace(key, (int)groups.size());
