@@ -88,6 +88,34 @@ def test_sharing_in_chunks_and_with_offset(qn):
     np.testing.assert_allclose(pa, pb, atol=1e-12)
 
 
+@pytest.mark.parametrize("n,K,noise", [
+    (12, 1, dict(p1=1e-2, p2=3e-2, damping=0.05)),   # one state through every group
+    (12, 2, dict(p1=0.2, p2=0.4, damping=0.1)),      # forks at nearly every group, the last block too
+    (16, 5, dict(p1=5e-3, p2=2e-2, damping=0.02)),   # more tile bits, a ragged chunk of states
+])
+def test_grouped_mode_tiny_ensembles(qn, n, K, noise):
+    """Shared prefixes with phase groups and mixer blocks on a handful of trajectories:
+    the last block swept for its norms only and applied again by the sigma pass, with
+    one state, forks at the last block, and short chunks."""
+    w = W.qaoa_workload(f"tiny_n{n}_K{K}", n, 1, index=50 + K, trajectories=K, batch=K, **noise)
+    with qn.Batch(w.n, K, w.seed) as b:
+        b.set_sharing(True)
+        b.set_fusion(True)
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        mean, _ = b.expectation()
+        probs = b.probs()
+        info = b.run_info()
+        br = b.traj_debug(0, K, amps=False, c=False)["branches"]
+    assert info["states"] == len({bytes(r) for r in br})
+    assert abs(probs.sum() - 1) < 1e-12 and np.all(probs >= 0)
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    ref = oracle.traj_run(w.n, w.edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, 0, K,
+                          want_amps=False)
+    assert np.any(br != ref["branches"], axis=1).sum() == 0
+    assert abs(mean - ref["s1"] / K) < 8 * U32 * G * len(w.edges)
+    assert oracle.error(probs, ref["probs_sum"] / K) < 1e-9
+
+
 def test_bench_mode_full_size_sample_against_oracle(qn):
     """The bench's mode (shared prefixes, phase groups, 4-qubit mixer blocks; the last
     block swept for its norms only and applied again by the sigma pass) on the 20-qubit
