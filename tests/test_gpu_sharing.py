@@ -116,6 +116,31 @@ def test_grouped_mode_tiny_ensembles(qn, n, K, noise):
     assert oracle.error(probs, ref["probs_sum"] / K) < 1e-9
 
 
+@pytest.mark.parametrize("n", [26, 28])
+def test_grouped_mode_large_n_against_per_gate_sweeps(qn, n):
+    """Large states (512 MiB and 2 GiB; n=26 ends on a partial mixer block whose sweep
+    stores the states, n=28 on a full one swept for its norms only): the grouped mode
+    against one sweep per gate in shared-prefix mode (itself checked against the oracle
+    at smaller n) on the same draws -- the same distinct states, <C> within the FP32
+    bound, sigma to FP32 state rounding, and sum(sigma) = 1 to FP64 rounding."""
+    w = W.qaoa_workload(f"grouped_n{n}", n, 1, index=60, trajectories=6, batch=6, p1=5e-3, p2=3e-2, damping=0.03)
+    out = {}
+    for fusion in (False, True):
+        with qn.Batch(w.n, w.trajectories, w.seed) as b:
+            b.set_sharing(True)
+            b.set_fusion(fusion)
+            b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+            out[fusion] = (b.expectation()[0], b.probs(), b.run_info())
+    (m1, p1, i1), (m2, p2, i2) = out[False], out[True]
+    assert i1["states"] == i2["states"]
+    assert i2["sweep_bytes"] < 0.5 * i1["sweep_bytes"]
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    assert abs(m2 - m1) < 8 * U32 * G * len(w.edges)
+    assert abs(p1.sum() - 1) < 1e-12 and abs(p2.sum() - 1) < 1e-12
+    assert np.abs(p2 - p1).max() < 1e-6
+    assert oracle.error(p2, p1) < 1e-9
+
+
 def test_bench_mode_full_size_sample_against_oracle(qn):
     """The bench's mode (shared prefixes, phase groups, 4-qubit mixer blocks; the last
     block swept for its norms only and applied again by the sigma pass) on the 20-qubit
