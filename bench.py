@@ -311,6 +311,8 @@ def gpu_arm(args):
     _, main_mode, other_mode = WORKLOADS[args.workload]
     if not args.sharing:
         main_mode = (False, main_mode[1])
+    if not args.fusion:
+        main_mode = (main_mode[0], False)
     sharing = main_mode[0] and w.damping > 0
     main = measure(qn, w, args, main_mode, stream, rank, world, local, pg, with_e2e=True)
     other = None
@@ -446,7 +448,7 @@ def serving_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(sharing=False, depth=1):
+def profile_case(sharing=False, depth=1, fusion=True):
     """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state);
     depth 2 adds a layer, so the last mixer block of the first one forms the next layer's joint."""
     from paper_2210_15874_gb300 import build
@@ -462,6 +464,7 @@ def profile_case(sharing=False, depth=1):
         w = W.qaoa_workload(f"ncu_n20_p{depth}_damp", 20, depth, index=1, trajectories=32, batch=32, damping=5e-3)
     with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
         b.set_sharing(sharing)
+        b.set_fusion(fusion)
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
         print(json.dumps({"case": w.name, "c": b.expectation(), "states": b.run_info()["states"]}))
 
@@ -489,6 +492,9 @@ def main():
     ap.add_argument("--sharing", type=int, default=1, choices=[0, 1],
                     help="1: shared-prefix mode (trajectories share common Kraus prefixes); "
                          "0: every trajectory evolved separately, 64 per launch")
+    ap.add_argument("--fusion", type=int, default=1, choices=[0, 1],
+                    help="1: fused sweeps (phase groups and mixer blocks with damping, fused layers without); "
+                         "0: one sweep per gate")
     ap.add_argument("--single-mode", action="store_true",
                     help="time only the selected mode (skip the per-trajectory comparison run)")
     ap.add_argument("--profile-case", action="store_true",
@@ -497,7 +503,7 @@ def main():
     ap.add_argument("--profile-depth", type=int, default=1, choices=[1, 2], help="QAOA depth of --profile-case")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(bool(args.sharing), args.profile_depth)
+        profile_case(bool(args.sharing), args.profile_depth, bool(args.fusion))
         return
     if args.workload == "serving":
         serving_arm(args)
