@@ -288,6 +288,42 @@ def test_noiseless_p1_closed_form(graph):
             assert abs(expect - n * (0.5 + 0.25 * np.sin(4 * beta) * np.sin(2 * gamma))) < 1e-12
 
 
+@pytest.mark.parametrize("graph", ["ring7", "reg3_n8", "reg3_n10"])
+def test_noiseless_multilayer_reduces_to_p1_closed_form(graph):
+    """P2 for p >= 2, pinning the oracle's layer loop (which angle goes to which
+    layer, and the order of the cost and mixer halves within a layer).
+
+    A layer with beta = 0 has the identity mixer, and U_C(gamma) commutes with
+    C and with every other U_C.  So, noiseless:
+      (gamma1, 0), (gamma2, beta2)              -> Wang p=1 at (gamma1 + gamma2, beta2)
+      (gamma2, beta2), (gamma1, 0)              -> Wang p=1 at (gamma2, beta2)
+      (gamma1, 0), (gamma2, 0), (gamma3, beta3) -> Wang p=1 at (gamma1 + gamma2 + gamma3, beta3)
+    A loop that reused layer 0's angles, swapped gamma and beta, or ran the mixer
+    before the cost layer gives other values (checked to differ by > 1e-3 here)."""
+    if graph.startswith("ring"):
+        n = int(graph[4:])
+        edges = workloads.ring_graph(n)
+    else:
+        n = int(graph.split("n")[-1])
+        edges = workloads.regular_graph(n, 3, 29 + n)
+    nz = oracle.make_noise()
+    g1, g2, g3, b2, b3 = 0.37, 1.21, 0.58, 2.47, 0.83
+    cases = [([g1, g2], [0.0, b2], wang_p1(n, edges, g1 + g2, b2)),
+             ([g2, g1], [b2, 0.0], wang_p1(n, edges, g2, b2)),
+             ([g1, g2, g3], [0.0, 0.0, b3], wang_p1(n, edges, g1 + g2 + g3, b3))]
+    # the plausible layer-loop mistakes land elsewhere
+    assert abs(cases[0][2] - wang_p1(n, edges, 2 * g1, b2)) > 1e-3      # gammas[0] reused
+    assert abs(cases[0][2] - wang_p1(n, edges, g2, b2)) > 1e-3          # first layer dropped
+    assert abs(cases[0][2] - cases[1][2]) > 1e-3                        # layers swapped
+    for gammas, betas, expect in cases:
+        gates, G = oracle.qaoa_gates(n, edges, gammas, betas)
+        assert G == n + len(gammas) * (len(edges) + n)
+        dm = oracle.dm_run(n, edges, gates, G, nz)
+        tr = oracle.traj_run(n, edges, gates, G, nz, 5, 0, 1)
+        assert abs(dm["c"] - expect) < 1e-12, (gammas, betas)
+        assert abs(tr["c_traj"][0] - expect) < 1e-12, (gammas, betas)
+
+
 def test_noiseless_dm_is_pure_trajectory():
     """P6: with p = gamma = 0, rho = |psi><psi| for the (single, deterministic) trajectory."""
     n = 5
