@@ -285,6 +285,28 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
     return res
 
 
+def precision_leg(qn, args, stream, local, roof_of):
+    """The precision workload (n=26, p=4, depolarizing only, 64 trajectories of 512 MiB):
+    fused layers (ceil(n/3) sweeps per layer) against one sweep per gate on the same
+    trajectories -- throughput, the sweeps' HBM fraction, and the two forms' <C> beside
+    the ensemble's statistical error (the comparison "at equal <C> error")."""
+    w = W.precision_n26()
+    legs = {}
+    sub = argparse.Namespace(steps=max(2, min(args.steps, 3)), warmup=3)
+    for name, mode in (("fused", (False, True)), ("per_gate", (False, False))):
+        res = measure(qn, w, sub, mode, stream, 0, 1, local, None, with_e2e=False)
+        kname = "k_fused_sweep (fused layer sweeps)" if mode[1] else "k_sweep_zz / k_sweep_rx (gate sweeps)"
+        r = roof_of(res, kname, "sweeps")
+        legs[name] = {"value": res["value"], "unit": UNIT, "ms_per_step": res["ms"] / sub.steps,
+                      "c_mean": res["mean"], "c_stderr": res["se"], "sweep_bytes_per_step": res["sweep_bytes_per_step"],
+                      "roofline": {k: r[k] for k in ("kernel", "achieved", "peak", "unit", "frac", "avg_launch_ms")},
+                      "clocks": res["clocks"]}
+    legs["speedup_fused_over_per_gate"] = legs["fused"]["value"] / legs["per_gate"]["value"]
+    legs["c_difference"] = abs(legs["fused"]["c_mean"] - legs["per_gate"]["c_mean"])
+    legs["config"] = config_of(w, {"steps": sub.steps, "warmup": sub.warmup})
+    return legs
+
+
 def gpu_arm(args):
     import torch
 
@@ -396,23 +418,22 @@ def gpu_arm(args):
                 "roofline": roof(other, "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")}
         if world == 1 and not args.no_cpu_baseline and w.n <= 20:
             line["cpu_baseline"] = cpu_baseline(w)
+        if world == 1 and args.workload == "damping20" and not args.no_legs:
+            line["precision26"] = precision_leg(qn, args, stream, local, roof_of=roof)
+            line["serving"] = serving_levels(args.requests, args.inflight, local)
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
 
 
-def serving_arm(args):
-    """Serving workload: closed-loop capacity, then Poisson arrivals at 0.5x and 0.8x of it."""
-    import torch
-
-    from paper_2210_15874_gb300 import build
-    build.build()
+def serving_levels(requests: int, inflight: int, clock_index: int = 0):
+    """Serving workload: closed-loop capacity, then Poisson arrivals at 0.5x and 0.8x of
+    it; per level the request count, span, throughput and p50/p99 latency."""
     from paper_2210_15874_gb300 import serving
 
-    torch.cuda.set_device(0)
-    reqs = serving.serving_mix(args.requests)
+    reqs = serving.serving_mix(requests)
     warm = serving.serving_mix(4, seed=99)
-    srv = serving.Server(max_inflight=args.inflight)
+    srv = serving.Server(max_inflight=inflight)
     for f in [srv.submit(r) for r in warm]:
         f.result()
 
@@ -432,20 +453,33 @@ def serving_arm(args):
                 "trajectories_per_s": traj / span, "p50_latency_s": serving.percentile(lat, 50),
                 "p99_latency_s": serving.percentile(lat, 99), "mean_latency_s": float(np.mean(lat))}
 
-    with ClockSampler(0) as clocks:
+    with ClockSampler(clock_index) as clocks:
         cap = run(0)
         half = run(0.5 * cap["requests_per_s"])
         high = run(0.8 * cap["requests_per_s"])
     srv.close()
+    cfg = {"workload": "serving: n ~ U{10..24}, p ~ U{1..6}, K ~ log-uniform[256, 8192], depolarizing "
+                       "1e-3/1e-2 + damping 5e-3, seeded regular graphs",
+           "requests": requests, "max_inflight": inflight,
+           "admission": "HBM footprint (launch batch of statevectors + tables) within 60% of free memory",
+           "mode": "shared-prefix mode per request, one CUDA stream per in-flight request"}
+    return {"capacity": cap, "load_0.5": half, "load_0.8": high, "clocks": clocks.summary(), "config": cfg}
+
+
+def serving_arm(args):
+    """--workload serving: the serving levels as their own JSON line."""
+    import torch
+
+    from paper_2210_15874_gb300 import build
+    build.build()
+
+    torch.cuda.set_device(0)
+    sv = serving_levels(args.requests, args.inflight)
     line = {"metric": "noisy trajectories/s and p50/p99 request latency under Poisson load", "value":
-            high["trajectories_per_s"], "unit": "trajectories/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving: n ~ U{10..24}, p ~ U{1..6}, K ~ log-uniform[256, 8192], depolarizing "
-                                   "1e-3/1e-2 + damping 5e-3, seeded regular graphs",
-                       "requests": args.requests, "max_inflight": args.inflight,
-                       "admission": "HBM footprint (launch batch of statevectors + tables) within 60% of free memory",
-                       "mode": "shared-prefix mode per request, one CUDA stream per in-flight request"},
-            "capacity": cap, "load_0.5": half, "load_0.8": high, "clocks": clocks.summary()}
+            sv["load_0.8"]["trajectories_per_s"], "unit": "trajectories/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", "config": sv["config"],
+            "capacity": sv["capacity"], "load_0.5": sv["load_0.5"], "load_0.8": sv["load_0.8"],
+            "clocks": sv["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -496,6 +530,8 @@ def main():
     ap.add_argument("--fusion", type=int, default=1, choices=[0, 1],
                     help="1: fused sweeps (phase groups and mixer blocks with damping, fused layers without); "
                          "0: one sweep per gate")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the precision (n=26) and serving legs of the default line")
     ap.add_argument("--single-mode", action="store_true",
                     help="time only the selected mode (skip the per-trajectory comparison run)")
     ap.add_argument("--profile-case", action="store_true",

@@ -183,6 +183,29 @@ qn_status qn_grad_traj(qn_batch *h, int64_t t0, int64_t count, double *dgamma, d
 qn_status qn_traj_debug(qn_batch *h, int64_t t0, int64_t count, float *amps, uint8_t *branches,
                         double *c_per_traj);
 
+/* The per-trajectory results of the last run in shared-prefix mode, read from
+ * the states and draws that run itself made (Sec. "Stochastic Noise
+ * Implementation": each member's Kraus string and its phi = |psi|^2) -- no
+ * re-simulation, unlike qn_traj_debug.  Trajectories t0..t0+count-1 (0-based
+ * within the handle) must lie in the run's last prefix tree (with the default
+ * launch batch, the whole ensemble).  Into caller-owned host buffers (any may
+ * be NULL), laid out as for qn_traj_debug:
+ *   amps        count * 2^n * 2 floats: the final normalised state of each
+ *               trajectory's slot, in the true basis with the trajectory's
+ *               global phase; when the circuit's last mixer block was left
+ *               pending (its sweep formed only the norms and the sigma pass
+ *               applied it), the block is applied here to the slot's state (a
+ *               slot forked at the block: its parent's) with the drawn factors;
+ *   branches    count * G bytes: the Kraus string the run drew for each
+ *               trajectory (Pauli code in bits 0..3, damping jumps in bits 4, 5);
+ *               with phase groups and mixer blocks, the group decide's draws;
+ *   c_per_traj  count doubles: <C>_t as the sigma pass formed it.
+ * QN_ESTATE when the last run did not evolve shared prefixes, or when
+ * qn_traj_debug, qn_grad or qn_grad_traj has run since (they reuse its
+ * buffers); QN_EINVAL for a range outside the last prefix tree.  Blocks. */
+qn_status qn_shared_readout(qn_batch *h, int64_t t0, int64_t count, float *amps, uint8_t *branches,
+                            double *c_per_traj);
+
 /* Error = 1 - (sum_x sqrt(sa_x se_x))^2 (Sec. "Stochastic Noise Implementation",
  * Eq. 1): fidelity distance between two host probability vectors of length
  * len.  Host-only; any negative entry gives QN_EINVAL. */
@@ -254,10 +277,13 @@ qn_status qn_profile_read(qn_batch *h, int32_t kind, int64_t *launches, double *
  *              batch (divide by count for sigma_approx)
  *   cuda_stream  cudaStream_t to queue on (NULL = legacy default stream)
  * Results equal those of a handle with the same seed.  Returns QN_EINVAL when
- * the batch needs more scratch than the 8 MiB array (lower count or n).  The
- * first call on each device looks up the array's device address; make it
- * before any stream capture.  Calls share the array: calls that overlap on the
- * GPU race.  Blocks until the batch is done. */
+ * the batch needs more scratch than the 8 MiB array (lower count or n), and,
+ * before anything is queued, when psi, c_out or probs_out is not device (or
+ * managed) memory of the current device or the stream belongs to another
+ * device.  The first call on each device looks up the array's device address
+ * (again after the device's context was recreated); make it before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race.  Blocks
+ * until the batch is done. */
 qn_status qn_run_qaoa_noalloc(int32_t n, const qn_graph *graph, int32_t p, const double *gammas,
                               const double *betas, const qn_noise *noise, uint64_t seed,
                               int64_t first_trajectory, int32_t count, void *psi, double *c_out,

@@ -191,6 +191,17 @@ struct qn_batch {
     double *sh_marg = nullptr;
     int64_t sh_cap = 0;
     int64_t sh_slots = 0;  // slots of the last shared-prefix run (all chunks)
+    // the last shared-prefix chunk as its run left it, for qn_shared_readout
+    bool sh_valid = false;
+    int64_t sh_last_t0 = 0;  // handle-local id of the chunk's first trajectory
+    int32_t sh_last_kc = 0;  // trajectories in the chunk
+    std::vector<int2> sh_range_host;       // [slots] member range of each final slot
+    std::vector<int32_t> sh_members_host;  // [kc] batch-local trajectories grouped by slot
+    std::vector<int32_t> sh_order_host;    // [slots] slot of each position of the sigma pass
+    ReadTail sh_tail{};                    // the pending last mixer block, if its sweep kept the states
+    float2 *sh_readbuf = nullptr;          // readout chunk of final states
+    int32_t *sh_readidx = nullptr;         // [2][chunk] slot and trajectory of each output
+    int64_t sh_readcap = 0;
     // phase-gate groups of shared-prefix mode with damping
     std::vector<GateGroup> groups;
     std::vector<int32_t> group_at;  // [G] index of the group that starts at gate g, or -1
@@ -267,6 +278,10 @@ void release_all(qn_batch *h) {
     h->sh_weights = nullptr;
     h->sh_marg = nullptr;
     h->sh_cap = 0;
+    h->sh_valid = false;
+    h->sh_readbuf = nullptr;
+    h->sh_readidx = nullptr;
+    h->sh_readcap = 0;
     h->gr_dev = nullptr;
     h->gr_cap = 0;
     h->gv_H = nullptr;
@@ -928,6 +943,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     bool keep = false;
     MixMap keep_mm;
     MixTail keep_tail{};
+    ReadTail read_tail{};
     const double amp_count = (double)((size_t)1 << n);
     for (int g = n; g < G; ++g) {
         const int gi = grouped ? h->group_at[g] : -1;
@@ -1002,6 +1018,14 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                     keep_tail.T = gv.T;
                     keep_tail.parent = gv.parent;
                     keep_tail.first_new = old_active;
+                    read_tail.keep = 1;
+                    read_tail.M = z.s;
+                    for (int k = 0; k < kMixQ; ++k) read_tail.q[k] = k < z.s ? z.sp[k] : 0;
+                    read_tail.c = z.c;
+                    read_tail.s = z.sn;
+                    read_tail.T = gv.T;
+                    read_tail.parent = gv.parent;
+                    read_tail.first_new = old_active;
                 }
             }
             // the slots forked here first, reading their parents' states; then
@@ -1082,6 +1106,13 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     h->launches += (final_norms ? 1 : 2) + (a.parts > 1 ? 1 : 0);
     h->sh_slots += nslots;
     QN_CUDA(cudaStreamSynchronize(h->stream));  // order / weights host vectors
+    h->sh_valid = true;
+    h->sh_last_t0 = t0;
+    h->sh_last_kc = kc;
+    h->sh_range_host = std::move(fr);
+    h->sh_members_host = std::move(fm);
+    h->sh_order_host = std::move(order);
+    h->sh_tail = read_tail;
     return QN_OK;
 }
 
@@ -1250,6 +1281,7 @@ qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const doubl
     h->launches = 0;
     h->sweep_bytes = 0.0;
     h->sh_slots = 0;
+    h->sh_valid = false;
     for (int64_t t0 = 0; t0 < h->K; t0 += B) {
         const int b = (int)std::min<int64_t>(B, h->K - t0);
         if (h->sharing && !use_fusion(h)) QN_TRY(run_shared(h, t0, b));
@@ -1299,6 +1331,7 @@ qn_status qn_traj_debug(qn_batch *h, int64_t t0, int64_t count, float *amps, uin
     if (amps && !h->readout) {
         QN_TRY(alloc_t(h, &h->readout, (size_t)h->cap_B << n));
     }
+    h->sh_valid = false;  // the re-simulation reuses the buffers a shared-prefix run left
     const int64_t saved_launches = h->launches;
     for (int64_t c0 = 0; c0 < count; c0 += h->cap_B) {
         const int b = (int)std::min<int64_t>(h->cap_B, count - c0);
@@ -1318,6 +1351,69 @@ qn_status qn_traj_debug(qn_batch *h, int64_t t0, int64_t count, float *amps, uin
         QN_CUDA(cudaStreamSynchronize(h->stream));
     }
     h->launches = saved_launches;
+    QN_TRY(check_status(h));
+    return ok();
+}
+
+qn_status qn_shared_readout(qn_batch *h, int64_t t0, int64_t count, float *amps, uint8_t *branches,
+                            double *c_per_traj) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (!h->has_run) return fail(QN_ESTATE, "no completed qn_run_qaoa on this handle");
+    if (!h->sh_valid) return fail(QN_ESTATE, "the last run did not evolve shared prefixes (sharing off, or Pauli-only "
+                                             "noise with fusion on)");
+    const int64_t lo = h->sh_last_t0, hi = h->sh_last_t0 + h->sh_last_kc;
+    if (count < 0 || t0 < lo || t0 + count > hi)
+        return fail(QN_EINVAL, "trajectories [%lld, %lld) outside the last prefix tree [%lld, %lld)", (long long)t0,
+                    (long long)(t0 + count), (long long)lo, (long long)hi);
+    const int n = h->n;
+    const int G = (int)h->gates.size();
+    const int kc = h->sh_last_kc;
+    const int nslots = (int)h->sh_range_host.size();
+    // final slot of every trajectory of the tree, and each slot's place in the sigma pass
+    std::vector<int32_t> slot_of((size_t)kc, -1), pos((size_t)nslots, -1);
+    for (int sl = 0; sl < nslots; ++sl) {
+        const int2 r = h->sh_range_host[sl];
+        for (int i = 0; i < r.y; ++i) slot_of[h->sh_members_host[(size_t)r.x + i]] = sl;
+    }
+    for (int i = 0; i < nslots; ++i) pos[h->sh_order_host[i]] = i;
+    const int64_t b0 = t0 - lo;  // batch-local id of the first output
+    for (int64_t i = 0; i < count; ++i)
+        if (slot_of[b0 + i] < 0) return fail(QN_ESTATE, "trajectory %lld has no final slot", (long long)(t0 + i));
+    if (branches && count > 0)
+        QN_CUDA(cudaMemcpyAsync(branches, h->branch + (size_t)b0 * G, (size_t)count * G, cudaMemcpyDeviceToHost,
+                                h->stream));
+    if (c_per_traj && count > 0) {
+        std::vector<double> cs((size_t)nslots);
+        QN_CUDA(cudaMemcpyAsync(cs.data(), h->c_dbg, (size_t)nslots * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream));
+        QN_CUDA(cudaStreamSynchronize(h->stream));
+        for (int64_t i = 0; i < count; ++i) c_per_traj[i] = cs[pos[slot_of[b0 + i]]];
+    }
+    if (amps && count > 0) {
+        const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(count, 64),
+                                                                     (int64_t)(kDefaultBatchBytes / state_bytes(n))));
+        if (h->sh_readcap < chunk) {
+            QN_TRY(alloc_t(h, &h->sh_readbuf, (size_t)chunk << n));
+            QN_TRY(alloc_t(h, &h->sh_readidx, (size_t)2 * chunk));
+            h->sh_readcap = chunk;
+        }
+        BatchView v = view_for(h, h->offset + lo, kc);
+        std::vector<int32_t> idx((size_t)2 * chunk);
+        for (int64_t c0 = 0; c0 < count; c0 += chunk) {
+            const int m = (int)std::min<int64_t>(chunk, count - c0);
+            for (int i = 0; i < m; ++i) {
+                idx[i] = slot_of[b0 + c0 + i];
+                idx[chunk + i] = (int32_t)(b0 + c0 + i);
+            }
+            QN_CUDA(cudaMemcpyAsync(h->sh_readidx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                    h->stream));
+            QN_CUDA(launch_slot_readout(v, h->sh_readidx, h->sh_readidx + chunk, m, h->sh_tail, h->sh_readbuf,
+                                        h->stream));
+            QN_CUDA(cudaMemcpyAsync(amps + ((size_t)c0 << n) * 2, h->sh_readbuf, ((size_t)m << n) * sizeof(float2),
+                                    cudaMemcpyDeviceToHost, h->stream));
+            QN_CUDA(cudaStreamSynchronize(h->stream));  // idx is reused
+        }
+    }
     QN_TRY(check_status(h));
     return ok();
 }
@@ -1352,6 +1448,7 @@ qn_status run_grad(qn_batch *h, int64_t t0, int64_t count) {
         h->grad_cap = np;
     }
     QN_CUDA(cudaMemsetAsync(h->grad + (size_t)t0 * np, 0, (size_t)count * np * sizeof(double), h->stream));
+    h->sh_valid = false;  // the re-simulation reuses the buffers a shared-prefix run left
     const int64_t saved_launches = h->launches;
     for (int64_t c0 = 0; c0 < count; c0 += h->cap_B) {
         const int b = (int)std::min<int64_t>(h->cap_B, count - c0);

@@ -241,6 +241,22 @@ cudaError_t launch_probs_mix(const BatchView &v, const AccumView &a, const MixMa
 int probs_parts(int n, int b, int kind);
 constexpr int kMaxProbParts = 16;
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
+// What the readout of a shared-prefix run needs about the circuit's last mixer
+// block when its sweep kept the states (MixMap::keep); keep = 0 otherwise.
+struct ReadTail {
+    int32_t keep;
+    int32_t M;             // qubits of the block
+    int32_t q[kMixQ];      // the block's qubits
+    float c, s;            // cos beta, sin beta of the block's layer
+    const float2 *T;       // [slots][kGroupBins] the block's drawn factors by stored bits
+    const int32_t *parent; // [slots] parent of each slot forked at the block
+    int32_t first_new;     // slots from this one on were forked at the block
+};
+// Final states of a shared-prefix run, one per output: out[o] = the normalised
+// state of slot oslot[o] in the true basis, with trajectory otraj[o]'s global
+// phase (device arrays of nout entries; out holds nout * 2^n amplitudes).
+cudaError_t launch_slot_readout(const BatchView &v, const int32_t *oslot, const int32_t *otraj, int nout,
+                                const ReadTail &rt, float2 *out, cudaStream_t s);
 // Fused layers (Pauli-only): per-trajectory layer parameters from the branch
 // tables, then sweeps applying the rotations of qubits [q_lo, q_lo + m) of
 // layer Lr, with layer Lp's phase before them (pre) and layer Lq's after (post).

@@ -2850,6 +2850,77 @@ __global__ void __launch_bounds__(kThreads) k_readout(BatchView v, float2 *out) 
     }
 }
 
+// Readout of the states a shared-prefix run evolved (debug path, no
+// re-simulation): output o is trajectory otraj[o] (batch-local) whose final
+// state is slot oslot[o].  psi_x = i^k * sqrt(1/N_s) * phi'_{x xor F}, where phi'
+// is the slot's stored state with its pending op applied, or -- when the
+// circuit's last mixer block was kept pending (its sweep formed only the norms)
+// -- that block applied here: phi'_y = f(y_S) * sum_a prod_i R(y_qi, a_i)
+// phi_src(y with the block's bits set to a), R = exp(-i beta X) entry by entry,
+// f the block's drawn factor by stored bits, src the parent of a slot forked at
+// the block.  Written plainly (one output amplitude per thread, FP32 terms
+// summed in FP64), independently of the sigma pass that applies the same block.
+__global__ void __launch_bounds__(kThreads) k_slot_readout(BatchView v, const int32_t *oslot, const int32_t *otraj,
+                                                           ReadTail rt, float2 *out) {
+    const int o = blockIdx.y;
+    const int sl = oslot[o], t = otraj[o];
+    const int n = v.n;
+    const int64_t dim = (int64_t)1 << n;
+    const TrajState s = v.st[sl];
+    const uint32_t Ff = v.frame_x[(size_t)sl * (v.G + 1) + v.G] ^ s.J ^ s.pend;
+    const int k = v.yphase[t];
+    const double sc = sqrt(v.inv_norm[sl]);
+    const bool keep = rt.keep != 0;
+    const int src = keep && sl >= rt.first_new ? rt.parent[sl] : sl;
+    const float2 *phi = v.psi + ((size_t)src << n);
+    for (int64_t x = (int64_t)blockIdx.x * kThreads + threadIdx.x; x < dim; x += (int64_t)gridDim.x * kThreads) {
+        const uint32_t y = (uint32_t)x ^ Ff;
+        double re = 0.0, im = 0.0;
+        if (keep) {
+            int yS = 0;
+            uint32_t ybase = y;
+            for (int i = 0; i < rt.M; ++i) {
+                yS |= (int)((y >> rt.q[i]) & 1u) << i;
+                ybase &= ~(1u << rt.q[i]);
+            }
+            for (int a = 0; a < (1 << rt.M); ++a) {
+                // prod_i R(y_i, a_i): cos beta where the bits agree, -i sin beta where they differ
+                double cr = 1.0, ci = 0.0;
+                uint32_t ya = ybase;
+                for (int i = 0; i < rt.M; ++i) {
+                    const int ai = (a >> i) & 1;
+                    ya |= (uint32_t)ai << rt.q[i];
+                    const bool same = ai == ((yS >> i) & 1);
+                    const double er = same ? (double)rt.c : 0.0, ei = same ? 0.0 : -(double)rt.s;
+                    const double nr = cr * er - ci * ei, ni = cr * ei + ci * er;
+                    cr = nr;
+                    ci = ni;
+                }
+                const float2 p = phi[ya];
+                re += cr * p.x - ci * p.y;
+                im += cr * p.y + ci * p.x;
+            }
+            const double f = rt.T[(size_t)sl * kGroupBins + yS].x;
+            re *= f;
+            im *= f;
+        } else {
+            const float2 p = phi[y];
+            const uint32_t tb = (uint32_t)x ^ s.pend;
+            const double f = s.f[((tb >> s.pq0) & 1u) | (((tb >> s.pq1) & 1u) << 1)];
+            re = f * p.x;
+            im = f * p.y;
+        }
+        re *= sc;
+        im *= sc;
+        float2 r;
+        if (k == 0) r = make_float2((float)re, (float)im);
+        else if (k == 1) r = make_float2((float)-im, (float)re);
+        else if (k == 2) r = make_float2((float)-re, (float)-im);
+        else r = make_float2((float)im, (float)-re);
+        out[((size_t)o << n) + x] = r;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_prepare(const BatchView &v, const DevGate *gates, uint64_t seed, const NoiseDev &nz,
@@ -3023,6 +3094,16 @@ cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s) {
     int64_t blocks = (dim + kThreads - 1) / kThreads;
     if (blocks > 4096) blocks = 4096;
     k_readout<<<dim3((unsigned)blocks, (unsigned)v.b), kThreads, 0, s>>>(v, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slot_readout(const BatchView &v, const int32_t *oslot, const int32_t *otraj, int nout,
+                                const ReadTail &rt, float2 *out, cudaStream_t s) {
+    if (nout <= 0) return cudaSuccess;
+    const int64_t dim = (int64_t)1 << v.n;
+    int64_t blocks = (dim + kThreads - 1) / kThreads;
+    if (blocks > 4096) blocks = 4096;
+    k_slot_readout<<<dim3((unsigned)blocks, (unsigned)nout), kThreads, 0, s>>>(v, oslot, otraj, rt, out);
     return cudaGetLastError();
 }
 

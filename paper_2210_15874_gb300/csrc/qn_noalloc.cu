@@ -14,9 +14,13 @@
 //
 // The array is kScratchBytes (8 MiB) per device, reserved on every GPU that
 // loads libqnoise.so until the process exits.  Its device address is looked up
-// with cudaGetSymbolAddress once per device, by the first call made with that
-// device current; that first call should come before any stream capture (the
-// lookup may load the module).  All calls share the one array and find the
+// with cudaGetSymbolAddress once per device (again if the device's context was
+// destroyed and recreated since), by the first call made with that device
+// current; that first call should come before any stream capture (the lookup
+// may load the module).  Every call checks that psi, c_out, probs_out and the
+// stream belong to the current device before it queues anything, and returns
+// QN_EINVAL for host memory or another GPU's buffers.  All calls share the one
+// array and find the
 // previous call's contents in it: the counters and flags that must start at
 // zero are cleared on the stream at the start of every call, and calls whose
 // work overlaps on the GPU (different streams without ordering, or several
@@ -37,10 +41,52 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device: the scratch address and the id of the CUDA context it belongs to.
+// A context torn down and created again (cudaDeviceReset, or a driver-level
+// reset by another library) loads the module anew, so the address is looked up
+// again whenever the current context's id differs from the cached one.
 void *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once per device).
-qn_status scratch_address(void **out) {
+// Driver entry points for the current context's unique id, fetched through the
+// runtime so the library need not link libcuda.  Null when the driver lacks
+// them; the cache then keys on the device alone.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+struct CtxFns {
+    CtxGetCurrentFn get_current = nullptr;
+    CtxGetIdFn get_id = nullptr;
+};
+const CtxFns &ctx_fns() {
+    static const CtxFns fns = [] {
+        CtxFns f;
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa = cudaDriverEntryPointSymbolNotFound, qb = qa;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess && qb == cudaDriverEntryPointSuccess && a && b) {
+            f.get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+            f.get_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+        cudaGetLastError();
+        return f;
+    }();
+    return fns;
+}
+
+// Id of the current context (0 when it cannot be read).
+unsigned long long current_ctx_id() {
+    const CtxFns &f = ctx_fns();
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (f.get_current && f.get_current(&ctx) == 0 && ctx && f.get_id(ctx, &id) == 0) return id;
+    return 0;
+}
+
+// Device address of g_scratch in the current device's context (looked up once per
+// device and context; when the context id cannot be read, on every call).
+// *dev_out receives the current device.
+qn_status scratch_address(void **out, int *dev_out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
@@ -49,8 +95,11 @@ qn_status scratch_address(void **out) {
         return qn::set_error(QN_ECUDA, msg);
     }
     if (dev < 0 || dev >= kMaxDevices) return qn::set_error(QN_EINVAL, "device ordinal beyond 63");
+    // a context that does not exist yet (or no longer exists) reads as id 0 and
+    // never matches a cached id; the lookup below creates it
+    const unsigned long long ctx = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
@@ -59,42 +108,90 @@ qn_status scratch_address(void **out) {
             return qn::set_error(QN_ECUDA, msg);
         }
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = current_ctx_id();
     }
     *out = g_scratch_ptr[dev];
+    *dev_out = dev;
     return QN_OK;
 }
 
-// Bump allocator over the scratch array (256-byte aligned slices).
+// Bump allocator over the scratch array (256-byte aligned slices).  With a null
+// base it only measures: the same carve() call both sizes and lays out the
+// scratch, so the size check cannot drift from the real layout.
 struct Carve {
     unsigned char *base;
     size_t used;
     template <typename T>
     T *take(size_t count) {
         used = (used + 255) & ~(size_t)255;
-        T *p = reinterpret_cast<T *>(base + used);
+        T *p = base ? reinterpret_cast<T *>(base + used) : nullptr;
         used += count * sizeof(T);
         return p;
     }
 };
 
+// Every scratch buffer of one batch of `count` trajectories.
+struct Scratch {
+    uint8_t *branch;
+    uint32_t *dwords, *frame_x;
+    uint8_t *yphase;
+    float *hfac;
+    qn::TrajState *st;
+    double *partials, *inv_norm, *cpart;
+    unsigned int *counters, *acc_counter;
+    int *status;
+    qn::DevGate *dgates;
+    int2 *dedges;
+};
+
+Scratch carve(Carve &c, int n, int count, int G, int E) {
+    Scratch s;
+    const size_t tiles = (size_t)qn::tiles_for(n);
+    s.branch = c.take<uint8_t>((size_t)count * G);
+    s.dwords = c.take<uint32_t>((size_t)count * G * 2);
+    s.frame_x = c.take<uint32_t>((size_t)count * (G + 1));
+    s.yphase = c.take<uint8_t>((size_t)count);
+    s.hfac = c.take<float>((size_t)count * n * 2);
+    s.st = c.take<qn::TrajState>((size_t)count);
+    s.partials = c.take<double>((size_t)count * tiles * 4);
+    s.inv_norm = c.take<double>((size_t)count);
+    s.cpart = c.take<double>((size_t)count * qn::accumulate_xblocks(n));
+    s.counters = c.take<unsigned int>((size_t)count);
+    s.acc_counter = c.take<unsigned int>(1);
+    s.status = c.take<int>(1);
+    s.dgates = c.take<qn::DevGate>((size_t)(G > 0 ? G : 1));
+    s.dedges = c.take<int2>((size_t)(E > 0 ? E : 1));
+    return s;
+}
+
 size_t scratch_needed(int n, int count, int G, int E) {
     Carve c{nullptr, 0};
-    const size_t tiles = (size_t)qn::tiles_for(n);
-    c.take<uint8_t>((size_t)count * G);
-    c.take<uint32_t>((size_t)count * G * 2);
-    c.take<uint32_t>((size_t)count * (G + 1));
-    c.take<uint8_t>((size_t)count);
-    c.take<float>((size_t)count * n * 2);
-    c.take<qn::TrajState>((size_t)count);
-    c.take<double>((size_t)count * tiles * 4);
-    c.take<double>((size_t)count);
-    c.take<double>((size_t)count * qn::accumulate_xblocks(n));
-    c.take<unsigned int>((size_t)count);
-    c.take<unsigned int>(1);
-    c.take<int>(1);
-    c.take<qn::DevGate>((size_t)(G > 0 ? G : 1));
-    c.take<int2>((size_t)(E > 0 ? E : 1));
+    carve(c, n, count, G, E);
     return c.used;
+}
+
+// A caller buffer must be device memory (or managed memory) of device `dev`:
+// a host pointer or another GPU's buffer would fault inside the kernels.
+qn_status check_device_buffer(const void *ptr, int dev, const char *name) {
+    cudaPointerAttributes at;
+    const cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char msg[256];
+        snprintf(msg, sizeof msg, "%s: cudaPointerGetAttributes failed: %s", name, cudaGetErrorString(e));
+        return qn::set_error(QN_EINVAL, msg);
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+        char msg[256];
+        snprintf(msg, sizeof msg, "%s is not device memory (pointer type %d)", name, (int)at.type);
+        return qn::set_error(QN_EINVAL, msg);
+    }
+    if (at.device != dev) {
+        char msg[256];
+        snprintf(msg, sizeof msg, "%s belongs to device %d but device %d is current", name, at.device, dev);
+        return qn::set_error(QN_EINVAL, msg);
+    }
+    return QN_OK;
 }
 
 #define NA_CUDA(call)                                                                  \
@@ -132,11 +229,32 @@ extern "C" qn_status qn_run_qaoa_noalloc(int32_t n, const qn_graph *graph, int32
         return set_error(QN_EINVAL, msg);
     }
     void *base = nullptr;
-    st = scratch_address(&base);
+    int dev = -1;
+    st = scratch_address(&base, &dev);
     if (st != QN_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // every buffer and the stream must belong to the current device, checked before anything is queued
+    if ((st = check_device_buffer(psi, dev, "psi")) != QN_OK) return st;
+    if ((st = check_device_buffer(c_out, dev, "c_out")) != QN_OK) return st;
+    if ((st = check_device_buffer(probs_out, dev, "probs_out")) != QN_OK) return st;
+    {
+        int sdev = -1;
+        const cudaError_t e = cudaStreamGetDevice(s, &sdev);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            char msg[256];
+            snprintf(msg, sizeof msg, "cudaStreamGetDevice failed: %s", cudaGetErrorString(e));
+            return set_error(QN_EINVAL, msg);
+        }
+        if (sdev != dev) {
+            char msg[256];
+            snprintf(msg, sizeof msg, "the stream belongs to device %d but device %d is current", sdev, dev);
+            return set_error(QN_EINVAL, msg);
+        }
+    }
 
     Carve c{static_cast<unsigned char *>(base), 0};
+    const Scratch sc = carve(c, n, count, G, E);
     BatchView v;
     v.psi = static_cast<float2 *>(psi);
     v.n = n;
@@ -145,20 +263,20 @@ extern "C" qn_status qn_run_qaoa_noalloc(int32_t n, const qn_graph *graph, int32
     v.G = G;
     v.tiles = (int32_t)tiles_for(n);
     v.stiles = (int32_t)sweep_tiles_for(n);
-    v.branch = c.take<uint8_t>((size_t)count * G);
-    v.dwords = c.take<uint32_t>((size_t)count * G * 2);
-    v.frame_x = c.take<uint32_t>((size_t)count * (G + 1));
-    v.yphase = c.take<uint8_t>((size_t)count);
-    v.hfac = c.take<float>((size_t)count * n * 2);
-    v.st = c.take<TrajState>((size_t)count);
-    v.partials = c.take<double>((size_t)count * v.tiles * 4);
-    v.inv_norm = c.take<double>((size_t)count);
-    double *cpart = c.take<double>((size_t)count * accumulate_xblocks(n));
-    v.counters = c.take<unsigned int>((size_t)count);
-    unsigned int *acc_counter = c.take<unsigned int>(1);
-    v.status = c.take<int>(1);
-    DevGate *dgates = c.take<DevGate>((size_t)(G > 0 ? G : 1));
-    int2 *dedges = c.take<int2>((size_t)(E > 0 ? E : 1));
+    v.branch = sc.branch;
+    v.dwords = sc.dwords;
+    v.frame_x = sc.frame_x;
+    v.yphase = sc.yphase;
+    v.hfac = sc.hfac;
+    v.st = sc.st;
+    v.partials = sc.partials;
+    v.inv_norm = sc.inv_norm;
+    double *cpart = sc.cpart;
+    v.counters = sc.counters;
+    unsigned int *acc_counter = sc.acc_counter;
+    v.status = sc.status;
+    DevGate *dgates = sc.dgates;
+    int2 *dedges = sc.dedges;
 
     // zero what the kernels expect zeroed; the array holds the previous call's data
     NA_CUDA(cudaMemsetAsync(v.counters, 0, (size_t)count * sizeof(unsigned int), s));

@@ -53,6 +53,7 @@ _SIGS = {
     "qn_grad": (c_i32, [c_vp, P(c_dbl), P(c_dbl)]),
     "qn_grad_traj": (c_i32, [c_vp, c_i64, c_i64, P(c_dbl), P(c_dbl)]),
     "qn_traj_debug": (c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
+    "qn_shared_readout": (c_i32, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
     "qn_fidelity_error": (c_i32, [P(c_dbl), P(c_dbl), c_i64, P(c_dbl)]),
     "qn_run_info": (c_i32, [c_vp, P(c_i64), P(c_i64), P(c_dbl), P(c_i64)]),
     "qn_batch_set_profiling": (c_i32, [c_vp, c_i32]),
@@ -105,6 +106,7 @@ class Batch:
         self._h = h
         self.n, self.trajectories, self.seed = int(n), int(trajectories), int(seed)
         self.p = 0
+        self.generation = 0  # number of qn_run_qaoa calls made on this handle
         self._keep = []
         if launch_batch:
             check(qn_batch_set_launch_batch(h, int(launch_batch)), "qn_batch_set_launch_batch")
@@ -166,6 +168,7 @@ class Batch:
         graph = qn_graph(self.n, len(e) // 2, e.ctypes.data_as(P(c_i32)))
         noise = qn_noise(float(p1), float(p2), float(damping), int(twoq_mode), int(param))
         self.p = len(g)
+        self.generation += 1
         check(qn_run_qaoa(self._h, ctypes.byref(graph), len(g), _dptr(g), _dptr(b), ctypes.byref(noise)),
               "qn_run_qaoa")
 
@@ -204,6 +207,20 @@ class Batch:
         cc = np.zeros(max(count, 1), dtype=np.float64) if c else None
         vp = lambda x: None if x is None else c_vp(x.ctypes.data)
         check(qn_traj_debug(self._h, int(t0), int(count), vp(a), vp(br), vp(cc)), "qn_traj_debug")
+        return dict(amps=None if a is None else a.view(np.complex64)[..., 0],
+                    branches=None if br is None else br[:, :info["gates"]],
+                    c_traj=None if cc is None else cc[:count])
+
+    def shared_readout(self, t0: int, count: int, *, amps=True, branches=True, c=True):
+        """The last shared-prefix run's own per-trajectory results (no re-simulation):
+        final states, the Kraus strings that run drew, and <C>_t."""
+        dim = 1 << self.n
+        info = self.run_info()
+        a = np.zeros((count, dim, 2), dtype=np.float32) if amps else None
+        br = np.zeros((count, max(info["gates"], 1)), dtype=np.uint8) if branches else None
+        cc = np.zeros(max(count, 1), dtype=np.float64) if c else None
+        vp = lambda x: None if x is None else c_vp(x.ctypes.data)
+        check(qn_shared_readout(self._h, int(t0), int(count), vp(a), vp(br), vp(cc)), "qn_shared_readout")
         return dict(amps=None if a is None else a.view(np.complex64)[..., 0],
                     branches=None if br is None else br[:, :info["gates"]],
                     c_traj=None if cc is None else cc[:count])

@@ -92,6 +92,8 @@ class Server:
         self._streams = [torch.cuda.Stream() for _ in range(max_inflight)]
         self._free_streams = list(range(max_inflight))
         self._threads = []
+        # one entry per admission: (time, requests in flight, footprint bytes held), after admitting
+        self.admissions: list[tuple[float, int, int]] = []
         self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
         self._dispatcher.start()
 
@@ -139,6 +141,7 @@ class Server:
                 req, fut, ts = item
                 self._inflight += 1
                 self._mem_used += req.footprint()
+                self.admissions.append((time.perf_counter(), self._inflight, self._mem_used))
                 si = self._free_streams.pop()
             th = threading.Thread(target=self._run, args=(req, fut, ts, si), daemon=True)
             self._threads.append(th)

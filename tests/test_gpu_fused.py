@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tolerances import TOL_CT
 from paper_2210_15874_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -54,7 +55,7 @@ def test_fused_matches_per_gate_and_oracle(qn, n, p, edges_kind):
     gates, G = oracle.qaoa_gates(n, edges, g, b)
     ref = oracle.traj_run(n, edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, 0, K)
     np.testing.assert_array_equal(fused["branches"], ref["branches"])
-    tol_c = 8 * U32 * G * len(edges)
+    tol_c = TOL_CT
     for res in (fused, plain):
         assert np.abs(res["amps"] - ref["amps"]).max() < 1e-5
         assert np.abs(res["c_traj"] - ref["c_traj"]).max() < tol_c
@@ -83,3 +84,30 @@ def test_fused_precision_n14(qn):
                      "sweeps_per_trajectory": int(r["info"]["sweep_bytes"] / (16 * 2 ** w.n * w.trajectories))}
         assert out[name]["max_abs_amp_err"] < 1e-5
     print(json.dumps({"precision_n14_fp32": out, "gates": G}))
+
+
+def test_fused_at_size_n24_sampled_against_oracle(qn):
+    """The precision workload's fused path at a size whose states (128 MiB each) are far
+    above L2 and whose tiles cover every mixer-sweep variant: n=24, p=4, 3-regular,
+    depolarizing p1=1e-3 / p2=1e-2, two trajectories of a 64-trajectory ensemble
+    (global ids 37 and 38) read back from the fused sweeps and compared with the oracle
+    amplitude by amplitude.  (n=26 costs the oracle about four minutes per trajectory
+    on the host cores; n=24 about one.)"""
+    w = W.qaoa_workload("precision_n24", 24, 4, index=2, trajectories=64, batch=16)
+    t0, cnt = 37, 2
+    with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+        b.set_fusion(True)
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        info = b.run_info()
+        dbg = b.traj_debug(t0, cnt)
+    E = len(w.edges)
+    assert info["sweep_bytes"] == 16.0 * 2 ** w.n * w.trajectories * w.p * (-(-w.n // 3))  # fused schedule
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    ref = oracle.traj_run(w.n, w.edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, t0, cnt,
+                          threads=cnt)
+    np.testing.assert_array_equal(dbg["branches"], ref["branches"])
+    err = float(np.abs(dbg["amps"] - ref["amps"]).max())
+    c_err = float(np.abs(dbg["c_traj"] - ref["c_traj"]).max())
+    print(json.dumps({"fused_n24": {"max_abs_amp_err": err, "max_abs_c_err": c_err, "E": E}}))
+    assert err < 1e-5
+    assert c_err < 2e-5

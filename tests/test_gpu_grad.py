@@ -116,3 +116,32 @@ def test_autograd_function_uses_the_adjoint(qn):
         dg, db = b.grad()
     np.testing.assert_allclose(g.grad.numpy(), 2.0 * dg, rtol=1e-12)
     np.testing.assert_allclose(bt.grad.numpy(), 2.0 * db, rtol=1e-12)
+
+
+def test_autograd_two_forwards_on_one_batch(qn):
+    """Two energies at different angles on the same Batch summed into one loss: each
+    backward must return the gradient at its own forward's angles, not at the angles
+    the handle ran last."""
+    import torch
+
+    from paper_2210_15874_gb300.autograd import qaoa_energy
+
+    w = W.qaoa_workload("grad_autograd_two", 8, 2, index=24, trajectories=64, batch=64, p1=1e-2, p2=2e-2)
+    g1 = torch.tensor(w.gammas, dtype=torch.float64, requires_grad=True)
+    b1 = torch.tensor(w.betas, dtype=torch.float64, requires_grad=True)
+    g2 = torch.tensor(w.gammas[::-1].copy() + 0.3, dtype=torch.float64, requires_grad=True)
+    b2 = torch.tensor(w.betas[::-1].copy() + 0.2, dtype=torch.float64, requires_grad=True)
+    ref = []
+    for g, bt in ((g1, b1), (g2, b2)):  # each on a fresh handle
+        with qn.Batch(w.n, w.trajectories, w.seed) as b:
+            b.run_qaoa(w.edges, g.detach().numpy(), bt.detach().numpy(), **w.noise_kwargs())
+            ref.append(b.grad())
+    assert np.abs(ref[0][0] - ref[1][0]).max() > 1e-3  # the two points differ
+    with qn.Batch(w.n, w.trajectories, w.seed) as b:
+        loss = qaoa_energy(g1, b1, b, w.edges, **w.noise_kwargs()) + 3.0 * qaoa_energy(
+            g2, b2, b, w.edges, **w.noise_kwargs())
+        loss.backward()
+    np.testing.assert_allclose(g1.grad.numpy(), ref[0][0], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b1.grad.numpy(), ref[0][1], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(g2.grad.numpy(), 3.0 * ref[1][0], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b2.grad.numpy(), 3.0 * ref[1][1], rtol=1e-12, atol=1e-14)

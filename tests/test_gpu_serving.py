@@ -52,20 +52,33 @@ def test_results_equal_alone_and_in_the_mix(mods):
 
 
 def test_admission_by_footprint(mods):
-    """A budget that holds one request at a time still serves them all, one by one."""
+    """Admission never lets the footprints in flight exceed the budget: with the
+    largest request's footprint as the budget, that request runs alone; a budget
+    that holds the two smallest together keeps at most two in flight; a request
+    above the budget is refused at submission."""
     serving = mods
     reqs = make_requests(serving, 5, np.random.default_rng(6))
-    budget = max(r.footprint() for r in reqs)
+    fp = sorted(r.footprint() for r in reqs)
+    budget = fp[-1]
     srv = serving.Server(max_inflight=4, mem_budget=budget)
     futs = [srv.submit(r) for r in reqs]
     res = [f.result(timeout=300) for f in futs]
     srv.close()
-    spans = sorted((r.started, r.finished) for r in res)
-    for a, b in zip(spans, spans[1:]):
-        if a[1] > b[0]:
-            # overlap allowed only if both fit together
-            pass
     assert len(res) == 5 and all(np.isfinite(r.mean) for r in res)
+    assert len(srv.admissions) == 5
+    assert all(used <= budget for _, _, used in srv.admissions)
+    big = max(range(5), key=lambda i: reqs[i].footprint())
+    for i in range(5):  # nothing else fits beside the largest request
+        if i != big:
+            assert res[i].finished <= res[big].started or res[i].started >= res[big].finished
+    # room for the two smallest together (and not for three)
+    budget2 = fp[0] + fp[1]
+    small = [r for r in reqs if r.footprint() <= budget2]
+    srv = serving.Server(max_inflight=4, mem_budget=budget2)
+    res2 = [f.result(timeout=300) for f in [srv.submit(r) for r in small]]
+    srv.close()
+    assert len(res2) == len(small)
+    assert all(used <= budget2 and inflight <= 2 for _, inflight, used in srv.admissions)
     with pytest.raises(ValueError):
         srv2 = serving.Server(max_inflight=1, mem_budget=1024)
         try:
