@@ -214,7 +214,7 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
+def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e, precision=0):
     """Time `args.steps` whole-ensemble steps (after `args.warmup`) in one mode."""
     import torch
 
@@ -222,6 +222,7 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
     b = qn.Batch(w.n, w.trajectories, w.seed, launch_batch=0 if sharing else w.batch, stream=stream)
     b.set_sharing(sharing)
     b.set_fusion(fusion)
+    b.set_precision(precision)
     # weak scaling: rank r evolves global trajectories [r K, (r+1) K)
     if world > 1:
         b.set_offset(rank * w.trajectories)
@@ -287,22 +288,26 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e):
 
 def precision_leg(qn, args, stream, local, roof_of):
     """The precision workload (n=26, p=4, depolarizing only, 64 trajectories of 512 MiB):
-    fused layers (ceil(n/3) sweeps per layer) against one sweep per gate on the same
-    trajectories -- throughput, the sweeps' HBM fraction, and the two forms' <C> beside
-    the ensemble's statistical error (the comparison "at equal <C> error")."""
+    fused layers (FP32, ceil(n/3) sweeps per layer; tensor cores in TF32 and BF16x3,
+    ceil(n/5) sweeps per layer) against one sweep per gate on the same trajectories --
+    throughput, the sweeps' HBM fraction, and each form's <C> beside the ensemble's
+    statistical error (the comparison "at equal <C> error")."""
     w = W.precision_n26()
     legs = {}
     sub = argparse.Namespace(steps=max(2, min(args.steps, 3)), warmup=3)
-    for name, mode in (("fused", (False, True)), ("per_gate", (False, False))):
-        res = measure(qn, w, sub, mode, stream, 0, 1, local, None, with_e2e=False)
-        kname = "k_fused_sweep (fused layer sweeps)" if mode[1] else "k_sweep_zz / k_sweep_rx (gate sweeps)"
+    for name, mode, prec in (("fused", (False, True), 0), ("tensor_tf32", (False, True), 1),
+                             ("tensor_bf16x3", (False, True), 2), ("per_gate", (False, False), 0)):
+        res = measure(qn, w, sub, mode, stream, 0, 1, local, None, with_e2e=False, precision=prec)
+        kname = ("k_tc_sweep (tensor-core windows of 5 qubits, 16 B per amplitude)" if prec else
+                 "k_fused_sweep (fused layer sweeps)") if mode[1] else "k_sweep_zz / k_sweep_rx (gate sweeps)"
         r = roof_of(res, kname, "sweeps")
         legs[name] = {"value": res["value"], "unit": UNIT, "ms_per_step": res["ms"] / sub.steps,
                       "c_mean": res["mean"], "c_stderr": res["se"], "sweep_bytes_per_step": res["sweep_bytes_per_step"],
                       "roofline": {k: r[k] for k in ("kernel", "achieved", "peak", "unit", "frac", "avg_launch_ms")},
                       "clocks": res["clocks"]}
-    legs["speedup_fused_over_per_gate"] = legs["fused"]["value"] / legs["per_gate"]["value"]
-    legs["c_difference"] = abs(legs["fused"]["c_mean"] - legs["per_gate"]["c_mean"])
+    for name in ("fused", "tensor_tf32", "tensor_bf16x3"):
+        legs[name]["speedup_over_per_gate"] = legs[name]["value"] / legs["per_gate"]["value"]
+        legs[name]["c_difference_to_per_gate"] = abs(legs[name]["c_mean"] - legs["per_gate"]["c_mean"])
     legs["config"] = config_of(w, {"steps": sub.steps, "warmup": sub.warmup})
     return legs
 

@@ -125,6 +125,20 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
  * mode damping runs are swept gate by gate. */
 qn_status qn_batch_set_fusion(qn_batch *h, int32_t on);
 
+/* Arithmetic of the fused layers (Pauli-only noise, fusion on, n >= 11):
+ *   0  FP32 on the CUDA cores, three qubits per sweep (the default);
+ *   1  TF32 tensor cores: the mixer rotations of five qubits per sweep as two
+ *      GEMMs with the +-1 Hadamard matrix (exp(-i beta X) = H diag(e^{-i beta},
+ *      e^{i beta}) H), TF32 operands, FP32 accumulation (ceil(n / 5) sweeps per
+ *      layer);
+ *   2  the same with BF16x3 operands: each FP32 value split exactly into three
+ *      bf16 terms, whose products with the +-1 matrix are exact (FP32
+ *      accumulation: about FP32 accuracy).
+ * A choice of arithmetic with no counterpart in the paper: every mode draws the
+ * same Kraus operators (Sec. "Stochastic Noise Implementation") and differs only
+ * by rounding.  Other runs ignore the setting.  QN_EINVAL for another mode. */
+qn_status qn_batch_set_precision(qn_batch *h, int32_t mode);
+
 /* Shared-prefix mode (on = 1; default 0).  Trajectories whose Kraus strings
  * agree so far share one statevector; when a trajectory's own Pauli or damping
  * draw differs from the shared branch it forks into a copy.  Every trajectory

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libqnoise.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["qn_api.cpp", "qn_kernels.cu", "qn_noalloc.cu"]
+SOURCES = ["qn_api.cpp", "qn_kernels.cu", "qn_noalloc.cu", "qn_tc.cu"]
 HEADERS = [os.path.join(CSRC, "qn_internal.h"), os.path.join(INCLUDE, "qn.h")]
 
 

@@ -173,6 +173,7 @@ struct qn_batch {
     float2 *readout = nullptr;
     // fused layers (Pauli-only noise)
     int32_t fusion = 1;
+    int32_t precision = kPrecFP32;  // arithmetic of the fused layers (qn_batch_set_precision)
     uint64_t *fl_ev = nullptr;    // [4][256]
     float2 *fl_phase = nullptr;   // [p][E+1]
     int2 *fl_edges = nullptr;     // [E]
@@ -733,6 +734,31 @@ qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, boo
         h->launches += 1;
     }
     EventPair ep;
+    if (h->precision != kPrecFP32 && n >= 11) {
+        // tensor cores: windows of five qubits, ceil(n / 5) sweeps per layer; the last window
+        // of a layer is the top five qubits with only the remaining ones rotated
+        for (int l = 0; l < p; ++l) {
+            for (int q_lo = 0; q_lo < n; q_lo += 5) {
+                const int m = std::min(5, n - q_lo);
+                TcSweep sw;
+                sw.wl = std::min(q_lo, n - 5);
+                sw.act = ((1u << m) - 1u) << (q_lo - sw.wl);
+                for (int k = 0; k < 6; ++k) {
+                    const double ang = h->betas[l] * (double)(m - 2 * k);
+                    sw.dph[k] = make_float2((float)(std::cos(ang) / 32.0), (float)(-std::sin(ang) / 32.0));
+                }
+                const bool pre = l == 0 && q_lo == 0;
+                const bool post = q_lo + m >= n && l + 1 < p;
+                QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));
+                QN_CUDA(launch_tc_sweep(v, layer_view(h, l), layer_view(h, l), layer_view(h, post ? l + 1 : l), sw, pre,
+                                        post, h->precision, h->stream));
+                QN_TRY(prof_end(h, &ep));
+                h->launches += 1;
+                if (ensemble) h->sweep_bytes += amp_bytes * 16.0;
+            }
+        }
+        return QN_OK;
+    }
     for (int l = 0; l < p; ++l) {
         for (int q_lo = 0; q_lo < n; q_lo += kFuse) {
             const int m = std::min(kFuse, n - q_lo);
@@ -1206,6 +1232,15 @@ qn_status qn_batch_set_fusion(qn_batch *h, int32_t on) {
     if (!h) return fail(QN_EINVAL, "handle is NULL");
     if (on != 0 && on != 1) return fail(QN_EINVAL, "fusion must be 0 or 1");
     h->fusion = on;
+    h->has_run = false;
+    return ok();
+}
+
+qn_status qn_batch_set_precision(qn_batch *h, int32_t mode) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (mode != kPrecFP32 && mode != kPrecTF32 && mode != kPrecBF16x3)
+        return fail(QN_EINVAL, "precision must be 0 (FP32), 1 (TF32 tensor cores) or 2 (BF16x3 tensor cores)");
+    h->precision = mode;
     h->has_run = false;
     return ok();
 }

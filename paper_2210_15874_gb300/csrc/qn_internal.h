@@ -184,6 +184,34 @@ struct LayerView {
     float cb, sb;            // cos beta, sin beta of the layer
 };
 
+#if defined(__CUDACC__)
+// The cost layer's diagonal factor at amplitude y (stored basis) for one
+// trajectory: e^{-i gamma k} with k the number of edges whose stored endpoint
+// bits differ from the frame's (EV byte tables xor s), times the sign of the
+// Pauli Z parts (popc(y & zm) xor zc).
+__device__ __forceinline__ float2 layer_phase(const LayerView &L, uint32_t y, uint64_t sv, uint32_t zm, uint32_t zc) {
+    const uint64_t ev = __ldg(L.ev + (y & 255u)) ^ __ldg(L.ev + 256 + ((y >> 8) & 255u)) ^
+                        __ldg(L.ev + 512 + ((y >> 16) & 255u)) ^ __ldg(L.ev + 768 + (y >> 24));
+    const int k = __popcll(ev ^ sv);
+    const float2 ph = __ldg(L.phase + k);
+    const float sg = ((__popc(y & zm) ^ zc) & 1u) ? -1.0f : 1.0f;
+    return make_float2(ph.x * sg, ph.y * sg);
+}
+#endif
+
+// Arithmetic of the fused layers (Pauli-only noise): FP32 on the CUDA cores, or
+// the mixer rotations as GEMMs on the tensor cores with TF32 operands or BF16x3
+// split operands (FP32 accumulation either way).
+enum Precision : int32_t { kPrecFP32 = 0, kPrecTF32 = 1, kPrecBF16x3 = 2 };
+
+// One tensor-core sweep: the mixer rotations of the qubits `act` (bits of the
+// window wl .. wl + 4) of one layer, dph[k] = e^{-i beta (popc(act) - 2k)} / 32.
+struct TcSweep {
+    int32_t wl;
+    uint32_t act;
+    float2 dph[6];
+};
+
 constexpr int kFuse = 3;     // qubits per fused mixer sweep
 
 struct NoiseDev {
@@ -264,6 +292,11 @@ cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, 
 cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
                                int q_lo, int m, bool pre, bool post, cudaStream_t s);
 cudaError_t launch_phase_sweep(const BatchView &v, const LayerView &L, cudaStream_t s);
+// Tensor-core form of a fused sweep (n >= 11): the window's rotations as two
+// GEMMs with the +-1 Hadamard matrix (qn_tc.cu), PRE / POST phases as for
+// launch_fused_sweep.  kind: kPrecTF32 or kPrecBF16x3.
+cudaError_t launch_tc_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
+                            const TcSweep &sw, bool pre, bool post, int kind, cudaStream_t s);
 // Shared-prefix mode, gate g: sweep the `active` live slots; then draw each
 // member's branch, fork the slots whose members drew other branches and copy
 // the forked states (three launches; the new live-slot count is left in

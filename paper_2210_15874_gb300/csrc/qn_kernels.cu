@@ -2716,14 +2716,6 @@ __global__ void k_layer_params(BatchView v, LayerView L, int g0, int E) {
     L.mf[t] = mf;
 }
 
-__device__ __forceinline__ float2 layer_phase(const LayerView &L, uint32_t y, uint64_t sv, uint32_t zm, uint32_t zc) {
-    const uint64_t ev = __ldg(L.ev + (y & 255u)) ^ __ldg(L.ev + 256 + ((y >> 8) & 255u)) ^
-                        __ldg(L.ev + 512 + ((y >> 16) & 255u)) ^ __ldg(L.ev + 768 + (y >> 24));
-    const int k = __popcll(ev ^ sv);
-    const float2 ph = __ldg(L.phase + k);
-    const float sg = ((__popc(y & zm) ^ zc) & 1u) ? -1.0f : 1.0f;
-    return make_float2(ph.x * sg, ph.y * sg);
-}
 
 __device__ __forceinline__ void cmul_inplace(float &re, float &im, float2 w) {
     const float r = re * w.x - im * w.y, i = re * w.y + im * w.x;

@@ -47,6 +47,7 @@ _SIGS = {
     "qn_batch_set_offset": (c_i32, [c_vp, c_i64]),
     "qn_batch_set_sharing": (c_i32, [c_vp, c_i32]),
     "qn_batch_set_fusion": (c_i32, [c_vp, c_i32]),
+    "qn_batch_set_precision": (c_i32, [c_vp, c_i32]),
     "qn_run_qaoa": (c_i32, [c_vp, P(qn_graph), c_i32, P(c_dbl), P(c_dbl), P(qn_noise)]),
     "qn_expectation": (c_i32, [c_vp, P(c_dbl), P(c_dbl)]),
     "qn_probs": (c_i32, [c_vp, P(c_dbl), c_i64]),
@@ -145,6 +146,12 @@ class Batch:
     def set_fusion(self, on: bool) -> None:
         """Fused layers for Pauli-only noise (default on)."""
         check(qn_batch_set_fusion(self._h, int(bool(on))), "qn_batch_set_fusion")
+
+    def set_precision(self, mode) -> None:
+        """Arithmetic of the fused layers: 0 / "fp32" (CUDA cores), 1 / "tf32" or 2 / "bf16x3"
+        (tensor cores, five qubits per sweep)."""
+        m = {"fp32": 0, "tf32": 1, "bf16x3": 2}.get(mode, mode)
+        check(qn_batch_set_precision(self._h, int(m)), "qn_batch_set_precision")
 
     def set_sharing(self, on: bool) -> None:
         """Shared-prefix mode: trajectories share their common Kraus prefix."""
