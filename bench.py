@@ -288,7 +288,7 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e, precisi
 
 def precision_leg(qn, args, stream, local, roof_of):
     """The precision workload (n=26, p=4, depolarizing only, 64 trajectories of 512 MiB):
-    fused layers (FP32, ceil(n/3) sweeps per layer; tensor cores in TF32 and BF16x3,
+    fused layers (FP32, qubits 0-4 then four per sweep; tensor cores in TF32 and BF16x3,
     ceil(n/5) sweeps per layer) against one sweep per gate on the same trajectories --
     throughput, the sweeps' HBM fraction, and each form's <C> beside the ensemble's
     statistical error (the comparison "at equal <C> error")."""
@@ -396,7 +396,7 @@ def gpu_arm(args):
                          "prefix tree" + ("; phase gates applied in groups on <= 10 qubits and mixer rotations "
                                           "in blocks of 4 qubits, one sweep per group or block" if grouped
                                           else "; one sweep per gate")) if sharing else
-                        (f"fused layers: ceil(n/3) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused
+                        (f"fused layers: 1 + ceil((n-5)/4) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused
                          else f"one statevector per trajectory, one sweep per gate, {w.batch} per launch")}),
             "amp_updates_per_s": main["value"] * G * (1 << n),
             "distinct_states_per_step": main["states_per_step"],
@@ -488,13 +488,23 @@ def serving_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(sharing=False, depth=1, fusion=True):
+def profile_case(sharing=False, depth=1, fusion=True, precision=0):
     """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state);
-    depth 2 adds a layer, so the last mixer block of the first one forms the next layer's joint."""
+    depth 2 adds a layer, so the last mixer block of the first one forms the next layer's joint.
+    precision 1 or 2: the precision workload's fused layers on the tensor cores (n=24, p=1,
+    depolarizing only, 8 states of 128 MiB)."""
     from paper_2210_15874_gb300 import build
     build.build()
     from paper_2210_15874_gb300 import qn
 
+    if precision:
+        w = W.qaoa_workload("ncu_n24_p1_tc", 24, 1, index=2, trajectories=8, batch=8)
+        with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+            b.set_fusion(True)
+            b.set_precision(precision)
+            b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+            print(json.dumps({"case": w.name, "precision": precision, "c": b.expectation()}))
+        return
     if sharing:
         # heavy Pauli noise so that most of the 64 trajectories fork early: the
         # late gates sweep ~64 live states (512 MiB, above L2)
@@ -543,9 +553,11 @@ def main():
                     help="run one small ensemble for ncu captures, then exit (n=20, p=1: 32 trajectories in "
                          "one launch, or with --sharing 1 64 heavily noisy trajectories)")
     ap.add_argument("--profile-depth", type=int, default=1, choices=[1, 2], help="QAOA depth of --profile-case")
+    ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2],
+                    help="--profile-case of the tensor-core fused layers (1 TF32, 2 BF16x3)")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(bool(args.sharing), args.profile_depth, bool(args.fusion))
+        profile_case(bool(args.sharing), args.profile_depth, bool(args.fusion), args.profile_precision)
         return
     if args.workload == "serving":
         serving_arm(args)

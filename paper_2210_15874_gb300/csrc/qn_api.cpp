@@ -723,9 +723,10 @@ LayerView layer_view(const qn_batch *h, int l) {
     return L;
 }
 
-// All gates after the H layer as fused sweeps: per layer ceil(n / kFuse)
-// mixer sweeps; the cost phase of layer 0 rides on the first sweep and that of
-// layer l+1 on the last mixer sweep of layer l.
+// All gates after the H layer as fused sweeps: per layer one sweep over qubits
+// 0 .. kFuse0-1 and ceil((n - kFuse0) / kFuse) over the rest; the cost phase of
+// layer 0 rides on the first sweep and that of layer l+1 on the last mixer sweep
+// of layer l.
 qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, bool ensemble) {
     const int n = h->n, p = h->p;
     const int E = (int)h->edges.size() / 2;
@@ -760,8 +761,8 @@ qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, boo
         return QN_OK;
     }
     for (int l = 0; l < p; ++l) {
-        for (int q_lo = 0; q_lo < n; q_lo += kFuse) {
-            const int m = std::min(kFuse, n - q_lo);
+        for (int q_lo = 0; q_lo < n; q_lo += q_lo == 0 ? kFuse0 : kFuse) {
+            const int m = std::min(q_lo == 0 ? kFuse0 : kFuse, n - q_lo);
             const bool pre = l == 0 && q_lo == 0;
             const bool post = q_lo + m >= n && l + 1 < p;
             QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));

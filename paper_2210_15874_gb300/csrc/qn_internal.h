@@ -212,7 +212,8 @@ struct TcSweep {
     float2 dph[6];
 };
 
-constexpr int kFuse = 3;     // qubits per fused mixer sweep
+constexpr int kFuse0 = 5;    // qubits of the fused mixer sweep that holds qubit 0 (16 float4 per thread)
+constexpr int kFuse = 4;     // qubits of the other fused mixer sweeps (16 float4 per thread)
 
 struct NoiseDev {
     double gamma;              // damping (0 = off)

@@ -2684,7 +2684,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_sweep(BatchView v, float2 *lam
 //    s_e flips edge e when the frame differs on its endpoints at that gate;
 //  * the mixer layer is a tensor product of one 2x2 matrix per qubit (the
 //    rotation with the row signs of its Pauli's Z part), applied in register
-//    fibers over kFuse consecutive qubits per sweep.
+//    fibers over kFuse0 consecutive qubits (the window holding qubit 0) or
+//    kFuse (the others) per sweep.
 // A sweep applies [phase of layer l] (first sweep) and the rotations of one
 // qubit group; the last group of a layer also applies the next layer's phase.
 // ---------------------------------------------------------------------------
@@ -2723,35 +2724,66 @@ __device__ __forceinline__ void cmul_inplace(float &re, float &im, float2 w) {
     im = i;
 }
 
+// The cost layer's factor at y = y0 | yk with disjoint bits, from EV(y0), EV(yk)
+// and the Z parity of y0 (both the edge-difference vector and the parity are
+// linear in y): layer_phase split into a per-thread and a per-pattern part.
+__device__ __forceinline__ float2 split_phase(const LayerView &L, uint64_t ev0, uint64_t evk, uint64_t sv, uint32_t zp0,
+                                              uint32_t yk, uint32_t zm) {
+    const int k = __popcll(ev0 ^ evk ^ sv);
+    const float2 ph = __ldg(L.phase + k);
+    const float sg = ((zp0 ^ __popc(yk & zm)) & 1u) ? -1.0f : 1.0f;
+    return make_float2(ph.x * sg, ph.y * sg);
+}
+
+__device__ __forceinline__ uint64_t ev_of(const LayerView &L, uint32_t y) {
+    return __ldg(L.ev + (y & 255u)) ^ __ldg(L.ev + 256 + ((y >> 8) & 255u)) ^ __ldg(L.ev + 512 + ((y >> 16) & 255u)) ^
+           __ldg(L.ev + 768 + (y >> 24));
+}
+
 // One fused sweep.  The group is qubits [q_lo, q_lo + M); with HAS0 (q_lo == 0)
 // bit 0 lies inside each float4 and a thread holds 2^(M-1) float4, otherwise
-// 2^M float4 along f bits q_lo-1 .. q_lo+M-2.  PRE: phase of layer `lp` before
-// the rotations; POST: phase of layer `lq` after them.
+// 2^M float4 along f bits q_lo-1 .. q_lo+M-2 (at most 16 float4: M <= 5 with
+// qubit 0, M <= 4 without).  PRE: phase of layer `lp` before the rotations;
+// POST: phase of layer `lq` after them.  The phase of element k, half e, is
+// that of y0 | 2 (k << fl) | e, split into the thread's y0 and the block-wide
+// tables of the patterns 2 (k << fl) and e.
 template <int M, bool HAS0, bool PRE, bool POST>
 __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerView Lp, LayerView Lr, LayerView Lq,
                                                              int q_lo) {
     constexpr int D = HAS0 ? M - 1 : M;  // fiber bits in float4 index space
     constexpr int NE = 1 << D;
+    static_assert(NE <= 16, "at most 16 float4 per thread");
     const int t = blockIdx.y;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
     const int fl = HAS0 ? 0 : q_lo - 1;
     const int64_t nfib = nf >> D;
+    __shared__ uint64_t evk[NE + 1];  // EV of each element's offset; [NE]: EV of bit 0
+    if (PRE || POST) {
+        const LayerView &L = PRE ? Lp : Lq;  // the edge tables are the graph's, the same in every layer
+        if ((int)threadIdx.x < NE) evk[threadIdx.x] = ev_of(L, 2u * ((uint32_t)threadIdx.x << fl));
+        if ((int)threadIdx.x == NE) evk[NE] = ev_of(L, 1u);
+        __syncthreads();
+    }
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
     const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (r >= nfib) return;
     const int64_t fbase = ((r >> fl) << (fl + D)) | (r & (((int64_t)1 << fl) - 1));
+    const uint32_t y0 = (uint32_t)(2 * fbase);
     float4 val[NE];
 #pragma unroll
     for (int k = 0; k < NE; ++k) val[k] = p4[fbase + ((int64_t)k << fl)];
     if (PRE) {
         const uint64_t sv = Lp.s[t];
-        const uint32_t zm = Lp.zm[t], zc = Lp.zc[t];
+        const uint32_t zm = Lp.zm[t];
+        const uint64_t ev0 = ev_of(Lp, y0);
+        const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lp.zc[t];
+        const uint64_t ev1 = evk[NE];
 #pragma unroll
         for (int k = 0; k < NE; ++k) {
-            const uint32_t y = (uint32_t)(2 * (fbase + ((int64_t)k << fl)));
-            cmul_inplace(val[k].x, val[k].y, layer_phase(Lp, y, sv, zm, zc));
-            cmul_inplace(val[k].z, val[k].w, layer_phase(Lp, y | 1u, sv, zm, zc));
+            const uint32_t yk = 2u * ((uint32_t)k << fl);
+            cmul_inplace(val[k].x, val[k].y, split_phase(Lp, ev0, evk[k], sv, zp0, yk, zm));
+            cmul_inplace(val[k].z, val[k].w, split_phase(Lp, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
         }
     }
     const uint32_t mz = Lr.mz[t], mf = Lr.mf[t];
@@ -2789,12 +2821,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
     }
     if (POST) {
         const uint64_t sv = Lq.s[t];
-        const uint32_t zm = Lq.zm[t], zc = Lq.zc[t];
+        const uint32_t zm = Lq.zm[t];
+        const uint64_t ev0 = ev_of(Lq, y0);
+        const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lq.zc[t];
+        const uint64_t ev1 = evk[NE];
 #pragma unroll
         for (int k = 0; k < NE; ++k) {
-            const uint32_t y = (uint32_t)(2 * (fbase + ((int64_t)k << fl)));
-            cmul_inplace(val[k].x, val[k].y, layer_phase(Lq, y, sv, zm, zc));
-            cmul_inplace(val[k].z, val[k].w, layer_phase(Lq, y | 1u, sv, zm, zc));
+            const uint32_t yk = 2u * ((uint32_t)k << fl);
+            cmul_inplace(val[k].x, val[k].y, split_phase(Lq, ev0, evk[k], sv, zp0, yk, zm));
+            cmul_inplace(val[k].z, val[k].w, split_phase(Lq, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
         }
     }
 #pragma unroll
@@ -3123,8 +3158,9 @@ static cudaError_t fused_dispatch(const BatchView &v, const LayerView &Lp, const
     constexpr int D = HAS0 ? M - 1 : M;
     const int64_t nfib = ((int64_t)1 << (v.n - 1)) >> D;
     const dim3 grid((unsigned)((nfib + kThreads - 1) / kThreads), (unsigned)v.b);
-    if (pre && post) k_fused_sweep<M, HAS0, true, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
-    else if (pre) k_fused_sweep<M, HAS0, true, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    if (!HAS0 && pre) return cudaErrorInvalidValue;  // the first layer's phase rides on the qubit-0 window
+    if (HAS0 && pre && post) k_fused_sweep<M, HAS0, HAS0, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    else if (HAS0 && pre) k_fused_sweep<M, HAS0, HAS0, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
     else if (post) k_fused_sweep<M, HAS0, false, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
     else k_fused_sweep<M, HAS0, false, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
     return cudaGetLastError();
@@ -3132,15 +3168,24 @@ static cudaError_t fused_dispatch(const BatchView &v, const LayerView &Lp, const
 
 cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
                                int q_lo, int m, bool pre, bool post, cudaStream_t s) {
-    const bool has0 = q_lo == 0;
-    // fiber dimension D must stay below the n-1 float4 index bits
+    // windows of up to kFuse0 qubits with qubit 0 (it sits inside the float4) and up to
+    // kFuse without; the fiber dimension D stays below the n-1 float4 index bits
+    if (q_lo == 0) {
+        switch (m) {
+        case 1: return fused_dispatch<1, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 2: return fused_dispatch<2, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 3: return fused_dispatch<3, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 4: return fused_dispatch<4, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 5: return fused_dispatch<5, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (m) {
-    case 1: return has0 ? fused_dispatch<1, true>(v, Lp, Lr, Lq, q_lo, pre, post, s)
-                        : fused_dispatch<1, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    case 2: return has0 ? fused_dispatch<2, true>(v, Lp, Lr, Lq, q_lo, pre, post, s)
-                        : fused_dispatch<2, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    default: return has0 ? fused_dispatch<3, true>(v, Lp, Lr, Lq, q_lo, pre, post, s)
-                         : fused_dispatch<3, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 1: return fused_dispatch<1, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 2: return fused_dispatch<2, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 3: return fused_dispatch<3, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 4: return fused_dispatch<4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    default: return cudaErrorInvalidValue;
     }
 }
 

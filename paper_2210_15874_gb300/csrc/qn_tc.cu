@@ -54,6 +54,9 @@ constexpr uint32_t kTcCols = 64;                   // TMEM columns: D1 0..31, D2
 
 template <int KIND>
 __host__ __device__ constexpr int tc_ops() { return KIND == kPrecTF32 ? 1 : 2; }
+// Resident blocks per SM the register budget is compiled for (shared memory admits as many).
+template <int KIND>
+__host__ __device__ constexpr int kTcMinBlocks() { return KIND == kPrecTF32 ? 4 : 3; }
 template <int KIND>
 __host__ __device__ constexpr int tc_smem_bytes() { return 1024 + tc_ops<KIND>() * kTcOpBytes + kTcBBytes + 2 * kTcRawBytes; }
 
@@ -203,7 +206,7 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gmem) {
 }
 
 template <int KIND, bool PRE, bool POST>
-__global__ void __launch_bounds__(kTcThreads, 3) k_tc_sweep(BatchView v, LayerView Lp, LayerView Lr, LayerView Lq,
+__global__ void __launch_bounds__(kTcThreads, kTcMinBlocks<KIND>()) k_tc_sweep(BatchView v, LayerView Lp, LayerView Lr, LayerView Lq,
                                                          TcSweep sw) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char *smem = tc_smem_raw + ((1024u - (su32(tc_smem_raw) & 1023u)) & 1023u);
@@ -426,13 +429,18 @@ cudaError_t tc_launch(const BatchView &v, const LayerView &Lp, const LayerView &
     auto kern = k_tc_sweep<KIND, PRE, POST>;
     constexpr int smem = tc_smem_bytes<KIND>();
     static const int per_sm = [&] {  // once per instantiation, on first use
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTcThreads, smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTcThreads, smem);
+        if (e != cudaSuccess || per < 1) {
+            cudaGetLastError();
+            per = kTcMinBlocks<KIND>();  // what the launch bounds were compiled for
+        }
         // TMEM holds 512 columns per SM: never more resident blocks than that admits
-        per = per < 1 ? 1 : (per > 512 / (int)kTcCols ? 512 / (int)kTcCols : per);
+        if (per > 512 / (int)kTcCols) per = 512 / (int)kTcCols;
         return (sms > 0 ? sms : 152) * per;
     }();
     const int64_t units = (int64_t)v.b << (v.n - 11);
