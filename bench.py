@@ -342,7 +342,7 @@ def gpu_arm(args):
     if not args.fusion:
         main_mode = (main_mode[0], False)
     sharing = main_mode[0] and w.damping > 0
-    main = measure(qn, w, args, main_mode, stream, rank, world, local, pg, with_e2e=True)
+    main = measure(qn, w, args, main_mode, stream, rank, world, local, pg, with_e2e=True, precision=args.precision)
     other = None
     if not args.single_mode and other_mode != main_mode:
         other = measure(qn, w, args, other_mode, stream, rank, world, local, pg, with_e2e=False)
@@ -384,12 +384,16 @@ def gpu_arm(args):
         kname = "k_mix_sweep + k_mix_first (mixer blocks of 4 qubits over live prefix states, 16 B per amplitude)" if blocks else \
             "k_slot_sweep (mixer gate sweeps over live prefix states)" if grouped else \
             "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
-            ("k_fused_sweep (fused layer sweeps, 16 B per amplitude)" if fused else
+            (("k_tc_sweep (tensor-core windows of 5 qubits, %s, 16 B per amplitude)" %
+              ("TF32" if args.precision == 1 else "BF16x3") if args.precision and w.n >= 11 else
+              "k_fused_sweep (fused layer sweeps, 16 B per amplitude)") if fused else
              "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")
         line = {
             "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f32", 1: "tf32 (f32 accumulate)", 2: "bf16x3 (f32 accumulate)"}[args.precision if fused else 0],
+            "data": "synthetic",
             "config": config_of(w, {
                 "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
                 "mode": ("shared-prefix: one statevector per distinct Kraus prefix, all trajectories in one "
@@ -545,6 +549,9 @@ def main():
     ap.add_argument("--fusion", type=int, default=1, choices=[0, 1],
                     help="1: fused sweeps (phase groups and mixer blocks with damping, fused layers without); "
                          "0: one sweep per gate")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="arithmetic of the fused layers of Pauli-only workloads: 0 FP32 (default), 1 TF32 or "
+                         "2 BF16x3 tensor cores")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the precision (n=26) and serving legs of the default line")
     ap.add_argument("--single-mode", action="store_true",

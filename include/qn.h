@@ -120,9 +120,11 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
  * in shared-prefix mode only: consecutive phase gates of a layer on at most 10
  * qubits form a group whose damping branches are all drawn from one joint
  * distribution of those qubits, and the group is applied in one sweep; for
- * n >= 12 the mixer rotations go four qubits per sweep, their damping drawn
- * from the joint of those qubits after the rotations (the same Kraus draws as
- * gate by gate; the state differs by FP32 rounding).  Without shared-prefix
+ * n >= 12 the mixer rotations go in blocks -- qubits 0-7 (the sweep of the
+ * layer's last phase group rotates qubits 0-3, the block's own sweep qubits
+ * 4-7), then four qubits per sweep -- each block's damping drawn from the joint
+ * of its qubits after its rotations (the same Kraus draws as gate by gate; the
+ * state differs by FP32 rounding).  Without shared-prefix
  * mode damping runs are swept gate by gate. */
 qn_status qn_batch_set_fusion(qn_batch *h, int32_t on);
 

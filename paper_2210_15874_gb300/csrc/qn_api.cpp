@@ -448,9 +448,10 @@ void build_gates(qn_batch *h) {
     for (int e = 0; e < E; ++e) h->edges_host.push_back(make_int2(h->edges[2 * e], h->edges[2 * e + 1]));
 }
 
-// Mixer blocks need at least one full block of 256 fibers of three qubits and a
+// Mixer blocks need the block over qubits 0-7 and a full block after it, and a
 // phase group before them (whose apply sweep forms the first block's joint).
 bool mixer_blocks_fit(int n, int E) { return n >= 12 && E > 0; }
+constexpr int kWideBlock = 2 * kMixQ;  // qubits of the layer's first mixer block
 
 // Phase-gate groups of every layer: greedy runs of consecutive ZZ gates whose
 // qubits number at most kMaxGroupQubits (joints of 2^10 bins), at most
@@ -501,13 +502,15 @@ void build_groups(qn_batch *h) {
             h->groups.push_back(z);
         }
         if (!mixer_blocks_fit(n, E)) continue;
-        // mixer rotations in blocks of kMixQ consecutive qubits
-        for (int q = 0; q < n; q += kMixQ) {
+        // mixer rotations in blocks of consecutive qubits: qubits 0-7 first (the sweep of the
+        // layer's last phase group rotates qubits 0-3 and forms this block's joint, the block's
+        // own sweep rotates qubits 4-7), then kMixQ at a time
+        for (int q = 0; q < n; q += q == 0 ? kWideBlock : kMixQ) {
             GateGroup z;
             std::memset(&z, 0, sizeof z);
             z.kind = 1;
             z.g0 = base + E + q;
-            z.m = z.s = std::min(kMixQ, n - q);
+            z.m = z.s = std::min(q == 0 ? kWideBlock : kMixQ, n - q);
             for (int k = 0; k < z.m; ++k) {
                 z.sp[k] = q + k;
                 z.ei[k] = z.ej[k] = k;
@@ -983,10 +986,13 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             // a phase group needs its own joint pass unless the sweep before it
             // (a phase group or the previous layer's last mixer block) formed it
             const bool first = z.kind == 0 && (gi == 0 || h->groups[gi - 1].g0 + h->groups[gi - 1].m != z.g0);
+            // a phase group before the layer's first mixer block (qubits 0-7) also rotates qubits
+            // 0-3 and forms that block's joint (k_group_mix)
+            const bool wide_next = z.kind == 0 && nz && nz->kind == 1 && nz->s == kWideBlock;
             GroupView gv;
             gv.grp = h->gr_dev + gi;
             gv.next = nz && nz->kind == 0 ? h->gr_dev + gi + 1 : nullptr;
-            gv.vq = nz && nz->kind == 1 && z.kind == 0 ? nz->s : 0;
+            gv.vq = nz && nz->kind == 1 && z.kind == 0 && !wide_next ? nz->s : 0;
             gv.vc = nz ? nz->c : 1.0f;
             gv.vs = nz ? nz->sn : 0.0f;
             gv.Hcur = h->gv_H + (size_t)(gi & 1) * h->gv_cap * kGroupBins;
@@ -1027,11 +1033,17 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             const int old_active = active;
             active = *active_host;
             MixMap mm;
+            if (wide_next) {
+                mm = mix_map(n, 0, kMixQ, {4, 5, 6, 7});
+                mm.tanf = std::fabs(nz->c) >= std::fabs(nz->sn);
+            }
             if (z.kind == 1) {
                 std::vector<int> next;
                 if (nz && nz->kind == 1)
                     for (int k = 0; k < nz->s; ++k) next.push_back(nz->sp[k]);
-                mm = mix_map(n, z.sp[0], z.s, next);
+                const bool wide = z.s == kWideBlock;  // its qubits 0-3 were rotated by the sweep before
+                mm = wide ? mix_map(n, kMixQ, kMixQ, next) : mix_map(n, z.sp[0], z.s, next);
+                mm.wide = wide;
                 mm.tanf = std::fabs(z.c) >= std::fabs(z.sn);
                 mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
                 final_norms = final_norms || mm.final_norm;
@@ -1065,8 +1077,9 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                 if (count <= 0) continue;
                 gv.src = part == 0 ? gv.parent : nullptr;
                 gv.slot_base = first;
-                e = z.kind == 0 ? launch_group_apply(v, sv, gv, count, h->stream)
-                                : launch_mix_sweep(v, gv, mm, count, h->stream);
+                e = z.kind == 1 ? launch_mix_sweep(v, gv, mm, count, h->stream)
+                    : wide_next ? launch_group_mix(v, gv, mm, count, h->stream)
+                                : launch_group_apply(v, sv, gv, count, h->stream);
                 h->launches += 1;
             }
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));

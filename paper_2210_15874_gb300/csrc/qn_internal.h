@@ -117,6 +117,8 @@ struct MixMap {
     int32_t tanf;     // |cos beta| >= |sin beta|: rotations in the tan form, else the cot form
     int32_t keep = 0;  // with final_norm: form only the norms and leave the states as they were
                        // (the sigma pass applies the block; full blocks off qubit 0 only)
+    int32_t wide = 0;  // qubits 4-7 of a block over qubits 0-7 whose qubits 0-3 the sweep before
+                       // rotated: the factor table covers all eight (L bits = qubits 1-3)
 };
 
 // The circuit's last mixer block when its sweep kept the states (MixMap::keep):
@@ -313,6 +315,11 @@ cudaError_t launch_group_hist(const BatchView &v, const SlotView &sv, const Grou
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int ns, int active,
                                 double gamma, cudaStream_t s);
 cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s);
+// The last phase group of a layer (gv.grp, its factors in gv.T) applied with the
+// rotations of qubits 0-3 of the layer's first mixer block (angle gv.vc, gv.vs),
+// which covers qubits 0-7: the sweep forms that block's joint in gv.Hnext after
+// rotating qubits 4-7 as well (mm: the tile map of qubits 0-3 with next 4-7).
+cudaError_t launch_group_mix(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s);
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &sv, const GroupView &gv, int active, cudaStream_t s);
 // Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n
 // adding d<C>_t / d theta_param into grad[t * nparam + param] (FP64).

@@ -1212,7 +1212,11 @@ __device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
 // and kMixAny, which reads everything from the map (and stores the final states
 // of a last block it sweeps).  The block holding qubit 0 with a full next block
 // has a kernel of its own (k_mix_first).
-enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixKeep = 4 };
+//   kMixWide  the qubits 4-7 of a block that covers qubits 0-7 (the sweep before
+//             rotated qubits 0-3, k_group_mix): a full next block, and the factor
+//             table of all eight qubits (qubit 0 = the float4 half, qubits 1-3 =
+//             the lane bits L, qubits 4-7 = the element index j)
+enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixKeep = 4, kMixWide = 8 };
 
 template <bool TANF, int VAR>
 __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
@@ -1228,20 +1232,24 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     const GateGroup *nx = kFix ? (VAR == kMixHist ? gv.next : nullptr) : gv.next;
     const bool has0 = kFix ? false : mm.has0 != 0;
     const int M = kFix ? kMixQ : mm.M;
-    const int nN = kFix ? (VAR == kMixMid ? kMixQ : 0) : mm.nN;
+    const int nN = kFix ? ((VAR == kMixMid || VAR == kMixWide) ? kMixQ : 0) : mm.nN;
     const bool final_norm = kFix ? VAR == kMixKeep : mm.final_norm != 0;
     const float c = gv.grp->c, sn = gv.grp->sn;
     const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;  // rotation = rsc * (tangent form)
     float scM = 1.0f;  // rsc^M: the block's rotations, folded into its factors
     for (int i = 0; i < M; ++i) scM *= rsc;
-    __shared__ float Df[16];
+    constexpr int kDf = VAR == kMixWide ? 256 : 16;
+    __shared__ float Df[kDf];
     // the block's histogram of the next phase group's joint (variants that form one; 2^-60
     // fixed point, one row for all warps), and the per-warp rows of the next mixer block's joint
     constexpr bool kHist = VAR == kMixAny || VAR == kMixHist;
     __shared__ unsigned long long hist[kHist ? kGroupBins : 1];
     __shared__ float red[kWarps * kJointBins];
-    if (threadIdx.x < 16u)
+    if (VAR == kMixWide) {
+        for (int i = threadIdx.x; i < kDf; i += kMixThreads) Df[i] = gv.T[(size_t)slot * kGroupBins + i].x * scM;
+    } else if (threadIdx.x < 16u) {
         Df[threadIdx.x] = threadIdx.x < (1u << M) ? gv.T[(size_t)slot * kGroupBins + threadIdx.x].x * scM : 0.0f;
+    }
     if (nx)
         for (int i = threadIdx.x; i < kGroupBins; i += kMixThreads) hist[i] = 0ull;
     // float4 indices fit 32 bits (n <= 30)
@@ -1373,7 +1381,11 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
 #pragma unroll
         for (int j = 0; j < kMixE; ++j) {
             const int d = j & dmask;
-            const float f0 = has0 ? Df[d << 1] : Df[d], f1 = has0 ? Df[(d << 1) | 1] : Df[d];
+            float f0 = has0 ? Df[d << 1] : Df[d], f1 = has0 ? Df[(d << 1) | 1] : Df[d];
+            if (VAR == kMixWide) {  // qubit 0 the half, qubits 1-3 the lane bits L, qubits 4-7 j
+                f0 = Df[(j << 4) | (tL << 1)];
+                f1 = Df[(j << 4) | (tL << 1) | 1];
+            }
             if (VAR == kMixKeep) {  // nothing stored: |f x|^2 as the sigma pass forms it
                 df_add(nh, nl, prob_of(f0, x[j].x, x[j].y));
                 df_add(nh, nl, prob_of(f1, x[j].z, x[j].w));
@@ -1609,6 +1621,136 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_first(BatchView v, Group
     }
     __syncthreads();
     lane_joint_commit(kMixE, kWarps, red, gv.Hnext + (size_t)slot * kGroupBins);
+}
+
+// The last phase group of a layer, applied together with the rotations of
+// qubits 0-3 of the layer's first mixer block, whose other four qubits (4-7)
+// the next sweep rotates: that block covers qubits 0-7 and its Kraus draws
+// come from the joint of all eight after their rotations (the same draws as
+// gate by gate: an op on one qubit commutes with rotations of the others), which
+// this sweep forms by rotating qubits 4-7 in registers without keeping them.
+// Tile and lanes as in k_mix_first: qubit 0 inside the float4, qubits 1-3 lane
+// bits 0-2, qubits 4-7 the register index j, f7-f10 lane bits 3-4 and the warp.
+// Per element: the phase group's factor T[stored bits of S] (and rsc^4 of the
+// tangent-form rotations), the rotations of qubits 0-3, the store; then the
+// rotations of qubits 4-7, binned by the stored bits of qubits 0-7 (256 bins:
+// e | lane bits 0-2 << 1 | j << 4).  No pending op (the gate before is a group).
+template <bool TANF>
+__global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, GroupView gv, MixMap mm) {
+    extern __shared__ float4 mix_buf[];  // [2][kMixE][kMixThreads]
+    constexpr int kWarps = kMixThreads / 32;
+    static_assert(kMixThreads == 128 && kMixE == 16 && kMixQ == 4, "the tile is f0-f10: 16 float4 x 128 threads");
+    grid_dependency_wait();
+    const int slot = blockIdx.y + gv.slot_base;
+    const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const GateGroup *gp = gv.grp;
+    const float c = gv.vc, sn = gv.vs;  // the mixer layer's angle
+    const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;
+    float scM = 1.0f;  // rsc^4: the tangent-form rotations of qubits 0-3, folded into T
+    for (int i = 0; i < kMixQ; ++i) scM *= rsc;
+    __shared__ float2 Ts[kGroupBins];
+    __shared__ uint16_t binj[kMixE];
+    float *red = reinterpret_cast<float *>(mix_buf);  // [kWarps][256], after the tile loop
+    for (int i = threadIdx.x; i < (1 << gp->s); i += kMixThreads) {
+        const float2 t = gv.T[(size_t)slot * kGroupBins + i];
+        Ts[i] = make_float2(t.x * scM, t.y * scM);
+    }
+    if (threadIdx.x < (unsigned)kMixE) binj[threadIdx.x] = (uint16_t)group_bin(gp, 2u * (threadIdx.x << 3));
+    const int bin1 = group_bin(gp, 1u);
+    const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)from << v.n));
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << v.n));
+    const int nsubs = mm.ntile >= 2 ? kMixSubs : (1 << mm.ntile);
+    uint32_t tbits = 0;  // tile bits of the block's first tile
+    {
+        const uint32_t t0 = blockIdx.x * nsubs;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
+            if (i < mm.ntile) tbits |= ((t0 >> i) & 1u) << mm.ftile[i];
+    }
+    const uint32_t ts1 = mm.ntile > 0 ? 1u << mm.ftile[0] : 0u;
+    const uint32_t ts2 = mm.ntile > 1 ? 1u << mm.ftile[1] : 0u;
+    const uint32_t fth = (uint32_t)(lane & 7) | ((uint32_t)(lane >> 3) << 7) | ((uint32_t)warp << 9);
+    auto tile_f = [&](int sub) { return tbits | ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u) | fth; };
+    auto fetch = [&](int sub) {
+        const uint32_t fb = tile_f(sub);
+        float4 *buf = mix_buf + (sub & 1) * kMixTile + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) cp_async16(buf + j * kMixThreads, q4 + (fb | ((uint32_t)j << 3)));
+        cp_async_commit();
+    };
+    float acc0[kMixE], acc1[kMixE];  // |.|^2 after the rotations of qubits 4-7 by j, for qubit 0 = 0 / 1
+#pragma unroll
+    for (int j = 0; j < kMixE; ++j) acc0[j] = acc1[j] = 0.0f;
+    fetch(0);
+    __syncthreads();  // Ts, binj
+    for (int sub = 0; sub < nsubs; ++sub) {
+        if (sub + 1 < nsubs) {
+            fetch(sub + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const float4 *buf = mix_buf + (sub & 1) * kMixTile + threadIdx.x;
+        const uint32_t fb = tile_f(sub);
+        const int binb = group_bin(gp, 2u * fb);  // the bits of S outside j and qubit 0
+        float4 x[kMixE];
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) {
+            const float4 a = buf[j * kMixThreads];
+            const int bj = binb | binj[j];
+            const float2 w0 = Ts[bj], w1 = Ts[bj | bin1];
+            x[j].x = a.x * w0.x - a.y * w0.y;
+            x[j].y = a.x * w0.y + a.y * w0.x;
+            x[j].z = a.z * w1.x - a.w * w1.y;
+            x[j].w = a.z * w1.y + a.w * w1.x;
+        }
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) rx_pair_t<TANF>(x[j].x, x[j].y, x[j].z, x[j].w, rt);  // qubit 0
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {  // qubits 1-3
+#pragma unroll
+            for (int j = 0; j < kMixE; ++j) rx_lanes_t<TANF>(x[j], 1 << i, rt);
+        }
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) p4[fb | ((uint32_t)j << 3)] = x[j];
+        // the rotations of qubits 4-7, kept only as squared magnitudes
+#pragma unroll
+        for (int i = 0; i < kMixQ; ++i) {
+#pragma unroll
+            for (int j = 0; j < kMixE; ++j)
+                if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
+        }
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) {
+            acc0[j] += x[j].x * x[j].x + x[j].y * x[j].y;
+            acc1[j] += x[j].z * x[j].z + x[j].w * x[j].w;
+        }
+    }
+    allow_dependent_launch();
+    float sc2 = 1.0f;  // qubits 4-7 were rotated up to rsc each: restore |.|^2
+    for (int i = 0; i < kMixQ; ++i) sc2 *= rsc * rsc;
+    __syncthreads();  // every thread is done with the tile buffers, which now hold the per-warp bins
+    // sum over lane bits 3-4 (f7-f8); lanes 0-7 then hold the bins of their qubits 1-3
+#pragma unroll
+    for (int j = 0; j < kMixE; ++j) {
+        float a = acc0[j] * sc2, b = acc1[j] * sc2;
+        a += __shfl_xor_sync(0xffffffffu, a, 8);
+        a += __shfl_xor_sync(0xffffffffu, a, 16);
+        b += __shfl_xor_sync(0xffffffffu, b, 8);
+        b += __shfl_xor_sync(0xffffffffu, b, 16);
+        if (lane < 8) {
+            red[warp * 256 + ((j << 4) | (lane << 1))] = a;
+            red[warp * 256 + ((j << 4) | (lane << 1) | 1)] = b;
+        }
+    }
+    __syncthreads();
+    unsigned long long *H = gv.Hnext + (size_t)slot * kGroupBins;
+    for (int b = threadIdx.x; b < 256; b += kMixThreads) {
+        double sum = 0.0;
+        for (int w = 0; w < kWarps; ++w) sum += (double)red[w * 256 + b];
+        if (sum > 0.0) atomicAdd(H + b, __double2ull_rn(sum * kHistScale));
+    }
 }
 
 __device__ __forceinline__ float warp_sumf(float x) {
@@ -3236,23 +3378,41 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
     return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
 }
 
-cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
+// The mixer sweeps' dynamic shared memory (two tiles), set once for every variant.
+static cudaError_t launch_mix_sweep_attrs() {
     static const cudaError_t attr = [] {
         const void *ks[] = {(const void *)k_mix_sweep<true, kMixAny>,   (const void *)k_mix_sweep<true, kMixMid>,
                             (const void *)k_mix_sweep<true, kMixHist>,  (const void *)k_mix_sweep<true, kMixKeep>,
                             (const void *)k_mix_sweep<false, kMixAny>,  (const void *)k_mix_sweep<false, kMixMid>,
                             (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixKeep>,
-                            (const void *)k_mix_first<true>,            (const void *)k_mix_first<false>};
+                            (const void *)k_mix_sweep<true, kMixWide>,  (const void *)k_mix_sweep<false, kMixWide>,
+                            (const void *)k_mix_first<true>,            (const void *)k_mix_first<false>,
+                            (const void *)k_group_mix<true>,            (const void *)k_group_mix<false>};
         for (const void *k : ks) {
             const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     }();
+    return attr;
+}
+
+cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
+    const cudaError_t attr = launch_mix_sweep_attrs();
     if (attr != cudaSuccess) return attr;
     const unsigned blocks = mm.ntile >= 2 ? (1u << mm.ntile) / kMixSubs : 1u;
     const dim3 grid(blocks, (unsigned)active), block(kMixThreads);
     int var = kMixAny;
+    if (mm.wide) {
+        // qubits 4-7 with the factors of qubits 0-7: the lane bits must be qubits 1-3, the block
+        // qubits 4-7 and a full next block
+        const bool ok = mm.M == kMixQ && !mm.has0 && mm.nN == kMixQ && !gv.next && !mm.final_norm &&
+                        mm.fL[0] == 0 && mm.fL[1] == 1 && mm.fL[2] == 2 && mm.fA[0] == 3 && mm.fA[1] == 4 &&
+                        mm.fA[2] == 5 && mm.fA[3] == 6;
+        if (!ok) return cudaErrorInvalidValue;
+        return mm.tanf ? launch_pdl_smem(k_mix_sweep<true, kMixWide>, grid, block, kMixSmem, s, v, gv, mm)
+                       : launch_pdl_smem(k_mix_sweep<false, kMixWide>, grid, block, kMixSmem, s, v, gv, mm);
+    }
     if (mm.M == kMixQ) {
         const bool next_full = mm.nN == kMixQ && !gv.next && !mm.final_norm;
         const bool natural = mm.fA[0] == 0 && mm.fA[1] == 1 && mm.fA[2] == 2 && mm.fA[3] == 7 && mm.fB[0] == 3 &&
@@ -3274,6 +3434,19 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
     default: return mm.tanf ? QN_MIX(true, kMixAny) : QN_MIX(false, kMixAny);
     }
 #undef QN_MIX
+}
+
+cudaError_t launch_group_mix(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
+    cudaError_t e = launch_mix_sweep_attrs();
+    if (e != cudaSuccess) return e;
+    const bool natural = mm.has0 && mm.M == kMixQ && mm.nN == kMixQ && mm.fA[0] == 0 && mm.fA[1] == 1 &&
+                         mm.fA[2] == 2 && mm.fA[3] == 7 && mm.fB[0] == 3 && mm.fB[1] == 4 && mm.fB[2] == 5 &&
+                         mm.fB[3] == 6 && mm.fL[0] == 8 && mm.fL[1] == 9 && mm.fL[2] == 10;
+    if (!natural || gv.pend) return cudaErrorInvalidValue;
+    const unsigned blocks = mm.ntile >= 2 ? (1u << mm.ntile) / kMixSubs : 1u;
+    const dim3 grid(blocks, (unsigned)active), block(kMixThreads);
+    return mm.tanf ? launch_pdl_smem(k_group_mix<true>, grid, block, kMixSmem, s, v, gv, mm)
+                   : launch_pdl_smem(k_group_mix<false>, grid, block, kMixSmem, s, v, gv, mm);
 }
 
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {

@@ -51,6 +51,7 @@ constexpr int kTcRawBytes = 64 * kTcPitch * 4;     // one staged tile: 17408 B
 constexpr int kTcOpBytes = 128 * 128;              // one K-major operand: 128 rows x 128 B
 constexpr int kTcBBytes = 32 * 128;                // H5 (BF16: [H5 | H5]): 32 rows x 128 B
 constexpr uint32_t kTcCols = 64;                   // TMEM columns: D1 0..31, D2 32..63
+constexpr int kTcChunk = 8;                        // consecutive tiles per block (one staged ahead)
 
 template <int KIND>
 __host__ __device__ constexpr int tc_ops() { return KIND == kPrecTF32 ? 1 : 2; }
@@ -300,11 +301,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks<KIND>()) k_tc_sweep(B
     uint32_t phase = 0;
     bool aborted = false;
     int slot = 0;
-    if ((int)blockIdx.x < units) fetch(blockIdx.x, 0);
-    for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
-        const int next = unit + gridDim.x;
+    const int ubeg = (int)blockIdx.x * kTcChunk;
+    const int uend = ubeg + kTcChunk < units ? ubeg + kTcChunk : units;
+    if (ubeg < uend) fetch(ubeg, 0);
+    for (int unit = ubeg; unit < uend; ++unit) {
+        const int next = unit + 1;
         __syncthreads();  // the other buffer's last tile has been stored
-        if (next < units) {
+        if (next < uend) {
             fetch(next, slot ^ 1);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
@@ -428,25 +431,19 @@ cudaError_t tc_launch(const BatchView &v, const LayerView &Lp, const LayerView &
                       const TcSweep &sw, cudaStream_t s) {
     auto kern = k_tc_sweep<KIND, PRE, POST>;
     constexpr int smem = tc_smem_bytes<KIND>();
-    static const int per_sm = [&] {  // once per instantiation, on first use
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static const cudaError_t attr = [&] {  // once per instantiation, on first use
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTcThreads, smem);
-        if (e != cudaSuccess || per < 1) {
-            cudaGetLastError();
-            per = kTcMinBlocks<KIND>();  // what the launch bounds were compiled for
-        }
-        // TMEM holds 512 columns per SM: never more resident blocks than that admits
-        if (per > 512 / (int)kTcCols) per = 512 / (int)kTcCols;
-        return (sms > 0 ? sms : 152) * per;
+        return e;
     }();
+    if (attr != cudaSuccess) return attr;
+    // kTcChunk consecutive tiles per block; the hardware keeps as many blocks resident as
+    // registers, shared memory and TMEM (64 of 512 columns each) admit
     const int64_t units = (int64_t)v.b << (v.n - 11);
-    const int blocks = (int)(units < per_sm ? units : per_sm);
+    const int64_t blocks = (units + kTcChunk - 1) / kTcChunk;
     if (blocks <= 0) return cudaSuccess;
-    kern<<<blocks, kTcThreads, smem, s>>>(v, Lp, Lr, Lq, sw);
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    kern<<<(unsigned)blocks, kTcThreads, smem, s>>>(v, Lp, Lr, Lq, sw);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,9 @@ sweeps (qn_mix_tile_map).
 The groups must cover the circuit's gates exactly once and in circuit order:
 consecutive phase gates of one layer on at most 10 qubits and at most 12 gates,
 each group ending only where the next gate would break a limit or the layer
-ends; for n >= 12, consecutive mixer rotations in blocks of four qubits.  A
+ends; for n >= 12, consecutive mixer rotations in blocks: qubits 0-7 (the sweep
+of the layer's last phase group rotates qubits 0-3 and forms the block's joint),
+then four qubits at a time.  A
 tile map must be a bijection of the float4-index bits that puts the block's
 qubits on its A bits and the next block's qubits on its B bits, which is what
 the sweep's register pairs rely on."""
@@ -14,7 +16,7 @@ import pytest
 
 from paper_2210_15874_gb300 import workloads as W
 
-MAX_QUBITS, MAX_GATES, BLOCK = 10, 12, 4
+MAX_QUBITS, MAX_GATES, BLOCK, WIDE = 10, 12, 4, 8
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +66,11 @@ def test_group_plan_covers_the_circuit(qn, name):
             assert n >= 12
             rot = [x - (n + layer * (E + n) + E) for x in gates]  # qubit of each rotation
             assert rot == list(range(rot[0], rot[0] + len(rot))) and rot[0] % BLOCK == 0
-            assert len(rot) == min(BLOCK, n - rot[0]) and g["qubits"] == rot
+            if rot[0] == 0:
+                assert len(rot) == WIDE and g["qubits"] == rot
+                assert plan[plan.index(g) - 1]["kind"] == 0  # a phase group's sweep starts it
+            else:
+                assert len(rot) == min(BLOCK, n - rot[0]) and g["qubits"] == rot
     expected = sorted(phase_gate)
     if n >= 12:  # the mixer rotations are grouped too
         expected = sorted(expected + [n + l * (E + n) + E + q for l in range(p) for q in range(n)])
