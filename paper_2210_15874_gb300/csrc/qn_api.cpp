@@ -992,7 +992,6 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             GroupView gv;
             gv.grp = h->gr_dev + gi;
             gv.next = nz && nz->kind == 0 ? h->gr_dev + gi + 1 : nullptr;
-            gv.vq = nz && nz->kind == 1 && z.kind == 0 && !wide_next ? nz->s : 0;
             gv.vc = nz ? nz->c : 1.0f;
             gv.vs = nz ? nz->sn : 0.0f;
             gv.Hcur = h->gv_H + (size_t)(gi & 1) * h->gv_cap * kGroupBins;

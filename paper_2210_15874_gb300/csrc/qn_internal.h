@@ -154,9 +154,8 @@ struct GroupView {
     int32_t slot_base;       // first slot of the launch (blockIdx.y + slot_base)
     int32_t pend;            // the gate before the group may have left a pending op
     int32_t *parent;         // [max_slots] decide writes each new slot's parent here
-    int32_t vq;              // > 0: the apply sweep accumulates instead the joint of the
-                             // mixer block on qubits 0 .. vq-1 after rotations (vc, vs)
-    float vc, vs;
+    float vc, vs;            // cos, sin of the mixer angle whose rotations of qubits 0-3 the
+                             // layer's last phase-group sweep applies (k_group_mix)
     unsigned long long *Hcur;   // [max_slots][kGroupBins] joint of this group, fixed point 2^-60
     unsigned long long *Hnext;  // [max_slots][kGroupBins] joint of the next group (zero on entry)
     float2 *T;             // [max_slots][kGroupBins] amplitude factor by stored bits of S

@@ -1011,40 +1011,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
     hist_commit(&hw[0][0], gb, gv.Hcur + (size_t)slot * kGroupBins);
 }
 
-// exp(-i beta X) on the amplitude pair (a, b) of one qubit: a' = c a - i s b,
-// b' = c b - i s a.
-__device__ __forceinline__ void rx_pair(float &ar, float &ai, float &br, float &bi, float c, float s) {
-    const float nar = c * ar + s * bi, nai = c * ai - s * br;
-    const float nbr = c * br + s * ai, nbi = c * bi - s * ar;
-    ar = nar;
-    ai = nai;
-    br = nbr;
-    bi = nbi;
-}
-
-// The same rotation on a qubit whose two values sit in lanes that differ in
-// `lanebit` (every lane of the warp takes part).
-__device__ __forceinline__ void rx_lanes(float4 &o, int lanebit, float c, float s) {
-    const float px = __shfl_xor_sync(0xffffffffu, o.x, lanebit), py = __shfl_xor_sync(0xffffffffu, o.y, lanebit);
-    const float pz = __shfl_xor_sync(0xffffffffu, o.z, lanebit), pw = __shfl_xor_sync(0xffffffffu, o.w, lanebit);
-    o.x = c * o.x + s * py;
-    o.y = c * o.y - s * px;
-    o.z = c * o.z + s * pw;
-    o.w = c * o.w - s * pz;
-}
-
-// Per-block joint of a mixer block whose qubits sit on lane bits.  put: this
-// lane's sum `acc` for bin `bin`, summed first over the lanes that differ only
-// in `lmask`, goes to the warp's row of hw[warps][kJointBins].  commit (after a block
-// barrier): warps summed in fixed order, the block's 2^nb bins added to H.
+// Per-block joint of a mixer block (at most 4 qubits): the per-warp rows
+// hw[warps][kJointBins] are summed in fixed order (after a block barrier) and the
+// block's 2^nb bins added to H as 2^-60 fixed-point integers.
 constexpr int kJointBins = 16;  // bins of a mixer block's joint (at most 4 qubits)
-
-__device__ __forceinline__ void lane_joint_put(float acc, int bin, unsigned lmask, float *hw) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-        if ((lmask >> i) & 1u) acc += __shfl_xor_sync(0xffffffffu, acc, 1 << i);
-    if (((threadIdx.x & 31u) & lmask) == 0u) hw[(threadIdx.x >> 5) * kJointBins + bin] = acc;
-}
 
 __device__ __forceinline__ void lane_joint_commit(int nb, int warps, const float *hw, unsigned long long *H) {
     if ((int)threadIdx.x < nb) {
@@ -1055,13 +1025,10 @@ __device__ __forceinline__ void lane_joint_commit(int nb, int warps, const float
 }
 
 // Apply a phase group: phi_y *= D(y) * T[slot][stored bits of S], D the pending
-// op of the gate before the group.  Then accumulate either the next phase
-// group's joint (gv.next) or the joint of the mixer block on qubits 0 .. vq-1
-// as it will be after that block's rotations (gv.vq > 0): qubit 0 is the pair
-// inside a float4, qubits 1 .. 3 are lane bits 0 .. 2 of the sweep layout.
-// PEND: the gate before left a pending op (else it is the identity and skipped).
-// NEXT: the joint this sweep forms -- 0 none, 1 the next phase group's, 2 the
-// first mixer block's after its rotations.
+// op of the gate before the group, and accumulate the next phase group's joint
+// (NEXT = 1, gv.next) on the way.  PEND: the gate before left a pending op
+// (else it is the identity and skipped).  The last phase group of a layer is
+// applied by k_group_mix instead, which also starts the mixer layer.
 template <bool PEND, int NEXT>
 __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupView gv) {
     grid_dependency_wait();
@@ -1069,7 +1036,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
     const GateGroup *gp = gv.grp;
     const GateGroup *nx = NEXT == 1 ? gv.next : nullptr;
-    const int vq = NEXT == 2 ? gv.vq : 0;
     __shared__ float2 Ts[kGroupBins];
     __shared__ float hw[kThreads / 32][kGroupBins];
     __shared__ uint16_t vT[2 * 4 * kGSub], vN[2 * 4 * kGSub];
@@ -1090,9 +1056,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     float *my = hw[threadIdx.x >> 5];
     const int tE1 = vT[1];
     const int nE1 = NEXT == 1 ? vN[1] : 0;
-    const float vc = gv.vc, vs = gv.vs;
     HistRun run;
-    float va0 = 0.0f, va1 = 0.0f;
     float4 cur[kF4PerThread], nxt[kF4PerThread];
     load_tile(cur, q4, fbase, nf);
 #pragma unroll
@@ -1118,14 +1082,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
             }
             if (NEXT == 1) hist_push(my, gn, nE1, vN[(k << 1) | (sub << 3)], o.x * o.x + o.y * o.y, o.z * o.z + o.w * o.w,
                               run);
-            if (NEXT == 2) {
-                rx_pair(o.x, o.y, o.z, o.w, vc, vs);
-                if (vq > 1) rx_lanes(o, 1, vc, vs);
-                if (vq > 2) rx_lanes(o, 2, vc, vs);
-                if (vq > 3) rx_lanes(o, 4, vc, vs);
-                va0 += o.x * o.x + o.y * o.y;
-                va1 += o.z * o.z + o.w * o.w;
-            }
         }
         if (sub + 1 < kGSub) {
 #pragma unroll
@@ -1136,16 +1092,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     __syncthreads();
     allow_dependent_launch();
     if (NEXT == 1) hist_commit(&hw[0][0], gn, gv.Hnext + (size_t)slot * kGroupBins);
-    if (NEXT == 2) {
-        // bins: qubit 0 = e, qubits 1 .. vq-1 = lane bits 0 .. vq-2
-        const unsigned lq = (1u << (vq > 0 ? vq - 1 : 0)) - 1u;
-        const unsigned lmask = 31u & ~lq;
-        const int lb = (int)((threadIdx.x & 31u) & lq) << 1;
-        lane_joint_put(va0, lb, lmask, &hw[0][0]);
-        lane_joint_put(va1, lb | 1, lmask, &hw[0][0]);
-        __syncthreads();
-        lane_joint_commit(1 << vq, kThreads / 32, &hw[0][0], gv.Hnext + (size_t)slot * kGroupBins);
-    }
 }
 
 // 16-byte asynchronous global -> shared copies (the copy engine of the SM
@@ -1210,8 +1156,7 @@ __device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
 //             stores nothing (the states stay as they were; the sigma pass,
 //             k_probs_mix, applies the block again on the fly)
 // and kMixAny, which reads everything from the map (and stores the final states
-// of a last block it sweeps).  The block holding qubit 0 with a full next block
-// has a kernel of its own (k_mix_first).
+// of a last block it sweeps); and
 //   kMixWide  the qubits 4-7 of a block that covers qubits 0-7 (the sweep before
 //             rotated qubits 0-3, k_group_mix): a full next block, and the factor
 //             table of all eight qubits (qubit 0 = the float4 half, qubits 1-3 =
@@ -1517,119 +1462,13 @@ __device__ __forceinline__ void rx_lanes_t(float4 &o, int lanebit, float t) {
     }
 }
 
-// Mixer block on qubits 0-3 followed by a full block on qubits 4-7 (shared-prefix
-// mode, n >= 12).  The tile is the contiguous float4 bits f0-f10: qubit 0 is the
-// pair inside a float4, qubits 1-3 (f0-f2) are lane bits 0-2, the next block's
-// qubits 4-7 (f3-f6) are the register index j, and f7-f10 are lane bits 3-4
-// and the warp.  So every copy and store is a run of 128 bytes, qubits 1-3
-// rotate across lanes by shuffles, and the next block's rotations and joint
-// stay in registers.  A thread stages only its own float4 (cp.async, one tile
-// ahead) and reads back only those, so the tile loop takes no block barrier.
-// Same operations per amplitude as k_mix_sweep: qubit 0, then 1, 2, 3, then the
-// block's factors; the next block's qubits in order 4 .. 7.
-template <bool TANF>
-__global__ void __launch_bounds__(kMixThreads, 3) k_mix_first(BatchView v, GroupView gv, MixMap mm) {
-    extern __shared__ float4 mix_buf[];  // [2][kMixE][kMixThreads]
-    constexpr int kWarps = kMixThreads / 32;
-    static_assert(kMixThreads == 128 && kMixE == 16 && kMixQ == 4, "the tile is f0-f10: 16 float4 x 128 threads");
-    grid_dependency_wait();
-    const int slot = blockIdx.y + gv.slot_base;
-    const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float c = gv.grp->c, sn = gv.grp->sn;
-    const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;
-    float scM = 1.0f;  // rsc^4: the block's rotations, folded into its factors
-    for (int i = 0; i < kMixQ; ++i) scM *= rsc;
-    __shared__ float Df[16];
-    __shared__ float red[kWarps * kJointBins];
-    if (threadIdx.x < 16u) Df[threadIdx.x] = gv.T[(size_t)slot * kGroupBins + threadIdx.x].x * scM;
-    const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)from << v.n));
-    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)slot << v.n));
-    const int nsubs = mm.ntile >= 2 ? kMixSubs : (1 << mm.ntile);
-    uint32_t tbits = 0;  // tile bits of the block's first tile
-    {
-        const uint32_t t0 = blockIdx.x * nsubs;
-#pragma unroll
-        for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
-            if (i < mm.ntile) tbits |= ((t0 >> i) & 1u) << mm.ftile[i];
-    }
-    const uint32_t ts1 = mm.ntile > 0 ? 1u << mm.ftile[0] : 0u;
-    const uint32_t ts2 = mm.ntile > 1 ? 1u << mm.ftile[1] : 0u;
-    // this thread's float4 of a tile, j = 0: f0-f2 lane bits 0-2, f7-f8 lane bits 3-4, f9-f10 the warp
-    const uint32_t fth = (uint32_t)(lane & 7) | ((uint32_t)(lane >> 3) << 7) | ((uint32_t)warp << 9);
-    auto tile_f = [&](int sub) { return tbits | ((sub & 1) ? ts1 : 0u) | ((sub & 2) ? ts2 : 0u) | fth; };
-    auto fetch = [&](int sub) {
-        const uint32_t fb = tile_f(sub);
-        float4 *buf = mix_buf + (sub & 1) * kMixTile + threadIdx.x;
-#pragma unroll
-        for (int j = 0; j < kMixE; ++j) cp_async16(buf + j * kMixThreads, q4 + (fb | ((uint32_t)j << 3)));
-        cp_async_commit();
-    };
-    float acc[kMixE];  // sum of |.|^2 after the next block's rotations, by its qubits (j)
-#pragma unroll
-    for (int j = 0; j < kMixE; ++j) acc[j] = 0.0f;
-    fetch(0);
-    __syncthreads();  // Df
-    const int d = lane & 7;  // qubits 1-3
-    const float g0 = Df[d << 1], g1 = Df[(d << 1) | 1];
-    for (int sub = 0; sub < nsubs; ++sub) {
-        if (sub + 1 < nsubs) {
-            fetch(sub + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        const float4 *buf = mix_buf + (sub & 1) * kMixTile + threadIdx.x;
-        float4 x[kMixE];
-#pragma unroll
-        for (int j = 0; j < kMixE; ++j) x[j] = buf[j * kMixThreads];
-#pragma unroll
-        for (int j = 0; j < kMixE; ++j) rx_pair_t<TANF>(x[j].x, x[j].y, x[j].z, x[j].w, rt);  // qubit 0
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {  // qubits 1-3
-#pragma unroll
-            for (int j = 0; j < kMixE; ++j) rx_lanes_t<TANF>(x[j], 1 << i, rt);
-        }
-        const uint32_t fb = tile_f(sub);
-#pragma unroll
-        for (int j = 0; j < kMixE; ++j) {
-            x[j].x *= g0;
-            x[j].y *= g0;
-            x[j].z *= g1;
-            x[j].w *= g1;
-            p4[fb | ((uint32_t)j << 3)] = x[j];
-        }
-        // the next block's rotations, kept only as squared magnitudes
-#pragma unroll
-        for (int i = 0; i < kMixQ; ++i) {
-#pragma unroll
-            for (int j = 0; j < kMixE; ++j)
-                if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
-        }
-#pragma unroll
-        for (int j = 0; j < kMixE; ++j) acc[j] += x[j].x * x[j].x + x[j].y * x[j].y + x[j].z * x[j].z + x[j].w * x[j].w;
-    }
-    allow_dependent_launch();
-    float sc2 = 1.0f;  // the next block's rotations were taken up to rsc each: restore |.|^2
-    for (int i = 0; i < kMixQ; ++i) sc2 *= rsc * rsc;
-#pragma unroll
-    for (int b = 0; b < kMixE; ++b) {
-        float x = acc[b] * sc2;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        if (lane == 0) red[warp * kJointBins + b] = x;
-    }
-    __syncthreads();
-    lane_joint_commit(kMixE, kWarps, red, gv.Hnext + (size_t)slot * kGroupBins);
-}
-
 // The last phase group of a layer, applied together with the rotations of
 // qubits 0-3 of the layer's first mixer block, whose other four qubits (4-7)
 // the next sweep rotates: that block covers qubits 0-7 and its Kraus draws
 // come from the joint of all eight after their rotations (the same draws as
 // gate by gate: an op on one qubit commutes with rotations of the others), which
 // this sweep forms by rotating qubits 4-7 in registers without keeping them.
-// Tile and lanes as in k_mix_first: qubit 0 inside the float4, qubits 1-3 lane
+// Tile: the contiguous f bits 0-10 -- qubit 0 inside the float4, qubits 1-3 lane
 // bits 0-2, qubits 4-7 the register index j, f7-f10 lane bits 3-4 and the warp.
 // Per element: the phase group's factor T[stored bits of S] (and rsc^4 of the
 // tangent-form rotations), the rotations of qubits 0-3, the store; then the
@@ -3386,7 +3225,6 @@ static cudaError_t launch_mix_sweep_attrs() {
                             (const void *)k_mix_sweep<false, kMixAny>,  (const void *)k_mix_sweep<false, kMixMid>,
                             (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixKeep>,
                             (const void *)k_mix_sweep<true, kMixWide>,  (const void *)k_mix_sweep<false, kMixWide>,
-                            (const void *)k_mix_first<true>,            (const void *)k_mix_first<false>,
                             (const void *)k_group_mix<true>,            (const void *)k_group_mix<false>};
         for (const void *k : ks) {
             const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem);
@@ -3415,13 +3253,6 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
     }
     if (mm.M == kMixQ) {
         const bool next_full = mm.nN == kMixQ && !gv.next && !mm.final_norm;
-        const bool natural = mm.fA[0] == 0 && mm.fA[1] == 1 && mm.fA[2] == 2 && mm.fA[3] == 7 && mm.fB[0] == 3 &&
-                             mm.fB[1] == 4 && mm.fB[2] == 5 && mm.fB[3] == 6 && mm.fL[0] == 8 && mm.fL[1] == 9 &&
-                             mm.fL[2] == 10;
-        if (next_full && mm.has0 && natural) {
-            return mm.tanf ? launch_pdl_smem(k_mix_first<true>, grid, block, kMixSmem, s, v, gv, mm)
-                           : launch_pdl_smem(k_mix_first<false>, grid, block, kMixSmem, s, v, gv, mm);
-        }
         if (next_full && !mm.has0) var = kMixMid;
         else if (!mm.has0 && mm.nN == 0 && gv.next && !mm.final_norm) var = kMixHist;
         else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm && mm.keep) var = kMixKeep;
@@ -3451,10 +3282,10 @@ cudaError_t launch_group_mix(const BatchView &v, const GroupView &gv, const MixM
 
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
     const dim3 grid(group_tiles(v.n), (unsigned)active), blk(kThreads);
-    const int next = gv.next ? 1 : (gv.vq > 0 ? 2 : 0);
+    const int next = gv.next ? 1 : 0;
 #define QN_APPLY(P, N) launch_pdl(k_group_apply<P, N>, grid, blk, s, v, gv)
-    if (gv.pend) return next == 1 ? QN_APPLY(true, 1) : next == 2 ? QN_APPLY(true, 2) : QN_APPLY(true, 0);
-    return next == 1 ? QN_APPLY(false, 1) : next == 2 ? QN_APPLY(false, 2) : QN_APPLY(false, 0);
+    if (gv.pend) return next == 1 ? QN_APPLY(true, 1) : QN_APPLY(true, 0);
+    return next == 1 ? QN_APPLY(false, 1) : QN_APPLY(false, 0);
 #undef QN_APPLY
 }
 
