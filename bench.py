@@ -381,7 +381,7 @@ def gpu_arm(args):
         fused = main_mode[1] and w.damping == 0
         grouped = sharing and main_mode[1] and main["groups"]["launches"] > 0
         blocks = grouped and main["mixers"]["launches"] > 0
-        kname = "k_mix_sweep + k_mix_first (mixer blocks of 4 qubits over live prefix states, 16 B per amplitude)" if blocks else \
+        kname = "k_mix_sweep (mixer blocks over live prefix states: qubits 4-7 of the block over 0-7, then 4 qubits per sweep; 16 B per amplitude)" if blocks else \
             "k_slot_sweep (mixer gate sweeps over live prefix states)" if grouped else \
             "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
             (("k_tc_sweep (tensor-core windows of 5 qubits, %s, 16 B per amplitude)" %
@@ -416,8 +416,8 @@ def gpu_arm(args):
             "clocks": main["clocks"],
         }
         if grouped:
-            line["roofline_phase_groups"] = roof(main, "k_group_apply + k_group_hist (phase-group sweeps, 16 B and "
-                                                       "8 B per amplitude)", "groups")
+            line["roofline_phase_groups"] = roof(main, "k_group_apply + k_group_mix + k_group_hist (phase-group "
+                                                       "sweeps, 16 B and 8 B per amplitude)", "groups")
         if other is not None:
             key = "per_trajectory_mode" if sharing else "per_gate_mode"
             line[key] = {
