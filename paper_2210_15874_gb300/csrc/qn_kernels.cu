@@ -3209,6 +3209,8 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
         QN_GD(1)
     } else if (ns <= 7) {
         QN_GD(4)
+    } else if (ns <= 8) {  // the 8-qubit first mixer block, and 8-qubit phase groups
+        QN_GD(8)
     } else {
         QN_GD(kGroupBins / 32)
     }
