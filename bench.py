@@ -288,7 +288,7 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e, precisi
 
 def precision_leg(qn, args, stream, local, roof_of):
     """The precision workload (n=26, p=4, depolarizing only, 64 trajectories of 512 MiB):
-    fused layers (FP32, qubits 0-4 then four per sweep; tensor cores in TF32 and BF16x3,
+    fused layers (FP32 on the CUDA cores and the tensor cores in TF32 and BF16x3, all
     ceil(n/5) sweeps per layer) against one sweep per gate on the same trajectories --
     throughput, the sweeps' HBM fraction, and each form's <C> beside the ensemble's
     statistical error (the comparison "at equal <C> error")."""
@@ -310,6 +310,41 @@ def precision_leg(qn, args, stream, local, roof_of):
         legs[name]["c_difference_to_per_gate"] = abs(legs[name]["c_mean"] - legs["per_gate"]["c_mean"])
     legs["config"] = config_of(w, {"steps": sub.steps, "warmup": sub.warmup})
     return legs
+
+
+def gradient_leg(qn, args, stream, local):
+    """The gradient workload (n=16, p=6, depolarizing only, K=2048): one step is the noisy
+    forward run of the whole ensemble plus the adjoint gradient of <C> in all 12 angles
+    (qn_run_qaoa + qn_grad), timed with CUDA events on the library's stream."""
+    import torch
+
+    w = W.gradient_n16()
+    steps, warmup = max(2, min(args.steps, 3)), 3
+    b = qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch, stream=stream)
+    kw = w.noise_kwargs()
+
+    def step():
+        b.run_qaoa(w.edges, w.gammas, w.betas, **kw)
+        return b.grad()
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(steps):
+            dg, db = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    mean, se = b.expectation()
+    b.close()
+    return {"value": w.trajectories * steps / (ms / 1e3), "unit": "trajectories/s (forward + adjoint gradient)",
+            "ms_per_step": ms / steps, "c_mean": mean, "c_stderr": se,
+            "dC_dgamma": [float(x) for x in dg], "dC_dbeta": [float(x) for x in db], "clocks": clocks.summary(),
+            "config": config_of(w, {"steps": steps, "warmup": warmup,
+                                    "step": "qn_run_qaoa (fused layers) + qn_grad (adjoint, one reverse sweep per gate)"})}
 
 
 def gpu_arm(args):
@@ -400,7 +435,7 @@ def gpu_arm(args):
                          "prefix tree" + ("; phase gates applied in groups on <= 10 qubits and mixer rotations "
                                           "in blocks of 4 qubits, one sweep per group or block" if grouped
                                           else "; one sweep per gate")) if sharing else
-                        (f"fused layers: 1 + ceil((n-5)/4) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused
+                        (f"fused layers: ceil(n/5) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused
                          else f"one statevector per trajectory, one sweep per gate, {w.batch} per launch")}),
             "amp_updates_per_s": main["value"] * G * (1 << n),
             "distinct_states_per_step": main["states_per_step"],
@@ -429,6 +464,7 @@ def gpu_arm(args):
             line["cpu_baseline"] = cpu_baseline(w)
         if world == 1 and args.workload == "damping20" and not args.no_legs:
             line["precision26"] = precision_leg(qn, args, stream, local, roof_of=roof)
+            line["gradient16"] = gradient_leg(qn, args, stream, local)
             line["serving"] = serving_levels(args.requests, args.inflight, local)
         print(json.dumps(line), flush=True)
     if pg:
@@ -553,7 +589,7 @@ def main():
                     help="arithmetic of the fused layers of Pauli-only workloads: 0 FP32 (default), 1 TF32 or "
                          "2 BF16x3 tensor cores")
     ap.add_argument("--no-legs", action="store_true",
-                    help="skip the precision (n=26) and serving legs of the default line")
+                    help="skip the precision (n=26), gradient (n=16) and serving legs of the default line")
     ap.add_argument("--single-mode", action="store_true",
                     help="time only the selected mode (skip the per-trajectory comparison run)")
     ap.add_argument("--profile-case", action="store_true",

@@ -111,10 +111,10 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
 
 /* Fused layers (on = 1, the default; 0 = one sweep per gate).  With Pauli-only
  * noise (damping == 0) no branch depends on the state, so each QAOA layer is
- * applied as 1 + ceil((n - 5) / 4) sweeps instead of E + n: the cost layer
+ * applied as ceil(n / 5) sweeps instead of E + n: the cost layer
  * (every phase gate and every Pauli's Z part) is one diagonal factor folded
- * into a mixer sweep, and the mixer rotations are applied to qubits 0-4 in one
- * sweep and to four further qubits in each of the others.  Needs
+ * into a mixer sweep, and the mixer rotations are applied five qubits per
+ * sweep.  Needs
  * at most 64 edges; otherwise gates are swept one by one.  With damping == 0
  * fusion takes precedence over shared-prefix mode.  With damping, fusion acts
  * in shared-prefix mode only: consecutive phase gates of a layer on at most 10

@@ -727,7 +727,7 @@ LayerView layer_view(const qn_batch *h, int l) {
 }
 
 // All gates after the H layer as fused sweeps: per layer one sweep over qubits
-// 0 .. kFuse0-1 and ceil((n - kFuse0) / kFuse) over the rest; the cost phase of
+// 0 .. kFuse0-1 and ceil((n - kFuse0) / kFuse) over the rest (ceil(n / 5)); the cost phase of
 // layer 0 rides on the first sweep and that of layer l+1 on the last mixer sweep
 // of layer l.
 qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, bool ensemble) {

@@ -214,7 +214,8 @@ struct TcSweep {
 };
 
 constexpr int kFuse0 = 5;    // qubits of the fused mixer sweep that holds qubit 0 (16 float4 per thread)
-constexpr int kFuse = 4;     // qubits of the other fused mixer sweeps (16 float4 per thread)
+constexpr int kFuse = 5;     // qubits of the other fused mixer sweeps (16 float4 per thread, the
+                             // fifth qubit across lane pairs)
 
 struct NoiseDev {
     double gamma;              // damping (0 = off)

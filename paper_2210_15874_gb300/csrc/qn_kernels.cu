@@ -2731,14 +2731,17 @@ __device__ __forceinline__ uint64_t ev_of(const LayerView &L, uint32_t y) {
 template <int M, bool HAS0, bool PRE, bool POST>
 __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerView Lp, LayerView Lr, LayerView Lq,
                                                              int q_lo) {
-    constexpr int D = HAS0 ? M - 1 : M;  // fiber bits in float4 index space
+    // M = 5 without qubit 0: four qubits on the register index, the fifth across lane bit 4
+    // (two threads per fiber, the rotation by shuffles)
+    constexpr bool LANE = !HAS0 && M == 5;
+    constexpr int D = HAS0 ? M - 1 : (LANE ? 4 : M);  // fiber bits held in registers
     constexpr int NE = 1 << D;
     static_assert(NE <= 16, "at most 16 float4 per thread");
     const int t = blockIdx.y;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
     const int fl = HAS0 ? 0 : q_lo - 1;
-    const int64_t nfib = nf >> D;
+    const int64_t nfib = nf >> (LANE ? 5 : D);
     __shared__ uint64_t evk[NE + 1];  // EV of each element's offset; [NE]: EV of bit 0
     if (PRE || POST) {
         const LayerView &L = PRE ? Lp : Lq;  // the edge tables are the graph's, the same in every layer
@@ -2747,9 +2750,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
         __syncthreads();
     }
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
-    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t tg = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    // LANE: lanes l and l ^ 16 hold the fiber's two halves along qubit q_lo + 4 (bit hb); the
+    // fibers of a warp are 16 consecutive ones, so a warp stays or leaves as a whole
+    const uint32_t hb = LANE ? (threadIdx.x >> 4) & 1u : 0u;
+    const int64_t r = LANE ? ((tg & 15) | ((tg >> 5) << 4)) : tg;
     if (r >= nfib) return;
-    const int64_t fbase = ((r >> fl) << (fl + D)) | (r & (((int64_t)1 << fl) - 1));
+    constexpr int DB = LANE ? 5 : D;  // fiber bits in float4 index space
+    const int64_t fbase = ((r >> fl) << (fl + DB)) | (r & (((int64_t)1 << fl) - 1)) | ((int64_t)hb << (fl + 4));
     const uint32_t y0 = (uint32_t)(2 * fbase);
     float4 val[NE];
 #pragma unroll
@@ -2783,6 +2791,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
                 val[k].y = c0 * i0 - sn0 * r1;
                 val[k].z = c1 * r1 + sn1 * i0;
                 val[k].w = c1 * i1 - sn1 * r0;
+            }
+        } else if (LANE && j == 4) {
+            // own' = s_own (c own - i s partner), the partner in lane ^ 16
+            const float co = hb ? c1 : c0, so = hb ? sn1 : sn0;
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                const float px = __shfl_xor_sync(0xffffffffu, val[k].x, 16), py = __shfl_xor_sync(0xffffffffu, val[k].y, 16);
+                const float pz = __shfl_xor_sync(0xffffffffu, val[k].z, 16), pw = __shfl_xor_sync(0xffffffffu, val[k].w, 16);
+                val[k] = make_float4(co * val[k].x + so * py, co * val[k].y - so * px, co * val[k].z + so * pw,
+                                     co * val[k].w - so * pz);
             }
         } else {
             const int bit = HAS0 ? j - 1 : j;  // element-index bit of qubit q
@@ -3136,9 +3154,9 @@ cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, 
 template <int M, bool HAS0>
 static cudaError_t fused_dispatch(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
                                   int q_lo, bool pre, bool post, cudaStream_t s) {
-    constexpr int D = HAS0 ? M - 1 : M;
-    const int64_t nfib = ((int64_t)1 << (v.n - 1)) >> D;
-    const dim3 grid((unsigned)((nfib + kThreads - 1) / kThreads), (unsigned)v.b);
+    constexpr int D = HAS0 ? M - 1 : M;  // with M = 5 off qubit 0: two threads per fiber of 5 bits
+    const int64_t threads = ((int64_t)1 << (v.n - 1)) >> (!HAS0 && M == 5 ? 4 : D);
+    const dim3 grid((unsigned)((threads + kThreads - 1) / kThreads), (unsigned)v.b);
     if (!HAS0 && pre) return cudaErrorInvalidValue;  // the first layer's phase rides on the qubit-0 window
     if (HAS0 && pre && post) k_fused_sweep<M, HAS0, HAS0, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
     else if (HAS0 && pre) k_fused_sweep<M, HAS0, HAS0, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
@@ -3166,6 +3184,9 @@ cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const La
     case 2: return fused_dispatch<2, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
     case 3: return fused_dispatch<3, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
     case 4: return fused_dispatch<4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 5:  // the fifth qubit across lane pairs: 16 fibers of 5 bits per warp (q_lo >= 5, n >= 10)
+        if (q_lo < 5 || v.n < 10) return cudaErrorInvalidValue;
+        return fused_dispatch<5, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -63,6 +63,10 @@ class Result:
     submitted: float
     started: float
     finished: float
+    # the request's span on the device: CUDA events on its stream at its first and after its
+    # last launch, in ms after the server's reference event (None outside a Server)
+    device_start: float | None = None
+    device_end: float | None = None
 
     @property
     def latency(self) -> float:
@@ -90,6 +94,9 @@ class Server:
         self._mem_used = 0
         self._stop = False
         self._streams = [torch.cuda.Stream() for _ in range(max_inflight)]
+        self._ref = torch.cuda.Event(enable_timing=True)  # origin of the requests' device spans
+        self._ref.record()
+        self._ref.synchronize()
         self._free_streams = list(range(max_inflight))
         self._threads = []
         # one entry per admission: (time, requests in flight, footprint bytes held), after admitting
@@ -153,13 +160,18 @@ class Server:
             torch.cuda.set_device(self.device)
             stream = self._streams[si]
             started = time.perf_counter()
+            ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev_a.record(stream)
             with qn.Batch(req.n, req.trajectories, req.seed, launch_batch=req.launch_batch(), stream=stream,
                           torch_allocator=True) as b:
                 b.set_sharing(req.damping > 0)
                 b.run_qaoa(req.edges, req.gammas, req.betas, p1=req.p1, p2=req.p2, damping=req.damping)
                 mean, se = b.expectation()
                 probs = b.probs() if req.want_probs else None
-            fut.set_result(Result(mean, se, probs, submitted, started, time.perf_counter()))
+                ev_b.record(stream)
+                ev_b.synchronize()
+            fut.set_result(Result(mean, se, probs, submitted, started, time.perf_counter(),
+                                  self._ref.elapsed_time(ev_a), self._ref.elapsed_time(ev_b)))
         except Exception as exc:  # delivered to the caller through the future
             fut.set_exception(exc)
         finally:

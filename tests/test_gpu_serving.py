@@ -46,9 +46,13 @@ def test_results_equal_alone_and_in_the_mix(mods):
     for a, m in zip(alone, mixed):
         assert abs(a.mean - m.mean) < 1e-12 and abs(a.std_err - m.std_err) < 1e-12
         np.testing.assert_allclose(m.probs, a.probs, rtol=1e-12, atol=1e-15)
-    # the requests overlapped: some started before others finished
+    # the requests overlapped: some started before others finished, on the host and on the
+    # device (CUDA events on each request's stream, against the server's reference event)
     spans = sorted((m.started, m.finished) for m in mixed)
     assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+    dev = sorted((m.device_start, m.device_end) for m in mixed)
+    assert all(a <= b for a, b in dev)
+    assert any(dev[i + 1][0] < dev[i][1] for i in range(len(dev) - 1))
 
 
 def test_admission_by_footprint(mods):
