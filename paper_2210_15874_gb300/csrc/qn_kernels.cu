@@ -2350,7 +2350,7 @@ __global__ void k_probs_combine(double *probs, const double *spart, int parts, i
 // its true position XOR the state's frame; since a rotation treats a pair's two
 // values alike, rotating in true order gives the stored-order values moved.
 template <bool TANF>
-__global__ void __launch_bounds__(kMixThreads) k_probs_mix(BatchView v, AccumView a, MixMap mm, MixTail tl,
+__global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, AccumView a, MixMap mm, MixTail tl,
                                                            int64_t xblocks) {
     constexpr int kR = kMixE / 2;  // float4 per thread
     constexpr int kE = 2 * kR;     // basis states per thread
@@ -2404,6 +2404,9 @@ __global__ void __launch_bounds__(kMixThreads) k_probs_mix(BatchView v, AccumVie
             s_cut[2 * j + e][threadIdx.x] = (float)cnt;
             s_acc[2 * j + e][threadIdx.x] = 0.0;
         }
+    float cut[kE];  // C(x) of this thread's basis states, constant over the states
+#pragma unroll
+    for (int i = 0; i < kE; ++i) cut[i] = s_cut[i][threadIdx.x];
     const int tbeg = (int)((int64_t)blockIdx.y * v.b / gridDim.y);
     const int tlim = (int)((int64_t)(blockIdx.y + 1) * v.b / gridDim.y);
     for (int t0c = tbeg; t0c < tlim; t0c += kAccChunk) {
@@ -2429,18 +2432,26 @@ __global__ void __launch_bounds__(kMixThreads) k_probs_mix(BatchView v, AccumVie
         float ah[kE], al[kE];  // sigma terms of this chunk (double-float)
 #pragma unroll
         for (int i = 0; i < kE; ++i) ah[i] = al[i] = 0.0f;
+        // element j's stored index: (base | aoff(j)) ^ Fq = (base ^ Fq) ^ aoff(j); the next
+        // state's float4 are loaded while the current one is computed
+        auto load_state = [&](int ci, float4 (&dst)[kR]) {
+            const uint32_t sb = base ^ (c_Ff[ci] >> 1);
+            const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)c_src[ci] << v.n));
+#pragma unroll
+            for (int j = 0; j < kR; ++j) dst[j] = q4[sb ^ aoff(j)];
+        };
+        float4 xn[kR];
+        if (cn > 0) load_state(0, xn);
         for (int ci = 0; ci < cn; ++ci) {
             const uint32_t Ff = c_Ff[ci], Fq = Ff >> 1;  // Fq: the frame on float4 indices
             // this lane's pattern on the block's qubits is (j | hi << 3); stored: that ^ fa
             int fa = (Fq & ao3) ? 8 : 0;
 #pragma unroll
             for (int i = 0; i < kMixQ - 1; ++i) fa |= (Fq & ao[i]) ? 1 << i : 0;
-            // element j's stored index: (base | aoff(j)) ^ Fq = (base ^ Fq) ^ aoff(j)
-            const uint32_t sb = base ^ Fq;
-            const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)c_src[ci] << v.n));
             float4 x[kR];
 #pragma unroll
-            for (int j = 0; j < kR; ++j) x[j] = q4[sb ^ aoff(j)];
+            for (int j = 0; j < kR; ++j) x[j] = xn[j];
+            if (ci + 1 < cn) load_state(ci + 1, xn);
 #pragma unroll
             for (int i = 0; i < kMixQ - 1; ++i) {
 #pragma unroll
@@ -2459,8 +2470,8 @@ __global__ void __launch_bounds__(kMixThreads) k_probs_mix(BatchView v, AccumVie
                 const float p0 = (Ff & 1u) ? pb : pa, p1 = (Ff & 1u) ? pa : pb;  // true qubit 0
                 df_add_prod(ah[2 * j], al[2 * j], p0, ih, il);
                 df_add_prod(ah[2 * j + 1], al[2 * j + 1], p1, ih, il);
-                cp += p0 * s_cut[2 * j][threadIdx.x];
-                cp += p1 * s_cut[2 * j + 1][threadIdx.x];
+                cp += p0 * cut[2 * j];
+                cp += p1 * cut[2 * j + 1];
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
