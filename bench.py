@@ -528,16 +528,16 @@ def serving_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(sharing=False, depth=1, fusion=True, precision=0):
+def profile_case(sharing=False, depth=1, fusion=True, precision=-1):
     """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state);
     depth 2 adds a layer, so the last mixer block of the first one forms the next layer's joint.
-    precision 1 or 2: the precision workload's fused layers on the tensor cores (n=24, p=1,
-    depolarizing only, 8 states of 128 MiB)."""
+    precision 0, 1 or 2: the precision workload's fused layers in FP32 or on the tensor cores
+    (n=24, p=1, depolarizing only, 8 states of 128 MiB)."""
     from paper_2210_15874_gb300 import build
     build.build()
     from paper_2210_15874_gb300 import qn
 
-    if precision:
+    if precision >= 0:
         w = W.qaoa_workload("ncu_n24_p1_tc", 24, 1, index=2, trajectories=8, batch=8)
         with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
             b.set_fusion(True)
@@ -596,8 +596,9 @@ def main():
                     help="run one small ensemble for ncu captures, then exit (n=20, p=1: 32 trajectories in "
                          "one launch, or with --sharing 1 64 heavily noisy trajectories)")
     ap.add_argument("--profile-depth", type=int, default=1, choices=[1, 2], help="QAOA depth of --profile-case")
-    ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2],
-                    help="--profile-case of the tensor-core fused layers (1 TF32, 2 BF16x3)")
+    ap.add_argument("--profile-precision", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="--profile-case of the Pauli-only fused layers (0 FP32, 1 TF32, 2 BF16x3 tensor cores) "
+                         "instead of the damping case")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(bool(args.sharing), args.profile_depth, bool(args.fusion), args.profile_precision)
