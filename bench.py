@@ -288,8 +288,9 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e, precisi
 
 def precision_leg(qn, args, stream, local, roof_of):
     """The precision workload (n=26, p=4, depolarizing only, 64 trajectories of 512 MiB):
-    fused layers (FP32 on the CUDA cores and the tensor cores in TF32 and BF16x3, all
-    ceil(n/5) sweeps per layer) against one sweep per gate on the same trajectories --
+    fused layers (FP32 on the CUDA cores, 4 sweeps per layer at n=26, and the tensor cores
+    in TF32 and BF16x3, ceil(n/5) sweeps per layer) against one sweep per gate on the same
+    trajectories --
     throughput, the sweeps' HBM fraction, and each form's <C> beside the ensemble's
     statistical error (the comparison "at equal <C> error")."""
     w = W.precision_n26()
@@ -435,7 +436,8 @@ def gpu_arm(args):
                          "prefix tree" + ("; phase gates applied in groups on <= 10 qubits and mixer rotations "
                                           "in blocks of 4 qubits, one sweep per group or block" if grouped
                                           else "; one sweep per gate")) if sharing else
-                        (f"fused layers: ceil(n/5) sweeps per QAOA layer, {w.batch} trajectories per launch" if fused
+                        (f"fused layers: qubits 0-7, then windows of <= 7 qubits, one sweep each per QAOA layer, "
+                         f"{w.batch} trajectories per launch" if fused
                          else f"one statevector per trajectory, one sweep per gate, {w.batch} per launch")}),
             "amp_updates_per_s": main["value"] * G * (1 << n),
             "distinct_states_per_step": main["states_per_step"],
@@ -532,13 +534,14 @@ def profile_case(sharing=False, depth=1, fusion=True, precision=-1):
     """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state);
     depth 2 adds a layer, so the last mixer block of the first one forms the next layer's joint.
     precision 0, 1 or 2: the precision workload's fused layers in FP32 or on the tensor cores
-    (n=24, p=1, depolarizing only, 8 states of 128 MiB)."""
+    (n=24, p=depth, depolarizing only, 8 states of 128 MiB; with depth 2 the first layer's last
+    window also applies the second layer's phase)."""
     from paper_2210_15874_gb300 import build
     build.build()
     from paper_2210_15874_gb300 import qn
 
     if precision >= 0:
-        w = W.qaoa_workload("ncu_n24_p1_tc", 24, 1, index=2, trajectories=8, batch=8)
+        w = W.qaoa_workload(f"ncu_n24_p{depth}_tc", 24, depth, index=2, trajectories=8, batch=8)
         with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
             b.set_fusion(True)
             b.set_precision(precision)

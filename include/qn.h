@@ -111,10 +111,11 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
 
 /* Fused layers (on = 1, the default; 0 = one sweep per gate).  With Pauli-only
  * noise (damping == 0) no branch depends on the state, so each QAOA layer is
- * applied as ceil(n / 5) sweeps instead of E + n: the cost layer
- * (every phase gate and every Pauli's Z part) is one diagonal factor folded
- * into a mixer sweep, and the mixer rotations are applied five qubits per
- * sweep.  Needs
+ * applied as a few sweeps instead of E + n: the cost layer (every phase gate
+ * and every Pauli's Z part) is one diagonal factor folded into a mixer sweep,
+ * and the mixer rotations are applied in windows of consecutive qubits -- for
+ * n >= 10 qubits 0-7, then ceil((n - 8) / 7) windows of at most 7 (3 sweeps
+ * per layer at n = 20, 4 at n = 26); below 10 qubits five per sweep.  Needs
  * at most 64 edges; otherwise gates are swept one by one.  With damping == 0
  * fusion takes precedence over shared-prefix mode.  With damping, fusion acts
  * in shared-prefix mode only: consecutive phase gates of a layer on at most 10
@@ -129,7 +130,7 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
 qn_status qn_batch_set_fusion(qn_batch *h, int32_t on);
 
 /* Arithmetic of the fused layers (Pauli-only noise, fusion on, n >= 11):
- *   0  FP32 on the CUDA cores, three qubits per sweep (the default);
+ *   0  FP32 on the CUDA cores, the windows of qn_batch_set_fusion (the default);
  *   1  TF32 tensor cores: the mixer rotations of five qubits per sweep as two
  *      GEMMs with the +-1 Hadamard matrix (exp(-i beta X) = H diag(e^{-i beta},
  *      e^{i beta}) H), TF32 operands, FP32 accumulation (ceil(n / 5) sweeps per

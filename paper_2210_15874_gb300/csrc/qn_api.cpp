@@ -726,10 +726,30 @@ LayerView layer_view(const qn_batch *h, int l) {
     return L;
 }
 
-// All gates after the H layer as fused sweeps: per layer one sweep over qubits
-// 0 .. kFuse0-1 and ceil((n - kFuse0) / kFuse) over the rest (ceil(n / 5)); the cost phase of
-// layer 0 rides on the first sweep and that of layer l+1 on the last mixer sweep
-// of layer l.
+// The fused mixer windows (first qubit, qubits) of one layer.  n >= 10: qubits
+// 0 .. kFuse0-1, then ceil((n - kFuse0) / kFuse) windows of balanced sizes (at most
+// kFuse, the larger ones first); n < 10: windows of kFuseSmall qubits.
+std::vector<std::pair<int, int>> fused_windows(int n) {
+    std::vector<std::pair<int, int>> w;
+    if (n < 10) {
+        for (int q_lo = 0; q_lo < n; q_lo += kFuseSmall) w.emplace_back(q_lo, std::min(kFuseSmall, n - q_lo));
+        return w;
+    }
+    w.emplace_back(0, kFuse0);
+    const int rest = n - kFuse0;
+    const int count = (rest + kFuse - 1) / kFuse;
+    int q_lo = kFuse0;
+    for (int i = 0; i < count; ++i) {
+        const int m = rest / count + (i < rest % count ? 1 : 0);
+        w.emplace_back(q_lo, m);
+        q_lo += m;
+    }
+    return w;
+}
+
+// All gates after the H layer as fused sweeps over the windows of fused_windows;
+// the cost phase of layer 0 rides on the first sweep and that of layer l+1 on the
+// last mixer sweep of layer l.
 qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, bool ensemble) {
     const int n = h->n, p = h->p;
     const int E = (int)h->edges.size() / 2;
@@ -763,9 +783,10 @@ qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, boo
         }
         return QN_OK;
     }
+    const std::vector<std::pair<int, int>> windows = fused_windows(n);
     for (int l = 0; l < p; ++l) {
-        for (int q_lo = 0; q_lo < n; q_lo += q_lo == 0 ? kFuse0 : kFuse) {
-            const int m = std::min(q_lo == 0 ? kFuse0 : kFuse, n - q_lo);
+        for (const auto &wd : windows) {
+            const int q_lo = wd.first, m = wd.second;
             const bool pre = l == 0 && q_lo == 0;
             const bool post = q_lo + m >= n && l + 1 < p;
             QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));

@@ -213,9 +213,11 @@ struct TcSweep {
     float2 dph[6];
 };
 
-constexpr int kFuse0 = 5;    // qubits of the fused mixer sweep that holds qubit 0 (16 float4 per thread)
-constexpr int kFuse = 5;     // qubits of the other fused mixer sweeps (16 float4 per thread, the
-                             // fifth qubit across lane pairs)
+// Fused mixer windows (16 float4 per thread, the qubits beyond four on lane bits):
+constexpr int kFuse0 = 8;      // the window that holds qubit 0 (n >= 10): qubit 0 in the float4,
+                               // 1-3 on lane bits, 4-7 in registers
+constexpr int kFuse = 7;       // at most, each of the other windows (n >= 10)
+constexpr int kFuseSmall = 5;  // n < 10: windows of five qubits, registers only
 
 struct NoiseDev {
     double gamma;              // damping (0 = off)

@@ -2675,9 +2675,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_sweep(BatchView v, float2 *lam
 //    the stored bits of edge e's endpoints differ (XOR of four byte tables) and
 //    s_e flips edge e when the frame differs on its endpoints at that gate;
 //  * the mixer layer is a tensor product of one 2x2 matrix per qubit (the
-//    rotation with the row signs of its Pauli's Z part), applied in register
-//    fibers over kFuse0 consecutive qubits (the window holding qubit 0) or
-//    kFuse (the others) per sweep.
+//    rotation with the row signs of its Pauli's Z part), applied in fibres over
+//    windows of consecutive qubits: up to kFuse0 with qubit 0, kFuse without
+//    (four qubits in registers, the others on lane bits).
 // A sweep applies [phase of layer l] (first sweep) and the rotations of one
 // qubit group; the last group of a layer also applies the next layer's phase.
 // ---------------------------------------------------------------------------
@@ -2732,47 +2732,55 @@ __device__ __forceinline__ uint64_t ev_of(const LayerView &L, uint32_t y) {
            __ldg(L.ev + 768 + (y >> 24));
 }
 
-// One fused sweep.  The group is qubits [q_lo, q_lo + M); with HAS0 (q_lo == 0)
-// bit 0 lies inside each float4 and a thread holds 2^(M-1) float4, otherwise
-// 2^M float4 along f bits q_lo-1 .. q_lo+M-2 (at most 16 float4: M <= 5 with
-// qubit 0, M <= 4 without).  PRE: phase of layer `lp` before the rotations;
-// POST: phase of layer `lq` after them.  The phase of element k, half e, is
-// that of y0 | 2 (k << fl) | e, split into the thread's y0 and the block-wide
-// tables of the patterns 2 (k << fl) and e.
-template <int M, bool HAS0, bool PRE, bool POST>
+// One fused sweep over a window of M = HAS0 + LQ + RQ qubits.  A fibre is the
+// 2^(M - HAS0) float4 of one value of the float4-index bits outside the window:
+//  * with HAS0 (q_lo == 0) qubit 0 is the float4 half, qubits 1 .. LQ are lane
+//    bits 0 .. LQ-1 (float4-index bits 0 .. LQ-1) and the next RQ qubits the
+//    register index; the upper lane bits index fibres, so runs of 2^LQ
+//    consecutive float4 fill a warp's accesses;
+//  * otherwise qubits q_lo .. q_lo+LQ-1 are lane bits 5-LQ .. 4 and the next RQ
+//    the register index; lane bits 0 .. 4-LQ are the float4-index bits 0 .. 4-LQ
+//    below the window.
+// The rotation of a lane qubit takes the partner half from lane ^ (1 << b) by
+// shuffle.  PRE: phase of layer `lp` before the rotations; POST: phase of layer
+// `lq` after them.  The phase of register element k, half e, is that of
+// y0 | 2 (k << rs) | e (rs the float4-index bit of register bit 0), split into
+// the thread's y0 and the block-wide tables of the patterns 2 (k << rs) and e.
+template <int LQ, int RQ, bool HAS0, bool PRE, bool POST>
 __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerView Lp, LayerView Lr, LayerView Lq,
                                                              int q_lo) {
-    // M = 5 without qubit 0: four qubits on the register index, the fifth across lane bit 4
-    // (two threads per fiber, the rotation by shuffles)
-    constexpr bool LANE = !HAS0 && M == 5;
-    constexpr int D = HAS0 ? M - 1 : (LANE ? 4 : M);  // fiber bits held in registers
-    constexpr int NE = 1 << D;
-    static_assert(NE <= 16, "at most 16 float4 per thread");
+    constexpr int NE = 1 << RQ;
+    constexpr int DB = LQ + RQ;  // window bits in the float4 index
+    constexpr int LO = 5 - LQ;   // lane bits that index fibres
+    static_assert(NE <= 16 && LQ <= 3, "at most 16 float4 per thread and 3 lane qubits");
     const int t = blockIdx.y;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
-    const int fl = HAS0 ? 0 : q_lo - 1;
-    const int64_t nfib = nf >> (LANE ? 5 : D);
-    __shared__ uint64_t evk[NE + 1];  // EV of each element's offset; [NE]: EV of bit 0
+    const int wlo = HAS0 ? 0 : q_lo - 1;  // lowest float4-index bit of the window
+    const int rs = wlo + LQ;
+    const int64_t nfib = nf >> DB;
+    __shared__ uint64_t evk[NE + 1];  // EV of each register element's offset; [NE]: EV of bit 0
     if (PRE || POST) {
         const LayerView &L = PRE ? Lp : Lq;  // the edge tables are the graph's, the same in every layer
-        if ((int)threadIdx.x < NE) evk[threadIdx.x] = ev_of(L, 2u * ((uint32_t)threadIdx.x << fl));
+        if ((int)threadIdx.x < NE) evk[threadIdx.x] = ev_of(L, 2u * ((uint32_t)threadIdx.x << rs));
         if ((int)threadIdx.x == NE) evk[NE] = ev_of(L, 1u);
         __syncthreads();
     }
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
     const int64_t tg = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    // LANE: lanes l and l ^ 16 hold the fiber's two halves along qubit q_lo + 4 (bit hb); the
-    // fibers of a warp are 16 consecutive ones, so a warp stays or leaves as a whole
-    const uint32_t hb = LANE ? (threadIdx.x >> 4) & 1u : 0u;
-    const int64_t r = LANE ? ((tg & 15) | ((tg >> 5) << 4)) : tg;
+    const uint32_t lane = threadIdx.x & 31u;
+    // wb: the window's lane bits; r: the fibre.  With LQ > 0 a warp's fibres are
+    // 2^LO consecutive ones, so a warp stays or leaves as a whole.
+    const uint32_t wb = LQ == 0 ? 0u : HAS0 ? lane & ((1u << LQ) - 1u) : lane >> LO;
+    const int64_t r = LQ == 0 ? tg
+                      : HAS0  ? (int64_t)(lane >> LQ) | ((tg >> 5) << LO)
+                              : (int64_t)(lane & ((1u << LO) - 1u)) | ((tg >> 5) << LO);
     if (r >= nfib) return;
-    constexpr int DB = LANE ? 5 : D;  // fiber bits in float4 index space
-    const int64_t fbase = ((r >> fl) << (fl + DB)) | (r & (((int64_t)1 << fl) - 1)) | ((int64_t)hb << (fl + 4));
+    const int64_t fbase = ((r >> wlo) << (wlo + DB)) | (r & (((int64_t)1 << wlo) - 1)) | ((int64_t)wb << wlo);
     const uint32_t y0 = (uint32_t)(2 * fbase);
     float4 val[NE];
 #pragma unroll
-    for (int k = 0; k < NE; ++k) val[k] = p4[fbase + ((int64_t)k << fl)];
+    for (int k = 0; k < NE; ++k) val[k] = p4[fbase + ((int64_t)k << rs)];
     if (PRE) {
         const uint64_t sv = Lp.s[t];
         const uint32_t zm = Lp.zm[t];
@@ -2781,52 +2789,69 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
         const uint64_t ev1 = evk[NE];
 #pragma unroll
         for (int k = 0; k < NE; ++k) {
-            const uint32_t yk = 2u * ((uint32_t)k << fl);
+            const uint32_t yk = 2u * ((uint32_t)k << rs);
             cmul_inplace(val[k].x, val[k].y, split_phase(Lp, ev0, evk[k], sv, zp0, yk, zm));
             cmul_inplace(val[k].z, val[k].w, split_phase(Lp, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
         }
     }
     const uint32_t mz = Lr.mz[t], mf = Lr.mf[t];
     const float cb = Lr.cb, sb = Lr.sb;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        const int q = q_lo + j;
+    // the 2x2 rotation of qubit q with the row signs of its Pauli's Z part:
+    // row 0 (stored bit 0) c0, sn0; row 1 c1, sn1
+    auto coeffs = [&](int q, float &c0, float &sn0, float &c1, float &sn1) {
         const uint32_t z = (mz >> q) & 1u, fb = (mf >> q) & 1u;
         const float s0 = (z && fb) ? -1.0f : 1.0f, s1 = (z && !fb) ? -1.0f : 1.0f;
-        const float c0 = cb * s0, sn0 = sb * s0, c1 = cb * s1, sn1 = sb * s1;
-        if (HAS0 && j == 0) {
+        c0 = cb * s0;
+        sn0 = sb * s0;
+        c1 = cb * s1;
+        sn1 = sb * s1;
+    };
+    const int ql = q_lo + (HAS0 ? 1 : 0);  // first lane qubit
+    if (HAS0) {
+        float c0, sn0, c1, sn1;
+        coeffs(0, c0, sn0, c1, sn1);
 #pragma unroll
-            for (int k = 0; k < NE; ++k) {
-                const float r0 = val[k].x, i0 = val[k].y, r1 = val[k].z, i1 = val[k].w;
-                val[k].x = c0 * r0 + sn0 * i1;
-                val[k].y = c0 * i0 - sn0 * r1;
-                val[k].z = c1 * r1 + sn1 * i0;
-                val[k].w = c1 * i1 - sn1 * r0;
-            }
-        } else if (LANE && j == 4) {
-            // own' = s_own (c own - i s partner), the partner in lane ^ 16
-            const float co = hb ? c1 : c0, so = hb ? sn1 : sn0;
+        for (int k = 0; k < NE; ++k) {
+            const float r0 = val[k].x, i0 = val[k].y, r1 = val[k].z, i1 = val[k].w;
+            val[k].x = c0 * r0 + sn0 * i1;
+            val[k].y = c0 * i0 - sn0 * r1;
+            val[k].z = c1 * r1 + sn1 * i0;
+            val[k].w = c1 * i1 - sn1 * r0;
+        }
+    }
 #pragma unroll
-            for (int k = 0; k < NE; ++k) {
-                const float px = __shfl_xor_sync(0xffffffffu, val[k].x, 16), py = __shfl_xor_sync(0xffffffffu, val[k].y, 16);
-                const float pz = __shfl_xor_sync(0xffffffffu, val[k].z, 16), pw = __shfl_xor_sync(0xffffffffu, val[k].w, 16);
-                val[k] = make_float4(co * val[k].x + so * py, co * val[k].y - so * px, co * val[k].z + so * pw,
-                                     co * val[k].w - so * pz);
-            }
-        } else {
-            const int bit = HAS0 ? j - 1 : j;  // element-index bit of qubit q
+    for (int j = 0; j < LQ; ++j) {
+        // own' = c own - i s partner with the row of the lane's own bit
+        const int b = HAS0 ? j : LO + j;
+        const uint32_t hb = (lane >> b) & 1u;
+        float c0, sn0, c1, sn1;
+        coeffs(ql + j, c0, sn0, c1, sn1);
+        const float co = hb ? c1 : c0, so = hb ? sn1 : sn0;
 #pragma unroll
-            for (int k = 0; k < NE; ++k) {
-                if (k & (1 << bit)) continue;
-                float4 &a = val[k];
-                float4 &b = val[k | (1 << bit)];
-                float nx = c0 * a.x + sn0 * b.y, ny = c0 * a.y - sn0 * b.x;
-                float mx = c1 * b.x + sn1 * a.y, my = c1 * b.y - sn1 * a.x;
-                float nz = c0 * a.z + sn0 * b.w, nw = c0 * a.w - sn0 * b.z;
-                float mzv = c1 * b.z + sn1 * a.w, mw = c1 * b.w - sn1 * a.z;
-                a = make_float4(nx, ny, nz, nw);
-                b = make_float4(mx, my, mzv, mw);
-            }
+        for (int k = 0; k < NE; ++k) {
+            const float px = __shfl_xor_sync(0xffffffffu, val[k].x, 1 << b);
+            const float py = __shfl_xor_sync(0xffffffffu, val[k].y, 1 << b);
+            const float pz = __shfl_xor_sync(0xffffffffu, val[k].z, 1 << b);
+            const float pw = __shfl_xor_sync(0xffffffffu, val[k].w, 1 << b);
+            val[k] = make_float4(co * val[k].x + so * py, co * val[k].y - so * px, co * val[k].z + so * pw,
+                                 co * val[k].w - so * pz);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RQ; ++j) {
+        float c0, sn0, c1, sn1;
+        coeffs(ql + LQ + j, c0, sn0, c1, sn1);
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            if (k & (1 << j)) continue;
+            float4 &a = val[k];
+            float4 &b = val[k | (1 << j)];
+            const float nx = c0 * a.x + sn0 * b.y, ny = c0 * a.y - sn0 * b.x;
+            const float mx = c1 * b.x + sn1 * a.y, my = c1 * b.y - sn1 * a.x;
+            const float nz = c0 * a.z + sn0 * b.w, nw = c0 * a.w - sn0 * b.z;
+            const float mzv = c1 * b.z + sn1 * a.w, mw = c1 * b.w - sn1 * a.z;
+            a = make_float4(nx, ny, nz, nw);
+            b = make_float4(mx, my, mzv, mw);
         }
     }
     if (POST) {
@@ -2837,13 +2862,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
         const uint64_t ev1 = evk[NE];
 #pragma unroll
         for (int k = 0; k < NE; ++k) {
-            const uint32_t yk = 2u * ((uint32_t)k << fl);
+            const uint32_t yk = 2u * ((uint32_t)k << rs);
             cmul_inplace(val[k].x, val[k].y, split_phase(Lq, ev0, evk[k], sv, zp0, yk, zm));
             cmul_inplace(val[k].z, val[k].w, split_phase(Lq, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
         }
     }
 #pragma unroll
-    for (int k = 0; k < NE; ++k) p4[fbase + ((int64_t)k << fl)] = val[k];
+    for (int k = 0; k < NE; ++k) p4[fbase + ((int64_t)k << rs)] = val[k];
 }
 
 // Phase only (a circuit whose layers have no mixer qubits left to fuse with).
@@ -3162,42 +3187,51 @@ cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, 
     return cudaGetLastError();
 }
 
-template <int M, bool HAS0>
+template <int LQ, int RQ, bool HAS0>
 static cudaError_t fused_dispatch(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
                                   int q_lo, bool pre, bool post, cudaStream_t s) {
-    constexpr int D = HAS0 ? M - 1 : M;  // with M = 5 off qubit 0: two threads per fiber of 5 bits
-    const int64_t threads = ((int64_t)1 << (v.n - 1)) >> (!HAS0 && M == 5 ? 4 : D);
+    const int64_t threads = ((int64_t)1 << (v.n - 1)) >> RQ;  // 2^LQ threads per fibre of LQ + RQ bits
     const dim3 grid((unsigned)((threads + kThreads - 1) / kThreads), (unsigned)v.b);
     if (!HAS0 && pre) return cudaErrorInvalidValue;  // the first layer's phase rides on the qubit-0 window
-    if (HAS0 && pre && post) k_fused_sweep<M, HAS0, HAS0, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
-    else if (HAS0 && pre) k_fused_sweep<M, HAS0, HAS0, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
-    else if (post) k_fused_sweep<M, HAS0, false, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
-    else k_fused_sweep<M, HAS0, false, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    if (HAS0 && pre && post) k_fused_sweep<LQ, RQ, HAS0, HAS0, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    else if (HAS0 && pre) k_fused_sweep<LQ, RQ, HAS0, HAS0, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    else if (post) k_fused_sweep<LQ, RQ, HAS0, false, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
+    else k_fused_sweep<LQ, RQ, HAS0, false, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
                                int q_lo, int m, bool pre, bool post, cudaStream_t s) {
-    // windows of up to kFuse0 qubits with qubit 0 (it sits inside the float4) and up to
-    // kFuse without; the fiber dimension D stays below the n-1 float4 index bits
+    if (m < 1 || q_lo < 0 || q_lo + m > v.n) return cudaErrorInvalidValue;
+    // lane qubits need whole warps of fibres (2^(RQ+5) float4 per state, RQ = 4) and,
+    // off qubit 0, the 5 - LQ float4-index bits below the window free (q_lo - 1 >= 5 - LQ,
+    // LQ = m - 4)
+    const bool lanes_ok = v.n >= 10 && (q_lo == 0 || q_lo - 1 >= 9 - m);
     if (q_lo == 0) {
         switch (m) {
-        case 1: return fused_dispatch<1, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        case 2: return fused_dispatch<2, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        case 3: return fused_dispatch<3, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        case 4: return fused_dispatch<4, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        case 5: return fused_dispatch<5, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 1: return fused_dispatch<0, 0, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 2: return fused_dispatch<0, 1, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 3: return fused_dispatch<0, 2, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 4: return fused_dispatch<0, 3, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 5: return fused_dispatch<0, 4, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 8:  // qubit 0 in the float4, 1-3 on lane bits, 4-7 in registers
+            if (!lanes_ok) return cudaErrorInvalidValue;
+            return fused_dispatch<3, 4, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
         default: return cudaErrorInvalidValue;
         }
     }
     switch (m) {
-    case 1: return fused_dispatch<1, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    case 2: return fused_dispatch<2, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    case 3: return fused_dispatch<3, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    case 4: return fused_dispatch<4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    case 5:  // the fifth qubit across lane pairs: 16 fibers of 5 bits per warp (q_lo >= 5, n >= 10)
-        if (q_lo < 5 || v.n < 10) return cudaErrorInvalidValue;
-        return fused_dispatch<5, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 1: return fused_dispatch<0, 1, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 2: return fused_dispatch<0, 2, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 3: return fused_dispatch<0, 3, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 4: return fused_dispatch<0, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 5:
+    case 6:
+    case 7:  // m - 4 qubits on lane bits, 4 in registers
+        if (!lanes_ok) return cudaErrorInvalidValue;
+        if (m == 5) return fused_dispatch<1, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        if (m == 6) return fused_dispatch<2, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        return fused_dispatch<3, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
     default: return cudaErrorInvalidValue;
     }
 }

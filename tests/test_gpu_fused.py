@@ -1,5 +1,5 @@
-"""Fused layers (Pauli-only noise): one sweep per five qubits per QAOA layer
-instead of one per gate.  Checked against the per-gate sweeps and the FP64 oracle on the
+"""Fused layers (Pauli-only noise): one sweep per window of up to eight qubits per
+QAOA layer instead of one per gate.  Checked against the per-gate sweeps and the FP64 oracle on the
 same trajectories: Pauli codes bit-exact, amplitudes within 1e-5, <C>_t within
 the FP32 bound; the precision figures at n=14 are printed (pytest -s)."""
 import json
@@ -16,9 +16,33 @@ pytestmark = pytest.mark.gpu
 U32 = 2.0 ** -24
 
 
+def fused_windows(n):
+    """Windows (first qubit, qubits) of one layer of the FP32 fused schedule: below ten
+    qubits five at a time (registers only); from ten on qubits 0-7 (qubit 0 in the float4,
+    1-3 on lane bits, 4-7 in registers), then ceil((n-8)/7) windows of balanced sizes,
+    larger first (the qubits beyond four on lane bits)."""
+    if n < 10:
+        return [(q, min(5, n - q)) for q in range(0, n, 5)]
+    rest = n - 8
+    count = -(-rest // 7)
+    out, q = [(0, 8)], 8
+    for i in range(count):
+        m = rest // count + (1 if i < rest % count else 0)
+        out.append((q, m))
+        q += m
+    return out
+
+
 def fused_sweeps(n):
-    """Sweeps per layer of the FP32 fused schedule: five qubits at a time."""
-    return -(-n // 5)
+    return len(fused_windows(n))
+
+
+def test_fused_windows_cover_each_qubit_once():
+    for n in range(2, 33):
+        w = fused_windows(n)
+        assert [q for lo, m in w for q in range(lo, lo + m)] == list(range(n))
+        assert all(m <= (7 if n >= 10 else 5) for _, m in w[1:])
+    assert [fused_sweeps(n) for n in (14, 20, 24, 26)] == [2, 3, 4, 4]
 
 
 @pytest.fixture(scope="module")
@@ -43,8 +67,12 @@ def run(qn, w, fusion, launch_batch=0):
     return dict(mean=mean, se=se, probs=probs, info=info, **dbg)
 
 
+# every window form: registers only (n < 10, and the 2-4-qubit windows after qubit 7),
+# qubits 0-7 with three lane qubits (n >= 10), and 5, 6, 7-qubit windows with one, two,
+# three lane qubits (n = 13, 14, 15; n = 17 has 5 + 4)
 @pytest.mark.parametrize("n,p,edges_kind", [(2, 1, "one"), (3, 2, "ring"), (4, 2, "ring"), (7, 2, "reg"),
-                                            (8, 1, "reg"), (12, 3, "reg"), (14, 2, "reg")])
+                                            (8, 1, "reg"), (10, 2, "reg"), (12, 3, "reg"), (13, 2, "reg"),
+                                            (14, 2, "reg"), (15, 2, "reg"), (17, 1, "reg")])
 def test_fused_matches_per_gate_and_oracle(qn, n, p, edges_kind):
     if edges_kind == "one":
         edges = np.array([[0, 1]], dtype=np.int32)

@@ -107,7 +107,8 @@ def test_tensor_core_precision_n14(qn):
     print(json.dumps({"precision_n14": out, "gates": G}))
     assert out["bf16x3"]["max_abs_amp_err"] < TOL_AMP and out["fp32"]["max_abs_amp_err"] < TOL_AMP
     assert out["tf32"]["max_abs_c_err"] < 4 * TF32_U * 12 * len(w.edges)
-    assert out["bf16x3"]["sweeps_per_trajectory"] == 12 and out["fp32"]["sweeps_per_trajectory"] == 12
+    # tensor cores: five-qubit windows (3 per layer at n=14); FP32: qubits 0-7 and 8-13 (2 per layer)
+    assert out["bf16x3"]["sweeps_per_trajectory"] == 12 and out["fp32"]["sweeps_per_trajectory"] == 8
 
 
 def test_precision_mode_validation(qn):
