@@ -218,6 +218,7 @@ constexpr int kFuse0 = 8;      // the window that holds qubit 0 (n >= 10): qubit
                                // 1-3 on lane bits, 4-7 in registers
 constexpr int kFuse = 7;       // at most, each of the other windows (n >= 10)
 constexpr int kFuseSmall = 5;  // n < 10: windows of five qubits, registers only
+constexpr int kFuseChunks = 8;  // chunks of kThreads fibre-threads per fused-sweep block
 
 struct NoiseDev {
     double gamma;              // damping (0 = off)

@@ -2746,6 +2746,10 @@ __device__ __forceinline__ uint64_t ev_of(const LayerView &L, uint32_t y) {
 // `lq` after them.  The phase of register element k, half e, is that of
 // y0 | 2 (k << rs) | e (rs the float4-index bit of register bit 0), split into
 // the thread's y0 and the block-wide tables of the patterns 2 (k << rs) and e.
+// A block takes kFuseChunks consecutive chunks of kThreads fibre-threads; each
+// thread copies its next chunk's float4 into its own shared slots (cp.async)
+// while it rotates the current one, so the loads stay in flight through the
+// arithmetic.
 template <int LQ, int RQ, bool HAS0, bool PRE, bool POST>
 __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerView Lp, LayerView Lr, LayerView Lq,
                                                              int q_lo) {
@@ -2753,6 +2757,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
     constexpr int DB = LQ + RQ;  // window bits in the float4 index
     constexpr int LO = 5 - LQ;   // lane bits that index fibres
     static_assert(NE <= 16 && LQ <= 3, "at most 16 float4 per thread and 3 lane qubits");
+    extern __shared__ float4 fslot[];  // [NE][kThreads]: each thread's landing slots
     const int t = blockIdx.y;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1);
@@ -2767,33 +2772,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
         __syncthreads();
     }
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
-    const int64_t tg = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31u;
-    // wb: the window's lane bits; r: the fibre.  With LQ > 0 a warp's fibres are
-    // 2^LO consecutive ones, so a warp stays or leaves as a whole.
+    // wb: the window's lane bits; the fibre r of chunk c.  With LQ > 0 a warp's
+    // fibres are 2^LO consecutive ones, so a warp is in or out as a whole.
     const uint32_t wb = LQ == 0 ? 0u : HAS0 ? lane & ((1u << LQ) - 1u) : lane >> LO;
-    const int64_t r = LQ == 0 ? tg
-                      : HAS0  ? (int64_t)(lane >> LQ) | ((tg >> 5) << LO)
-                              : (int64_t)(lane & ((1u << LO) - 1u)) | ((tg >> 5) << LO);
-    if (r >= nfib) return;
-    const int64_t fbase = ((r >> wlo) << (wlo + DB)) | (r & (((int64_t)1 << wlo) - 1)) | ((int64_t)wb << wlo);
-    const uint32_t y0 = (uint32_t)(2 * fbase);
-    float4 val[NE];
-#pragma unroll
-    for (int k = 0; k < NE; ++k) val[k] = p4[fbase + ((int64_t)k << rs)];
-    if (PRE) {
-        const uint64_t sv = Lp.s[t];
-        const uint32_t zm = Lp.zm[t];
-        const uint64_t ev0 = ev_of(Lp, y0);
-        const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lp.zc[t];
-        const uint64_t ev1 = evk[NE];
-#pragma unroll
-        for (int k = 0; k < NE; ++k) {
-            const uint32_t yk = 2u * ((uint32_t)k << rs);
-            cmul_inplace(val[k].x, val[k].y, split_phase(Lp, ev0, evk[k], sv, zp0, yk, zm));
-            cmul_inplace(val[k].z, val[k].w, split_phase(Lp, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
-        }
-    }
+    auto fibre_of = [&](int64_t c, int64_t &fbase) -> bool {
+        const int64_t tg = c * kThreads + threadIdx.x;
+        const int64_t r = LQ == 0 ? tg
+                          : HAS0  ? (int64_t)(lane >> LQ) | ((tg >> 5) << LO)
+                                  : (int64_t)(lane & ((1u << LO) - 1u)) | ((tg >> 5) << LO);
+        fbase = ((r >> wlo) << (wlo + DB)) | (r & (((int64_t)1 << wlo) - 1)) | ((int64_t)wb << wlo);
+        return r < nfib;
+    };
     const uint32_t mz = Lr.mz[t], mf = Lr.mf[t];
     const float cb = Lr.cb, sb = Lr.sb;
     // the 2x2 rotation of qubit q with the row signs of its Pauli's Z part:
@@ -2807,68 +2797,108 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
         sn1 = sb * s1;
     };
     const int ql = q_lo + (HAS0 ? 1 : 0);  // first lane qubit
-    if (HAS0) {
-        float c0, sn0, c1, sn1;
-        coeffs(0, c0, sn0, c1, sn1);
+    const int64_t c_begin = (int64_t)blockIdx.x * kFuseChunks;
+    int64_t fnext;
+    bool ok_next = fibre_of(c_begin, fnext);
+    if (ok_next) {
 #pragma unroll
-        for (int k = 0; k < NE; ++k) {
-            const float r0 = val[k].x, i0 = val[k].y, r1 = val[k].z, i1 = val[k].w;
-            val[k].x = c0 * r0 + sn0 * i1;
-            val[k].y = c0 * i0 - sn0 * r1;
-            val[k].z = c1 * r1 + sn1 * i0;
-            val[k].w = c1 * i1 - sn1 * r0;
-        }
+        for (int k = 0; k < NE; ++k) cp_async16(&fslot[k * kThreads + threadIdx.x], p4 + fnext + ((int64_t)k << rs));
     }
+    cp_async_commit();
+    for (int j = 0; j < kFuseChunks; ++j) {
+        const int64_t fbase = fnext;
+        const bool ok = ok_next;
+        float4 val[NE];
+        cp_async_wait<0>();
+        if (ok) {
 #pragma unroll
-    for (int j = 0; j < LQ; ++j) {
-        // own' = c own - i s partner with the row of the lane's own bit
-        const int b = HAS0 ? j : LO + j;
-        const uint32_t hb = (lane >> b) & 1u;
-        float c0, sn0, c1, sn1;
-        coeffs(ql + j, c0, sn0, c1, sn1);
-        const float co = hb ? c1 : c0, so = hb ? sn1 : sn0;
-#pragma unroll
-        for (int k = 0; k < NE; ++k) {
-            const float px = __shfl_xor_sync(0xffffffffu, val[k].x, 1 << b);
-            const float py = __shfl_xor_sync(0xffffffffu, val[k].y, 1 << b);
-            const float pz = __shfl_xor_sync(0xffffffffu, val[k].z, 1 << b);
-            const float pw = __shfl_xor_sync(0xffffffffu, val[k].w, 1 << b);
-            val[k] = make_float4(co * val[k].x + so * py, co * val[k].y - so * px, co * val[k].z + so * pw,
-                                 co * val[k].w - so * pz);
+            for (int k = 0; k < NE; ++k) val[k] = fslot[k * kThreads + threadIdx.x];
         }
-    }
+        __syncwarp();  // the slots' reads are performed before the next chunk's copies land in them
+        ok_next = j + 1 < kFuseChunks && fibre_of(c_begin + j + 1, fnext);
+        if (ok_next) {
 #pragma unroll
-    for (int j = 0; j < RQ; ++j) {
-        float c0, sn0, c1, sn1;
-        coeffs(ql + LQ + j, c0, sn0, c1, sn1);
-#pragma unroll
-        for (int k = 0; k < NE; ++k) {
-            if (k & (1 << j)) continue;
-            float4 &a = val[k];
-            float4 &b = val[k | (1 << j)];
-            const float nx = c0 * a.x + sn0 * b.y, ny = c0 * a.y - sn0 * b.x;
-            const float mx = c1 * b.x + sn1 * a.y, my = c1 * b.y - sn1 * a.x;
-            const float nz = c0 * a.z + sn0 * b.w, nw = c0 * a.w - sn0 * b.z;
-            const float mzv = c1 * b.z + sn1 * a.w, mw = c1 * b.w - sn1 * a.z;
-            a = make_float4(nx, ny, nz, nw);
-            b = make_float4(mx, my, mzv, mw);
+            for (int k = 0; k < NE; ++k) cp_async16(&fslot[k * kThreads + threadIdx.x], p4 + fnext + ((int64_t)k << rs));
         }
-    }
-    if (POST) {
-        const uint64_t sv = Lq.s[t];
-        const uint32_t zm = Lq.zm[t];
-        const uint64_t ev0 = ev_of(Lq, y0);
-        const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lq.zc[t];
-        const uint64_t ev1 = evk[NE];
+        cp_async_commit();
+        if (!ok) continue;
+        const uint32_t y0 = (uint32_t)(2 * fbase);
+        if (PRE) {
+            const uint64_t sv = Lp.s[t];
+            const uint32_t zm = Lp.zm[t];
+            const uint64_t ev0 = ev_of(Lp, y0);
+            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lp.zc[t];
+            const uint64_t ev1 = evk[NE];
 #pragma unroll
-        for (int k = 0; k < NE; ++k) {
-            const uint32_t yk = 2u * ((uint32_t)k << rs);
-            cmul_inplace(val[k].x, val[k].y, split_phase(Lq, ev0, evk[k], sv, zp0, yk, zm));
-            cmul_inplace(val[k].z, val[k].w, split_phase(Lq, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
+            for (int k = 0; k < NE; ++k) {
+                const uint32_t yk = 2u * ((uint32_t)k << rs);
+                cmul_inplace(val[k].x, val[k].y, split_phase(Lp, ev0, evk[k], sv, zp0, yk, zm));
+                cmul_inplace(val[k].z, val[k].w, split_phase(Lp, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
+            }
         }
-    }
+        if (HAS0) {
+            float c0, sn0, c1, sn1;
+            coeffs(0, c0, sn0, c1, sn1);
 #pragma unroll
-    for (int k = 0; k < NE; ++k) p4[fbase + ((int64_t)k << rs)] = val[k];
+            for (int k = 0; k < NE; ++k) {
+                const float r0 = val[k].x, i0 = val[k].y, r1 = val[k].z, i1 = val[k].w;
+                val[k].x = c0 * r0 + sn0 * i1;
+                val[k].y = c0 * i0 - sn0 * r1;
+                val[k].z = c1 * r1 + sn1 * i0;
+                val[k].w = c1 * i1 - sn1 * r0;
+            }
+        }
+#pragma unroll
+        for (int jq = 0; jq < LQ; ++jq) {
+            // own' = c own - i s partner with the row of the lane's own bit
+            const int b = HAS0 ? jq : LO + jq;
+            const uint32_t hb = (lane >> b) & 1u;
+            float c0, sn0, c1, sn1;
+            coeffs(ql + jq, c0, sn0, c1, sn1);
+            const float co = hb ? c1 : c0, so = hb ? sn1 : sn0;
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                const float px = __shfl_xor_sync(0xffffffffu, val[k].x, 1 << b);
+                const float py = __shfl_xor_sync(0xffffffffu, val[k].y, 1 << b);
+                const float pz = __shfl_xor_sync(0xffffffffu, val[k].z, 1 << b);
+                const float pw = __shfl_xor_sync(0xffffffffu, val[k].w, 1 << b);
+                val[k] = make_float4(co * val[k].x + so * py, co * val[k].y - so * px, co * val[k].z + so * pw,
+                                     co * val[k].w - so * pz);
+            }
+        }
+#pragma unroll
+        for (int jq = 0; jq < RQ; ++jq) {
+            float c0, sn0, c1, sn1;
+            coeffs(ql + LQ + jq, c0, sn0, c1, sn1);
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                if (k & (1 << jq)) continue;
+                float4 &a = val[k];
+                float4 &b = val[k | (1 << jq)];
+                const float nx = c0 * a.x + sn0 * b.y, ny = c0 * a.y - sn0 * b.x;
+                const float mx = c1 * b.x + sn1 * a.y, my = c1 * b.y - sn1 * a.x;
+                const float nz = c0 * a.z + sn0 * b.w, nw = c0 * a.w - sn0 * b.z;
+                const float mzv = c1 * b.z + sn1 * a.w, mw = c1 * b.w - sn1 * a.z;
+                a = make_float4(nx, ny, nz, nw);
+                b = make_float4(mx, my, mzv, mw);
+            }
+        }
+        if (POST) {
+            const uint64_t sv = Lq.s[t];
+            const uint32_t zm = Lq.zm[t];
+            const uint64_t ev0 = ev_of(Lq, y0);
+            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lq.zc[t];
+            const uint64_t ev1 = evk[NE];
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                const uint32_t yk = 2u * ((uint32_t)k << rs);
+                cmul_inplace(val[k].x, val[k].y, split_phase(Lq, ev0, evk[k], sv, zp0, yk, zm));
+                cmul_inplace(val[k].z, val[k].w, split_phase(Lq, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NE; ++k) p4[fbase + ((int64_t)k << rs)] = val[k];
+    }
 }
 
 // Phase only (a circuit whose layers have no mixer qubits left to fuse with).
@@ -3187,17 +3217,35 @@ cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, 
     return cudaGetLastError();
 }
 
+template <int LQ, int RQ, bool HAS0, bool PRE, bool POST>
+static cudaError_t fused_launch(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
+                                int q_lo, cudaStream_t s) {
+    constexpr size_t smem = sizeof(float4) * (size_t)(1 << RQ) * kThreads;  // the threads' landing slots
+    static const cudaError_t attr = cudaFuncSetAttribute(k_fused_sweep<LQ, RQ, HAS0, PRE, POST>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    const int64_t threads = ((int64_t)1 << (v.n - 1)) >> RQ;  // 2^LQ threads per fibre of LQ + RQ bits
+    const int64_t per_block = (int64_t)kThreads * kFuseChunks;
+    const dim3 grid((unsigned)((threads + per_block - 1) / per_block), (unsigned)v.b);
+    k_fused_sweep<LQ, RQ, HAS0, PRE, POST><<<grid, kThreads, smem, s>>>(v, Lp, Lr, Lq, q_lo);
+    return cudaGetLastError();
+}
+
 template <int LQ, int RQ, bool HAS0>
 static cudaError_t fused_dispatch(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
                                   int q_lo, bool pre, bool post, cudaStream_t s) {
-    const int64_t threads = ((int64_t)1 << (v.n - 1)) >> RQ;  // 2^LQ threads per fibre of LQ + RQ bits
-    const dim3 grid((unsigned)((threads + kThreads - 1) / kThreads), (unsigned)v.b);
     if (!HAS0 && pre) return cudaErrorInvalidValue;  // the first layer's phase rides on the qubit-0 window
-    if (HAS0 && pre && post) k_fused_sweep<LQ, RQ, HAS0, HAS0, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
-    else if (HAS0 && pre) k_fused_sweep<LQ, RQ, HAS0, HAS0, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
-    else if (post) k_fused_sweep<LQ, RQ, HAS0, false, true><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
-    else k_fused_sweep<LQ, RQ, HAS0, false, false><<<grid, kThreads, 0, s>>>(v, Lp, Lr, Lq, q_lo);
-    return cudaGetLastError();
+    if constexpr (HAS0 && LQ > 0) {
+        // the 8-qubit window needs n >= 10, so it is never a layer's last
+        if (post) return cudaErrorInvalidValue;
+        if (pre) return fused_launch<LQ, RQ, true, true, false>(v, Lp, Lr, Lq, q_lo, s);
+        return fused_launch<LQ, RQ, true, false, false>(v, Lp, Lr, Lq, q_lo, s);
+    } else {
+        if (HAS0 && pre && post) return fused_launch<LQ, RQ, HAS0, HAS0, true>(v, Lp, Lr, Lq, q_lo, s);
+        if (HAS0 && pre) return fused_launch<LQ, RQ, HAS0, HAS0, false>(v, Lp, Lr, Lq, q_lo, s);
+        if (post) return fused_launch<LQ, RQ, HAS0, false, true>(v, Lp, Lr, Lq, q_lo, s);
+        return fused_launch<LQ, RQ, HAS0, false, false>(v, Lp, Lr, Lq, q_lo, s);
+    }
 }
 
 cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
