@@ -749,8 +749,10 @@ std::vector<std::pair<int, int>> fused_windows(int n) {
 
 // All gates after the H layer as fused sweeps over the windows of fused_windows;
 // the cost phase of layer 0 rides on the first sweep and that of layer l+1 on the
-// last mixer sweep of layer l.
-qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, bool ensemble) {
+// last mixer sweep of layer l.  *norms: whether the circuit's last sweep also
+// formed 1/N_t (FP32 windows, last window off qubit 0), so no norm pass follows.
+qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, bool ensemble, bool *norms) {
+    *norms = false;
     const int n = h->n, p = h->p;
     const int E = (int)h->edges.size() / 2;
     for (int l = 0; l < p; ++l) {
@@ -789,9 +791,11 @@ qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, boo
             const int q_lo = wd.first, m = wd.second;
             const bool pre = l == 0 && q_lo == 0;
             const bool post = q_lo + m >= n && l + 1 < p;
+            const bool norm = q_lo + m >= n && l + 1 == p && q_lo > 0;
+            if (norm) *norms = true;
             QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));
             QN_CUDA(launch_fused_sweep(v, layer_view(h, l), layer_view(h, l), layer_view(h, post ? l + 1 : l), q_lo, m,
-                                       pre, post, h->stream));
+                                       pre, post, norm, h->stream));
             QN_TRY(prof_end(h, &ep));
             h->launches += 1;
             if (ensemble) h->sweep_bytes += amp_bytes * 16.0;
@@ -816,8 +820,9 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     QN_CUDA(launch_init(v, h->stream));
     QN_TRY(prof_end(h, &ep));
     h->launches += 1;
+    bool norms = false;
     if (use_fusion(h)) {
-        QN_TRY(run_fused_gates(h, v, amp_bytes, ensemble));
+        QN_TRY(run_fused_gates(h, v, amp_bytes, ensemble, &norms));
     } else {
         for (int g = n; g < G; ++g) {
             QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));
@@ -838,13 +843,16 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
     a.probs = ensemble ? h->probs : nullptr;
     a.sums = ensemble ? h->sums : nullptr;
     QN_TRY(probs_rows(h, b, &a, 0));
-    QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
-    QN_CUDA(launch_observe(v, a, h->stream));
-    QN_TRY(prof_end(h, &ep));
+    if (!norms) {
+        QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
+        QN_CUDA(launch_observe(v, a, h->stream));
+        QN_TRY(prof_end(h, &ep));
+        h->launches += 1;
+    }
     QN_TRY(prof_begin(h, &ep, 2, amp_bytes * 8.0));
     QN_CUDA(launch_probs(v, a, h->stream));
     QN_TRY(prof_end(h, &ep));
-    h->launches += 2 + (a.parts > 1 ? 1 : 0);
+    h->launches += 1 + (a.parts > 1 ? 1 : 0);
     return QN_OK;
 }
 

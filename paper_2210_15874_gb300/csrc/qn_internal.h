@@ -293,10 +293,11 @@ cudaError_t launch_slot_readout(const BatchView &v, const int32_t *oslot, const 
                                 const ReadTail &rt, float2 *out, cudaStream_t s);
 // Fused layers (Pauli-only): per-trajectory layer parameters from the branch
 // tables, then sweeps applying the rotations of qubits [q_lo, q_lo + m) of
-// layer Lr, with layer Lp's phase before them (pre) and layer Lq's after (post).
+// layer Lr, with layer Lp's phase before them (pre) and layer Lq's after (post);
+// norm (the circuit's last sweep, q_lo > 0): also 1/N_t, as launch_observe.
 cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, int E, cudaStream_t s);
 cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
-                               int q_lo, int m, bool pre, bool post, cudaStream_t s);
+                               int q_lo, int m, bool pre, bool post, bool norm, cudaStream_t s);
 cudaError_t launch_phase_sweep(const BatchView &v, const LayerView &L, cudaStream_t s);
 // Tensor-core form of a fused sweep (n >= 11): the window's rotations as two
 // GEMMs with the +-1 Hadamard matrix (qn_tc.cu), PRE / POST phases as for

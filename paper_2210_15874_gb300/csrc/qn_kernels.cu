@@ -2103,13 +2103,48 @@ __global__ void k_fork_finish(SlotView sv) {
 // forms <C>_t and adds S1, S2 in trajectory order.
 // ---------------------------------------------------------------------------
 
+// The end of a norm pass over state t, blocks tile = 0 .. ntiles-1 (kThreads
+// threads each, every thread holding its double-float sum (sh, sl)): the block
+// sum goes to partials, and the last block to finish stores 1/N_t.
+__device__ void norm_finish(const BatchView &v, int t, int tile, int ntiles, float sh, float sl) {
+    __shared__ double redd[kThreads / 32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double sn = df_warp_sum(sh, sl);
+    if (lane == 0) redd[warp] = sn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+        v.partials[((size_t)t * v.tiles + tile) * 4] = sum;
+        __threadfence();
+        const unsigned prev = atomicAdd(&v.counters[t], 1u);
+        last = prev == (unsigned)(ntiles - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0;
+    for (int i = threadIdx.x; i < ntiles; i += kThreads) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    __syncthreads();
+    if (lane == 0) redd[warp] = s0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double N = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) N += redd[w];
+        if (!(N > 0.0) || !isfinite(N)) atomicOr(v.status, 2);
+        v.inv_norm[t] = 1.0 / N;
+        v.counters[t] = 0;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
     const int t = blockIdx.y;
     const int tile = blockIdx.x;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
-    __shared__ double redd[kThreads / 32];
-    __shared__ int last;
     const TrajState st = v.st[t];
     SweepCtx c;
     c.Fa = v.frame_x[(size_t)t * (v.G + 1) + v.G] ^ st.J;
@@ -2129,35 +2164,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
             df_add(sh, sl, prob_of(f1, val.z, val.w));
         }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double sn = df_warp_sum(sh, sl);
-    if (lane == 0) redd[warp] = sn;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
-        v.partials[((size_t)t * v.tiles + tile) * 4] = sum;
-        __threadfence();
-        const unsigned prev = atomicAdd(&v.counters[t], 1u);
-        last = prev == (unsigned)(v.tiles - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double s0 = 0.0;
-    for (int i = threadIdx.x; i < v.tiles; i += kThreads) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-    __syncthreads();
-    if (lane == 0) redd[warp] = s0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double N = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) N += redd[w];
-        if (!(N > 0.0) || !isfinite(N)) atomicOr(v.status, 2);
-        v.inv_norm[t] = 1.0 / N;
-        v.counters[t] = 0;
-    }
+    norm_finish(v, t, tile, v.tiles, sh, sl);
 }
 
 constexpr int kAccChunk = 32;
@@ -2749,8 +2756,10 @@ __device__ __forceinline__ uint64_t ev_of(const LayerView &L, uint32_t y) {
 // A block takes kFuseChunks consecutive chunks of kThreads fibre-threads; each
 // thread copies its next chunk's float4 into its own shared slots (cp.async)
 // while it rotates the current one, so the loads stay in flight through the
-// arithmetic.
-template <int LQ, int RQ, bool HAS0, bool PRE, bool POST>
+// arithmetic.  NORM (the circuit's last sweep): the block also sums |psi|^2 of
+// what it stores, and the last block of the state stores 1/N_t, as the norm
+// pass does.
+template <int LQ, int RQ, bool HAS0, bool PRE, bool POST, bool NORM>
 __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerView Lp, LayerView Lr, LayerView Lq,
                                                              int q_lo) {
     constexpr int NE = 1 << RQ;
@@ -2805,6 +2814,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
         for (int k = 0; k < NE; ++k) cp_async16(&fslot[k * kThreads + threadIdx.x], p4 + fnext + ((int64_t)k << rs));
     }
     cp_async_commit();
+    float sh = 0.0f, sl = 0.0f;  // NORM: this thread's sum of |psi|^2 (double-float)
     for (int j = 0; j < kFuseChunks; ++j) {
         const int64_t fbase = fnext;
         const bool ok = ok_next;
@@ -2898,7 +2908,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
         }
 #pragma unroll
         for (int k = 0; k < NE; ++k) p4[fbase + ((int64_t)k << rs)] = val[k];
+        if (NORM) {
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                df_add(sh, sl, prob_of(1.0f, val[k].x, val[k].y));
+                df_add(sh, sl, prob_of(1.0f, val[k].z, val[k].w));
+            }
+        }
     }
+    if (NORM) norm_finish(v, t, blockIdx.x, gridDim.x, sh, sl);
 }
 
 // Phase only (a circuit whose layers have no mixer qubits left to fuse with).
@@ -3217,24 +3235,31 @@ cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, 
     return cudaGetLastError();
 }
 
-template <int LQ, int RQ, bool HAS0, bool PRE, bool POST>
+template <int LQ, int RQ, bool HAS0, bool PRE, bool POST, bool NORM = false>
 static cudaError_t fused_launch(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
                                 int q_lo, cudaStream_t s) {
     constexpr size_t smem = sizeof(float4) * (size_t)(1 << RQ) * kThreads;  // the threads' landing slots
-    static const cudaError_t attr = cudaFuncSetAttribute(k_fused_sweep<LQ, RQ, HAS0, PRE, POST>,
+    static const cudaError_t attr = cudaFuncSetAttribute(k_fused_sweep<LQ, RQ, HAS0, PRE, POST, NORM>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
     const int64_t threads = ((int64_t)1 << (v.n - 1)) >> RQ;  // 2^LQ threads per fibre of LQ + RQ bits
     const int64_t per_block = (int64_t)kThreads * kFuseChunks;
-    const dim3 grid((unsigned)((threads + per_block - 1) / per_block), (unsigned)v.b);
-    k_fused_sweep<LQ, RQ, HAS0, PRE, POST><<<grid, kThreads, smem, s>>>(v, Lp, Lr, Lq, q_lo);
+    const int64_t blocks = (threads + per_block - 1) / per_block;
+    if (NORM && blocks > v.tiles) return cudaErrorInvalidValue;  // the partial sums hold v.tiles per state
+    const dim3 grid((unsigned)blocks, (unsigned)v.b);
+    k_fused_sweep<LQ, RQ, HAS0, PRE, POST, NORM><<<grid, kThreads, smem, s>>>(v, Lp, Lr, Lq, q_lo);
     return cudaGetLastError();
 }
 
 template <int LQ, int RQ, bool HAS0>
 static cudaError_t fused_dispatch(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
-                                  int q_lo, bool pre, bool post, cudaStream_t s) {
+                                  int q_lo, bool pre, bool post, bool norm, cudaStream_t s) {
     if (!HAS0 && pre) return cudaErrorInvalidValue;  // the first layer's phase rides on the qubit-0 window
+    if (norm) {
+        // the circuit's last window (off qubit 0, so n > 5): no later phase
+        if constexpr (HAS0) return cudaErrorInvalidValue;
+        else return post ? cudaErrorInvalidValue : fused_launch<LQ, RQ, false, false, false, true>(v, Lp, Lr, Lq, q_lo, s);
+    }
     if constexpr (HAS0 && LQ > 0) {
         // the 8-qubit window needs n >= 10, so it is never a layer's last
         if (post) return cudaErrorInvalidValue;
@@ -3249,7 +3274,7 @@ static cudaError_t fused_dispatch(const BatchView &v, const LayerView &Lp, const
 }
 
 cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
-                               int q_lo, int m, bool pre, bool post, cudaStream_t s) {
+                               int q_lo, int m, bool pre, bool post, bool norm, cudaStream_t s) {
     if (m < 1 || q_lo < 0 || q_lo + m > v.n) return cudaErrorInvalidValue;
     // lane qubits need whole warps of fibres (2^(RQ+5) float4 per state, RQ = 4) and,
     // off qubit 0, the 5 - LQ float4-index bits below the window free (q_lo - 1 >= 5 - LQ,
@@ -3257,29 +3282,29 @@ cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const La
     const bool lanes_ok = v.n >= 10 && (q_lo == 0 || q_lo - 1 >= 9 - m);
     if (q_lo == 0) {
         switch (m) {
-        case 1: return fused_dispatch<0, 0, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        case 2: return fused_dispatch<0, 1, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        case 3: return fused_dispatch<0, 2, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        case 4: return fused_dispatch<0, 3, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        case 5: return fused_dispatch<0, 4, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        case 1: return fused_dispatch<0, 0, true>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+        case 2: return fused_dispatch<0, 1, true>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+        case 3: return fused_dispatch<0, 2, true>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+        case 4: return fused_dispatch<0, 3, true>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+        case 5: return fused_dispatch<0, 4, true>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
         case 8:  // qubit 0 in the float4, 1-3 on lane bits, 4-7 in registers
             if (!lanes_ok) return cudaErrorInvalidValue;
-            return fused_dispatch<3, 4, true>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+            return fused_dispatch<3, 4, true>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
         default: return cudaErrorInvalidValue;
         }
     }
     switch (m) {
-    case 1: return fused_dispatch<0, 1, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    case 2: return fused_dispatch<0, 2, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    case 3: return fused_dispatch<0, 3, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-    case 4: return fused_dispatch<0, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+    case 1: return fused_dispatch<0, 1, false>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+    case 2: return fused_dispatch<0, 2, false>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+    case 3: return fused_dispatch<0, 3, false>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+    case 4: return fused_dispatch<0, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
     case 5:
     case 6:
     case 7:  // m - 4 qubits on lane bits, 4 in registers
         if (!lanes_ok) return cudaErrorInvalidValue;
-        if (m == 5) return fused_dispatch<1, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        if (m == 6) return fused_dispatch<2, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
-        return fused_dispatch<3, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, s);
+        if (m == 5) return fused_dispatch<1, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+        if (m == 6) return fused_dispatch<2, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
+        return fused_dispatch<3, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
     default: return cudaErrorInvalidValue;
     }
 }
