@@ -206,6 +206,7 @@ struct qn_batch {
     // phase-gate groups of shared-prefix mode with damping
     std::vector<GateGroup> groups;
     std::vector<int32_t> group_at;  // [G] index of the group that starts at gate g, or -1
+    bool split8 = false;            // mixer blocks 0-7 and 8-15 rotated whole (see build_groups)
     GateGroup *gr_dev = nullptr;
     int64_t gr_cap = 0;
     unsigned long long *gv_H = nullptr;  // [2][gv_cap][256]
@@ -452,6 +453,11 @@ void build_gates(qn_batch *h) {
 // phase group before them (whose apply sweep forms the first block's joint).
 bool mixer_blocks_fit(int n, int E) { return n >= 12 && E > 0; }
 constexpr int kWideBlock = 2 * kMixQ;  // qubits of the layer's first mixer block
+// Two 8-qubit blocks then full 4-qubit ones: the last phase group's sweep rotates
+// qubits 0-7 whole, the next sweep applies their factors, rotates qubits 8-11 and
+// forms the joint of 8-15 (12-15 rotated without being kept), the one after
+// rotates 12-15: one sweep fewer per layer than blocks 0-7, 8-11, 12-15, ...
+bool split8_fits(int n) { return n >= 20 && n % kMixQ == 0; }
 
 // Phase-gate groups of every layer: greedy runs of consecutive ZZ gates whose
 // qubits number at most kMaxGroupQubits (joints of 2^10 bins), at most
@@ -461,6 +467,7 @@ void build_groups(qn_batch *h) {
     const int n = h->n, E = (int)h->edges.size() / 2;
     h->groups.clear();
     h->group_at.assign(h->gates.size(), -1);
+    h->split8 = false;
     for (int l = 0; l < h->p; ++l) {
         const int base = n + l * (E + n);
         int g = base;
@@ -504,17 +511,21 @@ void build_groups(qn_batch *h) {
         if (!mixer_blocks_fit(n, E)) continue;
         // mixer rotations in blocks of consecutive qubits: qubits 0-7 first (the sweep of the
         // layer's last phase group rotates qubits 0-3 and forms this block's joint, the block's
-        // own sweep rotates qubits 4-7), then kMixQ at a time
-        for (int q = 0; q < n; q += q == 0 ? kWideBlock : kMixQ) {
+        // own sweep rotates qubits 4-7), then kMixQ at a time; with split8 qubits 0-7 and 8-15
+        // (the sweep before rotates all of 0-7; blocks 8-15 split over two sweeps)
+        h->split8 = split8_fits(n);
+        for (int q = 0; q < n;) {
+            const int w = q == 0 || (q == kWideBlock && h->split8) ? kWideBlock : kMixQ;
             GateGroup z;
             std::memset(&z, 0, sizeof z);
             z.kind = 1;
             z.g0 = base + E + q;
-            z.m = z.s = std::min(q == 0 ? kWideBlock : kMixQ, n - q);
+            z.m = z.s = std::min(w, n - q);
             for (int k = 0; k < z.m; ++k) {
                 z.sp[k] = q + k;
                 z.ei[k] = z.ej[k] = k;
             }
+            q += w;
             z.c = h->dgates_host[z.g0].c;
             z.sn = h->dgates_host[z.g0].s;
             h->group_at[z.g0] = (int32_t)h->groups.size();
@@ -1017,7 +1028,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             const bool first = z.kind == 0 && (gi == 0 || h->groups[gi - 1].g0 + h->groups[gi - 1].m != z.g0);
             // a phase group before the layer's first mixer block (qubits 0-7) also rotates qubits
             // 0-3 and forms that block's joint (k_group_mix)
-            const bool wide_next = z.kind == 0 && nz && nz->kind == 1 && nz->s == kWideBlock;
+            const bool wide_next = z.kind == 0 && nz && nz->kind == 1 && nz->s == kWideBlock && nz->sp[0] == 0;
             GroupView gv;
             gv.grp = h->gr_dev + gi;
             gv.next = nz && nz->kind == 0 ? h->gr_dev + gi + 1 : nullptr;
@@ -1064,14 +1075,29 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             if (wide_next) {
                 mm = mix_map(n, 0, kMixQ, {4, 5, 6, 7});
                 mm.tanf = std::fabs(nz->c) >= std::fabs(nz->sn);
+                mm.full8 = h->split8;  // rotate qubits 4-7 as well
             }
             if (z.kind == 1) {
                 std::vector<int> next;
                 if (nz && nz->kind == 1)
                     for (int k = 0; k < nz->s; ++k) next.push_back(nz->sp[k]);
-                const bool wide = z.s == kWideBlock;  // its qubits 0-3 were rotated by the sweep before
-                mm = wide ? mix_map(n, kMixQ, kMixQ, next) : mix_map(n, z.sp[0], z.s, next);
-                mm.wide = wide;
+                const bool wide = z.s == kWideBlock;
+                if (wide && z.sp[0] == 0 && h->split8) {
+                    // the factors of 0-7 (all rotated before), the rotations of 8-11 and the
+                    // joint of 8-15 (12-15 rotated without being kept)
+                    mm = mix_map(n, kWideBlock, kMixQ, {12, 13, 14, 15});
+                    mm.wide = 2;
+                    mm.wsh = 3;  // qubits 4-7: f bits 3-6
+                } else if (wide && z.sp[0] == kWideBlock) {
+                    // the second half of 8-15: the rotations of 12-15, then the block's factors
+                    mm = mix_map(n, kWideBlock + kMixQ, kMixQ, next);
+                    mm.wide = 3;
+                    mm.wsh = kWideBlock - 1;  // qubits 8-11: f bits 7-10
+                } else {
+                    // a block over 0-7 whose qubits 0-3 the sweep before rotated, or kMixQ qubits
+                    mm = wide ? mix_map(n, kMixQ, kMixQ, next) : mix_map(n, z.sp[0], z.s, next);
+                    mm.wide = wide ? 1 : 0;
+                }
                 mm.tanf = std::fabs(z.c) >= std::fabs(z.sn);
                 mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
                 final_norms = final_norms || mm.final_norm;

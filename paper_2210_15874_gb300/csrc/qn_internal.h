@@ -117,8 +117,18 @@ struct MixMap {
     int32_t tanf;     // |cos beta| >= |sin beta|: rotations in the tan form, else the cot form
     int32_t keep = 0;  // with final_norm: form only the norms and leave the states as they were
                        // (the sigma pass applies the block; full blocks off qubit 0 only)
-    int32_t wide = 0;  // qubits 4-7 of a block over qubits 0-7 whose qubits 0-3 the sweep before
-                       // rotated: the factor table covers all eight (L bits = qubits 1-3)
+    // 8-qubit blocks (the factor table covers eight qubits, 256 entries):
+    //  1  qubits 4-7 of the block over qubits 0-7 whose qubits 0-3 the sweep before rotated
+    //     (L bits = qubits 1-3, A = qubits 4-7)
+    //  2  the factors of the block over qubits 0-7, all of which the sweep before rotated
+    //     (qubit 0 the float4 half, qubits 1-3 the L bits, qubits 4-7 the tile's f bits
+    //     wsh .. wsh+3), with the rotations of A, the first half of the next (8-qubit) block,
+    //     and that block's joint over A and B (B = its second half, rotated without being kept)
+    //  3  the second half (A) of an 8-qubit block whose first half the sweep before rotated:
+    //     that half sits on the tile's f bits wsh .. wsh+3, A is the high half of the index
+    int32_t wide = 0;
+    int32_t wsh = 0;
+    int32_t full8 = 0;  // k_group_mix: rotate qubits 4-7 too and bin the stored values
 };
 
 // The circuit's last mixer block when its sweep kept the states (MixMap::keep):

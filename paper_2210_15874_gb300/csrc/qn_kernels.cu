@@ -1161,7 +1161,14 @@ __device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
 //             rotated qubits 0-3, k_group_mix): a full next block, and the factor
 //             table of all eight qubits (qubit 0 = the float4 half, qubits 1-3 =
 //             the lane bits L, qubits 4-7 = the element index j)
-enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixKeep = 4, kMixWide = 8 };
+//   kMixW1    (MixMap::wide 2) the factors of the block over qubits 0-7, all eight
+//             rotated by the sweep before (k_group_mix FULL); A = the first half of
+//             the next, 8-qubit block, B its second half; that block's joint has
+//             256 bins, A | B << 4
+//   kMixW2    (MixMap::wide 3) the second half A of an 8-qubit block whose first
+//             half (tile f bits wsh .. wsh+3) kMixW1 rotated: the block's factors
+//             by A << 4 | first half, and a full next block
+enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixKeep = 4, kMixWide = 8, kMixW1 = 16, kMixW2 = 32 };
 
 template <bool TANF, int VAR>
 __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
@@ -1177,20 +1184,21 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     const GateGroup *nx = kFix ? (VAR == kMixHist ? gv.next : nullptr) : gv.next;
     const bool has0 = kFix ? false : mm.has0 != 0;
     const int M = kFix ? kMixQ : mm.M;
-    const int nN = kFix ? ((VAR == kMixMid || VAR == kMixWide) ? kMixQ : 0) : mm.nN;
+    constexpr bool kW8 = VAR == kMixWide || VAR == kMixW1 || VAR == kMixW2;  // 256-entry factor table
+    const int nN = kFix ? ((VAR == kMixMid || kW8) ? kMixQ : 0) : mm.nN;
     const bool final_norm = kFix ? VAR == kMixKeep : mm.final_norm != 0;
     const float c = gv.grp->c, sn = gv.grp->sn;
     const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;  // rotation = rsc * (tangent form)
     float scM = 1.0f;  // rsc^M: the block's rotations, folded into its factors
     for (int i = 0; i < M; ++i) scM *= rsc;
-    constexpr int kDf = VAR == kMixWide ? 256 : 16;
+    constexpr int kDf = kW8 ? 256 : 16;
     __shared__ float Df[kDf];
     // the block's histogram of the next phase group's joint (variants that form one; 2^-60
     // fixed point, one row for all warps), and the per-warp rows of the next mixer block's joint
     constexpr bool kHist = VAR == kMixAny || VAR == kMixHist;
     __shared__ unsigned long long hist[kHist ? kGroupBins : 1];
     __shared__ float red[kWarps * kJointBins];
-    if (VAR == kMixWide) {
+    if (kW8) {
         for (int i = threadIdx.x; i < kDf; i += kMixThreads) Df[i] = gv.T[(size_t)slot * kGroupBins + i].x * scM;
     } else if (threadIdx.x < 16u) {
         Df[threadIdx.x] = threadIdx.x < (1u << M) ? gv.T[(size_t)slot * kGroupBins + threadIdx.x].x * scM : 0.0f;
@@ -1331,6 +1339,14 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
                 f0 = Df[(j << 4) | (tL << 1)];
                 f1 = Df[(j << 4) | (tL << 1) | 1];
             }
+            if (VAR == kMixW1) {  // qubit 0 the half, qubits 1-3 L, qubits 4-7 the tile's f bits
+                const int t47 = (int)((fb >> mm.wsh) & 15u) << 4;
+                f0 = Df[t47 | (tL << 1)];
+                f1 = Df[t47 | (tL << 1) | 1];
+            }
+            if (VAR == kMixW2) {  // the block's first half on the tile's f bits, its second j
+                f0 = f1 = Df[(j << 4) | (int)((fb >> mm.wsh) & 15u)];
+            }
             if (VAR == kMixKeep) {  // nothing stored: |f x|^2 as the sigma pass forms it
                 df_add(nh, nl, prob_of(f0, x[j].x, x[j].y));
                 df_add(nh, nl, prob_of(f1, x[j].z, x[j].w));
@@ -1387,7 +1403,24 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         if (nN > 0 || has0) __syncthreads();  // the buffer is refilled two tiles on
     }
     allow_dependent_launch();
-    if (nN > 0) {
+    if (VAR == kMixW1) {
+        // 256 bins A | B << 4: this thread's A is tH and its B is j; sum over the L lanes
+        float sc2 = 1.0f;  // B was rotated up to rsc per qubit: restore |.|^2
+        for (int i = 0; i < kMixQ; ++i) sc2 *= rsc * rsc;
+        __syncthreads();  // the tile buffers now hold the bins
+        float *bins = reinterpret_cast<float *>(mix_buf);
+#pragma unroll
+        for (int j = 0; j < kMixE; ++j) {
+            float x = acc[j] * sc2;
+#pragma unroll
+            for (int off = 1; off < (1 << kMixL); off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (tL == 0) bins[tH | (j << 4)] = x;
+        }
+        __syncthreads();
+        unsigned long long *H = gv.Hnext + (size_t)slot * kGroupBins;
+        for (int b = threadIdx.x; b < 256; b += kMixThreads)
+            if (bins[b] > 0.0f) atomicAdd(H + b, __double2ull_rn((double)bins[b] * kHistScale));
+    } else if (nN > 0) {
         // bins of the next block are the low nN bits of j: fold, then lanes and warps
         const int nb = 1 << nN;
 #pragma unroll
@@ -1474,7 +1507,10 @@ __device__ __forceinline__ void rx_lanes_t(float4 &o, int lanebit, float t) {
 // tangent-form rotations), the rotations of qubits 0-3, the store; then the
 // rotations of qubits 4-7, binned by the stored bits of qubits 0-7 (256 bins:
 // e | lane bits 0-2 << 1 | j << 4).  No pending op (the gate before is a group).
-template <bool TANF>
+// FULL: the rotations of qubits 4-7 are kept too (stored after them), so the
+// block's joint is binned from the stored state and its own sweep only applies
+// its factors (MixMap::wide 2).
+template <bool TANF, bool FULL>
 __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, GroupView gv, MixMap mm) {
     extern __shared__ float4 mix_buf[];  // [2][kMixE][kMixThreads]
     constexpr int kWarps = kMixThreads / 32;
@@ -1486,8 +1522,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, Group
     const GateGroup *gp = gv.grp;
     const float c = gv.vc, sn = gv.vs;  // the mixer layer's angle
     const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;
-    float scM = 1.0f;  // rsc^4: the tangent-form rotations of qubits 0-3, folded into T
-    for (int i = 0; i < kMixQ; ++i) scM *= rsc;
+    float scM = 1.0f;  // rsc^4 (FULL: rsc^8): the tangent-form rotations kept, folded into T
+    for (int i = 0; i < (FULL ? 2 : 1) * kMixQ; ++i) scM *= rsc;
     __shared__ float2 Ts[kGroupBins];
     __shared__ uint16_t binj[kMixE];
     float *red = reinterpret_cast<float *>(mix_buf);  // [kWarps][256], after the tile loop
@@ -1551,14 +1587,20 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, Group
 #pragma unroll
             for (int j = 0; j < kMixE; ++j) rx_lanes_t<TANF>(x[j], 1 << i, rt);
         }
+        if (!FULL) {
 #pragma unroll
-        for (int j = 0; j < kMixE; ++j) p4[fb | ((uint32_t)j << 3)] = x[j];
-        // the rotations of qubits 4-7, kept only as squared magnitudes
+            for (int j = 0; j < kMixE; ++j) p4[fb | ((uint32_t)j << 3)] = x[j];
+        }
+        // the rotations of qubits 4-7, kept only as squared magnitudes unless FULL
 #pragma unroll
         for (int i = 0; i < kMixQ; ++i) {
 #pragma unroll
             for (int j = 0; j < kMixE; ++j)
                 if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
+        }
+        if (FULL) {
+#pragma unroll
+            for (int j = 0; j < kMixE; ++j) p4[fb | ((uint32_t)j << 3)] = x[j];
         }
 #pragma unroll
         for (int j = 0; j < kMixE; ++j) {
@@ -1567,8 +1609,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, Group
         }
     }
     allow_dependent_launch();
-    float sc2 = 1.0f;  // qubits 4-7 were rotated up to rsc each: restore |.|^2
-    for (int i = 0; i < kMixQ; ++i) sc2 *= rsc * rsc;
+    float sc2 = 1.0f;  // qubits 4-7 were rotated up to rsc each: restore |.|^2 (FULL: in T)
+    for (int i = 0; i < (FULL ? 0 : kMixQ); ++i) sc2 *= rsc * rsc;
     __syncthreads();  // every thread is done with the tile buffers, which now hold the per-warp bins
     // sum over lane bits 3-4 (f7-f8); lanes 0-7 then hold the bins of their qubits 1-3
 #pragma unroll
@@ -3366,7 +3408,10 @@ static cudaError_t launch_mix_sweep_attrs() {
                             (const void *)k_mix_sweep<false, kMixAny>,  (const void *)k_mix_sweep<false, kMixMid>,
                             (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixKeep>,
                             (const void *)k_mix_sweep<true, kMixWide>,  (const void *)k_mix_sweep<false, kMixWide>,
-                            (const void *)k_group_mix<true>,            (const void *)k_group_mix<false>};
+                            (const void *)k_mix_sweep<true, kMixW1>,    (const void *)k_mix_sweep<false, kMixW1>,
+                            (const void *)k_mix_sweep<true, kMixW2>,    (const void *)k_mix_sweep<false, kMixW2>,
+                            (const void *)k_group_mix<true, false>,     (const void *)k_group_mix<false, false>,
+                            (const void *)k_group_mix<true, true>,      (const void *)k_group_mix<false, true>};
         for (const void *k : ks) {
             const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem);
             if (e != cudaSuccess) return e;
@@ -3382,6 +3427,26 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
     const unsigned blocks = mm.ntile >= 2 ? (1u << mm.ntile) / kMixSubs : 1u;
     const dim3 grid(blocks, (unsigned)active), block(kMixThreads);
     int var = kMixAny;
+    if (mm.wide == 2 || mm.wide == 3) {
+        // full blocks off qubit 0 with a full next block; the other half's four f bits
+        // (wsh ..) lie on tile bits; kMixW1 also needs qubits 1-3 on the L bits
+        bool ok = mm.M == kMixQ && !mm.has0 && mm.nN == kMixQ && !gv.next && !mm.final_norm && mm.wsh >= 0 &&
+                  mm.wsh + 4 <= v.n - 1;
+        for (int i = 0; i < 5 && ok; ++i) {
+            const int f = i < kMixL ? mm.fL[i] : -1;
+            if (f >= mm.wsh && f < mm.wsh + 4) ok = false;
+        }
+        for (int i = 0; i < kMixQ && ok; ++i)
+            if ((mm.fA[i] >= mm.wsh && mm.fA[i] < mm.wsh + 4) || (mm.fB[i] >= mm.wsh && mm.fB[i] < mm.wsh + 4))
+                ok = false;
+        if (mm.wide == 2) ok = ok && mm.fL[0] == 0 && mm.fL[1] == 1 && mm.fL[2] == 2 && mm.wsh == 3;
+        if (!ok) return cudaErrorInvalidValue;
+        if (mm.wide == 2)
+            return mm.tanf ? launch_pdl_smem(k_mix_sweep<true, kMixW1>, grid, block, kMixSmem, s, v, gv, mm)
+                           : launch_pdl_smem(k_mix_sweep<false, kMixW1>, grid, block, kMixSmem, s, v, gv, mm);
+        return mm.tanf ? launch_pdl_smem(k_mix_sweep<true, kMixW2>, grid, block, kMixSmem, s, v, gv, mm)
+                       : launch_pdl_smem(k_mix_sweep<false, kMixW2>, grid, block, kMixSmem, s, v, gv, mm);
+    }
     if (mm.wide) {
         // qubits 4-7 with the factors of qubits 0-7: the lane bits must be qubits 1-3, the block
         // qubits 4-7 and a full next block
@@ -3417,8 +3482,11 @@ cudaError_t launch_group_mix(const BatchView &v, const GroupView &gv, const MixM
     if (!natural || gv.pend) return cudaErrorInvalidValue;
     const unsigned blocks = mm.ntile >= 2 ? (1u << mm.ntile) / kMixSubs : 1u;
     const dim3 grid(blocks, (unsigned)active), block(kMixThreads);
-    return mm.tanf ? launch_pdl_smem(k_group_mix<true>, grid, block, kMixSmem, s, v, gv, mm)
-                   : launch_pdl_smem(k_group_mix<false>, grid, block, kMixSmem, s, v, gv, mm);
+    if (mm.full8)
+        return mm.tanf ? launch_pdl_smem(k_group_mix<true, true>, grid, block, kMixSmem, s, v, gv, mm)
+                       : launch_pdl_smem(k_group_mix<false, true>, grid, block, kMixSmem, s, v, gv, mm);
+    return mm.tanf ? launch_pdl_smem(k_group_mix<true, false>, grid, block, kMixSmem, s, v, gv, mm)
+                   : launch_pdl_smem(k_group_mix<false, false>, grid, block, kMixSmem, s, v, gv, mm);
 }
 
 cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
