@@ -77,6 +77,9 @@ CASES = {
     "n16_bench_noise": (16, 3, 72, 512, dict(p1=1e-3, p2=1e-2, damping=5e-3), 3),  # last block pending
     "n13_one_qubit_block": (13, 2, 73, 400, dict(p1=5e-3, p2=2e-2, damping=0.02), 4),  # generic last block
     "n9_per_gate_mixers": (9, 2, 74, 600, dict(p1=5e-3, p2=2e-2, damping=0.03), 4),  # mixer gates one by one
+    # mixer blocks 0-7 (rotated whole by the last phase group's sweep), 8-15 (over two sweeps),
+    # 16-19; heavy noise so that slots fork at every block
+    "n20_split8_blocks": (20, 2, 75, 16, dict(p1=3e-2, p2=8e-2, damping=0.05), 3),
 }
 
 
@@ -113,7 +116,7 @@ def test_shared_prefix_states_against_oracle(qn, case, fusion):
 
 def test_bench_mode_full_ensemble_against_oracle_and_per_trajectory_path(qn):
     """The bench's own run (n=20, p=3, depolarizing + damping, K=4096, shared prefixes
-    with phase groups and 4-qubit mixer blocks, the last block pending): trajectories
+    with phase groups and mixer blocks 0-7, 8-15, 16-19, the last block pending): trajectories
     2000..2047 of that run against the oracle, member by member (amplitudes for
     2000..2015); and the Kraus strings of all 4096 trajectories against the
     one-state-per-trajectory path (FP64 draws gate by gate): Pauli codes bit-exact,
