@@ -223,6 +223,7 @@ def measure(qn, w, args, mode, stream, rank, world, local, pg, with_e2e, precisi
     b.set_sharing(sharing)
     b.set_fusion(fusion)
     b.set_precision(precision)
+    b.set_launch_mode(getattr(args, "launch_mode", 0))
     # weak scaling: rank r evolves global trajectories [r K, (r+1) K)
     if world > 1:
         b.set_offset(rank * w.trajectories)
@@ -382,6 +383,12 @@ def gpu_arm(args):
     other = None
     if not args.single_mode and other_mode != main_mode:
         other = measure(qn, w, args, other_mode, stream, rank, world, local, pg, with_e2e=False)
+    # the same step with device-driven launches, and as a replayed CUDA graph
+    modes = {}
+    if main_mode[0] and not args.single_mode and args.launch_mode == 0:
+        for lm in (1, 2):
+            a2 = argparse.Namespace(**{**vars(args), "launch_mode": lm})
+            modes[lm] = measure(qn, w, a2, main_mode, stream, rank, world, local, pg, with_e2e=(lm == 2))
 
     G, n, K = w.gate_count, w.n, w.trajectories
     h2d = int(len(w.edges) * 8 + 2 * w.p * 8 + 40 + G * 20)
@@ -462,25 +469,37 @@ def gpu_arm(args):
                 "c_mean": other["mean"], "gpu_launches": other["launches"], "clocks": other["clocks"],
                 "sweep_bytes_per_step": other["sweep_bytes_per_step"],
                 "roofline": roof(other, "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")}
+        if modes:
+            line["launch_modes"] = {
+                {1: "device_driven", 2: "cuda_graph"}[lm]: {
+                    "value": r["value"], "unit": UNIT, "ms_per_step": r["ms"] / args.steps, "c_mean": r["mean"],
+                    "clocks": r["clocks"], **({"e2e": r["e2e_value"]} if "e2e_value" in r else {}),
+                    "launches": ("persistent sweeps over the slots the device counts; the host reads nothing "
+                                 "until the step is over" if lm == 1 else
+                                 "the same launches captured once in a CUDA graph, replayed every step")}
+                for lm, r in modes.items()}
         if world == 1 and not args.no_cpu_baseline and w.n <= 20:
             line["cpu_baseline"] = cpu_baseline(w)
         if world == 1 and args.workload == "damping20" and not args.no_legs:
             line["precision26"] = precision_leg(qn, args, stream, local, roof_of=roof)
             line["gradient16"] = gradient_leg(qn, args, stream, local)
             line["serving"] = serving_levels(args.requests, args.inflight, local)
+            line["serving_host_launches"] = serving_levels(args.requests, args.inflight, local, policy="host",
+                                                           levels=(0.8,))
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
 
 
-def serving_levels(requests: int, inflight: int, clock_index: int = 0):
-    """Serving workload: closed-loop capacity, then Poisson arrivals at 0.5x and 0.8x of
-    it; per level the request count, span, throughput and p50/p99 latency."""
+def serving_levels(requests: int, inflight: int, clock_index: int = 0, policy: str = "auto",
+                   levels=(0.5, 0.8)):
+    """Serving workload: closed-loop capacity, then Poisson arrivals at the given fractions
+    of it; per level the request count, span, throughput and p50/p99 latency."""
     from paper_2210_15874_gb300 import serving
 
     reqs = serving.serving_mix(requests)
     warm = serving.serving_mix(4, seed=99)
-    srv = serving.Server(max_inflight=inflight)
+    srv = serving.Server(max_inflight=inflight, launch_policy=policy)
     for f in [srv.submit(r) for r in warm]:
         f.result()
 
@@ -500,17 +519,26 @@ def serving_levels(requests: int, inflight: int, clock_index: int = 0):
                 "trajectories_per_s": traj / span, "p50_latency_s": serving.percentile(lat, 50),
                 "p99_latency_s": serving.percentile(lat, 99), "mean_latency_s": float(np.mean(lat))}
 
+    out = {}
     with ClockSampler(clock_index) as clocks:
         cap = run(0)
-        half = run(0.5 * cap["requests_per_s"])
-        high = run(0.8 * cap["requests_per_s"])
+        out["capacity"] = cap
+        for f in levels:
+            out[f"load_{f}"] = run(f * cap["requests_per_s"])
     srv.close()
+    launches = {"auto": "device-driven launches (persistent sweeps reading the live-slot count on the device); "
+                        "a request that runs in several launch batches captures its first in a CUDA graph and "
+                        "replays it",
+                "host": "launches sized on the host from the live-slot count read after every decide",
+                "device": "device-driven launches", "graph": "device-driven launches captured in CUDA graphs"}
     cfg = {"workload": "serving: n ~ U{10..24}, p ~ U{1..6}, K ~ log-uniform[256, 8192], depolarizing "
                        "1e-3/1e-2 + damping 5e-3, seeded regular graphs",
            "requests": requests, "max_inflight": inflight,
            "admission": "HBM footprint (launch batch of statevectors + tables) within 60% of free memory",
-           "mode": "shared-prefix mode per request, one CUDA stream per in-flight request"}
-    return {"capacity": cap, "load_0.5": half, "load_0.8": high, "clocks": clocks.summary(), "config": cfg}
+           "mode": "shared-prefix mode per request, one CUDA stream per in-flight request",
+           "launch_policy": policy, "launches": launches[policy]}
+    out.update({"clocks": clocks.summary(), "config": cfg})
+    return out
 
 
 def serving_arm(args):
@@ -521,7 +549,7 @@ def serving_arm(args):
     build.build()
 
     torch.cuda.set_device(0)
-    sv = serving_levels(args.requests, args.inflight)
+    sv = serving_levels(args.requests, args.inflight, policy=args.serving_policy)
     line = {"metric": "noisy trajectories/s and p50/p99 request latency under Poisson load", "value":
             sv["load_0.8"]["trajectories_per_s"], "unit": "trajectories/s", "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic", "config": sv["config"],
@@ -591,6 +619,11 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="arithmetic of the fused layers of Pauli-only workloads: 0 FP32 (default), 1 TF32 or "
                          "2 BF16x3 tensor cores")
+    ap.add_argument("--serving-policy", default="auto", choices=["auto", "host", "device", "graph"],
+                    help="serving workload: launch policy of the requests")
+    ap.add_argument("--launch-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="shared-prefix launches sized on the host (0), on the device (1), or the run as a "
+                         "CUDA graph (2)")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the precision (n=26), gradient (n=16) and serving legs of the default line")
     ap.add_argument("--single-mode", action="store_true",

@@ -155,6 +155,30 @@ qn_status qn_batch_set_precision(qn_batch *h, int32_t mode);
  * one). */
 qn_status qn_batch_set_sharing(qn_batch *h, int32_t on);
 
+/* How the launches of a shared-prefix run are sized (an execution choice with no
+ * counterpart in the paper; results are the same in every mode up to the order of
+ * FP64 sums, and the Kraus strings, states and <C>_t bit-identical):
+ *   0  on the host: after every decide the host reads the live-slot count and sizes
+ *      the next sweep's grid from it (the default);
+ *   1  on the device: every sweep is a persistent launch whose blocks stride over the
+ *      slots the device counts, every decide kernel reads the live count on the
+ *      device, and the sigma pass takes its slot order and row blocks from device
+ *      steps; the host reads nothing until the run is over (one wait at its end
+ *      instead of one per group of gates);
+ *   2  as 1, with the run after the noisy H layer captured in a CUDA graph on the
+ *      handle's first run of a circuit and replayed by later runs whose circuit,
+ *      noise, launch batch and buffers are the same (any seed, offset or trajectory
+ *      count that keeps the launch batch); a run of another circuit captures again
+ *      and updates the instantiated graph in place when its launches have the same
+ *      shape.  Profiling (qn_batch_set_profiling) does not see replayed launches.
+ * Other runs ignore the setting.  QN_EINVAL for another mode. */
+qn_status qn_batch_set_launch_mode(qn_batch *h, int32_t mode);
+
+/* Graph use of a handle in launch mode 2: runs that captured (and instantiated or
+ * updated) a graph, runs that replayed one, and captures that updated the existing
+ * graph in place.  Any pointer may be NULL. */
+qn_status qn_graph_info(const qn_batch *h, int64_t *captures, int64_t *replays, int64_t *updates);
+
 /* Global id of the handle's first trajectory (default 0): the handle evolves
  * trajectories first_trajectory .. first_trajectory + trajectories - 1, so
  * disjoint ranges on several handles or GPUs are shards of one ensemble whose

@@ -67,6 +67,18 @@ struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
     int kind = 0;
     double bytes = 0.0;
+    // device-driven runs: bytes = per_state x the live count after `log_k` decides (known
+    // once the run is over); -1: bytes is final
+    int32_t log_k = -1;
+    double per_state = 0.0;
+};
+
+// What a device-driven shared-prefix run leaves for the host to finish once it is over.
+struct DevRun {
+    std::vector<std::pair<int32_t, double>> acct;  // per sweep: (decides before it, bytes per live state)
+    int64_t launches = 0;
+    int32_t decides = 0;
+    ReadTail read_tail{};  // first_new still to be read from the device
 };
 
 constexpr int kMaxQubits = 30;
@@ -218,6 +230,20 @@ struct qn_batch {
     float *gv_p1m = nullptr;    // [gv_cap][2 kMaxGroupEdges]
     GroupClass *gv_cls = nullptr;
     int64_t gv_cap = 0;
+    // device-driven launches (qn_batch_set_launch_mode): 0 = sized on the host from the
+    // live-slot count read after every decide; 1 = persistent launches that read it on
+    // the device; 2 = as 1, the run after its noisy H layer captured in a CUDA graph and
+    // replayed while the circuit, noise and launch batch stay the same
+    int32_t launch_mode = 0;
+    int32_t *sh_log = nullptr;  // [1 + decides] the live-slot count after each decide
+    int64_t sh_log_cap = 0;
+    int32_t *sh_queue = nullptr;  // [sweep launches] work counters of the persistent sweeps
+    int64_t sh_queue_cap = 0;
+    cudaStream_t cap_stream = nullptr;  // private stream that graphs are captured on
+    cudaGraphExec_t graph_exec = nullptr;
+    std::string graph_sig;              // the launches the graph holds (kernels' arguments)
+    int64_t graph_captures = 0, graph_replays = 0, graph_updates = 0;
+    DevRun graph_run;                   // what the host finishes after a replay of the graph
     double *spart = nullptr;   // sigma terms of k_probs row blocks 1 .. parts-1
     int64_t spart_cap = 0;     // doubles
     float2 *lambda = nullptr;  // adjoint vectors (qn_grad), allocated on first use
@@ -263,8 +289,15 @@ qn_status alloc_t(qn_batch *h, T **out, size_t count) {
     return st;
 }
 
+void drop_graph(qn_batch *h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+    h->graph_sig.clear();
+}
+
 void release_all(qn_batch *h) {
     if (!h->blocks.empty()) cudaStreamSynchronize(h->stream);
+    drop_graph(h);
     for (void *p : h->blocks) {
         if (h->free_fn) h->free_fn(p, h->alloc_ctx);
         else cudaFree(p);
@@ -280,6 +313,10 @@ void release_all(qn_batch *h) {
     h->sh_weights = nullptr;
     h->sh_marg = nullptr;
     h->sh_cap = 0;
+    h->sh_log = nullptr;
+    h->sh_log_cap = 0;
+    h->sh_queue = nullptr;
+    h->sh_queue_cap = 0;
     h->sh_valid = false;
     h->sh_readbuf = nullptr;
     h->sh_readidx = nullptr;
@@ -869,6 +906,369 @@ qn_status run_batch(qn_batch *h, int64_t t0, int b, bool ensemble) {
 
 // Shared-prefix run of trajectories t0 .. t0 + kc - 1 (kc <= cap_B): one slot
 // per distinct Kraus prefix, forked on the device as branches diverge.
+// The device view of group gi (the group after it: nz, or nullptr) for a prefix tree of kc
+// trajectories.
+GroupView group_view(qn_batch *h, int gi, const GateGroup *nz, const SlotView &sv, int kc) {
+    const GateGroup &z = h->groups[gi];
+    GroupView gv;
+    gv.grp = h->gr_dev + gi;
+    gv.next = nz && nz->kind == 0 ? h->gr_dev + gi + 1 : nullptr;
+    gv.vc = nz ? nz->c : 1.0f;
+    gv.vs = nz ? nz->sn : 0.0f;
+    gv.Hcur = h->gv_H + (size_t)(gi & 1) * h->gv_cap * kGroupBins;
+    gv.Hnext = h->gv_H + (size_t)((gi + 1) & 1) * h->gv_cap * kGroupBins;
+    gv.T = h->gv_T;
+    gv.st_prev = h->gv_stprev;
+    gv.ekey = h->gv_ekey;
+    gv.evt = h->gv_i32;
+    gv.rep = h->gv_i32 + h->gv_cap;
+    gv.lead = h->gv_i32 + 2 * h->gv_cap;
+    gv.lstart = h->gv_i32 + 3 * h->gv_cap;
+    gv.lcount = h->gv_i32 + 4 * h->gv_cap;
+    gv.parent = h->gv_i32 + 5 * h->gv_cap;
+    gv.pos_slot = h->gv_i32 + 6 * h->gv_cap;
+    gv.members = kc;
+    gv.Htrue = h->gv_htrue;
+    gv.p1m = h->gv_p1m;
+    gv.cls = h->gv_cls;
+    gv.ncls = sv.fork_count;  // reset by the fork-finish kernel
+    gv.src = nullptr;
+    gv.slot_base = 0;
+    // a group right after the H layer or after another group finds no pending op
+    // (decides leave none); one after a per-gate sweep may
+    gv.pend = !(z.g0 == h->n || (gi > 0 && h->groups[gi - 1].g0 + h->groups[gi - 1].m == z.g0));
+    return gv;
+}
+
+// The tile map of the sweep that applies group z (the group after it: nz): a mixer block's
+// own map, or for the layer's last phase group (wide_next) the map of the rotations of
+// qubits 0-3 that its sweep also applies.  keep: the circuit's last block, a full block off
+// qubit 0 whose states the sigma pass reads anyway -- its sweep forms only the norms.
+MixMap group_mix_map(const qn_batch *h, const GateGroup &z, const GateGroup *nz, bool wide_next) {
+    const int n = h->n;
+    const int G = (int)h->gates.size();
+    MixMap mm;
+    if (wide_next) {
+        mm = mix_map(n, 0, kMixQ, {4, 5, 6, 7});
+        mm.tanf = std::fabs(nz->c) >= std::fabs(nz->sn);
+        mm.full8 = h->split8;  // rotate qubits 4-7 as well
+    }
+    if (z.kind != 1) return mm;
+    std::vector<int> next;
+    if (nz && nz->kind == 1)
+        for (int k = 0; k < nz->s; ++k) next.push_back(nz->sp[k]);
+    const bool wide = z.s == kWideBlock;
+    if (wide && z.sp[0] == 0 && h->split8) {
+        // the factors of 0-7 (all rotated before), the rotations of 8-11 and the
+        // joint of 8-15 (12-15 rotated without being kept)
+        mm = mix_map(n, kWideBlock, kMixQ, {12, 13, 14, 15});
+        mm.wide = 2;
+        mm.wsh = 3;  // qubits 4-7: f bits 3-6
+    } else if (wide && z.sp[0] == kWideBlock) {
+        // the second half of 8-15: the rotations of 12-15, then the block's factors
+        mm = mix_map(n, kWideBlock + kMixQ, kMixQ, next);
+        mm.wide = 3;
+        mm.wsh = kWideBlock - 1;  // qubits 8-11: f bits 7-10
+    } else {
+        // a block over 0-7 whose qubits 0-3 the sweep before rotated, or kMixQ qubits
+        mm = wide ? mix_map(n, kMixQ, kMixQ, next) : mix_map(n, z.sp[0], z.s, next);
+        mm.wide = wide ? 1 : 0;
+    }
+    mm.tanf = std::fabs(z.c) >= std::fabs(z.sn);
+    mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
+    const bool next_phase = nz && nz->kind == 0;
+    // its states are read once more by the sigma pass anyway: form only the norms there and
+    // let that pass apply the block, so no state is written
+    if (mm.final_norm && mm.M == kMixQ && !mm.has0 && mm.nN == 0 && !next_phase) mm.keep = 1;
+    return mm;
+}
+
+// What the readout needs about the circuit's last mixer block z when its sweep kept the
+// states (first_new: the slots from there on were forked at the block).
+ReadTail keep_read_tail(const GateGroup &z, const GroupView &gv, int32_t first_new) {
+    ReadTail rt{};
+    rt.keep = 1;
+    rt.M = z.s;
+    for (int k = 0; k < kMixQ; ++k) rt.q[k] = k < z.s ? z.sp[k] : 0;
+    rt.c = z.c;
+    rt.s = z.sn;
+    rt.T = gv.T;
+    rt.parent = gv.parent;
+    rt.first_new = first_new;
+    return rt;
+}
+
+// The sigma pass's view of a shared-prefix run's accumulators (slot order and weights in
+// sh_order, sh_weights); trivial_pending: the last sweep left no pending op.
+AccumView shared_accum(qn_batch *h, bool trivial_pending) {
+    AccumView a;
+    a.num_edges = (int32_t)h->edges_host.size();
+    a.edges = h->dedges;
+    a.order = h->sh_order;
+    a.weights = h->sh_weights;
+    a.cpart = h->cpart;
+    a.acc_counter = h->acc_counter;
+    a.c_out = h->c_dbg;
+    a.probs = h->probs;
+    a.sums = h->sums;
+    a.trivial_pending = trivial_pending ? 1 : 0;
+    return a;
+}
+
+
+// The shared-prefix run after its noisy H layer with device-driven launches: every sweep
+// is a persistent launch over the slots the device counts, every decide kernel reads the
+// live-slot count on the device, the sigma pass takes its order and weights from a device
+// step, and nothing is read back until the run is over.  The same launches (arguments and
+// grids) come out whatever the draws, so a captured run replays for any seed and range of
+// trajectories of the same circuit.  `st` is the handle's stream, or the capture stream.
+qn_status enqueue_shared_dev(qn_batch *h, const BatchView &vh, const SlotView &svh, int kc, cudaStream_t st,
+                             bool profile, DevRun *out) {
+    const int n = h->n;
+    const int G = (int)h->gates.size();
+    const bool grouped = use_groups(h);
+    DevRun &r = *out;
+    BatchView v = vh;
+    v.t0 = 0;  // only k_prepare reads the global ids
+    v.b = kc;
+    SlotView sv = svh;
+    sv.dyn = 1;
+    sv.prev_active = h->sh_ctr + 3;
+    sv.live_log = h->sh_log;
+    // a sweep over the slots [*lo, *hi) with a work counter of its own
+    int64_t queues = 0;
+    auto over = [&](const int32_t *lo, const int32_t *hi) {
+        BatchView w = v;
+        w.dyn_lo = lo;
+        w.dyn_hi = hi;
+        w.dyn_queue = h->sh_queue + std::min<int64_t>(queues++, h->sh_queue_cap - 1);
+        return w;
+    };
+    auto v_all = [&]() { return over(nullptr, sv.active); };         // the live slots
+    auto v_new = [&]() { return over(sv.prev_active, sv.active); };  // the slots forked by the last decide
+    auto v_old = [&]() { return over(nullptr, sv.prev_active); };    // the slots live before it
+    const double amp = (double)((size_t)1 << n);
+    QN_CUDA(cudaMemsetAsync(h->sh_queue, 0, (size_t)h->sh_queue_cap * sizeof(int32_t), st));
+    int32_t decides = 0;
+    EventPair ep;
+    auto begin = [&](int kind, double per_state) -> qn_status {
+        ep.kind = -1;
+        if (!profile) return QN_OK;
+        QN_TRY(prof_begin(h, &ep, kind, 0.0));
+        ep.log_k = decides;
+        ep.per_state = per_state;
+        return QN_OK;
+    };
+    auto end = [&]() -> qn_status { return profile ? prof_end(h, &ep) : QN_OK; };
+    QN_CUDA(cudaMemsetAsync(h->sh_log, 0, sizeof(int32_t), st));
+    QN_TRY(begin(1, 8.0 * amp));
+    QN_CUDA(launch_init(over(nullptr, sv.slot_count), st));
+    QN_TRY(end());
+    r.launches += 1;
+    bool final_norms = false, keep = false;
+    MixMap keep_mm;
+    MixTail keep_tail{};
+    for (int g = n; g < G; ++g) {
+        const int gi = grouped ? h->group_at[g] : -1;
+        if (gi >= 0) {
+            const GateGroup &z = h->groups[gi];
+            const int ng = (int)h->groups.size();
+            const GateGroup *nz = gi + 1 < ng && h->groups[gi + 1].g0 == z.g0 + z.m ? &h->groups[gi + 1] : nullptr;
+            const bool first = z.kind == 0 && (gi == 0 || h->groups[gi - 1].g0 + h->groups[gi - 1].m != z.g0);
+            const bool wide_next = z.kind == 0 && nz && nz->kind == 1 && nz->s == kWideBlock && nz->sp[0] == 0;
+            GroupView gv = group_view(h, gi, nz, sv, kc);
+            if (first) {
+                QN_TRY(begin(3, 8.0 * amp));
+                QN_CUDA(launch_group_hist(v_all(), sv, gv, kc, st));
+                QN_TRY(end());
+                r.acct.emplace_back(decides, 8.0 * amp);
+                r.launches += 1;
+            }
+            QN_CUDA(launch_group_decide(v, sv, gv, z.s, kc, h->nz.gamma, st));
+            ++decides;
+            MixMap mm = group_mix_map(h, z, nz, wide_next);
+            if (z.kind == 1) {
+                final_norms = final_norms || mm.final_norm;
+                if (mm.keep) {
+                    keep = true;
+                    keep_mm = mm;
+                    keep_tail.grp = gv.grp;
+                    keep_tail.T = gv.T;
+                    keep_tail.parent = gv.parent;
+                    keep_tail.first_new_dev = sv.prev_active;
+                    r.read_tail = keep_read_tail(z, gv, 0);
+                }
+            }
+            const double per_state = (mm.keep && z.kind == 1 ? 8.0 : 16.0) * amp;
+            QN_TRY(begin(z.kind == 0 ? 3 : 4, per_state));
+            for (int part = 0; part < 2; ++part) {
+                const BatchView vp = part == 0 ? v_new() : v_old();
+                gv.src = part == 0 ? gv.parent : nullptr;
+                gv.slot_base = 0;
+                QN_CUDA(z.kind == 1 ? launch_mix_sweep(vp, gv, mm, kc, st)
+                        : wide_next ? launch_group_mix(vp, gv, mm, kc, st)
+                                    : launch_group_apply(vp, sv, gv, kc, st));
+            }
+            QN_TRY(end());
+            r.acct.emplace_back(decides, per_state);
+            r.launches += 4;  // decide, finish, the two sweeps
+            g += z.m - 1;
+            continue;
+        }
+        QN_TRY(begin(0, 16.0 * amp));
+        QN_CUDA(launch_slot_sweep(v_all(), sv, kc, g, h->dgates_host[g], h->damping_on, st));
+        QN_TRY(end());
+        QN_CUDA(launch_slot_fork(v, sv, kc, g, h->dgates_host[g], h->nz, h->damping_on, st));
+        r.acct.emplace_back(decides, 16.0 * amp);
+        ++decides;
+        r.launches += 4;
+    }
+    // the sigma pass over the final slots, in the order of their first members
+    QN_CUDA(launch_slot_order(sv, sv.tmp, h->sh_order, h->sh_weights, kc, h->status, st));
+    AccumView a = shared_accum(h, final_norms);
+    const int kind = keep ? 2 : (final_norms ? 1 : 0);
+    a.rows = probs_row_plan(n, kind);
+    a.rows.used = 1;
+    a.parts = a.rows.pmax;
+    a.spart = a.parts > 1 ? h->spart : nullptr;
+    QN_TRY(begin(2, (final_norms ? 8.0 : 16.0) * amp));
+    if (!final_norms) QN_CUDA(launch_observe(v_all(), a, st));
+    const BatchView vo = over(nullptr, sv.active);  // the sigma pass reads only the state count
+    if (keep) QN_CUDA(launch_probs_mix(vo, a, keep_mm, keep_tail, st));
+    else QN_CUDA(launch_probs(vo, a, st));
+    if (queues > h->sh_queue_cap) return fail(QN_ESTATE, "device-driven run needs %lld work counters (%lld)",
+                                              (long long)queues, (long long)h->sh_queue_cap);
+    QN_TRY(end());
+    r.launches += 3 + (final_norms ? 0 : 1) + (a.parts > 1 ? 1 : 0);  // order (2), observe, probs, combine
+    r.decides = decides;
+    return QN_OK;
+}
+
+// Bytes that fix every launch of a device-driven run (kernel arguments and grids): the
+// handle's buffers, the circuit, the noise and the launch batch.  Equal signatures give
+// the same launches, so a captured graph of one run serves the other.
+std::string dev_signature(const qn_batch *h, const BatchView &v, const SlotView &sv, int kc) {
+    std::string sig;
+    auto put = [&](const void *p, size_t nb) { sig.append(reinterpret_cast<const char *>(p), nb); };
+    // field by field: the structs' padding bytes are not initialised
+    const void *vp[] = {v.psi, v.branch, v.dwords, v.frame_x, v.yphase, v.hfac, v.st, v.partials, v.inv_norm,
+                        v.counters, v.status, sv.members, sv.tmp, sv.cls, sv.range, sv.slot_count, sv.active,
+                        sv.forks, sv.fork_count, sv.marg};
+    put(vp, sizeof vp);
+    const int32_t vi[] = {v.n, v.b, v.G, v.tiles, v.stiles, sv.max_slots, kc};
+    put(vi, sizeof vi);
+    put(&h->nz.gamma, sizeof h->nz.gamma);
+    put(h->nz.thr1, sizeof h->nz.thr1);
+    put(h->nz.thr2, sizeof h->nz.thr2);
+    put(&h->damping_on, sizeof h->damping_on);
+    put(&h->fusion, sizeof h->fusion);
+    const int32_t split = h->split8 ? 1 : 0;
+    put(&split, sizeof split);
+    for (const DevGate &g : h->dgates_host) {
+        const int32_t gi[] = {g.kind, g.q0, g.q1};
+        const float gf[] = {g.c, g.s};
+        put(gi, sizeof gi);
+        put(gf, sizeof gf);
+    }
+    static_assert(sizeof(GateGroup) == 4 * (4 + kMaxGroupQubits + 2 * kMaxGroupEdges + 2) + 2 * 4 * 256,
+                  "GateGroup has no padding");
+    if (!h->groups.empty()) put(h->groups.data(), h->groups.size() * sizeof(GateGroup));
+    if (!h->group_at.empty()) put(h->group_at.data(), h->group_at.size() * sizeof(int32_t));
+    const int32_t ne = (int32_t)h->edges_host.size();
+    put(&ne, sizeof ne);
+    const void *ptrs[] = {h->gr_dev, h->gv_H, h->gv_T, h->gv_stprev, h->gv_ekey, h->gv_i32, h->gv_htrue,
+                          h->gv_p1m, h->gv_cls, h->sh_log, h->sh_order, h->sh_weights, h->cpart, h->acc_counter,
+                          h->c_dbg, h->probs, h->sums, h->dedges, h->spart};
+    put(ptrs, sizeof ptrs);
+    put(&h->gv_cap, sizeof h->gv_cap);
+    return sig;
+}
+
+// A shared-prefix run with device-driven launches (launch modes 1 and 2), after its noisy
+// H layer was grouped into ns slots: enqueue (mode 1), or replay / capture and replay the
+// CUDA graph of the run (mode 2); then, once it is over, read what the host keeps of it.
+qn_status run_shared_dev(qn_batch *h, const BatchView &v, const SlotView &sv, int64_t t0, int kc, int ns) {
+    const int n = h->n;
+    DevRun run;
+    if (h->launch_mode == 2) {
+        std::string sig = dev_signature(h, v, sv, kc);
+        if (!h->graph_exec || sig != h->graph_sig) {
+            if (!h->cap_stream) QN_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            QN_CUDA(prewarm_dev_launches());
+            QN_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            const qn_status st = enqueue_shared_dev(h, v, sv, kc, h->cap_stream, false, &run);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+            if (st != QN_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ec != cudaSuccess) return fail(QN_ECUDA, "capturing the run: %s", cudaGetErrorString(ec));
+            cudaError_t e = cudaErrorUnknown;
+            if (h->graph_exec) {
+                // same launches in the same order (another circuit of the same shape): update in place
+                cudaGraphExecUpdateResultInfo info{};
+                e = cudaGraphExecUpdate(h->graph_exec, graph, &info);
+                if (e == cudaSuccess) h->graph_updates += 1;
+                else {
+                    (void)cudaGetLastError();
+                    cudaGraphExecDestroy(h->graph_exec);
+                    h->graph_exec = nullptr;
+                }
+            }
+            if (!h->graph_exec) e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                h->graph_exec = nullptr;
+                h->graph_sig.clear();
+                return fail(QN_ECUDA, "instantiating the run's graph: %s", cudaGetErrorString(e));
+            }
+            h->graph_sig = std::move(sig);
+            h->graph_run = run;
+            h->graph_captures += 1;
+        } else {
+            run = h->graph_run;
+            h->graph_replays += 1;
+        }
+        QN_CUDA(cudaGraphLaunch(h->graph_exec, h->stream));
+    } else {
+        QN_TRY(enqueue_shared_dev(h, v, sv, kc, h->stream, true, &run));
+    }
+    h->launches += run.launches;
+    // once the run is over: its status, the live-slot log, and the final slots
+    QN_TRY(check_status(h));  // synchronises
+    int32_t ctr[4] = {0, 0, 0, 0};
+    QN_CUDA(cudaMemcpy(ctr, h->sh_ctr, sizeof ctr, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> log((size_t)run.decides + 1, 0);
+    QN_CUDA(cudaMemcpy(log.data(), h->sh_log, log.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const int nslots = ctr[1];
+    if (ctr[0] > kc || nslots > kc || nslots < 1)
+        return fail(QN_ESTATE, "shared-prefix run created %d slots for %d trajectories", ctr[0], kc);
+    auto live_after = [&](int k) { return k == 0 ? ns : log[std::min<size_t>((size_t)k, log.size() - 1)]; };
+    for (const auto &a : run.acct) h->sweep_bytes += (double)live_after(a.first) * a.second;
+    for (EventPair &ep : h->events)
+        if (ep.log_k >= 0) {
+            ep.bytes = (double)live_after(ep.log_k) * ep.per_state;
+            ep.log_k = -1;
+        }
+    std::vector<int2> fr((size_t)nslots);
+    std::vector<int32_t> fm((size_t)kc), order((size_t)nslots);
+    QN_CUDA(cudaMemcpy(fr.data(), h->sh_range, fr.size() * sizeof(int2), cudaMemcpyDeviceToHost));
+    QN_CUDA(cudaMemcpy(fm.data(), h->sh_members, fm.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    QN_CUDA(cudaMemcpy(order.data(), h->sh_order, order.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    h->sh_slots += nslots;
+    h->sh_valid = true;
+    h->sh_last_t0 = t0;
+    h->sh_last_kc = kc;
+    h->sh_range_host = std::move(fr);
+    h->sh_members_host = std::move(fm);
+    h->sh_order_host = std::move(order);
+    h->sh_tail = run.read_tail;
+    h->sh_tail.first_new = ctr[3];  // the live slots before the last decide
+    (void)n;
+    return QN_OK;
+}
+
 qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     const int n = h->n;
     const int G = (int)h->gates.size();
@@ -899,6 +1299,26 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     if (grouped && h->gr_cap < (int64_t)h->groups.size()) {
         QN_TRY(alloc_t(h, &h->gr_dev, h->groups.size()));
         h->gr_cap = (int64_t)h->groups.size();
+    }
+    if (h->launch_mode != 0) {
+        // device-driven: the live-slot log (one entry per decide), and sigma scratch for the
+        // most row blocks the device may choose
+        const int64_t need_log = (int64_t)G - n + 2;
+        if (h->sh_log_cap < need_log) {
+            QN_TRY(alloc_t(h, &h->sh_log, (size_t)need_log));
+            h->sh_log_cap = need_log;
+        }
+        const int64_t need_queue = 3 * ((int64_t)G - n) + 8;  // at most three sweeps per gate, init, observe
+        if (h->sh_queue_cap < need_queue) {
+            QN_TRY(alloc_t(h, &h->sh_queue, (size_t)need_queue));
+            h->sh_queue_cap = need_queue;
+        }
+        const int pmax = probs_row_plan(n, 0).pmax;
+        const int64_t need = (int64_t)(pmax - 1) << n;
+        if (pmax > 1 && h->spart_cap < need) {
+            QN_TRY(alloc_t(h, &h->spart, (size_t)need));
+            h->spart_cap = need;
+        }
     }
     if (grouped) {
         QN_CUDA(cudaMemcpyAsync(h->gr_dev, h->groups.data(), h->groups.size() * sizeof(GateGroup),
@@ -990,6 +1410,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
     sv.fork_count = h->sh_ctr + 2;
     sv.marg = h->sh_marg;
     sv.max_slots = kc;
+    if (h->launch_mode != 0) return run_shared_dev(h, v, sv, t0, kc, ns);
 
     BatchView vs = v;
     vs.b = ns;
@@ -1029,33 +1450,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             // a phase group before the layer's first mixer block (qubits 0-7) also rotates qubits
             // 0-3 and forms that block's joint (k_group_mix)
             const bool wide_next = z.kind == 0 && nz && nz->kind == 1 && nz->s == kWideBlock && nz->sp[0] == 0;
-            GroupView gv;
-            gv.grp = h->gr_dev + gi;
-            gv.next = nz && nz->kind == 0 ? h->gr_dev + gi + 1 : nullptr;
-            gv.vc = nz ? nz->c : 1.0f;
-            gv.vs = nz ? nz->sn : 0.0f;
-            gv.Hcur = h->gv_H + (size_t)(gi & 1) * h->gv_cap * kGroupBins;
-            gv.Hnext = h->gv_H + (size_t)((gi + 1) & 1) * h->gv_cap * kGroupBins;
-            gv.T = h->gv_T;
-            gv.st_prev = h->gv_stprev;
-            gv.ekey = h->gv_ekey;
-            gv.evt = h->gv_i32;
-            gv.rep = h->gv_i32 + h->gv_cap;
-            gv.lead = h->gv_i32 + 2 * h->gv_cap;
-            gv.lstart = h->gv_i32 + 3 * h->gv_cap;
-            gv.lcount = h->gv_i32 + 4 * h->gv_cap;
-            gv.parent = h->gv_i32 + 5 * h->gv_cap;
-            gv.pos_slot = h->gv_i32 + 6 * h->gv_cap;
-            gv.members = kc;
-            gv.Htrue = h->gv_htrue;
-            gv.p1m = h->gv_p1m;
-            gv.cls = h->gv_cls;
-            gv.ncls = sv.fork_count;  // reset by the fork-finish kernel
-            gv.src = nullptr;
-            gv.slot_base = 0;
-            // a group right after the H layer or after another group finds no pending op
-            // (decides leave none); one after a per-gate sweep may
-            gv.pend = !(z.g0 == n || (gi > 0 && h->groups[gi - 1].g0 + h->groups[gi - 1].m == z.g0));
+            GroupView gv = group_view(h, gi, nz, sv, kc);
             cudaError_t e = cudaSuccess;
             if (first) {
                 QN_TRY(prof_begin(h, &ep, 3, (double)active * 8.0 * amp_count));
@@ -1071,54 +1466,17 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
             const int old_active = active;
             active = *active_host;
-            MixMap mm;
-            if (wide_next) {
-                mm = mix_map(n, 0, kMixQ, {4, 5, 6, 7});
-                mm.tanf = std::fabs(nz->c) >= std::fabs(nz->sn);
-                mm.full8 = h->split8;  // rotate qubits 4-7 as well
-            }
+            MixMap mm = group_mix_map(h, z, nz, wide_next);
             if (z.kind == 1) {
-                std::vector<int> next;
-                if (nz && nz->kind == 1)
-                    for (int k = 0; k < nz->s; ++k) next.push_back(nz->sp[k]);
-                const bool wide = z.s == kWideBlock;
-                if (wide && z.sp[0] == 0 && h->split8) {
-                    // the factors of 0-7 (all rotated before), the rotations of 8-11 and the
-                    // joint of 8-15 (12-15 rotated without being kept)
-                    mm = mix_map(n, kWideBlock, kMixQ, {12, 13, 14, 15});
-                    mm.wide = 2;
-                    mm.wsh = 3;  // qubits 4-7: f bits 3-6
-                } else if (wide && z.sp[0] == kWideBlock) {
-                    // the second half of 8-15: the rotations of 12-15, then the block's factors
-                    mm = mix_map(n, kWideBlock + kMixQ, kMixQ, next);
-                    mm.wide = 3;
-                    mm.wsh = kWideBlock - 1;  // qubits 8-11: f bits 7-10
-                } else {
-                    // a block over 0-7 whose qubits 0-3 the sweep before rotated, or kMixQ qubits
-                    mm = wide ? mix_map(n, kMixQ, kMixQ, next) : mix_map(n, z.sp[0], z.s, next);
-                    mm.wide = wide ? 1 : 0;
-                }
-                mm.tanf = std::fabs(z.c) >= std::fabs(z.sn);
-                mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
                 final_norms = final_norms || mm.final_norm;
-                if (mm.final_norm && mm.M == kMixQ && !mm.has0 && mm.nN == 0 && !gv.next) {
-                    // its states are read once more by the sigma pass anyway: form only the
-                    // norms here and let that pass apply the block, so no state is written
-                    mm.keep = 1;
+                if (mm.keep) {
                     keep = true;
                     keep_mm = mm;
                     keep_tail.grp = gv.grp;
                     keep_tail.T = gv.T;
                     keep_tail.parent = gv.parent;
                     keep_tail.first_new = old_active;
-                    read_tail.keep = 1;
-                    read_tail.M = z.s;
-                    for (int k = 0; k < kMixQ; ++k) read_tail.q[k] = k < z.s ? z.sp[k] : 0;
-                    read_tail.c = z.c;
-                    read_tail.s = z.sn;
-                    read_tail.T = gv.T;
-                    read_tail.parent = gv.parent;
-                    read_tail.first_new = old_active;
+                    read_tail = keep_read_tail(z, gv, old_active);
                 }
             }
             // the slots forked here first, reading their parents' states; then
@@ -1180,17 +1538,7 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                             h->stream));
     BatchView vo = v;
     vo.b = nslots;
-    AccumView a;
-    a.num_edges = (int32_t)h->edges_host.size();
-    a.edges = h->dedges;
-    a.order = h->sh_order;
-    a.weights = h->sh_weights;
-    a.cpart = h->cpart;
-    a.acc_counter = h->acc_counter;
-    a.c_out = h->c_dbg;
-    a.probs = h->probs;
-    a.sums = h->sums;
-    a.trivial_pending = final_norms;  // the last sweep left no pending op
+    AccumView a = shared_accum(h, final_norms);  // the last sweep left no pending op
     QN_TRY(probs_rows(h, nslots, &a, keep ? 2 : (final_norms ? 1 : 0)));
     QN_TRY(prof_begin(h, &ep, 2, (double)nslots * (final_norms ? 8.0 : 16.0) * (double)((size_t)1 << n)));
     if (!final_norms) QN_CUDA(launch_observe(vo, a, h->stream));
@@ -1318,6 +1666,22 @@ qn_status qn_batch_set_sharing(qn_batch *h, int32_t on) {
     if (on != 0 && on != 1) return fail(QN_EINVAL, "sharing must be 0 or 1");
     h->sharing = on;
     h->has_run = false;
+    return ok();
+}
+
+qn_status qn_batch_set_launch_mode(qn_batch *h, int32_t mode) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (mode < 0 || mode > 2) return fail(QN_EINVAL, "launch mode must be 0, 1 or 2");
+    h->launch_mode = mode;
+    h->has_run = false;
+    return ok();
+}
+
+qn_status qn_graph_info(const qn_batch *h, int64_t *captures, int64_t *replays, int64_t *updates) {
+    if (!h) return fail(QN_EINVAL, "handle is NULL");
+    if (captures) *captures = h->graph_captures;
+    if (replays) *replays = h->graph_replays;
+    if (updates) *updates = h->graph_updates;
     return ok();
 }
 
@@ -1711,6 +2075,7 @@ const char *qn_last_error(void) { return g_last_error.c_str(); }
 void qn_batch_destroy(qn_batch *h) {
     if (!h) return;
     release_all(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     pinned_word_give(h->pinned_word);
     for (EventPair &ep : h->events) {
         cudaEventDestroy(ep.a);

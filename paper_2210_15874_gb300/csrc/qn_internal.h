@@ -54,6 +54,15 @@ struct BatchView {
     double *inv_norm;       // [b] 1 / ||psi||^2 of the final state (set by k_observe)
     unsigned int *counters; // [b]
     int *status;            // device error word
+    // Device-driven launches (shared-prefix mode): a sweep covers the slots
+    // [*dyn_lo, *dyn_hi) (dyn_lo == nullptr: from 0), counts read on the device, as
+    // dyn_tiles tiles per slot, handed out to a persistent grid in order from the
+    // launch's counter *dyn_queue (zero at launch).  dyn_hi == nullptr: the grid was
+    // sized on the host, one block per tile and slot.
+    const int32_t *dyn_lo = nullptr;
+    const int32_t *dyn_hi = nullptr;
+    int32_t *dyn_queue = nullptr;
+    int32_t dyn_tiles = 0;
 };
 
 // Shared-prefix mode: slots (distinct states) and their member trajectories.
@@ -68,6 +77,12 @@ struct SlotView {
     int32_t *fork_count;
     double *marg;        // [max_slots][4] damping marginal of each slot at the current gate
     int32_t max_slots;
+    int32_t *prev_active = nullptr;  // live slots before the last decide (the slots from here
+                                     // on were forked by it); set by the fork-finish kernel
+    int32_t *live_log = nullptr;     // [1 + decides] decides so far, then the live-slot count
+                                     // after each (device-driven runs: the host reads it after
+                                     // the run for its byte accounting)
+    int32_t dyn = 0;                 // device-driven: decide kernels read *active on the device
 };
 
 // Consecutive phase gates of one layer whose qubits S number at most 10 (shared-
@@ -138,6 +153,7 @@ struct MixTail {
     const float2 *T;        // [slots][kGroupBins] the block's drawn factors by stored bits
     const int32_t *parent;  // [slots] the parent of each slot forked at the block
     int32_t first_new;      // slots from this one on were forked at the block
+    const int32_t *first_new_dev = nullptr;  // device-driven runs: first_new read on the device
 };
 constexpr int kMixSubs = 4;  // tiles per thread block (streamed through two shared buffers)
 
@@ -236,6 +252,34 @@ struct NoiseDev {
     uint64_t thr2[16];         // cumulative thresholds, 2q
 };
 
+// The rule that splits a sigma pass over b states into row blocks (probs_parts):
+// xb blocks per state, res resident blocks, at most pmax rows (kMaxProbParts and
+// the sigma copies that fit); used = 0: the host chose the rows.
+struct RowPlan {
+    int64_t xb;
+    int32_t res;
+    int32_t pmax;
+    int32_t used;
+};
+__host__ __device__ inline int row_parts(const RowPlan &r, int b) {
+    // Every block of a row streams all of the row's states, so the launch takes about
+    // ceil(xb P / res) rounds of b / P states each: take the P with the fewest
+    // state-rounds (the smaller on a tie).  A row keeps at least one chunk of 32 states.
+    const int64_t cap = ((int64_t)b + 31) / 32;
+    const int pmax = (int)(cap < (int64_t)r.pmax ? (cap > 1 ? cap : 1) : r.pmax);
+    int best = 1;
+    double best_cost = 0.0;
+    for (int p = 1; p <= pmax; ++p) {
+        const double rounds = (double)((r.xb * p + r.res - 1) / r.res);
+        const double cost = rounds * (double)(((int64_t)b + p - 1) / p);
+        if (p == 1 || cost < best_cost * 0.995) {
+            best = p;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 struct AccumView {
     int32_t num_edges;
     const int2 *edges;         // device
@@ -249,6 +293,10 @@ struct AccumView {
     int32_t trivial_pending = 0;  // every state's pending op is the identity
     int32_t parts = 1;            // row blocks that split the states (k_probs grid y)
     double *spart = nullptr;      // [parts - 1][2^n] sigma terms of rows 1 .. parts-1
+    // Device-driven runs: the state count b is *v.dyn_hi, read on the device, and the row
+    // blocks are chosen there from it by the rule the host applies (row_plan); the grid's
+    // y extent is the largest count, and rows beyond the chosen one leave at once.
+    RowPlan rows{};
 };
 
 constexpr int kThreads = 256;        // threads per sweep block
@@ -275,6 +323,13 @@ cudaError_t launch_init(const BatchView &v, cudaStream_t s);
 cudaError_t launch_sweep(const BatchView &v, int g, const DevGate &gate, const NoiseDev &nz, int damping_on,
                          cudaStream_t s);
 cudaError_t launch_observe(const BatchView &v, const AccumView &a, cudaStream_t s);
+// Device-driven shared-prefix runs: order[0 .. slots) = the live slots by their first
+// members (trajectory order), weights[slot] = its member count; pos is [K] scratch.
+// Run once before a stream capture: the launch wrappers' one-time set-up (occupancy
+// figures, shared-memory attributes), so that a captured run makes no such calls.
+cudaError_t prewarm_dev_launches();
+cudaError_t launch_slot_order(const SlotView &sv, int32_t *pos, int32_t *order, double *weights, int K, int *status,
+                              cudaStream_t s);
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s);
 // The sigma pass that applies the circuit's last mixer block on the fly (states
 // kept by a MixMap::keep sweep); same outputs as launch_probs.
@@ -283,6 +338,7 @@ cudaError_t launch_probs_mix(const BatchView &v, const AccumView &a, const MixMa
 // Row blocks worth giving the sigma pass for b states (1 .. kMaxProbParts): k_probs
 // with a pending op (kind 0) or without (1), or the pass of launch_probs_mix (2).
 int probs_parts(int n, int b, int kind);
+RowPlan probs_row_plan(int n, int kind);  // the inputs of that rule (row_parts) for n qubits
 constexpr int kMaxProbParts = 16;
 cudaError_t launch_readout(const BatchView &v, float2 *out, cudaStream_t s);
 // What the readout of a shared-prefix run needs about the circuit's last mixer

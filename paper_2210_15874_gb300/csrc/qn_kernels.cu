@@ -24,6 +24,8 @@
 #include "qn_internal.h"
 
 #include <array>
+#include <mutex>
+#include <unordered_map>
 
 namespace qn {
 namespace {
@@ -54,6 +56,63 @@ __device__ __forceinline__ int pick_code(uint32_t w, const uint64_t *thr, int co
 
 __device__ __forceinline__ uint32_t xpart_1q(int code) { return (uint32_t)((code ^ (code >> 1)) & 1); }
 __device__ __forceinline__ uint32_t zpart_1q(int code) { return (uint32_t)((code >> 1) & 1); }
+
+// Work items of a sweep launch: one tile of one slot each.  A launch sized on the host
+// (v.dyn_hi == nullptr) gives each block one item, tile blockIdx.x of slot base +
+// blockIdx.y.  A device-driven launch has a persistent grid: its items k = 0, 1, ...
+// cover the v.dyn_tiles tiles of each slot in [*v.dyn_lo, *v.dyn_hi) (read on the
+// device, after grid_dependency_wait: the kernel before wrote them), tile k % dyn_tiles
+// of slot lo + k / dyn_tiles, and are handed out in order from the launch's counter
+// v.dyn_queue (zero at launch).  So the blocks at work at any moment hold consecutive
+// items -- the order in which the hardware starts the blocks of a host-sized grid,
+// which keeps the tiles of a slot in flight together -- and the host never reads the
+// live-slot count: a whole run can be captured in a CUDA graph.  Thread 0 claims each
+// item one item ahead (nxt, its register), so the counter's round trip overlaps the
+// work on the item before; an item claimed beyond the end is dropped.  q_* are the
+// block's shared words; `it` counts the block's items.  Called by every thread.
+template <bool DYN>
+__device__ __forceinline__ bool sweep_item(const BatchView &v, int base, int it, int &q_item, int &q_lo, int &q_n,
+                                           int &nxt, int &tile, int &slot) {
+    if (!DYN) {
+        tile = (int)blockIdx.x;
+        slot = base + (int)blockIdx.y;
+        return it == 0;
+    }
+    __syncthreads();  // the previous item's shared memory is free
+    if (threadIdx.x == 0) {
+        if (it == 0) {
+            q_lo = v.dyn_lo ? *v.dyn_lo : 0;
+            q_n = v.dyn_tiles * max(*v.dyn_hi - q_lo, 0);
+            nxt = atomicAdd(v.dyn_queue, 1);
+        }
+        q_item = nxt;
+        if (nxt < q_n) nxt = atomicAdd(v.dyn_queue, 1);
+    }
+    __syncthreads();
+    const int k = q_item;
+    if (k >= q_n) return false;
+    tile = k % v.dyn_tiles;
+    slot = q_lo + k / v.dyn_tiles;
+    return true;
+}
+// FP32 arithmetic of the sweeps in one fixed rounding sequence (no contraction left to
+// the compiler), so that every variant of a kernel -- host-sized or device-driven, whose
+// code the compiler schedules differently -- gives bit-identical values.
+__device__ __forceinline__ float norm2_rn(float re, float im) { return __fmaf_rn(re, re, __fmul_rn(im, im)); }
+__device__ __forceinline__ void cmul_rn(float ar, float ai, float br, float bi, float &re, float &im) {
+    re = __fmaf_rn(ar, br, -__fmul_rn(ai, bi));
+    im = __fmaf_rn(ar, bi, __fmul_rn(ai, br));
+}
+
+// The same, DYN decided at run time (the small sweeps: init, observables).
+__device__ __forceinline__ bool sweep_item_rt(const BatchView &v, int base, int it, int &q_item, int &q_lo, int &q_n,
+                                              int &nxt, int &tile, int &slot) {
+    return v.dyn_hi ? sweep_item<true>(v, base, it, q_item, q_lo, q_n, nxt, tile, slot)
+                    : sweep_item<false>(v, base, it, q_item, q_lo, q_n, nxt, tile, slot);
+}
+// Tiles per slot of a sweep launch (the host-sized grid's x extent).
+template <bool DYN>
+__device__ __forceinline__ int sweep_tiles(const BatchView &v) { return DYN ? v.dyn_tiles : (int)gridDim.x; }
 
 // ---------------------------------------------------------------------------
 // Per-trajectory preparation: Philox draws for every gate, Pauli codes, X-frame
@@ -134,8 +193,10 @@ __global__ void k_prepare(BatchView v, const DevGate *__restrict__ gates, uint64
 // per-block scalar.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_init(BatchView v) {
-    const int t = blockIdx.y;
-    const int tile = blockIdx.x;
+    __shared__ int q_item, q_lo, q_n;
+    int nxt = 0;  // thread 0: the next item claimed
+    int tile, t;
+    for (int it = 0; sweep_item_rt(v, 0, it, q_item, q_lo, q_n, nxt, tile, t); ++it) {
     __shared__ float lo[64], mid[32];
     __shared__ float hi_s;
     const float *hf = v.hfac + (size_t)t * v.n * 2;
@@ -175,6 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_init(BatchView v) {
             a1 = m * lo[(y & 63) | 1];
         }
         p4[f] = make_float4(a0, 0.0f, a1, 0.0f);
+    }
     }
 }
 
@@ -306,6 +368,7 @@ __device__ void decide_damping(const BatchView &v, int t, int g, const DevGate &
 // kernel drains; it waits here before touching anything that kernel wrote.
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 
 // Block reduction of the damping marginal of one unit -> partials[t][tile];
 // returns true in the last block to finish trajectory (or slot) t, with the
@@ -751,18 +814,22 @@ __device__ __forceinline__ void decide_slot(const BatchView &v, const SlotView &
 // Slot sweeps: grid (sweep tiles, slots alive before this gate), one unit per
 // block, the same body as the batch sweeps; the last block of a slot stores the
 // slot's marginal for k_slot_decide.
-template <bool DAMP, int KIND>
+template <bool DAMP, int KIND, bool DYN = false>
 __global__ void __launch_bounds__(kThreads, 4) k_slot_sweep(BatchView v, SlotView sv, int g, DevGate gt) {
     grid_dependency_wait();
-    const int slot = blockIdx.y, tile = blockIdx.x;
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-    if (KIND == kGateZZ) zz_unit<DAMP, true>(v, slot, tile, g, gt, a0, a1, a2, a3);
-    else rx_unit<DAMP, true>(v, slot, tile, g, gt, a0, a3);
-    allow_dependent_launch();
-    if (DAMP) {
-        __shared__ double m[4];
-        if (reduce_marginal(v, slot, tile, a0, a1, a2, a3, m) && threadIdx.x < 4)
-            sv.marg[(size_t)slot * 4 + threadIdx.x] = m[threadIdx.x];
+    __shared__ int q_item, q_lo, q_n;
+    int nxt = 0;  // thread 0: the next item claimed
+    int tile, slot;
+    for (int it = 0; sweep_item<DYN>(v, 0, it, q_item, q_lo, q_n, nxt, tile, slot); ++it) {
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        if (KIND == kGateZZ) zz_unit<DAMP, true>(v, slot, tile, g, gt, a0, a1, a2, a3);
+        else rx_unit<DAMP, true>(v, slot, tile, g, gt, a0, a3);
+        allow_dependent_launch();
+        if (DAMP) {
+            __shared__ double m[4];
+            if (reduce_marginal(v, slot, tile, a0, a1, a2, a3, m) && threadIdx.x < 4)
+                sv.marg[(size_t)slot * 4 + threadIdx.x] = m[threadIdx.x];
+        }
     }
 }
 
@@ -770,7 +837,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_slot_sweep(BatchView v, SlotVie
 template <bool DAMP>
 __global__ void __launch_bounds__(kThreads) k_slot_decide(BatchView v, SlotView sv, int g, DevGate gt, double gamma) {
     grid_dependency_wait();
-    decide_slot(v, sv, blockIdx.x, g, gt, sv.marg + (size_t)blockIdx.x * 4, gamma, DAMP);
+    // a block per live slot (device-driven runs: blocks stride over the live count)
+    const int active = sv.dyn ? *sv.active : (int)gridDim.x;
+    for (int slot = blockIdx.x; slot < active; slot += gridDim.x) {
+        decide_slot(v, sv, slot, g, gt, sv.marg + (size_t)slot * 4, gamma, DAMP);
+        if (slot + (int)gridDim.x < active) __syncthreads();
+    }
     allow_dependent_launch();
 }
 
@@ -964,10 +1036,13 @@ __device__ __forceinline__ SweepCtx pending_ctx(const TrajState &s) {
 
 // Joint of the first group of a layer: a read-only pass that applies the
 // pending op of the gate before on the fly.  Grid (sweep tiles, live slots).
-template <bool PEND>
+template <bool PEND, bool DYN = false>
 __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupView gv) {
     grid_dependency_wait();
-    const int slot = blockIdx.y, tile = blockIdx.x;
+    __shared__ int q_item, q_lo, q_n;
+    int nxt = 0;  // thread 0: the next item claimed
+    int tile, slot;
+    for (int it = 0; sweep_item<DYN>(v, 0, it, q_item, q_lo, q_n, nxt, tile, slot); ++it) {
     const GateGroup *gp = gv.grp;
     __shared__ float hw[kThreads / 32][kGroupBins];
     __shared__ uint16_t vtab[2 * 4 * kGSub];
@@ -995,8 +1070,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
             if (f < nf) {
                 const uint32_t y = (uint32_t)(2 * f);
                 const float fa0 = PEND ? pend_factor(c, y) : 1.0f, fa1 = PEND ? pend_factor(c, y | 1u) : 1.0f;
-                p0 = fa0 * fa0 * (cur[k].x * cur[k].x + cur[k].y * cur[k].y);
-                p1 = fa1 * fa1 * (cur[k].z * cur[k].z + cur[k].w * cur[k].w);
+                p0 = __fmul_rn(__fmul_rn(fa0, fa0), norm2_rn(cur[k].x, cur[k].y));
+                p1 = __fmul_rn(__fmul_rn(fa1, fa1), norm2_rn(cur[k].z, cur[k].w));
             }
             hist_push(my, gb, e1, vtab[(k << 1) | (sub << 3)], p0, p1, run);
         }
@@ -1009,6 +1084,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_hist(BatchView v, GroupVi
     __syncthreads();
     allow_dependent_launch();
     hist_commit(&hw[0][0], gb, gv.Hcur + (size_t)slot * kGroupBins);
+    }
 }
 
 // Per-block joint of a mixer block (at most 4 qubits): the per-warp rows
@@ -1029,10 +1105,13 @@ __device__ __forceinline__ void lane_joint_commit(int nb, int warps, const float
 // (NEXT = 1, gv.next) on the way.  PEND: the gate before left a pending op
 // (else it is the identity and skipped).  The last phase group of a layer is
 // applied by k_group_mix instead, which also starts the mixer layer.
-template <bool PEND, int NEXT>
+template <bool PEND, int NEXT, bool DYN = false>
 __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupView gv) {
     grid_dependency_wait();
-    const int slot = blockIdx.y + gv.slot_base, tile = blockIdx.x;
+    __shared__ int q_item, q_lo, q_n;
+    int nxt = 0;  // thread 0: the next item claimed
+    int tile, slot;
+    for (int it = 0; sweep_item<DYN>(v, gv.slot_base, it, q_item, q_lo, q_n, nxt, tile, slot); ++it) {
     const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
     const GateGroup *gp = gv.grp;
     const GateGroup *nx = NEXT == 1 ? gv.next : nullptr;
@@ -1072,16 +1151,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
                 const int tb = gt.hi | gt.base | vT[(k << 1) | (sub << 3)];
                 const float fa0 = PEND ? pend_factor(c, y) : 1.0f, fa1 = PEND ? pend_factor(c, y | 1u) : 1.0f;
                 const float2 w0 = Ts[tb], w1 = Ts[tb | tE1];
-                const float wr0 = w0.x * fa0, wi0 = w0.y * fa0, wr1 = w1.x * fa1, wi1 = w1.y * fa1;
+                const float wr0 = __fmul_rn(w0.x, fa0), wi0 = __fmul_rn(w0.y, fa0);
+                const float wr1 = __fmul_rn(w1.x, fa1), wi1 = __fmul_rn(w1.y, fa1);
                 const float4 a = cur[k];
-                o.x = a.x * wr0 - a.y * wi0;
-                o.y = a.x * wi0 + a.y * wr0;
-                o.z = a.z * wr1 - a.w * wi1;
-                o.w = a.z * wi1 + a.w * wr1;
+                cmul_rn(a.x, a.y, wr0, wi0, o.x, o.y);
+                cmul_rn(a.z, a.w, wr1, wi1, o.z, o.w);
                 p4[f] = o;
             }
-            if (NEXT == 1) hist_push(my, gn, nE1, vN[(k << 1) | (sub << 3)], o.x * o.x + o.y * o.y, o.z * o.z + o.w * o.w,
-                              run);
+            if (NEXT == 1) hist_push(my, gn, nE1, vN[(k << 1) | (sub << 3)], norm2_rn(o.x, o.y), norm2_rn(o.z, o.w), run);
         }
         if (sub + 1 < kGSub) {
 #pragma unroll
@@ -1092,6 +1169,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_group_apply(BatchView v, GroupV
     __syncthreads();
     allow_dependent_launch();
     if (NEXT == 1) hist_commit(&hw[0][0], gn, gv.Hnext + (size_t)slot * kGroupBins);
+    }
 }
 
 // 16-byte asynchronous global -> shared copies (the copy engine of the SM
@@ -1170,12 +1248,15 @@ __device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
 //             by A << 4 | first half, and a full next block
 enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixKeep = 4, kMixWide = 8, kMixW1 = 16, kMixW2 = 32 };
 
-template <bool TANF, int VAR>
+template <bool TANF, int VAR, bool DYN = false>
 __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
     extern __shared__ float4 mix_buf[];  // [2][kMixTile]
     constexpr int kWarps = kMixThreads / 32;
     grid_dependency_wait();
-    const int slot = blockIdx.y + gv.slot_base;
+    __shared__ int q_item, q_lo, q_n;
+    int nxt = 0;  // thread 0: the next item claimed
+    int bx, slot;  // the block of tiles (kMixSubs per block) and the slot this item sweeps
+    for (int it = 0; sweep_item<DYN>(v, gv.slot_base, it, q_item, q_lo, q_n, nxt, bx, slot); ++it) {
     const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tL = threadIdx.x & ((1 << kMixL) - 1), tH = threadIdx.x >> kMixL;  // L part, A or B part
@@ -1228,7 +1309,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     // tile offsets: the block's first tile, plus sub-tile steps (tile bits 0, 1)
     uint32_t tbits = 0;  // tile bits of the block's first tile
     {
-        const uint32_t t0 = blockIdx.x * nsubs;
+        const uint32_t t0 = (uint32_t)bx * nsubs;
 #pragma unroll
         for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
             if (i < mm.ntile) tbits |= ((t0 >> i) & 1u) << mm.ftile[i];
@@ -1364,7 +1445,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
                 int ks = 0;
 #pragma unroll
                 for (int i = 0; i < kMixQ; ++i) ks |= (j & (1 << i)) ? nab[i] : 0;
-                hist_push(hist, gn, ne1, ks, x[j].x * x[j].x + x[j].y * x[j].y, x[j].z * x[j].z + x[j].w * x[j].w, run);
+                hist_push(hist, gn, ne1, ks, norm2_rn(x[j].x, x[j].y), norm2_rn(x[j].z, x[j].w), run);
             }
             if (final_norm) {
                 df_add(nh, nl, prob_of(1.0f, x[j].x, x[j].y));
@@ -1398,7 +1479,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
                     if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
             }
 #pragma unroll
-            for (int j = 0; j < kMixE; ++j) acc[j] += x[j].x * x[j].x + x[j].y * x[j].y + x[j].z * x[j].z + x[j].w * x[j].w;
+            for (int j = 0; j < kMixE; ++j)
+                acc[j] = __fadd_rn(acc[j], __fadd_rn(norm2_rn(x[j].x, x[j].y), norm2_rn(x[j].z, x[j].w)));
         }
         if (nN > 0 || has0) __syncthreads();  // the buffer is refilled two tiles on
     }
@@ -1411,7 +1493,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         float *bins = reinterpret_cast<float *>(mix_buf);
 #pragma unroll
         for (int j = 0; j < kMixE; ++j) {
-            float x = acc[j] * sc2;
+            float x = __fmul_rn(acc[j], sc2);
 #pragma unroll
             for (int off = 1; off < (1 << kMixL); off <<= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
             if (tL == 0) bins[tH | (j << 4)] = x;
@@ -1434,7 +1516,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         for (int i = 0; i < nN; ++i) sc2 *= rsc * rsc;
 #pragma unroll
         for (int b = 0; b < kMixE; ++b) {
-            float x = acc[b] * sc2;
+            float x = __fmul_rn(acc[b], sc2);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
             if (lane == 0) red[warp * kJointBins + b] = x;
@@ -1457,20 +1539,21 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
         if (threadIdx.x == 0) {
             double sum = 0.0;
             for (int w = 0; w < kWarps; ++w) sum += redd[w];
-            v.partials[((size_t)slot * v.tiles + blockIdx.x) * 4] = sum;
+            v.partials[((size_t)slot * v.tiles + bx) * 4] = sum;
             __threadfence();
             const unsigned prev = atomicAdd(&v.counters[slot], 1u);
-            last = prev == gridDim.x - 1;
+            last = prev == (unsigned)sweep_tiles<DYN>(v) - 1;
         }
         __syncthreads();
         if (last && threadIdx.x == 0) {
             __threadfence();
             double N = 0.0;
-            for (unsigned i = 0; i < gridDim.x; ++i) N += __ldcg(v.partials + ((size_t)slot * v.tiles + i) * 4);
+            for (int i = 0; i < sweep_tiles<DYN>(v); ++i) N += __ldcg(v.partials + ((size_t)slot * v.tiles + i) * 4);
             if (!(N > 0.0) || !isfinite(N)) atomicOr(v.status, 2);
             v.inv_norm[slot] = 1.0 / N;
             v.counters[slot] = 0;
         }
+    }
     }
 }
 
@@ -1510,13 +1593,16 @@ __device__ __forceinline__ void rx_lanes_t(float4 &o, int lanebit, float t) {
 // FULL: the rotations of qubits 4-7 are kept too (stored after them), so the
 // block's joint is binned from the stored state and its own sweep only applies
 // its factors (MixMap::wide 2).
-template <bool TANF, bool FULL>
+template <bool TANF, bool FULL, bool DYN = false>
 __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, GroupView gv, MixMap mm) {
     extern __shared__ float4 mix_buf[];  // [2][kMixE][kMixThreads]
     constexpr int kWarps = kMixThreads / 32;
     static_assert(kMixThreads == 128 && kMixE == 16 && kMixQ == 4, "the tile is f0-f10: 16 float4 x 128 threads");
     grid_dependency_wait();
-    const int slot = blockIdx.y + gv.slot_base;
+    __shared__ int q_item, q_lo, q_n;
+    int nxt = 0;  // thread 0: the next item claimed
+    int bx, slot;  // the block of tiles (kMixSubs per block) and the slot this item sweeps
+    for (int it = 0; sweep_item<DYN>(v, gv.slot_base, it, q_item, q_lo, q_n, nxt, bx, slot); ++it) {
     const int from = gv.src ? gv.src[slot] : slot;  // a new slot's first sweep reads its parent
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const GateGroup *gp = gv.grp;
@@ -1538,7 +1624,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, Group
     const int nsubs = mm.ntile >= 2 ? kMixSubs : (1 << mm.ntile);
     uint32_t tbits = 0;  // tile bits of the block's first tile
     {
-        const uint32_t t0 = blockIdx.x * nsubs;
+        const uint32_t t0 = (uint32_t)bx * nsubs;
 #pragma unroll
         for (int i = 0; i < 32; ++i)  // constant indices: the map stays in parameter space
             if (i < mm.ntile) tbits |= ((t0 >> i) & 1u) << mm.ftile[i];
@@ -1575,10 +1661,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, Group
             const float4 a = buf[j * kMixThreads];
             const int bj = binb | binj[j];
             const float2 w0 = Ts[bj], w1 = Ts[bj | bin1];
-            x[j].x = a.x * w0.x - a.y * w0.y;
-            x[j].y = a.x * w0.y + a.y * w0.x;
-            x[j].z = a.z * w1.x - a.w * w1.y;
-            x[j].w = a.z * w1.y + a.w * w1.x;
+            cmul_rn(a.x, a.y, w0.x, w0.y, x[j].x, x[j].y);
+            cmul_rn(a.z, a.w, w1.x, w1.y, x[j].z, x[j].w);
         }
 #pragma unroll
         for (int j = 0; j < kMixE; ++j) rx_pair_t<TANF>(x[j].x, x[j].y, x[j].z, x[j].w, rt);  // qubit 0
@@ -1604,8 +1688,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, Group
         }
 #pragma unroll
         for (int j = 0; j < kMixE; ++j) {
-            acc0[j] += x[j].x * x[j].x + x[j].y * x[j].y;
-            acc1[j] += x[j].z * x[j].z + x[j].w * x[j].w;
+            acc0[j] = __fadd_rn(acc0[j], norm2_rn(x[j].x, x[j].y));
+            acc1[j] = __fadd_rn(acc1[j], norm2_rn(x[j].z, x[j].w));
         }
     }
     allow_dependent_launch();
@@ -1615,7 +1699,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, Group
     // sum over lane bits 3-4 (f7-f8); lanes 0-7 then hold the bins of their qubits 1-3
 #pragma unroll
     for (int j = 0; j < kMixE; ++j) {
-        float a = acc0[j] * sc2, b = acc1[j] * sc2;
+        float a = __fmul_rn(acc0[j], sc2), b = __fmul_rn(acc1[j], sc2);
         a += __shfl_xor_sync(0xffffffffu, a, 8);
         a += __shfl_xor_sync(0xffffffffu, a, 16);
         b += __shfl_xor_sync(0xffffffffu, b, 8);
@@ -1631,6 +1715,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_group_mix(BatchView v, Group
         double sum = 0.0;
         for (int w = 0; w < kWarps; ++w) sum += (double)red[w * 256 + b];
         if (sum > 0.0) atomicAdd(H + b, __double2ull_rn(sum * kHistScale));
+    }
     }
 }
 
@@ -1776,6 +1861,7 @@ __global__ void __launch_bounds__(kThreads) k_gd_joint(BatchView v, SlotView sv,
     grid_dependency_wait();
     const int lane = threadIdx.x & 31;
     const int slot = blockIdx.x * (kThreads / 32) + (int)(threadIdx.x >> 5);  // warp per slot
+    if (sv.dyn) active = *sv.active;  // device-driven runs: the grid covers every slot there can be
     if (slot >= active) return;
     const GateGroup *gp = gv.grp;
     const int m = gp->m, ns = gp->s, nbins = 1 << ns, nsite = gp->kind == 0 ? 2 : 1;
@@ -1911,7 +1997,10 @@ __device__ void block_scan_excl(int cnt, const int *in, int *out, int base) {
 
 __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView sv, GroupView gv) {
     grid_dependency_wait();
-    const int slot = blockIdx.x;
+    // a block per live slot (device-driven runs: blocks stride over the live count)
+    const int active = sv.dyn ? *sv.active : (int)gridDim.x;
+    for (int slot = blockIdx.x; slot < active; slot += gridDim.x) {
+    if (slot != (int)blockIdx.x) __syncthreads();  // the previous slot's shared memory
     __shared__ int child_base;
     const int2 rg = sv.range[slot];
     const int off = rg.x, cnt = rg.y;
@@ -2006,6 +2095,7 @@ __global__ void __launch_bounds__(kThreads) k_gd_classes(BatchView v, SlotView s
             continue;
         }
         gv.cls[atomicAdd(gv.ncls, 1)] = gc;
+    }
     }
     allow_dependent_launch();
 }
@@ -2130,8 +2220,51 @@ __global__ void __launch_bounds__(kThreads) k_fork_copy(BatchView v, SlotView sv
 __global__ void k_fork_finish(SlotView sv) {
     grid_dependency_wait();
     const int sc = *sv.slot_count;
-    *sv.active = sc < sv.max_slots ? sc : sv.max_slots;
+    const int live = sc < sv.max_slots ? sc : sv.max_slots;
+    if (sv.prev_active) *sv.prev_active = *sv.active;
+    if (sv.live_log) sv.live_log[1 + sv.live_log[0]++] = live;
+    *sv.active = live;
     *sv.fork_count = 0;
+}
+
+// The sigma pass takes the slots of a shared-prefix run in the order of their first
+// members, so that its sums do not depend on how the forks numbered the slots.  A
+// device-driven run forms that order on the device.  First each slot marks its first
+// member's place among the K trajectories (pos[t] = slot; pos starts at -1) and records
+// its member count as its weight; a slot without members, or a member index out of
+// range, sets status bit 16.
+__global__ void k_order_mark(SlotView sv, int32_t *pos, double *weights, int K, int *status) {
+    const int ns = min(*sv.slot_count, sv.max_slots);
+    for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl < ns; sl += gridDim.x * blockDim.x) {
+        const int2 r = sv.range[sl];
+        const int t = r.y > 0 && r.x >= 0 && r.x < K ? sv.members[r.x] : -1;
+        if (t >= 0 && t < K) pos[t] = sl;
+        else atomicOr(status, 16);
+        weights[sl] = (double)r.y;
+    }
+}
+
+// ... then one block lists the marked slots in trajectory order: chunks of kThreads
+// trajectories, a ballot and a block scan per chunk.
+__global__ void __launch_bounds__(kThreads) k_order_compact(const int32_t *pos, int K, int32_t *order) {
+    __shared__ int wsum[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int carry = 0;  // slots listed by earlier chunks (the same in every thread)
+    for (int c0 = 0; c0 < K; c0 += kThreads) {
+        const int t = c0 + (int)threadIdx.x;
+        const int sl = t < K ? pos[t] : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, sl >= 0);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int base = carry, total = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            if (w < warp) base += wsum[w];
+            total += wsum[w];
+        }
+        if (sl >= 0) order[base + __popc(m & ((1u << lane) - 1u))] = sl;
+        carry += total;
+        __syncthreads();  // wsum is rewritten by the next chunk
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2183,8 +2316,10 @@ __device__ void norm_finish(const BatchView &v, int t, int tile, int ntiles, flo
 }
 
 __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
-    const int t = blockIdx.y;
-    const int tile = blockIdx.x;
+    __shared__ int q_item, q_lo, q_n;
+    int nxt = 0;  // thread 0: the next item claimed
+    int tile, t;
+    for (int it = 0; sweep_item_rt(v, 0, it, q_item, q_lo, q_n, nxt, tile, t); ++it) {
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
     const TrajState st = v.st[t];
@@ -2207,6 +2342,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(BatchView v) {
         }
     }
     norm_finish(v, t, tile, v.tiles, sh, sl);
+    }
 }
 
 constexpr int kAccChunk = 32;
@@ -2214,18 +2350,18 @@ constexpr int kAccChunk = 32;
 // The end of a sigma pass, after a block's sigma terms are out: the last block
 // to finish forms <C>_t of every state from the per-block partial sums and adds
 // S1, S2 in state order.
-__device__ void probs_finish(const BatchView &v, const AccumView &a, int64_t xblocks) {
+__device__ void probs_finish(const BatchView &v, const AccumView &a, int64_t xblocks, int nb, int rows) {
     __shared__ int last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(a.acc_counter, 1u);
-        last = prev == (unsigned)(xblocks * gridDim.y - 1);
+        last = prev == (unsigned)(xblocks * rows - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int tt = threadIdx.x; tt < v.b; tt += blockDim.x) {
+    for (int tt = threadIdx.x; tt < nb; tt += blockDim.x) {
         double sum = 0.0;
         for (int64_t i = 0; i < xblocks; ++i) sum += __ldcg(a.cpart + (size_t)tt * xblocks + i);
         a.c_out[tt] = sum * v.inv_norm[a.order ? a.order[tt] : tt];
@@ -2234,7 +2370,7 @@ __device__ void probs_finish(const BatchView &v, const AccumView &a, int64_t xbl
     if (threadIdx.x == 0) {
         if (a.sums) {
             double s1 = a.sums[0], s2 = a.sums[1];
-            for (int tt = 0; tt < v.b; ++tt) {
+            for (int tt = 0; tt < nb; ++tt) {
                 const double cv = a.c_out[tt];
                 const double w = a.weights ? a.weights[a.order ? a.order[tt] : tt] : 1.0;
                 s1 += w * cv;
@@ -2253,6 +2389,10 @@ __device__ void probs_finish(const BatchView &v, const AccumView &a, int64_t xbl
 // row order afterwards).
 template <bool TRIVIAL>
 __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, int64_t xblocks) {
+    // the states (device-driven runs: counted on the device) and the row blocks taken
+    const int nb = v.dyn_hi ? *v.dyn_hi : v.b;
+    const int rows = a.rows.used ? row_parts(a.rows, nb) : (int)gridDim.y;
+    if ((int)blockIdx.y >= rows) return;
     const int xb = blockIdx.x;
     const int n = v.n;
     const int64_t nf = (int64_t)1 << (n - 1 > 0 ? n - 1 : 0);
@@ -2316,8 +2456,8 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
         for (int off = 16; off > 0; off >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, off);
         if (lane == 0) cw[ci][warp] = cp;
     };
-    const int tbeg = (int)((int64_t)blockIdx.y * v.b / gridDim.y);
-    const int tlim = (int)((int64_t)(blockIdx.y + 1) * v.b / gridDim.y);
+    const int tbeg = (int)((int64_t)blockIdx.y * nb / rows);
+    const int tlim = (int)((int64_t)(blockIdx.y + 1) * nb / rows);
     for (int t0c = tbeg; t0c < tlim; t0c += kAccChunk) {
         const int tend = min(tlim, t0c + kAccChunk);
         // the chunk's per-state parameters, once per block
@@ -2373,11 +2513,13 @@ __global__ void __launch_bounds__(kThreads) k_probs(BatchView v, AccumView a, in
                 }
             }
     }
-    probs_finish(v, a, xblocks);
+    probs_finish(v, a, xblocks, nb, rows);
 }
 
 // sigma += the other row blocks' terms, in row order.
-__global__ void k_probs_combine(double *probs, const double *spart, int parts, int64_t dim) {
+__global__ void k_probs_combine(double *probs, const double *spart, int parts, int64_t dim, RowPlan rp,
+                                const int32_t *nbp) {
+    if (rp.used) parts = row_parts(rp, *nbp);
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < dim; x += (int64_t)gridDim.x * blockDim.x) {
         double acc = probs[x];
         for (int p = 0; p + 1 < parts; ++p) acc += spart[(size_t)p * dim + x];
@@ -2405,6 +2547,11 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
     constexpr int kE = 2 * kR;     // basis states per thread
     constexpr int kWarps = kMixThreads / 32;
     static_assert(kMixQ == 4 && kMixL == 3 && kMixThreads == 128, "lanes: 3 L bits, 1 B bit, the fourth qubit");
+    // the states (device-driven runs: counted on the device) and the row blocks taken
+    const int nb = v.dyn_hi ? *v.dyn_hi : v.b;
+    const int rows = a.rows.used ? row_parts(a.rows, nb) : (int)gridDim.y;
+    if ((int)blockIdx.y >= rows) return;
+    const int first_new = tl.first_new_dev ? *tl.first_new_dev : tl.first_new;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ float cw[kAccChunk][kWarps];
     __shared__ int c_src[kAccChunk];
@@ -2456,8 +2603,8 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
     float cut[kE];  // C(x) of this thread's basis states, constant over the states
 #pragma unroll
     for (int i = 0; i < kE; ++i) cut[i] = s_cut[i][threadIdx.x];
-    const int tbeg = (int)((int64_t)blockIdx.y * v.b / gridDim.y);
-    const int tlim = (int)((int64_t)(blockIdx.y + 1) * v.b / gridDim.y);
+    const int tbeg = (int)((int64_t)blockIdx.y * nb / rows);
+    const int tlim = (int)((int64_t)(blockIdx.y + 1) * nb / rows);
     for (int t0c = tbeg; t0c < tlim; t0c += kAccChunk) {
         const int cn = min(tlim, t0c + kAccChunk) - t0c;
         // the chunk's per-state parameters, once per block
@@ -2465,7 +2612,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
             const int tt = t0c + threadIdx.x;
             const int sl = a.order ? a.order[tt] : tt;
             const TrajState st = v.st[sl];
-            c_src[threadIdx.x] = sl >= tl.first_new ? tl.parent[sl] : sl;
+            c_src[threadIdx.x] = sl >= first_new ? tl.parent[sl] : sl;
             c_Ff[threadIdx.x] = v.frame_x[(size_t)sl * (v.G + 1) + v.G] ^ st.J ^ st.pend;
             const double inv = v.inv_norm[sl] * (a.weights ? a.weights[sl] : 1.0);
             const float ih = (float)inv;
@@ -2550,7 +2697,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
             }
         }
     }
-    probs_finish(v, a, xblocks);
+    probs_finish(v, a, xblocks, nb, rows);
 }
 
 // ---------------------------------------------------------------------------
@@ -3082,8 +3229,55 @@ cudaError_t launch_prepare(const BatchView &v, const DevGate *gates, uint64_t se
     return cudaGetLastError();
 }
 
+// Blocks of one kernel that fit on one SM at once (cached per kernel).
+static int blocks_per_sm(const void *kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(kernel);
+    if (it != cache.end()) return it->second;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess) per = 1;
+    per = std::max(per, 1);
+    cache.emplace(kernel, per);
+    return per;
+}
+
+static int sm_count() {
+    static const int sms = [] {  // initialised once, safely under concurrent first calls
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 152;
+    }();
+    return sms;
+}
+
+// The grid of a sweep launch of gx blocks (tiles) per slot over `most` slots.  Sized on
+// the host: (gx, most), one block per tile and slot.  Device-driven (v.dyn_hi set; `most` =
+// the slots there can be): a persistent grid of as many blocks as the device holds of this
+// kernel at once (at most gx * most), which take the items of v's counter (*lv: v with the
+// tile count set).
+static dim3 sweep_grid(const BatchView &v, const void *kernel, int threads, size_t smem, unsigned gx, int most,
+                       BatchView *lv) {
+    *lv = v;
+    if (!v.dyn_hi) return dim3(gx, (unsigned)most);
+    lv->dyn_tiles = (int32_t)gx;
+    const int64_t resident = (int64_t)blocks_per_sm(kernel, threads, smem) * sm_count();
+    return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, (int64_t)gx * std::max(most, 1))));
+}
+
+// Blocks of a block-per-slot decide kernel: one per live slot, or (device-driven) enough to
+// fill the device, each striding over the slots.
+static unsigned slot_blocks(const SlotView &sv, const void *kernel, int active) {
+    if (!sv.dyn) return (unsigned)active;
+    return (unsigned)std::max(1, std::min(active, blocks_per_sm(kernel, kThreads, 0) * sm_count()));
+}
+
 cudaError_t launch_init(const BatchView &v, cudaStream_t s) {
-    k_init<<<dim3((unsigned)v.tiles, (unsigned)v.b), kThreads, 0, s>>>(v);
+    BatchView lv;
+    const dim3 grid = sweep_grid(v, (const void *)k_init, kThreads, 0, (unsigned)v.tiles, v.b, &lv);
+    k_init<<<grid, kThreads, 0, s>>>(lv);
     return cudaGetLastError();
 }
 
@@ -3120,15 +3314,6 @@ static int persistent_blocks() {
     return blocks;
 }
 
-// Blocks of kThreads that fit on the device at once (kernel without dynamic shared memory).
-template <typename K>
-static int resident_blocks(K kernel) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0);
-    return (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
-}
 
 template <typename K, typename... Args>
 static cudaError_t launch_pdl_smem(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
@@ -3152,32 +3337,50 @@ static cudaError_t launch_pdl(K kernel, dim3 grid, dim3 block, cudaStream_t s, A
 
 cudaError_t launch_slot_sweep(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
                               int damping_on, cudaStream_t s) {
-    const dim3 grid((unsigned)v.stiles, (unsigned)active), block(kThreads);
-    if (gate.kind == kGateZZ)
-        return damping_on ? launch_pdl(k_slot_sweep<true, kGateZZ>, grid, block, s, v, sv, g, gate)
-                          : launch_pdl(k_slot_sweep<false, kGateZZ>, grid, block, s, v, sv, g, gate);
-    return damping_on ? launch_pdl(k_slot_sweep<true, kGateRX>, grid, block, s, v, sv, g, gate)
-                      : launch_pdl(k_slot_sweep<false, kGateRX>, grid, block, s, v, sv, g, gate);
+    BatchView lv;
+    const dim3 grid = sweep_grid(v, (const void *)k_slot_sweep<true, kGateZZ, true>, kThreads, 0, (unsigned)v.stiles,
+                                 active, &lv),
+               block(kThreads);
+#define QN_SLOT(D, K)                                                                                    \
+    (v.dyn_hi ? launch_pdl(k_slot_sweep<D, K, true>, grid, block, s, lv, sv, g, gate)                   \
+              : launch_pdl(k_slot_sweep<D, K, false>, grid, block, s, lv, sv, g, gate))
+    if (gate.kind == kGateZZ) return damping_on ? QN_SLOT(true, kGateZZ) : QN_SLOT(false, kGateZZ);
+    return damping_on ? QN_SLOT(true, kGateRX) : QN_SLOT(false, kGateRX);
+#undef QN_SLOT
 }
 
 cudaError_t launch_slot_fork(const BatchView &v, const SlotView &sv, int active, int g, const DevGate &gate,
                              const NoiseDev &nz, int damping_on, cudaStream_t s) {
     const int blocks = persistent_blocks();
     const dim3 block(kThreads);
-    cudaError_t e = damping_on ? launch_pdl(k_slot_decide<true>, dim3((unsigned)active), block, s, v, sv, g, gate, nz.gamma)
-                               : launch_pdl(k_slot_decide<false>, dim3((unsigned)active), block, s, v, sv, g, gate, nz.gamma);
+    const dim3 slots(slot_blocks(sv, (const void *)k_slot_decide<true>, active));
+    cudaError_t e = damping_on ? launch_pdl(k_slot_decide<true>, slots, block, s, v, sv, g, gate, nz.gamma)
+                               : launch_pdl(k_slot_decide<false>, slots, block, s, v, sv, g, gate, nz.gamma);
     if (e != cudaSuccess) return e;
     e = launch_pdl(k_fork_copy, dim3(blocks), block, s, v, sv);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_fork_finish, dim3(1), dim3(1), s, sv);
 }
 
-cudaError_t launch_observe(const BatchView &v, const AccumView &, cudaStream_t s) {
-    k_observe<<<dim3((unsigned)v.tiles, (unsigned)v.b), kThreads, 0, s>>>(v);
+cudaError_t launch_slot_order(const SlotView &sv, int32_t *pos, int32_t *order, double *weights, int K, int *status,
+                              cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(pos, 0xff, (size_t)K * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(order, 0, (size_t)K * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)std::max(1, std::min((K + kThreads - 1) / kThreads, 4 * sm_count()));
+    k_order_mark<<<blocks, kThreads, 0, s>>>(sv, pos, weights, K, status);
+    k_order_compact<<<1, kThreads, 0, s>>>(pos, K, order);
     return cudaGetLastError();
 }
 
-int probs_parts(int n, int b, int kind) {
+cudaError_t launch_observe(const BatchView &v, const AccumView &, cudaStream_t s) {
+    BatchView lv;
+    const dim3 grid = sweep_grid(v, (const void *)k_observe, kThreads, 0, (unsigned)v.tiles, v.b, &lv);
+    k_observe<<<grid, kThreads, 0, s>>>(lv);
+    return cudaGetLastError();
+}
+
+RowPlan probs_row_plan(int n, int kind) {
     // blocks per state: k_probs covers 2048 amplitudes per block, k_probs_mix 2048 (half a mixer tile)
     const int64_t xb = kind == 2 ? std::max<int64_t>(2, (int64_t)1 << std::max(0, n - 11)) : accumulate_xblocks(n);
     // resident blocks of each pass, initialised once (safely under concurrent first calls)
@@ -3193,26 +3396,17 @@ int probs_parts(int n, int b, int kind) {
         for (int k = 0; k < 3; ++k) r[k] = std::max(sms, 1) * std::max(occ[k], 1);
         return r;
     }();
-    const int res = resident[kind < 0 ? 0 : kind > 2 ? 2 : kind];
-    // Every block of a row streams all of the row's states, so the launch takes about
-    // ceil(xb P / resident) rounds of b / P states each: take the P with the fewest
-    // state-rounds (the smaller on a tie).  A row keeps at least one chunk of states,
-    // and rows past the first hold a sigma copy (8 B per basis state), 64 MiB at most.
+    RowPlan r{};
+    r.xb = xb;
+    r.res = resident[kind < 0 ? 0 : kind > 2 ? 2 : kind];
+    // rows past the first hold a sigma copy (8 B per basis state), 64 MiB at most
     const int64_t copies = std::max<int64_t>(0, ((int64_t)64 << 20) / ((int64_t)8 << n));
-    const int64_t row_cap = std::min<int64_t>((int64_t)kMaxProbParts, ((int64_t)b + kAccChunk - 1) / kAccChunk);
-    const int pmax = (int)std::max<int64_t>(1, std::min<int64_t>(row_cap, 1 + copies));
-    int best = 1;
-    double best_cost = 0.0;
-    for (int p = 1; p <= pmax; ++p) {
-        const double rounds = (double)((xb * p + res - 1) / res);
-        const double cost = rounds * std::ceil((double)b / p);
-        if (p == 1 || cost < best_cost * 0.995) {
-            best = p;
-            best_cost = cost;
-        }
-    }
-    return best;
+    r.pmax = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)kMaxProbParts, 1 + copies));
+    r.used = 0;
+    return r;
 }
+
+int probs_parts(int n, int b, int kind) { return row_parts(probs_row_plan(n, kind), b); }
 
 cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s) {
     const int64_t xb = accumulate_xblocks(v.n);
@@ -3223,7 +3417,8 @@ cudaError_t launch_probs(const BatchView &v, const AccumView &a, cudaStream_t s)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || parts == 1) return e;
     const int64_t dim = (int64_t)1 << v.n;
-    k_probs_combine<<<(unsigned)std::min<int64_t>((dim + 255) / 256, 4096), 256, 0, s>>>(a.probs, a.spart, parts, dim);
+    k_probs_combine<<<(unsigned)std::min<int64_t>((dim + 255) / 256, 4096), 256, 0, s>>>(a.probs, a.spart, parts, dim,
+                                                                                        a.rows, v.dyn_hi);
     return cudaGetLastError();
 }
 
@@ -3237,7 +3432,8 @@ cudaError_t launch_probs_mix(const BatchView &v, const AccumView &a, const MixMa
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || parts == 1) return e;
     const int64_t dim = (int64_t)1 << v.n;
-    k_probs_combine<<<(unsigned)std::min<int64_t>((dim + 255) / 256, 4096), 256, 0, s>>>(a.probs, a.spart, parts, dim);
+    k_probs_combine<<<(unsigned)std::min<int64_t>((dim + 255) / 256, 4096), 256, 0, s>>>(a.probs, a.spart, parts, dim,
+                                                                                        a.rows, v.dyn_hi);
     return cudaGetLastError();
 }
 
@@ -3366,20 +3562,24 @@ static unsigned group_tiles(int n) {
 }
 
 cudaError_t launch_group_hist(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
-    const dim3 grid(group_tiles(v.n), (unsigned)active);
-    return gv.pend ? launch_pdl(k_group_hist<true>, grid, dim3(kThreads), s, v, gv)
-                   : launch_pdl(k_group_hist<false>, grid, dim3(kThreads), s, v, gv);
+    BatchView lv;
+    const dim3 grid = sweep_grid(v, (const void *)k_group_hist<true, true>, kThreads, 0, group_tiles(v.n), active, &lv);
+    if (v.dyn_hi)
+        return gv.pend ? launch_pdl(k_group_hist<true, true>, grid, dim3(kThreads), s, lv, gv)
+                       : launch_pdl(k_group_hist<false, true>, grid, dim3(kThreads), s, lv, gv);
+    return gv.pend ? launch_pdl(k_group_hist<true>, grid, dim3(kThreads), s, lv, gv)
+                   : launch_pdl(k_group_hist<false>, grid, dim3(kThreads), s, lv, gv);
 }
 
 cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const GroupView &gv, int ns, int active,
                                 double gamma, cudaStream_t s) {
     const dim3 blk(kThreads);
-    const dim3 slots((unsigned)active);
+    const dim3 slots(slot_blocks(sv, (const void *)k_gd_classes, active));
     const dim3 slot_warps((unsigned)((active + kThreads / 32 - 1) / (kThreads / 32)));
     const int class_blocks = (sv.max_slots + kThreads / 32 - 1) / (kThreads / 32);
     cudaError_t e;
 #define QN_GD(R)                                                                                \
-    static const int resident = resident_blocks(k_gd_tables<R>);                                \
+    const int resident = blocks_per_sm((const void *)k_gd_tables<R>, kThreads, 0) * sm_count();  \
     const dim3 classes((unsigned)std::min(class_blocks, resident));                             \
     const dim3 members((unsigned)((gv.members + gd_members_per_block(R) - 1) / gd_members_per_block(R))); \
     e = launch_pdl(k_gd_joint<R>, slot_warps, blk, s, v, sv, gv, gamma, active);                \
@@ -3403,15 +3603,18 @@ cudaError_t launch_group_decide(const BatchView &v, const SlotView &sv, const Gr
 // The mixer sweeps' dynamic shared memory (two tiles), set once for every variant.
 static cudaError_t launch_mix_sweep_attrs() {
     static const cudaError_t attr = [] {
-        const void *ks[] = {(const void *)k_mix_sweep<true, kMixAny>,   (const void *)k_mix_sweep<true, kMixMid>,
-                            (const void *)k_mix_sweep<true, kMixHist>,  (const void *)k_mix_sweep<true, kMixKeep>,
-                            (const void *)k_mix_sweep<false, kMixAny>,  (const void *)k_mix_sweep<false, kMixMid>,
-                            (const void *)k_mix_sweep<false, kMixHist>, (const void *)k_mix_sweep<false, kMixKeep>,
-                            (const void *)k_mix_sweep<true, kMixWide>,  (const void *)k_mix_sweep<false, kMixWide>,
-                            (const void *)k_mix_sweep<true, kMixW1>,    (const void *)k_mix_sweep<false, kMixW1>,
-                            (const void *)k_mix_sweep<true, kMixW2>,    (const void *)k_mix_sweep<false, kMixW2>,
-                            (const void *)k_group_mix<true, false>,     (const void *)k_group_mix<false, false>,
-                            (const void *)k_group_mix<true, true>,      (const void *)k_group_mix<false, true>};
+#define QN_KS(D)                                                                                          \
+    (const void *)k_mix_sweep<true, kMixAny, D>, (const void *)k_mix_sweep<true, kMixMid, D>,             \
+        (const void *)k_mix_sweep<true, kMixHist, D>, (const void *)k_mix_sweep<true, kMixKeep, D>,       \
+        (const void *)k_mix_sweep<false, kMixAny, D>, (const void *)k_mix_sweep<false, kMixMid, D>,       \
+        (const void *)k_mix_sweep<false, kMixHist, D>, (const void *)k_mix_sweep<false, kMixKeep, D>,     \
+        (const void *)k_mix_sweep<true, kMixWide, D>, (const void *)k_mix_sweep<false, kMixWide, D>,      \
+        (const void *)k_mix_sweep<true, kMixW1, D>, (const void *)k_mix_sweep<false, kMixW1, D>,          \
+        (const void *)k_mix_sweep<true, kMixW2, D>, (const void *)k_mix_sweep<false, kMixW2, D>,          \
+        (const void *)k_group_mix<true, false, D>, (const void *)k_group_mix<false, false, D>,            \
+        (const void *)k_group_mix<true, true, D>, (const void *)k_group_mix<false, true, D>
+        const void *ks[] = {QN_KS(false), QN_KS(true)};
+#undef QN_KS
         for (const void *k : ks) {
             const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem);
             if (e != cudaSuccess) return e;
@@ -3421,11 +3624,17 @@ static cudaError_t launch_mix_sweep_attrs() {
     return attr;
 }
 
-cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
+cudaError_t launch_mix_sweep(const BatchView &vh, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
     const cudaError_t attr = launch_mix_sweep_attrs();
     if (attr != cudaSuccess) return attr;
     const unsigned blocks = mm.ntile >= 2 ? (1u << mm.ntile) / kMixSubs : 1u;
-    const dim3 grid(blocks, (unsigned)active), block(kMixThreads);
+    BatchView v;
+    const dim3 grid = sweep_grid(vh, (const void *)k_mix_sweep<true, kMixMid, true>, kMixThreads, kMixSmem, blocks,
+                                 active, &v),
+               block(kMixThreads);
+#define QN_MIX(T, V)                                                                                     \
+    (v.dyn_hi ? launch_pdl_smem(k_mix_sweep<T, V, true>, grid, block, kMixSmem, s, v, gv, mm)            \
+              : launch_pdl_smem(k_mix_sweep<T, V, false>, grid, block, kMixSmem, s, v, gv, mm))
     int var = kMixAny;
     if (mm.wide == 2 || mm.wide == 3) {
         // full blocks off qubit 0 with a full next block; the other half's four f bits
@@ -3442,10 +3651,10 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
         if (mm.wide == 2) ok = ok && mm.fL[0] == 0 && mm.fL[1] == 1 && mm.fL[2] == 2 && mm.wsh == 3;
         if (!ok) return cudaErrorInvalidValue;
         if (mm.wide == 2)
-            return mm.tanf ? launch_pdl_smem(k_mix_sweep<true, kMixW1>, grid, block, kMixSmem, s, v, gv, mm)
-                           : launch_pdl_smem(k_mix_sweep<false, kMixW1>, grid, block, kMixSmem, s, v, gv, mm);
-        return mm.tanf ? launch_pdl_smem(k_mix_sweep<true, kMixW2>, grid, block, kMixSmem, s, v, gv, mm)
-                       : launch_pdl_smem(k_mix_sweep<false, kMixW2>, grid, block, kMixSmem, s, v, gv, mm);
+            return mm.tanf ? QN_MIX(true, kMixW1)
+                           : QN_MIX(false, kMixW1);
+        return mm.tanf ? QN_MIX(true, kMixW2)
+                       : QN_MIX(false, kMixW2);
     }
     if (mm.wide) {
         // qubits 4-7 with the factors of qubits 0-7: the lane bits must be qubits 1-3, the block
@@ -3454,8 +3663,8 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
                         mm.fL[0] == 0 && mm.fL[1] == 1 && mm.fL[2] == 2 && mm.fA[0] == 3 && mm.fA[1] == 4 &&
                         mm.fA[2] == 5 && mm.fA[3] == 6;
         if (!ok) return cudaErrorInvalidValue;
-        return mm.tanf ? launch_pdl_smem(k_mix_sweep<true, kMixWide>, grid, block, kMixSmem, s, v, gv, mm)
-                       : launch_pdl_smem(k_mix_sweep<false, kMixWide>, grid, block, kMixSmem, s, v, gv, mm);
+        return mm.tanf ? QN_MIX(true, kMixWide)
+                       : QN_MIX(false, kMixWide);
     }
     if (mm.M == kMixQ) {
         const bool next_full = mm.nN == kMixQ && !gv.next && !mm.final_norm;
@@ -3463,7 +3672,6 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
         else if (!mm.has0 && mm.nN == 0 && gv.next && !mm.final_norm) var = kMixHist;
         else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm && mm.keep) var = kMixKeep;
     }
-#define QN_MIX(T, V) launch_pdl_smem(k_mix_sweep<T, V>, grid, block, kMixSmem, s, v, gv, mm)
     switch (var) {
     case kMixMid: return mm.tanf ? QN_MIX(true, kMixMid) : QN_MIX(false, kMixMid);
     case kMixHist: return mm.tanf ? QN_MIX(true, kMixHist) : QN_MIX(false, kMixHist);
@@ -3473,7 +3681,7 @@ cudaError_t launch_mix_sweep(const BatchView &v, const GroupView &gv, const MixM
 #undef QN_MIX
 }
 
-cudaError_t launch_group_mix(const BatchView &v, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
+cudaError_t launch_group_mix(const BatchView &vh, const GroupView &gv, const MixMap &mm, int active, cudaStream_t s) {
     cudaError_t e = launch_mix_sweep_attrs();
     if (e != cudaSuccess) return e;
     const bool natural = mm.has0 && mm.M == kMixQ && mm.nN == kMixQ && mm.fA[0] == 0 && mm.fA[1] == 1 &&
@@ -3481,18 +3689,44 @@ cudaError_t launch_group_mix(const BatchView &v, const GroupView &gv, const MixM
                          mm.fB[3] == 6 && mm.fL[0] == 8 && mm.fL[1] == 9 && mm.fL[2] == 10;
     if (!natural || gv.pend) return cudaErrorInvalidValue;
     const unsigned blocks = mm.ntile >= 2 ? (1u << mm.ntile) / kMixSubs : 1u;
-    const dim3 grid(blocks, (unsigned)active), block(kMixThreads);
-    if (mm.full8)
-        return mm.tanf ? launch_pdl_smem(k_group_mix<true, true>, grid, block, kMixSmem, s, v, gv, mm)
-                       : launch_pdl_smem(k_group_mix<false, true>, grid, block, kMixSmem, s, v, gv, mm);
-    return mm.tanf ? launch_pdl_smem(k_group_mix<true, false>, grid, block, kMixSmem, s, v, gv, mm)
-                   : launch_pdl_smem(k_group_mix<false, false>, grid, block, kMixSmem, s, v, gv, mm);
+    BatchView v;
+    const dim3 grid = sweep_grid(vh, (const void *)k_group_mix<true, true, true>, kMixThreads, kMixSmem, blocks, active,
+                                 &v),
+               block(kMixThreads);
+#define QN_GMIX(T, F)                                                                                    \
+    (v.dyn_hi ? launch_pdl_smem(k_group_mix<T, F, true>, grid, block, kMixSmem, s, v, gv, mm)            \
+              : launch_pdl_smem(k_group_mix<T, F, false>, grid, block, kMixSmem, s, v, gv, mm))
+    if (mm.full8) return mm.tanf ? QN_GMIX(true, true) : QN_GMIX(false, true);
+    return mm.tanf ? QN_GMIX(true, false) : QN_GMIX(false, false);
+#undef QN_GMIX
 }
 
-cudaError_t launch_group_apply(const BatchView &v, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
-    const dim3 grid(group_tiles(v.n), (unsigned)active), blk(kThreads);
+cudaError_t prewarm_dev_launches() {
+    const cudaError_t e = launch_mix_sweep_attrs();
+    if (e != cudaSuccess) return e;
+    (void)sm_count();
+    const void *plain[] = {(const void *)k_init, (const void *)k_observe, (const void *)k_group_hist<true, true>,
+                           (const void *)k_group_apply<true, 1, true>, (const void *)k_slot_sweep<true, kGateZZ, true>,
+                           (const void *)k_slot_decide<true>, (const void *)k_gd_classes,
+                           (const void *)k_gd_tables<1>, (const void *)k_gd_tables<4>, (const void *)k_gd_tables<8>,
+                           (const void *)k_gd_tables<kGroupBins / 32>};
+    for (const void *k : plain) (void)blocks_per_sm(k, kThreads, 0);
+    (void)blocks_per_sm((const void *)k_mix_sweep<true, kMixMid, true>, kMixThreads, kMixSmem);
+    (void)blocks_per_sm((const void *)k_group_mix<true, true, true>, kMixThreads, kMixSmem);
+    (void)persistent_blocks();
+    (void)probs_row_plan(1, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_apply(const BatchView &vh, const SlotView &, const GroupView &gv, int active, cudaStream_t s) {
+    BatchView v;
+    const dim3 grid = sweep_grid(vh, (const void *)k_group_apply<true, 1, true>, kThreads, 0, group_tiles(vh.n), active,
+                                 &v),
+               blk(kThreads);
     const int next = gv.next ? 1 : 0;
-#define QN_APPLY(P, N) launch_pdl(k_group_apply<P, N>, grid, blk, s, v, gv)
+#define QN_APPLY(P, N)                                                                                   \
+    (v.dyn_hi ? launch_pdl(k_group_apply<P, N, true>, grid, blk, s, v, gv)                               \
+              : launch_pdl(k_group_apply<P, N, false>, grid, blk, s, v, gv))
     if (gv.pend) return next == 1 ? QN_APPLY(true, 1) : QN_APPLY(true, 0);
     return next == 1 ? QN_APPLY(false, 1) : QN_APPLY(false, 0);
 #undef QN_APPLY

@@ -48,6 +48,8 @@ _SIGS = {
     "qn_batch_set_sharing": (c_i32, [c_vp, c_i32]),
     "qn_batch_set_fusion": (c_i32, [c_vp, c_i32]),
     "qn_batch_set_precision": (c_i32, [c_vp, c_i32]),
+    "qn_batch_set_launch_mode": (c_i32, [c_vp, c_i32]),
+    "qn_graph_info": (c_i32, [c_vp, P(c_i64), P(c_i64), P(c_i64)]),
     "qn_run_qaoa": (c_i32, [c_vp, P(qn_graph), c_i32, P(c_dbl), P(c_dbl), P(qn_noise)]),
     "qn_expectation": (c_i32, [c_vp, P(c_dbl), P(c_dbl)]),
     "qn_probs": (c_i32, [c_vp, P(c_dbl), c_i64]),
@@ -156,6 +158,18 @@ class Batch:
     def set_sharing(self, on: bool) -> None:
         """Shared-prefix mode: trajectories share their common Kraus prefix."""
         check(qn_batch_set_sharing(self._h, int(bool(on))), "qn_batch_set_sharing")
+
+    def set_launch_mode(self, mode) -> None:
+        """How shared-prefix launches are sized: 0 / "host" (from the live-slot count read
+        after every decide), 1 / "device" (persistent launches that read it on the device),
+        2 / "graph" (as 1, the run captured in a CUDA graph and replayed)."""
+        m = {"host": 0, "device": 1, "graph": 2}.get(mode, mode)
+        check(qn_batch_set_launch_mode(self._h, int(m)), "qn_batch_set_launch_mode")
+
+    def graph_info(self) -> dict:
+        c, r, u = c_i64(), c_i64(), c_i64()
+        check(qn_graph_info(self._h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(u)), "qn_graph_info")
+        return dict(captures=c.value, replays=r.value, updates=u.value)
 
     def set_offset(self, first_trajectory: int) -> None:
         """Global id of this handle's first trajectory (shards of one ensemble)."""

@@ -11,10 +11,20 @@ are on the GPU start at once and their kernels overlap on the device.  Device
 memory comes from the PyTorch caching allocator, so finishing a request frees
 nothing device-wide (no cudaFree synchronisation).
 
+Launches (qn_batch_set_launch_mode, shared-prefix requests): with the default
+policy "auto" a request runs device-driven -- persistent sweeps that read the
+live-slot count on the device, so its worker thread never waits on the GPU
+between groups of gates and its launches queue up behind the other requests'
+-- and a request that runs in more than one launch batch (chunk) captures its
+first chunk in a CUDA graph, which its later chunks replay.  "host" sizes every
+launch on the host (a read of the live count after each decide), "device" and
+"graph" force modes 1 and 2.
+
 All arithmetic runs in libqnoise's kernels; this module only schedules.  A
-request's result does not depend on what runs beside it: its launch batch
-size is a function of the request alone and every draw is keyed by
-(seed, trajectory id).
+request's result does not depend on what runs beside it, nor on the launch
+policy: its launch batch size is a function of the request alone, every draw
+is keyed by (seed, trajectory id), and every launch mode gives bit-identical
+results.
 """
 from __future__ import annotations
 
@@ -47,6 +57,10 @@ class Request:
     def launch_batch(self) -> int:
         return int(max(1, min(self.trajectories, STATE_BUDGET_BYTES // (8 << self.n))))
 
+    def chunks(self) -> int:
+        """Launch batches (prefix trees) the request runs in, one after the other."""
+        return -(-self.trajectories // self.launch_batch())
+
     def footprint(self) -> int:
         """HBM bytes the request holds while it runs: its launch batch of complex64
         statevectors plus per-trajectory tables and the sigma accumulator."""
@@ -67,19 +81,36 @@ class Result:
     # last launch, in ms after the server's reference event (None outside a Server)
     device_start: float | None = None
     device_end: float | None = None
+    # the launch mode the request ran in, and its graph use (qn_graph_info)
+    launch: dict | None = None
 
     @property
     def latency(self) -> float:
         return self.finished - self.submitted
 
 
-class Server:
-    """Admit-and-run loop.  `max_inflight` worker threads (one CUDA stream each)
-    and a device memory budget in bytes."""
+LAUNCH_POLICIES = ("auto", "host", "device", "graph")
 
-    def __init__(self, max_inflight: int = 4, mem_budget: int | None = None, lookahead: int = 8):
+
+def launch_mode_for(req: Request, policy: str = "auto") -> int:
+    """qn_batch_set_launch_mode value of a request under a launch policy."""
+    if policy not in LAUNCH_POLICIES:
+        raise ValueError(f"launch policy {policy!r} not in {LAUNCH_POLICIES}")
+    if policy == "auto":
+        return 2 if req.chunks() > 1 else 1
+    return {"host": 0, "device": 1, "graph": 2}[policy]
+
+
+class Server:
+    """Admit-and-run loop.  `max_inflight` worker threads (one CUDA stream each),
+    a device memory budget in bytes and a launch policy (LAUNCH_POLICIES)."""
+
+    def __init__(self, max_inflight: int = 4, mem_budget: int | None = None, lookahead: int = 8,
+                 launch_policy: str = "auto"):
         import torch
 
+        launch_mode_for(Request(1, np.zeros((0, 2), np.int32), np.zeros(0), np.zeros(0), 1, 0), launch_policy)
+        self.launch_policy = launch_policy
         self._torch = torch
         self.device = torch.cuda.current_device()
         if mem_budget is None:
@@ -165,13 +196,16 @@ class Server:
             with qn.Batch(req.n, req.trajectories, req.seed, launch_batch=req.launch_batch(), stream=stream,
                           torch_allocator=True) as b:
                 b.set_sharing(req.damping > 0)
+                mode = launch_mode_for(req, self.launch_policy)
+                b.set_launch_mode(mode)
                 b.run_qaoa(req.edges, req.gammas, req.betas, p1=req.p1, p2=req.p2, damping=req.damping)
                 mean, se = b.expectation()
                 probs = b.probs() if req.want_probs else None
                 ev_b.record(stream)
                 ev_b.synchronize()
+                launch = dict(mode=mode, **b.graph_info())
             fut.set_result(Result(mean, se, probs, submitted, started, time.perf_counter(),
-                                  self._ref.elapsed_time(ev_a), self._ref.elapsed_time(ev_b)))
+                                  self._ref.elapsed_time(ev_a), self._ref.elapsed_time(ev_b), launch))
         except Exception as exc:  # delivered to the caller through the future
             fut.set_exception(exc)
         finally:
@@ -182,11 +216,12 @@ class Server:
                 self._lock.notify_all()
 
 
-def run_alone(req: Request) -> Result:
+def run_alone(req: Request, launch_policy: str = "host") -> Result:
     """The same request on its own (a fresh handle on the default stream)."""
     t0 = time.perf_counter()
     with qn.Batch(req.n, req.trajectories, req.seed, launch_batch=req.launch_batch()) as b:
         b.set_sharing(req.damping > 0)
+        b.set_launch_mode(launch_mode_for(req, launch_policy))
         b.run_qaoa(req.edges, req.gammas, req.betas, p1=req.p1, p2=req.p2, damping=req.damping)
         mean, se = b.expectation()
         probs = b.probs() if req.want_probs else None

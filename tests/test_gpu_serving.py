@@ -1,7 +1,8 @@
 """Continuous batching (paper_2210_15874_gb300.serving): requests of mixed n,
 depth, trajectory count and noise are admitted by HBM footprint as slots free
-up and run concurrently on separate streams.  Each result must equal the same
-request run alone."""
+up and run concurrently on separate streams, with device-driven launches (and
+CUDA graphs replayed over the chunks of a request that runs in several).  Each
+result must equal the same request run alone with host-sized launches."""
 import numpy as np
 import pytest
 
@@ -89,3 +90,23 @@ def test_admission_by_footprint(mods):
             srv2.submit(reqs[0])
         finally:
             srv2.close()
+
+
+def test_chunked_requests_replay_their_graphs(mods, monkeypatch):
+    """With launch batches smaller than the requests, the default launch policy captures
+    each damping request's first chunk in a CUDA graph and replays it for the others; the
+    results equal host-sized runs of the same requests, alone."""
+    serving = mods
+    monkeypatch.setattr(serving, "STATE_BUDGET_BYTES", 2 << 20)  # small launch batches: several chunks
+    reqs = [r for r in make_requests(serving, 16, np.random.default_rng(8)) if r.damping > 0 and r.chunks() >= 2]
+    assert len(reqs) >= 3
+    alone = [serving.run_alone(r, "host") for r in reqs]
+    srv = serving.Server(max_inflight=3)
+    mixed = [f.result(timeout=300) for f in [srv.submit(r) for r in reqs]]
+    srv.close()
+    for r, a, m in zip(reqs, alone, mixed):
+        assert m.launch["mode"] == 2
+        assert m.launch["captures"] + m.launch["replays"] == r.chunks()
+        assert m.launch["replays"] >= r.chunks() - 2  # only a shorter last chunk captures again
+        assert a.mean == m.mean and a.std_err == m.std_err
+        np.testing.assert_array_equal(m.probs, a.probs)
