@@ -424,7 +424,7 @@ def gpu_arm(args):
         fused = main_mode[1] and w.damping == 0
         grouped = sharing and main_mode[1] and main["groups"]["launches"] > 0
         blocks = grouped and main["mixers"]["launches"] > 0
-        kname = "k_mix_sweep (mixer blocks over live prefix states: qubits 4-7 of the block over 0-7, then 4 qubits per sweep; 16 B per amplitude)" if blocks else \
+        kname = "k_mix_sweep (mixer blocks over live prefix states: the factors of block 0-7 with the rotations of 8-11, the rotations of 12-15 with the factors of block 8-15, then 4 qubits per sweep; 16 B per amplitude)" if blocks else \
             "k_slot_sweep (mixer gate sweeps over live prefix states)" if grouped else \
             "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
             (("k_tc_sweep (tensor-core windows of 5 qubits, %s, 16 B per amplitude)" %
@@ -440,9 +440,13 @@ def gpu_arm(args):
             "config": config_of(w, {
                 "parallelism": f"trajectory shards x{world}" if world > 1 else "single GPU",
                 "mode": ("shared-prefix: one statevector per distinct Kraus prefix, all trajectories in one "
-                         "prefix tree" + ("; phase gates applied in groups on <= 10 qubits and mixer rotations "
-                                          "in blocks of 4 qubits, one sweep per group or block" if grouped
-                                          else "; one sweep per gate")) if sharing else
+                         "prefix tree" + ("; phase gates applied in groups on <= 10 qubits, one sweep per group, "
+                                          "and each layer's mixer rotations in blocks: qubits 0-7 and 8-15 drawn as "
+                                          "8-qubit blocks over two sweeps each, then 4 qubits per sweep" if grouped
+                                          else "; one sweep per gate")
+                         + ("; launches sized on the host from the live-slot count" if args.launch_mode == 0 else
+                            "; device-driven persistent launches" + (" replayed as a CUDA graph"
+                                                                      if args.launch_mode == 2 else ""))) if sharing else
                         (f"fused layers: qubits 0-7, then windows of <= 7 qubits, one sweep each per QAOA layer, "
                          f"{w.batch} trajectories per launch" if fused
                          else f"one statevector per trajectory, one sweep per gate, {w.batch} per launch")}),
@@ -558,7 +562,7 @@ def serving_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(sharing=False, depth=1, fusion=True, precision=-1):
+def profile_case(sharing=False, depth=1, fusion=True, precision=-1, launch_mode=0):
     """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state);
     depth 2 adds a layer, so the last mixer block of the first one forms the next layer's joint.
     precision 0, 1 or 2: the precision workload's fused layers in FP32 or on the tensor cores
@@ -586,6 +590,7 @@ def profile_case(sharing=False, depth=1, fusion=True, precision=-1):
     with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
         b.set_sharing(sharing)
         b.set_fusion(fusion)
+        b.set_launch_mode(launch_mode)
         b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
         print(json.dumps({"case": w.name, "c": b.expectation(), "states": b.run_info()["states"]}))
 
@@ -637,7 +642,8 @@ def main():
                          "instead of the damping case")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(bool(args.sharing), args.profile_depth, bool(args.fusion), args.profile_precision)
+        profile_case(bool(args.sharing), args.profile_depth, bool(args.fusion), args.profile_precision,
+                     args.launch_mode)
         return
     if args.workload == "serving":
         serving_arm(args)

@@ -11,14 +11,16 @@ are on the GPU start at once and their kernels overlap on the device.  Device
 memory comes from the PyTorch caching allocator, so finishing a request frees
 nothing device-wide (no cudaFree synchronisation).
 
-Launches (qn_batch_set_launch_mode, shared-prefix requests): with the default
-policy "auto" a request runs device-driven -- persistent sweeps that read the
-live-slot count on the device, so its worker thread never waits on the GPU
-between groups of gates and its launches queue up behind the other requests'
--- and a request that runs in more than one launch batch (chunk) captures its
-first chunk in a CUDA graph, which its later chunks replay.  "host" sizes every
-launch on the host (a read of the live count after each decide), "device" and
-"graph" force modes 1 and 2.
+Launches (qn_batch_set_launch_mode, shared-prefix requests).  A small request
+(up to AUTO_DEVICE_QUBITS qubits) is launch-bound: under the default policy
+"auto" it runs device-driven -- persistent sweeps that read the live-slot count
+on the device, so its worker never waits on the GPU between groups of gates --
+and, when it runs in more than one launch batch (chunk), its first chunk is
+captured in a CUDA graph that the later chunks replay.  A larger request is
+bound by HBM, where host-sized grids sweep a few percent faster than
+persistent ones, so it runs with launches sized on the host (a read of the
+live count after each decide).  "host", "device" and "graph" force modes 0, 1
+and 2 for every request.
 
 All arithmetic runs in libqnoise's kernels; this module only schedules.  A
 request's result does not depend on what runs beside it, nor on the launch
@@ -39,6 +41,9 @@ import numpy as np
 from . import qn
 
 STATE_BUDGET_BYTES = 8 << 30  # statevectors per launch batch (one prefix tree) of one request
+# The largest request the "auto" launch policy runs device-driven (measured on GB300: at
+# 10-12 qubits device-driven runs are 3-10% faster, at 14 qubits even, beyond slower).
+AUTO_DEVICE_QUBITS = 12
 
 
 @dataclasses.dataclass
@@ -97,6 +102,8 @@ def launch_mode_for(req: Request, policy: str = "auto") -> int:
     if policy not in LAUNCH_POLICIES:
         raise ValueError(f"launch policy {policy!r} not in {LAUNCH_POLICIES}")
     if policy == "auto":
+        if req.n > AUTO_DEVICE_QUBITS:
+            return 0
         return 2 if req.chunks() > 1 else 1
     return {"host": 0, "device": 1, "graph": 2}[policy]
 

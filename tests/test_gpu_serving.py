@@ -93,15 +93,15 @@ def test_admission_by_footprint(mods):
 
 
 def test_chunked_requests_replay_their_graphs(mods, monkeypatch):
-    """With launch batches smaller than the requests, the default launch policy captures
-    each damping request's first chunk in a CUDA graph and replays it for the others; the
+    """With launch batches smaller than the requests, the graph launch policy captures each
+    damping request's first chunk in a CUDA graph and replays it for the others; the
     results equal host-sized runs of the same requests, alone."""
     serving = mods
     monkeypatch.setattr(serving, "STATE_BUDGET_BYTES", 2 << 20)  # small launch batches: several chunks
     reqs = [r for r in make_requests(serving, 16, np.random.default_rng(8)) if r.damping > 0 and r.chunks() >= 2]
     assert len(reqs) >= 3
     alone = [serving.run_alone(r, "host") for r in reqs]
-    srv = serving.Server(max_inflight=3)
+    srv = serving.Server(max_inflight=3, launch_policy="graph")
     mixed = [f.result(timeout=300) for f in [srv.submit(r) for r in reqs]]
     srv.close()
     for r, a, m in zip(reqs, alone, mixed):
