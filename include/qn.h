@@ -198,7 +198,12 @@ qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const doubl
 qn_status qn_expectation(const qn_batch *h, double *mean, double *std_err);
 
 /* sigma_approx = sum_t |psi_t|^2 / K (Sec. "Stochastic Noise Implementation")
- * into the caller's host buffer out[len], len == 2^n.  Blocks on the stream. */
+ * into the caller's host buffer out[len], len == 2^n, each psi_t normalised.
+ * The norms are exact to FP32 rounding of the states (a shared-prefix run that
+ * ends on a full mixer block takes them from the joint the block was drawn
+ * from), so the ensemble sum has mass K to that accuracy; it is scaled to unit
+ * mass exactly.  QN_ESTATE if the mass is not positive and finite.  Blocks on
+ * the stream. */
 qn_status qn_probs(const qn_batch *h, double *out, int64_t len);
 
 /* Ensemble gradient d<C>/d gamma_l and d<C>/d beta_l (host outputs, p values

@@ -943,7 +943,7 @@ GroupView group_view(qn_batch *h, int gi, const GateGroup *nz, const SlotView &s
 // The tile map of the sweep that applies group z (the group after it: nz): a mixer block's
 // own map, or for the layer's last phase group (wide_next) the map of the rotations of
 // qubits 0-3 that its sweep also applies.  keep: the circuit's last block, a full block off
-// qubit 0 whose states the sigma pass reads anyway -- its sweep forms only the norms.
+// qubit 0 whose states the sigma pass reads anyway -- no sweep applies it: the sigma pass does.
 MixMap group_mix_map(const qn_batch *h, const GateGroup &z, const GateGroup *nz, bool wide_next) {
     const int n = h->n;
     const int G = (int)h->gates.size();
@@ -977,8 +977,8 @@ MixMap group_mix_map(const qn_batch *h, const GateGroup &z, const GateGroup *nz,
     mm.tanf = std::fabs(z.c) >= std::fabs(z.sn);
     mm.final_norm = z.g0 + z.m == G;  // the circuit's last sweep
     const bool next_phase = nz && nz->kind == 0;
-    // its states are read once more by the sigma pass anyway: form only the norms there and
-    // let that pass apply the block, so no state is written
+    // its states are read once more by the sigma pass anyway: let that pass apply the block,
+    // so no state is written and no sweep runs
     if (mm.final_norm && mm.M == kMixQ && !mm.has0 && mm.nN == 0 && !next_phase) mm.keep = 1;
     return mm;
 }
@@ -1084,22 +1084,25 @@ qn_status enqueue_shared_dev(qn_batch *h, const BatchView &vh, const SlotView &s
                 r.acct.emplace_back(decides, 8.0 * amp);
                 r.launches += 1;
             }
+            const MixMap mm = group_mix_map(h, z, nz, wide_next);
+            const bool last_block = z.kind == 1 && mm.keep;  // applied by the sigma pass, not swept
+            gv.final_norm = last_block ? 1 : 0;
             QN_CUDA(launch_group_decide(v, sv, gv, z.s, kc, h->nz.gamma, st));
             ++decides;
-            MixMap mm = group_mix_map(h, z, nz, wide_next);
-            if (z.kind == 1) {
-                final_norms = final_norms || mm.final_norm;
-                if (mm.keep) {
-                    keep = true;
-                    keep_mm = mm;
-                    keep_tail.grp = gv.grp;
-                    keep_tail.T = gv.T;
-                    keep_tail.parent = gv.parent;
-                    keep_tail.first_new_dev = sv.prev_active;
-                    r.read_tail = keep_read_tail(z, gv, 0);
-                }
+            if (z.kind == 1) final_norms = final_norms || mm.final_norm;
+            if (last_block) {
+                keep = true;
+                keep_mm = mm;
+                keep_tail.grp = gv.grp;
+                keep_tail.T = gv.T;
+                keep_tail.parent = gv.parent;
+                keep_tail.first_new_dev = sv.prev_active;
+                r.read_tail = keep_read_tail(z, gv, 0);
+                r.launches += 2;  // decide, finish
+                g += z.m - 1;
+                continue;
             }
-            const double per_state = (mm.keep && z.kind == 1 ? 8.0 : 16.0) * amp;
+            const double per_state = 16.0 * amp;
             QN_TRY(begin(z.kind == 0 ? 3 : 4, per_state));
             for (int part = 0; part < 2; ++part) {
                 const BatchView vp = part == 0 ? v_new() : v_old();
@@ -1459,6 +1462,12 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
                 h->sweep_bytes += (double)active * 8.0 * amp_count;
                 h->launches += 1;
             }
+            const MixMap mm = group_mix_map(h, z, nz, wide_next);
+            // the circuit's last mixer block, a full block off qubit 0: its states are read once
+            // more by the sigma pass anyway, so no sweep applies it -- that pass does, on the fly,
+            // and the decide forms the final norms from the joint the block was drawn from
+            const bool last_block = z.kind == 1 && mm.keep;
+            gv.final_norm = last_block ? 1 : 0;
             if (e == cudaSuccess) e = launch_group_decide(v, sv, gv, z.s, active, h->nz.gamma, h->stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(active_host, sv.active, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                                       h->stream);
@@ -1466,22 +1475,22 @@ qn_status run_shared(qn_batch *h, int64_t t0, int kc) {
             if (e != cudaSuccess) return fail(QN_ECUDA, "shared-prefix group at gate %d: %s", g, cudaGetErrorString(e));
             const int old_active = active;
             active = *active_host;
-            MixMap mm = group_mix_map(h, z, nz, wide_next);
-            if (z.kind == 1) {
-                final_norms = final_norms || mm.final_norm;
-                if (mm.keep) {
-                    keep = true;
-                    keep_mm = mm;
-                    keep_tail.grp = gv.grp;
-                    keep_tail.T = gv.T;
-                    keep_tail.parent = gv.parent;
-                    keep_tail.first_new = old_active;
-                    read_tail = keep_read_tail(z, gv, old_active);
-                }
+            if (z.kind == 1) final_norms = final_norms || mm.final_norm;
+            if (last_block) {
+                keep = true;
+                keep_mm = mm;
+                keep_tail.grp = gv.grp;
+                keep_tail.T = gv.T;
+                keep_tail.parent = gv.parent;
+                keep_tail.first_new = old_active;
+                read_tail = keep_read_tail(z, gv, old_active);
+                h->launches += 2;  // decide, finish
+                g += z.m - 1;
+                continue;
             }
             // the slots forked here first, reading their parents' states; then
             // the older slots in place (the launch order keeps parents unread-over)
-            const double sweep_b = (double)active * (mm.keep && z.kind == 1 ? 8.0 : 16.0) * amp_count;
+            const double sweep_b = (double)active * 16.0 * amp_count;
             QN_TRY(prof_begin(h, &ep, z.kind == 0 ? 3 : 4, sweep_b));
             for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
                 const int first = part == 0 ? old_active : 0;
@@ -1781,7 +1790,18 @@ qn_status qn_probs(const qn_batch *h, double *out, int64_t len) {
     if (!h->has_run) return fail(QN_ESTATE, "no completed qn_run_qaoa on this handle");
     QN_CUDA(cudaMemcpyAsync(out, h->probs, sizeof(double) * (size_t)len, cudaMemcpyDeviceToHost, h->stream));
     QN_TRY(check_status(h));
-    const double inv = 1.0 / (double)h->K;
+    // sigma_approx = the ensemble's sum over trajectories of phi_t / ||phi_t||^2, scaled to unit
+    // mass: the norms are exact to FP32 rounding (a shared-prefix run that ends on a mixer block
+    // takes them from the block's joint), so the mass is K to that accuracy.  Eight partial sums
+    // in fixed order (independent chains: the loop runs at the memory rate)
+    double part[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t x0 = 0;
+    for (; x0 + 8 <= len; x0 += 8)
+        for (int k = 0; k < 8; ++k) part[k] += out[x0 + k];
+    for (; x0 < len; ++x0) part[0] += out[x0];
+    const double sum = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
+    if (!(sum > 0.0) || !std::isfinite(sum)) return fail(QN_ESTATE, "sigma has mass %g", sum);
+    const double inv = 1.0 / sum;
     for (int64_t x = 0; x < len; ++x) out[x] *= inv;
     return ok();
 }

@@ -130,8 +130,8 @@ struct MixMap {
     int32_t nN;       // qubits of the next block (0: no joint to accumulate)
     int32_t final_norm;  // last sweep of the circuit: also form 1 / ||psi||^2 per state
     int32_t tanf;     // |cos beta| >= |sin beta|: rotations in the tan form, else the cot form
-    int32_t keep = 0;  // with final_norm: form only the norms and leave the states as they were
-                       // (the sigma pass applies the block; full blocks off qubit 0 only)
+    int32_t keep = 0;  // with final_norm: no sweep applies the block -- the sigma pass applies it
+                       // on the fly and the group decide forms the norms (full blocks off qubit 0)
     // 8-qubit blocks (the factor table covers eight qubits, 256 entries):
     //  1  qubits 4-7 of the block over qubits 0-7 whose qubits 0-3 the sweep before rotated
     //     (L bits = qubits 1-3, A = qubits 4-7)
@@ -198,6 +198,10 @@ struct GroupView {
     int32_t *lcount;       // [K] per slot: members of each opened class
     GroupClass *cls;       // [max_slots] the classes of all slots
     int32_t *ncls;         // device counter of cls (reset by the fork-finish kernel)
+    // The circuit's last mixer block, which no sweep applies (the sigma pass applies it to
+    // each state on the fly): the table step also stores 1 / ||psi||^2 of every class's
+    // final state, sum_b |T_b|^2 J_b over the joint J the block was drawn from.
+    int32_t final_norm = 0;
 };
 
 // One QAOA layer for the fused (Pauli-only) sweeps.

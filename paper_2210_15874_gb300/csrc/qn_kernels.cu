@@ -1246,7 +1246,7 @@ __device__ __forceinline__ void rx_pair4_t(float4 &a, float4 &b, float t) {
 //   kMixW2    (MixMap::wide 3) the second half A of an 8-qubit block whose first
 //             half (tile f bits wsh .. wsh+3) kMixW1 rotated: the block's factors
 //             by A << 4 | first half, and a full next block
-enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixKeep = 4, kMixWide = 8, kMixW1 = 16, kMixW2 = 32 };
+enum { kMixAny = 0, kMixMid = 1, kMixHist = 2, kMixWide = 8, kMixW1 = 16, kMixW2 = 32 };
 
 template <bool TANF, int VAR, bool DYN = false>
 __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, GroupView gv, MixMap mm) {
@@ -1267,7 +1267,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
     const int M = kFix ? kMixQ : mm.M;
     constexpr bool kW8 = VAR == kMixWide || VAR == kMixW1 || VAR == kMixW2;  // 256-entry factor table
     const int nN = kFix ? ((VAR == kMixMid || kW8) ? kMixQ : 0) : mm.nN;
-    const bool final_norm = kFix ? VAR == kMixKeep : mm.final_norm != 0;
+    const bool final_norm = kFix ? false : mm.final_norm != 0;
     const float c = gv.grp->c, sn = gv.grp->sn;
     const float rt = TANF ? sn / c : c / sn, rsc = TANF ? c : sn;  // rotation = rsc * (tangent form)
     float scM = 1.0f;  // rsc^M: the block's rotations, folded into its factors
@@ -1428,17 +1428,12 @@ __global__ void __launch_bounds__(kMixThreads, 3) k_mix_sweep(BatchView v, Group
             if (VAR == kMixW2) {  // the block's first half on the tile's f bits, its second j
                 f0 = f1 = Df[(j << 4) | (int)((fb >> mm.wsh) & 15u)];
             }
-            if (VAR == kMixKeep) {  // nothing stored: |f x|^2 as the sigma pass forms it
-                df_add(nh, nl, prob_of(f0, x[j].x, x[j].y));
-                df_add(nh, nl, prob_of(f1, x[j].z, x[j].w));
-                continue;
-            }
             x[j].x *= f0;
             x[j].y *= f0;
             x[j].z *= f1;
             x[j].w *= f1;
             if (has0) buf[idx1(j)] = x[j];  // stored from the tile in copy order below
-            else if (VAR != kMixKeep) p4[fb | aoff(j)] = x[j];
+            else p4[fb | aoff(j)] = x[j];
             if (nN > 0 && !has0) buf[idx1(j)] = x[j];
             if (nx) {
                 if (j == 0) gn.base = nb0 | ((sub & 1) ? nb1 : 0) | ((sub & 2) ? nb2 : 0);
@@ -2160,6 +2155,15 @@ __device__ __forceinline__ void gd_table(const BatchView &v, const SlotView &sv,
     N = warp_sumf(N);
     const float sc = 1.0f / sqrtf(N);
     if (lane == 0 && !(N > 0.0f && isfinite(sc))) atomicOr(v.status, 1);
+    if (gv.final_norm) {
+        // the class's final state T_b phi_b has norm sc^2 sum_b w_b (w_b = J_b |a_b|^2)
+        double nd = 0.0;
+#pragma unroll
+        for (int r = 0; r < kPatR; ++r) nd += (double)w[r];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nd += __shfl_xor_sync(0xffffffffu, nd, off);
+        if (lane == 0) v.inv_norm[gc.target] = 1.0 / (nd * (double)sc * (double)sc);
+    }
 #pragma unroll
     for (int r = 0; r < kPatR; ++r) {
         const int b = lane + 32 * r;
@@ -2527,14 +2531,12 @@ __global__ void k_probs_combine(double *probs, const double *spart, int parts, i
     }
 }
 
-// The sigma pass when the circuit ends on a full mixer block off qubit 0 whose
-// sweep (kMixKeep) formed only the final norms and left every state as it was
-// before the block.  The pass applies the block to each state on the fly --
-// the same rotations in the same order as k_mix_sweep, then |f x|^2 with the
-// drawn factor f formed as that sweep forms it -- so each probability is
-// bit-identical to the ones the norms summed, and the final states are never
-// written.  A slot forked at the block
-// reads its parent's state.  Grid (half tiles of the block's map, row blocks) x
+// The sigma pass when the circuit ends on a full mixer block off qubit 0, which
+// no sweep applies: every state is as it was before the block, and the group
+// decide formed each final state's norm from the joint the block was drawn
+// from.  The pass applies the block to each state on the fly -- the rotations of
+// k_mix_sweep, then |f x|^2 with the drawn factor f -- so the final states are
+// never written.  A slot forked at the block reads its parent's state.  Grid (half tiles of the block's map, row blocks) x
 // kMixThreads: two lanes (lane bit 4 = the block's fourth qubit) share a fiber
 // of 16 float4 along the block's qubits, 8 each (the first three qubits on the
 // register index), at true bits fixed over the states.  Each float4 is read from
@@ -2661,7 +2663,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
             float cp = 0.0f;
 #pragma unroll
             for (int j = 0; j < kR; ++j) {
-                const float f = c_df[ci][j ^ fd];  // |f x|^2 as the kMixKeep sweep forms it
+                const float f = c_df[ci][j ^ fd];  // |f x|^2 with the drawn factor f
                 const float pa = prob_of(f, x[j].x, x[j].y), pb = prob_of(f, x[j].z, x[j].w);
                 const float p0 = (Ff & 1u) ? pb : pa, p1 = (Ff & 1u) ? pa : pb;  // true qubit 0
                 df_add_prod(ah[2 * j], al[2 * j], p0, ih, il);
@@ -3605,9 +3607,9 @@ static cudaError_t launch_mix_sweep_attrs() {
     static const cudaError_t attr = [] {
 #define QN_KS(D)                                                                                          \
     (const void *)k_mix_sweep<true, kMixAny, D>, (const void *)k_mix_sweep<true, kMixMid, D>,             \
-        (const void *)k_mix_sweep<true, kMixHist, D>, (const void *)k_mix_sweep<true, kMixKeep, D>,       \
+        (const void *)k_mix_sweep<true, kMixHist, D>,                                                     \
         (const void *)k_mix_sweep<false, kMixAny, D>, (const void *)k_mix_sweep<false, kMixMid, D>,       \
-        (const void *)k_mix_sweep<false, kMixHist, D>, (const void *)k_mix_sweep<false, kMixKeep, D>,     \
+        (const void *)k_mix_sweep<false, kMixHist, D>,                                                    \
         (const void *)k_mix_sweep<true, kMixWide, D>, (const void *)k_mix_sweep<false, kMixWide, D>,      \
         (const void *)k_mix_sweep<true, kMixW1, D>, (const void *)k_mix_sweep<false, kMixW1, D>,          \
         (const void *)k_mix_sweep<true, kMixW2, D>, (const void *)k_mix_sweep<false, kMixW2, D>,          \
@@ -3670,12 +3672,10 @@ cudaError_t launch_mix_sweep(const BatchView &vh, const GroupView &gv, const Mix
         const bool next_full = mm.nN == kMixQ && !gv.next && !mm.final_norm;
         if (next_full && !mm.has0) var = kMixMid;
         else if (!mm.has0 && mm.nN == 0 && gv.next && !mm.final_norm) var = kMixHist;
-        else if (!mm.has0 && mm.nN == 0 && !gv.next && mm.final_norm && mm.keep) var = kMixKeep;
     }
     switch (var) {
     case kMixMid: return mm.tanf ? QN_MIX(true, kMixMid) : QN_MIX(false, kMixMid);
     case kMixHist: return mm.tanf ? QN_MIX(true, kMixHist) : QN_MIX(false, kMixHist);
-    case kMixKeep: return mm.tanf ? QN_MIX(true, kMixKeep) : QN_MIX(false, kMixKeep);
     default: return mm.tanf ? QN_MIX(true, kMixAny) : QN_MIX(false, kMixAny);
     }
 #undef QN_MIX
