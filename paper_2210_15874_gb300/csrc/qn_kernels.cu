@@ -2558,7 +2558,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
     __shared__ float cw[kAccChunk][kWarps];
     __shared__ int c_src[kAccChunk];
     __shared__ uint32_t c_Ff[kAccChunk];
-    __shared__ float c_ih[kAccChunk], c_il[kAccChunk];
+    __shared__ float c_w[kAccChunk];
     __shared__ float c_df[kAccChunk][kMixE];
     __shared__ float s_cut[kE][kMixThreads];
     __shared__ double s_acc[kE][kMixThreads];
@@ -2616,10 +2616,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
             const TrajState st = v.st[sl];
             c_src[threadIdx.x] = sl >= first_new ? tl.parent[sl] : sl;
             c_Ff[threadIdx.x] = v.frame_x[(size_t)sl * (v.G + 1) + v.G] ^ st.J ^ st.pend;
-            const double inv = v.inv_norm[sl] * (a.weights ? a.weights[sl] : 1.0);
-            const float ih = (float)inv;
-            c_ih[threadIdx.x] = ih;
-            c_il[threadIdx.x] = (float)(inv - (double)ih);
+            c_w[threadIdx.x] = (float)(v.inv_norm[sl] * (a.weights ? a.weights[sl] : 1.0));
         }
         for (int i = threadIdx.x; i < cn * kMixE; i += kMixThreads) {
             const int tt = t0c + i / kMixE;
@@ -2627,9 +2624,11 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
             c_df[i / kMixE][i % kMixE] = tl.T[(size_t)sl * kGroupBins + i % kMixE].x * scM;
         }
         __syncthreads();
-        float ah[kE], al[kE];  // sigma terms of this chunk (double-float)
+        // sigma terms of this chunk: FP32 sums of at most kAccChunk weighted probabilities,
+        // added to the FP64 sums once per chunk (relative error below 2^-24 kAccChunk)
+        float ah[kE];
 #pragma unroll
-        for (int i = 0; i < kE; ++i) ah[i] = al[i] = 0.0f;
+        for (int i = 0; i < kE; ++i) ah[i] = 0.0f;
         // element j's stored index: (base | aoff(j)) ^ Fq = (base ^ Fq) ^ aoff(j); the next
         // state's float4 are loaded while the current one is computed
         auto load_state = [&](int ci, float4 (&dst)[kR]) {
@@ -2658,7 +2657,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
             }
 #pragma unroll
             for (int j = 0; j < kR; ++j) rx_lanes_t<TANF>(x[j], 16, rt);  // the fourth qubit
-            const float ih = c_ih[ci], il = c_il[ci];
+            const float wc = c_w[ci];  // the state's weight / ||psi||^2
             const int fd = fa ^ (hi << 3);
             float cp = 0.0f;
 #pragma unroll
@@ -2666,8 +2665,8 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
                 const float f = c_df[ci][j ^ fd];  // |f x|^2 with the drawn factor f
                 const float pa = prob_of(f, x[j].x, x[j].y), pb = prob_of(f, x[j].z, x[j].w);
                 const float p0 = (Ff & 1u) ? pb : pa, p1 = (Ff & 1u) ? pa : pb;  // true qubit 0
-                df_add_prod(ah[2 * j], al[2 * j], p0, ih, il);
-                df_add_prod(ah[2 * j + 1], al[2 * j + 1], p1, ih, il);
+                ah[2 * j] = __fmaf_rn(p0, wc, ah[2 * j]);
+                ah[2 * j + 1] = __fmaf_rn(p1, wc, ah[2 * j + 1]);
                 cp += p0 * cut[2 * j];
                 cp += p1 * cut[2 * j + 1];
             }
@@ -2676,7 +2675,7 @@ __global__ void __launch_bounds__(kMixThreads, 4) k_probs_mix(BatchView v, Accum
             if (lane == 0) cw[ci][warp] = cp;
         }
 #pragma unroll
-        for (int i = 0; i < kE; ++i) s_acc[i][threadIdx.x] += (double)ah[i] + (double)al[i];
+        for (int i = 0; i < kE; ++i) s_acc[i][threadIdx.x] += (double)ah[i];
         __syncthreads();
         if ((int)threadIdx.x < cn) {
             double sum = 0.0;
