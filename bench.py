@@ -346,7 +346,8 @@ def gradient_leg(qn, args, stream, local):
             "ms_per_step": ms / steps, "c_mean": mean, "c_stderr": se,
             "dC_dgamma": [float(x) for x in dg], "dC_dbeta": [float(x) for x in db], "clocks": clocks.summary(),
             "config": config_of(w, {"steps": steps, "warmup": warmup,
-                                    "step": "qn_run_qaoa (fused layers) + qn_grad (adjoint, one reverse sweep per gate)"})}
+                                    "step": "qn_run_qaoa (fused layers) + qn_grad (fused adjoint: a layer's mixer "
+                                            "reversed in windows of 2-4 qubits, its cost diagonal in one sweep)"})}
 
 
 def gpu_arm(args):

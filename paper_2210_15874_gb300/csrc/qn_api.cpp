@@ -1911,6 +1911,25 @@ namespace {
 
 // Parameter index of gate g (>= n): 2l for the phase gates of layer l, 2l+1 for
 // its mixer gates.
+// Windows (first qubit, qubits) of the fused adjoint's mixer sweeps: qubits 0-3 (qubit 0
+// in the float4, three on the register index), then the others in windows of two or
+// three (a single one only when one qubit is left after the first window).
+std::vector<std::pair<int, int>> adj_windows(int n) {
+    std::vector<std::pair<int, int>> w;
+    const int first = std::min(4, n);
+    w.emplace_back(0, first);
+    const int rest = n - first;
+    if (rest <= 0) return w;
+    const int count = (rest + 2) / 3;
+    int q_lo = first;
+    for (int i = 0; i < count; ++i) {
+        const int m = rest / count + (i < rest % count ? 1 : 0);
+        w.emplace_back(q_lo, m);
+        q_lo += m;
+    }
+    return w;
+}
+
 int param_of(const qn_batch *h, int g) {
     const int E = (int)h->edges.size() / 2;
     const int r = g - h->n;
@@ -1946,8 +1965,19 @@ qn_status run_grad(qn_batch *h, int64_t t0, int64_t count) {
         a.edges = h->dedges;
         QN_CUDA(launch_adj_init(v, h->lambda, a, h->stream));
         double *gr = h->grad + (size_t)(t0 + c0) * np;
-        for (int g = G - 1; g >= n; --g)
-            QN_CUDA(launch_adj_sweep(v, h->lambda, g, h->dgates_host[g], gr, param_of(h, g), np, h->stream));
+        if (use_fusion(h)) {
+            // the fused forward left every layer's parameters: the reverse takes a layer's
+            // mixer in windows of a few qubits and its cost diagonal in one sweep
+            for (int l = h->p - 1; l >= 0; --l) {
+                const LayerView L = layer_view(h, l);
+                for (const auto &wd : adj_windows(n))
+                    QN_CUDA(launch_adj_mixer(v, h->lambda, L, wd.first, wd.second, gr, 2 * l + 1, np, h->stream));
+                QN_CUDA(launch_adj_phase(v, h->lambda, L, gr, 2 * l, np, h->stream));
+            }
+        } else {
+            for (int g = G - 1; g >= n; --g)
+                QN_CUDA(launch_adj_sweep(v, h->lambda, g, h->dgates_host[g], gr, param_of(h, g), np, h->stream));
+        }
     }
     h->launches = saved_launches;
     QN_TRY(check_status(h));

@@ -398,6 +398,15 @@ cudaError_t launch_group_apply(const BatchView &v, const SlotView &sv, const Gro
 // Adjoint gradient: lambda = C psi_T, then one reverse sweep per gate g >= n
 // adding d<C>_t / d theta_param into grad[t * nparam + param] (FP64).
 cudaError_t launch_adj_init(const BatchView &v, float2 *lam, const AccumView &a, cudaStream_t s);
+// Fused adjoint (Pauli-only noise, after a fused forward run that left the layer
+// parameters of every layer): the reverse of the mixer rotations of qubits
+// [q_lo, q_lo + m) of layer L on psi and lambda (m <= 4 with qubit 0, else <= 3),
+// adding their terms to grad[t][param] (d<C>_t / d beta); and the reverse of layer
+// L's cost diagonal, adding its term to grad[t][param] (d<C>_t / d gamma).
+cudaError_t launch_adj_mixer(const BatchView &v, float2 *lam, const LayerView &L, int q_lo, int m, double *grad,
+                             int param, int nparam, cudaStream_t s);
+cudaError_t launch_adj_phase(const BatchView &v, float2 *lam, const LayerView &L, double *grad, int param, int nparam,
+                             cudaStream_t s);
 cudaError_t launch_adj_sweep(const BatchView &v, float2 *lam, int g, const DevGate &gate, double *grad, int param,
                              int nparam, cudaStream_t s);
 int64_t accumulate_xblocks(int n);

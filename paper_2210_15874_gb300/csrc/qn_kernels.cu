@@ -2742,6 +2742,46 @@ __global__ void __launch_bounds__(kThreads) k_adj_init(BatchView v, float2 *lam,
     }
 }
 
+// The end of an adjoint sweep over trajectory t, in block blk of its nblk blocks
+// (kThreads threads, every thread with its FP32 part of the inner product): the
+// block's sum goes to partials[t][blk] in FP64, and the trajectory's last block
+// to finish adds 2 x their sum / ||psi||^2 to grad[t][param], in block order.
+__device__ void adj_finish(const BatchView &v, int t, int blk, int nblk, float acc, double *grad, int param,
+                           int nparam) {
+    __shared__ double redd[kThreads / 32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double d = (double)acc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (lane == 0) redd[warp] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+        v.partials[((size_t)t * v.tiles + blk) * 4] = sum;
+        __threadfence();
+        const unsigned prev = atomicAdd(&v.counters[t], 1u);
+        last = prev == (unsigned)(nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s0 = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += kThreads) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    __syncthreads();
+    if (lane == 0) redd[warp] = s0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+        grad[(size_t)t * nparam + param] += 2.0 * sum * v.inv_norm[t];
+        v.counters[t] = 0;
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) k_adj_sweep(BatchView v, float2 *lam, int g, DevGate gt, double *grad,
                                                          int param, int nparam) {
@@ -2828,39 +2868,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_sweep(BatchView v, float2 *lam
             }
         }
     }
-    // block reduction -> per-tile partial; last block adds 2 * sum to grad[t][param]
-    __shared__ double redd[kThreads / 32];
-    __shared__ int last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double d = (double)acc;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-    if (lane == 0) redd[warp] = d;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
-        v.partials[((size_t)t * v.tiles + tile) * 4] = sum;
-        __threadfence();
-        const unsigned prev = atomicAdd(&v.counters[t], 1u);
-        last = prev == (unsigned)(v.tiles - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double s0 = 0.0;
-    for (int i = threadIdx.x; i < v.tiles; i += kThreads) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-    __syncthreads();
-    if (lane == 0) redd[warp] = s0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sum = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
-        grad[(size_t)t * nparam + param] += 2.0 * sum * v.inv_norm[t];
-        v.counters[t] = 0;
-    }
+    adj_finish(v, t, tile, v.tiles, acc, grad, param, nparam);
 }
 
 // ---------------------------------------------------------------------------
@@ -3124,6 +3132,153 @@ __global__ void __launch_bounds__(kThreads) k_phase_sweep(BatchView v, LayerView
         cmul_inplace(val.z, val.w, layer_phase(L, y | 1u, sv, zm, zc));
         p4[f] = val;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Fused adjoint (Pauli-only noise), the reverse of the fused layers on psi and
+// lambda together.  In the stored basis a layer is the cost diagonal D(y) =
+// (-1)^{popc(y & zm) + zc} e^{-i gamma k(y)} followed by the mixer, a tensor
+// product of M_q = S_q exp(-i beta X_q) over the qubits (S_q the row signs of the
+// qubit's Pauli's Z part on its true bit).  So, at the point after the layer,
+//   d<C>_t/d beta  += sum_q 2 sigma_q Im <lambda|X_q|psi>   (S X S = sigma X,
+//                     sigma_q = -1 when the Pauli has a Z part),
+// and, at the point after the cost layer (the mixer undone),
+//   d<C>_t/d gamma += 2 Im <lambda|k|psi>                   (dD/dgamma = -i k D).
+// The qubits' terms may be taken window by window: the rotations of the other
+// windows commute with X_q.  A window sweep takes the terms of its qubits and then
+// applies M_q^dagger = exp(+i beta X_q) S_q to both vectors; the phase sweep takes
+// the k term and applies D^dagger.  32 B per amplitude per sweep.
+// ---------------------------------------------------------------------------
+
+// One qubit of a window: the pair (a0, a1) of psi and (m0, m1) of lambda at stored
+// bits 0 and 1 of the qubit.  Adds sigma Im(conj(m0) a1 + conj(m1) a0) to acc, then
+// applies S (s0, s1) and exp(+i beta X) = [[c, i s], [i s, c]] to both pairs.
+__device__ __forceinline__ void adj_pair(float &a0r, float &a0i, float &a1r, float &a1i, float &m0r, float &m0i,
+                                         float &m1r, float &m1i, float sg, float s0, float s1, float cb, float sb,
+                                         float &acc) {
+    acc += sg * ((m0r * a1i - m0i * a1r) + (m1r * a0i - m1i * a0r));
+    a0r *= s0;
+    a0i *= s0;
+    a1r *= s1;
+    a1i *= s1;
+    m0r *= s0;
+    m0i *= s0;
+    m1r *= s1;
+    m1i *= s1;
+    float n0r = cb * a0r - sb * a1i, n0i = cb * a0i + sb * a1r;
+    float n1r = cb * a1r - sb * a0i, n1i = cb * a1i + sb * a0r;
+    a0r = n0r;
+    a0i = n0i;
+    a1r = n1r;
+    a1i = n1i;
+    n0r = cb * m0r - sb * m1i;
+    n0i = cb * m0i + sb * m1r;
+    n1r = cb * m1r - sb * m0i;
+    n1i = cb * m1i + sb * m0r;
+    m0r = n0r;
+    m0i = n0i;
+    m1r = n1r;
+    m1i = n1i;
+}
+
+// Reverse of one mixer window of layer L: qubits q_lo .. q_lo + HAS0 + R - 1.  With
+// HAS0 (q_lo == 0) qubit 0 is the float4 half and qubits 1 .. R the float4-index bits
+// 0 .. R-1; otherwise qubits q_lo .. q_lo + R - 1 are the float4-index bits q_lo - 1 ..
+// A thread holds one fibre of 2^R float4 of each vector (the window's bits varied,
+// the others fixed); consecutive threads take consecutive values of the bits below
+// the window.  Grid (fibres / kThreads, trajectories).
+template <int R, bool HAS0>
+__global__ void __launch_bounds__(kThreads) k_adj_mixer(BatchView v, float2 *lam, LayerView L, int q_lo, double *grad,
+                                                         int param, int nparam) {
+    constexpr int E = 1 << R;
+    const int t = blockIdx.y;
+    const int64_t nf = (int64_t)1 << (v.n - 1 > 0 ? v.n - 1 : 0);
+    const int wlo = HAS0 ? 0 : q_lo - 1;  // float4-index bit of the window's first register qubit
+    const int q1 = HAS0 ? 1 : q_lo;       // qubit on register bit 0
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    float acc = 0.0f;
+    if (r < (nf >> R)) {
+        const int64_t lowm = ((int64_t)1 << wlo) - 1;
+        const int64_t base = ((r & ~lowm) << R) | (r & lowm);
+        float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << v.n));
+        float4 *l4 = reinterpret_cast<float4 *>(lam + ((size_t)t << v.n));
+        float4 a[E], m[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            a[j] = p4[base | ((int64_t)j << wlo)];
+            m[j] = l4[base | ((int64_t)j << wlo)];
+        }
+        const uint32_t mz = L.mz[t], mf = L.mf[t];
+        const float cb = L.cb, sb = L.sb;
+        if (HAS0) {
+            const uint32_t z = mz & 1u, fq = mf & 1u;
+            const float sg = z ? -1.0f : 1.0f, s0 = (z && fq) ? -1.0f : 1.0f, s1 = (z && !fq) ? -1.0f : 1.0f;
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                adj_pair(a[j].x, a[j].y, a[j].z, a[j].w, m[j].x, m[j].y, m[j].z, m[j].w, sg, s0, s1, cb, sb, acc);
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int q = q1 + i;
+            const uint32_t z = (mz >> q) & 1u, fq = (mf >> q) & 1u;
+            const float sg = z ? -1.0f : 1.0f, s0 = (z && fq) ? -1.0f : 1.0f, s1 = (z && !fq) ? -1.0f : 1.0f;
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                if (j & (1 << i)) continue;
+                const int k = j | (1 << i);
+                adj_pair(a[j].x, a[j].y, a[k].x, a[k].y, m[j].x, m[j].y, m[k].x, m[k].y, sg, s0, s1, cb, sb, acc);
+                adj_pair(a[j].z, a[j].w, a[k].z, a[k].w, m[j].z, m[j].w, m[k].z, m[k].w, sg, s0, s1, cb, sb, acc);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            p4[base | ((int64_t)j << wlo)] = a[j];
+            l4[base | ((int64_t)j << wlo)] = m[j];
+        }
+    }
+    adj_finish(v, t, blockIdx.x, gridDim.x, acc, grad, param, nparam);
+}
+
+// Reverse of the cost layer L: adds 2 Im <lambda|k|psi> to d<C>_t/d gamma (via
+// adj_finish), then applies D^dagger = (-1)^{popc(y & zm) + zc} e^{+i gamma k(y)} to
+// both vectors.  One tile of kTileF4 float4 per block, grid (tiles, trajectories).
+__global__ void __launch_bounds__(kThreads) k_adj_phase(BatchView v, float2 *lam, LayerView L, double *grad, int param,
+                                                         int nparam) {
+    const int t = blockIdx.y, tile = blockIdx.x;
+    const int64_t nf = (int64_t)1 << (v.n - 1 > 0 ? v.n - 1 : 0);
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << v.n));
+    float4 *l4 = reinterpret_cast<float4 *>(lam + ((size_t)t << v.n));
+    const uint64_t sv = L.s[t];
+    const uint32_t zm = L.zm[t], zc = L.zc[t];
+    const uint64_t ev1 = ev_of(L, 1u);
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kF4PerThread; ++k) {
+        const int64_t f = (int64_t)tile * kTileF4 + threadIdx.x + k * kThreads;
+        if (f >= nf) continue;
+        float4 a = p4[f], m = l4[f];
+        const uint32_t y = (uint32_t)(2 * f);
+        const uint64_t e0 = ev_of(L, y);
+        float av[4] = {a.x, a.y, a.z, a.w}, mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int kk = __popcll((e ? e0 ^ ev1 : e0) ^ sv);
+            const float2 ph = __ldg(L.phase + kk);  // e^{-i gamma k}
+            const float sg = ((__popc((y | (uint32_t)e) & zm) ^ zc) & 1u) ? -1.0f : 1.0f;
+            float &ar = av[2 * e], &ai = av[2 * e + 1], &mr = mv[2 * e], &mi = mv[2 * e + 1];
+            acc += (float)kk * (mr * ai - mi * ar);
+            const float cr = ph.x * sg, ci = -ph.y * sg;  // conj(D(y))
+            const float nar = ar * cr - ai * ci, nai = ar * ci + ai * cr;
+            const float nmr = mr * cr - mi * ci, nmi = mr * ci + mi * cr;
+            ar = nar;
+            ai = nai;
+            mr = nmr;
+            mi = nmi;
+        }
+        p4[f] = make_float4(av[0], av[1], av[2], av[3]);
+        l4[f] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+    }
+    adj_finish(v, t, tile, v.tiles, acc, grad, param, nparam);
 }
 
 // Readout of psi_x = i^k * D * phi_{x xor F} in the true basis (debug path).
@@ -3466,6 +3621,40 @@ cudaError_t launch_adj_sweep(const BatchView &v, float2 *lam, int g, const DevGa
     const dim3 grid((unsigned)v.tiles, (unsigned)v.b);
     if (gate.kind == kGateZZ) k_adj_sweep<kGateZZ><<<grid, kThreads, 0, s>>>(v, lam, g, gate, grad, param, nparam);
     else k_adj_sweep<kGateRX><<<grid, kThreads, 0, s>>>(v, lam, g, gate, grad, param, nparam);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_mixer(const BatchView &v, float2 *lam, const LayerView &L, int q_lo, int m, double *grad,
+                             int param, int nparam, cudaStream_t s) {
+    const bool has0 = q_lo == 0;
+    const int R = has0 ? m - 1 : m;
+    if (R < 0 || R > 3 || (!has0 && R == 0) || q_lo + m > v.n) return cudaErrorInvalidValue;
+    const int64_t nf = (int64_t)1 << (v.n - 1 > 0 ? v.n - 1 : 0);
+    const int64_t fibres = nf >> R;
+    const dim3 grid((unsigned)((fibres + kThreads - 1) / kThreads), (unsigned)v.b);
+    if ((int64_t)grid.x > v.tiles) return cudaErrorInvalidValue;  // partials hold v.tiles per trajectory
+#define QN_ADJM(RR, H) k_adj_mixer<RR, H><<<grid, kThreads, 0, s>>>(v, lam, L, q_lo, grad, param, nparam)
+    if (has0) {
+        switch (R) {
+        case 0: QN_ADJM(0, true); break;
+        case 1: QN_ADJM(1, true); break;
+        case 2: QN_ADJM(2, true); break;
+        default: QN_ADJM(3, true); break;
+        }
+    } else {
+        switch (R) {
+        case 1: QN_ADJM(1, false); break;
+        case 2: QN_ADJM(2, false); break;
+        default: QN_ADJM(3, false); break;
+        }
+    }
+#undef QN_ADJM
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_phase(const BatchView &v, float2 *lam, const LayerView &L, double *grad, int param, int nparam,
+                             cudaStream_t s) {
+    k_adj_phase<<<dim3((unsigned)v.tiles, (unsigned)v.b), kThreads, 0, s>>>(v, lam, L, grad, param, nparam);
     return cudaGetLastError();
 }
 

@@ -145,3 +145,30 @@ def test_autograd_two_forwards_on_one_batch(qn):
     np.testing.assert_allclose(b1.grad.numpy(), ref[0][1], rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(g2.grad.numpy(), 3.0 * ref[1][0], rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(b2.grad.numpy(), 3.0 * ref[1][1], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,p,d", [(2, 2, 1), (3, 2, 2), (5, 2, 4), (8, 3, 3), (9, 2, 4), (13, 2, 4), (16, 2, 3)])
+def test_fused_adjoint_matches_per_gate_adjoint_and_oracle(qn, n, p, d):
+    """The fused adjoint (the reverse of a layer's mixer in windows of two to four qubits,
+    its cost diagonal in one sweep: what the default fused mode runs) against the one
+    reverse sweep per gate (fusion off) on the same trajectories, and against CRN finite
+    differences of the oracle.  The windows cover every width: the qubit-0 window alone
+    (n = 2, 3), a single-qubit window (n = 5), windows of two and three, n = 16."""
+    if n == 2:  # the one-edge graph
+        w = W.Workload("fadj_n2", 2, np.array([[0, 1]], np.int32), p, *W.angles(p, 4462), 1e-2, 3e-2, 0.0, 32, 32,
+                       W.PHILOX_SEED_BASE + 42)
+    else:
+        w = W.qaoa_workload(f"fadj_n{n}", n, p, index=40 + n, trajectories=32, batch=32, p1=1e-2, p2=3e-2, d=d)
+    res = {}
+    for fusion in (True, False):
+        with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+            b.set_fusion(fusion)
+            b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+            res[fusion] = b.grad_traj(0, w.trajectories)
+    tol = 8 * U32 * w.gate_count * len(w.edges) + 1e-4
+    for k in range(2):
+        assert np.abs(res[True][k] - res[False][k]).max() < tol, (k, np.abs(res[True][k] - res[False][k]).max())
+    fg, fb = fd_traj(w, 0, 8)
+    assert np.abs(res[True][0][:8] - fg).max() < tol
+    assert np.abs(res[True][1][:8] - fb).max() < tol
+    assert np.abs(fg).max() + np.abs(fb).max() > 0.05  # non-trivial gradients
