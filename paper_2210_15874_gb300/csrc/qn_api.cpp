@@ -145,6 +145,9 @@ struct qn_batch {
 
     // problem of the last run
     bool has_run = false;
+    // the statevector buffer holds the final states of the whole ensemble (one launch batch,
+    // one state per trajectory) as the last run left them: the adjoint can start from them
+    bool final_states = false;
     std::vector<int32_t> edges;
     int32_t p = 0;
     std::vector<double> gammas, betas;
@@ -1744,6 +1747,7 @@ qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const doubl
     B = std::min<int64_t>(std::min<int64_t>(B, h->K), 65535);
     h->B = B;
     h->has_run = false;
+    h->final_states = false;
     QN_TRY(ensure_buffers(h, B, (int32_t)G, graph->num_edges));
     QN_CUDA(cudaMemcpyAsync(h->dgates, h->dgates_host.data(), h->dgates_host.size() * sizeof(DevGate),
                             cudaMemcpyHostToDevice, h->stream));
@@ -1764,6 +1768,7 @@ qn_status qn_run_qaoa(qn_batch *h, const qn_graph *graph, int32_t p, const doubl
         else QN_TRY(run_batch(h, t0, b, true));
     }
     h->has_run = true;
+    h->final_states = !(h->sharing && !use_fusion(h)) && B >= h->K;
     return ok();
 }
 
@@ -1819,6 +1824,7 @@ qn_status qn_traj_debug(qn_batch *h, int64_t t0, int64_t count, float *amps, uin
         QN_TRY(alloc_t(h, &h->readout, (size_t)h->cap_B << n));
     }
     h->sh_valid = false;  // the re-simulation reuses the buffers a shared-prefix run left
+    h->final_states = false;
     const int64_t saved_launches = h->launches;
     for (int64_t c0 = 0; c0 < count; c0 += h->cap_B) {
         const int b = (int)std::min<int64_t>(h->cap_B, count - c0);
@@ -1956,9 +1962,12 @@ qn_status run_grad(qn_batch *h, int64_t t0, int64_t count) {
     QN_CUDA(cudaMemsetAsync(h->grad + (size_t)t0 * np, 0, (size_t)count * np * sizeof(double), h->stream));
     h->sh_valid = false;  // the re-simulation reuses the buffers a shared-prefix run left
     const int64_t saved_launches = h->launches;
+    // the whole ensemble in one launch batch whose final states the run left: no re-simulation
+    const bool reuse = h->final_states && t0 == 0 && count == h->K;
+    h->final_states = false;  // the reverse sweeps take the states back to the start
     for (int64_t c0 = 0; c0 < count; c0 += h->cap_B) {
         const int b = (int)std::min<int64_t>(h->cap_B, count - c0);
-        QN_TRY(run_batch(h, t0 + c0, b, false));
+        if (!reuse) QN_TRY(run_batch(h, t0 + c0, b, false));
         BatchView v = view_for(h, h->offset + t0 + c0, b);
         AccumView a = {};
         a.num_edges = (int32_t)h->edges_host.size();

@@ -122,5 +122,6 @@ def precision_n30() -> Workload:
 
 
 def gradient_n16() -> Workload:
-    """QAOA p=6 on a seeded 3-regular n=16 graph, depolarizing only, K=2048."""
-    return qaoa_workload("qaoa_n16_p6_depol_K2048", 16, 6, index=4, trajectories=2048, batch=256)
+    """QAOA p=6 on a seeded 3-regular n=16 graph, depolarizing only, K=2048 in one launch
+    batch (2048 states of 512 KiB, 1 GiB)."""
+    return qaoa_workload("qaoa_n16_p6_depol_K2048", 16, 6, index=4, trajectories=2048, batch=2048)
