@@ -314,6 +314,28 @@ def precision_leg(qn, args, stream, local, roof_of):
     return legs
 
 
+def hbm_peak_of():
+    """The measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, GB/s), else the fallback."""
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(pk_path)) if os.path.exists(pk_path) else {}
+    return float(peaks.get("hbm_gbs", 6800.0)), ("measured" if "hbm_gbs" in peaks else "fallback")
+
+
+def fused_window_count(n: int) -> int:
+    """Sweeps per layer of the fused forward layers (the library's fused_windows: qubits 0-7,
+    then windows of at most 7; five per window below 10 qubits)."""
+    if n < 10:
+        return -(-n // 5)
+    return 1 + -(-(n - 8) // 7)
+
+
+def adjoint_window_count(n: int) -> int:
+    """Mixer sweeps per layer of the fused adjoint (the library's adj_windows: qubits 0-3,
+    then windows of two or three)."""
+    rest = n - min(4, n)
+    return 1 + (-(-rest // 3) if rest > 0 else 0)
+
+
 def gradient_leg(qn, args, stream, local):
     """The gradient workload (n=16, p=6, depolarizing only, K=2048): one step is the noisy
     forward run of the whole ensemble plus the adjoint gradient of <C> in all 12 angles
@@ -342,8 +364,19 @@ def gradient_leg(qn, args, stream, local):
     ms = ev0.elapsed_time(ev1)
     mean, se = b.expectation()
     b.close()
+    # bytes of one step: the fused forward sweeps (16 B per amplitude), the sigma pass (8 B), the
+    # adjoint's start (read psi, write lambda: 16 B) and its sweeps (psi and lambda: 32 B), each
+    # layer's mixer windows plus its cost diagonal
+    amps = float(w.trajectories) * (1 << w.n)
+    step_bytes = amps * (16.0 * fused_window_count(w.n) * w.p + 8.0 + 16.0 +
+                         32.0 * (adjoint_window_count(w.n) + 1) * w.p)
+    peak, peak_src = hbm_peak_of()
+    achieved = step_bytes / (ms / steps / 1e3) / 1e9
     return {"value": w.trajectories * steps / (ms / 1e3), "unit": "trajectories/s (forward + adjoint gradient)",
             "ms_per_step": ms / steps, "c_mean": mean, "c_stderr": se,
+            "step_roofline": {"bound": "hbm", "bytes_per_step": step_bytes, "achieved": achieved, "peak": peak,
+                              "unit": "GB/s", "frac": achieved / peak,
+                              "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"},
             "dC_dgamma": [float(x) for x in dg], "dC_dbeta": [float(x) for x in db], "clocks": clocks.summary(),
             "config": config_of(w, {"steps": steps, "warmup": warmup,
                                     "step": "qn_run_qaoa (fused layers) + qn_grad (fused adjoint: a layer's mixer "
@@ -366,12 +399,7 @@ def gpu_arm(args):
     from paper_2210_15874_gb300 import qn
 
     w = workload(args.workload)
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    hbm_peak, peak_src = hbm_peak_of()
     stream = torch.cuda.current_stream()
 
     _, main_mode, other_mode = WORKLOADS[args.workload]
