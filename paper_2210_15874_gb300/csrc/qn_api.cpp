@@ -1183,10 +1183,12 @@ std::string dev_signature(const qn_batch *h, const BatchView &v, const SlotView 
     const int32_t ne = (int32_t)h->edges_host.size();
     put(&ne, sizeof ne);
     const void *ptrs[] = {h->gr_dev, h->gv_H, h->gv_T, h->gv_stprev, h->gv_ekey, h->gv_i32, h->gv_htrue,
-                          h->gv_p1m, h->gv_cls, h->sh_log, h->sh_order, h->sh_weights, h->cpart, h->acc_counter,
+                          h->gv_p1m, h->gv_cls, h->sh_log, h->sh_queue, h->sh_order, h->sh_weights, h->cpart,
+                          h->acc_counter,
                           h->c_dbg, h->probs, h->sums, h->dedges, h->spart};
     put(ptrs, sizeof ptrs);
     put(&h->gv_cap, sizeof h->gv_cap);
+    put(&h->sh_queue_cap, sizeof h->sh_queue_cap);
     return sig;
 }
 
