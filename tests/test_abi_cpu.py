@@ -55,6 +55,15 @@ def test_create_validates_before_device_work(qn):
     m, s = ctypes.c_double(), ctypes.c_double()
     assert qn.qn_expectation(h, ctypes.byref(m), ctypes.byref(s)) == qn.QN_ESTATE
     assert qn.qn_batch_set_launch_batch(h, -1) == qn.QN_EINVAL
+    for bad in (-1, 3):
+        assert qn.qn_batch_set_launch_mode(h, bad) == qn.QN_EINVAL
+    for good in (0, 1, 2):
+        assert qn.qn_batch_set_launch_mode(h, good) == qn.QN_OK
+    c, r, u = ctypes.c_int64(-1), ctypes.c_int64(-1), ctypes.c_int64(-1)
+    assert qn.qn_graph_info(h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(u)) == qn.QN_OK
+    assert (c.value, r.value, u.value) == (0, 0, 0)
+    assert qn.qn_graph_info(h, None, None, None) == qn.QN_OK
+    assert qn.qn_graph_info(None, None, None, None) == qn.QN_EINVAL
     qn.qn_batch_destroy(h)
     qn.qn_batch_destroy(None)
 
