@@ -301,7 +301,8 @@ def precision_leg(qn, args, stream, local, roof_of):
                              ("tensor_bf16x3", (False, True), 2), ("per_gate", (False, False), 0)):
         res = measure(qn, w, sub, mode, stream, 0, 1, local, None, with_e2e=False, precision=prec)
         kname = ("k_tc_sweep (tensor-core windows of 5 qubits, 16 B per amplitude)" if prec else
-                 "k_fused_sweep (fused layer sweeps)") if mode[1] else "k_sweep_zz / k_sweep_rx (gate sweeps)"
+                 "k_fused_tile12 / k_fused_win / k_fused_sweep (fused layer sweeps)") if mode[1] else \
+            "k_sweep_zz / k_sweep_rx (gate sweeps)"
         r = roof_of(res, kname, "sweeps")
         legs[name] = {"value": res["value"], "unit": UNIT, "ms_per_step": res["ms"] / sub.steps,
                       "c_mean": res["mean"], "c_stderr": res["se"], "sweep_bytes_per_step": res["sweep_bytes_per_step"],
@@ -322,11 +323,12 @@ def hbm_peak_of():
 
 
 def fused_window_count(n: int) -> int:
-    """Sweeps per layer of the fused forward layers (the library's fused_windows: qubits 0-7,
-    then windows of at most 7; five per window below 10 qubits)."""
+    """Sweeps per layer of the fused forward layers (the library's fused_windows: the window
+    of qubits 0-11 where it saves a sweep, else 0-7, then windows of at most 7; five per
+    window below 10 qubits)."""
     if n < 10:
         return -(-n // 5)
-    return 1 + -(-(n - 8) // 7)
+    return 1 + min(-(-(n - 8) // 7), -(-(n - 12) // 7) if n > 12 else n)
 
 
 def adjoint_window_count(n: int) -> int:
@@ -458,7 +460,7 @@ def gpu_arm(args):
             "k_slot_sweep (gate sweeps over live prefix states)" if sharing else \
             (("k_tc_sweep (tensor-core windows of 5 qubits, %s, 16 B per amplitude)" %
               ("TF32" if args.precision == 1 else "BF16x3") if args.precision and w.n >= 11 else
-              "k_fused_sweep (fused layer sweeps, 16 B per amplitude)") if fused else
+              "k_fused_tile12 / k_fused_win / k_fused_sweep (fused layer sweeps, 16 B per amplitude)") if fused else
              "k_sweep_zz / k_sweep_rx (gate sweeps, 16 B per amplitude)")
         line = {
             "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -476,7 +478,8 @@ def gpu_arm(args):
                          + ("; launches sized on the host from the live-slot count" if args.launch_mode == 0 else
                             "; device-driven persistent launches" + (" replayed as a CUDA graph"
                                                                       if args.launch_mode == 2 else ""))) if sharing else
-                        (f"fused layers: qubits 0-7, then windows of <= 7 qubits, one sweep each per QAOA layer, "
+                        (f"fused layers: qubits 0-11 (one shared-memory tile) or 0-7, then windows of <= 7 qubits, "
+                         f"one sweep each per QAOA layer, "
                          f"{w.batch} trajectories per launch" if fused
                          else f"one statevector per trajectory, one sweep per gate, {w.batch} per launch")}),
             "amp_updates_per_s": main["value"] * G * (1 << n),

@@ -114,8 +114,10 @@ qn_status qn_batch_set_launch_batch(qn_batch *h, int64_t B);
  * applied as a few sweeps instead of E + n: the cost layer (every phase gate
  * and every Pauli's Z part) is one diagonal factor folded into a mixer sweep,
  * and the mixer rotations are applied in windows of consecutive qubits -- for
- * n >= 10 qubits 0-7, then ceil((n - 8) / 7) windows of at most 7 (3 sweeps
- * per layer at n = 20, 4 at n = 26); below 10 qubits five per sweep.  Needs
+ * n >= 10 a first window of qubits 0-11 where that makes fewer windows than
+ * qubits 0-7 does (n = 16-19, 23-26, 30), then windows of at most 7 over the
+ * rest (2 sweeps per layer at n = 16, 3 at n = 20-26, 4 at n = 30); below 10
+ * qubits five per sweep.  Needs
  * at most 64 edges; otherwise gates are swept one by one.  With damping == 0
  * fusion takes precedence over shared-prefix mode.  With damping, fusion acts
  * in shared-prefix mode only: consecutive phase gates of a layer on at most 10

@@ -777,19 +777,23 @@ LayerView layer_view(const qn_batch *h, int l) {
     return L;
 }
 
-// The fused mixer windows (first qubit, qubits) of one layer.  n >= 10: qubits
-// 0 .. kFuse0-1, then ceil((n - kFuse0) / kFuse) windows of balanced sizes (at most
-// kFuse, the larger ones first); n < 10: windows of kFuseSmall qubits.
+// The fused mixer windows (first qubit, qubits) of one layer.  n >= 10: the window
+// that holds qubit 0, then ceil(rest / kFuse) windows of balanced sizes over the rest
+// (at most kFuse, the larger ones first); the first window is qubits 0 .. kFuseTile-1
+// (one tile in shared memory) where that makes fewer windows than qubits
+// 0 .. kFuse0-1 (n = 16-19, 23-26, 30, ...).  n < 10: windows of kFuseSmall qubits.
 std::vector<std::pair<int, int>> fused_windows(int n) {
     std::vector<std::pair<int, int>> w;
     if (n < 10) {
         for (int q_lo = 0; q_lo < n; q_lo += kFuseSmall) w.emplace_back(q_lo, std::min(kFuseSmall, n - q_lo));
         return w;
     }
-    w.emplace_back(0, kFuse0);
-    const int rest = n - kFuse0;
-    const int count = (rest + kFuse - 1) / kFuse;
-    int q_lo = kFuse0;
+    auto rest_windows = [&](int first) { return (n - first + kFuse - 1) / kFuse; };
+    const int first = n > kFuseTile && rest_windows(kFuseTile) < rest_windows(kFuse0) ? kFuseTile : kFuse0;
+    w.emplace_back(0, first);
+    const int rest = n - first;
+    const int count = rest_windows(first);
+    int q_lo = first;
     for (int i = 0; i < count; ++i) {
         const int m = rest / count + (i < rest % count ? 1 : 0);
         w.emplace_back(q_lo, m);
@@ -845,8 +849,14 @@ qn_status run_fused_gates(qn_batch *h, const BatchView &v, double amp_bytes, boo
             const bool norm = q_lo + m >= n && l + 1 == p && q_lo > 0;
             if (norm) *norms = true;
             QN_TRY(prof_begin(h, &ep, 0, amp_bytes * 16.0));
-            QN_CUDA(launch_fused_sweep(v, layer_view(h, l), layer_view(h, l), layer_view(h, post ? l + 1 : l), q_lo, m,
-                                       pre, post, norm, h->stream));
+            if (m == kFuseTile)  // never the last window of a layer (n > kFuseTile)
+                QN_CUDA(launch_fused_tile12(v, layer_view(h, l), layer_view(h, l), pre, h->stream));
+            else if (fused_win_ok(n, q_lo, m, post, norm))
+                QN_CUDA(launch_fused_win(v, layer_view(h, l), layer_view(h, post ? l + 1 : l), q_lo, m, post, norm,
+                                         h->stream));
+            else
+                QN_CUDA(launch_fused_sweep(v, layer_view(h, l), layer_view(h, l), layer_view(h, post ? l + 1 : l),
+                                           q_lo, m, pre, post, norm, h->stream));
             QN_TRY(prof_end(h, &ep));
             h->launches += 1;
             if (ensemble) h->sweep_bytes += amp_bytes * 16.0;

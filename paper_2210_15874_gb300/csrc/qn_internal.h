@@ -246,6 +246,8 @@ struct TcSweep {
 // Fused mixer windows (16 float4 per thread, the qubits beyond four on lane bits):
 constexpr int kFuse0 = 8;      // the window that holds qubit 0 (n >= 10): qubit 0 in the float4,
                                // 1-3 on lane bits, 4-7 in registers
+constexpr int kFuseTile = 12;  // the window of qubits 0-11 as one 2048-float4 tile in shared memory,
+                               // taken where it saves a sweep per layer
 constexpr int kFuse = 7;       // at most, each of the other windows (n >= 10)
 constexpr int kFuseSmall = 5;  // n < 10: windows of five qubits, registers only
 constexpr int kFuseChunks = 8;  // chunks of kThreads fibre-threads per fused-sweep block
@@ -369,6 +371,19 @@ cudaError_t launch_layer_params(const BatchView &v, const LayerView &L, int g0, 
 cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const LayerView &Lr, const LayerView &Lq,
                                int q_lo, int m, bool pre, bool post, bool norm, cudaStream_t s);
 cudaError_t launch_phase_sweep(const BatchView &v, const LayerView &L, cudaStream_t s);
+// A fused window off qubit 0 of 4-7 qubits whose float4-index bits start at 11 - m or
+// above: tiles of runs of consecutive float4 times the window's values, through shared
+// memory; post: the next layer's phase (Lq) after the rotations; norm: the final norms
+// (the circuit's last sweep).  fused_win_ok: the windows it takes (the others take
+// launch_fused_sweep).
+bool fused_win_ok(int n, int q_lo, int m, bool post, bool norm);
+cudaError_t launch_fused_win(const BatchView &v, const LayerView &Lr, const LayerView &Lq, int q_lo, int m, bool post,
+                             bool norm, cudaStream_t s);
+// The first window of a fused layer for n >= 13: the rotations of qubits 0-11 of layer Lr
+// in one sweep of 2048-float4 tiles (two phases through shared memory), with layer Lp's
+// phase before them when pre.
+cudaError_t launch_fused_tile12(const BatchView &v, const LayerView &Lp, const LayerView &Lr, bool pre,
+                                cudaStream_t s);
 // Tensor-core form of a fused sweep (n >= 11): the window's rotations as two
 // GEMMs with the +-1 Hadamard matrix (qn_tc.cu), PRE / POST phases as for
 // launch_fused_sweep.  kind: kPrecTF32 or kPrecBF16x3.

@@ -2282,11 +2282,12 @@ __global__ void __launch_bounds__(kThreads) k_order_compact(const int32_t *pos, 
 // forms <C>_t and adds S1, S2 in trajectory order.
 // ---------------------------------------------------------------------------
 
-// The end of a norm pass over state t, blocks tile = 0 .. ntiles-1 (kThreads
-// threads each, every thread holding its double-float sum (sh, sl)): the block
+// The end of a norm pass over state t, blocks tile = 0 .. ntiles-1 (WARPS warps
+// each, every thread holding its double-float sum (sh, sl)): the block
 // sum goes to partials, and the last block to finish stores 1/N_t.
+template <int WARPS = kThreads / 32>
 __device__ void norm_finish(const BatchView &v, int t, int tile, int ntiles, float sh, float sl) {
-    __shared__ double redd[kThreads / 32];
+    __shared__ double redd[WARPS];
     __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double sn = df_warp_sum(sh, sl);
@@ -2294,7 +2295,7 @@ __device__ void norm_finish(const BatchView &v, int t, int tile, int ntiles, flo
     __syncthreads();
     if (threadIdx.x == 0) {
         double sum = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) sum += redd[w];
+        for (int w = 0; w < WARPS; ++w) sum += redd[w];
         v.partials[((size_t)t * v.tiles + tile) * 4] = sum;
         __threadfence();
         const unsigned prev = atomicAdd(&v.counters[t], 1u);
@@ -2304,7 +2305,7 @@ __device__ void norm_finish(const BatchView &v, int t, int tile, int ntiles, flo
     if (!last) return;
     __threadfence();
     double s0 = 0.0;
-    for (int i = threadIdx.x; i < ntiles; i += kThreads) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4);
+    for (int i = threadIdx.x; i < ntiles; i += WARPS * 32) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
     __syncthreads();
@@ -2312,7 +2313,7 @@ __device__ void norm_finish(const BatchView &v, int t, int tile, int ntiles, flo
     __syncthreads();
     if (threadIdx.x == 0) {
         double N = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) N += redd[w];
+        for (int w = 0; w < WARPS; ++w) N += redd[w];
         if (!(N > 0.0) || !isfinite(N)) atomicOr(v.status, 2);
         v.inv_norm[t] = 1.0 / N;
         v.counters[t] = 0;
@@ -3117,6 +3118,281 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
     if (NORM) norm_finish(v, t, blockIdx.x, gridDim.x, sh, sl);
 }
 
+// The first window of a fused layer for n >= 13: the mixer rotations of qubits 0-11 (and,
+// with PRE, layer Lp's phase before them), one 2048-float4 tile of consecutive float4 at a
+// time -- qubit 0 the float4 half, qubits 1-11 the tile's float4-index bits 0-10.  Tiles
+// stream through two shared buffers (cp.async, one tile ahead, 512 contiguous bytes per
+// warp copy); each tile takes three register phases over the buffer, 16 float4 per thread:
+//   A  register index j = bits 0-3 (the phase, qubits 0 and 1-4),
+//   B  j = bits 4-7 (qubits 5-8),
+//   C  j bit 0 = bit 7, bits 1-3 = bits 8-10 (qubits 9-11), stored to HBM from there.
+// The rotations take the tangent form (rx_pair_t) with the common factor rsc^12 and the
+// row signs of the drawn Paulis' Z parts applied once, after the window: qubit q's row r
+// carries -1 when z_q and r != x_q (the frame's X bit), so an amplitude y of the window
+// carries (-1)^popc(z & (x ^ y)).  Slot of float4 f in a buffer: f ^ ((f >> 4) & 7), so
+// that each quarter warp of every phase hits eight distinct 16-byte bank groups.
+// Grid (blocks of up to kT12Subs tiles, trajectories) x 128 threads.
+constexpr int kT12Subs = 4;
+constexpr size_t kT12Smem = 2 * 2048 * sizeof(float4);
+
+template <bool TANF, bool PRE>
+__global__ void __launch_bounds__(128, 3) k_fused_tile12(BatchView v, LayerView Lp, LayerView Lr) {
+    extern __shared__ float4 t12_buf[];  // [2][2048]
+    __shared__ uint64_t evk[17];         // PRE: EV of the phase-A register offsets 2j; [16]: EV of bit 0
+    const int t = blockIdx.y;
+    const uint32_t tid = threadIdx.x;
+    const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)t << v.n));
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << v.n));
+    const int ntiles = 1 << (v.n - 12);
+    const int nsubs = ntiles < kT12Subs ? ntiles : kT12Subs;
+    const uint32_t tile0 = (uint32_t)blockIdx.x * (uint32_t)nsubs;
+    if (PRE) {
+        if (tid < 16u) evk[tid] = ev_of(Lp, 2u * tid);
+        if (tid == 16u) evk[16] = ev_of(Lp, 1u);
+    }
+    const float cb = Lr.cb, sb = Lr.sb;
+    const float rt = TANF ? sb / cb : cb / sb, rsc = TANF ? cb : sb;
+    float sc12 = 1.0f;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) sc12 *= rsc;
+    const uint32_t zw = Lr.mz[t] & 0xfffu;
+    const uint32_t sgn0 = (uint32_t)__popc(zw & Lr.mf[t]);  // the parity's constant part
+    auto sw = [](uint32_t f) { return f ^ ((f >> 4) & 7u); };
+    auto fetch = [&](int sub) {
+        float4 *buf = t12_buf + (sub & 1) * 2048;
+        const float4 *src = q4 + ((size_t)(tile0 + (uint32_t)sub) << 11);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t f = tid | ((uint32_t)k << 7);
+            cp_async16(buf + sw(f), src + f);
+        }
+        cp_async_commit();
+    };
+    fetch(0);
+    for (int sub = 0; sub < nsubs; ++sub) {
+        if (sub + 1 < nsubs) {
+            fetch(sub + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // every thread's copies of this tile (and evk)
+        float4 *buf = t12_buf + (sub & 1) * 2048;
+        const uint32_t tb = (tile0 + (uint32_t)sub) << 11;  // the tile's first float4 (n <= 30)
+        float4 x[16];
+        // phase A: f = j | tid << 4
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = buf[sw((uint32_t)j | (tid << 4))];
+        if (PRE) {
+            const uint64_t sv = Lp.s[t];
+            const uint32_t zm = Lp.zm[t];
+            const uint32_t y0 = 2u * (tb | (tid << 4));
+            const uint64_t ev0 = ev_of(Lp, y0);
+            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lp.zc[t];
+            const uint64_t ev1 = evk[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const uint32_t yk = 2u * (uint32_t)j;
+                cmul_inplace(x[j].x, x[j].y, split_phase(Lp, ev0, evk[j], sv, zp0, yk, zm));
+                cmul_inplace(x[j].z, x[j].w, split_phase(Lp, ev0 ^ ev1, evk[j], sv, zp0, yk | 1u, zm));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) rx_pair_t<TANF>(x[j].x, x[j].y, x[j].z, x[j].w, rt);  // qubit 0
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) buf[sw((uint32_t)j | (tid << 4))] = x[j];
+        __syncthreads();
+        // phase B: f = (tid & 15) | j << 4 | (tid >> 4) << 8
+        const uint32_t fB = (tid & 15u) | ((tid >> 4) << 8);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = buf[sw(fB | ((uint32_t)j << 4))];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) buf[sw(fB | ((uint32_t)j << 4))] = x[j];
+        __syncthreads();
+        // phase C: f = tid | (j & 1) << 7 | (j >> 1) << 8
+        auto fC = [&](int j) { return tid | ((uint32_t)(j & 1) << 7) | ((uint32_t)(j >> 1) << 8); };
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = buf[sw(fC(j))];
+#pragma unroll
+        for (int i = 1; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (!(j & (1 << i))) rx_pair4_t<TANF>(x[j], x[j | (1 << i)], rt);
+        const uint32_t pt = sgn0 ^ (uint32_t)__popc(zw & (2u * tid));  // parity of the thread's part
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint32_t par = pt ^ (uint32_t)__popc(zw & (2u * (fC(j) & ~tid)));
+            const float s0 = (par & 1u) ? -sc12 : sc12, s1 = ((par ^ zw) & 1u) ? -sc12 : sc12;
+            p4[tb + fC(j)] = make_float4(x[j].x * s0, x[j].y * s0, x[j].z * s1, x[j].w * s1);
+        }
+        __syncthreads();  // the buffer's reads are done before the next copy into it
+    }
+}
+
+// A fused window off qubit 0: the mixer rotations of M = 4..7 qubits q_lo .. q_lo+M-1,
+// float4-index bits w .. w+M-1 (w = q_lo - 1 >= 11 - M), with the next layer's phase
+// after them (MODE kWinPost) or the final norms (kWinNorm, the circuit's last sweep).
+// A tile is 2^(11-M) consecutive float4 (the run, bits 0 .. 10-M of the float4 index,
+// all below the window) times the 2^M values of the window's bits: tile index
+// i = run | window << (11 - M).  Tiles stream through two shared buffers (cp.async, one
+// tile ahead, copied in index order, so a warp copies runs of at least 256 contiguous
+// bytes however far apart the window's bits place them); then 16 float4 per thread:
+//   phase 1  register index j = window bits 0-3, the thread = the run and window bits 4..
+//   phase 2  (M > 4) j = run bits 3 .. 10-M and window bits 4 .., the thread = run bits
+//            0-2 and window bits 0-3,
+// the row signs of the drawn Paulis (folded into the phase's sign with kWinPost) and the
+// phase or the norm terms on the last phase's registers, back to the buffer, and stored
+// in index order.  Buffer slot of i: i itself (in every access the eight threads of a
+// quarter warp differ exactly in tile-index bits 0-2, eight distinct 16-byte bank groups).
+// Grid (blocks of up to kT12Subs tiles, trajectories) x 128 threads.
+enum { kWinPlain = 0, kWinPost = 1, kWinNorm = 2 };
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(128, 3) k_fused_win(BatchView v, LayerView Lr, LayerView Lq, int q_lo) {
+    constexpr int RL = 11 - M;  // run bits
+    constexpr int LJ = 8 - M;   // phase 2: run bits in the register index (bits 3 .. RL-1)
+    static_assert(M >= 4 && M <= 7, "windows of 4 to 7 qubits");
+    extern __shared__ float4 win_buf[];  // [2][2048]
+    __shared__ uint64_t evk[17];         // kWinPost: EV of the last phase's register offsets; [16]: EV of bit 0
+    const int t = blockIdx.y;
+    const uint32_t tid = threadIdx.x;
+    const int w = q_lo - 1;
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << v.n));
+    const int ntiles = 1 << (v.n - 12);
+    const int nsubs = ntiles < kT12Subs ? ntiles : kT12Subs;
+    const uint32_t tile0 = (uint32_t)blockIdx.x * (uint32_t)nsubs;
+    // float4 offset of tile index i, and the first float4 of tile u (its n-12 bits: the
+    // bits between the run and the window, then those above the window)
+    auto off = [&](uint32_t i) { return (i & ((1u << RL) - 1u)) | ((i >> RL) << w); };
+    auto tile_base = [&](uint32_t u) {
+        const uint32_t mid = (uint32_t)(w - RL);
+        return ((u & ((1u << mid) - 1u)) << RL) | ((u >> mid) << (w + M));
+    };
+    // the last phase's tile index: the thread's part and register j's part
+    const uint32_t it_last = M == 4 ? (tid & ((1u << RL) - 1u)) | ((tid >> RL) << (RL + 4)) : (tid & 7u) | ((tid >> 3) << RL);
+    auto ij_last = [](int j) -> uint32_t {
+        if (M == 4) return (uint32_t)j << RL;
+        return ((uint32_t)(j & ((1 << LJ) - 1)) << 3) | ((uint32_t)(j >> LJ) << (RL + 4));
+    };
+    // Rotations without the row signs; those are a diagonal after the window's rotations:
+    // -1 on qubit q's row r when z_q and r != x_q, so a tile index i carries
+    // (-1)^popc(zw & (xw ^ (i >> RL))) (zw, xw: the window's Z and frame bits).
+    const uint32_t zw = (Lr.mz[t] >> q_lo) & ((1u << M) - 1u), xw = (Lr.mf[t] >> q_lo) & ((1u << M) - 1u);
+    const float cb = Lr.cb, sb = Lr.sb;
+    uint32_t pj = 0;  // bit j: the parity of register j's part (and, with kWinPost, of its phase sign)
+    const uint32_t zmq = MODE == kWinPost ? Lq.zm[t] : 0u;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const uint32_t ij = ij_last(j);
+        uint32_t par = (uint32_t)__popc(zw & (ij >> RL));
+        if (MODE == kWinPost) par ^= (uint32_t)__popc(2u * off(ij) & zmq);
+        pj |= (par & 1u) << j;
+    }
+    const uint32_t pt = (uint32_t)__popc(zw & xw) ^ (uint32_t)__popc(zw & (it_last >> RL));  // the thread's part
+    if (MODE == kWinPost) {
+        if (tid < 16u) evk[tid] = ev_of(Lq, 2u * off(ij_last((int)tid)));
+        if (tid == 16u) evk[16] = ev_of(Lq, 1u);
+    }
+    auto rot = [&](float4 *x, int bit) {  // exp(-i beta X) on register bit `bit`
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j & (1 << bit)) continue;
+            float4 &a = x[j];
+            float4 &b = x[j | (1 << bit)];
+            const float nx = cb * a.x + sb * b.y, ny = cb * a.y - sb * b.x;
+            const float mx = cb * b.x + sb * a.y, my = cb * b.y - sb * a.x;
+            const float nz = cb * a.z + sb * b.w, nw = cb * a.w - sb * b.z;
+            const float mzv = cb * b.z + sb * a.w, mw = cb * b.w - sb * a.z;
+            a = make_float4(nx, ny, nz, nw);
+            b = make_float4(mx, my, mzv, mw);
+        }
+    };
+    // index order: thread tid takes i = tid | k << 7, k = 0..15; tile-index bit 7 is a
+    // window bit (RL <= 7), float4 offset 2^kst
+    const uint32_t off_t = off(tid);
+    const int kst = w + 7 - RL;
+    auto fetch = [&](int sub) {
+        float4 *buf = win_buf + (sub & 1) * 2048 + tid;
+        const float4 *src = p4 + tile_base(tile0 + (uint32_t)sub) + off_t;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) cp_async16(buf + (k << 7), src + ((size_t)k << kst));
+        cp_async_commit();
+    };
+    float sh = 0.0f, sl = 0.0f;  // kWinNorm: this thread's sum of |psi|^2 (double-float)
+    fetch(0);
+    for (int sub = 0; sub < nsubs; ++sub) {
+        if (sub + 1 < nsubs) {
+            fetch(sub + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // every thread's copies of this tile (and evk)
+        float4 *buf = win_buf + (sub & 1) * 2048;
+        float4 x[16];
+        // phase 1: j = window bits 0-3
+        const uint32_t i1 = (tid & ((1u << RL) - 1u)) | ((tid >> RL) << (RL + 4));
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = buf[i1 | ((uint32_t)j << RL)];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rot(x, b);
+        if (M > 4) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) buf[i1 | ((uint32_t)j << RL)] = x[j];
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = buf[it_last | ij_last(j)];
+#pragma unroll
+            for (int b = LJ; b < 4; ++b) rot(x, b);
+        }
+        if (MODE == kWinPost) {  // the next layer's phase, with the row signs folded into its sign
+            const uint64_t sv = Lq.s[t];
+            const uint32_t y0 = 2u * (tile_base(tile0 + (uint32_t)sub) | off(it_last));
+            const uint64_t ev0 = ev_of(Lq, y0), ev1 = evk[16];
+            const uint32_t p0 = (uint32_t)__popc(y0 & zmq) ^ Lq.zc[t] ^ pt;
+            const uint32_t p1 = p0 ^ (zmq & 1u);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float2 f0 = __ldg(Lq.phase + __popcll(ev0 ^ evk[j] ^ sv));
+                const float2 f1 = __ldg(Lq.phase + __popcll(ev0 ^ ev1 ^ evk[j] ^ sv));
+                const float g0 = ((p0 ^ (pj >> j)) & 1u) ? -1.0f : 1.0f;
+                const float g1 = ((p1 ^ (pj >> j)) & 1u) ? -1.0f : 1.0f;
+                cmul_inplace(x[j].x, x[j].y, make_float2(f0.x * g0, f0.y * g0));
+                cmul_inplace(x[j].z, x[j].w, make_float2(f1.x * g1, f1.y * g1));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if ((pt ^ (pj >> j)) & 1u) x[j] = make_float4(-x[j].x, -x[j].y, -x[j].z, -x[j].w);
+        }
+        if (MODE == kWinNorm) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                df_add(sh, sl, prob_of(1.0f, x[j].x, x[j].y));
+                df_add(sh, sl, prob_of(1.0f, x[j].z, x[j].w));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) buf[it_last | ij_last(j)] = x[j];  // the slots this thread read
+        __syncthreads();
+        float4 *dst = p4 + tile_base(tile0 + (uint32_t)sub) + off_t;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dst[(size_t)k << kst] = buf[tid + (k << 7)];
+        __syncthreads();  // the buffer's reads are done before the next copy into it
+    }
+    if (MODE == kWinNorm) norm_finish<4>(v, t, blockIdx.x, gridDim.x, sh, sl);
+}
+
 // Phase only (a circuit whose layers have no mixer qubits left to fuse with).
 __global__ void __launch_bounds__(kThreads) k_phase_sweep(BatchView v, LayerView L) {
     const int t = blockIdx.y;
@@ -3735,6 +4011,71 @@ cudaError_t launch_fused_sweep(const BatchView &v, const LayerView &Lp, const La
         return fused_dispatch<3, 4, false>(v, Lp, Lr, Lq, q_lo, pre, post, norm, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_fused_tile12(const BatchView &v, const LayerView &Lp, const LayerView &Lr, bool pre,
+                                cudaStream_t s) {
+    if (v.n < 13 || v.n > 30) return cudaErrorInvalidValue;
+    static const cudaError_t attr = [] {
+        for (auto k : {k_fused_tile12<true, true>, k_fused_tile12<true, false>, k_fused_tile12<false, true>,
+                       k_fused_tile12<false, false>}) {
+            const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT12Smem);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }();
+    if (attr != cudaSuccess) return attr;
+    const int ntiles = 1 << (v.n - 12);
+    const dim3 grid((unsigned)(ntiles < kT12Subs ? 1 : ntiles / kT12Subs), (unsigned)v.b);
+    const bool tanf = std::fabs(Lr.cb) >= std::fabs(Lr.sb);
+    if (tanf) {
+        if (pre) k_fused_tile12<true, true><<<grid, 128, kT12Smem, s>>>(v, Lp, Lr);
+        else k_fused_tile12<true, false><<<grid, 128, kT12Smem, s>>>(v, Lp, Lr);
+    } else {
+        if (pre) k_fused_tile12<false, true><<<grid, 128, kT12Smem, s>>>(v, Lp, Lr);
+        else k_fused_tile12<false, false><<<grid, 128, kT12Smem, s>>>(v, Lp, Lr);
+    }
+    return cudaGetLastError();
+}
+
+template <int M, int MODE>
+static cudaError_t win_launch(const BatchView &v, const LayerView &Lr, const LayerView &Lq, int q_lo, cudaStream_t s) {
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_fused_win<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT12Smem);
+    if (attr != cudaSuccess) return attr;
+    const int ntiles = 1 << (v.n - 12);
+    const int blocks = ntiles < kT12Subs ? 1 : ntiles / kT12Subs;
+    if (MODE == kWinNorm && blocks > v.tiles) return cudaErrorInvalidValue;  // partial sums: v.tiles per state
+    k_fused_win<M, MODE><<<dim3((unsigned)blocks, (unsigned)v.b), 128, kT12Smem, s>>>(v, Lr, Lq, q_lo);
+    return cudaGetLastError();
+}
+
+// Which windows take k_fused_win (measured on the fused layers at n = 16-26): the tiled form
+// streams at the copy rate wherever the register sweep's lane runs are short (64 bytes for a
+// 7-qubit window, far apart at the top qubits), and for the plain and norm sweeps; the
+// register sweep (256 threads, more warps in flight) applies the next layer's phase faster
+// in windows of up to six qubits.  Plain windows of four or five qubits off qubit 0 do not
+// occur for n <= 30.
+bool fused_win_ok(int n, int q_lo, int m, bool post, bool norm) {
+    if (n < 12 || n > 30 || m < 4 || m > 7 || q_lo < 1 || q_lo - 1 < 11 - m || q_lo + m > n || (post && norm))
+        return false;
+    if (post) return m == 7;
+    return norm || m >= 6;
+}
+
+cudaError_t launch_fused_win(const BatchView &v, const LayerView &Lr, const LayerView &Lq, int q_lo, int m, bool post,
+                             bool norm, cudaStream_t s) {
+    if (!fused_win_ok(v.n, q_lo, m, post, norm)) return cudaErrorInvalidValue;
+    if (norm) {
+        switch (m) {
+        case 4: return win_launch<4, kWinNorm>(v, Lr, Lq, q_lo, s);
+        case 5: return win_launch<5, kWinNorm>(v, Lr, Lq, q_lo, s);
+        case 6: return win_launch<6, kWinNorm>(v, Lr, Lq, q_lo, s);
+        default: return win_launch<7, kWinNorm>(v, Lr, Lq, q_lo, s);
+        }
+    }
+    if (post) return win_launch<7, kWinPost>(v, Lr, Lq, q_lo, s);
+    return m == 6 ? win_launch<6, kWinPlain>(v, Lr, Lq, q_lo, s) : win_launch<7, kWinPlain>(v, Lr, Lq, q_lo, s);
 }
 
 cudaError_t launch_phase_sweep(const BatchView &v, const LayerView &L, cudaStream_t s) {

@@ -18,14 +18,17 @@ U32 = 2.0 ** -24
 
 def fused_windows(n):
     """Windows (first qubit, qubits) of one layer of the FP32 fused schedule: below ten
-    qubits five at a time (registers only); from ten on qubits 0-7 (qubit 0 in the float4,
-    1-3 on lane bits, 4-7 in registers), then ceil((n-8)/7) windows of balanced sizes,
-    larger first (the qubits beyond four on lane bits)."""
+    qubits five at a time (registers only); from ten on the window that holds qubit 0,
+    then balanced windows of at most 7 over the rest, larger first (the qubits beyond
+    four on lane bits).  The first window is qubits 0-11 (one 2048-float4 tile in
+    shared memory) where that leaves fewer windows than qubits 0-7 (qubit 0 in the
+    float4, 1-3 on lane bits, 4-7 in registers) does."""
     if n < 10:
         return [(q, min(5, n - q)) for q in range(0, n, 5)]
-    rest = n - 8
+    first = 12 if n > 12 and -(-(n - 12) // 7) < -(-(n - 8) // 7) else 8
+    rest = n - first
     count = -(-rest // 7)
-    out, q = [(0, 8)], 8
+    out, q = [(0, first)], first
     for i in range(count):
         m = rest // count + (1 if i < rest % count else 0)
         out.append((q, m))
@@ -42,7 +45,9 @@ def test_fused_windows_cover_each_qubit_once():
         w = fused_windows(n)
         assert [q for lo, m in w for q in range(lo, lo + m)] == list(range(n))
         assert all(m <= (7 if n >= 10 else 5) for _, m in w[1:])
-    assert [fused_sweeps(n) for n in (14, 20, 24, 26)] == [2, 3, 4, 4]
+    assert [fused_sweeps(n) for n in (14, 16, 20, 24, 26, 30)] == [2, 2, 3, 3, 3, 4]
+    assert [fused_windows(n)[0][1] for n in range(13, 32)] == \
+        [8, 8, 8, 12, 12, 12, 12, 8, 8, 8, 12, 12, 12, 12, 8, 8, 8, 12, 12]
 
 
 @pytest.fixture(scope="module")
@@ -67,12 +72,14 @@ def run(qn, w, fusion, launch_batch=0):
     return dict(mean=mean, se=se, probs=probs, info=info, **dbg)
 
 
-# every window form: registers only (n < 10, and the 2-4-qubit windows after qubit 7),
-# qubits 0-7 with three lane qubits (n >= 10), and 5, 6, 7-qubit windows with one, two,
-# three lane qubits (n = 13, 14, 15; n = 17 has 5 + 4)
+# every window form: registers only (n < 10, and the 2-4-qubit windows after qubit 7 or 11),
+# qubits 0-7 with three lane qubits (n >= 10), 5, 6, 7-qubit windows with one, two,
+# three lane qubits (n = 13, 14, 15, 19), and the 12-qubit tile (n = 16: 12 + 4, 16 tiles
+# per state; n = 17: 12 + 5; n = 19: 12 + 7)
 @pytest.mark.parametrize("n,p,edges_kind", [(2, 1, "one"), (3, 2, "ring"), (4, 2, "ring"), (7, 2, "reg"),
                                             (8, 1, "reg"), (10, 2, "reg"), (12, 3, "reg"), (13, 2, "reg"),
-                                            (14, 2, "reg"), (15, 2, "reg"), (17, 1, "reg")])
+                                            (14, 2, "reg"), (15, 2, "reg"), (16, 2, "reg"), (17, 1, "reg"),
+                                            (19, 1, "reg")])
 def test_fused_matches_per_gate_and_oracle(qn, n, p, edges_kind):
     if edges_kind == "one":
         edges = np.array([[0, 1]], dtype=np.int32)
