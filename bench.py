@@ -332,10 +332,13 @@ def fused_window_count(n: int) -> int:
 
 
 def adjoint_window_count(n: int) -> int:
-    """Mixer sweeps per layer of the fused adjoint (the library's adj_windows: qubits 0-3,
-    then windows of two or three)."""
+    """Sweeps per layer of the fused adjoint (the library's adj_tile_windows for n >= 12:
+    qubits 0-9, then windows of at most six, the cost diagonal in the last one's sweep;
+    adj_windows below: qubits 0-3, then windows of two or three, plus the phase sweep)."""
+    if n >= 12:
+        return 1 + -(-(n - 10) // 6)
     rest = n - min(4, n)
-    return 1 + (-(-rest // 3) if rest > 0 else 0)
+    return 2 + (-(-rest // 3) if rest > 0 else 0)
 
 
 def gradient_leg(qn, args, stream, local):
@@ -368,10 +371,10 @@ def gradient_leg(qn, args, stream, local):
     b.close()
     # bytes of one step: the fused forward sweeps (16 B per amplitude), the sigma pass (8 B), the
     # adjoint's start (read psi, write lambda: 16 B) and its sweeps (psi and lambda: 32 B), each
-    # layer's mixer windows plus its cost diagonal
+    # layer's mixer windows and its cost diagonal
     amps = float(w.trajectories) * (1 << w.n)
     step_bytes = amps * (16.0 * fused_window_count(w.n) * w.p + 8.0 + 16.0 +
-                         32.0 * (adjoint_window_count(w.n) + 1) * w.p)
+                         32.0 * adjoint_window_count(w.n) * w.p)
     peak, peak_src = hbm_peak_of()
     achieved = step_bytes / (ms / steps / 1e3) / 1e9
     return {"value": w.trajectories * steps / (ms / 1e3), "unit": "trajectories/s (forward + adjoint gradient)",
@@ -594,16 +597,26 @@ def serving_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(sharing=False, depth=1, fusion=True, precision=-1, launch_mode=0):
+def profile_case(sharing=False, depth=1, fusion=True, precision=-1, launch_mode=0, grad=False):
     """Small case of the bench's kernels for ncu (inputs larger than L2, 256 MiB of state);
     depth 2 adds a layer, so the last mixer block of the first one forms the next layer's joint.
     precision 0, 1 or 2: the precision workload's fused layers in FP32 or on the tensor cores
     (n=24, p=depth, depolarizing only, 8 states of 128 MiB; with depth 2 the first layer's last
-    window also applies the second layer's phase)."""
+    window also applies the second layer's phase).  grad: the gradient workload's circuit
+    (n=16, p=depth, depolarizing only) for 512 trajectories in one launch batch (256 MiB of
+    states and 256 MiB of adjoint states): the fused forward run and the fused adjoint."""
     from paper_2210_15874_gb300 import build
     build.build()
     from paper_2210_15874_gb300 import qn
 
+    if grad:
+        w = W.qaoa_workload(f"ncu_n16_p{depth}_grad", 16, depth, index=4, trajectories=512, batch=512)
+        with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+            b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+            dg, db = b.grad()
+            print(json.dumps({"case": w.name, "c": b.expectation(), "dC_dgamma": [float(x) for x in dg],
+                              "dC_dbeta": [float(x) for x in db]}))
+        return
     if precision >= 0:
         w = W.qaoa_workload(f"ncu_n24_p{depth}_tc", 24, depth, index=2, trajectories=8, batch=8)
         with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
@@ -669,13 +682,15 @@ def main():
                     help="run one small ensemble for ncu captures, then exit (n=20, p=1: 32 trajectories in "
                          "one launch, or with --sharing 1 64 heavily noisy trajectories)")
     ap.add_argument("--profile-depth", type=int, default=1, choices=[1, 2], help="QAOA depth of --profile-case")
+    ap.add_argument("--profile-grad", action="store_true",
+                    help="--profile-case: the gradient workload's circuit, forward run and fused adjoint")
     ap.add_argument("--profile-precision", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="--profile-case of the Pauli-only fused layers (0 FP32, 1 TF32, 2 BF16x3 tensor cores) "
                          "instead of the damping case")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(bool(args.sharing), args.profile_depth, bool(args.fusion), args.profile_precision,
-                     args.launch_mode)
+                     args.launch_mode, args.profile_grad)
         return
     if args.workload == "serving":
         serving_arm(args)

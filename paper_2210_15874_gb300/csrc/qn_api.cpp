@@ -1948,6 +1948,23 @@ std::vector<std::pair<int, int>> adj_windows(int n) {
     return w;
 }
 
+// The tiled reverse windows of one layer for n >= 12 (launch_adj_win): qubits 0-9, then
+// ceil((n - 10) / 6) windows of balanced sizes (at most 6, the larger ones first); the
+// last window also undoes the cost diagonal.
+std::vector<std::pair<int, int>> adj_tile_windows(int n) {
+    std::vector<std::pair<int, int>> w;
+    w.emplace_back(0, 10);
+    const int rest = n - 10;
+    const int count = (rest + 5) / 6;
+    int q_lo = 10;
+    for (int i = 0; i < count; ++i) {
+        const int m = rest / count + (i < rest % count ? 1 : 0);
+        w.emplace_back(q_lo, m);
+        q_lo += m;
+    }
+    return w;
+}
+
 int param_of(const qn_batch *h, int g) {
     const int E = (int)h->edges.size() / 2;
     const int r = g - h->n;
@@ -1991,6 +2008,13 @@ qn_status run_grad(qn_batch *h, int64_t t0, int64_t count) {
             // mixer in windows of a few qubits and its cost diagonal in one sweep
             for (int l = h->p - 1; l >= 0; --l) {
                 const LayerView L = layer_view(h, l);
+                if (n >= 12) {  // tiles through shared memory, the cost diagonal in the last window's sweep
+                    const std::vector<std::pair<int, int>> ws = adj_tile_windows(n);
+                    for (size_t i = 0; i < ws.size(); ++i)
+                        QN_CUDA(launch_adj_win(v, h->lambda, L, ws[i].first, ws[i].second, i + 1 == ws.size(), gr,
+                                               2 * l + 1, 2 * l, np, h->stream));
+                    continue;
+                }
                 for (const auto &wd : adj_windows(n))
                     QN_CUDA(launch_adj_mixer(v, h->lambda, L, wd.first, wd.second, gr, 2 * l + 1, np, h->stream));
                 QN_CUDA(launch_adj_phase(v, h->lambda, L, gr, 2 * l, np, h->stream));

@@ -420,6 +420,12 @@ cudaError_t launch_adj_init(const BatchView &v, float2 *lam, const AccumView &a,
 // L's cost diagonal, adding its term to grad[t][param] (d<C>_t / d gamma).
 cudaError_t launch_adj_mixer(const BatchView &v, float2 *lam, const LayerView &L, int q_lo, int m, double *grad,
                              int param, int nparam, cudaStream_t s);
+// The tiled reverse of one mixer window (n >= 12): qubits 0-9 (q_lo = 0, m = 10), or
+// m = 2..6 qubits from q_lo >= 10; with phase also the layer's cost diagonal (the last
+// window of the layer to be undone).  Terms to grad[t][pbeta] and, with phase,
+// grad[t][pgamma].
+cudaError_t launch_adj_win(const BatchView &v, float2 *lam, const LayerView &L, int q_lo, int m, bool phase,
+                           double *grad, int pbeta, int pgamma, int nparam, cudaStream_t s);
 cudaError_t launch_adj_phase(const BatchView &v, float2 *lam, const LayerView &L, double *grad, int param, int nparam,
                              cudaStream_t s);
 cudaError_t launch_adj_sweep(const BatchView &v, float2 *lam, int g, const DevGate &gate, double *grad, int param,

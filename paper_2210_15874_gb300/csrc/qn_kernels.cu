@@ -3557,6 +3557,311 @@ __global__ void __launch_bounds__(kThreads) k_adj_phase(BatchView v, float2 *lam
     adj_finish(v, t, tile, v.tiles, acc, grad, param, nparam);
 }
 
+// The end of a tiled adjoint sweep: as adj_finish for NV inner products at once (WARPS
+// warps per block), each into partials slot v of the block and grad[t][param[v]].
+template <int WARPS, int NV>
+__device__ void adj_finish_n(const BatchView &v, int t, int blk, int nblk, const float *acc, double *grad,
+                             const int *param, int nparam) {
+    __shared__ double redd[NV][WARPS];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double d = (double)acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+        if (lane == 0) redd[k][warp] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) {
+            double sum = 0.0;
+            for (int w = 0; w < WARPS; ++w) sum += redd[k][w];
+            v.partials[((size_t)t * v.tiles + blk) * 4 + k] = sum;
+        }
+        __threadfence();
+        const unsigned prev = atomicAdd(&v.counters[t], 1u);
+        last = prev == (unsigned)(nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s0 = 0.0;
+        for (int i = threadIdx.x; i < nblk; i += WARPS * 32) s0 += __ldcg(v.partials + ((size_t)t * v.tiles + i) * 4 + k);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        __syncthreads();
+        if (lane == 0) redd[k][warp] = s0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) {
+            double sum = 0.0;
+            for (int w = 0; w < WARPS; ++w) sum += redd[k][w];
+            grad[(size_t)t * nparam + param[k]] += 2.0 * sum * v.inv_norm[t];
+        }
+        v.counters[t] = 0;
+    }
+}
+
+// The layout of a tiled adjoint window.  A tile is 1024 float4 of psi and the same 1024
+// of lambda, tile index i (10 bits).  HAS0: the tile is float4 bits 0-9 and the window
+// qubits 0-9 (qubit 0 the float4 half, qubits 1-9 tile bits 0-8); otherwise tile bits
+// 0 .. L-1 are the run (float4 bits 0 .. L-1, below the window) and bits L .. 9 the
+// window's NB qubits q_lo .. (float4 bits q_lo-1 ..).  A thread holds 8 float4 of each
+// vector per phase: in phase p register bit b is tile bit rb(p, b) -- window bits
+// 3p .. 3p+2, or, past the window's last, the run's top bits -- and the thread's 7 bits
+// are the other tile bits in increasing order (so its bits 0-2 are tile bits 3-5 in
+// phase 0 with HAS0, tile bits 0-2 otherwise).  Buffer slot of i: i + (i >> 3), which
+// puts the eight threads of a quarter warp on distinct 16-byte bank groups in every
+// phase and adds over disjoint bit fields (base + constant addressing).
+template <bool HAS0, int NB>
+struct AdjWin {
+    static constexpr int L = HAS0 ? 10 : 10 - NB;
+    static constexpr int NP = HAS0 ? 3 : (NB > 3 ? 2 : 1);
+    __host__ __device__ static constexpr int wp(int p) { return HAS0 ? 3 : (NB - 3 * p < 3 ? NB - 3 * p : 3); }
+    __host__ __device__ static constexpr int rb(int p, int b) {
+        return HAS0 ? 3 * p + b : (b < wp(p) ? L + 3 * p + b : L - 1 - (b - wp(p)));
+    }
+    __host__ __device__ static constexpr bool in_rb(int p, int bit) {
+        return rb(p, 0) == bit || rb(p, 1) == bit || rb(p, 2) == bit;
+    }
+    __host__ __device__ static constexpr int tb(int p, int k) {  // tile bit of thread bit k
+        int c = 0;
+        for (int bit = 0; bit < 10; ++bit)
+            if (!in_rb(p, bit)) {
+                if (c == k) return bit;
+                ++c;
+            }
+        return -1;
+    }
+    __host__ __device__ static constexpr uint32_t ij(int p, int j) {  // register j's tile bits
+        return ((uint32_t)(j & 1) << rb(p, 0)) | ((uint32_t)((j >> 1) & 1) << rb(p, 1)) |
+               ((uint32_t)((j >> 2) & 1) << rb(p, 2));
+    }
+    __host__ __device__ static constexpr uint32_t slot(uint32_t i) { return i + (i >> 3); }
+};
+constexpr int kAdjTile = 1024;                       // float4 per vector and tile
+constexpr int kAdjSlots = kAdjTile + kAdjTile / 8;   // with one pad slot per eight
+constexpr int kAdjSubs = 4;                          // tiles per block
+constexpr size_t kAdjSmem = 2 * 2 * kAdjSlots * sizeof(float4);  // [buffer][psi, lambda][slot]
+
+// The reverse of one mixer window of layer L over tiles of psi and lambda (layout
+// AdjWin), and with PHASE also of the layer's cost diagonal (the window is the layer's
+// last to be undone).  Per tile: phase 0 applies the window's Pauli row signs S_q to both
+// vectors (a diagonal: (-1)^popc(z & (x ^ y)) over the window); then per phase, for each
+// register qubit, the term Im(conj(m0) a1 + conj(m1) a0) of d<C>_t/d beta (the row signs
+// are in: S_q's two signs multiply to sigma_q) and exp(+i beta X_q) on both vectors in
+// the tangent form of k_fused_tile12 with beta -> -beta (the common factor rsc^N taken
+// in phase 0).
+// With PHASE the last phase adds k(y) Im(conj(m) a) to d<C>_t/d gamma and applies
+// D(y)^dagger.  The terms of the other windows' qubits are unaffected (their rotations
+// commute with X_q).  Tiles stream through two buffers (cp.async, one tile ahead).
+// Grid (blocks of kAdjSubs tiles, trajectories) x 128 threads.
+template <bool HAS0, int NB, bool PHASE, bool TANF>
+__global__ void __launch_bounds__(128, 3) k_adj_win(BatchView v, float2 *lam, LayerView L, int q_lo, double *grad,
+                                                     int pbeta, int pgamma, int nparam) {
+    using A = AdjWin<HAS0, NB>;
+    constexpr int RL = A::L;
+    extern __shared__ float4 adj_buf[];  // [2][2][kAdjSlots]
+    __shared__ uint64_t evk[9];          // PHASE: EV of the last phase's register offsets; [8]: EV of bit 0
+    const int t = blockIdx.y;
+    const uint32_t tid = threadIdx.x;
+    const int w = HAS0 ? 0 : q_lo - 1;
+    float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << v.n));
+    float4 *l4 = reinterpret_cast<float4 *>(lam + ((size_t)t << v.n));
+    const int ntiles = 1 << (v.n - 11);
+    const int nsubs = ntiles < kAdjSubs ? ntiles : kAdjSubs;
+    const uint32_t tile0 = (uint32_t)blockIdx.x * (uint32_t)nsubs;
+    // float4 offset of tile index i, and the first float4 of tile u
+    auto off = [&](uint32_t i) -> uint32_t {
+        if constexpr (HAS0) return i;
+        else return (i & ((1u << RL) - 1u)) | ((i >> RL) << w);
+    };
+    auto tile_base = [&](uint32_t u) -> uint32_t {
+        if constexpr (HAS0) {
+            return u << 10;
+        } else {
+            const uint32_t mid = (uint32_t)(w - RL);
+            return ((u & ((1u << mid) - 1u)) << RL) | ((u >> mid) << (w + NB));
+        }
+    };
+    auto it_of = [&](int p) {  // the thread's tile bits in phase p
+        uint32_t i = 0;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) i |= ((tid >> k) & 1u) << A::tb(p, k);
+        return i;
+    };
+    // the window's amplitude bits of tile index i (float4 half 0): the Z and frame bits
+    // of its qubits line up with them
+    auto wbits = [&](uint32_t i) -> uint32_t {
+        return HAS0 ? (2u * i) & 0x3ffu : (i >> RL) & ((1u << NB) - 1u);
+    };
+    const uint32_t wmask = HAS0 ? 0x3ffu : (1u << NB) - 1u;
+    const uint32_t zw = (HAS0 ? L.mz[t] : L.mz[t] >> q_lo) & wmask, xw = (HAS0 ? L.mf[t] : L.mf[t] >> q_lo) & wmask;
+    uint32_t pj0 = 0;  // bit j: the row-sign parity of phase-0 register j's bits
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pj0 |= ((uint32_t)__popc(zw & wbits(A::ij(0, j))) & 1u) << j;
+    const uint32_t pt0 = (uint32_t)__popc(zw & xw) ^ (uint32_t)__popc(zw & wbits(it_of(0)));
+    // exp(+i beta X) = exp(-i (-beta) X): the forward's tangent form with sin beta negated
+    const float cb = L.cb, sb = -L.sb;
+    const float rt = TANF ? sb / cb : cb / sb, rsc = TANF ? cb : sb;
+    constexpr int PL = A::NP - 1;  // the last phase
+    uint32_t pjD = 0;
+    const uint32_t zmD = PHASE ? L.zm[t] : 0u;
+    if (PHASE) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pjD |= ((uint32_t)__popc(2u * off(A::ij(PL, j)) & zmD) & 1u) << j;
+        if (tid < 8u) evk[tid] = ev_of(L, 2u * off(A::ij(PL, (int)tid)));
+        if (tid == 8u) evk[8] = ev_of(L, 1u);
+    }
+    const uint32_t off_t = off(tid);  // index order: i = tid | k << 7
+    auto fetch = [&](int sub) {
+        float4 *bp = adj_buf + (sub & 1) * 2 * kAdjSlots;
+        const uint32_t tbs = tile_base(tile0 + (uint32_t)sub);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t i = tid | ((uint32_t)k << 7);
+            const uint32_t o = tbs + off_t + off((uint32_t)k << 7);
+            cp_async16(bp + A::slot(i), p4 + o);
+            cp_async16(bp + kAdjSlots + A::slot(i), l4 + o);
+        }
+        cp_async_commit();
+    };
+    float accb = 0.0f, accg = 0.0f;
+    // Phase 0 scales both vectors by rsc^N (N: the window's qubits) with the row signs, so
+    // that after the window's N tangent-form rotations they carry their true scale; the
+    // terms of phase p, taken on values still short of the rotations before it, are scaled
+    // by rsc^(2 (N - nprev)) and corrected once per phase.
+    constexpr int NQ = HAS0 ? 10 : NB;
+    float rscN = 1.0f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) rscN *= rsc;
+    float corr[A::NP];  // 1 / rsc^(2 (N - qubits rotated before phase p))
+    {
+        int prev = 0;
+#pragma unroll
+        for (int p = 0; p < A::NP; ++p) {
+            float c = 1.0f;
+            for (int q = prev; q < NQ; ++q) c *= rsc * rsc;
+            corr[p] = 1.0f / c;
+            prev += A::wp(p) + ((HAS0 && p == 0) ? 1 : 0);
+        }
+    }
+    float accp = 0.0f;  // the current phase's terms
+    auto term = [&](float a0r, float a0i, float a1r, float a1i, float m0r, float m0i, float m1r, float m1i) {
+        accp += (m0r * a1i - m0i * a1r) + (m1r * a0i - m1i * a0r);
+    };
+    fetch(0);
+    for (int sub = 0; sub < nsubs; ++sub) {
+        if (sub + 1 < nsubs) {
+            fetch(sub + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // every thread's copies of this tile (and evk)
+        float4 *bp = adj_buf + (sub & 1) * 2 * kAdjSlots;
+        float4 a[8], m[8];
+#pragma unroll
+        for (int p = 0; p < A::NP; ++p) {
+            const uint32_t st = A::slot(it_of(p));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                a[j] = bp[st + A::slot(A::ij(p, j))];
+                m[j] = bp[kAdjSlots + st + A::slot(A::ij(p, j))];
+            }
+            if (p == 0) {  // the row signs of the window's qubits, and rsc^N
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t par = pt0 ^ (pj0 >> j);
+                    const float s0 = (par & 1u) ? -rscN : rscN;
+                    const float s1 = HAS0 ? (((par ^ zw) & 1u) ? -rscN : rscN) : s0;
+                    a[j] = make_float4(a[j].x * s0, a[j].y * s0, a[j].z * s1, a[j].w * s1);
+                    m[j] = make_float4(m[j].x * s0, m[j].y * s0, m[j].z * s1, m[j].w * s1);
+                }
+            }
+            // the terms of the phase's qubits, all on the values as the phase read them (the
+            // tangent-form rotations are unitary only up to rsc, applied at the phase's end)
+            if (HAS0 && p == 0) {  // qubit 0: the float4 halves
+#pragma unroll
+                for (int j = 0; j < 8; ++j) term(a[j].x, a[j].y, a[j].z, a[j].w, m[j].x, m[j].y, m[j].z, m[j].w);
+            }
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (b >= A::wp(p)) break;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j & (1 << b)) continue;
+                    const int k = j | (1 << b);
+                    term(a[j].x, a[j].y, a[k].x, a[k].y, m[j].x, m[j].y, m[k].x, m[k].y);
+                    term(a[j].z, a[j].w, a[k].z, a[k].w, m[j].z, m[j].w, m[k].z, m[k].w);
+                }
+            }
+            accb = __fmaf_rn(accp, corr[p], accb);
+            accp = 0.0f;
+            if (HAS0 && p == 0) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    rx_pair_t<TANF>(a[j].x, a[j].y, a[j].z, a[j].w, rt);
+                    rx_pair_t<TANF>(m[j].x, m[j].y, m[j].z, m[j].w, rt);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (b >= A::wp(p)) break;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j & (1 << b)) continue;
+                    rx_pair4_t<TANF>(a[j], a[j | (1 << b)], rt);
+                    rx_pair4_t<TANF>(m[j], m[j | (1 << b)], rt);
+                }
+            }
+            if (PHASE && p == PL) {  // the cost diagonal: its gamma term, then D^dagger
+                const uint64_t sv = L.s[t];
+                const uint32_t y0 = 2u * (tile_base(tile0 + (uint32_t)sub) | off(it_of(p)));
+                const uint64_t ev0 = ev_of(L, y0), ev1 = evk[8];
+                const uint32_t p0 = (uint32_t)__popc(y0 & zmD) ^ L.zc[t];
+                const uint32_t p1 = p0 ^ (zmD & 1u);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int k0 = __popcll(ev0 ^ evk[j] ^ sv), k1 = __popcll(ev0 ^ ev1 ^ evk[j] ^ sv);
+                    accg += (float)k0 * (m[j].x * a[j].y - m[j].y * a[j].x);
+                    accg += (float)k1 * (m[j].z * a[j].w - m[j].w * a[j].z);
+                    const float2 f0 = __ldg(L.phase + k0), f1 = __ldg(L.phase + k1);
+                    const float g0 = ((p0 ^ (pjD >> j)) & 1u) ? -1.0f : 1.0f;
+                    const float g1 = ((p1 ^ (pjD >> j)) & 1u) ? -1.0f : 1.0f;
+                    const float2 d0 = make_float2(f0.x * g0, -f0.y * g0), d1 = make_float2(f1.x * g1, -f1.y * g1);
+                    cmul_inplace(a[j].x, a[j].y, d0);
+                    cmul_inplace(a[j].z, a[j].w, d1);
+                    cmul_inplace(m[j].x, m[j].y, d0);
+                    cmul_inplace(m[j].z, m[j].w, d1);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {  // back to the slots this thread read
+                bp[st + A::slot(A::ij(p, j))] = a[j];
+                bp[kAdjSlots + st + A::slot(A::ij(p, j))] = m[j];
+            }
+            __syncthreads();
+        }
+        const uint32_t tbs = tile_base(tile0 + (uint32_t)sub);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t i = tid | ((uint32_t)k << 7);
+            const uint32_t o = tbs + off_t + off((uint32_t)k << 7);
+            p4[o] = bp[A::slot(i)];
+            l4[o] = bp[kAdjSlots + A::slot(i)];
+        }
+        __syncthreads();  // the buffer's reads are done before the next copy into it
+    }
+    const float acc2[2] = {accb, accg};
+    const int par2[2] = {pbeta, pgamma};
+    adj_finish_n<4, PHASE ? 2 : 1>(v, t, blockIdx.x, gridDim.x, acc2, grad, par2, nparam);
+}
+
 // Readout of psi_x = i^k * D * phi_{x xor F} in the true basis (debug path).
 __global__ void __launch_bounds__(kThreads) k_readout(BatchView v, float2 *out) {
     const int t = blockIdx.y;
@@ -3926,6 +4231,50 @@ cudaError_t launch_adj_mixer(const BatchView &v, float2 *lam, const LayerView &L
     }
 #undef QN_ADJM
     return cudaGetLastError();
+}
+
+template <bool HAS0, int NB, bool PHASE>
+static cudaError_t adj_win_launch(const BatchView &v, float2 *lam, const LayerView &L, int q_lo, double *grad,
+                                  int pbeta, int pgamma, int nparam, cudaStream_t s) {
+    static const cudaError_t attr = [] {
+        cudaError_t e = cudaFuncSetAttribute(k_adj_win<HAS0, NB, PHASE, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_adj_win<HAS0, NB, PHASE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kAdjSmem);
+        return e;
+    }();
+    if (attr != cudaSuccess) return attr;
+    const int ntiles = 1 << (v.n - 11);
+    const int blocks = ntiles < kAdjSubs ? 1 : ntiles / kAdjSubs;
+    if (blocks > v.tiles) return cudaErrorInvalidValue;  // partials hold v.tiles per trajectory
+    const dim3 grid((unsigned)blocks, (unsigned)v.b);
+    if (std::fabs(L.cb) >= std::fabs(L.sb))
+        k_adj_win<HAS0, NB, PHASE, true><<<grid, 128, kAdjSmem, s>>>(v, lam, L, q_lo, grad, pbeta, pgamma, nparam);
+    else
+        k_adj_win<HAS0, NB, PHASE, false><<<grid, 128, kAdjSmem, s>>>(v, lam, L, q_lo, grad, pbeta, pgamma, nparam);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_win(const BatchView &v, float2 *lam, const LayerView &L, int q_lo, int m, bool phase,
+                           double *grad, int pbeta, int pgamma, int nparam, cudaStream_t s) {
+    if (v.n < 12 || v.n > 30) return cudaErrorInvalidValue;
+    if (q_lo == 0) {
+        if (m != 10 || phase) return cudaErrorInvalidValue;
+        return adj_win_launch<true, 9, false>(v, lam, L, 0, grad, pbeta, pgamma, nparam, s);
+    }
+    if (q_lo < 10 || m < 2 || m > 6 || q_lo + m > v.n) return cudaErrorInvalidValue;
+#define QN_ADJW(NB)                                                                                  \
+    return phase ? adj_win_launch<false, NB, true>(v, lam, L, q_lo, grad, pbeta, pgamma, nparam, s) \
+                 : adj_win_launch<false, NB, false>(v, lam, L, q_lo, grad, pbeta, pgamma, nparam, s)
+    switch (m) {
+    case 2: QN_ADJW(2);
+    case 3: QN_ADJW(3);
+    case 4: QN_ADJW(4);
+    case 5: QN_ADJW(5);
+    default: QN_ADJW(6);
+    }
+#undef QN_ADJW
 }
 
 cudaError_t launch_adj_phase(const BatchView &v, float2 *lam, const LayerView &L, double *grad, int param, int nparam,

@@ -152,13 +152,17 @@ def test_autograd_two_forwards_on_one_batch(qn):
     np.testing.assert_allclose(b2.grad.numpy(), 3.0 * ref[1][1], rtol=1e-12, atol=1e-14)
 
 
-@pytest.mark.parametrize("n,p,d", [(2, 2, 1), (3, 2, 2), (5, 2, 4), (8, 3, 3), (9, 2, 4), (13, 2, 4), (16, 2, 3)])
+@pytest.mark.parametrize("n,p,d", [(2, 2, 1), (3, 2, 2), (5, 2, 4), (8, 3, 3), (9, 2, 4), (11, 2, 4), (12, 2, 3),
+                                   (13, 2, 4), (14, 2, 3), (15, 2, 4), (16, 2, 3), (17, 1, 4)])
 def test_fused_adjoint_matches_per_gate_adjoint_and_oracle(qn, n, p, d):
-    """The fused adjoint (the reverse of a layer's mixer in windows of two to four qubits,
-    its cost diagonal in one sweep: what the default fused mode runs) against the one
-    reverse sweep per gate (fusion off) on the same trajectories, and against CRN finite
-    differences of the oracle.  The windows cover every width: the qubit-0 window alone
-    (n = 2, 3), a single-qubit window (n = 5), windows of two and three, n = 16."""
+    """The fused adjoint (what the default fused mode runs) against the one reverse sweep
+    per gate (fusion off) on the same trajectories, and against CRN finite differences of
+    the oracle.  Below 12 qubits the reverse takes a layer's mixer in register windows of
+    two to four qubits and its cost diagonal in a sweep of its own: the qubit-0 window
+    alone (n = 2, 3), a single-qubit window (n = 5), windows of two and three (n = 8-11).
+    From 12 on it takes tiles through shared memory: qubits 0-9, then windows of two to
+    six qubits, the last with the cost diagonal (n = 12-16: one window of 2-6; n = 17:
+    4 + 3)."""
     if n == 2:  # the one-edge graph
         w = W.Workload("fadj_n2", 2, np.array([[0, 1]], np.int32), p, *W.angles(p, 4462), 1e-2, 3e-2, 0.0, 32, 32,
                        W.PHILOX_SEED_BASE + 42)
@@ -177,3 +181,20 @@ def test_fused_adjoint_matches_per_gate_adjoint_and_oracle(qn, n, p, d):
     assert np.abs(res[True][0][:8] - fg).max() < tol
     assert np.abs(res[True][1][:8] - fb).max() < tol
     assert np.abs(fg).max() + np.abs(fb).max() > 0.05  # non-trivial gradients
+
+
+def test_tiled_adjoint_two_windows_n20(qn):
+    """n = 20 (qubits 0-9, then two windows of five: a plain one and the one with the
+    cost diagonal), 64 trajectories over two launch batches: the fused adjoint against
+    the one reverse sweep per gate on the same trajectories."""
+    w = W.qaoa_workload("fadj_n20", 20, 2, index=60, trajectories=64, batch=32, p1=1e-2, p2=3e-2)
+    res = {}
+    for fusion in (True, False):
+        with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+            b.set_fusion(fusion)
+            b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+            res[fusion] = b.grad_traj(0, w.trajectories)
+    tol = 8 * U32 * w.gate_count * len(w.edges) + 1e-4
+    for k in range(2):
+        assert np.abs(res[True][k] - res[False][k]).max() < tol, (k, np.abs(res[True][k] - res[False][k]).max())
+    assert np.abs(res[False][0]).max() + np.abs(res[False][1]).max() > 0.05
