@@ -385,7 +385,8 @@ def gradient_leg(qn, args, stream, local):
             "dC_dgamma": [float(x) for x in dg], "dC_dbeta": [float(x) for x in db], "clocks": clocks.summary(),
             "config": config_of(w, {"steps": steps, "warmup": warmup,
                                     "step": "qn_run_qaoa (fused layers) + qn_grad (fused adjoint: a layer's mixer "
-                                            "reversed in windows of 2-4 qubits, its cost diagonal in one sweep)"})}
+                                            "reversed in tiles of psi and lambda through shared memory, qubits 0-9 "
+                                            "then windows of up to 6, the cost diagonal in the last window's sweep)"})}
 
 
 def gpu_arm(args):
