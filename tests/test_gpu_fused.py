@@ -152,3 +152,28 @@ def test_fused_at_size_n24_sampled_against_oracle(qn):
     print(json.dumps({"fused_n24": {"max_abs_amp_err": err, "max_abs_c_err": c_err, "E": E}}))
     assert err < 1e-5
     assert c_err < 2e-5
+
+
+def test_fused_tiled_windows_n22_sampled_against_oracle(qn):
+    """n=22, p=2 (3-regular, depolarizing p1=2e-2 / p2=5e-2): windows (0, 8), (8, 7), (15, 7), so the
+    tiled sweep of a 7-qubit window runs in all three forms -- plain (qubits 8-14), with the next
+    layer's phase (qubits 15-21, layer 0) and with the final norms (layer 1).  Two trajectories of an
+    8-trajectory ensemble (global ids 3 and 4) against the oracle, amplitude by amplitude."""
+    w = W.qaoa_workload("fused_n22", 22, 2, index=5, trajectories=8, batch=8, p1=2e-2, p2=5e-2)
+    assert fused_windows(22) == [(0, 8), (8, 7), (15, 7)]
+    t0, cnt = 3, 2
+    with qn.Batch(w.n, w.trajectories, w.seed, launch_batch=w.batch) as b:
+        b.set_fusion(True)
+        b.run_qaoa(w.edges, w.gammas, w.betas, **w.noise_kwargs())
+        info = b.run_info()
+        dbg = b.traj_debug(t0, cnt)
+    assert info["sweep_bytes"] == 16.0 * 2 ** w.n * w.trajectories * w.p * 3
+    gates, G = oracle.qaoa_gates(w.n, w.edges, w.gammas, w.betas)
+    ref = oracle.traj_run(w.n, w.edges, gates, G, oracle.make_noise(**w.noise_kwargs()), w.seed, t0, cnt,
+                          threads=cnt)
+    np.testing.assert_array_equal(dbg["branches"], ref["branches"])
+    err = float(np.abs(dbg["amps"] - ref["amps"]).max())
+    c_err = float(np.abs(dbg["c_traj"] - ref["c_traj"]).max())
+    print(json.dumps({"fused_n22": {"max_abs_amp_err": err, "max_abs_c_err": c_err}}))
+    assert err < 1e-5
+    assert c_err < 2e-5
