@@ -774,6 +774,7 @@ LayerView layer_view(const qn_batch *h, int l) {
     L.mf = h->fl_u + ((size_t)l * 4 + 3) * B;
     L.cb = (float)std::cos(h->betas[l]);
     L.sb = (float)std::sin(h->betas[l]);
+    L.num_edges = E;
     return L;
 }
 

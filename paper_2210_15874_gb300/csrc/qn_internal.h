@@ -213,6 +213,7 @@ struct LayerView {
     uint32_t *zm, *zc;       // [b] Z parts of the cost layer's Paulis: mask and frame parity
     uint32_t *mz, *mf;       // [b] mixer: Z part of each qubit's Pauli, frame bit at its gate
     float cb, sb;            // cos beta, sin beta of the layer
+    int32_t num_edges;       // E (at most 64)
 };
 
 #if defined(__CUDACC__)

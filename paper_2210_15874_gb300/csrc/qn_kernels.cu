@@ -2922,20 +2922,27 @@ __device__ __forceinline__ void cmul_inplace(float &re, float &im, float2 w) {
     im = i;
 }
 
-// The cost layer's factor at y = y0 | yk with disjoint bits, from EV(y0), EV(yk)
-// and the Z parity of y0 (both the edge-difference vector and the parity are
-// linear in y): layer_phase split into a per-thread and a per-pattern part.
-__device__ __forceinline__ float2 split_phase(const LayerView &L, uint64_t ev0, uint64_t evk, uint64_t sv, uint32_t zp0,
-                                              uint32_t yk, uint32_t zm) {
-    const int k = __popcll(ev0 ^ evk ^ sv);
-    const float2 ph = __ldg(L.phase + k);
-    const float sg = ((zp0 ^ __popc(yk & zm)) & 1u) ? -1.0f : 1.0f;
-    return make_float2(ph.x * sg, ph.y * sg);
-}
-
 __device__ __forceinline__ uint64_t ev_of(const LayerView &L, uint32_t y) {
     return __ldg(L.ev + (y & 255u)) ^ __ldg(L.ev + 256 + ((y >> 8) & 255u)) ^ __ldg(L.ev + 512 + ((y >> 16) & 255u)) ^
            __ldg(L.ev + 768 + (y >> 24));
+}
+
+// The cost layer's phase table in shared memory with the Z sign folded in:
+// ph2[2k + s] = (-1)^s e^{-i gamma k} (CONJ: its conjugate), k = 0 .. E, so that an
+// amplitude's factor is one shared load at (popc(EV(y) ^ s) << 1) | (Z parity of y).
+constexpr int kPh2 = 2 * 65;
+template <bool CONJ = false>
+__device__ __forceinline__ void load_phase2(const LayerView &L, float2 *ph2, int nthreads) {
+    for (int i = threadIdx.x; i < 2 * (L.num_edges + 1); i += nthreads) {
+        const float2 f = __ldg(L.phase + (i >> 1));
+        const float sg = (i & 1) ? -1.0f : 1.0f;
+        ph2[i] = make_float2(f.x * sg, CONJ ? -f.y * sg : f.y * sg);
+    }
+}
+// e: EV of the thread's part of y xor the frame's edge flips; evk: EV of the element's part;
+// par: the Z parity of y (bit 0)
+__device__ __forceinline__ float2 phase2(const float2 *ph2, uint64_t e, uint64_t evk, uint32_t par) {
+    return ph2[(__popcll(e ^ evk) << 1) | (par & 1u)];
 }
 
 // One fused sweep over a window of M = HAS0 + LQ + RQ qubits.  A fibre is the
@@ -2973,10 +2980,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
     const int rs = wlo + LQ;
     const int64_t nfib = nf >> DB;
     __shared__ uint64_t evk[NE + 1];  // EV of each register element's offset; [NE]: EV of bit 0
+    __shared__ float2 ph2p[PRE ? kPh2 : 1], ph2q[POST ? kPh2 : 1];  // the layers' phase tables
+    uint32_t pkp = 0, pkq = 0;  // bit k: the Z parity of register element k's offset (layers Lp, Lq)
     if (PRE || POST) {
         const LayerView &L = PRE ? Lp : Lq;  // the edge tables are the graph's, the same in every layer
         if ((int)threadIdx.x < NE) evk[threadIdx.x] = ev_of(L, 2u * ((uint32_t)threadIdx.x << rs));
         if ((int)threadIdx.x == NE) evk[NE] = ev_of(L, 1u);
+        if (PRE) load_phase2(Lp, ph2p, kThreads);
+        if (POST) load_phase2(Lq, ph2q, kThreads);
+        const uint32_t zmp = PRE ? Lp.zm[blockIdx.y] : 0u, zmq = POST ? Lq.zm[blockIdx.y] : 0u;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            const uint32_t yk = 2u * ((uint32_t)k << rs);
+            pkp |= ((uint32_t)__popc(yk & zmp) & 1u) << k;
+            pkq |= ((uint32_t)__popc(yk & zmq) & 1u) << k;
+        }
         __syncthreads();
     }
     float4 *p4 = reinterpret_cast<float4 *>(v.psi + ((size_t)t << n));
@@ -3033,16 +3051,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
         if (!ok) continue;
         const uint32_t y0 = (uint32_t)(2 * fbase);
         if (PRE) {
-            const uint64_t sv = Lp.s[t];
             const uint32_t zm = Lp.zm[t];
-            const uint64_t ev0 = ev_of(Lp, y0);
-            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lp.zc[t];
-            const uint64_t ev1 = evk[NE];
+            const uint64_t e0 = ev_of(Lp, y0) ^ Lp.s[t], e1 = e0 ^ evk[NE];
+            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lp.zc[t], zp1 = zp0 ^ (zm & 1u);
 #pragma unroll
             for (int k = 0; k < NE; ++k) {
-                const uint32_t yk = 2u * ((uint32_t)k << rs);
-                cmul_inplace(val[k].x, val[k].y, split_phase(Lp, ev0, evk[k], sv, zp0, yk, zm));
-                cmul_inplace(val[k].z, val[k].w, split_phase(Lp, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
+                cmul_inplace(val[k].x, val[k].y, phase2(ph2p, e0, evk[k], zp0 ^ (pkp >> k)));
+                cmul_inplace(val[k].z, val[k].w, phase2(ph2p, e1, evk[k], zp1 ^ (pkp >> k)));
             }
         }
         if (HAS0) {
@@ -3093,16 +3108,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_sweep(BatchView v, LayerV
             }
         }
         if (POST) {
-            const uint64_t sv = Lq.s[t];
             const uint32_t zm = Lq.zm[t];
-            const uint64_t ev0 = ev_of(Lq, y0);
-            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lq.zc[t];
-            const uint64_t ev1 = evk[NE];
+            const uint64_t e0 = ev_of(Lq, y0) ^ Lq.s[t], e1 = e0 ^ evk[NE];
+            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lq.zc[t], zp1 = zp0 ^ (zm & 1u);
 #pragma unroll
             for (int k = 0; k < NE; ++k) {
-                const uint32_t yk = 2u * ((uint32_t)k << rs);
-                cmul_inplace(val[k].x, val[k].y, split_phase(Lq, ev0, evk[k], sv, zp0, yk, zm));
-                cmul_inplace(val[k].z, val[k].w, split_phase(Lq, ev0 ^ ev1, evk[k], sv, zp0, yk | 1u, zm));
+                cmul_inplace(val[k].x, val[k].y, phase2(ph2q, e0, evk[k], zp0 ^ (pkq >> k)));
+                cmul_inplace(val[k].z, val[k].w, phase2(ph2q, e1, evk[k], zp1 ^ (pkq >> k)));
             }
         }
 #pragma unroll
@@ -3139,6 +3151,7 @@ template <bool TANF, bool PRE>
 __global__ void __launch_bounds__(128, 3) k_fused_tile12(BatchView v, LayerView Lp, LayerView Lr) {
     extern __shared__ float4 t12_buf[];  // [2][2048]
     __shared__ uint64_t evk[17];         // PRE: EV of the phase-A register offsets 2j; [16]: EV of bit 0
+    __shared__ float2 ph2[PRE ? kPh2 : 1];  // PRE: layer Lp's phase table
     const int t = blockIdx.y;
     const uint32_t tid = threadIdx.x;
     const float4 *q4 = reinterpret_cast<const float4 *>(v.psi + ((size_t)t << v.n));
@@ -3146,9 +3159,14 @@ __global__ void __launch_bounds__(128, 3) k_fused_tile12(BatchView v, LayerView 
     const int ntiles = 1 << (v.n - 12);
     const int nsubs = ntiles < kT12Subs ? ntiles : kT12Subs;
     const uint32_t tile0 = (uint32_t)blockIdx.x * (uint32_t)nsubs;
+    uint32_t pk = 0;  // PRE: bit j, the Z parity of the phase-A register offset 2j
     if (PRE) {
         if (tid < 16u) evk[tid] = ev_of(Lp, 2u * tid);
         if (tid == 16u) evk[16] = ev_of(Lp, 1u);
+        load_phase2(Lp, ph2, 128);
+        const uint32_t zm = Lp.zm[t];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) pk |= ((uint32_t)__popc((2u * (uint32_t)j) & zm) & 1u) << j;
     }
     const float cb = Lr.cb, sb = Lr.sb;
     const float rt = TANF ? sb / cb : cb / sb, rsc = TANF ? cb : sb;
@@ -3184,17 +3202,14 @@ __global__ void __launch_bounds__(128, 3) k_fused_tile12(BatchView v, LayerView 
 #pragma unroll
         for (int j = 0; j < 16; ++j) x[j] = buf[sw((uint32_t)j | (tid << 4))];
         if (PRE) {
-            const uint64_t sv = Lp.s[t];
             const uint32_t zm = Lp.zm[t];
             const uint32_t y0 = 2u * (tb | (tid << 4));
-            const uint64_t ev0 = ev_of(Lp, y0);
-            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lp.zc[t];
-            const uint64_t ev1 = evk[16];
+            const uint64_t e0 = ev_of(Lp, y0) ^ Lp.s[t], e1 = e0 ^ evk[16];
+            const uint32_t zp0 = (uint32_t)__popc(y0 & zm) ^ Lp.zc[t], zp1 = zp0 ^ (zm & 1u);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const uint32_t yk = 2u * (uint32_t)j;
-                cmul_inplace(x[j].x, x[j].y, split_phase(Lp, ev0, evk[j], sv, zp0, yk, zm));
-                cmul_inplace(x[j].z, x[j].w, split_phase(Lp, ev0 ^ ev1, evk[j], sv, zp0, yk | 1u, zm));
+                cmul_inplace(x[j].x, x[j].y, phase2(ph2, e0, evk[j], zp0 ^ (pk >> j)));
+                cmul_inplace(x[j].z, x[j].w, phase2(ph2, e1, evk[j], zp1 ^ (pk >> j)));
             }
         }
 #pragma unroll
@@ -3264,6 +3279,7 @@ __global__ void __launch_bounds__(128, 3) k_fused_win(BatchView v, LayerView Lr,
     static_assert(M >= 4 && M <= 7, "windows of 4 to 7 qubits");
     extern __shared__ float4 win_buf[];  // [2][2048]
     __shared__ uint64_t evk[17];         // kWinPost: EV of the last phase's register offsets; [16]: EV of bit 0
+    __shared__ float2 ph2[MODE == kWinPost ? kPh2 : 1];  // kWinPost: layer Lq's phase table
     const int t = blockIdx.y;
     const uint32_t tid = threadIdx.x;
     const int w = q_lo - 1;
@@ -3302,6 +3318,7 @@ __global__ void __launch_bounds__(128, 3) k_fused_win(BatchView v, LayerView Lr,
     if (MODE == kWinPost) {
         if (tid < 16u) evk[tid] = ev_of(Lq, 2u * off(ij_last((int)tid)));
         if (tid == 16u) evk[16] = ev_of(Lq, 1u);
+        load_phase2(Lq, ph2, 128);
     }
     auto rot = [&](float4 *x, int bit) {  // exp(-i beta X) on register bit `bit`
 #pragma unroll
@@ -3356,19 +3373,14 @@ __global__ void __launch_bounds__(128, 3) k_fused_win(BatchView v, LayerView Lr,
             for (int b = LJ; b < 4; ++b) rot(x, b);
         }
         if (MODE == kWinPost) {  // the next layer's phase, with the row signs folded into its sign
-            const uint64_t sv = Lq.s[t];
             const uint32_t y0 = 2u * (tile_base(tile0 + (uint32_t)sub) | off(it_last));
-            const uint64_t ev0 = ev_of(Lq, y0), ev1 = evk[16];
+            const uint64_t e0 = ev_of(Lq, y0) ^ Lq.s[t], e1 = e0 ^ evk[16];
             const uint32_t p0 = (uint32_t)__popc(y0 & zmq) ^ Lq.zc[t] ^ pt;
             const uint32_t p1 = p0 ^ (zmq & 1u);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float2 f0 = __ldg(Lq.phase + __popcll(ev0 ^ evk[j] ^ sv));
-                const float2 f1 = __ldg(Lq.phase + __popcll(ev0 ^ ev1 ^ evk[j] ^ sv));
-                const float g0 = ((p0 ^ (pj >> j)) & 1u) ? -1.0f : 1.0f;
-                const float g1 = ((p1 ^ (pj >> j)) & 1u) ? -1.0f : 1.0f;
-                cmul_inplace(x[j].x, x[j].y, make_float2(f0.x * g0, f0.y * g0));
-                cmul_inplace(x[j].z, x[j].w, make_float2(f1.x * g1, f1.y * g1));
+                cmul_inplace(x[j].x, x[j].y, phase2(ph2, e0, evk[j], p0 ^ (pj >> j)));
+                cmul_inplace(x[j].z, x[j].w, phase2(ph2, e1, evk[j], p1 ^ (pj >> j)));
             }
         } else {
 #pragma unroll
@@ -3658,7 +3670,8 @@ constexpr size_t kAdjSmem = 2 * 2 * kAdjSlots * sizeof(float4);  // [buffer][psi
 // in phase 0).
 // With PHASE the last phase adds k(y) Im(conj(m) a) to d<C>_t/d gamma and applies
 // D(y)^dagger.  The terms of the other windows' qubits are unaffected (their rotations
-// commute with X_q).  Tiles stream through two buffers (cp.async, one tile ahead).
+// commute with X_q).  Tiles stream through two buffers (cp.async, one tile ahead); the last
+// phase stores its registers to HBM.
 // Grid (blocks of kAdjSubs tiles, trajectories) x 128 threads.
 template <bool HAS0, int NB, bool PHASE, bool TANF>
 __global__ void __launch_bounds__(128, 3) k_adj_win(BatchView v, float2 *lam, LayerView L, int q_lo, double *grad,
@@ -3667,6 +3680,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_win(BatchView v, float2 *lam, La
     constexpr int RL = A::L;
     extern __shared__ float4 adj_buf[];  // [2][2][kAdjSlots]
     __shared__ uint64_t evk[9];          // PHASE: EV of the last phase's register offsets; [8]: EV of bit 0
+    __shared__ float2 ph2[PHASE ? kPh2 : 1];  // PHASE: the conjugate phase table of layer L
     const int t = blockIdx.y;
     const uint32_t tid = threadIdx.x;
     const int w = HAS0 ? 0 : q_lo - 1;
@@ -3716,6 +3730,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_win(BatchView v, float2 *lam, La
         for (int j = 0; j < 8; ++j) pjD |= ((uint32_t)__popc(2u * off(A::ij(PL, j)) & zmD) & 1u) << j;
         if (tid < 8u) evk[tid] = ev_of(L, 2u * off(A::ij(PL, (int)tid)));
         if (tid == 8u) evk[8] = ev_of(L, 1u);
+        load_phase2<true>(L, ph2, 128);
     }
     const uint32_t off_t = off(tid);  // index order: i = tid | k << 7
     auto fetch = [&](int sub) {
@@ -3820,40 +3835,39 @@ __global__ void __launch_bounds__(128, 3) k_adj_win(BatchView v, float2 *lam, La
                 }
             }
             if (PHASE && p == PL) {  // the cost diagonal: its gamma term, then D^dagger
-                const uint64_t sv = L.s[t];
                 const uint32_t y0 = 2u * (tile_base(tile0 + (uint32_t)sub) | off(it_of(p)));
-                const uint64_t ev0 = ev_of(L, y0), ev1 = evk[8];
+                const uint64_t e0 = ev_of(L, y0) ^ L.s[t], e1 = e0 ^ evk[8];
                 const uint32_t p0 = (uint32_t)__popc(y0 & zmD) ^ L.zc[t];
                 const uint32_t p1 = p0 ^ (zmD & 1u);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int k0 = __popcll(ev0 ^ evk[j] ^ sv), k1 = __popcll(ev0 ^ ev1 ^ evk[j] ^ sv);
+                    const uint32_t k0 = (uint32_t)__popcll(e0 ^ evk[j]), k1 = (uint32_t)__popcll(e1 ^ evk[j]);
                     accg += (float)k0 * (m[j].x * a[j].y - m[j].y * a[j].x);
                     accg += (float)k1 * (m[j].z * a[j].w - m[j].w * a[j].z);
-                    const float2 f0 = __ldg(L.phase + k0), f1 = __ldg(L.phase + k1);
-                    const float g0 = ((p0 ^ (pjD >> j)) & 1u) ? -1.0f : 1.0f;
-                    const float g1 = ((p1 ^ (pjD >> j)) & 1u) ? -1.0f : 1.0f;
-                    const float2 d0 = make_float2(f0.x * g0, -f0.y * g0), d1 = make_float2(f1.x * g1, -f1.y * g1);
+                    const float2 d0 = ph2[(k0 << 1) | ((p0 ^ (pjD >> j)) & 1u)];
+                    const float2 d1 = ph2[(k1 << 1) | ((p1 ^ (pjD >> j)) & 1u)];
                     cmul_inplace(a[j].x, a[j].y, d0);
                     cmul_inplace(a[j].z, a[j].w, d1);
                     cmul_inplace(m[j].x, m[j].y, d0);
                     cmul_inplace(m[j].z, m[j].w, d1);
                 }
             }
+            if (p < PL) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {  // back to the slots this thread read
-                bp[st + A::slot(A::ij(p, j))] = a[j];
-                bp[kAdjSlots + st + A::slot(A::ij(p, j))] = m[j];
+                for (int j = 0; j < 8; ++j) {  // back to the slots this thread read
+                    bp[st + A::slot(A::ij(p, j))] = a[j];
+                    bp[kAdjSlots + st + A::slot(A::ij(p, j))] = m[j];
+                }
+                __syncthreads();
+            } else {  // the last phase stores to HBM: a warp's lanes cover tile bits 0-4 (runs of >= 256 bytes)
+                const uint32_t ob = tile_base(tile0 + (uint32_t)sub) + off(it_of(p));
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t o = ob + off(A::ij(p, j));
+                    p4[o] = a[j];
+                    l4[o] = m[j];
+                }
             }
-            __syncthreads();
-        }
-        const uint32_t tbs = tile_base(tile0 + (uint32_t)sub);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t i = tid | ((uint32_t)k << 7);
-            const uint32_t o = tbs + off_t + off((uint32_t)k << 7);
-            p4[o] = bp[A::slot(i)];
-            l4[o] = bp[kAdjSlots + A::slot(i)];
         }
         __syncthreads();  // the buffer's reads are done before the next copy into it
     }
