@@ -47,3 +47,19 @@ def test_clock_sampler_without_samples():
     assert s.summary()["reasons"] == ["nvidia-smi unavailable"]
     s.proc = object()  # started, but nothing arrived within the timed region
     assert s.summary()["reasons"] == ["no sample: timed region under 200 ms"]
+
+
+def test_sweep_counts_follow_the_window_schedules():
+    """bench.py's byte counts use the library's window schedules: the fused forward layers
+    (the window list the GPU test mirrors) and the tiled adjoint (qubits 0-9, then windows of
+    at most six, the cost diagonal on the last; below 12 qubits register windows of 2-4 plus a
+    diagonal sweep)."""
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import bench
+    from test_gpu_fused import fused_windows
+
+    for n in range(2, 33):
+        assert bench.fused_window_count(n) == len(fused_windows(n)), n
+    assert [bench.fused_window_count(n) for n in (16, 20, 26, 30)] == [2, 3, 3, 4]
+    assert [bench.adjoint_window_count(n) for n in (8, 10, 11, 12, 16, 17, 22, 23)] == [4, 4, 5, 2, 2, 3, 3, 4]
