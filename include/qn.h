@@ -280,6 +280,23 @@ qn_status qn_run_info(const qn_batch *h, int64_t *gates, int64_t *launches, doub
 qn_status qn_group_plan(int32_t n, const qn_graph *graph, int32_t p, int32_t capacity, int32_t *kind,
                         int32_t *first_gate, int32_t *gates, uint32_t *qubit_mask, int32_t *count);
 
+/* The window schedule of the fused layers with Pauli-only noise -- a view of
+ * the schedule qn_run_qaoa and qn_grad use (no counterpart in the paper; host
+ * only, no device memory).  reverse = 0: the FP32 forward windows of one
+ * layer, each one sweep with the cost diagonal folded into a sweep (below 10
+ * qubits five per window; from 10 on qubits 0-11 or 0-7 first, the one that
+ * leaves fewer windows, then balanced windows of at most 7).  reverse = 1: the
+ * mixer windows of the fused adjoint of one layer (from 12 qubits on qubits
+ * 0-9, then balanced windows of at most 6, the last of which also undoes the
+ * cost diagonal; below 12 qubits 0 .. min(4, n)-1, then windows of two or
+ * three, followed by a sweep of its own for the diagonal).  Writes up to
+ * `capacity` windows (first qubit, qubits) in sweep order; *count is the
+ * number of windows, also when it exceeds capacity.  The output arrays may be
+ * NULL when capacity is 0.  QN_EINVAL unless 2 <= n <= 30 and reverse is 0 or
+ * 1. */
+qn_status qn_fused_windows(int32_t n, int32_t reverse, int32_t capacity, int32_t *q_lo, int32_t *qubits,
+                           int32_t *count);
+
 /* Tile map of the sweep of the mixer block on qubits q_lo .. q_lo + m - 1
  * whose next block has m_next qubits (q_lo + m .. q_lo + m + m_next - 1; 0:
  * no next block) -- exposed for tests (no counterpart in the paper; host

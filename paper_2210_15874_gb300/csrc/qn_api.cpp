@@ -2126,6 +2126,22 @@ qn_status qn_group_plan(int32_t n, const qn_graph *graph, int32_t p, int32_t cap
     return ok();
 }
 
+qn_status qn_fused_windows(int32_t n, int32_t reverse, int32_t capacity, int32_t *q_lo, int32_t *qubits,
+                           int32_t *count) {
+    if (!count) return fail(QN_EINVAL, "count is NULL");
+    if (n < 2 || n > kMaxQubits) return fail(QN_EINVAL, "n = %d outside [2, %d]", n, kMaxQubits);
+    if (reverse != 0 && reverse != 1) return fail(QN_EINVAL, "reverse must be 0 or 1");
+    if (capacity < 0 || (capacity > 0 && (!q_lo || !qubits))) return fail(QN_EINVAL, "bad output arrays");
+    const std::vector<std::pair<int, int>> w = reverse ? (n >= 12 ? adj_tile_windows(n) : adj_windows(n))
+                                                       : fused_windows(n);
+    for (size_t i = 0; i < w.size() && (int32_t)i < capacity; ++i) {
+        q_lo[i] = w[i].first;
+        qubits[i] = w[i].second;
+    }
+    *count = (int32_t)w.size();
+    return ok();
+}
+
 qn_status qn_mix_tile_map(int32_t n, int32_t q_lo, int32_t m, int32_t m_next, int8_t *lane_bits, int8_t *a_bits,
                           int8_t *b_bits, int8_t *tile_bits, int32_t *ntile) {
     if (!lane_bits || !a_bits || !b_bits || !tile_bits || !ntile) return fail(QN_EINVAL, "an output is NULL");

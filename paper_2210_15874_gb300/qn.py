@@ -65,6 +65,7 @@ _SIGS = {
                                     c_i32, c_vp, c_vp, c_vp, c_vp]),
     "qn_group_plan": (c_i32, [c_i32, P(qn_graph), c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, P(c_i32)]),
     "qn_mix_tile_map": (c_i32, [c_i32, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, P(c_i32)]),
+    "qn_fused_windows": (c_i32, [c_i32, c_i32, c_i32, c_vp, c_vp, P(c_i32)]),
     "qn_last_error": (ctypes.c_char_p, []),
     "qn_batch_destroy": (None, [c_vp]),
 }
@@ -299,6 +300,18 @@ def group_plan(n: int, edges, p: int) -> list:
                             ctypes.byref(cnt)), "qn_group_plan")
     return [dict(kind=int(k[i]), first_gate=int(f[i]), gates=int(m[i]),
                  qubits=[b for b in range(n) if (int(q[i]) >> b) & 1]) for i in range(cnt.value)]
+
+
+def fused_windows(n: int, reverse: bool = False) -> list:
+    """The fused layers' window schedule (host only): (first qubit, qubits) per sweep of one
+    layer, forward or, with reverse, the fused adjoint's mixer windows."""
+    cnt = c_i32()
+    check(qn_fused_windows(n, int(reverse), 0, None, None, ctypes.byref(cnt)), "qn_fused_windows")
+    lo = np.zeros(cnt.value, dtype=np.int32)
+    m = np.zeros(cnt.value, dtype=np.int32)
+    if cnt.value:
+        check(qn_fused_windows(n, int(reverse), cnt.value, _vp(lo), _vp(m), ctypes.byref(cnt)), "qn_fused_windows")
+    return [(int(lo[i]), int(m[i])) for i in range(cnt.value)]
 
 
 def mix_tile_map(n: int, q_lo: int, m: int, m_next: int) -> dict:

@@ -108,3 +108,36 @@ def test_plan_and_map_reject_bad_arguments(qn):
     with pytest.raises(qn.QnError, match="QN_EINVAL"):
         qn.mix_tile_map(20, 16, 4, 4)
     assert qn.group_plan(6, W.ring_graph(6), 0) == []
+
+
+def test_fused_window_schedules(qn):
+    """The library's window schedules of the fused layers (qn_fused_windows): every window
+    list covers the qubits once in order; the forward one equals the rule the GPU test
+    mirrors and the sweep counts the bench's byte figures use; the adjoint's takes qubits
+    0-9 and then at most six per window from 12 qubits on (its last window also undoes the
+    cost diagonal), qubits 0-3 and then two or three per window below."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from test_gpu_fused import fused_windows
+
+    for n in range(2, 31):
+        fw, aw = qn.fused_windows(n), qn.fused_windows(n, reverse=True)
+        for w in (fw, aw):
+            assert [q for lo, m in w for q in range(lo, lo + m)] == list(range(n)), (n, w)
+        assert fw == fused_windows(n), n
+        assert len(fw) == bench.fused_window_count(n), n
+        if n >= 12:
+            assert aw[0] == (0, 10) and all(1 <= m <= 6 for _, m in aw[1:]), (n, aw)
+            assert len(aw) == bench.adjoint_window_count(n) == 1 + -(-(n - 10) // 6), n
+        else:
+            assert aw[0] == (0, min(4, n)) and all(2 <= m <= 3 for _, m in aw[1:]) or n <= 5, (n, aw)
+            assert len(aw) + 1 == bench.adjoint_window_count(n), n  # plus the diagonal's sweep
+    assert qn.fused_windows(16) == [(0, 12), (12, 4)]
+    assert qn.fused_windows(26) == [(0, 12), (12, 7), (19, 7)]
+    assert qn.fused_windows(20) == [(0, 8), (8, 6), (14, 6)]
+    assert qn.fused_windows(16, reverse=True) == [(0, 10), (10, 6)]
+    assert qn.fused_windows(20, reverse=True) == [(0, 10), (10, 5), (15, 5)]
+    for bad in (1, 31):
+        with pytest.raises(qn.QnError, match="QN_EINVAL"):
+            qn.fused_windows(bad)
